@@ -1,0 +1,222 @@
+"""Cell classification and ghost-cell placement (oracle; test infrastructure).
+
+Sec. 3.1.  Cells are fluid (tag 0) or solid (tag 1) by the side of their
+centre (psi >= 0 is solid).  Ghost cells are tagged +2 (centre in the solid)
+or -2 (centre in the fluid).
+
+* CGC  (Sec. 3.1, Fig. 1(a)): a solid cell with at least one fluid cell among
+  its face neighbours (+-x, +-y[, +-z]) is a ghost (+2).  Face adjacency, not
+  diagonal: Fig. 3(b) draws (0.5,2.5) and (2.5,0.5), which touch the fluid
+  only diagonally, as plain solid cells.
+* HGC  (Sec. 3.1, Eqs. delta_n, HGC_criterion): a solid cell with
+  psi <= dn/2 becomes +2 and a fluid cell with -psi < dn/2 becomes -2, where
+  dn = [(n_x/dx)^2 + (n_y/dy)^2 + (n_z/dz)^2]^(-1/2) uses the normal at S and the
+  ghost's own cell widths.  Then the excess candidates are reclassified:
+    pass A: a -2 cell with no face neighbour tagged 1 becomes fluid (0);
+    pass B: a +2 cell with no face neighbour tagged 0 (tags after pass A)
+            becomes solid (1).
+  Each pass reads the tags as they were when the pass began.  "Solid cell"
+  and "fluid cell" in the reclassification are read as the tags 1 and 0; the
+  candidates (+-2) are neither.  Pass A before pass B is the reading taken
+  (the paper lists both without an order); it reproduces Fig. 3(c).
+* CGC_ES (Sec. 7, Eq. stencil_anisotropic): the CGC ghost set with the stencil
+  multipliers r_i = max(1, ceil(2 |n_i psi| / dx_i)); CGC and HGC use r_i = 1.
+
+Only cells with a face neighbour on the other side of the boundary can end as
+ghosts: a fluid cell without a solid neighbour has no neighbour tagged 1 and
+is reset by pass A; a solid cell without a fluid neighbour has no neighbour
+tagged 0 after pass A and is reset by pass B; CGC needs a fluid neighbour by
+definition.  So psi, S and n are evaluated on those "interface" cells only.
+(The brute-force test evaluates every cell and finds the same tags.)
+
+Stencil (Secs. 4-5): e_i = sgn(n_i) with e_i = +1 where n_i = 0 (Appendix A),
+and the stencil members are G + (d_x r_x e_x dx, d_y r_y e_y dy[, d_z r_z e_z dz])
+for the offsets d in the paper's order P_1..P_3 (2D) or P_1..P_7 (3D).
+"""
+
+import numpy as np
+
+from .geometry import Grid, Body, inside, closest_point
+
+HGC, CGC, CGC_ES = "HGC", "CGC", "CGC_ES"
+
+# error codes shared in meaning (not in code) with the library's status values
+E_STENCIL_OOB = "ESTENCIL_OOB"
+E_STENCIL_SOLID = "ESTENCIL_SOLID"
+E_CYCLE = "ECYCLE"
+
+
+class EBRError(Exception):
+    def __init__(self, code, msg=""):
+        super().__init__("%s: %s" % (code, msg))
+        self.code = code
+
+
+def stencil_offsets(dim):
+    """Offsets of P_1.. in units of (r_i e_i dx_i): 2D P1=(1,0), P2=(0,1),
+    P3=(1,1) (Sec. 4); 3D P1..P7 = (1,0,0),(0,1,0),(0,0,1),(1,1,0),(0,1,1),
+    (1,0,1),(1,1,1) (Sec. 5)."""
+    if dim == 2:
+        return [(1, 0), (0, 1), (1, 1)]
+    return [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (0, 1, 1), (1, 0, 1), (1, 1, 1)]
+
+
+class Classification:
+    """Tags for every cell and the ghost records (sorted by linear index)."""
+
+    def __init__(self, grid, body, placement, tags, idx, psi, n, e, r, ties):
+        self.grid = grid
+        self.body = body
+        self.placement = placement
+        self.tags = tags            # int8 [N]
+        self.idx = idx              # int64 [N_g], ascending
+        self.psi = psi              # float64 [N_g]
+        self.n = n                  # float64 [N_g, d]
+        self.e = e                  # int64 [N_g, d]
+        self.r = r                  # int64 [N_g, d]
+        self.ties = ties            # list of (cell index, reason, margin)
+
+    @property
+    def n_ghosts(self):
+        return int(self.idx.size)
+
+
+def _solid_all(grid, body):
+    """Inside predicate for every cell centre, slab by slab to bound memory."""
+    solid = np.zeros(grid.N, dtype=bool)
+    nx = grid.n[0]
+    plane = grid.N // grid.n[-1]
+    for s in range(grid.n[-1]):
+        ids = np.arange(s * plane, (s + 1) * plane, dtype=np.int64)
+        X = grid.centre(grid.unlin(ids))
+        solid[ids] = inside(body, X)
+    del nx
+    return solid
+
+
+def _face_neighbour_any(grid, flag):
+    """For each cell: does any in-grid face neighbour have ``flag`` set?"""
+    f = flag.reshape(grid.n[::-1])          # [(nz,) ny, nx]
+    out = np.zeros_like(f)
+    nd = grid.dim
+    for a in range(nd):
+        ax = nd - 1 - a                      # numpy axis of grid axis a
+        sl_lo = [slice(None)] * nd
+        sl_hi = [slice(None)] * nd
+        sl_lo[ax] = slice(0, -1)
+        sl_hi[ax] = slice(1, None)
+        out[tuple(sl_lo)] |= f[tuple(sl_hi)]     # neighbour at +1
+        out[tuple(sl_hi)] |= f[tuple(sl_lo)]     # neighbour at -1
+    return out.reshape(-1)
+
+
+def delta_n(grid, n):
+    """Eq. delta_n: normal cell thickness for unit normals n [M, d]."""
+    s = np.zeros(n.shape[0])
+    for a in range(grid.dim):
+        q = n[:, a] / grid.h[a]
+        s = s + q * q
+    return 1.0 / np.sqrt(s)
+
+
+def classify(grid, body, placement=HGC, tie_rel=1e-9, cells=None):
+    """Tags and ghost records.  ``cells`` (optional, for the brute-force test)
+    evaluates psi on the given cell set instead of the interface cells."""
+    if isinstance(grid, dict):
+        grid = Grid.from_dict(grid)
+    if isinstance(body, dict):
+        body = Body.from_dict(body)
+    d = grid.dim
+    solid = _solid_all(grid, body)
+    tags = solid.astype(np.int8)
+    iface = (solid & _face_neighbour_any(grid, ~solid)) | (~solid & _face_neighbour_any(grid, solid))
+    if cells is None:
+        cells = np.nonzero(iface)[0]
+    cells = np.asarray(cells, dtype=np.int64)
+    ijk = grid.unlin(cells)
+    X = grid.centre(ijk)
+    psi_c, n_c = closest_point(body, X)
+    sol_c = solid[cells]
+    if not np.array_equal(psi_c >= 0, sol_c):
+        raise AssertionError("inside predicate and psi sign disagree")
+    tol = tie_rel * min(grid.h)
+    ties = []
+    for k in np.nonzero(np.abs(psi_c) < tol)[0]:
+        ties.append((int(cells[k]), "psi~0", float(psi_c[k])))
+    for a in range(d):
+        for k in np.nonzero((n_c[:, a] != 0) & (np.abs(n_c[:, a]) < 1e-12))[0]:
+            ties.append((int(cells[k]), "n%d~0" % a, float(n_c[k, a])))
+
+    if placement in (CGC, CGC_ES):
+        ghost_c = sol_c & _face_neighbour_any(grid, ~solid)[cells]
+        tags[cells[ghost_c]] = 2
+    elif placement == HGC:
+        dn = delta_n(grid, n_c)
+        cand_s = sol_c & (psi_c <= dn / 2)
+        cand_f = (~sol_c) & (-psi_c < dn / 2)
+        for k in np.nonzero(np.abs(np.abs(psi_c) - dn / 2) < tol)[0]:
+            ties.append((int(cells[k]), "psi~dn/2", float(np.abs(psi_c[k]) - dn[k] / 2)))
+        tags[cells[cand_s]] = 2
+        tags[cells[cand_f]] = -2
+        # pass A: -2 without a face neighbour tagged 1 -> 0 (snapshot)
+        has1 = _face_neighbour_any(grid, tags == 1)
+        drop = (tags == -2) & ~has1
+        tags[drop] = 0
+        # pass B: +2 without a face neighbour tagged 0 -> 1 (snapshot after A)
+        has0 = _face_neighbour_any(grid, tags == 0)
+        drop = (tags == 2) & ~has0
+        tags[drop] = 1
+    else:
+        raise ValueError("unknown placement %r" % placement)
+
+    gmask = np.abs(tags[cells]) == 2
+    g_cells = cells[gmask]
+    order = np.argsort(g_cells)
+    g_cells = g_cells[order]
+    psi = psi_c[gmask][order]
+    n = n_c[gmask][order]
+    e = np.where(n >= 0, 1, -1).astype(np.int64)          # sgn(n), 0 -> +1
+    r = np.ones_like(e)
+    if placement == CGC_ES:
+        for a in range(d):
+            q = 2.0 * np.abs(psi * n[:, a]) / grid.h[a]
+            r[:, a] = np.maximum(1, np.ceil(q)).astype(np.int64)
+            near = (q > 1.0 - 1e-9) & (np.abs(q - np.round(q)) < 1e-9)
+            for k in np.nonzero(near)[0]:
+                ties.append((int(g_cells[k]), "r%d ceil" % a, float(q[k])))
+    return Classification(grid, body, placement, tags, g_cells, psi, n, e, r, ties)
+
+
+def stencil_members(cls):
+    """Member cells of every ghost: (ijk [N_g, K, d], in_grid [N_g, K],
+    active [N_g, K]).  A member is active (structurally non-zero weight) when
+    n_i != 0 on every axis along which it is offset (Sec. 3.2: n_i = 0 removes
+    the dependence on neighbours in direction i)."""
+    g = cls.grid
+    d = g.dim
+    offs = np.array(stencil_offsets(d), dtype=np.int64)          # [K, d]
+    gijk = g.unlin(cls.idx)                                        # [N_g, d]
+    step = cls.r * cls.e                                           # [N_g, d]
+    mijk = gijk[:, None, :] + offs[None, :, :] * step[:, None, :]
+    ing = np.ones(mijk.shape[:2], dtype=bool)
+    for a in range(d):
+        ing &= (mijk[:, :, a] >= 0) & (mijk[:, :, a] < g.n[a])
+    active = np.ones(mijk.shape[:2], dtype=bool)
+    for a in range(d):
+        active &= ~((offs[None, :, a] == 1) & (cls.n[:, None, a] == 0.0))
+    return mijk, ing, active
+
+
+def check_stencils(cls):
+    """Every stencil member must lie in the grid and must not be a plain solid
+    cell (tag 1): its value would be undefined.  Raises EBRError."""
+    mijk, ing, _ = stencil_members(cls)
+    if not np.all(ing):
+        g = int(np.nonzero(~ing.all(axis=1))[0][0])
+        raise EBRError(E_STENCIL_OOB, "ghost %d stencil leaves the grid" % int(cls.idx[g]))
+    midx = cls.grid.lin(mijk.reshape(-1, cls.grid.dim)).reshape(ing.shape)
+    bad = cls.tags[midx] == 1
+    if np.any(bad):
+        g = int(np.nonzero(bad.any(axis=1))[0][0])
+        raise EBRError(E_STENCIL_SOLID, "ghost %d stencil contains a solid cell" % int(cls.idx[g]))
+    return midx

@@ -1,0 +1,197 @@
+"""Pins of the oracle's level-by-level fill (Secs. 3.2, 4, 5), boundary
+quantities and forces (Sec. 6), and adjoint, against exactness properties,
+convergence orders, integral identities and finite differences."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_10165_b300 import inputs as I
+
+CASES = [
+    (I.grid(2, [40, 36], [-1.0, -1.0], [1.0, 1.0]), I.ellipse(0.03, -0.02, 0.6, 0.35, 0.7)),
+    (I.grid(2, [96, 48], [-1.0, -1.0], [3.0, 1.0]), I.airfoil(0.0, 0.0, 0.12, 1.0, 5.0)),
+    (I.grid(2, [33, 33], [-1.0, -1.0], [1.0, 1.0]), I.circle(0.0, 0.0, 0.55)),       # n_x = 0 ghosts
+    (I.grid(3, [17, 18, 19], [-1.0, -1.0, -1.0], [1.0, 1.0, 1.0]), I.sphere(0.02, -0.01, 0.03, 0.6)),
+    (I.grid(3, [17, 17, 17], [-1.0, -1.0, -1.0], [1.0, 1.0, 1.0]), I.sphere(0.0, 0.0, 0.0, 0.55)),
+]
+
+
+def _ghost_S(c):
+    X = c.grid.centre(c.grid.unlin(c.idx))
+    return X + c.psi[:, None] * c.n
+
+
+def _setup(case, placement, fields, bcs):
+    gd, bd = CASES[case]
+    c = O.classify(gd, bd, placement)
+    lev = O.build_levels(c)
+    S = _ghost_S(c)[lev.order]
+    nn = c.n[lev.order]
+    arrs = [f.on_grid(gd) for f in fields]
+    bc_data = [I.bc_values(f, k, S, nn) for f, k in zip(fields, bcs)]
+    return gd, c, lev, arrs, bc_data
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
+def test_fill_reproduces_multilinear_fields_everywhere(case, placement):
+    gd, bd = CASES[case]
+    d = gd["dim"]
+    fields = [I.Polynomial(d, 100 + case), I.Polynomial(d, 200 + case)]
+    bcs = [O.DIRICHLET, O.NEUMANN]
+    gd, c, lev, arrs, bc = _setup(case, placement, fields, bcs)
+    if case == 2:
+        assert np.any(c.n[:, 0] == 0.0)   # the n_i = 0 special case is exercised
+    # poison the ghost slots: the fill must overwrite them from valid data only
+    for a in arrs:
+        a[c.idx] = 1e30
+    out = O.fill(c, lev, arrs, bcs, bc)
+    X = c.grid.centre(c.grid.unlin(c.idx))
+    for f, a in zip(fields, out):
+        assert np.max(np.abs(a[c.idx] - f.value(X))) < 1e-12
+        # boundary value and gradient at S are exact too (Sec. 6)
+        ps, gr = O.boundary_quantities(c, lev, a)
+        S = _ghost_S(c)[lev.order]
+        assert np.max(np.abs(ps - f.value(S))) < 1e-11
+        assert np.max(np.abs(gr - f.gradient(S))) < 1e-9
+
+
+def test_fill_second_order_convergence():
+    # smooth field, Dirichlet and Neumann: ghost error O(dx^2).  The maximum
+    # over the ghosts depends on where the cells fall relative to the body, so
+    # it is compared over a 4x refinement (expected factor 16, required > 8).
+    f = I.CylinderU()
+    errs = {}
+    for bc in (O.DIRICHLET, O.NEUMANN):
+        es = []
+        for n in (128, 256, 512):
+            gd = I.grid(2, [n, n], [-2, -2], [2, 2])
+            bd = I.circle(0.0031, 0.0017, 0.5)
+            c = O.classify(gd, bd, "HGC")
+            lev = O.build_levels(c)
+            S = _ghost_S(c)[lev.order]
+            arr = f.on_grid(gd)
+            bcd = I.bc_values(f, bc, S, c.n[lev.order])
+            out = O.fill(c, lev, [arr], [bc], [bcd])[0]
+            X = c.grid.centre(c.grid.unlin(c.idx))
+            es.append(np.max(np.abs(out[c.idx] - f.value(X))))
+        errs[bc] = es
+        assert es[0] / es[2] > 8.0, es
+
+
+def test_perimeter_and_area_of_weights():
+    # sum_G w_G -> perimeter (2D) / surface area (3D) at O(dx): |error| <= 2 dx
+    # on every grid and it falls by more than half over a 4x refinement
+    for pl in ("HGC", "CGC"):
+        errs = []
+        for n in (128, 256, 512, 1024):
+            gd = I.grid(2, [n, n], [-2, -2], [2, 2])
+            c = O.classify(gd, I.circle(0.0031, 0.0017, 0.5), pl)
+            errs.append(abs(O.face_weights(c).sum() - 2 * math.pi * 0.5))
+            assert errs[-1] <= 2 * (4.0 / n)
+        assert errs[3] < 0.5 * errs[1]
+    gd = I.grid(3, [48, 48, 48], [-1, -1, -1], [1, 1, 1])
+    c = O.classify(gd, I.sphere(0.011, -0.007, 0.005, 0.6), "HGC")
+    assert abs(O.face_weights(c).sum() / (4 * math.pi * 0.36) - 1) < 0.05
+
+
+def test_pressure_force_divergence_theorem():
+    # p = b.x: -sum w p_s n -> -b * area (2D) at O(dx) (the staircase sum of a
+    # constant times n is itself only O(dx) small, so no constant is added);
+    # the viscous part of a rigid translation u = const vanishes
+    b = np.array([0.7, -0.3])
+    for gd, bd, area in [(I.grid(2, [256, 256], [-2, -2], [2, 2]), I.circle(0.0031, 0.0017, 0.5), math.pi * 0.25),
+                         (I.grid(2, [2048, 1024], [-1, -1], [3, 1]), I.airfoil(0.0, 0.0, 0.12, 1.0, 5.0), None)]:
+        c = O.classify(gd, bd, "HGC")
+        lev = O.build_levels(c)
+
+        class P:
+            def value(self, X):
+                return X @ b
+
+            def gradient(self, X):
+                return np.tile(b, (X.shape[0], 1))
+
+            def on_grid(self, g):
+                X = c.grid.centre(c.grid.unlin(np.arange(c.grid.N)))
+                return self.value(X)
+
+        p = P()
+        S = _ghost_S(c)[lev.order]
+        parr = O.fill(c, lev, [p.on_grid(gd)], [O.NEUMANN], [I.bc_values(p, 1, S, c.n[lev.order])])[0]
+        ones = np.ones(c.grid.N) * 0.25
+        uarr = O.fill(c, lev, [ones], [O.DIRICHLET], [np.full(c.n_ghosts, 0.25)])[0]
+        out, scale = O.forces(c, lev, parr, [uarr, None], 0.01, I.DRAG_LIFT_DIRS_2D)
+        if area is None:
+            # airfoil cross-section area = 2 int y_t dx (0.0822 for t = 0.12 ... 0.685 t c^2)
+            xs = np.linspace(0, 1, 200001)
+            area = 2 * np.trapezoid(O.geometry.airfoil_half_thickness(0.12, 1.0, xs), xs)
+        assert np.allclose(out[:2], -b * area, rtol=0, atol=0.03 * area * np.abs(b).max())
+        assert np.max(np.abs(out[2:4])) < 1e-12
+
+
+def _adjoint_case(case, placement):
+    gd, bd = CASES[case]
+    d = gd["dim"]
+    F = d + 1
+    rng = np.random.default_rng(case)
+    fields = [I.Polynomial(d, 300 + f) for f in range(F)]
+    bcs = [O.DIRICHLET] * d + [O.NEUMANN]
+    gd, c, lev, arrs, bc = _setup(case, placement, fields, bcs)
+    vel = list(range(d))
+    dirs = I.DRAG_LIFT_DIRS_2D if d == 2 else I.DRAG_LIFT_DIRS_3D
+    return c, lev, arrs, bc, bcs, vel, dirs, rng
+
+
+def _J(c, lev, arrs, bc, bcs, vel, dirs, seed, mu=0.01):
+    out = O.fill(c, lev, arrs, bcs, bc)
+    d = c.grid.dim
+    f, _ = O.forces(c, lev, out[d], [out[i] for i in vel], mu, dirs)
+    return seed[0] * f[2 * d] + seed[1] * f[2 * d + 1]
+
+
+@pytest.mark.parametrize("case", [0, 1, 3])
+@pytest.mark.parametrize("placement", ["HGC", "CGC_ES"])
+def test_adjoint_vs_finite_differences(case, placement):
+    c, lev, arrs, bc, bcs, vel, dirs, rng = _adjoint_case(case, placement)
+    seed = (0.8, -0.6)
+    d = c.grid.dim
+    gx, gb = O.adjoint_gradient(c, lev, bcs, d, vel, 0.01, dirs, seed)
+    assert np.all(gx[:, c.idx] == 0.0)
+    for _ in range(3):
+        vx = [rng.normal(size=a.size) for a in arrs]
+        vb = [rng.normal(size=b.size) for b in bc]
+        h = 1e-6
+        jp = _J(c, lev, [a + h * v for a, v in zip(arrs, vx)], [b + h * v for b, v in zip(bc, vb)], bcs, vel, dirs, seed)
+        jm = _J(c, lev, [a - h * v for a, v in zip(arrs, vx)], [b - h * v for b, v in zip(bc, vb)], bcs, vel, dirs, seed)
+        fd = (jp - jm) / (2 * h)
+        an = sum(float(g @ v) for g, v in zip(gx, vx)) + sum(float(g @ v) for g, v in zip(gb, vb))
+        scale = sum(float(np.abs(g) @ np.abs(v)) for g, v in zip(gx, vx)) + \
+            sum(float(np.abs(g) @ np.abs(v)) for g, v in zip(gb, vb))
+        assert abs(fd - an) < 1e-7 * scale + 1e-9, (fd, an)
+
+
+def test_adjoint_dot_product_identity():
+    # <A x, y> = <x, A^T y> for the ghost map of every field
+    c, lev, arrs, bc, bcs, vel, dirs, rng = _adjoint_case(0, "HGC")
+    mats = O.linear_map(c, lev, bcs)
+    ng = c.n_ghosts
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    I_ = sp.identity(ng, format="csc")
+    for Agg, Agx, Agb in mats:
+        x = rng.normal(size=c.grid.N)
+        x[c.idx] = 0
+        b = rng.normal(size=ng)
+        y = rng.normal(size=ng)
+        Ax = spla.spsolve((I_ - Agg).tocsc(), Agx @ x + Agb @ b)
+        lam = spla.spsolve((I_ - Agg).T.tocsc(), y)
+        lhs = float(Ax @ y)
+        rhs = float((Agx.T @ lam) @ x + (Agb.T @ lam) @ b)
+        assert abs(lhs - rhs) < 1e-12 * (abs(lhs) + np.abs(Ax).sum())
+        # and the linear map equals the level-by-level fill
+        xin = x.copy()
+        out = O.fill(c, lev, [xin], [O.DIRICHLET if Agb.diagonal().min() > 0 else O.NEUMANN], [b])
