@@ -1,0 +1,265 @@
+/*
+ * ebr.h -- C ABI of the B300 (sm_103a) direct ghost-cell reconstruction library.
+ *
+ * Method: "Stable, Compact, and Direct Ghost-Cell Reconstruction: A
+ * Non-Iterative Approach for Embedded-Boundary Methods".  The library
+ *   1. classifies the cells of Cartesian grids against analytic convex bodies
+ *      and places ghost cells (HGC, CGC, CGC_ES; Sec. 3.1, Sec. 7),
+ *   2. builds the ghost dependency DAG and its topological levels (Sec. 3.2),
+ *   3. fills the ghost values level by level from the closed-form Dirichlet /
+ *      Neumann relations (Secs. 4-5, Eqs. phi_G_Dir_2d, phi_G_Neu_2d,
+ *      phi_G_Dir_3d, phi_G_Neu_3d),
+ *   4. evaluates boundary values, gradients, pressure and viscous forces,
+ *      drag and lift from the same relations (Sec. 6),
+ *   5. and runs the adjoint of 3-4 (reverse level walk) for d(drag, lift).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an ebr_status; 0 is success, negative is an error.
+ *     No C++ exception crosses the ABI.  ebr_last_error() returns a message
+ *     for the last failing call on that context (valid until the next call).
+ *   - "d_" pointers are device pointers, "h_" pointers host pointers.  All
+ *     caller-owned buffers stay caller-owned; the library never frees them.
+ *     Library-owned device memory lives in the context and is released by
+ *     ebr_destroy().
+ *   - A call that takes a cudaStream_t enqueues its kernels on that stream
+ *     and returns without synchronising, except where stated.  Faults found
+ *     on the device (stencil outside the grid, cycle, non-finite input, a
+ *     mismatch with the planned sizes, a barrier timeout) set a status word in
+ *     the context; ebr_sync_status() synchronises the stream and returns it.
+ *   - A context handles one "geometry set": B >= 1 independent geometries,
+ *     each a grid and a body.  Cells of geometry b occupy the flat index range
+ *     [cell_offset[b], cell_offset[b+1]) of every per-cell array (tags,
+ *     fields, gradients), with offsets from ebr_layout() (geometries are
+ *     concatenated in order, without padding).  Inside a geometry the linear
+ *     index of cell (i, j, k) is i + n_x (j + n_y k).
+ *   - Ghosts of all geometries are numbered in the canonical order
+ *     (geometry, level, linear index).  Boundary data (d_bc) and boundary
+ *     gradients (d_grad_bc) use this order; ebr_ghost_info() returns the
+ *     ghost cells, their boundary points S and normals in the same order.
+ *   - One context must not be used from two host threads at once.
+ */
+#ifndef EBR_H
+#define EBR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ebr_stream;   /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  EBR_OK = 0,
+  EBR_EINVAL = -1,          /* bad argument (null pointer, size, enum, order of calls)     */
+  EBR_ENOMEM = -2,          /* device allocation failed                                    */
+  EBR_ECUDA = -3,           /* a CUDA runtime call failed                                  */
+  EBR_ECYCLE = -4,          /* the dependency graph has a cycle (Sec. 3.2 requires a DAG) */
+  EBR_ESTENCIL_OOB = -5,    /* a stencil member lies outside its grid                      */
+  EBR_ESTENCIL_SOLID = -6,  /* a stencil member is a solid (tag 1) cell: value undefined  */
+  EBR_ETIMEOUT = -7,        /* a bounded device-side wait gave up                          */
+  EBR_ENONFINITE = -8,      /* non-finite value met where the path needs a finite one     */
+  EBR_ESHAPE = -9           /* a re-run produced other counts than the planned geometry   */
+} ebr_status;
+
+typedef enum { EBR_HGC = 0, EBR_CGC = 1, EBR_CGC_ES = 2 } ebr_placement;
+typedef enum { EBR_F32 = 0, EBR_F64 = 1 } ebr_dtype;
+typedef enum { EBR_DIRICHLET = 0, EBR_NEUMANN = 1 } ebr_bc;
+typedef enum { EBR_CIRCLE = 0, EBR_SPHERE = 1, EBR_ELLIPSE = 2, EBR_AIRFOIL4 = 3 } ebr_body_kind;
+
+/* Uniform cell-centred grid.  dim = 2 or 3; n[2] = 1, lo[2] = 0, hi[2] = 1 in 2D.
+ * Cell widths h_a = (hi_a - lo_a) / n_a; cell centres lo_a + (i_a + 1/2) h_a. */
+typedef struct {
+  int32_t dim;
+  int32_t reserved;
+  int64_t n[3];
+  double lo[3];
+  double hi[3];
+} ebr_grid;
+
+/* Analytic convex body.  rot (row-major 3x3) maps body-frame vectors to the
+ * world frame: x_world = rot * x_body + centre.
+ *   EBR_CIRCLE   (2D): centre, radii[0] = r.
+ *   EBR_SPHERE   (3D): centre, radii[0] = r.
+ *   EBR_ELLIPSE  (2D): centre, semi-axes radii[0], radii[1] along the body x, y axes, rot.
+ *   EBR_AIRFOIL4 (2D): symmetric 4-digit thickness-formula section with an
+ *       open trailing edge closed by the base x = chord:
+ *       y_t(x) = 5 t c [0.2969 sqrt(x/c) - 0.1260 (x/c) - 0.3516 (x/c)^2
+ *                       + 0.2843 (x/c)^3 - 0.1015 (x/c)^4],
+ *       body frame with the leading edge at the origin and the chord along +x;
+ *       centre = leading edge in the world, thickness = t, chord = c, rot. */
+typedef struct {
+  int32_t kind;
+  int32_t reserved;
+  double centre[3];
+  double radii[3];
+  double rot[9];
+  double thickness;
+  double chord;
+} ebr_body;
+
+/* Per-geometry counts after planning (host copy). */
+typedef struct {
+  int64_t n_cells;
+  int64_t n_interface;   /* cells with a face neighbour on the other side of the boundary */
+  int64_t n_ghosts;
+  int32_t n_levels;
+  int32_t reserved;
+  int64_t n_fluid_targets;   /* fluid cells read by some ghost stencil (adjoint targets) */
+} ebr_geom_counts;
+
+/* ---------------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------------- */
+
+/* Create a context on the current CUDA device.  *out receives the handle. */
+ebr_status ebr_create(void** out);
+/* Release all library-owned device memory of the context; NULL is ignored. */
+void ebr_destroy(void* ctx);
+/* Message of the last failing call on ctx ("" if none).  Never NULL. */
+const char* ebr_last_error(const void* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Step 1: classification and ghost placement (Sec. 3.1, Sec. 7)
+ * ------------------------------------------------------------------------- */
+
+/* Plan a geometry set and classify it.
+ * n_geom >= 1 geometries; h_grids / h_bodies: host arrays [n_geom] (copied).
+ * Cell classification (Sec. 3.1, Eq. signed_distance): a cell is solid
+ * (tag 1) when its centre lies in the closed body, else fluid (tag 0).
+ * Placement: EBR_CGC -- solid cells with a fluid face neighbour become ghosts
+ * (+2); EBR_HGC -- Eqs. delta_n and HGC_criterion give candidates +2 / -2, then
+ * a -2 cell without a tag-1 face neighbour becomes 0 and (afterwards) a +2
+ * cell without a tag-0 face neighbour becomes 1; EBR_CGC_ES -- the CGC set with
+ * the stencil multipliers of Eq. stencil_anisotropic.
+ * d_tags: caller-owned int8 [total cells] receiving 0, 1, +2, -2.
+ * This call synchronises the stream (it sizes the context's buffers) and
+ * must come first; later calls reuse the plan until the next ebr_plan. */
+ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids,
+                    const ebr_body* h_bodies, int32_t placement, int8_t* d_tags,
+                    ebr_stream stream);
+
+/* Re-run the classification of the planned geometry set without host
+ * synchronisation (capturable in a CUDA graph).  Writes d_tags and the
+ * context's ghost records; a count that differs from the plan sets EBR_ESHAPE
+ * in the device status. */
+ebr_status ebr_classify(void* ctx, int8_t* d_tags, ebr_stream stream);
+
+/* Flat layout: h_cell_offset [n_geom + 1] (host) receives the cell offsets. */
+ebr_status ebr_layout(const void* ctx, int64_t* h_cell_offset);
+/* Planned counts: h_counts [n_geom] (host). */
+ebr_status ebr_counts(const void* ctx, ebr_geom_counts* h_counts);
+
+/* ---------------------------------------------------------------------------
+ * Step 2: dependency DAG and levels (Sec. 3.2)
+ * ------------------------------------------------------------------------- */
+
+/* Build the dependency levels of the classified ghosts: ghost G depends on
+ * each stencil member P_k that is a ghost with a structurally non-zero weight
+ * (n_i != 0 on every axis along which P_k is offset); level(G) = 1 + max level
+ * of its dependencies, 1 without any.  Ghosts are then stored in the canonical
+ * order (geometry, level, linear index).  Also validates every stencil member
+ * (EBR_ESTENCIL_OOB / EBR_ESTENCIL_SOLID) and detects cycles (EBR_ECYCLE),
+ * and builds the transposed incidence lists used by the adjoint.
+ * Device-side failures are reported through the status word. */
+ebr_status ebr_build_levels(void* ctx, ebr_stream stream);
+
+/* Ghost records in canonical order, copied to host arrays sized by the total
+ * ghost count (sum of n_ghosts); any pointer may be NULL to skip it.
+ *   h_geom  [Ng] int32 geometry of each ghost,
+ *   h_cell  [Ng] int64 linear cell index inside its geometry,
+ *   h_level [Ng] int32 dependency level (1-based),
+ *   h_tag   [Ng] int8  +2 (centre in the solid) or -2 (centre in the fluid),
+ *   h_psi   [Ng] double signed normal distance (Eq. signed_distance),
+ *   h_normal[Ng][3] double unit normal at S into the fluid,
+ *   h_S     [Ng][3] double boundary point S = centre + psi * normal,
+ *   h_r     [Ng][3] int32 stencil multipliers r_i (Eq. stencil_anisotropic).
+ * Synchronises the stream. */
+ebr_status ebr_ghost_info(void* ctx, int32_t* h_geom, int64_t* h_cell, int32_t* h_level,
+                          int8_t* h_tag, double* h_psi, double* h_normal, double* h_S,
+                          int32_t* h_r, ebr_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Step 3: level-by-level reconstruction (Secs. 3.2, 4, 5)
+ * ------------------------------------------------------------------------- */
+
+typedef enum {
+  EBR_MODE_LEVEL_LAUNCH = 0,  /* one grid-wide launch per level per geometry            */
+  EBR_MODE_PERSISTENT = 1     /* one launch; one CTA per geometry walks its levels with
+                                 block barriers (geometries larger than the CTA's shared
+                                 memory fall back to level launches)                    */
+} ebr_mode;
+
+/* Fill the ghost entries of n_fields fields in place.
+ * d_fields: host array [n_fields] of device pointers, each [total cells] of
+ *   dtype (float or double); only ghost entries are written, only stencil
+ *   members are read.
+ * h_bc_kind: host [n_fields] of ebr_bc.
+ * d_bc: host array [n_fields] of device pointers, each [total ghosts] of dtype
+ *   in canonical order: phi at S (Dirichlet) or dphi/dn at S (Neumann).
+ * Weights are evaluated in double (Eqs. phi_G_*), once per ghost; FP32 fields
+ * are combined in float with the weights rounded to float. */
+ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
+                           const int32_t* h_bc_kind, const void* const* d_bc,
+                           int32_t dtype, int32_t mode, ebr_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Step 4: boundary quantities and forces (Sec. 6)
+ * ------------------------------------------------------------------------- */
+
+/* Per geometry b, d_out[b * (2 dim + 2) + ...] = [Fp (dim), Fv (dim), drag, lift]:
+ *   Fp = sum_G w_G (-p_s n),  Fv = sum_G w_G mu (grad u + grad u^T)|_S n,
+ *   drag = (Fp + Fv) . h_dirs[0..dim), lift = (Fp + Fv) . h_dirs[dim..2 dim).
+ * p_s is the Dirichlet relation solved for phi_s on the filled pressure
+ * field; grad u at S from Eq. derivative_bilinear (2D) or
+ * Eqs. derivative_trilinear_x/y/z (3D).  w_G = sum over the faces of G shared
+ * with a tag-0 cell of (face area) |n_face . n| (the paper gives no quadrature;
+ * this local surface-element weight is the reading taken).
+ * d_vel: host array [dim] of device pointers to the filled velocity fields
+ *   (an entry may be NULL: that component is identically zero); d_p: filled
+ *   pressure field; d_out: device double [n_geom * (2 dim + 2)], written.
+ * Sums are deterministic (fixed reduction tree) in double. */
+ebr_status ebr_boundary_forces(void* ctx, const void* const* d_vel, const void* d_p,
+                               int32_t dtype, double mu, const double* h_dirs,
+                               double* d_out, ebr_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Step 5: adjoint (reverse level walk of steps 3-4)
+ * ------------------------------------------------------------------------- */
+
+/* Gradient of J = sum_b seed[b][0] drag_b + seed[b][1] lift_b with respect to
+ * the fluid field values and the boundary data.  Same field roles as
+ * ebr_boundary_forces: fields d_fields[0..n_fields) with kinds h_bc_kind, of
+ * which vel_index[0..dim) (-1: component absent) are the velocity components
+ * and p_index the pressure.
+ * d_seed: device double [n_geom][2].
+ * d_grad_fields: host array [n_fields] of device pointers [total cells] of
+ *   dtype; entries at stencil cells are written (accumulate = 0: overwritten,
+ *   1: added); ghost cells receive 0 (their input value is overwritten by the
+ *   fill); all other entries are left untouched.
+ * d_grad_bc: host array [n_fields] of device pointers [total ghosts] of dtype
+ *   (canonical order), written (or added when accumulate = 1).
+ * The pull form over transposed incidence lists makes the result bitwise
+ * deterministic.  The geometry must have been planned and levelled.  The
+ * field values themselves are not needed (the map is linear). */
+ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h_bc_kind,
+                                   const int32_t* h_vel_index, int32_t p_index, double mu,
+                                   const double* h_dirs, const double* d_seed,
+                                   void* const* d_grad_fields, void* const* d_grad_bc,
+                                   int32_t dtype, int32_t accumulate, int32_t mode,
+                                   ebr_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Status
+ * ------------------------------------------------------------------------- */
+
+/* Synchronise the stream, read and clear the device status word. */
+ebr_status ebr_sync_status(void* ctx, ebr_stream stream);
+
+/* Number of kernel launches this context has issued since creation. */
+int64_t ebr_launch_count(const void* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EBR_H */

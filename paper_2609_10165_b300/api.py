@@ -1,0 +1,178 @@
+"""Python binding of the C ABI (include/ebr.h) for torch tensors.
+
+PyTorch provides device memory and the current stream; every step of the
+path runs in the library's CUDA kernels.  Geometry and body descriptions are
+plain dicts (see ``inputs``): grid {"dim", "n", "lo", "hi"} and body
+{"kind", "centre", "radii", "rot", "thickness", "chord"}.
+"""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+KIND = {"circle": 0, "sphere": 1, "ellipse": 2, "airfoil": 3}
+PLACEMENT = {"HGC": 0, "CGC": 1, "CGC_ES": 2}
+MODE = {"level": 0, "persistent": 1}
+DTYPE = {torch.float32: 0, torch.float64: 1}
+
+
+def _grid_struct(g):
+    s = _lib.Grid()
+    s.dim = int(g["dim"])
+    n = list(g["n"]) + [1] * (3 - len(g["n"]))
+    lo = list(g["lo"]) + [0.0] * (3 - len(g["lo"]))
+    hi = list(g["hi"]) + [1.0] * (3 - len(g["hi"]))
+    for a in range(3):
+        s.n[a] = int(n[a]) if a < s.dim else 1
+        s.lo[a] = float(lo[a]) if a < s.dim else 0.0
+        s.hi[a] = float(hi[a]) if a < s.dim else 1.0
+    return s
+
+
+def _body_struct(b):
+    s = _lib.Body()
+    s.kind = KIND[b["kind"]]
+    for a in range(3):
+        s.centre[a] = float(b["centre"][a]) if a < len(b["centre"]) else 0.0
+        s.radii[a] = float(b["radii"][a]) if a < len(b["radii"]) else 0.0
+    for q in range(9):
+        s.rot[q] = float(b["rot"][q])
+    s.thickness = float(b.get("thickness", 0.0))
+    s.chord = float(b.get("chord", 0.0))
+    return s
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _ptr_array(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = t.data_ptr() if t is not None else 0
+    return arr
+
+
+class Reconstructor:
+    """One planned geometry set (B >= 1 grids with bodies) on one device."""
+
+    def __init__(self, grids, bodies, placement="HGC", device=None):
+        self.lib = _lib.load()
+        if isinstance(grids, dict):
+            grids, bodies = [grids], [bodies]
+        self.B = len(grids)
+        self.dim = int(grids[0]["dim"])
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.placement = placement
+        h = ctypes.c_void_p()
+        self._check(self.lib.ebr_create(ctypes.byref(h)), ctx=None)
+        self.ctx = h
+        self._grids = (_lib.Grid * self.B)(*[_grid_struct(g) for g in grids])
+        self._bodies = (_lib.Body * self.B)(*[_body_struct(b) for b in bodies])
+        ncell = sum(int(np.prod([g["n"][a] for a in range(int(g["dim"]))])) for g in grids)
+        self.tags = torch.empty(ncell, dtype=torch.int8, device=self.device)
+        self._check(self.lib.ebr_plan(self.ctx, self.B, self._grids, self._bodies,
+                                      PLACEMENT[placement], _ptr(self.tags), self._stream()))
+        off = (ctypes.c_int64 * (self.B + 1))()
+        self._check(self.lib.ebr_layout(self.ctx, off))
+        self.cell_offset = np.array(list(off), dtype=np.int64)
+        self.n_cells = int(self.cell_offset[-1])
+        self.levelled = False
+
+    # -- helpers -----------------------------------------------------------
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _check(self, code, ctx=0):
+        if code != 0:
+            c = self.ctx if ctx == 0 else ctx
+            msg = self.lib.ebr_last_error(c).decode() if c else ""
+            raise _lib.EBRError(code, msg)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.ebr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- steps ---------------------------------------------------------------
+    def classify(self, tags=None):
+        """Re-run the classification (no host synchronisation)."""
+        t = self.tags if tags is None else tags
+        self._check(self.lib.ebr_classify(self.ctx, _ptr(t), self._stream()))
+        return t
+
+    def build_levels(self):
+        self._check(self.lib.ebr_build_levels(self.ctx, self._stream()))
+        self.levelled = True
+
+    def counts(self):
+        arr = (_lib.GeomCounts * self.B)()
+        self._check(self.lib.ebr_counts(self.ctx, arr))
+        return [{"n_cells": a.n_cells, "n_interface": a.n_interface, "n_ghosts": a.n_ghosts,
+                 "n_levels": a.n_levels, "n_fluid_targets": a.n_fluid_targets} for a in arr]
+
+    @property
+    def n_ghosts(self):
+        return int(sum(c["n_ghosts"] for c in self.counts()))
+
+    def ghost_info(self):
+        ng = self.n_ghosts
+        out = {
+            "geom": np.zeros(ng, np.int32), "cell": np.zeros(ng, np.int64),
+            "level": np.zeros(ng, np.int32), "tag": np.zeros(ng, np.int8),
+            "psi": np.zeros(ng, np.float64), "normal": np.zeros((ng, 3), np.float64),
+            "S": np.zeros((ng, 3), np.float64), "r": np.zeros((ng, 3), np.int32),
+        }
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        self._check(self.lib.ebr_ghost_info(self.ctx, P(out["geom"]), P(out["cell"]), P(out["level"]),
+                                            P(out["tag"]), P(out["psi"]), P(out["normal"]),
+                                            P(out["S"]), P(out["r"]), self._stream()))
+        return out
+
+    def reconstruct(self, fields, bc_kinds, bc, mode="persistent"):
+        F = len(fields)
+        dt = fields[0].dtype
+        kinds = (ctypes.c_int32 * F)(*[int(k) for k in bc_kinds])
+        self._check(self.lib.ebr_reconstruct(self.ctx, F, _ptr_array(fields), kinds, _ptr_array(bc),
+                                             DTYPE[dt], MODE[mode], self._stream()))
+        return fields
+
+    def forces(self, vel, p, mu, dirs, out=None):
+        d = self.dim
+        W = 2 * d + 2
+        if out is None:
+            out = torch.empty(self.B * W, dtype=torch.float64, device=self.device)
+        dd = (ctypes.c_double * (2 * d))(*[float(v) for v in np.asarray(dirs, dtype=np.float64).reshape(-1)[: 2 * d]])
+        self._check(self.lib.ebr_boundary_forces(self.ctx, _ptr_array(list(vel)), _ptr(p),
+                                                 DTYPE[p.dtype], float(mu), dd, _ptr(out), self._stream()))
+        return out.view(self.B, W)
+
+    def adjoint(self, bc_kinds, vel_index, p_index, mu, dirs, seed, grad_fields, grad_bc,
+                accumulate=False, mode="persistent"):
+        F = len(bc_kinds)
+        d = self.dim
+        kinds = (ctypes.c_int32 * F)(*[int(k) for k in bc_kinds])
+        vi = (ctypes.c_int32 * 3)(*([(-1 if v is None else int(v)) for v in vel_index] + [-1] * (3 - len(vel_index))))
+        dd = (ctypes.c_double * (2 * d))(*[float(v) for v in np.asarray(dirs, dtype=np.float64).reshape(-1)[: 2 * d]])
+        seed = seed.to(device=self.device, dtype=torch.float64).contiguous()
+        self._check(self.lib.ebr_reconstruct_adjoint(
+            self.ctx, F, kinds, vi, int(p_index), float(mu), dd, _ptr(seed),
+            _ptr_array(grad_fields), _ptr_array(grad_bc), DTYPE[grad_fields[0].dtype],
+            1 if accumulate else 0, MODE[mode], self._stream()))
+        return grad_fields, grad_bc
+
+    def sync_status(self):
+        self._check(self.lib.ebr_sync_status(self.ctx, self._stream()))
+
+    @property
+    def launches(self):
+        return int(self.lib.ebr_launch_count(self.ctx))

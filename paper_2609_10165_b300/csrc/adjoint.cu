@@ -1,0 +1,319 @@
+// Adjoint of the fill and the forces: gradient of
+// J = sum_b seed_b0 drag_b + seed_b1 lift_b with respect to the fluid field
+// values and the boundary data.  For fixed geometry the path is linear, so
+// J = sum_(ghost H, slot s, field f) c[f][s][H] * value_f(slot s of H) where
+// the force coefficients c follow from the Sec. 6 relations (phi_s and grad
+// coefficients in ftab):
+//   pressure:     c = -w_H (q . n) alpha_s
+//   velocity u_m: c = w_H mu (q_m (beta_s . n) + n_m (q . beta_s))
+// with q = seed_0 e_drag + seed_1 e_lift.  With lambda_G = dJ / d phi_G:
+//   lambda_G = sum over incidences (H, s) whose slot s is G of
+//              c[f][s][H] + [s > 0 and member active] w_(H, s-1) lambda_H,
+// processed in reverse level order (consumers H sit in higher levels), then
+//   dJ/dx_T = the same sum for a fluid cell T,   dJ/db_G = w_(G, s) lambda_G.
+// Every target pulls its sources from a precomputed list in a fixed order:
+// no atomics, bitwise reproducible.
+#include "ebr_kernels.cuh"
+
+namespace ebr {
+
+struct AdjSet {
+  int kind[8];
+  void* grad[8];
+  void* gbc[8];
+};
+
+__global__ void k_adj_seed(int dim, int F, AdjSet roles_unused, int4 role, double mu, double dd0,
+                           double dd1, double dd2, double dl0, double dl1, double dl2,
+                           const double* __restrict__ seed, int ng, const int* __restrict__ g_geo,
+                           const double* __restrict__ g_n, const double* __restrict__ ftab,
+                           double* __restrict__ sv) {
+  (void)roles_unused;
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ng) return;
+  int b = g_geo[p];
+  double s0 = seed[2 * b], s1 = seed[2 * b + 1];
+  double q[3] = {s0 * dd0 + s1 * dl0, s0 * dd1 + s1 * dl1, s0 * dd2 + s1 * dl2};
+  double n[3] = {g_n[p], g_n[ng + p], g_n[2 * (size_t)ng + p]};
+  double wG = ftab[p];
+  double qn = 0.0;
+  for (int a = 0; a < dim; ++a) qn += q[a] * n[a];
+  const int vel[3] = {role.x, role.y, role.z};
+  const int pidx = role.w;
+  const int K = stencil_k(dim);
+  for (int f = 0; f < F; ++f) {
+    int m = -1;
+    for (int a = 0; a < dim; ++a)
+      if (vel[a] == f) m = a;
+    for (int s = 0; s < 8; ++s) {
+      double c = 0.0;
+      if (s <= K) {
+        if (f == pidx) {
+          c = -wG * qn * ftab[(size_t)(1 + s) * ng + p];
+        } else if (m >= 0) {
+          double bn = 0.0, qb = 0.0;
+          for (int a = 0; a < dim; ++a) {
+            double beta = ftab[(size_t)(9 + 8 * a + s) * ng + p];
+            bn += beta * n[a];
+            qb += beta * q[a];
+          }
+          c = wG * mu * (q[m] * bn + n[m] * qb);
+        }
+      }
+      sv[(size_t)(f * 8 + s) * ng + p] = c;
+    }
+  }
+}
+
+void launch_adj_seed(int dim, int F, const int* role, double mu, const double* dirs,
+                     const double* seed, int ng, const int* g_geo, const double* g_n,
+                     const double* ftab, double* sv, cudaStream_t s) {
+  if (ng <= 0) return;
+  AdjSet dummy{};
+  int4 r = make_int4(role[0], role[1], role[2], role[3]);
+  double dd[3] = {0, 0, 0}, dl[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) { dd[a] = dirs[a]; dl[a] = dirs[dim + a]; }
+  k_adj_seed<<<(ng + 127) / 128, 128, 0, s>>>(dim, F, dummy, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1],
+                                              dl[2], seed, ng, g_geo, g_n, ftab, sv);
+}
+
+template <typename T>
+__device__ inline T pull_sum(int f, int kind, int j0, int j1, const int* __restrict__ src,
+                             const uint32_t* __restrict__ g_meta, const double* __restrict__ wtab,
+                             const double* __restrict__ sv, int ng, const T* __restrict__ lam) {
+  T acc = T(0);
+  for (int j = j0; j < j1; ++j) {
+    int e = src[j];
+    int q = e >> 3, s = e & 7;
+    acc += (T)sv[(size_t)(f * 8 + s) * ng + q];
+    if (s > 0 && (meta_active(g_meta[q]) >> (s - 1) & 1u))
+      acc += (T)wtab[(size_t)(kind * 8 + s - 1) * ng + q] * lam[(size_t)f * ng + q];
+  }
+  return acc;
+}
+
+template <typename T>
+__global__ void k_adj_level(AdjSet A, int F, int p0, int p1, const int* __restrict__ gsrc_ptr,
+                            const int* __restrict__ gsrc, const uint32_t* __restrict__ g_meta,
+                            const double* __restrict__ wtab, const double* __restrict__ sv, int ng,
+                            T* __restrict__ lam) {
+  int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= p1) return;
+  for (int f = 0; f < F; ++f)
+    lam[(size_t)f * ng + p] = pull_sum<T>(f, A.kind[f], gsrc_ptr[p], gsrc_ptr[p + 1], gsrc, g_meta,
+                                          wtab, sv, ng, lam);
+}
+
+void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int p1,
+                      const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
+                      const double* wtab, const double* sv, int ng_total, void* lam, cudaStream_t s) {
+  (void)dim;
+  if (p1 <= p0) return;
+  AdjSet A{};
+  for (int f = 0; f < F && f < 8; ++f) A.kind[f] = bc_kind[f];
+  int n = p1 - p0, T = n < 128 ? 64 : 128;
+  if (dtype == 0)
+    k_adj_level<float><<<(n + T - 1) / T, T, 0, s>>>(A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (float*)lam);
+  else
+    k_adj_level<double><<<(n + T - 1) / T, T, 0, s>>>(A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (double*)lam);
+}
+
+// One CTA per geometry.  Phase 1 (parallel): lambda starts as the sum of the
+// force coefficients of all incidences, and the consumer incidences (active
+// members) are packed into shared memory with their weights.  Phase 2: reverse
+// levels on shared memory only.
+constexpr int AC_T = 512;
+
+size_t adj_chain_smem(int dtype, int F, int n, int n_src) {
+  size_t sz = dtype == 0 ? 4 : 8;
+  return (size_t)F * n * sz + (size_t)(n + 1) * sizeof(int) + (size_t)n_src * (sizeof(int) + 2 * sz) + 64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom* __restrict__ G,
+                                                    const int* __restrict__ geo_list,
+                                                    const int* __restrict__ lev_ptr,
+                                                    const int* __restrict__ gsrc_ptr,
+                                                    const int* __restrict__ gsrc,
+                                                    const uint32_t* __restrict__ g_meta,
+                                                    const double* __restrict__ wtab,
+                                                    const double* __restrict__ sv, int ng,
+                                                    T* __restrict__ lam) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int sh_warp[32];
+  __shared__ int sh_carry;
+  const Geom& g = G[geo_list[blockIdx.x]];
+  const int n = g.n_ghost, g0 = g.ghost_off;
+  const int nsrc = gsrc_ptr[g0 + n] - gsrc_ptr[g0];
+  T* L = reinterpret_cast<T*>(smem);                         // [F][n]
+  T* cw = L + (size_t)F * n;                                 // [2][nsrc]
+  int* cq = reinterpret_cast<int*>(cw + (size_t)2 * nsrc);   // [nsrc]
+  int* cptr = cq + nsrc;                                     // [n + 1]
+  // phase 1a: force-coefficient sums, consumer counts
+  if (threadIdx.x == 0) sh_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += AC_T) {
+    int s = base + threadIdx.x;
+    int cnt = 0;
+    if (s < n) {
+      int p = g0 + s;
+      int j0 = gsrc_ptr[p], j1 = gsrc_ptr[p + 1];
+      for (int f = 0; f < F; ++f) {
+        T acc = T(0);
+        for (int j = j0; j < j1; ++j) {
+          int e = gsrc[j];
+          acc += (T)sv[(size_t)(f * 8 + (e & 7)) * ng + (e >> 3)];
+        }
+        L[(size_t)f * n + s] = acc;
+      }
+      for (int j = j0; j < j1; ++j) {
+        int e = gsrc[j];
+        int q = e >> 3, sl = e & 7;
+        if (sl > 0 && (meta_active(g_meta[q]) >> (sl - 1) & 1u)) ++cnt;
+      }
+    }
+    // block exclusive scan of cnt
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sh_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int v = lane < (AC_T / 32) ? sh_warp[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      if (lane < AC_T / 32) sh_warp[lane] = v;
+    }
+    __syncthreads();
+    int ex = sh_carry + (w > 0 ? sh_warp[w - 1] : 0) + x - cnt;
+    if (s < n) cptr[s] = ex;
+    int tot = sh_warp[AC_T / 32 - 1];
+    __syncthreads();
+    if (threadIdx.x == 0) sh_carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cptr[n] = sh_carry;
+  __syncthreads();
+  // phase 1b: pack consumers
+  for (int s = threadIdx.x; s < n; s += AC_T) {
+    int p = g0 + s;
+    int o = cptr[s];
+    for (int j = gsrc_ptr[p]; j < gsrc_ptr[p + 1]; ++j) {
+      int e = gsrc[j];
+      int q = e >> 3, sl = e & 7;
+      if (sl > 0 && (meta_active(g_meta[q]) >> (sl - 1) & 1u)) {
+        cq[o] = q - g0;
+        cw[o] = (T)wtab[(size_t)(sl - 1) * ng + q];
+        cw[nsrc + o] = (T)wtab[(size_t)(8 + sl - 1) * ng + q];
+        ++o;
+      }
+    }
+  }
+  __syncthreads();
+  // phase 2: reverse levels
+  const int* lp = lev_ptr + g.lev_off;
+  for (int lv = g.n_levels; lv >= 1; --lv) {
+    int a = lp[lv - 1] - g0, b = lp[lv] - g0;
+    for (int s = a + threadIdx.x; s < b; s += AC_T) {
+      for (int f = 0; f < F; ++f) {
+        int kind = A.kind[f];
+        T v = L[(size_t)f * n + s];
+        for (int o = cptr[s]; o < cptr[s + 1]; ++o) v += cw[(size_t)kind * nsrc + o] * L[(size_t)f * n + cq[o]];
+        L[(size_t)f * n + s] = v;
+      }
+    }
+    __syncthreads();
+  }
+  for (int s = threadIdx.x; s < n; s += AC_T)
+    for (int f = 0; f < F; ++f) lam[(size_t)f * ng + g0 + s] = L[(size_t)f * n + s];
+}
+
+void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom* G,
+                      const int* geo_list, int n_list, const int* lev_ptr, const int* gsrc_ptr,
+                      const int* gsrc, const uint32_t* g_meta, const double* wtab, const double* sv,
+                      int ng_total, void* lam, size_t smem, cudaStream_t s) {
+  (void)dim;
+  if (n_list <= 0) return;
+  AdjSet A{};
+  for (int f = 0; f < F && f < 8; ++f) A.kind[f] = bc_kind[f];
+  if (dtype == 0) {
+    static size_t set_float = 0;
+    if (smem > set_float) {
+      cudaFuncSetAttribute(k_adj_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set_float = smem;
+    }
+    k_adj_chain<float><<<n_list, AC_T, smem, s>>>(A, F, G, geo_list, lev_ptr, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (float*)lam);
+  } else {
+    static size_t set_double = 0;
+    if (smem > set_double) {
+      cudaFuncSetAttribute(k_adj_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set_double = smem;
+    }
+    k_adj_chain<double><<<n_list, AC_T, smem, s>>>(A, F, G, geo_list, lev_ptr, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (double*)lam);
+  }
+}
+
+template <typename T>
+__global__ void k_adj_fluid(AdjSet A, int F, int nft, const int* __restrict__ ft_cell,
+                            const int* __restrict__ ft_geo, const int* __restrict__ ft_ptr,
+                            const int* __restrict__ ft_src, const Geom* __restrict__ G,
+                            const uint32_t* __restrict__ g_meta, const double* __restrict__ wtab,
+                            const double* __restrict__ sv, int ng, const T* __restrict__ lam,
+                            int accumulate) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nft) return;
+  long long c = G[ft_geo[t]].cell_off + ft_cell[t];
+  for (int f = 0; f < F; ++f) {
+    T v = pull_sum<T>(f, A.kind[f], ft_ptr[t], ft_ptr[t + 1], ft_src, g_meta, wtab, sv, ng, lam);
+    T* gr = static_cast<T*>(A.grad[f]);
+    if (accumulate) gr[c] += v; else gr[c] = v;
+  }
+}
+
+void launch_adj_fluid(int dtype, int dim, int F, const int* bc_kind, int nft, const int* ft_cell,
+                      const int* ft_geo, const int* ft_ptr, const int* ft_src, const Geom* G,
+                      const uint32_t* g_meta, const double* wtab, const double* sv, int ng_total,
+                      const void* lam, void* const* grad, int accumulate, cudaStream_t s) {
+  (void)dim;
+  if (nft <= 0) return;
+  AdjSet A{};
+  for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.grad[f] = grad[f]; }
+  if (dtype == 0)
+    k_adj_fluid<float><<<(nft + 127) / 128, 128, 0, s>>>(A, F, nft, ft_cell, ft_geo, ft_ptr, ft_src, G, g_meta, wtab, sv, ng_total, (const float*)lam, accumulate);
+  else
+    k_adj_fluid<double><<<(nft + 127) / 128, 128, 0, s>>>(A, F, nft, ft_cell, ft_geo, ft_ptr, ft_src, G, g_meta, wtab, sv, ng_total, (const double*)lam, accumulate);
+}
+
+template <typename T>
+__global__ void k_adj_bc(AdjSet A, int F, int ng, const Geom* __restrict__ G,
+                         const int* __restrict__ g_geo, const int* __restrict__ g_cell,
+                         const double* __restrict__ wtab, const T* __restrict__ lam, int accumulate) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ng) return;
+  long long c = G[g_geo[p]].cell_off + g_cell[p];
+  for (int f = 0; f < F; ++f) {
+    T v = (T)wtab[(size_t)(A.kind[f] * 8 + 7) * ng + p] * lam[(size_t)f * ng + p];
+    T* gb = static_cast<T*>(A.gbc[f]);
+    if (accumulate) gb[p] += v; else gb[p] = v;
+    if (!accumulate) static_cast<T*>(A.grad[f])[c] = T(0);
+  }
+}
+
+void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
+                   const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,
+                   void* const* grad, int accumulate, cudaStream_t s) {
+  if (ng <= 0) return;
+  AdjSet A{};
+  for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.gbc[f] = grad_bc[f]; A.grad[f] = grad[f]; }
+  if (dtype == 0)
+    k_adj_bc<float><<<(ng + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, wtab, (const float*)lam, accumulate);
+  else
+    k_adj_bc<double><<<(ng + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, wtab, (const double*)lam, accumulate);
+}
+
+}  // namespace ebr

@@ -1,0 +1,800 @@
+// C ABI (include/ebr.h): context, planning, and the orchestration of the
+// classification, level, fill, force and adjoint kernels.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ebr.h"
+#include "ebr_kernels.cuh"
+
+using namespace ebr;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct ChainPlan {
+  int* d_list = nullptr;
+  int n_list = 0;
+  size_t smem = 0;
+  std::vector<int> fallback;   // geometries served by level launches
+};
+
+struct Ctx {
+  int device = 0;
+  std::string err;
+  long long launches = 0;
+  std::vector<DevBuf> bufs;    // every library allocation, freed at destroy
+
+  // geometry set
+  int B = 0, placement = 0;
+  bool planned = false, levelled = false;
+  std::vector<Geom> hG;
+  std::vector<int> h_row_off;
+  long long total_cells = 0;
+  int total_rows = 0;
+  Geom* dG = nullptr;
+  int* d_row_off = nullptr;
+
+  // status / stats
+  int* d_status = nullptr;
+  int* d_stats = nullptr;      // [0] row fallbacks, [1] rmax, [2..] n_levels per geometry follow in d_nlev
+  int* d_nlev = nullptr;
+
+  // classification
+  int2* runs = nullptr;
+  int* row_cnt = nullptr;
+  int* row_ptr = nullptr;
+  int n_iface = 0;
+  int* iface_cell = nullptr;
+  int* iface_geo = nullptr;
+  int8_t* iface_solid = nullptr;
+  double* iface_psi = nullptr;
+  double* iface_n = nullptr;
+  int* gflag = nullptr;
+  int* gpos = nullptr;
+  void* scan_tmp = nullptr;
+  int8_t* tags = nullptr;      // last tag array the caller gave
+
+  // ghosts
+  int ng = 0;
+  int rmax = 1;
+  int *gs_cell = nullptr, *gs_geo = nullptr, *dep = nullptr, *level = nullptr, *order_pos = nullptr;
+  double *gs_psi = nullptr, *gs_n = nullptr;
+  uint32_t* gs_meta = nullptr;
+  int *g_cell = nullptr, *g_geo = nullptr, *g_dep = nullptr, *g_level = nullptr;
+  double *g_psi = nullptr, *g_n = nullptr;
+  uint32_t* g_meta = nullptr;
+  int* pos_of_cell = nullptr;
+  int* lev_ptr = nullptr;
+  std::vector<int> h_lev_ptr;
+  double* wtab = nullptr;
+  double* ftab = nullptr;
+  int *gsrc_cnt = nullptr, *gsrc_ptr = nullptr, *gsrc = nullptr;
+  int n_gsrc = 0;
+  std::vector<int> h_gsrc_geo;   // sources per geometry
+  int *own_flag = nullptr, *own_ptr = nullptr, *ft_cell = nullptr, *ft_geo = nullptr,
+      *ft_cnt = nullptr, *ft_ptr = nullptr, *ft_src = nullptr;
+  int nft = 0, n_fsrc = 0;
+  std::vector<long long> h_nft_geo;
+
+  // forces
+  int n_chunks = 0;
+  int4* chunks = nullptr;
+  int* chunk_ptr = nullptr;
+  double* partial = nullptr;
+
+  // adjoint scratch
+  double* sv = nullptr;
+  void* lam = nullptr;
+
+  std::vector<int> order_by_size;            // geometries, largest ghost count first
+  std::map<long long, ChainPlan> chain_plans;
+};
+
+ebr_status fail(Ctx* c, ebr_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(c, EBR_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
+                  __FILE__, __LINE__);                                                        \
+  } while (0)
+
+#define CKL()                                                                                 \
+  do {                                                                                        \
+    cudaError_t e_ = cudaGetLastError();                                                      \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(c, EBR_ECUDA, "kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_),   \
+                  __FILE__, __LINE__);                                                        \
+  } while (0)
+
+template <typename T>
+ebr_status dalloc(Ctx* c, T** p, size_t count) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, EBR_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->bufs.push_back({q, bytes});
+  *p = static_cast<T*>(q);
+  return EBR_OK;
+}
+
+ebr_status balloc(Ctx* c, void** p, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 16);
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, EBR_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->bufs.push_back({q, bytes});
+  *p = q;
+  return EBR_OK;
+}
+
+#define AL(ptr, count)                                           \
+  do {                                                           \
+    ebr_status s_ = dalloc(c, &(ptr), (size_t)(count));          \
+    if (s_ != EBR_OK) return s_;                                 \
+  } while (0)
+
+void free_all(Ctx* c) {
+  for (auto& b : c->bufs) cudaFree(b.p);
+  c->bufs.clear();
+  for (auto& kv : c->chain_plans) (void)kv;
+  c->chain_plans.clear();
+}
+
+cudaStream_t S(ebr_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// k_check: compare scanned offsets at geometry boundaries with the plan
+__global__ void k_check(const Geom* G, int B, const int* row_ptr, const int* gpos, int n_iface,
+                        int ng, const int* nlev, int stage, int* status) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const Geom& g = G[b];
+  if (stage == 0) {
+    if (row_ptr[g.row_off] != g.iface_off) set_status(status, S_ESHAPE);
+    if (b == B - 1 && row_ptr[g.row_off + g.n_rows] != n_iface) set_status(status, S_ESHAPE);
+  } else if (stage == 1) {
+    if (gpos[g.iface_off] != g.ghost_off) set_status(status, S_ESHAPE);
+    if (b == B - 1 && gpos[n_iface] != ng) set_status(status, S_ESHAPE);
+  } else {
+    if (nlev[b] != g.n_levels) set_status(status, S_ESHAPE);
+  }
+}
+
+ebr_status upload_geoms(Ctx* c) {
+  CK(cudaMemcpy(c->dG, c->hG.data(), sizeof(Geom) * c->B, cudaMemcpyHostToDevice));
+  return EBR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// classification pipeline (planning == true: synchronise and size buffers)
+// ---------------------------------------------------------------------------
+ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
+  c->tags = d_tags;
+  launch_rows(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, d_tags, c->d_status, c->d_stats, s);
+  c->launches += 1;
+  CKL();
+  launch_iface(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, c->row_cnt, nullptr, nullptr,
+               nullptr, nullptr, 0, 0, c->d_status, s);
+  launch_scan(c->row_cnt, c->row_ptr, c->total_rows, c->scan_tmp, s);
+  c->launches += 4;
+  CKL();
+  if (planning) {
+    std::vector<int> hp(c->total_rows + 1);
+    CK(cudaMemcpyAsync(hp.data(), c->row_ptr, sizeof(int) * (c->total_rows + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->n_iface = hp[c->total_rows];
+    for (int b = 0; b < c->B; ++b) {
+      c->hG[b].iface_off = hp[c->hG[b].row_off];
+      c->hG[b].n_iface = hp[c->hG[b].row_off + c->hG[b].n_rows] - c->hG[b].iface_off;
+    }
+    int ni = c->n_iface;
+    AL(c->iface_cell, ni);
+    AL(c->iface_geo, ni);
+    AL(c->iface_solid, ni);
+    AL(c->iface_psi, ni);
+    AL(c->iface_n, 3 * (size_t)ni);
+    AL(c->gflag, ni);
+    AL(c->gpos, ni + 1);
+  }
+  launch_iface(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, nullptr, c->row_ptr,
+               c->iface_cell, c->iface_geo, c->iface_solid, 1, c->n_iface, c->d_status, s);
+  launch_place(c->dG, c->n_iface, c->iface_cell, c->iface_geo, c->iface_solid, c->placement,
+               d_tags, c->iface_psi, c->iface_n, c->d_status, s);
+  c->launches += 2;
+  if (c->placement == EBR_HGC) {
+    launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 0, s);
+    launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 1, s);
+    c->launches += 2;
+  }
+  launch_ghost_flags(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->gflag, s);
+  launch_scan(c->gflag, c->gpos, c->n_iface, c->scan_tmp, s);
+  c->launches += 4;
+  CKL();
+  if (planning) {
+    std::vector<int> hp(c->n_iface + 1);
+    CK(cudaMemcpyAsync(hp.data(), c->gpos, sizeof(int) * (c->n_iface + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->ng = hp[c->n_iface];
+    for (int b = 0; b < c->B; ++b) {
+      Geom& g = c->hG[b];
+      g.ghost_off = hp[g.iface_off];
+      g.n_ghost = hp[g.iface_off + g.n_iface] - g.ghost_off;
+      g.lev_off = g.ghost_off + b;
+    }
+    int ng = c->ng;
+    AL(c->gs_cell, ng);
+    AL(c->gs_geo, ng);
+    AL(c->gs_psi, ng);
+    AL(c->gs_n, 3 * (size_t)ng);
+    AL(c->gs_meta, ng);
+    CK(cudaMemsetAsync(c->d_stats + 1, 0, sizeof(int), s));
+  } else {
+    k_check<<<(c->B + 127) / 128, 128, 0, s>>>(c->dG, c->B, c->row_ptr, c->gpos, c->n_iface, c->ng,
+                                               c->d_nlev, 0, c->d_status);
+    k_check<<<(c->B + 127) / 128, 128, 0, s>>>(c->dG, c->B, c->row_ptr, c->gpos, c->n_iface, c->ng,
+                                               c->d_nlev, 1, c->d_status);
+    c->launches += 2;
+  }
+  launch_ghost_write(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->iface_psi,
+                     c->iface_n, c->gpos, c->placement, c->ng, c->gs_cell, c->gs_geo, c->gs_psi,
+                     c->gs_n, c->gs_meta, c->d_stats + 1, c->d_status, s);
+  c->launches += 1;
+  CKL();
+  if (planning) {
+    CK(cudaMemcpyAsync(&c->rmax, c->d_stats + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->rmax < 1) c->rmax = 1;
+    ebr_status st = upload_geoms(c);
+    if (st) return st;
+  }
+  return EBR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// levels pipeline
+// ---------------------------------------------------------------------------
+ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
+  int ng = c->ng;
+  if (planning) {
+    AL(c->dep, 8 * (size_t)ng);
+    AL(c->level, ng);
+    AL(c->order_pos, ng);
+    AL(c->g_cell, ng);
+    AL(c->g_geo, ng);
+    AL(c->g_dep, 8 * (size_t)ng);
+    AL(c->g_level, ng);
+    AL(c->g_psi, ng);
+    AL(c->g_n, 3 * (size_t)ng);
+    AL(c->g_meta, ng);
+    AL(c->lev_ptr, ng + c->B + 1);
+    AL(c->wtab, 16 * (size_t)ng);
+    AL(c->ftab, 33 * (size_t)ng);
+    AL(c->gsrc_cnt, ng);
+    AL(c->gsrc_ptr, ng + 1);
+    AL(c->own_flag, 8 * (size_t)ng);
+    AL(c->own_ptr, 8 * (size_t)ng + 1);
+    AL(c->sv, 64 * (size_t)ng);
+    {
+      ebr_status st = balloc(c, &c->lam, 8 * 8 * (size_t)ng);   // [F <= 8][ng] doubles
+      if (st) return st;
+    }
+  }
+  launch_poscell(c->dG, ng, c->gs_cell, c->gs_geo, nullptr, c->pos_of_cell, s);
+  launch_deps(c->dG, ng, c->gs_cell, c->gs_geo, c->gs_meta, c->gs_n, c->tags, c->pos_of_cell,
+              c->dep, c->d_status, s);
+  launch_levels(c->dG, c->B, c->dep, ng, c->level, c->order_pos, c->lev_ptr, c->d_nlev,
+                c->d_status, s);
+  c->launches += 3;
+  CKL();
+  if (planning) {
+    std::vector<int> nl(c->B);
+    CK(cudaMemcpyAsync(nl.data(), c->d_nlev, sizeof(int) * c->B, cudaMemcpyDeviceToHost, s));
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs != 0) return fail(c, (ebr_status)hs, "device status %d while building levels", hs);
+    for (int b = 0; b < c->B; ++b) c->hG[b].n_levels = nl[b];
+    c->h_lev_ptr.assign(ng + c->B + 1, 0);
+    CK(cudaMemcpy(c->h_lev_ptr.data(), c->lev_ptr, sizeof(int) * (ng + c->B + 1), cudaMemcpyDeviceToHost));
+    ebr_status st = upload_geoms(c);
+    if (st) return st;
+  } else {
+    k_check<<<(c->B + 127) / 128, 128, 0, s>>>(c->dG, c->B, c->row_ptr, c->gpos, c->n_iface, c->ng,
+                                               c->d_nlev, 2, c->d_status);
+    c->launches += 1;
+  }
+  launch_reorder(ng, c->order_pos, c->gs_cell, c->gs_geo, c->gs_psi, c->gs_n, c->gs_meta, c->dep,
+                 c->level, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->g_dep, c->g_level, s);
+  launch_poscell(c->dG, ng, c->g_cell, c->g_geo, nullptr, c->pos_of_cell, s);
+  launch_tables(c->dG, ng, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->tags, c->wtab,
+                c->ftab, s);
+  // ghost-target sources
+  launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax, nullptr,
+              c->gsrc_cnt, 0, s);
+  launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, s);
+  c->launches += 7;
+  CKL();
+  if (planning) {
+    CK(cudaMemcpyAsync(&c->n_gsrc, c->gsrc_ptr + ng, sizeof(int), cudaMemcpyDeviceToHost, s));
+    std::vector<int> hp(ng + 1);
+    CK(cudaMemcpyAsync(hp.data(), c->gsrc_ptr, sizeof(int) * (ng + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->h_gsrc_geo.assign(c->B, 0);
+    for (int b = 0; b < c->B; ++b) {
+      const Geom& g = c->hG[b];
+      c->h_gsrc_geo[b] = hp[g.ghost_off + g.n_ghost] - hp[g.ghost_off];
+    }
+    AL(c->gsrc, c->n_gsrc);
+  }
+  launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
+              c->gsrc_ptr, c->gsrc, 1, s);
+  // fluid-target sources
+  launch_fsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax, nullptr,
+              c->own_flag, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s);
+  launch_scan(c->own_flag, c->own_ptr, 8 * ng, c->scan_tmp, s);
+  c->launches += 5;
+  CKL();
+  if (planning) {
+    CK(cudaMemcpyAsync(&c->nft, c->own_ptr + 8 * (size_t)ng, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    AL(c->ft_cell, c->nft);
+    AL(c->ft_geo, c->nft);
+    AL(c->ft_cnt, c->nft);
+    AL(c->ft_ptr, c->nft + 1);
+  }
+  launch_fsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
+              c->own_ptr, c->own_flag, c->ft_cell, c->ft_geo, c->ft_cnt, nullptr, nullptr, 1, s);
+  launch_scan(c->ft_cnt, c->ft_ptr, c->nft, c->scan_tmp, s);
+  c->launches += 4;
+  CKL();
+  if (planning) {
+    CK(cudaMemcpyAsync(&c->n_fsrc, c->ft_ptr + c->nft, sizeof(int), cudaMemcpyDeviceToHost, s));
+    std::vector<int> fg(c->nft);
+    CK(cudaMemcpyAsync(fg.data(), c->ft_geo, sizeof(int) * c->nft, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->h_nft_geo.assign(c->B, 0);
+    for (int t = 0; t < c->nft; ++t) c->h_nft_geo[fg[t]]++;
+    AL(c->ft_src, c->n_fsrc);
+  }
+  launch_fsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
+              c->own_ptr, c->own_flag, c->ft_cell, c->ft_geo, c->ft_cnt, c->ft_ptr, c->ft_src, 2, s);
+  c->launches += 1;
+  CKL();
+  if (planning) {
+    // force chunks (<= 256 ghosts, never straddling geometries)
+    std::vector<int4> ch;
+    std::vector<int> cp(c->B + 1, 0);
+    for (int b = 0; b < c->B; ++b) {
+      const Geom& g = c->hG[b];
+      cp[b] = (int)ch.size();
+      for (int p = g.ghost_off; p < g.ghost_off + g.n_ghost; p += 256)
+        ch.push_back(make_int4(b, p, std::min(p + 256, g.ghost_off + g.n_ghost), 0));
+    }
+    cp[c->B] = (int)ch.size();
+    c->n_chunks = (int)ch.size();
+    AL(c->chunks, c->n_chunks);
+    AL(c->chunk_ptr, c->B + 1);
+    AL(c->partial, 8 * (size_t)std::max(c->n_chunks, 1));
+    CK(cudaMemcpy(c->chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->chunk_ptr, cp.data(), sizeof(int) * cp.size(), cudaMemcpyHostToDevice));
+    c->order_by_size.resize(c->B);
+    for (int b = 0; b < c->B; ++b) c->order_by_size[b] = b;
+    std::stable_sort(c->order_by_size.begin(), c->order_by_size.end(),
+                     [&](int a, int b) { return c->hG[a].n_ghost > c->hG[b].n_ghost; });
+  }
+  return EBR_OK;
+}
+
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+// Chain plan for (kind of pass, dtype, F): geometries whose state fits in one
+// CTA's shared memory, largest first; the rest use level launches.
+ebr_status chain_plan(Ctx* c, int which, int dtype, int F, ChainPlan** out) {
+  long long key = (long long)which * 1000 + dtype * 100 + F;
+  auto it = c->chain_plans.find(key);
+  if (it != c->chain_plans.end()) { *out = &it->second; return EBR_OK; }
+  ChainPlan cp;
+  size_t limit = (size_t)max_smem_optin();
+  std::vector<int> list;
+  for (int b : c->order_by_size) {
+    const Geom& g = c->hG[b];
+    if (g.n_ghost == 0) continue;
+    size_t need = which == 0 ? fill_chain_smem(dtype, g.dim, F, g.n_ghost)
+                             : adj_chain_smem(dtype, F, g.n_ghost, c->h_gsrc_geo[b]);
+    if (need <= limit) {
+      list.push_back(b);
+      cp.smem = std::max(cp.smem, need);
+    } else {
+      cp.fallback.push_back(b);
+    }
+  }
+  cp.n_list = (int)list.size();
+  AL(cp.d_list, std::max<size_t>(list.size(), 1));
+  if (!list.empty())
+    CK(cudaMemcpy(cp.d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice));
+  c->chain_plans[key] = cp;
+  *out = &c->chain_plans[key];
+  return EBR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ebr_status ebr_create(void** out) {
+  if (!out) return EBR_EINVAL;
+  Ctx* c = new Ctx();
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    *out = nullptr;
+    return EBR_ECUDA;
+  }
+  *out = c;
+  return EBR_OK;
+}
+
+void ebr_destroy(void* ctx) {
+  if (!ctx) return;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  free_all(c);
+  delete c;
+}
+
+const char* ebr_last_error(const void* ctx) {
+  if (!ctx) return "null context";
+  return static_cast<const Ctx*>(ctx)->err.c_str();
+}
+
+int64_t ebr_launch_count(const void* ctx) {
+  return ctx ? static_cast<const Ctx*>(ctx)->launches : 0;
+}
+
+ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const ebr_body* h_bodies,
+                    int32_t placement, int8_t* d_tags, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  if (n_geom < 1 || !h_grids || !h_bodies || !d_tags)
+    return fail(c, EBR_EINVAL, "ebr_plan: n_geom >= 1 and non-null grids, bodies, tags required");
+  if (placement < 0 || placement > 2) return fail(c, EBR_EINVAL, "ebr_plan: bad placement %d", placement);
+  free_all(c);
+  c->B = n_geom;
+  c->placement = placement;
+  c->planned = c->levelled = false;
+  c->hG.assign(n_geom, Geom{});
+  c->h_row_off.assign(n_geom + 1, 0);
+  long long cells = 0;
+  int rows = 0;
+  for (int b = 0; b < n_geom; ++b) {
+    const ebr_grid& gr = h_grids[b];
+    const ebr_body& bd = h_bodies[b];
+    Geom& g = c->hG[b];
+    if (gr.dim != 2 && gr.dim != 3) return fail(c, EBR_EINVAL, "geometry %d: dim must be 2 or 3", b);
+    int want_dim = bd.kind == EBR_SPHERE ? 3 : 2;
+    if (bd.kind < 0 || bd.kind > 3) return fail(c, EBR_EINVAL, "geometry %d: bad body kind", b);
+    if (want_dim != gr.dim) return fail(c, EBR_EINVAL, "geometry %d: body kind needs dim %d", b, want_dim);
+    g.dim = gr.dim;
+    long long n3 = 1;
+    for (int a = 0; a < 3; ++a) {
+      long long na = a < gr.dim ? gr.n[a] : 1;
+      if (na < 2 && a < gr.dim) return fail(c, EBR_EINVAL, "geometry %d: n[%d] < 2", b, a);
+      if (a < gr.dim && !(gr.hi[a] > gr.lo[a])) return fail(c, EBR_EINVAL, "geometry %d: hi <= lo", b);
+      g.n[a] = (int)na;
+      g.lo[a] = a < gr.dim ? gr.lo[a] : 0.0;
+      g.h[a] = a < gr.dim ? (gr.hi[a] - gr.lo[a]) / (double)na : 1.0;
+      n3 *= na;
+    }
+    if (n3 > (1LL << 31) - 1) return fail(c, EBR_EINVAL, "geometry %d: more than 2^31-1 cells", b);
+    g.kind = bd.kind;
+    g.placement = placement;
+    for (int a = 0; a < 3; ++a) { g.centre[a] = bd.centre[a]; g.radii[a] = bd.radii[a]; }
+    for (int q = 0; q < 9; ++q) g.rot[q] = bd.rot[q];
+    g.t = bd.thickness;
+    g.c = bd.chord;
+    if ((bd.kind == EBR_CIRCLE || bd.kind == EBR_SPHERE) && !(bd.radii[0] > 0))
+      return fail(c, EBR_EINVAL, "geometry %d: radius must be positive", b);
+    if (bd.kind == EBR_ELLIPSE && !(bd.radii[0] > 0 && bd.radii[1] > 0))
+      return fail(c, EBR_EINVAL, "geometry %d: semi-axes must be positive", b);
+    if (bd.kind == EBR_AIRFOIL4 && !(bd.thickness > 0 && bd.chord > 0 && bd.rot[0] > 0))
+      return fail(c, EBR_EINVAL, "geometry %d: airfoil needs t > 0, chord > 0, |angle| < 90 deg", b);
+    g.cell_off = cells;
+    g.row_off = rows;
+    g.n_rows = g.n[1] * g.n[2];
+    c->h_row_off[b] = rows;
+    cells += n3;
+    rows += g.n_rows;
+  }
+  c->h_row_off[n_geom] = rows;
+  c->total_cells = cells;
+  c->total_rows = rows;
+  AL(c->dG, n_geom);
+  AL(c->d_row_off, n_geom + 1);
+  AL(c->d_status, 1);
+  AL(c->d_stats, 4);
+  AL(c->d_nlev, n_geom);
+  AL(c->runs, rows);
+  AL(c->row_cnt, rows);
+  AL(c->row_ptr, rows + 1);
+  AL(c->pos_of_cell, cells);
+  {
+    size_t tb = scan_temp_bytes(std::max(rows, 1 << 26));
+    ebr_status st = balloc(c, &c->scan_tmp, tb);
+    if (st) return st;
+  }
+  ebr_status st = upload_geoms(c);
+  if (st) return st;
+  CK(cudaMemcpy(c->d_row_off, c->h_row_off.data(), sizeof(int) * (n_geom + 1), cudaMemcpyHostToDevice));
+  CK(cudaMemset(c->d_status, 0, sizeof(int)));
+  CK(cudaMemset(c->d_stats, 0, 4 * sizeof(int)));
+  cudaStream_t s = S(stream);
+  st = run_classify(c, d_tags, s, true);
+  if (st) return st;
+  int hs = 0;
+  CK(cudaMemcpyAsync(&hs, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hs != 0) {
+    CK(cudaMemset(c->d_status, 0, sizeof(int)));
+    return fail(c, (ebr_status)hs, "device status %d during classification", hs);
+  }
+  c->planned = true;
+  return EBR_OK;
+}
+
+ebr_status ebr_classify(void* ctx, int8_t* d_tags, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  if (!c->planned) return fail(c, EBR_EINVAL, "ebr_classify: call ebr_plan first");
+  if (!d_tags) return fail(c, EBR_EINVAL, "ebr_classify: null tags");
+  return run_classify(c, d_tags, S(stream), false);
+}
+
+ebr_status ebr_layout(const void* ctx, int64_t* h_cell_offset) {
+  const Ctx* c = static_cast<const Ctx*>(ctx);
+  if (!c || !h_cell_offset || !c->planned) return EBR_EINVAL;
+  for (int b = 0; b < c->B; ++b) h_cell_offset[b] = c->hG[b].cell_off;
+  h_cell_offset[c->B] = c->total_cells;
+  return EBR_OK;
+}
+
+ebr_status ebr_counts(const void* ctx, ebr_geom_counts* h_counts) {
+  const Ctx* c = static_cast<const Ctx*>(ctx);
+  if (!c || !h_counts || !c->planned) return EBR_EINVAL;
+  for (int b = 0; b < c->B; ++b) {
+    const Geom& g = c->hG[b];
+    h_counts[b].n_cells = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    h_counts[b].n_interface = g.n_iface;
+    h_counts[b].n_ghosts = g.n_ghost;
+    h_counts[b].n_levels = c->levelled ? g.n_levels : 0;
+    h_counts[b].reserved = 0;
+    h_counts[b].n_fluid_targets = c->levelled && (int)c->h_nft_geo.size() == c->B ? c->h_nft_geo[b] : 0;
+  }
+  return EBR_OK;
+}
+
+ebr_status ebr_build_levels(void* ctx, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  if (!c->planned) return fail(c, EBR_EINVAL, "ebr_build_levels: call ebr_plan first");
+  bool planning = !c->levelled;
+  ebr_status st = run_levels(c, S(stream), planning);
+  if (st) return st;
+  c->levelled = true;
+  return EBR_OK;
+}
+
+ebr_status ebr_ghost_info(void* ctx, int32_t* h_geom, int64_t* h_cell, int32_t* h_level,
+                          int8_t* h_tag, double* h_psi, double* h_normal, double* h_S,
+                          int32_t* h_r, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_ghost_info: build the levels first");
+  cudaStream_t s = S(stream);
+  int ng = c->ng;
+  std::vector<int> geo(ng), cell(ng), lev(ng);
+  std::vector<uint32_t> meta(ng);
+  std::vector<double> psi(ng), n(3 * (size_t)ng);
+  CK(cudaMemcpyAsync(geo.data(), c->g_geo, sizeof(int) * ng, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(cell.data(), c->g_cell, sizeof(int) * ng, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(lev.data(), c->g_level, sizeof(int) * ng, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(meta.data(), c->g_meta, sizeof(uint32_t) * ng, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(psi.data(), c->g_psi, sizeof(double) * ng, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(n.data(), c->g_n, sizeof(double) * 3 * ng, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int p = 0; p < ng; ++p) {
+    const Geom& g = c->hG[geo[p]];
+    if (h_geom) h_geom[p] = geo[p];
+    if (h_cell) h_cell[p] = cell[p];
+    if (h_level) h_level[p] = lev[p];
+    if (h_tag) h_tag[p] = meta_fluid(meta[p]) ? -2 : 2;
+    if (h_psi) h_psi[p] = psi[p];
+    int ijk[3] = {cell[p] % g.n[0], (cell[p] / g.n[0]) % g.n[1], cell[p] / (g.n[0] * g.n[1])};
+    for (int a = 0; a < 3; ++a) {
+      double na = n[(size_t)a * ng + p];
+      if (h_normal) h_normal[3 * (size_t)p + a] = na;
+      if (h_S) {
+        double x = a < g.dim ? g.lo[a] + ((double)ijk[a] + 0.5) * g.h[a] : 0.0;
+        h_S[3 * (size_t)p + a] = a < g.dim ? x + psi[p] * na : 0.0;
+      }
+      if (h_r) h_r[3 * (size_t)p + a] = a < g.dim ? meta_r(meta[p], a) : 0;
+    }
+  }
+  return EBR_OK;
+}
+
+ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
+                           const int32_t* h_bc_kind, const void* const* d_bc, int32_t dtype,
+                           int32_t mode, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_reconstruct: build the levels first");
+  if (n_fields < 1 || n_fields > 8 || !d_fields || !h_bc_kind || !d_bc)
+    return fail(c, EBR_EINVAL, "ebr_reconstruct: 1..8 fields with kinds and boundary data required");
+  if (dtype != EBR_F32 && dtype != EBR_F64) return fail(c, EBR_EINVAL, "ebr_reconstruct: bad dtype");
+  for (int f = 0; f < n_fields; ++f) {
+    if (!d_fields[f] || !d_bc[f]) return fail(c, EBR_EINVAL, "ebr_reconstruct: null field %d", f);
+    if (h_bc_kind[f] != 0 && h_bc_kind[f] != 1) return fail(c, EBR_EINVAL, "ebr_reconstruct: bad bc kind");
+  }
+  cudaStream_t s = S(stream);
+  int kinds[8];
+  for (int f = 0; f < n_fields; ++f) kinds[f] = h_bc_kind[f];
+  std::vector<int> level_geoms;
+  if (mode == EBR_MODE_PERSISTENT) {
+    ChainPlan* cp = nullptr;
+    ebr_status st = chain_plan(c, 0, dtype, n_fields, &cp);
+    if (st) return st;
+    if (cp->n_list > 0) {
+      launch_fill_chain(dtype, 0, n_fields, d_fields, kinds, d_bc, c->dG, cp->d_list, cp->n_list,
+                        c->g_cell, c->g_meta, c->g_dep, c->lev_ptr, c->wtab, c->ng, cp->smem,
+                        c->d_status, s);
+      c->launches += 1;
+      CKL();
+    }
+    level_geoms = cp->fallback;
+  } else if (mode == EBR_MODE_LEVEL_LAUNCH) {
+    for (int b = 0; b < c->B; ++b) level_geoms.push_back(b);
+  } else {
+    return fail(c, EBR_EINVAL, "ebr_reconstruct: bad mode %d", mode);
+  }
+  for (int b : level_geoms) {
+    const Geom& g = c->hG[b];
+    for (int lv = 1; lv <= g.n_levels; ++lv) {
+      int p0 = c->h_lev_ptr[g.lev_off + lv - 1], p1 = c->h_lev_ptr[g.lev_off + lv];
+      launch_fill_level(dtype, g.dim, n_fields, d_fields, kinds, d_bc, g.cell_off, p0, p1, c->g_cell,
+                        c->g_meta, c->wtab, c->ng, g.n[0], g.n[1], s);
+      c->launches += 1;
+    }
+  }
+  CKL();
+  return EBR_OK;
+}
+
+ebr_status ebr_boundary_forces(void* ctx, const void* const* d_vel, const void* d_p, int32_t dtype,
+                               double mu, const double* h_dirs, double* d_out, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_boundary_forces: build the levels first");
+  if (!d_vel || !d_p || !h_dirs || !d_out) return fail(c, EBR_EINVAL, "ebr_boundary_forces: null argument");
+  if (dtype != EBR_F32 && dtype != EBR_F64) return fail(c, EBR_EINVAL, "ebr_boundary_forces: bad dtype");
+  int dim = c->hG[0].dim;
+  for (int b = 1; b < c->B; ++b)
+    if (c->hG[b].dim != dim) return fail(c, EBR_EINVAL, "ebr_boundary_forces: mixed dimensions");
+  launch_forces(dtype, dim, d_vel, d_p, mu, h_dirs, c->dG, c->n_chunks, c->chunks, c->g_cell,
+                c->g_geo, c->g_n, c->g_meta, c->ftab, c->ng, c->partial, c->B, d_out, c->chunk_ptr,
+                S(stream));
+  c->launches += c->n_chunks > 0 ? 2 : 1;
+  CKL();
+  return EBR_OK;
+}
+
+ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h_bc_kind,
+                                   const int32_t* h_vel_index, int32_t p_index, double mu,
+                                   const double* h_dirs, const double* d_seed,
+                                   void* const* d_grad_fields, void* const* d_grad_bc, int32_t dtype,
+                                   int32_t accumulate, int32_t mode, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: build the levels first");
+  if (n_fields < 1 || n_fields > 8 || !h_bc_kind || !h_vel_index || !h_dirs || !d_seed ||
+      !d_grad_fields || !d_grad_bc)
+    return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: bad arguments");
+  if (dtype != EBR_F32 && dtype != EBR_F64) return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: bad dtype");
+  int dim = c->hG[0].dim;
+  for (int b = 1; b < c->B; ++b)
+    if (c->hG[b].dim != dim) return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: mixed dimensions");
+  int role[4] = {-1, -1, -1, p_index};
+  for (int a = 0; a < dim; ++a) role[a] = h_vel_index[a];
+  for (int f = 0; f < n_fields; ++f) {
+    if (!d_grad_fields[f] || !d_grad_bc[f]) return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: null gradient %d", f);
+    if (h_bc_kind[f] != 0 && h_bc_kind[f] != 1) return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: bad bc kind");
+  }
+  cudaStream_t s = S(stream);
+  int kinds[8];
+  for (int f = 0; f < n_fields; ++f) kinds[f] = h_bc_kind[f];
+  launch_adj_seed(dim, n_fields, role, mu, h_dirs, d_seed, c->ng, c->g_geo, c->g_n, c->ftab, c->sv, s);
+  c->launches += 1;
+  std::vector<int> level_geoms;
+  if (mode == EBR_MODE_PERSISTENT) {
+    ChainPlan* cp = nullptr;
+    ebr_status st = chain_plan(c, 1, dtype, n_fields, &cp);
+    if (st) return st;
+    if (cp->n_list > 0) {
+      launch_adj_chain(dtype, dim, n_fields, kinds, c->dG, cp->d_list, cp->n_list, c->lev_ptr,
+                       c->gsrc_ptr, c->gsrc, c->g_meta, c->wtab, c->sv, c->ng, c->lam, cp->smem, s);
+      c->launches += 1;
+    }
+    level_geoms = cp->fallback;
+  } else if (mode == EBR_MODE_LEVEL_LAUNCH) {
+    for (int b = 0; b < c->B; ++b) level_geoms.push_back(b);
+  } else {
+    return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: bad mode %d", mode);
+  }
+  for (int b : level_geoms) {
+    const Geom& g = c->hG[b];
+    for (int lv = g.n_levels; lv >= 1; --lv) {
+      int p0 = c->h_lev_ptr[g.lev_off + lv - 1], p1 = c->h_lev_ptr[g.lev_off + lv];
+      launch_adj_level(dtype, dim, n_fields, kinds, p0, p1, c->gsrc_ptr, c->gsrc, c->g_meta, c->wtab,
+                       c->sv, c->ng, c->lam, s);
+      c->launches += 1;
+    }
+  }
+  launch_adj_fluid(dtype, dim, n_fields, kinds, c->nft, c->ft_cell, c->ft_geo, c->ft_ptr, c->ft_src,
+                   c->dG, c->g_meta, c->wtab, c->sv, c->ng, c->lam, d_grad_fields, accumulate, s);
+  launch_adj_bc(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->wtab, c->lam, d_grad_bc,
+                d_grad_fields, accumulate, s);
+  c->launches += 2;
+  CKL();
+  return EBR_OK;
+}
+
+ebr_status ebr_sync_status(void* ctx, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  if (!c->d_status) return EBR_OK;
+  int hs = 0;
+  cudaStream_t s = S(stream);
+  CK(cudaMemcpyAsync(&hs, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hs != 0) {
+    CK(cudaMemset(c->d_status, 0, sizeof(int)));
+    return fail(c, (ebr_status)hs, "device status %d", hs);
+  }
+  return EBR_OK;
+}
+
+}  // extern "C"

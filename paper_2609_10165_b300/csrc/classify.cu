@@ -1,0 +1,489 @@
+// Cell classification and ghost placement (Sec. 3.1, Sec. 7).
+//
+// Every body is convex, so the solid cells of one grid row (cells along x
+// with fixed j, k) form one run [s, t].  A warp owns 32 consecutive rows: each
+// lane estimates the run of its row in closed form (circle, sphere, ellipse)
+// or by float bracketing (airfoil), confirms both ends with the exact double
+// predicate on a 4-cell window, and then the whole warp streams the row's
+// tags (0 / 1) with 16-byte stores.  Cells whose tag can become +-2 are exactly
+// the cells with a face neighbour on the other side of the boundary
+// ("interface" cells); they follow from the runs of a row and its y / z
+// neighbour rows, so they are enumerated per row already sorted by linear
+// index, without re-reading the tag array.
+#include "ebr_kernels.cuh"
+
+namespace ebr {
+
+enum { ROW_EMPTY = 0, ROW_RUN = 1, ROW_TANGENT = 2 };
+
+__device__ inline int iceil_idx(double f) { return (int)ceil(f); }
+__device__ inline int ifloor_idx(double f) { return (int)floor(f); }
+
+// fractional cell coordinate of world position x along axis a: cell i has f = i
+__device__ inline double frac_cell(const Geom& g, int a, double x) {
+  return (x - g.lo[a]) / g.h[a] - 0.5;
+}
+
+__device__ inline float airfoil_f32(float t, float c, float r00, float r01, float bx, float by,
+                                    float x) {
+  // depth y_t(x') - |y'| along a row, x' = r00 x + bx, y' = r01 x + by
+  float xp = r00 * x + bx;
+  float yp = r01 * x + by;
+  float xi = fminf(fmaxf(xp / c, 0.0f), 1.0f);
+  float yt = 5.0f * t * c * (0.2969f * sqrtf(xi) + xi * (-0.1260f + xi * (-0.3516f + xi * (0.2843f + xi * -0.1015f))));
+  return yt - fabsf(yp);
+}
+
+// Estimate the solid run of row (j, k).
+__device__ void estimate_row(const Geom& g, int j, int k, int& state, int& ia, int& ib, int& iv) {
+  const int n = g.n[0];
+  double y = centre_of(g, 1, j);
+  double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
+  state = ROW_EMPTY; ia = 0; ib = -1; iv = 0;
+  double cx, xa, xb;
+  if (g.kind == CIRCLE || g.kind == SPHERE) {
+    double dy = y - g.centre[1];
+    double dz = g.kind == SPHERE ? z - g.centre[2] : 0.0;
+    double r2 = g.radii[0] * g.radii[0];
+    double D = r2 - dy * dy - dz * dz;
+    cx = g.centre[0];
+    if (D < -1e-9 * r2) return;
+    if (D <= 0.0) { state = ROW_TANGENT; iv = (int)lrint(frac_cell(g, 0, cx)); return; }
+    double sD = sqrt(D);
+    xa = cx - sD; xb = cx + sD;
+  } else if (g.kind == ELLIPSE) {
+    double r00 = g.rot[0], r01 = g.rot[1], r10 = g.rot[3], r11 = g.rot[4];
+    double ia2 = 1.0 / (g.radii[0] * g.radii[0]), ib2 = 1.0 / (g.radii[1] * g.radii[1]);
+    double v = y - g.centre[1];
+    double A = r00 * r00 * ia2 + r01 * r01 * ib2;
+    double Bq = 2.0 * v * (r00 * r10 * ia2 + r01 * r11 * ib2);
+    double C = v * v * (r10 * r10 * ia2 + r11 * r11 * ib2) - 1.0;
+    double disc = Bq * Bq - 4.0 * A * C;
+    double uv = -Bq / (2.0 * A);
+    cx = g.centre[0] + uv;
+    double scale = Bq * Bq + 4.0 * A * fabs(C);
+    if (disc < -1e-9 * scale) return;
+    if (disc <= 0.0) { state = ROW_TANGENT; iv = (int)lrint(frac_cell(g, 0, cx)); return; }
+    double sd = sqrt(disc) / (2.0 * A);
+    xa = cx - sd; xb = cx + sd;
+  } else {  // AIRFOIL4: float bracketing of the concave depth along the row
+    float r00 = (float)g.rot[0], r01 = (float)g.rot[1];
+    double by0 = y - g.centre[1];
+    // x' = r00 (x - lx) + r10 (y - ly); write x' = r00 * X + bx with X = x - lx
+    float bx = (float)(g.rot[3] * by0), byy = (float)(g.rot[4] * by0);
+    float c = (float)g.c, t = (float)g.t;
+    if (!(r00 > 0.0f)) { state = -1; return; }
+    float X0 = (0.0f - bx) / r00, X1 = (c - bx) / r00;
+    // quick reject: |y'| along the segment exceeds the maximum half thickness
+    float ymin = fminf(fabsf(r01 * X0 + byy), fabsf(r01 * X1 + byy));
+    if ((r01 * X0 + byy) * (r01 * X1 + byy) < 0.0f) ymin = 0.0f;
+    if (ymin > 0.6f * t * c + 1e-4f * c) return;
+    float lo = X0, hi = X1;
+    for (int it = 0; it < 60; ++it) {
+      float m1 = lo + (hi - lo) * (1.0f / 3.0f), m2 = hi - (hi - lo) * (1.0f / 3.0f);
+      if (airfoil_f32(t, c, r00, r01, bx, byy, m1) < airfoil_f32(t, c, r00, r01, bx, byy, m2)) lo = m1;
+      else hi = m2;
+    }
+    float xm = 0.5f * (lo + hi);
+    float fm = airfoil_f32(t, c, r00, r01, bx, byy, xm);
+    float tol = 1e-4f * c;
+    cx = g.centre[0] + (double)xm;
+    if (fm < -tol) return;
+    if (fm < tol) { state = ROW_TANGENT; iv = (int)lrint(frac_cell(g, 0, cx)); return; }
+    float a = X0, b = xm;
+    if (airfoil_f32(t, c, r00, r01, bx, byy, X0) < 0.0f) {
+      for (int it = 0; it < 40; ++it) {
+        float m = 0.5f * (a + b);
+        if (airfoil_f32(t, c, r00, r01, bx, byy, m) < 0.0f) a = m; else b = m;
+      }
+    }
+    float xa_f = 0.5f * (a + b);
+    a = xm; b = X1;
+    if (airfoil_f32(t, c, r00, r01, bx, byy, X1) < 0.0f) {
+      for (int it = 0; it < 40; ++it) {
+        float m = 0.5f * (a + b);
+        if (airfoil_f32(t, c, r00, r01, bx, byy, m) >= 0.0f) a = m; else b = m;
+      }
+    }
+    float xb_f = 0.5f * (a + b);
+    xa = g.centre[0] + (double)xa_f;
+    xb = g.centre[0] + (double)xb_f;
+  }
+  double fa = frac_cell(g, 0, xa), fb = frac_cell(g, 0, xb);
+  if (fb < -2.0 || fa > n + 1.0) return;
+  ia = iceil_idx(fmax(fa, -4.0));
+  ib = ifloor_idx(fmin(fb, (double)n + 3.0));
+  if (ia > ib) { state = ROW_TANGENT; iv = (int)lrint(frac_cell(g, 0, cx)); return; }
+  state = ROW_RUN;
+}
+
+__device__ inline bool pred_cell(const Geom& g, int i, int j, int k) {
+  if (i < 0 || i >= g.n[0]) return false;
+  return solid_cell(g, i, j, k);
+}
+
+// exact run [s, t] of a row (s > t: empty); counts fallbacks in stats[0]
+__device__ void exact_run(const Geom& g, int j, int k, int& s, int& t, int* status, int* stats) {
+  const int n = g.n[0];
+  int state, ia, ib, iv;
+  estimate_row(g, j, k, state, ia, ib, iv);
+  s = 0; t = -1;
+  if (state < 0) { set_status(status, S_EINVAL); return; }
+  if (state == ROW_EMPTY) return;
+  bool ok = true;
+  if (state == ROW_RUN) {
+    unsigned bl = 0, bu = 0;
+    for (int m = 0; m < 4; ++m) {
+      if (pred_cell(g, ia - 2 + m, j, k)) bl |= 1u << m;
+      if (pred_cell(g, ib - 1 + m, j, k)) bu |= 1u << m;
+    }
+    if (bl == 0 || bu == 0) ok = false;
+    else {
+      int m0 = __ffs(bl) - 1, m1 = 31 - __clz(bu);
+      s = ia - 2 + m0;
+      t = ib - 1 + m1;
+      if (m0 == 0 && s > 0) ok = false;
+      if (m1 == 3 && t < n - 1) ok = false;
+      if (s > t) ok = false;
+    }
+  } else {  // tangent: a short run (or none) around the vertex
+    unsigned bw = 0;
+    for (int m = 0; m < 8; ++m)
+      if (pred_cell(g, iv - 3 + m, j, k)) bw |= 1u << m;
+    if (bw == 0) { s = 0; t = -1; return; }
+    int m0 = __ffs(bw) - 1, m1 = 31 - __clz(bw);
+    s = iv - 3 + m0;
+    t = iv - 3 + m1;
+    if ((m0 == 0 && s > 0) || (m1 == 7 && t < n - 1)) ok = false;
+    unsigned run = bw >> m0;
+    if ((run & (run + 1)) != 0) ok = false;     // not contiguous
+  }
+  if (!ok) {
+    // robust fallback: sweep the whole row with the exact predicate
+    atomicAdd(&stats[0], 1);
+    s = 0; t = -1;
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+      if (solid_cell(g, i, j, k)) {
+        if (!any) { s = i; any = true; }
+        t = i;
+      }
+    }
+    if (!any) { s = 0; t = -1; }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_rows(const Geom* __restrict__ G, const int* __restrict__ row_off,
+                                              int B, int total_rows, int2* __restrict__ runs,
+                                              int8_t* __restrict__ tags, int* status, int* stats) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int base = warp * 32; base < total_rows; base += nwarps * 32) {
+    int row = base + lane;
+    int s = 0, t = -1, nx = 0;
+    long long start = 0;
+    if (row < total_rows) {
+      int b = find_seg(row_off, B, row);
+      const Geom& g = G[b];
+      int local = row - g.row_off;
+      int j = local % g.n[1];
+      int k = local / g.n[1];
+      exact_run(g, j, k, s, t, status, stats);
+      runs[row] = make_int2(s, t);
+      nx = g.n[0];
+      start = g.cell_off + (long long)local * nx;
+    }
+    // the warp streams the tags of its rows
+    int nvalid = min(32, total_rows - base);
+    for (int r = 0; r < nvalid; ++r) {
+      int rs = __shfl_sync(0xffffffffu, s, r);
+      int rt = __shfl_sync(0xffffffffu, t, r);
+      int rn = __shfl_sync(0xffffffffu, nx, r);
+      long long rst = __shfl_sync(0xffffffffu, start, r);
+      long long end = rst + rn;
+      // 16-byte alignment of the actual addresses (the caller's buffer may be offset)
+      long long mis = (long long)(reinterpret_cast<uintptr_t>(tags) & 15u);
+      long long a0 = ((rst + mis + 15) & ~15LL) - mis;
+      long long a1 = ((end + mis) & ~15LL) - mis;
+      if (a0 > end) a0 = end;
+      if (a1 < a0) a1 = a0;
+      // head bytes [rst, a0) and tail bytes [a1, end)
+      long long nh = a0 - rst, nt = end - a1;
+      if (lane < nh) {
+        long long i = lane;
+        tags[rst + i] = (int8_t)(i >= rs && i <= rt);
+      }
+      if (lane < nt) {
+        long long i = a1 + lane - rst;
+        tags[a1 + lane] = (int8_t)(i >= rs && i <= rt);
+      }
+      // aligned middle: 16 cells per lane per step
+      for (long long c = a0 + 16LL * lane; c < a1; c += 16LL * 32) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            long long i = c + 4 * q + m - rst;
+            v |= (uint32_t)(i >= rs && i <= rt) << (8 * m);
+          }
+          w[q] = v;
+        }
+        *reinterpret_cast<uint4*>(tags + c) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+  }
+}
+
+void launch_rows(const Geom* G, const int* row_off, int B, int total_rows, int2* runs,
+                 int8_t* tags, int* status, int* stats, cudaStream_t s) {
+  if (total_rows <= 0) return;
+  int warps = (total_rows + 31) / 32;
+  int blocks = (warps + 7) / 8;
+  k_rows<<<blocks, 256, 0, s>>>(G, row_off, B, total_rows, runs, tags, status, stats);
+}
+
+// ---------------------------------------------------------------------------
+// interface cells of a row from the runs of the row and its neighbour rows
+// ---------------------------------------------------------------------------
+struct Iv { int a, b; };
+
+__device__ inline void add_iv(Iv* v, int& m, int a, int b, int n) {
+  a = max(a, 0);
+  b = min(b, n - 1);
+  if (a <= b) { v[m].a = a; v[m].b = b; ++m; }
+}
+
+// R \ Q for runs (s > t empty)
+__device__ inline void add_diff(Iv* v, int& m, int2 R, int2 Q, int n) {
+  if (R.x > R.y) return;
+  if (Q.x > Q.y) { add_iv(v, m, R.x, R.y, n); return; }
+  add_iv(v, m, R.x, min(R.y, Q.x - 1), n);
+  add_iv(v, m, max(R.x, Q.y + 1), R.y, n);
+}
+
+__global__ void k_iface(const Geom* __restrict__ G, const int* __restrict__ row_off, int B,
+                        int total_rows, const int2* __restrict__ runs, int* __restrict__ row_cnt,
+                        const int* __restrict__ row_ptr, int* __restrict__ iface_cell,
+                        int* __restrict__ iface_geo, int8_t* __restrict__ iface_solid, int write,
+                        int cap, int* status) {
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= total_rows) return;
+  int b = find_seg(row_off, B, row);
+  const Geom& g = G[b];
+  int local = row - g.row_off;
+  int ny = g.n[1], nz = g.dim == 3 ? g.n[2] : 1, n = g.n[0];
+  int j = local % ny, k = local / ny;
+  int2 R = runs[row];
+  Iv v[24];
+  int m = 0;
+  if (R.x <= R.y) {
+    if (R.x > 0) { add_iv(v, m, R.x, R.x, n); add_iv(v, m, R.x - 1, R.x - 1, n); }
+    if (R.y < n - 1) { add_iv(v, m, R.y, R.y, n); add_iv(v, m, R.y + 1, R.y + 1, n); }
+  }
+  const int dj[4] = {-1, 1, 0, 0}, dk[4] = {0, 0, -1, 1};
+  for (int q = 0; q < 4; ++q) {
+    int jj = j + dj[q], kk = k + dk[q];
+    if (jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
+    int2 Q = runs[g.row_off + jj + ny * kk];
+    add_diff(v, m, R, Q, n);
+    add_diff(v, m, Q, R, n);
+  }
+  // sort by start, merge
+  for (int x = 1; x < m; ++x) {
+    Iv key = v[x];
+    int y = x - 1;
+    while (y >= 0 && v[y].a > key.a) { v[y + 1] = v[y]; --y; }
+    v[y + 1] = key;
+  }
+  int w = 0;
+  for (int x = 0; x < m; ++x) {
+    if (w > 0 && v[x].a <= v[w - 1].b + 1) v[w - 1].b = max(v[w - 1].b, v[x].b);
+    else v[w++] = v[x];
+  }
+  if (!write) {
+    int cnt = 0;
+    for (int x = 0; x < w; ++x) cnt += v[x].b - v[x].a + 1;
+    row_cnt[row] = cnt;
+    return;
+  }
+  int o = row_ptr[row];
+  int rowbase = n * (j + ny * k);
+  for (int x = 0; x < w; ++x) {
+    for (int i = v[x].a; i <= v[x].b; ++i) {
+      if (o >= cap) { set_status(status, S_ESHAPE); return; }
+      iface_cell[o] = rowbase + i;
+      iface_geo[o] = b;
+      iface_solid[o] = (int8_t)(i >= R.x && i <= R.y);
+      ++o;
+    }
+  }
+}
+
+void launch_iface(const Geom* G, const int* row_off, int B, int total_rows, const int2* runs,
+                  int* row_cnt, const int* row_ptr, int* iface_cell, int* iface_geo,
+                  int8_t* iface_solid, int write, int iface_cap, int* status, cudaStream_t s) {
+  if (total_rows <= 0) return;
+  k_iface<<<(total_rows + 127) / 128, 128, 0, s>>>(G, row_off, B, total_rows, runs, row_cnt,
+                                                   row_ptr, iface_cell, iface_geo, iface_solid,
+                                                   write, iface_cap, status);
+}
+
+// ---------------------------------------------------------------------------
+// placement: psi, n at interface cells; CGC / HGC candidate tags
+// ---------------------------------------------------------------------------
+__device__ inline void cell_ijk(const Geom& g, int cell, int& i, int& j, int& k) {
+  i = cell % g.n[0];
+  int r = cell / g.n[0];
+  j = r % g.n[1];
+  k = r / g.n[1];
+}
+
+__global__ void k_place(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
+                        const int* __restrict__ iface_geo, const int8_t* __restrict__ iface_solid,
+                        int placement, int8_t* __restrict__ tags, double* __restrict__ psi_out,
+                        double* __restrict__ n_out, int* status) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_iface) return;
+  const Geom& g = G[iface_geo[m]];
+  int cell = iface_cell[m];
+  bool solid = iface_solid[m] != 0;
+  int i, j, k;
+  cell_ijk(g, cell, i, j, k);
+  double psi = 0.0, nv[3] = {0.0, 0.0, 0.0};
+  int8_t tag = solid ? 1 : 0;
+  bool need = placement == HGC || solid;
+  if (need) {
+    double x = centre_of(g, 0, i), y = centre_of(g, 1, j);
+    double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
+    if (!closest_point(g, x, y, z, solid, psi, nv)) { set_status(status, S_EINVAL); return; }
+    if (placement == HGC) {
+      double half = 0.5 * delta_n(g, nv);
+      if (solid && psi <= half) tag = 2;
+      if (!solid && -psi < half) tag = -2;
+    } else {
+      tag = 2;   // solid interface cell = solid cell with a fluid face neighbour
+    }
+  }
+  psi_out[m] = psi;
+  n_out[m] = nv[0];
+  n_out[n_iface + m] = nv[1];
+  n_out[2 * (size_t)n_iface + m] = nv[2];
+  tags[g.cell_off + cell] = tag;
+}
+
+void launch_place(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
+                  const int8_t* iface_solid, int placement, int8_t* tags, double* iface_psi,
+                  double* iface_n, int* status, cudaStream_t s) {
+  if (n_iface <= 0) return;
+  k_place<<<(n_iface + 127) / 128, 128, 0, s>>>(G, n_iface, iface_cell, iface_geo, iface_solid,
+                                                placement, tags, iface_psi, iface_n, status);
+}
+
+// HGC reclassification.  pass 0 (A): -2 without a tag-1 face neighbour -> 0.
+// pass 1 (B): +2 without a tag-0 face neighbour -> 1.  In place is safe: pass A
+// only turns -2 into 0 and tests for 1; pass B only turns +2 into 1 and tests
+// for 0; pass B runs after pass A has completed.
+__global__ void k_reclassify(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
+                             const int* __restrict__ iface_geo, int8_t* __restrict__ tags, int pass) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_iface) return;
+  const Geom& g = G[iface_geo[m]];
+  int cell = iface_cell[m];
+  int8_t* tg = tags + g.cell_off;
+  int8_t me = tg[cell];
+  int8_t want_self = pass == 0 ? -2 : 2;
+  if (me != want_self) return;
+  int8_t look = pass == 0 ? 1 : 0;
+  int i, j, k;
+  cell_ijk(g, cell, i, j, k);
+  int ijk[3] = {i, j, k};
+  int stride[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  bool found = false;
+  for (int a = 0; a < g.dim && !found; ++a) {
+    if (ijk[a] > 0 && tg[cell - stride[a]] == look) found = true;
+    if (ijk[a] < g.n[a] - 1 && tg[cell + stride[a]] == look) found = true;
+  }
+  if (!found) tg[cell] = pass == 0 ? 0 : 1;
+}
+
+void launch_reclassify(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
+                       int8_t* tags, int pass, cudaStream_t s) {
+  if (n_iface <= 0) return;
+  k_reclassify<<<(n_iface + 127) / 128, 128, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, pass);
+}
+
+__global__ void k_ghost_flags(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
+                              const int* __restrict__ iface_geo, const int8_t* __restrict__ tags,
+                              int* __restrict__ flags) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_iface) return;
+  const Geom& g = G[iface_geo[m]];
+  int8_t t = tags[g.cell_off + iface_cell[m]];
+  flags[m] = (t == 2 || t == -2) ? 1 : 0;
+}
+
+void launch_ghost_flags(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
+                        const int8_t* tags, int* flags, cudaStream_t s) {
+  if (n_iface <= 0) return;
+  k_ghost_flags<<<(n_iface + 255) / 256, 256, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, flags);
+}
+
+__global__ void k_ghost_write(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
+                              const int* __restrict__ iface_geo, const int8_t* __restrict__ tags,
+                              const double* __restrict__ iface_psi, const double* __restrict__ iface_n,
+                              const int* __restrict__ gpos, int placement, int cap,
+                              int* __restrict__ gs_cell, int* __restrict__ gs_geo,
+                              double* __restrict__ gs_psi, double* __restrict__ gs_n,
+                              uint32_t* __restrict__ gs_meta, int* rmax, int* status) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_iface) return;
+  int b = iface_geo[m];
+  const Geom& g = G[b];
+  int cell = iface_cell[m];
+  int8_t t = tags[g.cell_off + cell];
+  if (t != 2 && t != -2) return;
+  int s = gpos[m];
+  if (s >= cap) { set_status(status, S_ESHAPE); return; }
+  double psi = iface_psi[m];
+  double nv[3] = {iface_n[m], iface_n[n_iface + m], iface_n[2 * (size_t)n_iface + m]};
+  uint32_t meta = 0;
+  int rloc = 1;
+  for (int a = 0; a < g.dim; ++a) {
+    if (nv[a] < 0.0) meta |= 1u << a;
+    int r = 1;
+    if (placement == CGC_ES) {
+      // Eq. stencil_anisotropic: r_i = max(1, ceil(2 |n_i psi| / dx_i))
+      double q = 2.0 * fabs(psi * nv[a]) / g.h[a];
+      r = max(1, (int)ceil(q));
+    }
+    if (r > 15) { set_status(status, S_EINVAL); r = 15; }
+    rloc = max(rloc, r);
+    meta |= (uint32_t)r << (3 + 4 * a);
+  }
+  if (t == -2) meta |= 1u << 22;
+  gs_cell[s] = cell;
+  gs_geo[s] = b;
+  gs_psi[s] = psi;
+  gs_n[s] = nv[0];
+  gs_n[cap + s] = nv[1];
+  gs_n[2 * (size_t)cap + s] = nv[2];
+  gs_meta[s] = meta;
+  atomicMax(rmax, rloc);
+}
+
+void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
+                        const int8_t* tags, const double* iface_psi, const double* iface_n,
+                        const int* gpos, int placement, int ng_cap, int* gs_cell, int* gs_geo,
+                        double* gs_psi, double* gs_n, uint32_t* gs_meta, int* rmax,
+                        int* status, cudaStream_t s) {
+  if (n_iface <= 0) return;
+  k_ghost_write<<<(n_iface + 127) / 128, 128, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags,
+                                                      iface_psi, iface_n, gpos, placement, ng_cap,
+                                                      gs_cell, gs_geo, gs_psi, gs_n, gs_meta, rmax,
+                                                      status);
+}
+
+}  // namespace ebr

@@ -1,0 +1,307 @@
+// Device-side data structures and geometry for the ghost-cell library.
+//
+// Geometry (Sec. 3.1): cell centres x_a = lo_a + (i_a + 1/2) h_a; a cell is
+// solid when its centre lies in the closed body (psi >= 0, Eq.
+// signed_distance).  psi, the boundary point S and the unit normal n (into the
+// fluid) are evaluated in double only on cells next to the boundary.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ebr {
+
+enum BodyKind { CIRCLE = 0, SPHERE = 1, ELLIPSE = 2, AIRFOIL4 = 3 };
+enum Placement { HGC = 0, CGC = 1, CGC_ES = 2 };
+
+// status codes (same values as ebr_status)
+enum Status {
+  S_OK = 0, S_EINVAL = -1, S_ENOMEM = -2, S_ECUDA = -3, S_ECYCLE = -4,
+  S_ESTENCIL_OOB = -5, S_ESTENCIL_SOLID = -6, S_ETIMEOUT = -7, S_ENONFINITE = -8,
+  S_ESHAPE = -9
+};
+
+constexpr int MAXK = 7;      // stencil members in 3D (P1..P7)
+
+// One geometry (grid + body) as the kernels see it.
+struct Geom {
+  int dim;
+  int n[3];
+  double lo[3];
+  double h[3];
+  int kind;
+  int placement;
+  double centre[3];
+  double radii[3];
+  double rot[9];        // body -> world, row-major
+  double t, c;          // airfoil thickness and chord
+  long long cell_off;   // first flat cell
+  int row_off;          // first flat row (rows run along x)
+  int n_rows;           // n[1] * n[2]
+  // planned sizes / offsets (filled after the planning pass)
+  int iface_off, n_iface;
+  int ghost_off, n_ghost;
+  int lev_off, n_levels;     // level pointers at lev_ptr[lev_off .. lev_off + n_levels]
+  int ftgt_off, n_ftgt;      // fluid adjoint targets
+};
+
+// ---------------------------------------------------------------------------
+// ghost meta word
+//   bits 0..2   e_a < 0 (sign of the normal component; n_a = 0 -> e_a = +1)
+//   bits 3..14  r_x, r_y, r_z (4 bits each)
+//   bits 15..21 active mask of P_1..P_K (structurally non-zero weight)
+//   bit  22     centre in the fluid (tag -2)
+//   bits 23..29 member k is itself a ghost (dependency)
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int meta_e(uint32_t m, int a) { return (m >> a) & 1u ? -1 : 1; }
+__host__ __device__ inline int meta_r(uint32_t m, int a) { return (m >> (3 + 4 * a)) & 15u; }
+__host__ __device__ inline uint32_t meta_active(uint32_t m) { return (m >> 15) & 127u; }
+__host__ __device__ inline bool meta_fluid(uint32_t m) { return (m >> 22) & 1u; }
+__host__ __device__ inline uint32_t meta_depmask(uint32_t m) { return (m >> 23) & 127u; }
+
+// Offsets of P_1..P_K in units of r_a e_a h_a (Secs. 4 and 5, Appendix A).
+__host__ __device__ inline int stencil_k(int dim) { return dim == 2 ? 3 : 7; }
+__host__ __device__ inline void stencil_off(int dim, int k, int o[3]) {
+  if (dim == 2) {
+    const int t[3][2] = {{1, 0}, {0, 1}, {1, 1}};
+    o[0] = t[k][0]; o[1] = t[k][1]; o[2] = 0;
+  } else {
+    const int t[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 1}};
+    o[0] = t[k][0]; o[1] = t[k][1]; o[2] = t[k][2];
+  }
+}
+
+// Cell centre along axis a, evaluated without contraction.
+__device__ __forceinline__ double centre_of(const Geom& g, int a, int i) {
+  return __dadd_rn(g.lo[a], __dmul_rn((double)i + 0.5, g.h[a]));
+}
+
+// ---------------------------------------------------------------------------
+// inside predicate (solid <=> psi >= 0), double, no contraction
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sq(double v) { return __dmul_rn(v, v); }
+
+__device__ inline double airfoil_yt(double t, double c, double x) {
+  // y_t(x) = 5 t c [a0 sqrt(xi) + a1 xi + a2 xi^2 + a3 xi^3 + a4 xi^4], xi = x / c
+  double xi = __ddiv_rn(x, c);
+  double poly = __dadd_rn(-0.1260, __dmul_rn(xi, __dadd_rn(-0.3516, __dmul_rn(xi, __dadd_rn(0.2843, __dmul_rn(xi, -0.1015))))));
+  double s = __dadd_rn(__dmul_rn(0.2969, __dsqrt_rn(xi)), __dmul_rn(xi, poly));
+  return __dmul_rn(__dmul_rn(__dmul_rn(5.0, t), c), s);
+}
+
+__device__ inline void to_body2(const Geom& g, double x, double y, double& px, double& py) {
+  double dx = __dadd_rn(x, -g.centre[0]);
+  double dy = __dadd_rn(y, -g.centre[1]);
+  px = __dadd_rn(__dmul_rn(g.rot[0], dx), __dmul_rn(g.rot[3], dy));
+  py = __dadd_rn(__dmul_rn(g.rot[1], dx), __dmul_rn(g.rot[4], dy));
+}
+
+__device__ inline bool solid_at(const Geom& g, double x, double y, double z) {
+  switch (g.kind) {
+    case CIRCLE: {
+      double q = __dadd_rn(sq(__dadd_rn(x, -g.centre[0])), sq(__dadd_rn(y, -g.centre[1])));
+      return __dsqrt_rn(q) <= g.radii[0];
+    }
+    case SPHERE: {
+      double q = __dadd_rn(__dadd_rn(sq(__dadd_rn(x, -g.centre[0])), sq(__dadd_rn(y, -g.centre[1]))),
+                           sq(__dadd_rn(z, -g.centre[2])));
+      return __dsqrt_rn(q) <= g.radii[0];
+    }
+    case ELLIPSE: {
+      double px, py;
+      to_body2(g, x, y, px, py);
+      double qx = __ddiv_rn(px, g.radii[0]);
+      double qy = __ddiv_rn(py, g.radii[1]);
+      return __dadd_rn(sq(qx), sq(qy)) <= 1.0;
+    }
+    default: {  // AIRFOIL4
+      double px, py;
+      to_body2(g, x, y, px, py);
+      if (!(px >= 0.0 && px <= g.c)) return false;
+      return fabs(py) <= airfoil_yt(g.t, g.c, px);
+    }
+  }
+}
+
+__device__ inline bool solid_cell(const Geom& g, int i, int j, int k) {
+  double x = centre_of(g, 0, i), y = centre_of(g, 1, j);
+  double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
+  return solid_at(g, x, y, z);
+}
+
+// ---------------------------------------------------------------------------
+// closest point: unsigned distance and unit normal (world frame, into fluid)
+// ---------------------------------------------------------------------------
+
+// Ellipse x^2/a^2 + y^2/b^2 = 1, body-frame point (p, q).  Closest point
+// X = a^2 p / (a^2 + t), Y = b^2 q / (b^2 + t) where t solves
+// F(t) = (a p / (a^2 + t))^2 + (b q / (b^2 + t))^2 - 1 = 0.  F is decreasing and
+// convex on t > -min(a^2, b^2), so safeguarded Newton from t = 0 converges.
+__device__ inline void ellipse_closest(double a, double b, double p, double q,
+                                       double& dist, double& nx, double& ny) {
+  double a2 = a * a, b2 = b * b;
+  double tmin = -fmin(a2, b2);
+  double t = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    double ua = a2 + t, ub = b2 + t;
+    double fx = a * p / ua, fy = b * q / ub;
+    double F = fx * fx + fy * fy - 1.0;
+    double dF = -2.0 * (fx * fx / ua + fy * fy / ub);
+    if (F == 0.0 || dF == 0.0) break;
+    double tn = t - F / dF;
+    if (!(tn > tmin)) tn = 0.5 * (t + tmin);
+    if (tn == t) break;
+    double dt = fabs(tn - t);
+    t = tn;
+    if (dt <= 1e-17 * fmax(fabs(t), 1e-300)) break;
+  }
+  double ua = a2 + t, ub = b2 + t;
+  // G - S = (p t / ua, q t / ub): no cancellation
+  double ex = p * t / ua, ey = q * t / ub;
+  dist = sqrt(ex * ex + ey * ey);
+  double X = a2 * p / ua, Y = b2 * q / ub;
+  double mx = X / a2, my = Y / b2;
+  double mn = sqrt(mx * mx + my * my);
+  nx = mx / mn;
+  ny = my / mn;
+}
+
+// Upper airfoil surface as polynomials in u = sqrt(x / c).
+__device__ inline void airfoil_u(double t, double c, double u, double& x, double& y,
+                                 double& dx, double& dy, double& ddx, double& ddy) {
+  const double a0 = 0.2969, a1 = -0.1260, a2 = -0.3516, a3 = 0.2843, a4 = -0.1015;
+  double k = 5.0 * t * c;
+  double u2 = u * u, u3 = u2 * u, u4 = u2 * u2, u5 = u4 * u, u6 = u4 * u2, u7 = u6 * u, u8 = u4 * u4;
+  x = c * u2;
+  y = k * (a0 * u + a1 * u2 + a2 * u4 + a3 * u6 + a4 * u8);
+  dx = 2.0 * c * u;
+  dy = k * (a0 + 2.0 * a1 * u + 4.0 * a2 * u3 + 6.0 * a3 * u5 + 8.0 * a4 * u7);
+  ddx = 2.0 * c;
+  ddy = k * (2.0 * a1 + 12.0 * a2 * u2 + 30.0 * a3 * u4 + 56.0 * a4 * u6);
+}
+
+// Closest point on the airfoil to the body-frame point (px, py): the upper
+// surface by coarse float sampling in u then safeguarded Newton on
+// g(u) = (P(u) - q) . P'(u) in double; the base x = c; the lower surface by
+// symmetry (|py|, exact ties -> upper surface).  At the trailing-edge corner
+// a fluid point's normal is (G - S) / |G - S|.
+__device__ inline void airfoil_closest(double t, double c, double px, double py, bool inside,
+                                       double& dist, double& nx, double& ny) {
+  double qx = px, qy = fabs(py);
+  // coarse sampling (float)
+  const int NS = 64;
+  float fqx = (float)qx, fqy = (float)qy, fc = (float)c, ft = (float)t;
+  int best = 0;
+  float bd = 3.4e38f;
+  for (int s = 0; s <= NS; ++s) {
+    float u = (float)s / NS;
+    float u2 = u * u;
+    float x = fc * u2;
+    float y = 5.0f * ft * fc * (0.2969f * u + u2 * (-0.1260f + u2 * (-0.3516f + u2 * (0.2843f + u2 * -0.1015f))));
+    float d = (x - fqx) * (x - fqx) + (y - fqy) * (y - fqy);
+    if (d < bd) { bd = d; best = s; }
+  }
+  double lo = fmax(0.0, (double)(best - 1) / NS), hi = fmin(1.0, (double)(best + 1) / NS);
+  auto g = [&](double u, double& gv, double& dg) {
+    double x, y, dx, dy, ddx, ddy;
+    airfoil_u(t, c, u, x, y, dx, dy, ddx, ddy);
+    gv = (x - qx) * dx + (y - qy) * dy;
+    dg = dx * dx + dy * dy + (x - qx) * ddx + (y - qy) * ddy;
+  };
+  double glo, dlo, ghi, dhi;
+  g(lo, glo, dlo);
+  g(hi, ghi, dhi);
+  double u;
+  if (glo >= 0.0) {
+    u = lo;                    // distance increases from lo on (lo == 0 here)
+  } else if (ghi <= 0.0) {
+    u = hi;                    // distance decreases up to hi (hi == 1 here)
+  } else {
+    u = 0.5 * (lo + hi);
+    for (int it = 0; it < 100; ++it) {
+      double gv, dg;
+      g(u, gv, dg);
+      if (gv == 0.0) break;
+      if (gv < 0.0) lo = u; else hi = u;
+      double un = u - gv / dg;
+      if (!(un > lo && un < hi) || dg <= 0.0) un = 0.5 * (lo + hi);
+      if (un == u || hi - lo <= 1e-17) { u = un; break; }
+      u = un;
+    }
+  }
+  double x, y, dx, dy, ddx, ddy;
+  airfoil_u(t, c, u, x, y, dx, dy, ddx, ddy);
+  double d2u = (x - qx) * (x - qx) + (y - qy) * (y - qy);
+  double yte, tmp1, tmp2, tmp3, tmp4, tmp5;
+  airfoil_u(t, c, 1.0, tmp1, yte, tmp2, tmp3, tmp4, tmp5);
+  double by = fmin(qy, yte);
+  double d2b = (qx - c) * (qx - c) + (qy - by) * (qy - by);
+  double sx, sy;
+  bool base = d2b < d2u;
+  if (base) {
+    sx = c; sy = by; nx = 1.0; ny = 0.0;
+  } else {
+    sx = x; sy = y;
+    double fn = sqrt(dx * dx + dy * dy);
+    nx = -dy / fn;
+    ny = dx / fn;
+  }
+  bool corner = !inside && ((base && qy > yte) || (!base && u == 1.0));
+  if (corner) {
+    sx = c; sy = yte;
+    double vx = qx - c, vy = qy - yte, vn = sqrt(vx * vx + vy * vy);
+    nx = vx / vn;
+    ny = vy / vn;
+  }
+  dist = sqrt((qx - sx) * (qx - sx) + (qy - sy) * (qy - sy));
+  if (py < 0.0) ny = -ny;
+}
+
+// psi (signed by the solid flag) and world-frame unit normal for a cell centre.
+// Returns false when the normal is undefined (centre at a circle's centre).
+__device__ inline bool closest_point(const Geom& g, double x, double y, double z, bool solid,
+                                     double& psi, double n[3]) {
+  n[0] = n[1] = n[2] = 0.0;
+  double dist;
+  switch (g.kind) {
+    case CIRCLE:
+    case SPHERE: {
+      double dx = x - g.centre[0], dy = y - g.centre[1];
+      double dz = g.kind == SPHERE ? z - g.centre[2] : 0.0;
+      double rho = __dsqrt_rn(__dadd_rn(__dadd_rn(sq(dx), sq(dy)), sq(dz)));
+      if (rho == 0.0) return false;
+      dist = fabs(g.radii[0] - rho);
+      n[0] = dx / rho; n[1] = dy / rho; n[2] = dz / rho;
+      break;
+    }
+    case ELLIPSE:
+    case AIRFOIL4: {
+      double px, py, bx, by;
+      to_body2(g, x, y, px, py);
+      if (g.kind == ELLIPSE) ellipse_closest(g.radii[0], g.radii[1], px, py, dist, bx, by);
+      else airfoil_closest(g.t, g.c, px, py, solid, dist, bx, by);
+      n[0] = g.rot[0] * bx + g.rot[1] * by;
+      n[1] = g.rot[3] * bx + g.rot[4] * by;
+      break;
+    }
+  }
+  psi = solid ? dist : -dist;
+  return true;
+}
+
+// Eq. delta_n with the ghost's own widths.
+__device__ inline double delta_n(const Geom& g, const double n[3]) {
+  double s = 0.0;
+  for (int a = 0; a < g.dim; ++a) {
+    double q = n[a] / g.h[a];
+    s += q * q;
+  }
+  return 1.0 / sqrt(s);
+}
+
+// status word: keep the first error
+__device__ inline void set_status(int* status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+}  // namespace ebr

@@ -1,0 +1,106 @@
+// Kernel declarations shared by the host-side orchestration (api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ebr_device.cuh"
+
+namespace ebr {
+
+// flat-row -> geometry by binary search over offsets [B + 1]
+__device__ inline int find_seg(const int* off, int B, int x) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---- classify.cu
+void launch_rows(const Geom* G, const int* row_off, int B, int total_rows, int2* runs,
+                 int8_t* tags, int* status, int* stats, cudaStream_t s);
+void launch_iface(const Geom* G, const int* row_off, int B, int total_rows, const int2* runs,
+                  int* row_cnt, const int* row_ptr, int* iface_cell, int* iface_geo,
+                  int8_t* iface_solid, int write, int iface_cap, int* status, cudaStream_t s);
+void launch_place(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
+                  const int8_t* iface_solid, int placement, int8_t* tags, double* iface_psi,
+                  double* iface_n, int* status, cudaStream_t s);
+void launch_reclassify(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
+                       int8_t* tags, int pass, cudaStream_t s);
+void launch_ghost_flags(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
+                        const int8_t* tags, int* flags, cudaStream_t s);
+void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
+                        const int8_t* tags, const double* iface_psi, const double* iface_n,
+                        const int* gpos, int placement, int ng_cap, int* gs_cell, int* gs_geo,
+                        double* gs_psi, double* gs_n, uint32_t* gs_meta, int* rmax,
+                        int* status, cudaStream_t s);
+
+// ---- scan.cu : exclusive scan of n int32 values into out[0..n]; out[n] = total
+size_t scan_temp_bytes(int n);
+void launch_scan(const int* in, int* out, int n, void* temp, cudaStream_t s);
+
+// ---- levels.cu
+void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, const int* pos_of,
+                    int* pos_of_cell, cudaStream_t s);
+void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, uint32_t* gs_meta,
+                 const double* gs_n, const int8_t* tags, const int* pos_of_cell, int* dep,
+                 int* status, cudaStream_t s);
+void launch_levels(const Geom* G, int B, const int* dep, int ng_total, int* level, int* order_pos,
+                   int* lev_ptr, int* n_levels, int* status, cudaStream_t s);
+void launch_reorder(int ng, const int* order_pos, const int* gs_cell, const int* gs_geo,
+                    const double* gs_psi, const double* gs_n, const uint32_t* gs_meta,
+                    const int* dep, const int* level, int* g_cell, int* g_geo, double* g_psi,
+                    double* g_n, uint32_t* g_meta, int* g_dep, int* g_level, cudaStream_t s);
+void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, const double* g_psi,
+                   const double* g_n, const uint32_t* g_meta, const int8_t* tags, double* wtab,
+                   double* ftab, cudaStream_t s);
+void launch_gsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
+                 const int8_t* tags, const int* pos_of_cell, int rmax, const int* ptr,
+                 int* cnt_or_src, int write, cudaStream_t s);
+void launch_fsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
+                 const int8_t* tags, const int* pos_of_cell, int rmax, const int* owner_ptr,
+                 int* owner_flag, int* ft_cell, int* ft_geo, int* ft_cnt, const int* ft_ptr,
+                 int* ft_src, int stage, cudaStream_t s);
+
+// ---- fill.cu
+void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
+                       const void* const* bc, long long cell_off, int p0, int p1, const int* g_cell,
+                       const uint32_t* g_meta, const double* wtab, int ng_total, int nx, int ny,
+                       cudaStream_t s);
+size_t fill_chain_smem(int dtype, int dim, int F, int n_ghost);
+void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
+                       const void* const* bc, const Geom* G, const int* geo_list, int n_list,
+                       const int* g_cell, const uint32_t* g_meta, const int* g_dep,
+                       const int* lev_ptr, const double* wtab, int ng_total, size_t smem,
+                       int* status, cudaStream_t s);
+
+// ---- forces.cu
+void launch_forces(int dtype, int dim, const void* const* vel, const void* p, double mu,
+                   const double* dirs, const Geom* G, int n_chunks, const int4* chunks,
+                   const int* g_cell, const int* g_geo, const double* g_n, const uint32_t* g_meta,
+                   const double* ftab, int ng_total, double* partial, int B, double* out,
+                   const int* chunk_ptr, cudaStream_t s);
+
+// ---- adjoint.cu
+void launch_adj_seed(int dim, int F, const int* role, double mu, const double* dirs,
+                     const double* seed, int ng, const int* g_geo, const double* g_n,
+                     const double* ftab, double* sv, cudaStream_t s);
+void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int p1,
+                      const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
+                      const double* wtab, const double* sv, int ng_total, void* lam, cudaStream_t s);
+size_t adj_chain_smem(int dtype, int F, int n_ghost, int n_src);
+void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom* G,
+                      const int* geo_list, int n_list, const int* lev_ptr, const int* gsrc_ptr,
+                      const int* gsrc, const uint32_t* g_meta, const double* wtab, const double* sv,
+                      int ng_total, void* lam, size_t smem, cudaStream_t s);
+void launch_adj_fluid(int dtype, int dim, int F, const int* bc_kind, int nft, const int* ft_cell,
+                      const int* ft_geo, const int* ft_ptr, const int* ft_src, const Geom* G,
+                      const uint32_t* g_meta, const double* wtab, const double* sv, int ng_total,
+                      const void* lam, void* const* grad, int accumulate, cudaStream_t s);
+void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
+                   const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,
+                   void* const* grad, int accumulate, cudaStream_t s);
+
+}  // namespace ebr

@@ -1,0 +1,180 @@
+// Level-by-level ghost fill (Sec. 3.2; closed forms of Secs. 4-5 through the
+// per-ghost weight table).
+//
+// Two schedules:
+//  * k_fill_level: one grid-wide launch per level of one geometry.
+//  * k_fill_chain: one CTA per geometry.  Everything that does not depend on
+//    another ghost -- the boundary term and the fluid members of every ghost,
+//    for every field -- is gathered first, in parallel, into shared memory;
+//    the dependency chain then runs level by level on shared memory only,
+//    separated by block barriers.  Long chains (an airfoil has ~60 levels)
+//    cost a few hundred cycles per level instead of a kernel launch each.
+// FP32 fields are combined in float with the weights rounded to float.
+#include "ebr_kernels.cuh"
+
+namespace ebr {
+
+struct FieldSet {
+  void* f[8];
+  const void* bc[8];
+  int kind[8];
+};
+
+template <typename T>
+__device__ inline T wload(const double* wtab, int ng, int bc, int slot, int p) {
+  return (T)wtab[(size_t)(bc * 8 + slot) * ng + p];
+}
+
+__device__ inline int member_cell(int dim, int cell, int nx, int ny, uint32_t m, int k) {
+  int o[3];
+  stencil_off(dim, k, o);
+  int off = o[0] * meta_r(m, 0) * meta_e(m, 0) + nx * (o[1] * meta_r(m, 1) * meta_e(m, 1));
+  if (dim == 3) off += nx * ny * (o[2] * meta_r(m, 2) * meta_e(m, 2));
+  return cell + off;
+}
+
+template <typename T>
+__global__ void k_fill_level(FieldSet P, int F, int dim, long long cell_off, int p0, int p1,
+                             const int* __restrict__ g_cell, const uint32_t* __restrict__ g_meta,
+                             const double* __restrict__ wtab, int ng, int nx, int ny) {
+  int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= p1) return;
+  const int K = stencil_k(dim);
+  int cell = g_cell[p];
+  uint32_t m = g_meta[p];
+  uint32_t act = meta_active(m);
+  for (int f = 0; f < F; ++f) {
+    T* fld = static_cast<T*>(P.f[f]) + cell_off;
+    const T* bc = static_cast<const T*>(P.bc[f]);
+    int kind = P.kind[f];
+    T acc = wload<T>(wtab, ng, kind, 7, p) * bc[p];
+    for (int k = 0; k < K; ++k) {
+      if (!(act >> k & 1u)) continue;
+      acc += wload<T>(wtab, ng, kind, k, p) * fld[member_cell(dim, cell, nx, ny, m, k)];
+    }
+    fld[cell] = acc;
+  }
+}
+
+void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
+                       const void* const* bc, long long cell_off, int p0, int p1, const int* g_cell,
+                       const uint32_t* g_meta, const double* wtab, int ng_total, int nx, int ny,
+                       cudaStream_t s) {
+  if (p1 <= p0) return;
+  FieldSet P;
+  for (int f = 0; f < 8; ++f) {
+    P.f[f] = f < F ? fields[f] : nullptr;
+    P.bc[f] = f < F ? bc[f] : nullptr;
+    P.kind[f] = f < F ? bc_kind[f] : 0;
+  }
+  int n = p1 - p0;
+  int T = n < 128 ? 64 : 128;
+  if (dtype == 0)
+    k_fill_level<float><<<(n + T - 1) / T, T, 0, s>>>(P, F, dim, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny);
+  else
+    k_fill_level<double><<<(n + T - 1) / T, T, 0, s>>>(P, F, dim, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny);
+}
+
+constexpr int CH_T = 512;
+
+size_t fill_chain_smem(int dtype, int dim, int F, int n) {
+  size_t sz = dtype == 0 ? 4 : 8;
+  int K = stencil_k(dim);
+  // vals[F][n], weights of dependency members for both kinds [2][K][n], positions [K][n]
+  return (size_t)n * (F * sz + 2 * K * sz + K * sizeof(int)) + 64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Geom* __restrict__ G,
+                                                     const int* __restrict__ geo_list,
+                                                     const int* __restrict__ g_cell,
+                                                     const uint32_t* __restrict__ g_meta,
+                                                     const int* __restrict__ g_dep,
+                                                     const int* __restrict__ lev_ptr,
+                                                     const double* __restrict__ wtab, int ng) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Geom& g = G[geo_list[blockIdx.x]];
+  const int n = g.n_ghost, g0 = g.ghost_off, dim = g.dim;
+  const int K = stencil_k(dim);
+  const int nx = g.n[0], ny = g.n[1];
+  T* vals = reinterpret_cast<T*>(smem);                 // [F][n]
+  T* wdep = vals + (size_t)F * n;                       // [2][K][n]
+  int* dpos = reinterpret_cast<int*>(wdep + (size_t)2 * K * n);  // [K][n]
+  // phase 1: boundary term + fluid members; dependency weights and positions
+  for (int s = threadIdx.x; s < n; s += CH_T) {
+    int p = g0 + s;
+    int cell = g_cell[p];
+    uint32_t m = g_meta[p];
+    uint32_t act = meta_active(m), dm = meta_depmask(m);
+    for (int f = 0; f < F; ++f) {
+      const T* fld = static_cast<const T*>(P.f[f]) + g.cell_off;
+      const T* bc = static_cast<const T*>(P.bc[f]);
+      int kind = P.kind[f];
+      T acc = wload<T>(wtab, ng, kind, 7, p) * bc[p];
+      for (int k = 0; k < K; ++k) {
+        if (!(act >> k & 1u) || (dm >> k & 1u)) continue;
+        acc += wload<T>(wtab, ng, kind, k, p) * fld[member_cell(dim, cell, nx, ny, m, k)];
+      }
+      vals[(size_t)f * n + s] = acc;
+    }
+    for (int k = 0; k < K; ++k) {
+      bool d = dm >> k & 1u;
+      dpos[(size_t)k * n + s] = d ? g_dep[(size_t)k * ng + p] - g0 : -1;
+      wdep[(size_t)k * n + s] = d ? wload<T>(wtab, ng, 0, k, p) : T(0);
+      wdep[(size_t)(K + k) * n + s] = d ? wload<T>(wtab, ng, 1, k, p) : T(0);
+    }
+  }
+  __syncthreads();
+  // phase 2: the dependency chain, level by level
+  const int* lp = lev_ptr + g.lev_off;
+  for (int lv = 1; lv <= g.n_levels; ++lv) {
+    int a = lp[lv - 1] - g0, b = lp[lv] - g0;
+    for (int s = a + threadIdx.x; s < b; s += CH_T) {
+      int cell = g_cell[g0 + s];
+      for (int f = 0; f < F; ++f) {
+        int kind = P.kind[f];
+        T v = vals[(size_t)f * n + s];
+        for (int k = 0; k < K; ++k) {
+          int d = dpos[(size_t)k * n + s];
+          if (d >= 0) v += wdep[(size_t)(kind * K + k) * n + s] * vals[(size_t)f * n + d];
+        }
+        vals[(size_t)f * n + s] = v;
+        static_cast<T*>(P.f[f])[g.cell_off + cell] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
+                       const void* const* bc, const Geom* G, const int* geo_list, int n_list,
+                       const int* g_cell, const uint32_t* g_meta, const int* g_dep,
+                       const int* lev_ptr, const double* wtab, int ng_total, size_t smem,
+                       int* status, cudaStream_t s) {
+  (void)dim;
+  (void)status;
+  if (n_list <= 0) return;
+  FieldSet P;
+  for (int f = 0; f < 8; ++f) {
+    P.f[f] = f < F ? fields[f] : nullptr;
+    P.bc[f] = f < F ? bc[f] : nullptr;
+    P.kind[f] = f < F ? bc_kind[f] : 0;
+  }
+  if (dtype == 0) {
+    static size_t set_float = 0;
+    if (smem > set_float) {
+      cudaFuncSetAttribute(k_fill_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set_float = smem;
+    }
+    k_fill_chain<float><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total);
+  } else {
+    static size_t set_double = 0;
+    if (smem > set_double) {
+      cudaFuncSetAttribute(k_fill_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set_double = smem;
+    }
+    k_fill_chain<double><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total);
+  }
+}
+
+}  // namespace ebr

@@ -1,0 +1,119 @@
+// Boundary quantities and forces (Sec. 6).
+//
+// Per ghost: p_s from the Dirichlet relation solved for phi_s, grad u at S from
+// Eq. derivative_bilinear / Eqs. derivative_trilinear_x/y/z (both through the
+// ftab coefficients), traction f = -p_s n + mu (grad u + grad u^T) n, weighted
+// by the ghost's surface element w_G.  Ghosts are cut into chunks of at most
+// 256 that never straddle geometries; each CTA reduces its chunk with a fixed
+// tree, and a second kernel adds the chunk partials of each geometry in order,
+// so the sums are bitwise reproducible.
+#include "ebr_kernels.cuh"
+
+namespace ebr {
+
+constexpr int FC_T = 256;
+
+struct VelSet {
+  const void* u[3];
+  const void* p;
+  double dirs[6];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(FC_T) k_forces_chunk(VelSet V, double mu, const Geom* __restrict__ G,
+                                                       const int4* __restrict__ chunks,
+                                                       const int* __restrict__ g_cell,
+                                                       const int* __restrict__ g_geo,
+                                                       const double* __restrict__ g_n,
+                                                       const uint32_t* __restrict__ g_meta,
+                                                       const double* __restrict__ ftab, int ng,
+                                                       double* __restrict__ partial) {
+  __shared__ double red[FC_T][8];
+  int4 ch = chunks[blockIdx.x];        // (geometry, p0, p1, -)
+  const Geom& g = G[ch.x];
+  const int d = g.dim, K = stencil_k(d), nx = g.n[0], ny = g.n[1];
+  int p = ch.y + threadIdx.x;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (p < ch.z) {
+    int cell = g_cell[p];
+    uint32_t m = g_meta[p];
+    int slots[8];
+    slots[0] = cell;
+    for (int k = 0; k < K; ++k) {
+      int o[3];
+      stencil_off(d, k, o);
+      int off = o[0] * meta_r(m, 0) * meta_e(m, 0) + nx * (o[1] * meta_r(m, 1) * meta_e(m, 1));
+      if (d == 3) off += nx * ny * (o[2] * meta_r(m, 2) * meta_e(m, 2));
+      slots[k + 1] = cell + off;
+    }
+    double n[3] = {g_n[p], g_n[ng + p], g_n[2 * (size_t)ng + p]};
+    double wG = ftab[p];
+    const T* pp = static_cast<const T*>(V.p) + g.cell_off;
+    double ps = 0.0;
+    for (int s = 0; s <= K; ++s) ps += ftab[(size_t)(1 + s) * ng + p] * (double)pp[slots[s]];
+    double Gm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // Gm[i][a] = d u_i / d x_a
+    for (int i = 0; i < d; ++i) {
+      if (!V.u[i]) continue;
+      const T* ui = static_cast<const T*>(V.u[i]) + g.cell_off;
+      for (int s = 0; s <= K; ++s) {
+        double v = (double)ui[slots[s]];
+        for (int a = 0; a < d; ++a) Gm[i][a] += ftab[(size_t)(9 + 8 * a + s) * ng + p] * v;
+      }
+    }
+    double fp[3], fv[3];
+    for (int i = 0; i < d; ++i) {
+      fp[i] = -ps * n[i] * wG;
+      double t = 0.0;
+      for (int a = 0; a < d; ++a) t += (Gm[i][a] + Gm[a][i]) * n[a];
+      fv[i] = mu * t * wG;
+    }
+    double dr = 0.0, li = 0.0;
+    for (int i = 0; i < d; ++i) {
+      acc[i] = fp[i];
+      acc[d + i] = fv[i];
+      dr += (fp[i] + fv[i]) * V.dirs[i];
+      li += (fp[i] + fv[i]) * V.dirs[d + i];
+    }
+    acc[2 * d] = dr;
+    acc[2 * d + 1] = li;
+  }
+  for (int q = 0; q < 8; ++q) red[threadIdx.x][q] = acc[q];
+  __syncthreads();
+  for (int w = FC_T / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 8; ++q) red[threadIdx.x][q] += red[threadIdx.x + w][q];
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) partial[(size_t)blockIdx.x * 8 + threadIdx.x] = red[0][threadIdx.x];
+}
+
+__global__ void k_forces_final(int B, const Geom* __restrict__ G, const int* __restrict__ chunk_ptr,
+                               const double* __restrict__ partial, double* __restrict__ out) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int d = G[b].dim, W = 2 * d + 2;
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int c = chunk_ptr[b]; c < chunk_ptr[b + 1]; ++c)
+    for (int q = 0; q < W; ++q) s[q] += partial[(size_t)c * 8 + q];
+  for (int q = 0; q < W; ++q) out[(size_t)b * W + q] = s[q];
+}
+
+void launch_forces(int dtype, int dim, const void* const* vel, const void* p, double mu,
+                   const double* dirs, const Geom* G, int n_chunks, const int4* chunks,
+                   const int* g_cell, const int* g_geo, const double* g_n, const uint32_t* g_meta,
+                   const double* ftab, int ng_total, double* partial, int B, double* out,
+                   const int* chunk_ptr, cudaStream_t s) {
+  VelSet V;
+  for (int i = 0; i < 3; ++i) V.u[i] = i < dim ? vel[i] : nullptr;
+  V.p = p;
+  for (int q = 0; q < 6; ++q) V.dirs[q] = q < 2 * dim ? dirs[q] : 0.0;
+  if (n_chunks > 0) {
+    if (dtype == 0)
+      k_forces_chunk<float><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+    else
+      k_forces_chunk<double><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+  }
+  k_forces_final<<<(B + 127) / 128, 128, 0, s>>>(B, G, chunk_ptr, partial, out);
+}
+
+}  // namespace ebr

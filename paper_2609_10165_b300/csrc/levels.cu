@@ -1,0 +1,477 @@
+// Dependency DAG, topological levels and canonical order (Sec. 3.2); per-ghost
+// coefficient tables (Secs. 4-6); transposed incidence lists for the adjoint.
+#include "ebr_kernels.cuh"
+
+namespace ebr {
+
+__device__ inline void cell_ijk3(const Geom& g, int cell, int ijk[3]) {
+  ijk[0] = cell % g.n[0];
+  int r = cell / g.n[0];
+  ijk[1] = r % g.n[1];
+  ijk[2] = r / g.n[1];
+}
+
+__device__ inline int cell_lin(const Geom& g, const int ijk[3]) {
+  return ijk[0] + g.n[0] * (ijk[1] + g.n[1] * ijk[2]);
+}
+
+__device__ inline bool in_grid(const Geom& g, const int ijk[3]) {
+  for (int a = 0; a < g.dim; ++a)
+    if (ijk[a] < 0 || ijk[a] >= g.n[a]) return false;
+  return true;
+}
+
+// member k of a ghost at ijk with meta m
+__device__ inline void member_ijk(const Geom& g, const int ijk[3], uint32_t m, int k, int out[3]) {
+  int o[3];
+  stencil_off(g.dim, k, o);
+  for (int a = 0; a < 3; ++a) out[a] = ijk[a] + (a < g.dim ? o[a] * meta_r(m, a) * meta_e(m, a) : 0);
+}
+
+__global__ void k_poscell(const Geom* __restrict__ G, int ng, const int* __restrict__ cell,
+                          const int* __restrict__ geo, const int* __restrict__ pos_of,
+                          int* __restrict__ pos_of_cell) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ng) return;
+  pos_of_cell[G[geo[s]].cell_off + cell[s]] = pos_of ? pos_of[s] : s;
+}
+
+void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, const int* pos_of,
+                    int* pos_of_cell, cudaStream_t s) {
+  if (ng <= 0) return;
+  k_poscell<<<(ng + 255) / 256, 256, 0, s>>>(G, ng, cell, geo, pos_of, pos_of_cell);
+}
+
+// Stencil members: validate (inside the grid, not tag 1), active mask
+// (n_i != 0 along every offset axis), dependencies on ghost members.
+__global__ void k_deps(const Geom* __restrict__ G, int ng, const int* __restrict__ gs_cell,
+                       const int* __restrict__ gs_geo, uint32_t* __restrict__ gs_meta,
+                       const double* __restrict__ gs_n, const int8_t* __restrict__ tags,
+                       const int* __restrict__ pos_of_cell, int* __restrict__ dep, int* status) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ng) return;
+  const Geom& g = G[gs_geo[s]];
+  int ijk[3];
+  cell_ijk3(g, gs_cell[s], ijk);
+  uint32_t m = gs_meta[s] & ~((127u << 15) | (127u << 23));
+  double nv[3] = {gs_n[s], gs_n[ng + s], gs_n[2 * (size_t)ng + s]};
+  const int K = stencil_k(g.dim);
+  uint32_t active = 0, depm = 0;
+  for (int k = 0; k < MAXK; ++k) {
+    int d = -1;
+    if (k < K) {
+      int mijk[3], o[3];
+      member_ijk(g, ijk, m, k, mijk);
+      stencil_off(g.dim, k, o);
+      if (!in_grid(g, mijk)) {
+        set_status(status, S_ESTENCIL_OOB);
+      } else {
+        bool act = true;
+        for (int a = 0; a < g.dim; ++a)
+          if (o[a] && nv[a] == 0.0) act = false;
+        long long mc = g.cell_off + cell_lin(g, mijk);
+        int8_t t = tags[mc];
+        if (t == 1) set_status(status, S_ESTENCIL_SOLID);
+        if (act) active |= 1u << k;
+        if (act && (t == 2 || t == -2)) {
+          d = pos_of_cell[mc];
+          depm |= 1u << k;
+        }
+      }
+    }
+    dep[(size_t)k * ng + s] = d;
+  }
+  gs_meta[s] = m | (active << 15) | (depm << 23);
+}
+
+void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, uint32_t* gs_meta,
+                 const double* gs_n, const int8_t* tags, const int* pos_of_cell, int* dep,
+                 int* status, cudaStream_t s) {
+  if (ng <= 0) return;
+  k_deps<<<(ng + 127) / 128, 128, 0, s>>>(G, ng, gs_cell, gs_geo, gs_meta, gs_n, tags,
+                                          pos_of_cell, dep, status);
+}
+
+// One CTA per geometry: integer frontier sweep.  In sweep L a ghost whose
+// dependencies all carry levels in [1, L-1] receives level L; a level written in
+// the same sweep reads as "not ready", so the result does not depend on the
+// thread schedule.  Then a stable counting sort by level gives the canonical
+// position (level, index) of every ghost.
+constexpr int LV_T = 1024;
+
+__global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int B,
+                                                 const int* __restrict__ dep, int ng_total,
+                                                 int* __restrict__ level, int* __restrict__ order_pos,
+                                                 int* __restrict__ lev_ptr, int* __restrict__ n_levels,
+                                                 int* status) {
+  __shared__ int sh_cnt;
+  __shared__ int sh_warp[32];
+  for (int b = blockIdx.x; b < B; b += gridDim.x) {
+    const Geom& g = G[b];
+    const int g0 = g.ghost_off, n = g.n_ghost;
+    const int K = stencil_k(g.dim);
+    int* lp = lev_ptr + g.lev_off;
+    for (int s = threadIdx.x; s < n; s += LV_T) level[g0 + s] = 0;
+    if (threadIdx.x == 0) lp[0] = g0;
+    __syncthreads();
+    int remaining = n, L = 0;
+    while (remaining > 0) {
+      ++L;
+      if (threadIdx.x == 0) sh_cnt = 0;
+      __syncthreads();
+      int mine = 0;
+      for (int s = threadIdx.x; s < n; s += LV_T) {
+        int gi = g0 + s;
+        if (level[gi] != 0) continue;
+        bool ok = true;
+        for (int k = 0; k < K && ok; ++k) {
+          int d = dep[(size_t)k * ng_total + gi];
+          if (d >= 0) {
+            int lv = ((volatile int*)level)[d];
+            if (lv == 0 || lv >= L) ok = false;
+          }
+        }
+        if (ok) { level[gi] = L; ++mine; }
+      }
+      if (mine) atomicAdd(&sh_cnt, mine);
+      __syncthreads();
+      int cnt = sh_cnt;
+      __syncthreads();
+      if (cnt == 0) {
+        if (threadIdx.x == 0) set_status(status, S_ECYCLE);
+        break;
+      }
+      remaining -= cnt;
+      if (threadIdx.x == 0) lp[L] = lp[L - 1] + cnt;
+      __syncthreads();
+    }
+    int nl = remaining > 0 ? 0 : L;
+    if (threadIdx.x == 0) n_levels[b] = nl;
+    __syncthreads();
+    if (remaining > 0) continue;
+    // stable counting sort: rank by index order within each level
+    for (int lv = 1; lv <= nl; ++lv) {
+      int carry = lp[lv - 1];
+      for (int base = 0; base < n; base += LV_T) {
+        int s = base + threadIdx.x;
+        int f = (s < n && level[g0 + s] == lv) ? 1 : 0;
+        // block exclusive scan of f
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        unsigned bal = __ballot_sync(0xffffffffu, f);
+        int inwarp = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) sh_warp[w] = __popc(bal);
+        __syncthreads();
+        if (w == 0) {
+          int v = sh_warp[lane];
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+          }
+          sh_warp[lane] = v;
+        }
+        __syncthreads();
+        int before = (w > 0 ? sh_warp[w - 1] : 0);
+        if (f) order_pos[g0 + s] = carry + before + inwarp;
+        int tot = sh_warp[31];
+        __syncthreads();
+        carry += tot;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_levels(const Geom* G, int B, const int* dep, int ng_total, int* level, int* order_pos,
+                   int* lev_ptr, int* n_levels, int* status, cudaStream_t s) {
+  if (B <= 0) return;
+  k_levels<<<B, LV_T, 0, s>>>(G, B, dep, ng_total, level, order_pos, lev_ptr, n_levels, status);
+}
+
+__global__ void k_reorder(int ng, const int* __restrict__ order_pos, const int* __restrict__ gs_cell,
+                          const int* __restrict__ gs_geo, const double* __restrict__ gs_psi,
+                          const double* __restrict__ gs_n, const uint32_t* __restrict__ gs_meta,
+                          const int* __restrict__ dep, const int* __restrict__ level,
+                          int* __restrict__ g_cell, int* __restrict__ g_geo, double* __restrict__ g_psi,
+                          double* __restrict__ g_n, uint32_t* __restrict__ g_meta,
+                          int* __restrict__ g_dep, int* __restrict__ g_level) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ng) return;
+  int p = order_pos[s];
+  g_cell[p] = gs_cell[s];
+  g_geo[p] = gs_geo[s];
+  g_psi[p] = gs_psi[s];
+  for (int a = 0; a < 3; ++a) g_n[(size_t)a * ng + p] = gs_n[(size_t)a * ng + s];
+  g_meta[p] = gs_meta[s];
+  g_level[p] = level[s];
+  for (int k = 0; k < MAXK; ++k) {
+    int d = dep[(size_t)k * ng + s];
+    g_dep[(size_t)k * ng + p] = d >= 0 ? order_pos[d] : -1;
+  }
+}
+
+void launch_reorder(int ng, const int* order_pos, const int* gs_cell, const int* gs_geo,
+                    const double* gs_psi, const double* gs_n, const uint32_t* gs_meta,
+                    const int* dep, const int* level, int* g_cell, int* g_geo, double* g_psi,
+                    double* g_n, uint32_t* g_meta, int* g_dep, int* g_level, cudaStream_t s) {
+  if (ng <= 0) return;
+  k_reorder<<<(ng + 255) / 256, 256, 0, s>>>(ng, order_pos, gs_cell, gs_geo, gs_psi, gs_n, gs_meta,
+                                             dep, level, g_cell, g_geo, g_psi, g_n, g_meta, g_dep,
+                                             g_level);
+}
+
+// ---------------------------------------------------------------------------
+// Per-ghost coefficient tables, evaluated once in double (the B300 FP64 pipe
+// is narrow, so each closed form is evaluated once per geometry by all SMs):
+//   wtab[(bc * 8 + slot) * ng + p]: weights on P_1..P_K (slots 0..K-1) and on
+//     the boundary datum (slot 7), Eqs. phi_G_Dir_2d/_3d (bc 0) and
+//     phi_G_Neu_2d/_3d (bc 1), local coordinates with the origin at G.
+//   ftab[q * ng + p]: q = 0 surface weight w_G; q = 1 + slot: coefficient of the
+//     slot value in phi_s (the Dirichlet relation solved for phi_s); q = 9 +
+//     8 a + slot: coefficient in d phi / d x_a at S (Eq. derivative_bilinear,
+//     Eqs. derivative_trilinear_x/y/z).  Slot 0 is G itself, slot k the member P_k.
+// ---------------------------------------------------------------------------
+__device__ void dirichlet_w(int dim, const double X2[3], const double Xs[3], double w[8]) {
+  double om[3];
+  for (int a = 0; a < dim; ++a) om[a] = (0.0 - Xs[a]) / (X2[a] - Xs[a]);
+  for (int q = 0; q < 8; ++q) w[q] = 0.0;
+  if (dim == 2) {
+    w[0] = om[0]; w[1] = om[1]; w[2] = -om[0] * om[1];
+    w[7] = (1.0 - om[0]) * (1.0 - om[1]);
+  } else {
+    w[0] = om[0]; w[1] = om[1]; w[2] = om[2];
+    w[3] = -om[0] * om[1]; w[4] = -om[1] * om[2]; w[5] = -om[0] * om[2];
+    w[6] = om[0] * om[1] * om[2];
+    w[7] = (1.0 - om[0]) * (1.0 - om[1]) * (1.0 - om[2]);
+  }
+}
+
+__device__ void neumann_w(int dim, const double X2[3], const double Xs[3], const double n[3],
+                          double w[8]) {
+  for (int q = 0; q < 8; ++q) w[q] = 0.0;
+  if (dim == 2) {
+    double a1 = n[0] * (0.0 - Xs[1]), a2 = n[0] * (X2[1] - Xs[1]);
+    double b1 = n[1] * (0.0 - Xs[0]), b2 = n[1] * (X2[0] - Xs[0]);
+    double den = a2 + b2;
+    double w1 = (a2 + b1) / den, w2 = (a1 + b2) / den;
+    w[0] = w1; w[1] = w2; w[2] = 1.0 - w1 - w2;
+    w[7] = -(X2[0] - 0.0) * (X2[1] - 0.0) / den;
+    return;
+  }
+  const double xi[2] = {0.0, X2[0]}, yi[2] = {0.0, X2[1]}, zi[2] = {0.0, X2[2]};
+  auto A = [&](int i, int j) { return n[0] * (yi[i - 1] - Xs[1]) * (zi[j - 1] - Xs[2]); };
+  auto Bf = [&](int i, int j) { return n[1] * (xi[i - 1] - Xs[0]) * (zi[j - 1] - Xs[2]); };
+  auto C = [&](int i, int j) { return n[2] * (xi[i - 1] - Xs[0]) * (yi[j - 1] - Xs[1]); };
+  double den = A(2, 2) + Bf(2, 2) + C(2, 2);
+  w[0] = (A(2, 2) + Bf(1, 2) + C(1, 2)) / den;
+  w[1] = (A(1, 2) + Bf(2, 2) + C(2, 1)) / den;
+  w[2] = (A(2, 1) + Bf(2, 1) + C(2, 2)) / den;
+  w[3] = -(A(1, 2) + Bf(1, 2) + C(1, 1)) / den;
+  w[4] = -(A(1, 1) + Bf(2, 1) + C(2, 1)) / den;
+  w[5] = -(A(2, 1) + Bf(1, 1) + C(1, 2)) / den;
+  w[6] = (A(1, 1) + Bf(1, 1) + C(1, 1)) / den;
+  w[7] = -(X2[0] - 0.0) * (X2[1] - 0.0) * (X2[2] - 0.0) / den;
+}
+
+__global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restrict__ g_cell,
+                         const int* __restrict__ g_geo, const double* __restrict__ g_psi,
+                         const double* __restrict__ g_n, const uint32_t* __restrict__ g_meta,
+                         const int8_t* __restrict__ tags, double* __restrict__ wtab,
+                         double* __restrict__ ftab) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ng) return;
+  const Geom& g = G[g_geo[p]];
+  const int d = g.dim;
+  uint32_t m = g_meta[p];
+  double psi = g_psi[p];
+  double n[3] = {g_n[p], g_n[ng + p], g_n[2 * (size_t)ng + p]};
+  double X2[3] = {0, 0, 0}, Xs[3] = {0, 0, 0};
+  for (int a = 0; a < d; ++a) {
+    X2[a] = meta_r(m, a) * meta_e(m, a) * g.h[a];
+    Xs[a] = psi * n[a];
+  }
+  double wd[8], wn[8];
+  dirichlet_w(d, X2, Xs, wd);
+  neumann_w(d, X2, Xs, n, wn);
+  for (int q = 0; q < 8; ++q) {
+    wtab[(size_t)q * ng + p] = wd[q];
+    wtab[(size_t)(8 + q) * ng + p] = wn[q];
+  }
+  // surface weight: faces shared with tag-0 cells, |n_face . n| times face area
+  int ijk[3];
+  cell_ijk3(g, g_cell[p], ijk);
+  const int8_t* tg = tags + g.cell_off;
+  double wG = 0.0;
+  for (int a = 0; a < d; ++a) {
+    double area = 1.0;
+    for (int b = 0; b < d; ++b)
+      if (b != a) area *= g.h[b];
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      int nb[3] = {ijk[0], ijk[1], ijk[2]};
+      nb[a] += sgn;
+      if (nb[a] < 0 || nb[a] >= g.n[a]) continue;
+      if (tg[cell_lin(g, nb)] == 0) wG += area * fabs(n[a]);
+    }
+  }
+  double f[33];
+  for (int q = 0; q < 33; ++q) f[q] = 0.0;
+  f[0] = wG;
+  // phi_s = (phi_G - sum_k wd_k phi_k) / wd_s
+  f[1] = 1.0 / wd[7];
+  const int K = stencil_k(d);
+  for (int k = 0; k < K; ++k) f[2 + k] = -wd[k] / wd[7];
+  // gradient at S, local coordinates (x_1 = 0)
+  double fx0 = (X2[0] - Xs[0]) / X2[0], fx1 = Xs[0] / X2[0];
+  double fy0 = (X2[1] - Xs[1]) / X2[1], fy1 = Xs[1] / X2[1];
+  double* bx = f + 9;
+  double* by = f + 17;
+  double* bz = f + 25;
+  if (d == 2) {
+    double hx = X2[0], hy = X2[1];
+    bx[0] = -fy0 / hx; bx[1] = fy0 / hx; bx[2] = -fy1 / hx; bx[3] = fy1 / hx;
+    by[0] = -fx0 / hy; by[1] = -fx1 / hy; by[2] = fx0 / hy; by[3] = fx1 / hy;
+  } else {
+    double fz0 = (X2[2] - Xs[2]) / X2[2], fz1 = Xs[2] / X2[2];
+    double hx = X2[0], hy = X2[1], hz = X2[2];
+    // slots: 0 G, 1 P1, 2 P2, 3 P3, 4 P4, 5 P5, 6 P6, 7 P7
+    bx[0] = -fy0 * fz0 / hx; bx[1] = fy0 * fz0 / hx; bx[2] = -fy1 * fz0 / hx; bx[4] = fy1 * fz0 / hx;
+    bx[3] = -fy0 * fz1 / hx; bx[6] = fy0 * fz1 / hx; bx[5] = -fy1 * fz1 / hx; bx[7] = fy1 * fz1 / hx;
+    by[0] = -fx0 * fz0 / hy; by[2] = fx0 * fz0 / hy; by[1] = -fx1 * fz0 / hy; by[4] = fx1 * fz0 / hy;
+    by[3] = -fx0 * fz1 / hy; by[5] = fx0 * fz1 / hy; by[6] = -fx1 * fz1 / hy; by[7] = fx1 * fz1 / hy;
+    bz[0] = -fx0 * fy0 / hz; bz[3] = fx0 * fy0 / hz; bz[1] = -fx1 * fy0 / hz; bz[6] = fx1 * fy0 / hz;
+    bz[2] = -fx0 * fy1 / hz; bz[5] = fx0 * fy1 / hz; bz[4] = -fx1 * fy1 / hz; bz[7] = fx1 * fy1 / hz;
+  }
+  for (int q = 0; q < 33; ++q) ftab[(size_t)q * ng + p] = f[q];
+}
+
+void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, const double* g_psi,
+                   const double* g_n, const uint32_t* g_meta, const int8_t* tags, double* wtab,
+                   double* ftab, cudaStream_t s) {
+  if (ng <= 0) return;
+  k_tables<<<(ng + 127) / 128, 128, 0, s>>>(G, ng, g_cell, g_geo, g_psi, g_n, g_meta, tags, wtab, ftab);
+}
+
+// ---------------------------------------------------------------------------
+// transposed incidences: for a target cell T, the (ghost H, slot) pairs with
+// member_slot(H) = T, found by probing H = T - delta over the box |delta_a| <= R
+// in a fixed order.  Slot 0 (H = T itself) is listed first for ghost targets.
+// ---------------------------------------------------------------------------
+template <typename Visit>
+__device__ inline void probe_sources(const Geom& g, const int tijk[3], const int8_t* tg,
+                                     const int* pcell, const uint32_t* g_meta, int R, Visit visit) {
+  const int K = stencil_k(g.dim);
+  int Rz = g.dim == 3 ? R : 0;
+  for (int dz = -Rz; dz <= Rz; ++dz)
+    for (int dy = -R; dy <= R; ++dy)
+      for (int dx = -R; dx <= R; ++dx) {
+        if (dx == 0 && dy == 0 && dz == 0) continue;
+        int hijk[3] = {tijk[0] - dx, tijk[1] - dy, tijk[2] - dz};
+        if (!in_grid(g, hijk)) continue;
+        int hc = cell_lin(g, hijk);
+        int8_t t = tg[hc];
+        if (t != 2 && t != -2) continue;
+        int q = pcell[hc];
+        uint32_t m = g_meta[q];
+        int dd[3] = {dx, dy, dz};
+        for (int k = 0; k < K; ++k) {
+          int o[3];
+          stencil_off(g.dim, k, o);
+          bool hit = true;
+          for (int a = 0; a < g.dim; ++a)
+            if (o[a] * meta_r(m, a) * meta_e(m, a) != dd[a]) hit = false;
+          if (hit) { if (!visit(q, k + 1)) return; }
+        }
+      }
+}
+
+// ghost targets: write = 0 counts, write = 1 writes sources (self first)
+__global__ void k_gsrc(const Geom* __restrict__ G, int ng, const int* __restrict__ g_cell,
+                       const int* __restrict__ g_geo, const uint32_t* __restrict__ g_meta,
+                       const int8_t* __restrict__ tags, const int* __restrict__ pos_of_cell, int R,
+                       const int* __restrict__ ptr, int* __restrict__ out, int write) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ng) return;
+  const Geom& g = G[g_geo[p]];
+  int tijk[3];
+  cell_ijk3(g, g_cell[p], tijk);
+  const int8_t* tg = tags + g.cell_off;
+  const int* pc = pos_of_cell + g.cell_off;
+  if (!write) {
+    int cnt = 1;
+    probe_sources(g, tijk, tg, pc, g_meta, R, [&](int, int) { ++cnt; return true; });
+    out[p] = cnt;
+  } else {
+    int o = ptr[p];
+    out[o++] = (p << 3) | 0;
+    probe_sources(g, tijk, tg, pc, g_meta, R, [&](int q, int slot) { out[o++] = (q << 3) | slot; return true; });
+  }
+}
+
+void launch_gsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
+                 const int8_t* tags, const int* pos_of_cell, int rmax, const int* ptr,
+                 int* cnt_or_src, int write, cudaStream_t s) {
+  if (ng <= 0) return;
+  k_gsrc<<<(ng + 127) / 128, 128, 0, s>>>(G, ng, g_cell, g_geo, g_meta, tags, pos_of_cell, rmax,
+                                          ptr, cnt_or_src, write);
+}
+
+// fluid targets.  Incidence i = p * 8 + k (ghost p, member k).  stage 0: owner
+// flag (the incidence is the first source of its fluid member in probe order);
+// stage 1: owners record the target and count its sources; stage 2: owners
+// write the sources.
+__global__ void k_fsrc(const Geom* __restrict__ G, int ng, const int* __restrict__ g_cell,
+                       const int* __restrict__ g_geo, const uint32_t* __restrict__ g_meta,
+                       const int8_t* __restrict__ tags, const int* __restrict__ pos_of_cell, int R,
+                       const int* __restrict__ owner_ptr, int* __restrict__ owner_flag,
+                       int* __restrict__ ft_cell, int* __restrict__ ft_geo, int* __restrict__ ft_cnt,
+                       const int* __restrict__ ft_ptr, int* __restrict__ ft_src, int stage) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ng * 8) return;
+  int p = i >> 3, k = i & 7;
+  const Geom& g = G[g_geo[p]];
+  const int K = stencil_k(g.dim);
+  bool owner = false;
+  int tijk[3] = {0, 0, 0};
+  const int8_t* tg = tags + g.cell_off;
+  const int* pc = pos_of_cell + g.cell_off;
+  if (k < K) {
+    int gijk[3];
+    cell_ijk3(g, g_cell[p], gijk);
+    member_ijk(g, gijk, g_meta[p], k, tijk);
+    if (in_grid(g, tijk) && tg[cell_lin(g, tijk)] == 0) {
+      if (stage == 0) {
+        int fq = -1, fs = -1;
+        probe_sources(g, tijk, tg, pc, g_meta, R, [&](int q, int slot) { fq = q; fs = slot; return false; });
+        owner = (fq == p && fs == k + 1);
+      } else {
+        owner = owner_flag[i] != 0;
+      }
+    }
+  }
+  if (stage == 0) { owner_flag[i] = owner ? 1 : 0; return; }
+  if (!owner) return;
+  int t = owner_ptr[i];
+  if (stage == 1) {
+    ft_cell[t] = cell_lin(g, tijk);
+    ft_geo[t] = g_geo[p];
+    int cnt = 0;
+    probe_sources(g, tijk, tg, pc, g_meta, R, [&](int, int) { ++cnt; return true; });
+    ft_cnt[t] = cnt;
+  } else {
+    int o = ft_ptr[t];
+    probe_sources(g, tijk, tg, pc, g_meta, R, [&](int q, int slot) { ft_src[o++] = (q << 3) | slot; return true; });
+  }
+}
+
+void launch_fsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
+                 const int8_t* tags, const int* pos_of_cell, int rmax, const int* owner_ptr,
+                 int* owner_flag, int* ft_cell, int* ft_geo, int* ft_cnt, const int* ft_ptr,
+                 int* ft_src, int stage, cudaStream_t s) {
+  if (ng <= 0) return;
+  int n = ng * 8;
+  k_fsrc<<<(n + 127) / 128, 128, 0, s>>>(G, ng, g_cell, g_geo, g_meta, tags, pos_of_cell, rmax,
+                                         owner_ptr, owner_flag, ft_cell, ft_geo, ft_cnt, ft_ptr,
+                                         ft_src, stage);
+}
+
+}  // namespace ebr

@@ -1,0 +1,105 @@
+// Device-wide exclusive scan of int32 counts (stream compaction offsets).
+// Three launches: per-block scan, scan of the block totals, add-back.
+// out has n + 1 entries; out[n] is the total.
+#include "ebr_kernels.cuh"
+
+namespace ebr {
+
+constexpr int SCAN_T = 256;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_T * SCAN_ITEMS;
+
+__device__ inline int block_excl_scan(int v, int* sh_warp, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    int s = lane < nw ? sh_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) sh_warp[lane] = s;
+  }
+  __syncthreads();
+  int before = w > 0 ? sh_warp[w - 1] : 0;
+  total = sh_warp[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int* __restrict__ in, int* __restrict__ out,
+                                                       int n, int* __restrict__ tile_sum) {
+  __shared__ int sh[32];
+  long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS];
+  int local = 0;
+#pragma unroll
+  for (int q = 0; q < SCAN_ITEMS; ++q) {
+    long long i = base + q;
+    v[q] = i < n ? in[i] : 0;
+    local += v[q];
+  }
+  int total;
+  int ex = block_excl_scan(local, sh, total);
+#pragma unroll
+  for (int q = 0; q < SCAN_ITEMS; ++q) {
+    long long i = base + q;
+    if (i < n) out[i] = ex;
+    ex += v[q];
+  }
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ tile_sum, int ntiles,
+                                                      int* __restrict__ out, int n) {
+  __shared__ int sh[32];
+  int carry = 0;
+  for (int base = 0; base < ntiles; base += SCAN_T) {
+    int i = base + threadIdx.x;
+    int v = i < ntiles ? tile_sum[i] : 0;
+    int total;
+    int ex = block_excl_scan(v, sh, total);
+    if (i < ntiles) tile_sum[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_add(int* __restrict__ out, int n,
+                                                     const int* __restrict__ tile_sum) {
+  long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  int add = tile_sum[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < SCAN_ITEMS; ++q) {
+    long long i = base + q;
+    if (i < n) out[i] += add;
+  }
+}
+
+size_t scan_temp_bytes(int n) {
+  int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  return sizeof(int) * (size_t)(ntiles > 0 ? ntiles : 1);
+}
+
+void launch_scan(const int* in, int* out, int n, void* temp, cudaStream_t s) {
+  int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  int* ts = static_cast<int*>(temp);
+  if (n <= 0) {
+    k_scan_sums<<<1, SCAN_T, 0, s>>>(ts, 0, out, 0);
+    return;
+  }
+  k_scan_tiles<<<ntiles, SCAN_T, 0, s>>>(in, out, n, ts);
+  k_scan_sums<<<1, SCAN_T, 0, s>>>(ts, ntiles, out, n);
+  k_scan_add<<<ntiles, SCAN_T, 0, s>>>(out, n, ts);
+}
+
+}  // namespace ebr

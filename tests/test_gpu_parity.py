@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Tags, ghost lists, canonical order and levels must be
+bit-exact; FP64 values within 1e-12 of the magnitude of their terms; FP32
+within 1e-5 of the field maximum (see tests/parity.py)."""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2609_10165_b300 import inputs as I
+from tests.parity import GPURun, oracle_run, term_magnitude, compare_structure, U32
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_cases():
+    # ragged sizes spanning several row groups and tiles; every body kind
+    return [
+        {"grid": I.grid(2, [37, 29], [-1.0, -1.0], [1.0, 1.0]), "body": I.ellipse(0.03, -0.02, 0.6, 0.35, 0.7)},
+        {"grid": I.grid(2, [131, 67], [-1.0, -1.0], [3.0, 1.0]), "body": I.airfoil(0.0, 0.0, 0.12, 1.0, 5.0)},
+        {"grid": I.grid(2, [33, 33], [-1.0, -1.0], [1.0, 1.0]), "body": I.circle(0.0, 0.0, 0.55)},
+        {"grid": I.grid(3, [21, 18, 19], [-1.0, -1.0, -1.0], [1.0, 1.0, 1.0]), "body": I.sphere(0.02, -0.01, 0.03, 0.6)},
+        {"grid": I.grid(3, [17, 17, 17], [-1.0, -1.0, -1.0], [1.0, 1.0, 1.0]), "body": I.sphere(0.0, 0.0, 0.0, 0.55)},
+    ]
+
+
+def _with_fields(case, seed):
+    d = case["grid"]["dim"]
+    fs = [I.FourierField(d, 4, case["grid"]["lo"], case["grid"]["hi"], seed + f) for f in range(d + 1)]
+    out = dict(case)
+    out.update({"fields": fs, "bc": [I.DIRICHLET] * d + [I.NEUMANN],
+                "roles": {"p": d, "vel": list(range(d))}, "mu": 0.01})
+    return out
+
+
+def _check_values(run, geoms, placement, dtype):
+    arrays = run.field_arrays()
+    if dtype == torch.float32:
+        arrays = [a.astype(np.float32).astype(np.float64) for a in arrays]
+    bcs = run.bc_arrays()
+    if dtype == torch.float32:
+        bcs = [b.astype(np.float32).astype(np.float64) for b in bcs]
+    ft, _ = run.fill(arrays, bcs)
+    got = [t.double().cpu().numpy() for t in ft]
+    info = run.info
+    worst = 0.0
+    for b, g in enumerate(geoms):
+        o0, o1 = run.R.cell_offset[b], run.R.cell_offset[b + 1]
+        sel = info["geom"] == b
+        # oracle on the same inputs, with the GPU's boundary data (same order)
+        c = O.classify(g["grid"], g["body"], placement)
+        lev = O.build_levels(c)
+        loc = [a[o0:o1] for a in arrays]
+        bl = [bb[sel] for bb in bcs]
+        out = O.fill(c, lev, loc, g["bc"], bl)
+        T = term_magnitude(c, lev, loc, bl, g["bc"])
+        cells = c.idx[lev.order]
+        K = 3 if g["grid"]["dim"] == 2 else 7
+        for f in range(len(g["fields"])):
+            diff = np.abs(got[f][o0:o1][cells] - out[f][cells])
+            if dtype == torch.float64:
+                tol = 1e-12 * T[f]
+            else:
+                fmax = np.abs(loc[f]).max()
+                tol = np.full(diff.shape, 1e-5 * fmax)
+                if placement == "CGC":
+                    tol = np.maximum(tol, 8 * (K + 2) * U32 * T[f])
+            bad = diff > tol
+            assert not np.any(bad), (b, f, int(bad.sum()), float(diff.max()), float(tol[np.argmax(diff - tol)]))
+            worst = max(worst, float(np.max(diff / np.maximum(tol, 1e-300))))
+            # non-ghost cells untouched
+            mask = np.ones(o1 - o0, bool)
+            mask[cells] = False
+            assert np.array_equal(got[f][o0:o1][mask], loc[f][mask])
+    return worst
+
+
+@pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
+@pytest.mark.parametrize("mode", ["level", "persistent"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_small_cases_all_bodies(placement, mode, dtype):
+    for k, case in enumerate(_small_cases()):
+        g = _with_fields(case, 50 + 10 * k)
+        run = GPURun([g], placement, mode=mode, dtype=dtype)
+        compare_structure(run, [g], placement)
+        _check_values(run, [g], placement, dtype)
+
+
+def test_small_cases_batched_together():
+    # the five small geometries in one 2D/3D-mixed set is not allowed for
+    # forces, but classification / levels / fill are per geometry
+    cases = [_with_fields(c, 90 + 10 * k) for k, c in enumerate(_small_cases()) if c["grid"]["dim"] == 2]
+    for placement in ("HGC", "CGC_ES"):
+        run = GPURun(cases, placement, mode="persistent")
+        compare_structure(run, cases, placement)
+        _check_values(run, cases, placement, torch.float64)
+
+
+@pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
+def test_cylinder_128(placement):
+    w = I.cylinder(128, 1)
+    run = GPURun([w], placement, mode="level")
+    res = compare_structure(run, [w], placement)
+    c, lev = res[0]
+    assert c.n_ghosts == run.info["cell"].size
+    _check_values(run, [w], placement, torch.float64)
+    run.mode = "persistent"
+    _check_values(run, [w], placement, torch.float64)
+
+
+def _forces_case(w, placement, dtype, mode="persistent"):
+    run = GPURun([w], placement, mode=mode, dtype=dtype)
+    arrays = run.field_arrays()
+    if dtype == torch.float32:
+        arrays = [a.astype(np.float32).astype(np.float64) for a in arrays]
+    bcs = run.bc_arrays()
+    if dtype == torch.float32:
+        bcs = [b.astype(np.float32).astype(np.float64) for b in bcs]
+    ft, _ = run.fill(arrays, bcs)
+    d = w["grid"]["dim"]
+    dirs = I.DRAG_LIFT_DIRS_2D if d == 2 else I.DRAG_LIFT_DIRS_3D
+    vel = [None if i is None else ft[i] for i in w["roles"]["vel"]]
+    out = run.R.forces(vel, ft[w["roles"]["p"]], w["mu"], dirs).cpu().numpy()[0]
+    # oracle on the GPU-filled values?  No: on its own fill of the same inputs
+    c = O.classify(w["grid"], w["body"], placement)
+    lev = O.build_levels(c)
+    sel = run.info["geom"] == 0
+    filled = O.fill(c, lev, arrays, w["bc"], [b[sel] for b in bcs])
+    vel_o = [None if i is None else filled[i] for i in w["roles"]["vel"]]
+    ref, scale = O.forces(c, lev, filled[w["roles"]["p"]], vel_o, w["mu"], dirs)
+    return out, ref, scale
+
+
+@pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
+def test_cylinder_forces_fp64(placement):
+    out, ref, scale = _forces_case(I.cylinder(128, 1), placement, torch.float64)
+    assert np.all(np.abs(out - ref) <= 1e-12 * scale + 1e-300), (out, ref, scale)
+
+
+@pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
+def test_airfoil_2048(placement):
+    w = I.airfoil_2048()
+    run = GPURun([w], placement, mode="persistent")
+    compare_structure(run, [w], placement)
+    _check_values(run, [w], placement, torch.float64)
+    run.dtype = torch.float32
+    _check_values(run, [w], placement, torch.float32)
+
+
+def test_airfoil_forces():
+    w = I.airfoil_2048()
+    out, ref, scale = _forces_case(w, "HGC", torch.float64)
+    assert np.all(np.abs(out - ref) <= 1e-12 * scale), (out, ref, scale)
+    out, ref, scale = _forces_case(w, "HGC", torch.float32)
+    assert np.all(np.abs(out - ref) <= 1e-4 * scale), (out, ref, scale)
+
+
+def test_batch_subset_both_modes():
+    geoms = I.batch()[:24]
+    run = GPURun(geoms, "HGC", mode="persistent", dtype=torch.float32)
+    compare_structure(run, geoms, "HGC")
+    _check_values(run, geoms, "HGC", torch.float32)
+    run.mode = "level"
+    run.dtype = torch.float64
+    _check_values(run, geoms, "HGC", torch.float64)
+
+
+def test_reclassify_is_deterministic_and_sync_free():
+    w = I.airfoil_2048()
+    run = GPURun([w], "HGC")
+    t0 = run.R.tags.clone()
+    info0 = run.R.ghost_info()
+    for _ in range(3):
+        run.R.classify()
+        run.R.build_levels()
+    run.R.sync_status()
+    assert torch.equal(run.R.tags, t0)
+    info1 = run.R.ghost_info()
+    for k in info0:
+        assert np.array_equal(info0[k], info1[k]), k
+
+
+def test_stencil_out_of_grid_is_reported():
+    # body touching the domain edge: a stencil leaves the grid
+    g = {"grid": I.grid(2, [32, 32], [-1.0, -1.0], [1.0, 1.0]), "body": I.circle(0.55, 0.0, 0.47)}
+    from paper_2609_10165_b300.api import Reconstructor
+    from paper_2609_10165_b300._lib import EBRError
+    with pytest.raises(EBRError) as ei:
+        R = Reconstructor(g["grid"], g["body"], "HGC")
+        R.build_levels()
+        R.sync_status()
+    assert ei.value.name == "EBR_ESTENCIL_OOB"
+    with pytest.raises(O.EBRError) as eo:
+        O.build_levels(O.classify(g["grid"], g["body"], "HGC"))
+    assert eo.value.code == "ESTENCIL_OOB"
+
+
+def test_invalid_arguments():
+    from paper_2609_10165_b300.api import Reconstructor
+    from paper_2609_10165_b300._lib import EBRError
+    with pytest.raises(EBRError) as ei:
+        Reconstructor(I.grid(2, [1, 32], [-1.0, -1.0], [1.0, 1.0]), I.circle(0, 0, 0.3))
+    assert ei.value.name == "EBR_EINVAL"
+    with pytest.raises(EBRError):
+        Reconstructor(I.grid(3, [8, 8, 8], [-1.0] * 3, [1.0] * 3), I.circle(0, 0, 0.3))
