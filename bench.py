@@ -1,0 +1,441 @@
+"""Benchmark: ghost-cell updates/s of the batched FP32 (FP64-coefficient)
+direct reconstruction, forward + adjoint, on the 256-geometry batch.
+
+One step = the whole hot path over the batch: classify + place ghosts,
+dependency levels, level-by-level fill of 3 fields, boundary forces
+(drag / lift), and the adjoint of fill + forces.  One update = one
+(ghost, field) value (forward value plus its adjoint contribution).
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl mine|reference]
+
+Prints one JSON line (rank 0).  Inputs are synthetic (seeded ellipses and
+4-digit airfoils, manufactured Fourier fields); the L2 cache is flushed
+between timed steps.  Under torchrun every rank runs its own batch (weak
+scaling, no collective on the data path).
+"""
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "batch_256"
+METRIC = "ghost-cell updates/s (fwd+adjoint), batched FP32 with FP64 coefficients"
+UNIT = "updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--geoms", type=int, default=256)
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--lite", action="store_true",
+                    help="headline step only (no plain FP64 path, no e2e, no CPU baseline), for profilers")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+
+def make_batch(n_geoms):
+    from paper_2609_10165_b300 import inputs as I
+    return I.batch(n_geoms)
+
+
+def setup(geoms, device, dtype):
+    import torch
+    from paper_2609_10165_b300 import inputs as I
+    from paper_2609_10165_b300.api import Reconstructor
+
+    R = Reconstructor([g["grid"] for g in geoms], [g["body"] for g in geoms], "HGC", device=device)
+    R.build_levels()
+    R.sync_status()
+    info = R.ghost_info()
+    F = 3
+    host_fields = []
+    for f in range(F):
+        host_fields.append(np.concatenate([g["fields"][f].on_grid(g["grid"], np.float32 if dtype == torch.float32 else np.float64)
+                                           for g in geoms]))
+    bcs = []
+    for f in range(F):
+        v = np.zeros(info["cell"].size)
+        for b, g in enumerate(geoms):
+            sel = info["geom"] == b
+            v[sel] = I.bc_values(g["fields"][f], g["bc"][f], info["S"][sel, :2], info["normal"][sel, :2])
+        bcs.append(v)
+    fields = [torch.tensor(a, dtype=dtype, device=device) for a in host_fields]
+    bct = [torch.tensor(b, dtype=dtype, device=device) for b in bcs]
+    return R, info, host_fields, bcs, fields, bct
+
+
+class Step:
+    """The timed hot path on resident device buffers."""
+
+    def __init__(self, R, fields, bcs, geoms, mode, adjoint=True):
+        import torch
+        self.R, self.fields, self.bcs, self.mode, self.adjoint = R, fields, bcs, mode, adjoint
+        self.kinds = geoms[0]["bc"]
+        self.vel = geoms[0]["roles"]["vel"]
+        self.p = geoms[0]["roles"]["p"]
+        self.mu = geoms[0]["mu"]
+        from paper_2609_10165_b300 import inputs as I
+        self.dirs = I.DRAG_LIFT_DIRS_2D
+        dev = R.device
+        self.out = torch.empty(R.B * 6, dtype=torch.float64, device=dev)
+        self.seed = torch.ones(R.B, 2, dtype=torch.float64, device=dev)
+        self.gf = [torch.zeros_like(f) for f in fields]
+        self.gb = [torch.zeros_like(b) for b in bcs]
+
+    def __call__(self):
+        R = self.R
+        R.classify()
+        R.build_levels()
+        R.reconstruct(self.fields, self.kinds, self.bcs, mode=self.mode)
+        R.forces([self.fields[i] for i in self.vel], self.fields[self.p], self.mu, self.dirs, out=self.out)
+        if self.adjoint:
+            R.adjoint(self.kinds, self.vel, self.p, self.mu, self.dirs, self.seed, self.gf, self.gb,
+                      mode=self.mode)
+
+
+def time_steps(fn, steps, stream, flush):
+    """Per-step device time with CUDA events on the launching stream, the L2
+    cache flushed (untimed) before every step.  Returns list of ms."""
+    import torch
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ts]
+
+
+def cpu_baseline(geoms_all, budget_s=15.0):
+    """The oracle as it stands on a bounded sample of the batch: classify,
+    levels, fill of 3 fields, forces and the explicit-matrix adjoint."""
+    import oracle as O
+    from paper_2609_10165_b300 import inputs as I
+
+    t0 = time.perf_counter()
+    updates = 0
+    done = 0
+    for g in geoms_all:
+        c = O.classify(g["grid"], g["body"], "HGC")
+        lev = O.build_levels(c)
+        X = c.grid.centre(c.grid.unlin(c.idx))
+        S = (X + c.psi[:, None] * c.n)[lev.order]
+        nn = c.n[lev.order]
+        arrays = [f.on_grid(g["grid"], np.float32).astype(np.float64) for f in g["fields"]]
+        bcs = [I.bc_values(f, k, S, nn) for f, k in zip(g["fields"], g["bc"])]
+        out = O.fill(c, lev, arrays, g["bc"], bcs)
+        O.forces(c, lev, out[2], [out[0], out[1]], g["mu"], I.DRAG_LIFT_DIRS_2D)
+        O.adjoint_gradient(c, lev, g["bc"], 2, [0, 1], g["mu"], I.DRAG_LIFT_DIRS_2D, (1.0, 1.0))
+        updates += c.n_ghosts * 3
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d of %d geometries of %s (classify, levels, fill of 3 fields, forces, "
+                      "explicit-matrix adjoint), %.1f s" % (done, len(geoms_all), WORKLOAD, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    geoms = make_batch(args.geoms)
+    ts = []
+    base = None
+    for s in range(args.warmup + args.steps):
+        # each step a bounded sample: a rotating window of geometries
+        k = s % len(geoms)
+        sample = geoms[k:k + 2] or geoms[:2]
+        r = cpu_baseline(sample, budget_s=2.0)
+        if s >= args.warmup:
+            ts.append(r)
+        base = r
+    val = float(np.mean([r["value"] for r in ts]))
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "impl": "reference",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "2 geometries per step"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": val,
+                             "sample": "per step 2 geometries of %s; last: %s" % (WORKLOAD, base["sample"])},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    geoms = make_batch(args.geoms)
+    R, info, host_fields, host_bcs, fields, bcs = setup(geoms, dev, torch.float32)
+    ng = int(info["cell"].size)
+    F = 3
+    updates = ng * F
+    counts = R.counts()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+
+    step = Step(R, fields, bcs, geoms, "persistent", adjoint=True)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    R.sync_status()
+    l0 = R.launches
+    step()
+    torch.cuda.synchronize()
+    launches_per_step = R.launches - l0
+
+    # CUDA graph of the whole step
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=side, capture_error_mode="relaxed"):
+            step()
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    R.sync_status()
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    ms = time_steps(g.replay, args.steps, stream, flush)
+    t_wall = time.perf_counter() - t_wall0
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    R.sync_status()
+    ms_step = float(np.mean(ms))
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = updates * world / (ms_step * 1e-3)
+
+    # forward only (same graph construction)
+    step_f = Step(R, fields, bcs, geoms, "persistent", adjoint=False)
+    gf = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        step_f()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(gf, stream=side, capture_error_mode="relaxed"):
+            step_f()
+    torch.cuda.synchronize()
+    ms_f = float(np.mean(time_steps(gf.replay, max(5, args.steps // 2), stream, flush)))
+
+    # per-kernel device times of an eager step (events bracket each launch)
+    R.profile(True)
+    for _ in range(3):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    prof = R.profile_read()
+    R.profile(False)
+    prof_ms = {k: v[0] / 3.0 for k, v in prof.items()}
+    prof_n = {k: v[1] / 3.0 for k, v in prof.items()}
+    top = max(prof_ms, key=prof_ms.get)
+
+    # plain FP64 path: one launch per level per geometry, FP64 fields, no graph
+    ms64 = float("nan")
+    try:
+        if args.lite:
+            raise StopIteration
+        fields64 = [torch.tensor(a.astype(np.float64), device=dev) for a in host_fields]
+        bcs64 = [torch.tensor(b, dtype=torch.float64, device=dev) for b in host_bcs]
+        step64 = Step(R, fields64, bcs64, geoms, "level", adjoint=True)
+        step64()
+        torch.cuda.synchronize()
+        ms64 = float(np.mean(time_steps(step64, max(3, args.steps // 5), stream, flush)))
+        del fields64, bcs64, step64
+    except StopIteration:
+        pass
+    except Exception as e:  # reported, not hidden
+        print("plain FP64 path failed: %s" % e, file=sys.stderr)
+
+    # end to end through host buffers: H2D of the fields and boundary data
+    # from pinned memory, the step, D2H of the forces
+    pin_f = [torch.from_numpy(a).pin_memory() for a in host_fields]
+    pin_b = [torch.from_numpy(b.astype(np.float32)).pin_memory() for b in host_bcs]
+    host_out = torch.empty(R.B * 6, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in pin_f + pin_b)
+    d2h = host_out.numel() * 8
+
+    def e2e_step():
+        for t, h in zip(fields, pin_f):
+            t.copy_(h, non_blocking=True)
+        for t, h in zip(bcs, pin_b):
+            t.copy_(h, non_blocking=True)
+        g.replay()
+        host_out.copy_(step.out, non_blocking=True)
+
+    e2e_ms = [float("nan")]
+    e2e_val = None
+    if not args.lite:
+        e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = time_steps(e2e_step, max(5, args.steps // 3), stream, flush)
+        e2e_val = updates * world / (np.mean(e2e_ms) * 1e-3)
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / duration
+    peak, peak_kind = measured_peaks()
+    n_cells = R.n_cells
+    rows = sum(c2["n_cells"] // geoms[b]["grid"]["n"][0] for b, c2 in enumerate(counts))
+    ni = sum(c2["n_interface"] for c2 in counts)
+    nft = sum(c2["n_fluid_targets"] for c2 in counts)
+    K = 3
+    algo = {
+        # tag stream: 1 byte per cell written + 8 B per row run
+        "rows": n_cells * 1 + rows * 8,
+        # fill: per update 3 stencil reads + BC + write (FP32), per ghost the
+        # record (cell 4, meta 4) and the weights (8 doubles per kind used)
+        "fill_chain": updates * 20 + ng * (8 + 2 * 8 * 8 + 4 * K),
+        "adj_chain": ng * (F * 4 + 8 * 8 * F) + ng * 4,
+        "place": ni * (4 + 4 + 1 + 8 + 24 + 1),
+    }
+    tb = algo.get(top)
+    if tb:
+        tb = tb / prof_n[top]                       # bytes per launch
+    achieved = (tb / (prof_ms[top] / prof_n[top] * 1e-3) / 1e9) if tb else None
+    roof = {"kernel": top, "bound": "hbm" if tb else "latency",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": None, "peak_source": peak_kind,
+            "kernel_ms": {k: round(v, 5) for k, v in sorted(prof_ms.items(), key=lambda kv: -kv[1])}}
+
+    baseline = None
+    if rank == 0 and not args.no_baseline and not args.lite:
+        baseline = cpu_baseline(geoms, budget_s=15.0)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 fields, f64 coefficients", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "geometries": args.geoms, "cells": n_cells, "ghosts": ng,
+                   "fields": F, "placement": "HGC", "max_levels": max(c2["n_levels"] for c2 in counts),
+                   "l2": "flushed before every timed step (512 MB write)", "graph": True,
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "fwd_updates_per_s": updates * world / (ms_f * 1e-3), "fwd_ms_per_step": ms_f,
+        "plain_fp64_updates_per_s": updates * world / (ms64 * 1e-3) if ms64 == ms64 else None,
+        "plain_fp64_ms_per_step": ms64,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": float(np.mean(e2e_ms))},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "roofline": roof,
+        "clocks": clk,
+        "cpu_baseline": baseline,
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -259,6 +259,22 @@ ebr_status ebr_sync_status(void* ctx, ebr_stream stream);
 /* Number of kernel launches this context has issued since creation. */
 int64_t ebr_launch_count(const void* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Timing (diagnostics; the paper has no counterpart)
+ * ------------------------------------------------------------------------- */
+
+/* enable != 0: from now on every kernel launch of the context is bracketed by
+ * two CUDA events recorded on the launching stream (adds a small gap between
+ * kernels).  Clears earlier records.  enable = 0 turns it off. */
+ebr_status ebr_profile(void* ctx, int32_t enable);
+/* Synchronise the recorded events and aggregate them by kernel name:
+ * h_names [max_entries][32] (NUL-terminated), h_ms [max_entries] total
+ * milliseconds, h_count [max_entries] launches.  Returns the number of
+ * distinct names (may exceed max_entries) or a negative ebr_status; clears
+ * the records.  Any output pointer may be NULL. */
+int32_t ebr_profile_read(void* ctx, int32_t max_entries, char* h_names, double* h_ms,
+                         int64_t* h_count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,6 +59,8 @@ _SIGS = {
                                           c_int32, c_int32, c_int32, c_void_p]),
     "ebr_sync_status": (c_int32, [c_void_p, c_void_p]),
     "ebr_launch_count": (c_int64, [c_void_p]),
+    "ebr_profile": (c_int32, [c_void_p, c_int32]),
+    "ebr_profile_read": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)

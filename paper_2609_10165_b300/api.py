@@ -173,6 +173,59 @@ class Reconstructor:
     def sync_status(self):
         self._check(self.lib.ebr_sync_status(self.ctx, self._stream()))
 
+    def profile(self, enable=True):
+        self._check(self.lib.ebr_profile(self.ctx, 1 if enable else 0))
+
+    def profile_read(self, max_entries=64):
+        names = ctypes.create_string_buffer(32 * max_entries)
+        ms = (ctypes.c_double * max_entries)()
+        cnt = (ctypes.c_int64 * max_entries)()
+        n = self.lib.ebr_profile_read(self.ctx, max_entries, names, ms, cnt)
+        if n < 0:
+            self._check(n)
+        out = {}
+        for k in range(min(n, max_entries)):
+            nm = names.raw[32 * k: 32 * k + 32].split(b"\0", 1)[0].decode()
+            out[nm] = (float(ms[k]), int(cnt[k]))
+        return out
+
     @property
     def launches(self):
         return int(self.lib.ebr_launch_count(self.ctx))
+
+    def drag_lift(self, fields, bcs, bc_kinds, vel_index, p_index, mu, dirs, mode="persistent"):
+        """(drag, lift) per geometry [B, 2], differentiable with respect to the
+        field values and the boundary data (backward = ebr_reconstruct_adjoint)."""
+        return DragLift.apply(self, tuple(int(k) for k in bc_kinds), tuple(vel_index), int(p_index),
+                              float(mu), tuple(np.asarray(dirs, np.float64).reshape(-1)), mode,
+                              *fields, *bcs)
+
+
+class DragLift(torch.autograd.Function):
+    """Fill (out of place) + forces forward; the library's adjoint backward.
+
+    The ghost entries of the input fields do not influence the result (the
+    fill overwrites them), so their gradient is zero."""
+
+    @staticmethod
+    def forward(ctx, R, bc_kinds, vel_index, p_index, mu, dirs, mode, *tensors):
+        F = len(bc_kinds)
+        fields = [t.detach().clone() for t in tensors[:F]]
+        bcs = [t.detach() for t in tensors[F:]]
+        R.reconstruct(fields, bc_kinds, bcs, mode=mode)
+        d = R.dim
+        vel = [fields[i] if i is not None and i >= 0 else None for i in vel_index]
+        out = R.forces(vel, fields[p_index], mu, np.asarray(dirs).reshape(2, d))
+        ctx.R, ctx.args = R, (bc_kinds, vel_index, p_index, mu, dirs, mode)
+        ctx.shapes = [(t.shape, t.dtype, t.device) for t in tensors]
+        return out[:, 2 * d: 2 * d + 2].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        R = ctx.R
+        bc_kinds, vel_index, p_index, mu, dirs, mode = ctx.args
+        F = len(bc_kinds)
+        grads = [torch.zeros(s, dtype=dt, device=dv) for s, dt, dv in ctx.shapes]
+        R.adjoint(bc_kinds, list(vel_index), p_index, mu, np.asarray(dirs).reshape(2, R.dim),
+                  g.detach().to(torch.float64), grads[:F], grads[F:], accumulate=False, mode=mode)
+        return (None,) * 7 + tuple(grads)

@@ -97,7 +97,39 @@ struct Ctx {
 
   std::vector<int> order_by_size;            // geometries, largest ghost count first
   std::map<long long, ChainPlan> chain_plans;
+
+  // optional per-kernel timing: events recorded on the launching stream
+  struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
 };
+
+cudaEvent_t take_event(Ctx* c) {
+  if (c->pool_used == c->pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->pool.push_back(e);
+  }
+  return c->pool[c->pool_used++];
+}
+
+void prof_begin(Ctx* c, cudaStream_t s, const char* name) {
+  if (!c->prof) return;
+  Ctx::ProfRec r{name, take_event(c), nullptr};
+  if (r.a) cudaEventRecord(r.a, s);
+  c->recs.push_back(r);
+}
+
+void prof_end(Ctx* c, cudaStream_t s) {
+  if (!c->prof || c->recs.empty()) return;
+  c->recs.back().b = take_event(c);
+  if (c->recs.back().b) cudaEventRecord(c->recs.back().b, s);
+}
 
 ebr_status fail(Ctx* c, ebr_status s, const char* fmt, ...) {
   char buf[512];
@@ -159,6 +191,10 @@ ebr_status balloc(Ctx* c, void** p, size_t bytes) {
   } while (0)
 
 void free_all(Ctx* c) {
+  for (auto& e : c->pool) cudaEventDestroy(e);
+  c->pool.clear();
+  c->pool_used = 0;
+  c->recs.clear();
   for (auto& b : c->bufs) cudaFree(b.p);
   c->bufs.clear();
   for (auto& kv : c->chain_plans) (void)kv;
@@ -194,12 +230,18 @@ ebr_status upload_geoms(Ctx* c) {
 // ---------------------------------------------------------------------------
 ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   c->tags = d_tags;
+  prof_begin(c, s, "rows");
   launch_rows(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, d_tags, c->d_status, c->d_stats, s);
+  prof_end(c, s);
   c->launches += 1;
   CKL();
+  prof_begin(c, s, "iface");
   launch_iface(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, c->row_cnt, nullptr, nullptr,
                nullptr, nullptr, 0, 0, c->d_status, s);
+  prof_end(c, s);
+  prof_begin(c, s, "scan");
   launch_scan(c->row_cnt, c->row_ptr, c->total_rows, c->scan_tmp, s);
+  prof_end(c, s);
   c->launches += 4;
   CKL();
   if (planning) {
@@ -220,18 +262,30 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
     AL(c->gflag, ni);
     AL(c->gpos, ni + 1);
   }
+  prof_begin(c, s, "iface");
   launch_iface(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, nullptr, c->row_ptr,
                c->iface_cell, c->iface_geo, c->iface_solid, 1, c->n_iface, c->d_status, s);
+  prof_end(c, s);
+  prof_begin(c, s, "place");
   launch_place(c->dG, c->n_iface, c->iface_cell, c->iface_geo, c->iface_solid, c->placement,
                d_tags, c->iface_psi, c->iface_n, c->d_status, s);
+  prof_end(c, s);
   c->launches += 2;
   if (c->placement == EBR_HGC) {
+    prof_begin(c, s, "reclassify");
     launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 0, s);
+    prof_end(c, s);
+    prof_begin(c, s, "reclassify");
     launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 1, s);
+    prof_end(c, s);
     c->launches += 2;
   }
+  prof_begin(c, s, "ghost_flags");
   launch_ghost_flags(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->gflag, s);
+  prof_end(c, s);
+  prof_begin(c, s, "scan");
   launch_scan(c->gflag, c->gpos, c->n_iface, c->scan_tmp, s);
+  prof_end(c, s);
   c->launches += 4;
   CKL();
   if (planning) {
@@ -259,9 +313,11 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
                                                c->d_nlev, 1, c->d_status);
     c->launches += 2;
   }
+  prof_begin(c, s, "ghost_write");
   launch_ghost_write(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->iface_psi,
                      c->iface_n, c->gpos, c->placement, c->ng, c->gs_cell, c->gs_geo, c->gs_psi,
                      c->gs_n, c->gs_meta, c->d_stats + 1, c->d_status, s);
+  prof_end(c, s);
   c->launches += 1;
   CKL();
   if (planning) {
@@ -303,11 +359,17 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
       if (st) return st;
     }
   }
+  prof_begin(c, s, "poscell");
   launch_poscell(c->dG, ng, c->gs_cell, c->gs_geo, nullptr, c->pos_of_cell, s);
+  prof_end(c, s);
+  prof_begin(c, s, "deps");
   launch_deps(c->dG, ng, c->gs_cell, c->gs_geo, c->gs_meta, c->gs_n, c->tags, c->pos_of_cell,
               c->dep, c->d_status, s);
+  prof_end(c, s);
+  prof_begin(c, s, "levels");
   launch_levels(c->dG, c->B, c->dep, ng, c->level, c->order_pos, c->lev_ptr, c->d_nlev,
                 c->d_status, s);
+  prof_end(c, s);
   c->launches += 3;
   CKL();
   if (planning) {
@@ -327,15 +389,25 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
                                                c->d_nlev, 2, c->d_status);
     c->launches += 1;
   }
+  prof_begin(c, s, "reorder");
   launch_reorder(ng, c->order_pos, c->gs_cell, c->gs_geo, c->gs_psi, c->gs_n, c->gs_meta, c->dep,
                  c->level, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->g_dep, c->g_level, s);
+  prof_end(c, s);
+  prof_begin(c, s, "poscell");
   launch_poscell(c->dG, ng, c->g_cell, c->g_geo, nullptr, c->pos_of_cell, s);
+  prof_end(c, s);
+  prof_begin(c, s, "tables");
   launch_tables(c->dG, ng, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->tags, c->wtab,
                 c->ftab, s);
+  prof_end(c, s);
   // ghost-target sources
+  prof_begin(c, s, "gsrc");
   launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax, nullptr,
               c->gsrc_cnt, 0, s);
+  prof_end(c, s);
+  prof_begin(c, s, "scan");
   launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, s);
+  prof_end(c, s);
   c->launches += 7;
   CKL();
   if (planning) {
@@ -350,12 +422,18 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     }
     AL(c->gsrc, c->n_gsrc);
   }
+  prof_begin(c, s, "gsrc");
   launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
               c->gsrc_ptr, c->gsrc, 1, s);
+  prof_end(c, s);
   // fluid-target sources
+  prof_begin(c, s, "fsrc");
   launch_fsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax, nullptr,
               c->own_flag, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s);
+  prof_end(c, s);
+  prof_begin(c, s, "scan");
   launch_scan(c->own_flag, c->own_ptr, 8 * ng, c->scan_tmp, s);
+  prof_end(c, s);
   c->launches += 5;
   CKL();
   if (planning) {
@@ -366,9 +444,13 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     AL(c->ft_cnt, c->nft);
     AL(c->ft_ptr, c->nft + 1);
   }
+  prof_begin(c, s, "fsrc");
   launch_fsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
               c->own_ptr, c->own_flag, c->ft_cell, c->ft_geo, c->ft_cnt, nullptr, nullptr, 1, s);
+  prof_end(c, s);
+  prof_begin(c, s, "scan");
   launch_scan(c->ft_cnt, c->ft_ptr, c->nft, c->scan_tmp, s);
+  prof_end(c, s);
   c->launches += 4;
   CKL();
   if (planning) {
@@ -380,8 +462,10 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     for (int t = 0; t < c->nft; ++t) c->h_nft_geo[fg[t]]++;
     AL(c->ft_src, c->n_fsrc);
   }
+  prof_begin(c, s, "fsrc");
   launch_fsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
               c->own_ptr, c->own_flag, c->ft_cell, c->ft_geo, c->ft_cnt, c->ft_ptr, c->ft_src, 2, s);
+  prof_end(c, s);
   c->launches += 1;
   CKL();
   if (planning) {
@@ -677,9 +761,11 @@ ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
     ebr_status st = chain_plan(c, 0, dtype, n_fields, &cp);
     if (st) return st;
     if (cp->n_list > 0) {
+      prof_begin(c, s, "fill_chain");
       launch_fill_chain(dtype, 0, n_fields, d_fields, kinds, d_bc, c->dG, cp->d_list, cp->n_list,
                         c->g_cell, c->g_meta, c->g_dep, c->lev_ptr, c->wtab, c->ng, cp->smem,
                         c->d_status, s);
+      prof_end(c, s);
       c->launches += 1;
       CKL();
     }
@@ -693,8 +779,10 @@ ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
     const Geom& g = c->hG[b];
     for (int lv = 1; lv <= g.n_levels; ++lv) {
       int p0 = c->h_lev_ptr[g.lev_off + lv - 1], p1 = c->h_lev_ptr[g.lev_off + lv];
+      prof_begin(c, s, "fill_level");
       launch_fill_level(dtype, g.dim, n_fields, d_fields, kinds, d_bc, g.cell_off, p0, p1, c->g_cell,
                         c->g_meta, c->wtab, c->ng, g.n[0], g.n[1], s);
+      prof_end(c, s);
       c->launches += 1;
     }
   }
@@ -713,9 +801,12 @@ ebr_status ebr_boundary_forces(void* ctx, const void* const* d_vel, const void* 
   int dim = c->hG[0].dim;
   for (int b = 1; b < c->B; ++b)
     if (c->hG[b].dim != dim) return fail(c, EBR_EINVAL, "ebr_boundary_forces: mixed dimensions");
+  cudaStream_t s = S(stream);
+  prof_begin(c, s, "forces");
   launch_forces(dtype, dim, d_vel, d_p, mu, h_dirs, c->dG, c->n_chunks, c->chunks, c->g_cell,
                 c->g_geo, c->g_n, c->g_meta, c->ftab, c->ng, c->partial, c->B, d_out, c->chunk_ptr,
-                S(stream));
+                s);
+  prof_end(c, s);
   c->launches += c->n_chunks > 0 ? 2 : 1;
   CKL();
   return EBR_OK;
@@ -746,7 +837,9 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
   cudaStream_t s = S(stream);
   int kinds[8];
   for (int f = 0; f < n_fields; ++f) kinds[f] = h_bc_kind[f];
+  prof_begin(c, s, "adj_seed");
   launch_adj_seed(dim, n_fields, role, mu, h_dirs, d_seed, c->ng, c->g_geo, c->g_n, c->ftab, c->sv, s);
+  prof_end(c, s);
   c->launches += 1;
   std::vector<int> level_geoms;
   if (mode == EBR_MODE_PERSISTENT) {
@@ -754,8 +847,10 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
     ebr_status st = chain_plan(c, 1, dtype, n_fields, &cp);
     if (st) return st;
     if (cp->n_list > 0) {
+      prof_begin(c, s, "adj_chain");
       launch_adj_chain(dtype, dim, n_fields, kinds, c->dG, cp->d_list, cp->n_list, c->lev_ptr,
                        c->gsrc_ptr, c->gsrc, c->g_meta, c->wtab, c->sv, c->ng, c->lam, cp->smem, s);
+      prof_end(c, s);
       c->launches += 1;
     }
     level_geoms = cp->fallback;
@@ -768,18 +863,65 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
     const Geom& g = c->hG[b];
     for (int lv = g.n_levels; lv >= 1; --lv) {
       int p0 = c->h_lev_ptr[g.lev_off + lv - 1], p1 = c->h_lev_ptr[g.lev_off + lv];
+      prof_begin(c, s, "adj_level");
       launch_adj_level(dtype, dim, n_fields, kinds, p0, p1, c->gsrc_ptr, c->gsrc, c->g_meta, c->wtab,
                        c->sv, c->ng, c->lam, s);
+      prof_end(c, s);
       c->launches += 1;
     }
   }
+  prof_begin(c, s, "adj_fluid");
   launch_adj_fluid(dtype, dim, n_fields, kinds, c->nft, c->ft_cell, c->ft_geo, c->ft_ptr, c->ft_src,
                    c->dG, c->g_meta, c->wtab, c->sv, c->ng, c->lam, d_grad_fields, accumulate, s);
+  prof_end(c, s);
+  prof_begin(c, s, "adj_bc");
   launch_adj_bc(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->wtab, c->lam, d_grad_bc,
                 d_grad_fields, accumulate, s);
+  prof_end(c, s);
   c->launches += 2;
   CKL();
   return EBR_OK;
+}
+
+ebr_status ebr_profile(void* ctx, int32_t enable) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->prof = enable != 0;
+  c->recs.clear();
+  c->pool_used = 0;
+  return EBR_OK;
+}
+
+int32_t ebr_profile_read(void* ctx, int32_t max_entries, char* h_names, double* h_ms,
+                         int64_t* h_count) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  std::vector<std::string> names;
+  std::vector<double> ms;
+  std::vector<long long> cnt;
+  for (auto& r : c->recs) {
+    if (!r.a || !r.b) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return fail(c, EBR_ECUDA, "event synchronise failed");
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return fail(c, EBR_ECUDA, "event timing failed");
+    size_t k = 0;
+    while (k < names.size() && names[k] != r.name) ++k;
+    if (k == names.size()) { names.push_back(r.name); ms.push_back(0.0); cnt.push_back(0); }
+    ms[k] += t;
+    cnt[k] += 1;
+  }
+  int n = (int)names.size();
+  for (int k = 0; k < n && k < max_entries; ++k) {
+    if (h_names) {
+      std::strncpy(h_names + 32 * k, names[k].c_str(), 31);
+      h_names[32 * k + 31] = 0;
+    }
+    if (h_ms) h_ms[k] = ms[k];
+    if (h_count) h_count[k] = cnt[k];
+  }
+  c->recs.clear();
+  c->pool_used = 0;
+  return n;
 }
 
 ebr_status ebr_sync_status(void* ctx, ebr_stream stream) {

@@ -206,3 +206,19 @@ def test_invalid_arguments():
     assert ei.value.name == "EBR_EINVAL"
     with pytest.raises(EBRError):
         Reconstructor(I.grid(3, [8, 8, 8], [-1.0] * 3, [1.0] * 3), I.circle(0, 0, 0.3))
+
+
+@pytest.mark.parametrize("name", ["sphere_256", "sphere_512"])
+def test_sphere_fp32(name):
+    w = I.WORKLOADS[name]()
+    run = GPURun([w], "HGC", mode="persistent", dtype=torch.float32)
+    compare_structure(run, [w], "HGC")
+    _check_values(run, [w], "HGC", torch.float32)
+
+
+def test_sphere_256_forces():
+    w = I.WORKLOADS["sphere_256"]()
+    out, ref, scale = _forces_case(w, "HGC", torch.float64)
+    assert np.all(np.abs(out - ref) <= 1e-12 * scale), (out, ref, scale)
+    out, ref, scale = _forces_case(w, "HGC", torch.float32)
+    assert np.all(np.abs(out - ref) <= 1e-4 * scale), (out, ref, scale)
