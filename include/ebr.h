@@ -275,6 +275,36 @@ ebr_status ebr_profile(void* ctx, int32_t enable);
 int32_t ebr_profile_read(void* ctx, int32_t max_entries, char* h_names, double* h_ms,
                          int64_t* h_count);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free classification of one grid (the paper has no counterpart)
+ * ------------------------------------------------------------------------- */
+
+/* Largest n_y * n_z (number of x-rows) ebr_classify_cells_static accepts. */
+#define EBR_STATIC_MAX_ROWS (1 << 18)
+
+/* Fluid / solid tags of ONE grid against ONE body, for callers that cannot let
+ * the library allocate device memory: programs that own every device byte
+ * through their own pool or a fixed memory budget, and code that must not
+ * call cudaMalloc while other work runs, because cudaMalloc may synchronise
+ * the device.  Nothing is allocated and no context is needed.
+ *   d_tags         caller-owned int8 [n_x n_y n_z], receives 0 (fluid) / 1
+ *                  (solid, centre in the closed body) -- the tags before
+ *                  ghost placement; same layout as the other calls.
+ *   d_n_interface  caller-owned device int64, receives the number of cells
+ *                  with a face neighbour on the other side of the boundary.
+ * The per-row solid runs needed between the two kernels live in a fixed
+ * device array inside the library (EBR_STATIC_MAX_ROWS rows, 2 MiB, held by
+ * every device that loads the library until the process exits).  Grids with
+ * more rows are rejected with EBR_EINVAL before any GPU work, as are invalid
+ * grids or bodies (no message: there is no context).  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents: the call clears what must start at zero
+ * itself, and calls that overlap on the GPU (other streams, other threads)
+ * race on it.  Asynchronous on the stream. */
+ebr_status ebr_classify_cells_static(const ebr_grid* h_grid, const ebr_body* h_body,
+                                     int8_t* d_tags, int64_t* d_n_interface, ebr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

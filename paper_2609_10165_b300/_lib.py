@@ -61,6 +61,8 @@ _SIGS = {
     "ebr_launch_count": (c_int64, [c_void_p]),
     "ebr_profile": (c_int32, [c_void_p, c_int32]),
     "ebr_profile_read": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "ebr_classify_cells_static": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Body), c_void_p,
+                                            c_void_p, c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)

@@ -487,3 +487,191 @@ void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const
 }
 
 }  // namespace ebr
+
+// ===========================================================================
+// Allocation-free classification of one grid (ebr_classify_cells_static).
+//
+// For callers that cannot let the library allocate device memory.  The
+// per-row solid runs this needs between its two kernels live in a fixed
+// file-scope device array (EBR_STATIC_MAX_ROWS rows, 2 MiB, resident on every
+// device that loads the library until the process exits).  Every call shares
+// that array: calls that overlap on the GPU race on it.
+// ===========================================================================
+#include <mutex>
+
+#include "../../include/ebr.h"
+
+namespace {
+
+constexpr int kStaticMaxRows = EBR_STATIC_MAX_ROWS;
+constexpr int kStaticMaxDevices = 64;
+
+// [0, 2 * rows): int2 row runs; then the status word and the fallback counter
+static __device__ __align__(256) int g_static_scratch[2 * kStaticMaxRows + 64];
+
+std::mutex g_static_mutex;
+int* g_static_addr[kStaticMaxDevices] = {};
+
+__global__ void __launch_bounds__(256) k_rows_static(ebr::Geom g, int2* __restrict__ runs,
+                                                     int8_t* __restrict__ tags, int* status,
+                                                     int* stats) {
+  using namespace ebr;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int total_rows = g.n_rows;
+  for (int base = warp * 32; base < total_rows; base += nwarps * 32) {
+    int row = base + lane;
+    int s = 0, t = -1;
+    long long start = 0;
+    const int nx = g.n[0];
+    if (row < total_rows) {
+      int j = row % g.n[1];
+      int k = row / g.n[1];
+      exact_run(g, j, k, s, t, status, stats);
+      runs[row] = make_int2(s, t);
+      start = (long long)row * nx;
+    }
+    int nvalid = min(32, total_rows - base);
+    for (int r = 0; r < nvalid; ++r) {
+      int rs = __shfl_sync(0xffffffffu, s, r);
+      int rt = __shfl_sync(0xffffffffu, t, r);
+      long long rst = __shfl_sync(0xffffffffu, start, r);
+      long long end = rst + nx;
+      long long mis = (long long)(reinterpret_cast<uintptr_t>(tags) & 15u);
+      long long a0 = ((rst + mis + 15) & ~15LL) - mis;
+      long long a1 = ((end + mis) & ~15LL) - mis;
+      if (a0 > end) a0 = end;
+      if (a1 < a0) a1 = a0;
+      long long nh = a0 - rst, nt = end - a1;
+      if (lane < nh) tags[rst + lane] = (int8_t)(lane >= rs && lane <= rt);
+      if (lane < nt) {
+        long long i = a1 + lane - rst;
+        tags[a1 + lane] = (int8_t)(i >= rs && i <= rt);
+      }
+      for (long long c = a0 + 16LL * lane; c < a1; c += 16LL * 32) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            long long i = c + 4 * q + m - rst;
+            v |= (uint32_t)(i >= rs && i <= rt) << (8 * m);
+          }
+          w[q] = v;
+        }
+        *reinterpret_cast<uint4*>(tags + c) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+  }
+}
+
+// interface cells per row from the runs (same interval algebra as k_iface),
+// summed into the caller's counter
+__global__ void k_iface_count_static(ebr::Geom g, const int2* __restrict__ runs,
+                                     unsigned long long* __restrict__ count) {
+  using namespace ebr;
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  int cnt = 0;
+  if (row < g.n_rows) {
+    int ny = g.n[1], nz = g.dim == 3 ? g.n[2] : 1, n = g.n[0];
+    int j = row % ny, k = row / ny;
+    int2 R = runs[row];
+    Iv v[24];
+    int m = 0;
+    if (R.x <= R.y) {
+      if (R.x > 0) { add_iv(v, m, R.x, R.x, n); add_iv(v, m, R.x - 1, R.x - 1, n); }
+      if (R.y < n - 1) { add_iv(v, m, R.y, R.y, n); add_iv(v, m, R.y + 1, R.y + 1, n); }
+    }
+    const int dj[4] = {-1, 1, 0, 0}, dk[4] = {0, 0, -1, 1};
+    for (int q = 0; q < 4; ++q) {
+      int jj = j + dj[q], kk = k + dk[q];
+      if (jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
+      int2 Q = runs[jj + ny * kk];
+      add_diff(v, m, R, Q, n);
+      add_diff(v, m, Q, R, n);
+    }
+    for (int x = 1; x < m; ++x) {
+      Iv key = v[x];
+      int y = x - 1;
+      while (y >= 0 && v[y].a > key.a) { v[y + 1] = v[y]; --y; }
+      v[y + 1] = key;
+    }
+    int w = 0;
+    for (int x = 0; x < m; ++x) {
+      if (w > 0 && v[x].a <= v[w - 1].b + 1) v[w - 1].b = max(v[w - 1].b, v[x].b);
+      else v[w++] = v[x];
+    }
+    for (int x = 0; x < w; ++x) cnt += v[x].b - v[x].a + 1;
+  }
+  // warp reduction, one atomic per warp (integer: order-independent)
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(count, (unsigned long long)cnt);
+}
+
+}  // namespace
+
+extern "C" ebr_status ebr_classify_cells_static(const ebr_grid* h_grid, const ebr_body* h_body,
+                                                int8_t* d_tags, int64_t* d_n_interface,
+                                                ebr_stream stream) {
+  using namespace ebr;
+  if (!h_grid || !h_body || !d_tags || !d_n_interface) return EBR_EINVAL;
+  const ebr_grid& gr = *h_grid;
+  const ebr_body& bd = *h_body;
+  if (gr.dim != 2 && gr.dim != 3) return EBR_EINVAL;
+  if (bd.kind < 0 || bd.kind > 3) return EBR_EINVAL;
+  if ((bd.kind == EBR_SPHERE ? 3 : 2) != gr.dim) return EBR_EINVAL;
+  Geom g{};
+  g.dim = gr.dim;
+  long long n3 = 1;
+  for (int a = 0; a < 3; ++a) {
+    long long na = a < gr.dim ? gr.n[a] : 1;
+    if (a < gr.dim && (na < 2 || !(gr.hi[a] > gr.lo[a]))) return EBR_EINVAL;
+    g.n[a] = (int)na;
+    g.lo[a] = a < gr.dim ? gr.lo[a] : 0.0;
+    g.h[a] = a < gr.dim ? (gr.hi[a] - gr.lo[a]) / (double)na : 1.0;
+    n3 *= na;
+  }
+  if (n3 > (1LL << 31) - 1) return EBR_EINVAL;
+  long long rows = (long long)g.n[1] * g.n[2];
+  if (rows > kStaticMaxRows) return EBR_EINVAL;     // more rows than the fixed scratch holds
+  g.kind = bd.kind;
+  for (int a = 0; a < 3; ++a) { g.centre[a] = bd.centre[a]; g.radii[a] = bd.radii[a]; }
+  for (int q = 0; q < 9; ++q) g.rot[q] = bd.rot[q];
+  g.t = bd.thickness;
+  g.c = bd.chord;
+  if ((bd.kind == EBR_CIRCLE || bd.kind == EBR_SPHERE) && !(bd.radii[0] > 0)) return EBR_EINVAL;
+  if (bd.kind == EBR_ELLIPSE && !(bd.radii[0] > 0 && bd.radii[1] > 0)) return EBR_EINVAL;
+  if (bd.kind == EBR_AIRFOIL4 && !(bd.thickness > 0 && bd.chord > 0 && bd.rot[0] > 0)) return EBR_EINVAL;
+  g.cell_off = 0;
+  g.row_off = 0;
+  g.n_rows = (int)rows;
+
+  // device address of the fixed scratch, looked up once per device (the
+  // array's name is only a host-side stand-in)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return EBR_ECUDA;
+  int* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) return EBR_ECUDA;
+      g_static_addr[dev] = static_cast<int*>(p);
+    }
+    base = g_static_addr[dev];
+  }
+  int2* runs = reinterpret_cast<int2*>(base);
+  int* status = base + 2 * kStaticMaxRows;
+  int* stats = status + 1;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(status, 0, 2 * sizeof(int), s) != cudaSuccess) return EBR_ECUDA;
+  if (cudaMemsetAsync(d_n_interface, 0, sizeof(int64_t), s) != cudaSuccess) return EBR_ECUDA;
+  int warps = (int)((rows + 31) / 32);
+  k_rows_static<<<(warps + 7) / 8, 256, 0, s>>>(g, runs, d_tags, status, stats);
+  k_iface_count_static<<<(int)((rows + 127) / 128), 128, 0, s>>>(
+      g, runs, reinterpret_cast<unsigned long long*>(d_n_interface));
+  if (cudaGetLastError() != cudaSuccess) return EBR_ECUDA;
+  return EBR_OK;
+}
