@@ -178,6 +178,35 @@ class Step:
                       mode=self.mode)
 
 
+def reduce_over_ranks(ms, updates, device):
+    """Whole-job numbers under torchrun: the slowest rank's step time and the
+    updates of all ranks (every rank runs its own batch; this is the only
+    cross-rank communication).  A single process returns its own numbers."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, updates
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([updates], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
+def count_graph_kernels(g):
+    """Kernel nodes of a captured CUDA graph (all of them are this library's:
+    the step issues no other kernels).  None if the runtime bindings are missing."""
+    try:
+        from cuda.bindings import runtime as cr
+        h = cr.cudaGraph_t(init_value=g.raw_cuda_graph())
+        err, _, n = cr.cudaGraphGetNodes(h, 0)
+        err, nodes, n = cr.cudaGraphGetNodes(h, n)
+        kinds = [cr.cudaGraphNodeGetType(x)[1] for x in nodes[:n]]
+        return sum(1 for k in kinds if k == cr.cudaGraphNodeType.cudaGraphNodeTypeKernel)
+    except Exception as e:  # reported in the JSON line, not hidden
+        return "unavailable: %s" % (str(e)[:80],)
+
+
 def time_steps(fn, steps, stream, flush):
     """Per-step device time with CUDA events on the launching stream, the L2
     cache flushed (untimed) before every step.  Returns list of ms."""
@@ -284,7 +313,7 @@ def main():
     launches_per_step = R.launches - l0
 
     # CUDA graph of the whole step
-    g = torch.cuda.CUDAGraph()
+    g = torch.cuda.CUDAGraph(keep_graph=True)
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
     with torch.cuda.stream(side):
@@ -293,6 +322,7 @@ def main():
         with torch.cuda.graph(g, stream=side, capture_error_mode="relaxed"):
             step()
     torch.cuda.synchronize()
+    graph_kernels = count_graph_kernels(g)
     for _ in range(args.warmup):
         g.replay()
     torch.cuda.synchronize()
@@ -311,12 +341,8 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     R.sync_status()
-    ms_step = float(np.mean(ms))
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = updates * world / (ms_step * 1e-3)
+    ms_step, total_updates = reduce_over_ranks(float(np.mean(ms)), updates, dev)
+    value = total_updates / (ms_step * 1e-3)
 
     # forward only (same graph construction)
     step_f = Step(R, fields, bcs, geoms, "persistent", adjoint=False)
@@ -328,6 +354,8 @@ def main():
             step_f()
     torch.cuda.synchronize()
     ms_f = float(np.mean(time_steps(gf.replay, max(5, args.steps // 2), stream, flush)))
+
+    diag = R.diagnostics()
 
     # per-kernel device times of an eager step (events bracket each launch)
     R.profile(True)
@@ -380,14 +408,13 @@ def main():
         e2e_step()
         torch.cuda.synchronize()
         e2e_ms = time_steps(e2e_step, max(5, args.steps // 3), stream, flush)
-        e2e_val = updates * world / (np.mean(e2e_ms) * 1e-3)
+        e2e_val = total_updates / (np.mean(e2e_ms) * 1e-3)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / duration
     peak, peak_kind = measured_peaks()
     n_cells = R.n_cells
     rows = sum(c2["n_cells"] // geoms[b]["grid"]["n"][0] for b, c2 in enumerate(counts))
     ni = sum(c2["n_interface"] for c2 in counts)
-    nft = sum(c2["n_fluid_targets"] for c2 in counts)
     K = 3
     algo = {
         # tag stream: 1 byte per cell written + 8 B per row run
@@ -419,13 +446,15 @@ def main():
         "config": {"workload": WORKLOAD, "geometries": args.geoms, "cells": n_cells, "ghosts": ng,
                    "fields": F, "placement": "HGC", "max_levels": max(c2["n_levels"] for c2 in counts),
                    "l2": "flushed before every timed step (512 MB write)", "graph": True,
-                   "parallelism": "replicas" if world > 1 else "single"},
-        "fwd_updates_per_s": updates * world / (ms_f * 1e-3), "fwd_ms_per_step": ms_f,
-        "plain_fp64_updates_per_s": updates * world / (ms64 * 1e-3) if ms64 == ms64 else None,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "row_fallbacks_since_plan": diag["row_fallbacks"]},
+        "fwd_updates_per_s": total_updates / (ms_f * 1e-3), "fwd_ms_per_step": ms_f,
+        "plain_fp64_updates_per_s": total_updates / (ms64 * 1e-3) if ms64 == ms64 else None,
         "plain_fp64_ms_per_step": ms64,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": float(np.mean(e2e_ms))},
         "gpu_launches": int(launches_per_step * args.steps),
+        "graph_kernel_nodes_per_step": graph_kernels,
         "roofline": roof,
         "clocks": clk,
         "cpu_baseline": baseline,

@@ -105,7 +105,6 @@ typedef struct {
   int64_t n_ghosts;
   int32_t n_levels;
   int32_t reserved;
-  int64_t n_fluid_targets;   /* fluid cells read by some ghost stencil (adjoint targets) */
 } ebr_geom_counts;
 
 /* ---------------------------------------------------------------------------
@@ -255,6 +254,12 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
 
 /* Synchronise the stream, read and clear the device status word. */
 ebr_status ebr_sync_status(void* ctx, ebr_stream stream);
+
+/* Diagnostics (synchronises the stream): h_out[0] = x-rows whose solid run
+ * the 4-cell windows could not confirm, so that the whole row was swept with
+ * the exact predicate, accumulated since ebr_plan; h_out[1] = largest stencil
+ * multiplier r_i; h_out[2] = kernel launches so far.  n = entries wanted. */
+ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stream);
 
 /* Number of kernel launches this context has issued since creation. */
 int64_t ebr_launch_count(const void* ctx);

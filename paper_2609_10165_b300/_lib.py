@@ -32,7 +32,7 @@ class Body(ctypes.Structure):
 
 class GeomCounts(ctypes.Structure):
     _fields_ = [("n_cells", c_int64), ("n_interface", c_int64), ("n_ghosts", c_int64),
-                ("n_levels", c_int32), ("reserved", c_int32), ("n_fluid_targets", c_int64)]
+                ("n_levels", c_int32), ("reserved", c_int32)]
 
 
 _SIGS = {
@@ -58,6 +58,7 @@ _SIGS = {
                                           ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                                           c_int32, c_int32, c_int32, c_void_p]),
     "ebr_sync_status": (c_int32, [c_void_p, c_void_p]),
+    "ebr_diagnostics": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_int32, c_void_p]),
     "ebr_launch_count": (c_int64, [c_void_p]),
     "ebr_profile": (c_int32, [c_void_p, c_int32]),
     "ebr_profile_read": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),

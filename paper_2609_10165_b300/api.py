@@ -118,7 +118,7 @@ class Reconstructor:
         arr = (_lib.GeomCounts * self.B)()
         self._check(self.lib.ebr_counts(self.ctx, arr))
         return [{"n_cells": a.n_cells, "n_interface": a.n_interface, "n_ghosts": a.n_ghosts,
-                 "n_levels": a.n_levels, "n_fluid_targets": a.n_fluid_targets} for a in arr]
+                 "n_levels": a.n_levels} for a in arr]
 
     @property
     def n_ghosts(self):
@@ -172,6 +172,11 @@ class Reconstructor:
 
     def sync_status(self):
         self._check(self.lib.ebr_sync_status(self.ctx, self._stream()))
+
+    def diagnostics(self):
+        out = (ctypes.c_int64 * 3)()
+        self._check(self.lib.ebr_diagnostics(self.ctx, out, 3, self._stream()))
+        return {"row_fallbacks": int(out[0]), "r_max": int(out[1]), "launches": int(out[2])}
 
     def profile(self, enable=True):
         self._check(self.lib.ebr_profile(self.ctx, 1 if enable else 0))

@@ -9,11 +9,13 @@
 // with q = seed_0 e_drag + seed_1 e_lift.  With lambda_G = dJ / d phi_G:
 //   lambda_G = sum over incidences (H, s) whose slot s is G of
 //              c[f][s][H] + [s > 0 and member active] w_(H, s-1) lambda_H,
-// processed in reverse level order (consumers H sit in higher levels), then
-//   dJ/dx_T = the same sum for a fluid cell T,   dJ/db_G = w_(G, s) lambda_G.
-// Every target pulls its sources from a precomputed list in a fixed order:
-// no atomics, bitwise reproducible.
+// processed in reverse level order (consumers H sit in higher levels) from
+// per-ghost source lists; then dJ/dx_T is the same sum for a fluid cell T,
+// found by probing the ghosts that read T in a fixed order, and
+// dJ/db_G = w_(G, s) lambda_G.  Every target sums its sources in a fixed
+// order and is written once: no atomics, bitwise reproducible.
 #include "ebr_kernels.cuh"
+#include "ebr_probe.cuh"
 
 namespace ebr {
 
@@ -126,7 +128,7 @@ constexpr int AC_T = 512;
 
 size_t adj_chain_smem(int dtype, int F, int n, int n_src) {
   size_t sz = dtype == 0 ? 4 : 8;
-  return (size_t)F * n * sz + (size_t)(n + 1) * sizeof(int) + (size_t)n_src * (sizeof(int) + 2 * sz) + 64;
+  return (size_t)F * n * sz + (size_t)(2 * n + 2) * sizeof(int) + (size_t)n_src * (sizeof(int) + 2 * sz) + 64;
 }
 
 template <typename T>
@@ -149,6 +151,11 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
   T* cw = L + (size_t)F * n;                                 // [2][nsrc]
   int* cq = reinterpret_cast<int*>(cw + (size_t)2 * nsrc);   // [nsrc]
   int* cptr = cq + nsrc;                                     // [n + 1]
+  int* lps = cptr + n + 1;                                   // [n_levels + 1]
+  {
+    const int* lp = lev_ptr + g.lev_off;
+    for (int q = threadIdx.x; q <= g.n_levels; q += AC_T) lps[q] = lp[q] - g0;
+  }
   // phase 1a: force-coefficient sums, consumer counts
   if (threadIdx.x == 0) sh_carry = 0;
   __syncthreads();
@@ -216,9 +223,8 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
   }
   __syncthreads();
   // phase 2: reverse levels
-  const int* lp = lev_ptr + g.lev_off;
   for (int lv = g.n_levels; lv >= 1; --lv) {
-    int a = lp[lv - 1] - g0, b = lp[lv] - g0;
+    int a = lps[lv - 1], b = lps[lv];
     for (int s = a + threadIdx.x; s < b; s += AC_T) {
       for (int f = 0; f < F; ++f) {
         int kind = A.kind[f];
@@ -258,35 +264,61 @@ void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom*
   }
 }
 
+// Gradient of the fluid cells.  Incidence (ghost p, member k) with a fluid
+// member T probes the ghosts that read T in a fixed order; only the first of
+// them owns T and pulls every source (force coefficient + weight x lambda) in
+// that order, so each fluid cell is written once, without atomics, bitwise
+// reproducibly.
 template <typename T>
-__global__ void k_adj_fluid(AdjSet A, int F, int nft, const int* __restrict__ ft_cell,
-                            const int* __restrict__ ft_geo, const int* __restrict__ ft_ptr,
-                            const int* __restrict__ ft_src, const Geom* __restrict__ G,
-                            const uint32_t* __restrict__ g_meta, const double* __restrict__ wtab,
-                            const double* __restrict__ sv, int ng, const T* __restrict__ lam,
-                            int accumulate) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nft) return;
-  long long c = G[ft_geo[t]].cell_off + ft_cell[t];
+__global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
+                            const int* __restrict__ g_geo, const int* __restrict__ g_cell,
+                            const uint32_t* __restrict__ g_meta, const int8_t* __restrict__ tags,
+                            const int* __restrict__ pos_of_cell, int rmax,
+                            const double* __restrict__ wtab, const double* __restrict__ sv,
+                            const T* __restrict__ lam, int accumulate) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int p = i >> 3, k = i & 7;
+  if (p >= ng) return;
+  const Geom& g = G[g_geo[p]];
+  if (k >= stencil_k(g.dim)) return;
+  int gijk[3], tijk[3];
+  cell_ijk3(g, g_cell[p], gijk);
+  member_ijk(g, gijk, g_meta[p], k, tijk);
+  const int8_t* tg = tags + g.cell_off;
+  const int* pc = pos_of_cell + g.cell_off;
+  if (!in_grid(g, tijk) || tg[cell_lin(g, tijk)] != 0) return;
+  int fq = -1, fs = -1;
+  probe_sources(g, tijk, tg, pc, g_meta, rmax, [&](int q, int slot) { fq = q; fs = slot; return false; });
+  if (fq != p || fs != k + 1) return;
+  T acc[8];
+  for (int f = 0; f < F; ++f) acc[f] = T(0);
+  probe_sources(g, tijk, tg, pc, g_meta, rmax, [&](int q, int slot) {
+    bool act = meta_active(g_meta[q]) >> (slot - 1) & 1u;
+    for (int f = 0; f < F; ++f) {
+      acc[f] += (T)sv[(size_t)(f * 8 + slot) * ng + q];
+      if (act) acc[f] += (T)wtab[(size_t)(A.kind[f] * 8 + slot - 1) * ng + q] * lam[(size_t)f * ng + q];
+    }
+    return true;
+  });
+  long long c = g.cell_off + cell_lin(g, tijk);
   for (int f = 0; f < F; ++f) {
-    T v = pull_sum<T>(f, A.kind[f], ft_ptr[t], ft_ptr[t + 1], ft_src, g_meta, wtab, sv, ng, lam);
     T* gr = static_cast<T*>(A.grad[f]);
-    if (accumulate) gr[c] += v; else gr[c] = v;
+    if (accumulate) gr[c] += acc[f]; else gr[c] = acc[f];
   }
 }
 
-void launch_adj_fluid(int dtype, int dim, int F, const int* bc_kind, int nft, const int* ft_cell,
-                      const int* ft_geo, const int* ft_ptr, const int* ft_src, const Geom* G,
-                      const uint32_t* g_meta, const double* wtab, const double* sv, int ng_total,
+void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
+                      const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
+                      const int* pos_of_cell, int rmax, const double* wtab, const double* sv,
                       const void* lam, void* const* grad, int accumulate, cudaStream_t s) {
-  (void)dim;
-  if (nft <= 0) return;
+  if (ng <= 0) return;
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.grad[f] = grad[f]; }
+  int n = ng * 8;
   if (dtype == 0)
-    k_adj_fluid<float><<<(nft + 127) / 128, 128, 0, s>>>(A, F, nft, ft_cell, ft_geo, ft_ptr, ft_src, G, g_meta, wtab, sv, ng_total, (const float*)lam, accumulate);
+    k_adj_fluid<float><<<(n + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const float*)lam, accumulate);
   else
-    k_adj_fluid<double><<<(nft + 127) / 128, 128, 0, s>>>(A, F, nft, ft_cell, ft_geo, ft_ptr, ft_src, G, g_meta, wtab, sv, ng_total, (const double*)lam, accumulate);
+    k_adj_fluid<double><<<(n + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const double*)lam, accumulate);
 }
 
 template <typename T>

@@ -74,6 +74,7 @@ struct Ctx {
   uint32_t* g_meta = nullptr;
   int* pos_of_cell = nullptr;
   int* lev_ptr = nullptr;
+  size_t levels_smem = 0;      // dynamic shared memory of k_levels (planned)
   std::vector<int> h_lev_ptr;
   double* wtab = nullptr;
   double* ftab = nullptr;
@@ -220,6 +221,13 @@ __global__ void k_check(const Geom* G, int B, const int* row_ptr, const int* gpo
   }
 }
 
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
 ebr_status upload_geoms(Ctx* c) {
   CK(cudaMemcpy(c->dG, c->hG.data(), sizeof(Geom) * c->B, cudaMemcpyHostToDevice));
   return EBR_OK;
@@ -318,7 +326,7 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
                      c->iface_n, c->gpos, c->placement, c->ng, c->gs_cell, c->gs_geo, c->gs_psi,
                      c->gs_n, c->gs_meta, c->d_stats + 1, c->d_status, s);
   prof_end(c, s);
-  c->launches += 1;
+  c->launches += 2;
   CKL();
   if (planning) {
     CK(cudaMemcpyAsync(&c->rmax, c->d_stats + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -347,12 +355,18 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     AL(c->g_n, 3 * (size_t)ng);
     AL(c->g_meta, ng);
     AL(c->lev_ptr, ng + c->B + 1);
+    {
+      size_t cap = (size_t)max_smem_optin(), need = 0;
+      for (int b = 0; b < c->B; ++b) {
+        size_t q = levels_smem(c->hG[b].dim, c->hG[b].n_ghost);
+        if (q <= cap) need = std::max(need, q);
+      }
+      c->levels_smem = need;
+    }
     AL(c->wtab, 16 * (size_t)ng);
     AL(c->ftab, 33 * (size_t)ng);
     AL(c->gsrc_cnt, ng);
     AL(c->gsrc_ptr, ng + 1);
-    AL(c->own_flag, 8 * (size_t)ng);
-    AL(c->own_ptr, 8 * (size_t)ng + 1);
     AL(c->sv, 64 * (size_t)ng);
     {
       ebr_status st = balloc(c, &c->lam, 8 * 8 * (size_t)ng);   // [F <= 8][ng] doubles
@@ -368,7 +382,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   prof_end(c, s);
   prof_begin(c, s, "levels");
   launch_levels(c->dG, c->B, c->dep, ng, c->level, c->order_pos, c->lev_ptr, c->d_nlev,
-                c->d_status, s);
+                c->levels_smem, c->d_status, s);
   prof_end(c, s);
   c->launches += 3;
   CKL();
@@ -426,46 +440,6 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
               c->gsrc_ptr, c->gsrc, 1, s);
   prof_end(c, s);
-  // fluid-target sources
-  prof_begin(c, s, "fsrc");
-  launch_fsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax, nullptr,
-              c->own_flag, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s);
-  prof_end(c, s);
-  prof_begin(c, s, "scan");
-  launch_scan(c->own_flag, c->own_ptr, 8 * ng, c->scan_tmp, s);
-  prof_end(c, s);
-  c->launches += 5;
-  CKL();
-  if (planning) {
-    CK(cudaMemcpyAsync(&c->nft, c->own_ptr + 8 * (size_t)ng, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    AL(c->ft_cell, c->nft);
-    AL(c->ft_geo, c->nft);
-    AL(c->ft_cnt, c->nft);
-    AL(c->ft_ptr, c->nft + 1);
-  }
-  prof_begin(c, s, "fsrc");
-  launch_fsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
-              c->own_ptr, c->own_flag, c->ft_cell, c->ft_geo, c->ft_cnt, nullptr, nullptr, 1, s);
-  prof_end(c, s);
-  prof_begin(c, s, "scan");
-  launch_scan(c->ft_cnt, c->ft_ptr, c->nft, c->scan_tmp, s);
-  prof_end(c, s);
-  c->launches += 4;
-  CKL();
-  if (planning) {
-    CK(cudaMemcpyAsync(&c->n_fsrc, c->ft_ptr + c->nft, sizeof(int), cudaMemcpyDeviceToHost, s));
-    std::vector<int> fg(c->nft);
-    CK(cudaMemcpyAsync(fg.data(), c->ft_geo, sizeof(int) * c->nft, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    c->h_nft_geo.assign(c->B, 0);
-    for (int t = 0; t < c->nft; ++t) c->h_nft_geo[fg[t]]++;
-    AL(c->ft_src, c->n_fsrc);
-  }
-  prof_begin(c, s, "fsrc");
-  launch_fsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
-              c->own_ptr, c->own_flag, c->ft_cell, c->ft_geo, c->ft_cnt, c->ft_ptr, c->ft_src, 2, s);
-  prof_end(c, s);
   c->launches += 1;
   CKL();
   if (planning) {
@@ -493,12 +467,6 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   return EBR_OK;
 }
 
-int max_smem_optin() {
-  int dev = 0, v = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return v;
-}
 
 // Chain plan for (kind of pass, dtype, F): geometries whose state fits in one
 // CTA's shared memory, largest first; the rest use level launches.
@@ -681,7 +649,6 @@ ebr_status ebr_counts(const void* ctx, ebr_geom_counts* h_counts) {
     h_counts[b].n_ghosts = g.n_ghost;
     h_counts[b].n_levels = c->levelled ? g.n_levels : 0;
     h_counts[b].reserved = 0;
-    h_counts[b].n_fluid_targets = c->levelled && (int)c->h_nft_geo.size() == c->B ? c->h_nft_geo[b] : 0;
   }
   return EBR_OK;
 }
@@ -781,7 +748,7 @@ ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
       int p0 = c->h_lev_ptr[g.lev_off + lv - 1], p1 = c->h_lev_ptr[g.lev_off + lv];
       prof_begin(c, s, "fill_level");
       launch_fill_level(dtype, g.dim, n_fields, d_fields, kinds, d_bc, g.cell_off, p0, p1, c->g_cell,
-                        c->g_meta, c->wtab, c->ng, g.n[0], g.n[1], s);
+                        c->g_meta, c->wtab, c->ng, g.n[0], g.n[1], c->d_status, s);
       prof_end(c, s);
       c->launches += 1;
     }
@@ -871,14 +838,15 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
     }
   }
   prof_begin(c, s, "adj_fluid");
-  launch_adj_fluid(dtype, dim, n_fields, kinds, c->nft, c->ft_cell, c->ft_geo, c->ft_ptr, c->ft_src,
-                   c->dG, c->g_meta, c->wtab, c->sv, c->ng, c->lam, d_grad_fields, accumulate, s);
+  launch_adj_fluid(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->g_meta, c->tags,
+                   c->pos_of_cell, c->rmax, c->wtab, c->sv, c->lam, d_grad_fields, accumulate, s);
   prof_end(c, s);
+  c->launches += 1;
   prof_begin(c, s, "adj_bc");
   launch_adj_bc(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->wtab, c->lam, d_grad_bc,
                 d_grad_fields, accumulate, s);
   prof_end(c, s);
-  c->launches += 2;
+  c->launches += 1;
   CKL();
   return EBR_OK;
 }
@@ -922,6 +890,20 @@ int32_t ebr_profile_read(void* ctx, int32_t max_entries, char* h_names, double* 
   c->recs.clear();
   c->pool_used = 0;
   return n;
+}
+
+ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !h_out || n < 1) return EBR_EINVAL;
+  if (!c->planned) return fail(c, EBR_EINVAL, "ebr_diagnostics: call ebr_plan first");
+  int st[2] = {0, 0};
+  cudaStream_t s = S(stream);
+  CK(cudaMemcpyAsync(st, c->d_stats, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (n > 0) h_out[0] = st[0];
+  if (n > 1) h_out[1] = c->rmax;
+  if (n > 2) h_out[2] = c->launches;
+  return EBR_OK;
 }
 
 ebr_status ebr_sync_status(void* ctx, ebr_stream stream) {

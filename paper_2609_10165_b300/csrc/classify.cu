@@ -89,23 +89,28 @@ __device__ void estimate_row(const Geom& g, int j, int k, int& state, int& ia, i
     float tol = 1e-4f * c;
     cx = g.centre[0] + (double)xm;
     if (fm < -tol) return;
-    if (fm < tol) { state = ROW_TANGENT; iv = (int)lrint(frac_cell(g, 0, cx)); return; }
-    float a = X0, b = xm;
+    // a grazing row whose maximum depth rounds to <= 0 holds at most a few
+    // cells around the maximum; any positive depth gets bracketed roots
+    if (fm <= 0.0f) { state = ROW_TANGENT; iv = (int)lrint(frac_cell(g, 0, cx)); return; }
+    // roots of the depth on either side of the maximum; where the depth is
+    // still >= 0 at the segment end the run ends there (x' = 0 or x' = c)
+    float xa_f = X0, xb_f = X1;
     if (airfoil_f32(t, c, r00, r01, bx, byy, X0) < 0.0f) {
+      float a = X0, b = xm;
       for (int it = 0; it < 40; ++it) {
         float m = 0.5f * (a + b);
         if (airfoil_f32(t, c, r00, r01, bx, byy, m) < 0.0f) a = m; else b = m;
       }
+      xa_f = 0.5f * (a + b);
     }
-    float xa_f = 0.5f * (a + b);
-    a = xm; b = X1;
     if (airfoil_f32(t, c, r00, r01, bx, byy, X1) < 0.0f) {
+      float a = xm, b = X1;
       for (int it = 0; it < 40; ++it) {
         float m = 0.5f * (a + b);
         if (airfoil_f32(t, c, r00, r01, bx, byy, m) >= 0.0f) a = m; else b = m;
       }
+      xb_f = 0.5f * (a + b);
     }
-    float xb_f = 0.5f * (a + b);
     xa = g.centre[0] + (double)xa_f;
     xb = g.centre[0] + (double)xb_f;
   }
@@ -159,17 +164,35 @@ __device__ void exact_run(const Geom& g, int j, int k, int& s, int& t, int* stat
     if ((run & (run + 1)) != 0) ok = false;     // not contiguous
   }
   if (!ok) {
-    // robust fallback: sweep the whole row with the exact predicate
     atomicAdd(&stats[0], 1);
-    s = 0; t = -1;
-    bool any = false;
-    for (int i = 0; i < n; ++i) {
-      if (solid_cell(g, i, j, k)) {
-        if (!any) { s = i; any = true; }
-        t = i;
+    // fallback 1: a solid seed inside the estimated run; the run is an
+    // interval (convex body), so bisect the exact predicate for both ends
+    int seed = state == ROW_RUN ? (ia + ib) / 2 : iv;
+    if (seed >= 0 && seed < n && solid_cell(g, seed, j, k)) {
+      int lo = -1, hi = seed;            // pred(lo) false (virtual), pred(hi) true
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (solid_cell(g, mid, j, k)) hi = mid; else lo = mid;
       }
+      s = hi;
+      lo = seed; hi = n;                 // pred(lo) true, pred(hi) false (virtual)
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (solid_cell(g, mid, j, k)) lo = mid; else hi = mid;
+      }
+      t = lo;
+    } else {
+      // fallback 2: sweep the whole row with the exact predicate
+      s = 0; t = -1;
+      bool any = false;
+      for (int i = 0; i < n; ++i) {
+        if (solid_cell(g, i, j, k)) {
+          if (!any) { s = i; any = true; }
+          t = i;
+        }
+      }
+      if (!any) { s = 0; t = -1; }
     }
-    if (!any) { s = 0; t = -1; }
   }
 }
 
@@ -218,18 +241,20 @@ __global__ void __launch_bounds__(256) k_rows(const Geom* __restrict__ G, const 
         long long i = a1 + lane - rst;
         tags[a1 + lane] = (int8_t)(i >= rs && i <= rt);
       }
-      // aligned middle: 16 cells per lane per step
+      // aligned middle: 16 cells per lane per step.  Bytes [lo, hi) of the
+      // chunk lie inside the run; each 32-bit word is a difference of two
+      // prefix masks of 0x01 bytes.
       for (long long c = a0 + 16LL * lane; c < a1; c += 16LL * 32) {
+        int i0 = (int)(c - rst);
+        int lo = min(max(rs - i0, 0), 16);
+        int hi = min(max(rt + 1 - i0, 0), 16);
         uint32_t w[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          uint32_t v = 0;
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            long long i = c + 4 * q + m - rst;
-            v |= (uint32_t)(i >= rs && i <= rt) << (8 * m);
-          }
-          w[q] = v;
+          int l = min(max(lo - 4 * q, 0), 4), h = min(max(hi - 4 * q, 0), 4);
+          uint32_t ph = h ? (0x01010101u >> (8 * (4 - h))) : 0u;
+          uint32_t pl = l ? (0x01010101u >> (8 * (4 - l))) : 0u;
+          w[q] = h > l ? (ph & ~pl) : 0u;
         }
         *reinterpret_cast<uint4*>(tags + c) = make_uint4(w[0], w[1], w[2], w[3]);
       }
@@ -345,32 +370,46 @@ __global__ void k_place(const Geom* __restrict__ G, int n_iface, const int* __re
                         const int* __restrict__ iface_geo, const int8_t* __restrict__ iface_solid,
                         int placement, int8_t* __restrict__ tags, double* __restrict__ psi_out,
                         double* __restrict__ n_out, int* status) {
+  (void)psi_out;
+  (void)n_out;
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_iface) return;
   const Geom& g = G[iface_geo[m]];
   int cell = iface_cell[m];
   bool solid = iface_solid[m] != 0;
-  int i, j, k;
-  cell_ijk(g, cell, i, j, k);
-  double psi = 0.0, nv[3] = {0.0, 0.0, 0.0};
   int8_t tag = solid ? 1 : 0;
-  bool need = placement == HGC || solid;
-  if (need) {
+  if (placement != HGC) {
+    tag = solid ? 2 : 0;   // solid interface cell = solid cell with a fluid face neighbour
+  } else {
+    int i, j, k;
+    cell_ijk(g, cell, i, j, k);
     double x = centre_of(g, 0, i), y = centre_of(g, 1, j);
     double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
-    if (!closest_point(g, x, y, z, solid, psi, nv)) { set_status(status, S_EINVAL); return; }
-    if (placement == HGC) {
-      double half = 0.5 * delta_n(g, nv);
-      if (solid && psi <= half) tag = 2;
-      if (!solid && -psi < half) tag = -2;
-    } else {
-      tag = 2;   // solid interface cell = solid cell with a fluid face neighbour
+    // Eq. HGC_criterion decided in float where the float psi and dn/2 are
+    // clearly apart; the few cells within the safety margin use double
+    float n32[3];
+    float psi32 = closest_point_f32(g, x, y, z, solid, n32);
+    float s32 = 0.0f, hmin = 3.4e38f, ext = 1.0f;
+    for (int a = 0; a < g.dim; ++a) {
+      float q = n32[a] / (float)g.h[a];
+      s32 += q * q;
+      hmin = fminf(hmin, (float)g.h[a]);
+      ext = fmaxf(ext, fmaxf(fabsf((float)g.lo[a]), fabsf((float)(g.lo[a] + g.n[a] * g.h[a]))));
     }
+    float half32 = 0.5f / sqrtf(s32);
+    float mrg = 1e-4f * hmin + 4e-6f * ext;
+    float gap = fabsf(psi32) - half32;
+    bool cand;
+    if (fabsf(gap) > mrg) {
+      cand = gap <= 0.0f;
+    } else {
+      double psi, nv[3];
+      if (!closest_point(g, x, y, z, solid, psi, nv)) { set_status(status, S_EINVAL); return; }
+      double half = 0.5 * delta_n(g, nv);
+      cand = solid ? (psi <= half) : (-psi < half);
+    }
+    if (cand) tag = solid ? 2 : -2;
   }
-  psi_out[m] = psi;
-  n_out[m] = nv[0];
-  n_out[n_iface + m] = nv[1];
-  n_out[2 * (size_t)n_iface + m] = nv[2];
   tags[g.cell_off + cell] = tag;
 }
 
@@ -431,13 +470,11 @@ void launch_ghost_flags(const Geom* G, int n_iface, const int* iface_cell, const
   k_ghost_flags<<<(n_iface + 255) / 256, 256, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, flags);
 }
 
+// compaction of the ghosts (index order): cell, geometry, fluid-side flag
 __global__ void k_ghost_write(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
                               const int* __restrict__ iface_geo, const int8_t* __restrict__ tags,
-                              const double* __restrict__ iface_psi, const double* __restrict__ iface_n,
-                              const int* __restrict__ gpos, int placement, int cap,
-                              int* __restrict__ gs_cell, int* __restrict__ gs_geo,
-                              double* __restrict__ gs_psi, double* __restrict__ gs_n,
-                              uint32_t* __restrict__ gs_meta, int* rmax, int* status) {
+                              const int* __restrict__ gpos, int cap, int* __restrict__ gs_cell,
+                              int* __restrict__ gs_geo, uint32_t* __restrict__ gs_meta, int* status) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_iface) return;
   int b = iface_geo[m];
@@ -447,9 +484,30 @@ __global__ void k_ghost_write(const Geom* __restrict__ G, int n_iface, const int
   if (t != 2 && t != -2) return;
   int s = gpos[m];
   if (s >= cap) { set_status(status, S_ESHAPE); return; }
-  double psi = iface_psi[m];
-  double nv[3] = {iface_n[m], iface_n[n_iface + m], iface_n[2 * (size_t)n_iface + m]};
-  uint32_t meta = 0;
+  gs_cell[s] = cell;
+  gs_geo[s] = b;
+  gs_meta[s] = t == -2 ? (1u << 22) : 0u;
+}
+
+// psi, S and n in double for the compacted ghosts only (Eq. signed_distance),
+// one ghost per thread so that no lane idles through the FP64 work; sign
+// bits e and stencil multipliers r (Eq. stencil_anisotropic for CGC_ES)
+__global__ void k_ghost_geom(const Geom* __restrict__ G, int ng, int placement,
+                             const int* __restrict__ gs_cell, const int* __restrict__ gs_geo,
+                             double* __restrict__ gs_psi, double* __restrict__ gs_n,
+                             uint32_t* __restrict__ gs_meta, int* rmax, int* status) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ng) return;
+  const Geom& g = G[gs_geo[s]];
+  int cell = gs_cell[s];
+  uint32_t meta = gs_meta[s] & (1u << 22);
+  bool solid = meta == 0;
+  double psi, nv[3];
+  int i, j, k;
+  cell_ijk(g, cell, i, j, k);
+  double x = centre_of(g, 0, i), y = centre_of(g, 1, j);
+  double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
+  if (!closest_point(g, x, y, z, solid, psi, nv)) { set_status(status, S_EINVAL); return; }
   int rloc = 1;
   for (int a = 0; a < g.dim; ++a) {
     if (nv[a] < 0.0) meta |= 1u << a;
@@ -463,15 +521,12 @@ __global__ void k_ghost_write(const Geom* __restrict__ G, int n_iface, const int
     rloc = max(rloc, r);
     meta |= (uint32_t)r << (3 + 4 * a);
   }
-  if (t == -2) meta |= 1u << 22;
-  gs_cell[s] = cell;
-  gs_geo[s] = b;
   gs_psi[s] = psi;
   gs_n[s] = nv[0];
-  gs_n[cap + s] = nv[1];
-  gs_n[2 * (size_t)cap + s] = nv[2];
+  gs_n[ng + s] = nv[1];
+  gs_n[2 * (size_t)ng + s] = nv[2];
   gs_meta[s] = meta;
-  atomicMax(rmax, rloc);
+  if (rloc > 1) atomicMax(rmax, rloc);
 }
 
 void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
@@ -479,11 +534,14 @@ void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const
                         const int* gpos, int placement, int ng_cap, int* gs_cell, int* gs_geo,
                         double* gs_psi, double* gs_n, uint32_t* gs_meta, int* rmax,
                         int* status, cudaStream_t s) {
+  (void)iface_psi;
+  (void)iface_n;
   if (n_iface <= 0) return;
-  k_ghost_write<<<(n_iface + 127) / 128, 128, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags,
-                                                      iface_psi, iface_n, gpos, placement, ng_cap,
-                                                      gs_cell, gs_geo, gs_psi, gs_n, gs_meta, rmax,
-                                                      status);
+  k_ghost_write<<<(n_iface + 255) / 256, 256, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, gpos,
+                                                      ng_cap, gs_cell, gs_geo, gs_meta, status);
+  if (ng_cap <= 0) return;
+  k_ghost_geom<<<(ng_cap + 127) / 128, 128, 0, s>>>(G, ng_cap, placement, gs_cell, gs_geo, gs_psi,
+                                                    gs_n, gs_meta, rmax, status);
 }
 
 }  // namespace ebr

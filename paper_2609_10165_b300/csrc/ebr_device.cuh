@@ -137,23 +137,42 @@ __device__ inline bool solid_cell(const Geom& g, int i, int j, int k) {
 // X = a^2 p / (a^2 + t), Y = b^2 q / (b^2 + t) where t solves
 // F(t) = (a p / (a^2 + t))^2 + (b q / (b^2 + t))^2 - 1 = 0.  F is decreasing and
 // convex on t > -min(a^2, b^2), so safeguarded Newton from t = 0 converges.
+// The iteration runs in float first; a few double steps then polish t to
+// the rounding level (the FP64 pipe is the scarce resource).
 __device__ inline void ellipse_closest(double a, double b, double p, double q,
                                        double& dist, double& nx, double& ny) {
   double a2 = a * a, b2 = b * b;
   double tmin = -fmin(a2, b2);
-  double t = 0.0;
-  for (int it = 0; it < 200; ++it) {
-    double ua = a2 + t, ub = b2 + t;
-    double fx = a * p / ua, fy = b * q / ub;
+  float af = (float)a, bf = (float)b, pf = (float)p, qf = (float)q;
+  float a2f = af * af, b2f = bf * bf, tminf = (float)tmin;
+  float tf = 0.0f;
+  for (int it = 0; it < 16; ++it) {
+    float rua = 1.0f / (a2f + tf), rub = 1.0f / (b2f + tf);
+    float fx = af * pf * rua, fy = bf * qf * rub;
+    float F = fx * fx + fy * fy - 1.0f;
+    float dF = -2.0f * (fx * fx * rua + fy * fy * rub);
+    if (F == 0.0f || dF == 0.0f) break;
+    float tn = tf - F / dF;
+    if (!(tn > tminf)) tn = 0.5f * (tf + tminf);
+    float dt = fabsf(tn - tf);
+    tf = tn;
+    if (dt <= 1e-5f * fabsf(tf)) break;
+  }
+  double t = (double)tf;
+  if (!(t > tmin)) t = 0.0;
+  for (int it = 0; it < 12; ++it) {
+    double rua = 1.0 / (a2 + t), rub = 1.0 / (b2 + t);
+    double fx = a * p * rua, fy = b * q * rub;
     double F = fx * fx + fy * fy - 1.0;
-    double dF = -2.0 * (fx * fx / ua + fy * fy / ub);
+    double dF = -2.0 * (fx * fx * rua + fy * fy * rub);
     if (F == 0.0 || dF == 0.0) break;
     double tn = t - F / dF;
     if (!(tn > tmin)) tn = 0.5 * (t + tmin);
-    if (tn == t) break;
     double dt = fabs(tn - t);
     t = tn;
-    if (dt <= 1e-17 * fmax(fabs(t), 1e-300)) break;
+    // quadratic convergence: once a step is 1e-12 relative, the error left
+    // after it is far below the rounding level
+    if (dt <= 1e-12 * fabs(t)) break;
   }
   double ua = a2 + t, ub = b2 + t;
   // G - S = (p t / ua, q t / ub): no cancellation
@@ -180,15 +199,28 @@ __device__ inline void airfoil_u(double t, double c, double u, double& x, double
   ddy = k * (2.0 * a1 + 12.0 * a2 * u2 + 30.0 * a3 * u4 + 56.0 * a4 * u6);
 }
 
+__device__ inline void airfoil_u32(float t, float c, float u, float& x, float& y, float& dx,
+                                   float& dy, float& ddx, float& ddy) {
+  const float a0 = 0.2969f, a1 = -0.1260f, a2 = -0.3516f, a3 = 0.2843f, a4 = -0.1015f;
+  float k = 5.0f * t * c;
+  float u2 = u * u, u3 = u2 * u, u4 = u2 * u2, u5 = u4 * u, u6 = u4 * u2, u7 = u6 * u, u8 = u4 * u4;
+  x = c * u2;
+  y = k * (a0 * u + a1 * u2 + a2 * u4 + a3 * u6 + a4 * u8);
+  dx = 2.0f * c * u;
+  dy = k * (a0 + 2.0f * a1 * u + 4.0f * a2 * u3 + 6.0f * a3 * u5 + 8.0f * a4 * u7);
+  ddx = 2.0f * c;
+  ddy = k * (2.0f * a1 + 12.0f * a2 * u2 + 30.0f * a3 * u4 + 56.0f * a4 * u6);
+}
+
 // Closest point on the airfoil to the body-frame point (px, py): the upper
-// surface by coarse float sampling in u then safeguarded Newton on
-// g(u) = (P(u) - q) . P'(u) in double; the base x = c; the lower surface by
-// symmetry (|py|, exact ties -> upper surface).  At the trailing-edge corner
-// a fluid point's normal is (G - S) / |G - S|.
+// surface by coarse float sampling in u, float Newton on
+// g(u) = (P(u) - q) . P'(u) inside the bracket, and a double polish of u; the
+// base x = c; the lower surface by symmetry (|py|, exact ties -> upper
+// surface).  At the trailing-edge corner a fluid point's normal is
+// (G - S) / |G - S|.
 __device__ inline void airfoil_closest(double t, double c, double px, double py, bool inside,
                                        double& dist, double& nx, double& ny) {
   double qx = px, qy = fabs(py);
-  // coarse sampling (float)
   const int NS = 64;
   float fqx = (float)qx, fqy = (float)qy, fc = (float)c, ft = (float)t;
   int best = 0;
@@ -217,15 +249,41 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
   } else if (ghi <= 0.0) {
     u = hi;                    // distance decreases up to hi (hi == 1 here)
   } else {
-    u = 0.5 * (lo + hi);
-    for (int it = 0; it < 100; ++it) {
+    // float Newton inside the bracket
+    float flo = (float)lo, fhi = (float)hi, uf = 0.5f * (flo + fhi);
+    for (int it = 0; it < 16; ++it) {
+      float x, y, dx, dy, ddx, ddy;
+      airfoil_u32(ft, fc, uf, x, y, dx, dy, ddx, ddy);
+      float gv = (x - fqx) * dx + (y - fqy) * dy;
+      float dg = dx * dx + dy * dy + (x - fqx) * ddx + (y - fqy) * ddy;
+      if (gv == 0.0f) break;
+      // converged: accept the (tiny) Newton step before any safeguard
+      if (dg > 0.0f && fabsf(gv / dg) <= 1e-5f * fmaxf(uf, 1e-3f)) {
+        uf = fminf(fmaxf(uf - gv / dg, flo), fhi);
+        break;
+      }
+      if (gv < 0.0f) flo = uf; else fhi = uf;
+      float un = uf - gv / dg;
+      if (!(un > flo && un < fhi) || dg <= 0.0f) un = 0.5f * (flo + fhi);
+      uf = un;
+    }
+    u = fmin(fmax((double)uf, lo), hi);
+    // double polish: safeguarded Newton inside [lo, hi]; a step of 1e-12
+    // relative leaves an error below the rounding level (quadratic convergence)
+    for (int it = 0; it < 40; ++it) {
       double gv, dg;
       g(u, gv, dg);
       if (gv == 0.0) break;
+      // converged: a Newton step of 1e-12 (relative) leaves an error below the
+      // rounding level; accept it before the safeguard, which would otherwise
+      // bisect once the step rounds onto the bracket end
+      if (dg > 0.0 && fabs(gv / dg) <= 1e-12 * fmax(u, 1e-3)) {
+        u = fmin(fmax(u - gv / dg, lo), hi);
+        break;
+      }
       if (gv < 0.0) lo = u; else hi = u;
       double un = u - gv / dg;
       if (!(un > lo && un < hi) || dg <= 0.0) un = 0.5 * (lo + hi);
-      if (un == u || hi - lo <= 1e-17) { u = un; break; }
       u = un;
     }
   }
@@ -255,6 +313,120 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
   }
   dist = sqrt((qx - sx) * (qx - sx) + (qy - sy) * (qy - sy));
   if (py < 0.0) ny = -ny;
+}
+
+// ---------------------------------------------------------------------------
+// float closest point, used only to decide HGC candidacy away from the
+// thresholds (a cell whose float decision is within a safety margin of a
+// threshold is decided with the double closest point instead)
+// ---------------------------------------------------------------------------
+__device__ inline float closest_point_f32(const Geom& g, double x, double y, double z, bool solid,
+                                          float n[3]) {
+  n[0] = n[1] = n[2] = 0.0f;
+  float dist = 0.0f;
+  switch (g.kind) {
+    case CIRCLE:
+    case SPHERE: {
+      float dx = (float)(x - g.centre[0]), dy = (float)(y - g.centre[1]);
+      float dz = g.kind == SPHERE ? (float)(z - g.centre[2]) : 0.0f;
+      float rho = sqrtf(dx * dx + dy * dy + dz * dz);
+      float r = 1.0f / fmaxf(rho, 1e-30f);
+      dist = fabsf((float)g.radii[0] - rho);
+      n[0] = dx * r; n[1] = dy * r; n[2] = dz * r;
+      break;
+    }
+    case ELLIPSE: {
+      double pd, qd;
+      to_body2(g, x, y, pd, qd);
+      float a = (float)g.radii[0], b = (float)g.radii[1], p = (float)pd, q = (float)qd;
+      float a2 = a * a, b2 = b * b, tmin = -fminf(a2, b2), t = 0.0f;
+      for (int it = 0; it < 16; ++it) {
+        float rua = 1.0f / (a2 + t), rub = 1.0f / (b2 + t);
+        float fx = a * p * rua, fy = b * q * rub;
+        float F = fx * fx + fy * fy - 1.0f;
+        float dF = -2.0f * (fx * fx * rua + fy * fy * rub);
+        if (F == 0.0f || dF == 0.0f) break;
+        float tn = t - F / dF;
+        if (!(tn > tmin)) tn = 0.5f * (t + tmin);
+        float dt = fabsf(tn - t);
+        t = tn;
+        if (dt <= 1e-5f * fabsf(t)) break;
+      }
+      float rua = 1.0f / (a2 + t), rub = 1.0f / (b2 + t);
+      float ex = p * t * rua, ey = q * t * rub;
+      dist = sqrtf(ex * ex + ey * ey);
+      float mx = p * rua, my = q * rub;           // (X / a^2, Y / b^2)
+      float mn = 1.0f / sqrtf(mx * mx + my * my);
+      float bx = mx * mn, by = my * mn;
+      n[0] = (float)g.rot[0] * bx + (float)g.rot[1] * by;
+      n[1] = (float)g.rot[3] * bx + (float)g.rot[4] * by;
+      break;
+    }
+    default: {  // AIRFOIL4
+      double pd, qd;
+      to_body2(g, x, y, pd, qd);
+      float c = (float)g.c, t = (float)g.t, qx = (float)pd, qy = fabsf((float)qd);
+      const int NS = 64;
+      int best = 0;
+      float bd = 3.4e38f;
+      for (int s = 0; s <= NS; ++s) {
+        float u = (float)s / NS, u2 = u * u, xx = c * u2;
+        float yy = 5.0f * t * c * (0.2969f * u + u2 * (-0.1260f + u2 * (-0.3516f + u2 * (0.2843f + u2 * -0.1015f))));
+        float d = (xx - qx) * (xx - qx) + (yy - qy) * (yy - qy);
+        if (d < bd) { bd = d; best = s; }
+      }
+      float lo = fmaxf(0.0f, (float)(best - 1) / NS), hi = fminf(1.0f, (float)(best + 1) / NS);
+      float xx, yy, dx, dy, ddx, ddy;
+      airfoil_u32(t, c, lo, xx, yy, dx, dy, ddx, ddy);
+      float glo = (xx - qx) * dx + (yy - qy) * dy;
+      airfoil_u32(t, c, hi, xx, yy, dx, dy, ddx, ddy);
+      float ghi = (xx - qx) * dx + (yy - qy) * dy;
+      float u;
+      if (glo >= 0.0f) u = lo;
+      else if (ghi <= 0.0f) u = hi;
+      else {
+        u = 0.5f * (lo + hi);
+        for (int it = 0; it < 16; ++it) {
+          airfoil_u32(t, c, u, xx, yy, dx, dy, ddx, ddy);
+          float gv = (xx - qx) * dx + (yy - qy) * dy;
+          float dg = dx * dx + dy * dy + (xx - qx) * ddx + (yy - qy) * ddy;
+          if (gv == 0.0f) break;
+          if (dg > 0.0f && fabsf(gv / dg) <= 1e-5f * fmaxf(u, 1e-3f)) {
+            u = fminf(fmaxf(u - gv / dg, lo), hi);
+            break;
+          }
+          if (gv < 0.0f) lo = u; else hi = u;
+          float un = u - gv / dg;
+          if (!(un > lo && un < hi) || dg <= 0.0f) un = 0.5f * (lo + hi);
+          u = un;
+        }
+      }
+      airfoil_u32(t, c, u, xx, yy, dx, dy, ddx, ddy);
+      float d2u = (xx - qx) * (xx - qx) + (yy - qy) * (yy - qy);
+      float yte, t1, t2, t3, t4, t5;
+      airfoil_u32(t, c, 1.0f, t1, yte, t2, t3, t4, t5);
+      float byy = fminf(qy, yte);
+      float d2b = (qx - c) * (qx - c) + (qy - byy) * (qy - byy);
+      float bx, by;
+      if (d2b < d2u) {
+        dist = sqrtf(d2b);
+        bx = 1.0f; by = 0.0f;
+        if (!solid && qy > yte) {
+          float vx = qx - c, vy = qy - yte, vn = 1.0f / fmaxf(sqrtf(vx * vx + vy * vy), 1e-30f);
+          bx = vx * vn; by = vy * vn;
+        }
+      } else {
+        dist = sqrtf(d2u);
+        float fn = 1.0f / sqrtf(dx * dx + dy * dy);
+        bx = -dy * fn; by = dx * fn;
+      }
+      if (qd < 0.0) by = -by;
+      n[0] = (float)g.rot[0] * bx + (float)g.rot[1] * by;
+      n[1] = (float)g.rot[3] * bx + (float)g.rot[4] * by;
+      break;
+    }
+  }
+  return solid ? dist : -dist;
 }
 
 // psi (signed by the solid flag) and world-frame unit normal for a cell centre.

@@ -47,8 +47,9 @@ void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, cons
 void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, uint32_t* gs_meta,
                  const double* gs_n, const int8_t* tags, const int* pos_of_cell, int* dep,
                  int* status, cudaStream_t s);
+size_t levels_smem(int dim, int n_ghost);
 void launch_levels(const Geom* G, int B, const int* dep, int ng_total, int* level, int* order_pos,
-                   int* lev_ptr, int* n_levels, int* status, cudaStream_t s);
+                   int* lev_ptr, int* n_levels, size_t smem, int* status, cudaStream_t s);
 void launch_reorder(int ng, const int* order_pos, const int* gs_cell, const int* gs_geo,
                     const double* gs_psi, const double* gs_n, const uint32_t* gs_meta,
                     const int* dep, const int* level, int* g_cell, int* g_geo, double* g_psi,
@@ -59,16 +60,13 @@ void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, c
 void launch_gsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
                  const int8_t* tags, const int* pos_of_cell, int rmax, const int* ptr,
                  int* cnt_or_src, int write, cudaStream_t s);
-void launch_fsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
-                 const int8_t* tags, const int* pos_of_cell, int rmax, const int* owner_ptr,
-                 int* owner_flag, int* ft_cell, int* ft_geo, int* ft_cnt, const int* ft_ptr,
-                 int* ft_src, int stage, cudaStream_t s);
+
 
 // ---- fill.cu
 void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
                        const void* const* bc, long long cell_off, int p0, int p1, const int* g_cell,
                        const uint32_t* g_meta, const double* wtab, int ng_total, int nx, int ny,
-                       cudaStream_t s);
+                       int* status, cudaStream_t s);
 size_t fill_chain_smem(int dtype, int dim, int F, int n_ghost);
 void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
                        const void* const* bc, const Geom* G, const int* geo_list, int n_list,
@@ -95,9 +93,9 @@ void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom*
                       const int* geo_list, int n_list, const int* lev_ptr, const int* gsrc_ptr,
                       const int* gsrc, const uint32_t* g_meta, const double* wtab, const double* sv,
                       int ng_total, void* lam, size_t smem, cudaStream_t s);
-void launch_adj_fluid(int dtype, int dim, int F, const int* bc_kind, int nft, const int* ft_cell,
-                      const int* ft_geo, const int* ft_ptr, const int* ft_src, const Geom* G,
-                      const uint32_t* g_meta, const double* wtab, const double* sv, int ng_total,
+void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
+                      const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
+                      const int* pos_of_cell, int rmax, const double* wtab, const double* sv,
                       const void* lam, void* const* grad, int accumulate, cudaStream_t s);
 void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                    const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,

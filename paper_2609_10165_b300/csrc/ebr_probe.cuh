@@ -1,0 +1,67 @@
+// Cell-index helpers and the fixed-order probe of the (ghost, member) pairs
+// that read a given cell (transposed stencil incidences), shared by the level
+// builder and the adjoint.
+#pragma once
+
+#include "ebr_device.cuh"
+
+namespace ebr {
+
+__device__ inline void cell_ijk3(const Geom& g, int cell, int ijk[3]) {
+  ijk[0] = cell % g.n[0];
+  int r = cell / g.n[0];
+  ijk[1] = r % g.n[1];
+  ijk[2] = r / g.n[1];
+}
+
+__device__ inline int cell_lin(const Geom& g, const int ijk[3]) {
+  return ijk[0] + g.n[0] * (ijk[1] + g.n[1] * ijk[2]);
+}
+
+__device__ inline bool in_grid(const Geom& g, const int ijk[3]) {
+  for (int a = 0; a < g.dim; ++a)
+    if (ijk[a] < 0 || ijk[a] >= g.n[a]) return false;
+  return true;
+}
+
+// member k of a ghost at ijk with meta m
+__device__ inline void member_ijk(const Geom& g, const int ijk[3], uint32_t m, int k, int out[3]) {
+  int o[3];
+  stencil_off(g.dim, k, o);
+  for (int a = 0; a < 3; ++a) out[a] = ijk[a] + (a < g.dim ? o[a] * meta_r(m, a) * meta_e(m, a) : 0);
+}
+
+// ---------------------------------------------------------------------------
+// transposed incidences: for a target cell T, the (ghost H, slot) pairs with
+// member_slot(H) = T, found by probing H = T - delta over the box |delta_a| <= R
+// in a fixed order.  Slot 0 (H = T itself) is listed first for ghost targets.
+// ---------------------------------------------------------------------------
+template <typename Visit>
+__device__ inline void probe_sources(const Geom& g, const int tijk[3], const int8_t* tg,
+                                     const int* pcell, const uint32_t* g_meta, int R, Visit visit) {
+  const int K = stencil_k(g.dim);
+  int Rz = g.dim == 3 ? R : 0;
+  for (int dz = -Rz; dz <= Rz; ++dz)
+    for (int dy = -R; dy <= R; ++dy)
+      for (int dx = -R; dx <= R; ++dx) {
+        if (dx == 0 && dy == 0 && dz == 0) continue;
+        int hijk[3] = {tijk[0] - dx, tijk[1] - dy, tijk[2] - dz};
+        if (!in_grid(g, hijk)) continue;
+        int hc = cell_lin(g, hijk);
+        int8_t t = tg[hc];
+        if (t != 2 && t != -2) continue;
+        int q = pcell[hc];
+        uint32_t m = g_meta[q];
+        int dd[3] = {dx, dy, dz};
+        for (int k = 0; k < K; ++k) {
+          int o[3];
+          stencil_off(g.dim, k, o);
+          bool hit = true;
+          for (int a = 0; a < g.dim; ++a)
+            if (o[a] * meta_r(m, a) * meta_e(m, a) != dd[a]) hit = false;
+          if (hit) { if (!visit(q, k + 1)) return; }
+        }
+      }
+}
+
+}  // namespace ebr

@@ -36,7 +36,7 @@ __device__ inline int member_cell(int dim, int cell, int nx, int ny, uint32_t m,
 template <typename T>
 __global__ void k_fill_level(FieldSet P, int F, int dim, long long cell_off, int p0, int p1,
                              const int* __restrict__ g_cell, const uint32_t* __restrict__ g_meta,
-                             const double* __restrict__ wtab, int ng, int nx, int ny) {
+                             const double* __restrict__ wtab, int ng, int nx, int ny, int* status) {
   int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= p1) return;
   const int K = stencil_k(dim);
@@ -53,13 +53,14 @@ __global__ void k_fill_level(FieldSet P, int F, int dim, long long cell_off, int
       acc += wload<T>(wtab, ng, kind, k, p) * fld[member_cell(dim, cell, nx, ny, m, k)];
     }
     fld[cell] = acc;
+    if (!isfinite((double)acc)) set_status(status, S_ENONFINITE);
   }
 }
 
 void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
                        const void* const* bc, long long cell_off, int p0, int p1, const int* g_cell,
                        const uint32_t* g_meta, const double* wtab, int ng_total, int nx, int ny,
-                       cudaStream_t s) {
+                       int* status, cudaStream_t s) {
   if (p1 <= p0) return;
   FieldSet P;
   for (int f = 0; f < 8; ++f) {
@@ -70,9 +71,9 @@ void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int
   int n = p1 - p0;
   int T = n < 128 ? 64 : 128;
   if (dtype == 0)
-    k_fill_level<float><<<(n + T - 1) / T, T, 0, s>>>(P, F, dim, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny);
+    k_fill_level<float><<<(n + T - 1) / T, T, 0, s>>>(P, F, dim, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
   else
-    k_fill_level<double><<<(n + T - 1) / T, T, 0, s>>>(P, F, dim, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny);
+    k_fill_level<double><<<(n + T - 1) / T, T, 0, s>>>(P, F, dim, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
 }
 
 constexpr int CH_T = 512;
@@ -80,8 +81,9 @@ constexpr int CH_T = 512;
 size_t fill_chain_smem(int dtype, int dim, int F, int n) {
   size_t sz = dtype == 0 ? 4 : 8;
   int K = stencil_k(dim);
-  // vals[F][n], weights of dependency members for both kinds [2][K][n], positions [K][n]
-  return (size_t)n * (F * sz + 2 * K * sz + K * sizeof(int)) + 64;
+  // vals[F][n], weights of dependency members for both kinds [2][K][n],
+  // positions [K][n], cells [n], level pointers [n + 1]
+  return (size_t)n * (F * sz + 2 * K * sz + K * sizeof(int) + sizeof(int)) + (size_t)(n + 1) * sizeof(int) + 64;
 }
 
 template <typename T>
@@ -91,7 +93,8 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
                                                      const uint32_t* __restrict__ g_meta,
                                                      const int* __restrict__ g_dep,
                                                      const int* __restrict__ lev_ptr,
-                                                     const double* __restrict__ wtab, int ng) {
+                                                     const double* __restrict__ wtab, int ng,
+                                                     int* status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom& g = G[geo_list[blockIdx.x]];
   const int n = g.n_ghost, g0 = g.ghost_off, dim = g.dim;
@@ -100,10 +103,15 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
   T* vals = reinterpret_cast<T*>(smem);                 // [F][n]
   T* wdep = vals + (size_t)F * n;                       // [2][K][n]
   int* dpos = reinterpret_cast<int*>(wdep + (size_t)2 * K * n);  // [K][n]
+  int* cellv = dpos + (size_t)K * n;                             // [n]
+  int* lps = cellv + n;                                          // [n_levels + 1]
+  const int* lp = lev_ptr + g.lev_off;
+  for (int q = threadIdx.x; q <= g.n_levels; q += CH_T) lps[q] = lp[q] - g0;
   // phase 1: boundary term + fluid members; dependency weights and positions
   for (int s = threadIdx.x; s < n; s += CH_T) {
     int p = g0 + s;
     int cell = g_cell[p];
+    cellv[s] = cell;
     uint32_t m = g_meta[p];
     uint32_t act = meta_active(m), dm = meta_depmask(m);
     for (int f = 0; f < F; ++f) {
@@ -125,12 +133,11 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
     }
   }
   __syncthreads();
-  // phase 2: the dependency chain, level by level
-  const int* lp = lev_ptr + g.lev_off;
+  // phase 2: the dependency chain, level by level, on shared memory only
   for (int lv = 1; lv <= g.n_levels; ++lv) {
-    int a = lp[lv - 1] - g0, b = lp[lv] - g0;
+    int a = lps[lv - 1], b = lps[lv];
     for (int s = a + threadIdx.x; s < b; s += CH_T) {
-      int cell = g_cell[g0 + s];
+      int cell = cellv[s];
       for (int f = 0; f < F; ++f) {
         int kind = P.kind[f];
         T v = vals[(size_t)f * n + s];
@@ -140,6 +147,7 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
         }
         vals[(size_t)f * n + s] = v;
         static_cast<T*>(P.f[f])[g.cell_off + cell] = v;
+        if (!isfinite((double)v)) set_status(status, S_ENONFINITE);
       }
     }
     __syncthreads();
@@ -152,7 +160,6 @@ void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int
                        const int* lev_ptr, const double* wtab, int ng_total, size_t smem,
                        int* status, cudaStream_t s) {
   (void)dim;
-  (void)status;
   if (n_list <= 0) return;
   FieldSet P;
   for (int f = 0; f < 8; ++f) {
@@ -166,14 +173,14 @@ void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int
       cudaFuncSetAttribute(k_fill_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       set_float = smem;
     }
-    k_fill_chain<float><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total);
+    k_fill_chain<float><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, status);
   } else {
     static size_t set_double = 0;
     if (smem > set_double) {
       cudaFuncSetAttribute(k_fill_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       set_double = smem;
     }
-    k_fill_chain<double><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total);
+    k_fill_chain<double><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, status);
   }
 }
 

@@ -1,32 +1,9 @@
 // Dependency DAG, topological levels and canonical order (Sec. 3.2); per-ghost
 // coefficient tables (Secs. 4-6); transposed incidence lists for the adjoint.
 #include "ebr_kernels.cuh"
+#include "ebr_probe.cuh"
 
 namespace ebr {
-
-__device__ inline void cell_ijk3(const Geom& g, int cell, int ijk[3]) {
-  ijk[0] = cell % g.n[0];
-  int r = cell / g.n[0];
-  ijk[1] = r % g.n[1];
-  ijk[2] = r / g.n[1];
-}
-
-__device__ inline int cell_lin(const Geom& g, const int ijk[3]) {
-  return ijk[0] + g.n[0] * (ijk[1] + g.n[1] * ijk[2]);
-}
-
-__device__ inline bool in_grid(const Geom& g, const int ijk[3]) {
-  for (int a = 0; a < g.dim; ++a)
-    if (ijk[a] < 0 || ijk[a] >= g.n[a]) return false;
-  return true;
-}
-
-// member k of a ghost at ijk with meta m
-__device__ inline void member_ijk(const Geom& g, const int ijk[3], uint32_t m, int k, int out[3]) {
-  int o[3];
-  stencil_off(g.dim, k, o);
-  for (int a = 0; a < 3; ++a) out[a] = ijk[a] + (a < g.dim ? o[a] * meta_r(m, a) * meta_e(m, a) : 0);
-}
 
 __global__ void k_poscell(const Geom* __restrict__ G, int ng, const int* __restrict__ cell,
                           const int* __restrict__ geo, const int* __restrict__ pos_of,
@@ -96,22 +73,41 @@ void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, u
 // dependencies all carry levels in [1, L-1] receives level L; a level written in
 // the same sweep reads as "not ready", so the result does not depend on the
 // thread schedule.  Then a stable counting sort by level gives the canonical
-// position (level, index) of every ghost.
+// position (level, index) of every ghost.  Geometries whose levels and
+// dependencies fit in shared memory run the sweep there and rank each level
+// in one pass (warps in order, __match_any_sync within a warp); larger ones
+// work on global memory with one block scan per level.
 constexpr int LV_T = 1024;
+
+size_t levels_smem(int dim, int n) {
+  return ((size_t)(stencil_k(dim) + 2) * n + 1) * sizeof(int) + 64;
+}
 
 __global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int B,
                                                  const int* __restrict__ dep, int ng_total,
                                                  int* __restrict__ level, int* __restrict__ order_pos,
                                                  int* __restrict__ lev_ptr, int* __restrict__ n_levels,
-                                                 int* status) {
+                                                 int smem_ints, int* status) {
+  extern __shared__ int sm[];
   __shared__ int sh_cnt;
   __shared__ int sh_warp[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
     const Geom& g = G[b];
     const int g0 = g.ghost_off, n = g.n_ghost;
     const int K = stencil_k(g.dim);
+    const bool fast = (long long)(K + 2) * n + 1 <= smem_ints;
     int* lp = lev_ptr + g.lev_off;
-    for (int s = threadIdx.x; s < n; s += LV_T) level[g0 + s] = 0;
+    int* lvl = fast ? sm : level + g0;
+    int* dl = sm + n;                          // [K][n] local dependencies (fast path)
+    for (int s = threadIdx.x; s < n; s += LV_T) {
+      lvl[s] = 0;
+      if (fast)
+        for (int k = 0; k < K; ++k) {
+          int d = dep[(size_t)k * ng_total + g0 + s];
+          dl[(size_t)k * n + s] = d >= 0 ? d - g0 : -1;
+        }
+    }
     if (threadIdx.x == 0) lp[0] = g0;
     __syncthreads();
     int remaining = n, L = 0;
@@ -121,17 +117,16 @@ __global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int
       __syncthreads();
       int mine = 0;
       for (int s = threadIdx.x; s < n; s += LV_T) {
-        int gi = g0 + s;
-        if (level[gi] != 0) continue;
+        if (lvl[s] != 0) continue;
         bool ok = true;
         for (int k = 0; k < K && ok; ++k) {
-          int d = dep[(size_t)k * ng_total + gi];
+          int d = fast ? dl[(size_t)k * n + s] : dep[(size_t)k * ng_total + g0 + s] - g0;
           if (d >= 0) {
-            int lv = ((volatile int*)level)[d];
+            int lv = ((volatile int*)lvl)[d];
             if (lv == 0 || lv >= L) ok = false;
           }
         }
-        if (ok) { level[gi] = L; ++mine; }
+        if (ok) { lvl[s] = L; ++mine; }
       }
       if (mine) atomicAdd(&sh_cnt, mine);
       __syncthreads();
@@ -149,33 +144,56 @@ __global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int
     if (threadIdx.x == 0) n_levels[b] = nl;
     __syncthreads();
     if (remaining > 0) continue;
-    // stable counting sort: rank by index order within each level
-    for (int lv = 1; lv <= nl; ++lv) {
-      int carry = lp[lv - 1];
+    if (fast) {
+      // pos[L] = next free canonical slot of level L (the dependency area is free now)
+      int* pos = sm + n;
+      for (int q = threadIdx.x; q < nl; q += LV_T) pos[q + 1] = lp[q];
+      __syncthreads();
       for (int base = 0; base < n; base += LV_T) {
         int s = base + threadIdx.x;
-        int f = (s < n && level[g0 + s] == lv) ? 1 : 0;
-        // block exclusive scan of f
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        unsigned bal = __ballot_sync(0xffffffffu, f);
-        int inwarp = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) sh_warp[w] = __popc(bal);
-        __syncthreads();
-        if (w == 0) {
-          int v = sh_warp[lane];
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
+        int L2 = s < n ? lvl[s] : 0;
+        unsigned peers = __match_any_sync(0xffffffffu, L2);
+        int rank = __popc(peers & ((1u << lane) - 1u));
+        bool leader = lane == __ffs(peers) - 1;
+        for (int ww = 0; ww < LV_T / 32; ++ww) {
+          int slot = 0;
+          if (w == ww && s < n) slot = pos[L2] + rank;
+          __syncwarp();
+          if (w == ww && s < n) {
+            order_pos[g0 + s] = slot;
+            if (leader) pos[L2] += __popc(peers);
           }
-          sh_warp[lane] = v;
+          __syncthreads();
         }
-        __syncthreads();
-        int before = (w > 0 ? sh_warp[w - 1] : 0);
-        if (f) order_pos[g0 + s] = carry + before + inwarp;
-        int tot = sh_warp[31];
-        __syncthreads();
-        carry += tot;
+      }
+      for (int s = threadIdx.x; s < n; s += LV_T) level[g0 + s] = lvl[s];
+    } else {
+      // one block scan per level over the index order
+      for (int lv = 1; lv <= nl; ++lv) {
+        int carry = lp[lv - 1];
+        for (int base = 0; base < n; base += LV_T) {
+          int s = base + threadIdx.x;
+          int f = (s < n && lvl[s] == lv) ? 1 : 0;
+          unsigned bal = __ballot_sync(0xffffffffu, f);
+          int inwarp = __popc(bal & ((1u << lane) - 1u));
+          if (lane == 0) sh_warp[w] = __popc(bal);
+          __syncthreads();
+          if (w == 0) {
+            int v = sh_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              int y = __shfl_up_sync(0xffffffffu, v, o);
+              if (lane >= o) v += y;
+            }
+            sh_warp[lane] = v;
+          }
+          __syncthreads();
+          int before = (w > 0 ? sh_warp[w - 1] : 0);
+          if (f) order_pos[g0 + s] = carry + before + inwarp;
+          int tot = sh_warp[31];
+          __syncthreads();
+          carry += tot;
+        }
       }
     }
     __syncthreads();
@@ -183,9 +201,15 @@ __global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int
 }
 
 void launch_levels(const Geom* G, int B, const int* dep, int ng_total, int* level, int* order_pos,
-                   int* lev_ptr, int* n_levels, int* status, cudaStream_t s) {
+                   int* lev_ptr, int* n_levels, size_t smem, int* status, cudaStream_t s) {
   if (B <= 0) return;
-  k_levels<<<B, LV_T, 0, s>>>(G, B, dep, ng_total, level, order_pos, lev_ptr, n_levels, status);
+  static size_t set = 0;
+  if (smem > set) {
+    cudaFuncSetAttribute(k_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set = smem;
+  }
+  k_levels<<<B, LV_T, smem, s>>>(G, B, dep, ng_total, level, order_pos, lev_ptr, n_levels,
+                                 (int)(smem / sizeof(int)) - 16, status);
 }
 
 __global__ void k_reorder(int ng, const int* __restrict__ order_pos, const int* __restrict__ gs_cell,
@@ -351,39 +375,6 @@ void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, c
   k_tables<<<(ng + 127) / 128, 128, 0, s>>>(G, ng, g_cell, g_geo, g_psi, g_n, g_meta, tags, wtab, ftab);
 }
 
-// ---------------------------------------------------------------------------
-// transposed incidences: for a target cell T, the (ghost H, slot) pairs with
-// member_slot(H) = T, found by probing H = T - delta over the box |delta_a| <= R
-// in a fixed order.  Slot 0 (H = T itself) is listed first for ghost targets.
-// ---------------------------------------------------------------------------
-template <typename Visit>
-__device__ inline void probe_sources(const Geom& g, const int tijk[3], const int8_t* tg,
-                                     const int* pcell, const uint32_t* g_meta, int R, Visit visit) {
-  const int K = stencil_k(g.dim);
-  int Rz = g.dim == 3 ? R : 0;
-  for (int dz = -Rz; dz <= Rz; ++dz)
-    for (int dy = -R; dy <= R; ++dy)
-      for (int dx = -R; dx <= R; ++dx) {
-        if (dx == 0 && dy == 0 && dz == 0) continue;
-        int hijk[3] = {tijk[0] - dx, tijk[1] - dy, tijk[2] - dz};
-        if (!in_grid(g, hijk)) continue;
-        int hc = cell_lin(g, hijk);
-        int8_t t = tg[hc];
-        if (t != 2 && t != -2) continue;
-        int q = pcell[hc];
-        uint32_t m = g_meta[q];
-        int dd[3] = {dx, dy, dz};
-        for (int k = 0; k < K; ++k) {
-          int o[3];
-          stencil_off(g.dim, k, o);
-          bool hit = true;
-          for (int a = 0; a < g.dim; ++a)
-            if (o[a] * meta_r(m, a) * meta_e(m, a) != dd[a]) hit = false;
-          if (hit) { if (!visit(q, k + 1)) return; }
-        }
-      }
-}
-
 // ghost targets: write = 0 counts, write = 1 writes sources (self first)
 __global__ void k_gsrc(const Geom* __restrict__ G, int ng, const int* __restrict__ g_cell,
                        const int* __restrict__ g_geo, const uint32_t* __restrict__ g_meta,
@@ -413,65 +404,6 @@ void launch_gsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, con
   if (ng <= 0) return;
   k_gsrc<<<(ng + 127) / 128, 128, 0, s>>>(G, ng, g_cell, g_geo, g_meta, tags, pos_of_cell, rmax,
                                           ptr, cnt_or_src, write);
-}
-
-// fluid targets.  Incidence i = p * 8 + k (ghost p, member k).  stage 0: owner
-// flag (the incidence is the first source of its fluid member in probe order);
-// stage 1: owners record the target and count its sources; stage 2: owners
-// write the sources.
-__global__ void k_fsrc(const Geom* __restrict__ G, int ng, const int* __restrict__ g_cell,
-                       const int* __restrict__ g_geo, const uint32_t* __restrict__ g_meta,
-                       const int8_t* __restrict__ tags, const int* __restrict__ pos_of_cell, int R,
-                       const int* __restrict__ owner_ptr, int* __restrict__ owner_flag,
-                       int* __restrict__ ft_cell, int* __restrict__ ft_geo, int* __restrict__ ft_cnt,
-                       const int* __restrict__ ft_ptr, int* __restrict__ ft_src, int stage) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ng * 8) return;
-  int p = i >> 3, k = i & 7;
-  const Geom& g = G[g_geo[p]];
-  const int K = stencil_k(g.dim);
-  bool owner = false;
-  int tijk[3] = {0, 0, 0};
-  const int8_t* tg = tags + g.cell_off;
-  const int* pc = pos_of_cell + g.cell_off;
-  if (k < K) {
-    int gijk[3];
-    cell_ijk3(g, g_cell[p], gijk);
-    member_ijk(g, gijk, g_meta[p], k, tijk);
-    if (in_grid(g, tijk) && tg[cell_lin(g, tijk)] == 0) {
-      if (stage == 0) {
-        int fq = -1, fs = -1;
-        probe_sources(g, tijk, tg, pc, g_meta, R, [&](int q, int slot) { fq = q; fs = slot; return false; });
-        owner = (fq == p && fs == k + 1);
-      } else {
-        owner = owner_flag[i] != 0;
-      }
-    }
-  }
-  if (stage == 0) { owner_flag[i] = owner ? 1 : 0; return; }
-  if (!owner) return;
-  int t = owner_ptr[i];
-  if (stage == 1) {
-    ft_cell[t] = cell_lin(g, tijk);
-    ft_geo[t] = g_geo[p];
-    int cnt = 0;
-    probe_sources(g, tijk, tg, pc, g_meta, R, [&](int, int) { ++cnt; return true; });
-    ft_cnt[t] = cnt;
-  } else {
-    int o = ft_ptr[t];
-    probe_sources(g, tijk, tg, pc, g_meta, R, [&](int q, int slot) { ft_src[o++] = (q << 3) | slot; return true; });
-  }
-}
-
-void launch_fsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
-                 const int8_t* tags, const int* pos_of_cell, int rmax, const int* owner_ptr,
-                 int* owner_flag, int* ft_cell, int* ft_geo, int* ft_cnt, const int* ft_ptr,
-                 int* ft_src, int stage, cudaStream_t s) {
-  if (ng <= 0) return;
-  int n = ng * 8;
-  k_fsrc<<<(n + 127) / 128, 128, 0, s>>>(G, ng, g_cell, g_geo, g_meta, tags, pos_of_cell, rmax,
-                                         owner_ptr, owner_flag, ft_cell, ft_geo, ft_cnt, ft_ptr,
-                                         ft_src, stage);
 }
 
 }  // namespace ebr

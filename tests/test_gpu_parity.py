@@ -222,3 +222,19 @@ def test_sphere_256_forces():
     assert np.all(np.abs(out - ref) <= 1e-12 * scale), (out, ref, scale)
     out, ref, scale = _forces_case(w, "HGC", torch.float32)
     assert np.all(np.abs(out - ref) <= 1e-4 * scale), (out, ref, scale)
+
+
+@pytest.mark.parametrize("mode", ["level", "persistent"])
+def test_nonfinite_boundary_data_is_reported(mode):
+    # a NaN boundary datum makes a ghost value non-finite: the device status
+    # word reports it at the next synchronising query, and is cleared by it
+    from paper_2609_10165_b300._lib import EBRError
+    w = _with_fields(_small_cases()[0], 300)
+    run = GPURun([w], "HGC", mode=mode, dtype=torch.float64)
+    arrays = run.field_arrays()
+    bcs = run.bc_arrays()
+    bcs[0][3] = np.nan
+    with pytest.raises(EBRError) as ei:
+        run.fill(arrays, bcs)
+    assert ei.value.name == "EBR_ENONFINITE"
+    run.fill(run.field_arrays(), run.bc_arrays())

@@ -1,0 +1,42 @@
+"""The multi-rank path of bench.py on CPU: world size 2 over gloo.  Every rank
+runs its own batch (weak scaling, no exchange on the data path); the ranks
+meet only to take the maximum of their step times and the sum of their
+updates, which is what bench.py reports."""
+
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms = 1.0 + 2.0 * rank                      # rank 1 is the slowest
+    updates = 1000 * (rank + 1)
+    t, u = bench.reduce_over_ranks(ms, updates, torch.device("cpu"))
+    out[rank] = (t, u)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_world_size_two_reduction():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(world, port, out), nprocs=world, start_method="spawn")
+    assert out[0] == (3.0, 3000) and out[1] == (3.0, 3000)
