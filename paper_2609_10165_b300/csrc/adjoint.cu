@@ -275,9 +275,9 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
                             const uint32_t* __restrict__ g_meta, const int8_t* __restrict__ tags,
                             const int* __restrict__ pos_of_cell, int rmax,
                             const double* __restrict__ wtab, const double* __restrict__ sv,
-                            const T* __restrict__ lam, int accumulate) {
+                            const T* __restrict__ lam, int accumulate, int kmax) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int p = i >> 3, k = i & 7;
+  int p = i / kmax, k = i - p * kmax;
   if (p >= ng) return;
   const Geom& g = G[g_geo[p]];
   if (k >= stencil_k(g.dim)) return;
@@ -287,12 +287,16 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
   const int8_t* tg = tags + g.cell_off;
   const int* pc = pos_of_cell + g.cell_off;
   if (!in_grid(g, tijk) || tg[cell_lin(g, tijk)] != 0) return;
-  int fq = -1, fs = -1;
-  probe_sources(g, tijk, tg, pc, g_meta, rmax, [&](int q, int slot) { fq = q; fs = slot; return false; });
-  if (fq != p || fs != k + 1) return;
+  // one pass: the first source met decides ownership; a non-owner stops there
   T acc[8];
   for (int f = 0; f < F; ++f) acc[f] = T(0);
+  bool first = true, owner = false;
   probe_sources(g, tijk, tg, pc, g_meta, rmax, [&](int q, int slot) {
+    if (first) {
+      first = false;
+      owner = (q == p && slot == k + 1);
+      if (!owner) return false;
+    }
     bool act = meta_active(g_meta[q]) >> (slot - 1) & 1u;
     for (int f = 0; f < F; ++f) {
       acc[f] += (T)sv[(size_t)(f * 8 + slot) * ng + q];
@@ -300,6 +304,7 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
     }
     return true;
   });
+  if (!owner) return;
   long long c = g.cell_off + cell_lin(g, tijk);
   for (int f = 0; f < F; ++f) {
     T* gr = static_cast<T*>(A.grad[f]);
@@ -310,15 +315,16 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
 void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                       const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
                       const int* pos_of_cell, int rmax, const double* wtab, const double* sv,
-                      const void* lam, void* const* grad, int accumulate, cudaStream_t s) {
+                      const void* lam, void* const* grad, int accumulate, int kmax, cudaStream_t s) {
   if (ng <= 0) return;
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.grad[f] = grad[f]; }
-  int n = ng * 8;
+  // one thread per (ghost, member): K = 3 in 2D, 7 in 3D (kmax covers both)
+  int n = ng * kmax;
   if (dtype == 0)
-    k_adj_fluid<float><<<(n + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const float*)lam, accumulate);
+    k_adj_fluid<float><<<(n + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const float*)lam, accumulate, kmax);
   else
-    k_adj_fluid<double><<<(n + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const double*)lam, accumulate);
+    k_adj_fluid<double><<<(n + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const double*)lam, accumulate, kmax);
 }
 
 template <typename T>

@@ -839,7 +839,8 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
   }
   prof_begin(c, s, "adj_fluid");
   launch_adj_fluid(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->g_meta, c->tags,
-                   c->pos_of_cell, c->rmax, c->wtab, c->sv, c->lam, d_grad_fields, accumulate, s);
+                   c->pos_of_cell, c->rmax, c->wtab, c->sv, c->lam, d_grad_fields, accumulate,
+                   stencil_k(dim), s);
   prof_end(c, s);
   c->launches += 1;
   prof_begin(c, s, "adj_bc");

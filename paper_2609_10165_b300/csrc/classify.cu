@@ -34,43 +34,119 @@ __device__ inline float airfoil_f32(float t, float c, float r00, float r01, floa
   return yt - fabsf(yp);
 }
 
-// Estimate the solid run of row (j, k).
-__device__ void estimate_row(const Geom& g, int j, int k, int& state, int& ia, int& ib, int& iv) {
-  const int n = g.n[0];
+// Per-row constants of the float pre-test of the inside predicate.
+struct RowF {
+  float ox, hx;        // x - c_x = ox + (i + 1/2) hx (body-relative x of cell i)
+  float c0, c1, c2;    // row-constant parts (y / z terms)
+  float m;             // safety margin of the float test
+  float ia, ib;        // ellipse 1/a, 1/b
+  float r00, r01;      // rotation entries multiplying x
+};
+
+// Float test of one cell of the row: 1 solid, 0 fluid, -1 too close to call.
+// The margins bound the float rounding of every quantity by a wide factor;
+// a cell within the margin of the boundary is decided by the double predicate.
+__device__ inline int solid_f32(const Geom& g, const RowF& R, int i) {
+  float x = R.ox + ((float)i + 0.5f) * R.hx;
+  switch (g.kind) {
+    case CIRCLE:
+    case SPHERE: {
+      float v = x * x + R.c0 - R.c1;             // |d|^2 - r^2
+      if (v > R.m) return 0;
+      if (v < -R.m) return 1;
+      return -1;
+    }
+    case ELLIPSE: {
+      float px = (R.r00 * x + R.c0) * R.ia, py = (R.r01 * x + R.c1) * R.ib;
+      float v = px * px + py * py - 1.0f;
+      if (v > R.m) return 0;
+      if (v < -R.m) return 1;
+      return -1;
+    }
+    default: {  // AIRFOIL4: depth y_t(x') - |y'|, x' in [0, c]
+      float px = R.r00 * x + R.c0, py = R.r01 * x + R.c1, c = (float)g.c;
+      if (px < -R.m || px > c + R.m) return 0;
+      if (px < 1e-3f * c || px > c - R.m) return -1;    // near the nose (sqrt) or the base
+      float xi = px / c;
+      float yt = 5.0f * (float)g.t * c *
+                 (0.2969f * sqrtf(xi) + xi * (-0.1260f + xi * (-0.3516f + xi * (0.2843f + xi * -0.1015f))));
+      float v = yt - fabsf(py);
+      if (v > R.m) return 1;
+      if (v < -R.m) return 0;
+      return -1;
+    }
+  }
+}
+
+__device__ inline void row_consts(const Geom& g, int j, int k, RowF& R) {
   double y = centre_of(g, 1, j);
   double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
-  state = ROW_EMPTY; ia = 0; ib = -1; iv = 0;
-  double cx, xa, xb;
+  float ext = 1.0f;
+  for (int a = 0; a < g.dim; ++a)
+    ext = fmaxf(ext, fmaxf(fabsf((float)(g.lo[a] - g.centre[a])),
+                           fabsf((float)(g.lo[a] + g.n[a] * g.h[a] - g.centre[a]))));
+  R.ox = (float)(g.lo[0] - g.centre[0]);
+  R.hx = (float)g.h[0];
+  R.ia = R.ib = 1.0f;
+  R.r00 = (float)g.rot[0];
+  R.r01 = (float)g.rot[1];
+  float dy = (float)(y - g.centre[1]);
   if (g.kind == CIRCLE || g.kind == SPHERE) {
-    double dy = y - g.centre[1];
-    double dz = g.kind == SPHERE ? z - g.centre[2] : 0.0;
-    double r2 = g.radii[0] * g.radii[0];
-    double D = r2 - dy * dy - dz * dz;
-    cx = g.centre[0];
-    if (D < -1e-9 * r2) return;
-    if (D <= 0.0) { state = ROW_TANGENT; iv = (int)lrint(frac_cell(g, 0, cx)); return; }
-    double sD = sqrt(D);
-    xa = cx - sD; xb = cx + sD;
+    float dz = g.kind == SPHERE ? (float)(z - g.centre[2]) : 0.0f;
+    float r = (float)g.radii[0];
+    R.c0 = dy * dy + dz * dz;
+    R.c1 = r * r;
+    R.m = 1e-5f * (3.0f * ext * ext + r * r);
   } else if (g.kind == ELLIPSE) {
-    double r00 = g.rot[0], r01 = g.rot[1], r10 = g.rot[3], r11 = g.rot[4];
-    double ia2 = 1.0 / (g.radii[0] * g.radii[0]), ib2 = 1.0 / (g.radii[1] * g.radii[1]);
-    double v = y - g.centre[1];
-    double A = r00 * r00 * ia2 + r01 * r01 * ib2;
-    double Bq = 2.0 * v * (r00 * r10 * ia2 + r01 * r11 * ib2);
-    double C = v * v * (r10 * r10 * ia2 + r11 * r11 * ib2) - 1.0;
-    double disc = Bq * Bq - 4.0 * A * C;
-    double uv = -Bq / (2.0 * A);
-    cx = g.centre[0] + uv;
-    double scale = Bq * Bq + 4.0 * A * fabs(C);
-    if (disc < -1e-9 * scale) return;
-    if (disc <= 0.0) { state = ROW_TANGENT; iv = (int)lrint(frac_cell(g, 0, cx)); return; }
-    double sd = sqrt(disc) / (2.0 * A);
+    float a = (float)g.radii[0], b = (float)g.radii[1];
+    R.c0 = (float)g.rot[3] * dy;
+    R.c1 = (float)g.rot[4] * dy;
+    R.ia = 1.0f / a;
+    R.ib = 1.0f / b;
+    float mn = fminf(a, b);
+    R.m = 1e-5f * (1.0f + 2.0f * ext * ext / (mn * mn));
+  } else {
+    R.c0 = (float)g.rot[3] * dy;
+    R.c1 = (float)g.rot[4] * dy;
+    R.m = 2e-5f * (1.0f + ext);
+  }
+}
+
+// Estimate the solid run of row (j, k) in float.  A row is declared empty
+// only with a wide margin; near-tangent rows are handed to the exact window.
+__device__ void estimate_row(const Geom& g, int j, int k, int& state, int& ia, int& ib, int& iv) {
+  const int n = g.n[0];
+  float y = (float)(centre_of(g, 1, j) - g.centre[1]);
+  float z = g.dim == 3 ? (float)(centre_of(g, 2, k) - g.centre[2]) : 0.0f;
+  float lo0 = (float)(g.lo[0] - g.centre[0]), h0 = (float)g.h[0];
+  auto frac = [&](float xr) { return (xr - lo0) / h0 - 0.5f; };   // body-relative x -> cell
+  state = ROW_EMPTY; ia = 0; ib = -1; iv = 0;
+  float cx, xa, xb;
+  if (g.kind == CIRCLE || g.kind == SPHERE) {
+    float r2 = (float)(g.radii[0] * g.radii[0]);
+    float yz = y * y + (g.kind == SPHERE ? z * z : 0.0f);
+    float D = r2 - yz;
+    cx = 0.0f;
+    if (D < -(1e-4f * r2 + 1e-6f * yz)) return;
+    if (D <= 0.0f) { state = ROW_TANGENT; iv = (int)lrintf(frac(cx)); return; }
+    float sD = sqrtf(D);
+    xa = -sD; xb = sD;
+  } else if (g.kind == ELLIPSE) {
+    float r00 = (float)g.rot[0], r01 = (float)g.rot[1], r10 = (float)g.rot[3], r11 = (float)g.rot[4];
+    float ia2 = 1.0f / (float)(g.radii[0] * g.radii[0]), ib2 = 1.0f / (float)(g.radii[1] * g.radii[1]);
+    float A = r00 * r00 * ia2 + r01 * r01 * ib2;
+    float Bq = 2.0f * y * (r00 * r10 * ia2 + r01 * r11 * ib2);
+    float C = y * y * (r10 * r10 * ia2 + r11 * r11 * ib2) - 1.0f;
+    float disc = Bq * Bq - 4.0f * A * C;
+    cx = -Bq / (2.0f * A);
+    float scale = Bq * Bq + 4.0f * A * fabsf(C);
+    if (disc < -1e-4f * scale) return;
+    if (disc <= 0.0f) { state = ROW_TANGENT; iv = (int)lrintf(frac(cx)); return; }
+    float sd = sqrtf(disc) / (2.0f * A);
     xa = cx - sd; xb = cx + sd;
-  } else {  // AIRFOIL4: float bracketing of the concave depth along the row
+  } else {  // AIRFOIL4: golden-section maximum of the concave depth, bisected roots
     float r00 = (float)g.rot[0], r01 = (float)g.rot[1];
-    double by0 = y - g.centre[1];
-    // x' = r00 (x - lx) + r10 (y - ly); write x' = r00 * X + bx with X = x - lx
-    float bx = (float)(g.rot[3] * by0), byy = (float)(g.rot[4] * by0);
+    float bx = (float)g.rot[3] * y, byy = (float)g.rot[4] * y;
     float c = (float)g.c, t = (float)g.t;
     if (!(r00 > 0.0f)) { state = -1; return; }
     float X0 = (0.0f - bx) / r00, X1 = (c - bx) / r00;
@@ -78,26 +154,28 @@ __device__ void estimate_row(const Geom& g, int j, int k, int& state, int& ia, i
     float ymin = fminf(fabsf(r01 * X0 + byy), fabsf(r01 * X1 + byy));
     if ((r01 * X0 + byy) * (r01 * X1 + byy) < 0.0f) ymin = 0.0f;
     if (ymin > 0.6f * t * c + 1e-4f * c) return;
+    const float gr = 0.6180339887f;
     float lo = X0, hi = X1;
-    for (int it = 0; it < 60; ++it) {
-      float m1 = lo + (hi - lo) * (1.0f / 3.0f), m2 = hi - (hi - lo) * (1.0f / 3.0f);
-      if (airfoil_f32(t, c, r00, r01, bx, byy, m1) < airfoil_f32(t, c, r00, r01, bx, byy, m2)) lo = m1;
-      else hi = m2;
+    float m1 = hi - gr * (hi - lo), m2 = lo + gr * (hi - lo);
+    float f1 = airfoil_f32(t, c, r00, r01, bx, byy, m1), f2 = airfoil_f32(t, c, r00, r01, bx, byy, m2);
+    for (int it = 0; it < 40; ++it) {
+      if (f1 < f2) { lo = m1; m1 = m2; f1 = f2; m2 = lo + gr * (hi - lo); f2 = airfoil_f32(t, c, r00, r01, bx, byy, m2); }
+      else { hi = m2; m2 = m1; f2 = f1; m1 = hi - gr * (hi - lo); f1 = airfoil_f32(t, c, r00, r01, bx, byy, m1); }
     }
     float xm = 0.5f * (lo + hi);
     float fm = airfoil_f32(t, c, r00, r01, bx, byy, xm);
     float tol = 1e-4f * c;
-    cx = g.centre[0] + (double)xm;
+    cx = xm;
     if (fm < -tol) return;
     // a grazing row whose maximum depth rounds to <= 0 holds at most a few
     // cells around the maximum; any positive depth gets bracketed roots
-    if (fm <= 0.0f) { state = ROW_TANGENT; iv = (int)lrint(frac_cell(g, 0, cx)); return; }
+    if (fm <= 0.0f) { state = ROW_TANGENT; iv = (int)lrintf(frac(cx)); return; }
     // roots of the depth on either side of the maximum; where the depth is
     // still >= 0 at the segment end the run ends there (x' = 0 or x' = c)
     float xa_f = X0, xb_f = X1;
     if (airfoil_f32(t, c, r00, r01, bx, byy, X0) < 0.0f) {
       float a = X0, b = xm;
-      for (int it = 0; it < 40; ++it) {
+      for (int it = 0; it < 28; ++it) {
         float m = 0.5f * (a + b);
         if (airfoil_f32(t, c, r00, r01, bx, byy, m) < 0.0f) a = m; else b = m;
       }
@@ -105,25 +183,26 @@ __device__ void estimate_row(const Geom& g, int j, int k, int& state, int& ia, i
     }
     if (airfoil_f32(t, c, r00, r01, bx, byy, X1) < 0.0f) {
       float a = xm, b = X1;
-      for (int it = 0; it < 40; ++it) {
+      for (int it = 0; it < 28; ++it) {
         float m = 0.5f * (a + b);
         if (airfoil_f32(t, c, r00, r01, bx, byy, m) >= 0.0f) a = m; else b = m;
       }
       xb_f = 0.5f * (a + b);
     }
-    xa = g.centre[0] + (double)xa_f;
-    xb = g.centre[0] + (double)xb_f;
+    xa = xa_f; xb = xb_f;
   }
-  double fa = frac_cell(g, 0, xa), fb = frac_cell(g, 0, xb);
-  if (fb < -2.0 || fa > n + 1.0) return;
-  ia = iceil_idx(fmax(fa, -4.0));
-  ib = ifloor_idx(fmin(fb, (double)n + 3.0));
-  if (ia > ib) { state = ROW_TANGENT; iv = (int)lrint(frac_cell(g, 0, cx)); return; }
+  float fa = frac(xa), fb = frac(xb);
+  if (fb < -2.0f || fa > n + 1.0f) return;
+  ia = (int)ceilf(fmaxf(fa, -4.0f));
+  ib = (int)floorf(fminf(fb, (float)n + 3.0f));
+  if (ia > ib) { state = ROW_TANGENT; iv = (int)lrintf(frac(cx)); return; }
   state = ROW_RUN;
 }
 
-__device__ inline bool pred_cell(const Geom& g, int i, int j, int k) {
+__device__ inline bool pred_cell(const Geom& g, const RowF& R, int i, int j, int k) {
   if (i < 0 || i >= g.n[0]) return false;
+  int q = solid_f32(g, R, i);
+  if (q >= 0) return q == 1;
   return solid_cell(g, i, j, k);
 }
 
@@ -135,12 +214,14 @@ __device__ void exact_run(const Geom& g, int j, int k, int& s, int& t, int* stat
   s = 0; t = -1;
   if (state < 0) { set_status(status, S_EINVAL); return; }
   if (state == ROW_EMPTY) return;
+  RowF R;
+  row_consts(g, j, k, R);
   bool ok = true;
   if (state == ROW_RUN) {
     unsigned bl = 0, bu = 0;
     for (int m = 0; m < 4; ++m) {
-      if (pred_cell(g, ia - 2 + m, j, k)) bl |= 1u << m;
-      if (pred_cell(g, ib - 1 + m, j, k)) bu |= 1u << m;
+      if (pred_cell(g, R, ia - 2 + m, j, k)) bl |= 1u << m;
+      if (pred_cell(g, R, ib - 1 + m, j, k)) bu |= 1u << m;
     }
     if (bl == 0 || bu == 0) ok = false;
     else {
@@ -154,7 +235,7 @@ __device__ void exact_run(const Geom& g, int j, int k, int& s, int& t, int* stat
   } else {  // tangent: a short run (or none) around the vertex
     unsigned bw = 0;
     for (int m = 0; m < 8; ++m)
-      if (pred_cell(g, iv - 3 + m, j, k)) bw |= 1u << m;
+      if (pred_cell(g, R, iv - 3 + m, j, k)) bw |= 1u << m;
     if (bw == 0) { s = 0; t = -1; return; }
     int m0 = __ffs(bw) - 1, m1 = 31 - __clz(bw);
     s = iv - 3 + m0;

@@ -96,7 +96,7 @@ void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom*
 void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                       const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
                       const int* pos_of_cell, int rmax, const double* wtab, const double* sv,
-                      const void* lam, void* const* grad, int accumulate, cudaStream_t s);
+                      const void* lam, void* const* grad, int accumulate, int kmax, cudaStream_t s);
 void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                    const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,
                    void* const* grad, int accumulate, cudaStream_t s);

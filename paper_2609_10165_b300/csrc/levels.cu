@@ -256,8 +256,9 @@ void launch_reorder(int ng, const int* order_pos, const int* gs_cell, const int*
 //     Eqs. derivative_trilinear_x/y/z).  Slot 0 is G itself, slot k the member P_k.
 // ---------------------------------------------------------------------------
 __device__ void dirichlet_w(int dim, const double X2[3], const double Xs[3], double w[8]) {
+  // w_a = (x_1 - x_s) / (x_2 - x_s) with x_1 = 0 (Eqs. phi_G_Dir_2d / _3d)
   double om[3];
-  for (int a = 0; a < dim; ++a) om[a] = (0.0 - Xs[a]) / (X2[a] - Xs[a]);
+  for (int a = 0; a < dim; ++a) om[a] = -Xs[a] / (X2[a] - Xs[a]);
   for (int q = 0; q < 8; ++q) w[q] = 0.0;
   if (dim == 2) {
     w[0] = om[0]; w[1] = om[1]; w[2] = -om[0] * om[1];
@@ -274,27 +275,31 @@ __device__ void neumann_w(int dim, const double X2[3], const double Xs[3], const
                           double w[8]) {
   for (int q = 0; q < 8; ++q) w[q] = 0.0;
   if (dim == 2) {
+    // Eq. phi_G_Neu_2d with x_1 = y_1 = 0; one reciprocal of the common denominator
     double a1 = n[0] * (0.0 - Xs[1]), a2 = n[0] * (X2[1] - Xs[1]);
     double b1 = n[1] * (0.0 - Xs[0]), b2 = n[1] * (X2[0] - Xs[0]);
-    double den = a2 + b2;
-    double w1 = (a2 + b1) / den, w2 = (a1 + b2) / den;
+    double rden = 1.0 / (a2 + b2);
+    double w1 = (a2 + b1) * rden, w2 = (a1 + b2) * rden;
     w[0] = w1; w[1] = w2; w[2] = 1.0 - w1 - w2;
-    w[7] = -(X2[0] - 0.0) * (X2[1] - 0.0) / den;
+    w[7] = -(X2[0] * X2[1]) * rden;
     return;
   }
-  const double xi[2] = {0.0, X2[0]}, yi[2] = {0.0, X2[1]}, zi[2] = {0.0, X2[2]};
-  auto A = [&](int i, int j) { return n[0] * (yi[i - 1] - Xs[1]) * (zi[j - 1] - Xs[2]); };
-  auto Bf = [&](int i, int j) { return n[1] * (xi[i - 1] - Xs[0]) * (zi[j - 1] - Xs[2]); };
-  auto C = [&](int i, int j) { return n[2] * (xi[i - 1] - Xs[0]) * (yi[j - 1] - Xs[1]); };
-  double den = A(2, 2) + Bf(2, 2) + C(2, 2);
-  w[0] = (A(2, 2) + Bf(1, 2) + C(1, 2)) / den;
-  w[1] = (A(1, 2) + Bf(2, 2) + C(2, 1)) / den;
-  w[2] = (A(2, 1) + Bf(2, 1) + C(2, 2)) / den;
-  w[3] = -(A(1, 2) + Bf(1, 2) + C(1, 1)) / den;
-  w[4] = -(A(1, 1) + Bf(2, 1) + C(2, 1)) / den;
-  w[5] = -(A(2, 1) + Bf(1, 1) + C(1, 2)) / den;
-  w[6] = (A(1, 1) + Bf(1, 1) + C(1, 1)) / den;
-  w[7] = -(X2[0] - 0.0) * (X2[1] - 0.0) * (X2[2] - 0.0) / den;
+  // Eq. phi_G_Neu_3d with a_ij = n_x (y_i - y_s)(z_j - z_s) etc., x_1 = 0
+  const double xi[2] = {0.0 - Xs[0], X2[0] - Xs[0]};
+  const double yi[2] = {0.0 - Xs[1], X2[1] - Xs[1]};
+  const double zi[2] = {0.0 - Xs[2], X2[2] - Xs[2]};
+  auto A = [&](int i, int j) { return n[0] * yi[i - 1] * zi[j - 1]; };
+  auto Bf = [&](int i, int j) { return n[1] * xi[i - 1] * zi[j - 1]; };
+  auto C = [&](int i, int j) { return n[2] * xi[i - 1] * yi[j - 1]; };
+  double rden = 1.0 / (A(2, 2) + Bf(2, 2) + C(2, 2));
+  w[0] = (A(2, 2) + Bf(1, 2) + C(1, 2)) * rden;
+  w[1] = (A(1, 2) + Bf(2, 2) + C(2, 1)) * rden;
+  w[2] = (A(2, 1) + Bf(2, 1) + C(2, 2)) * rden;
+  w[3] = -(A(1, 2) + Bf(1, 2) + C(1, 1)) * rden;
+  w[4] = -(A(1, 1) + Bf(2, 1) + C(2, 1)) * rden;
+  w[5] = -(A(2, 1) + Bf(1, 1) + C(1, 2)) * rden;
+  w[6] = (A(1, 1) + Bf(1, 1) + C(1, 1)) * rden;
+  w[7] = -(X2[0] * X2[1] * X2[2]) * rden;
 }
 
 __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restrict__ g_cell,
@@ -309,10 +314,11 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
   uint32_t m = g_meta[p];
   double psi = g_psi[p];
   double n[3] = {g_n[p], g_n[ng + p], g_n[2 * (size_t)ng + p]};
-  double X2[3] = {0, 0, 0}, Xs[3] = {0, 0, 0};
+  double X2[3] = {1, 1, 1}, Xs[3] = {0, 0, 0}, r2[3] = {1, 1, 1};
   for (int a = 0; a < d; ++a) {
     X2[a] = meta_r(m, a) * meta_e(m, a) * g.h[a];
     Xs[a] = psi * n[a];
+    r2[a] = 1.0 / X2[a];
   }
   double wd[8], wn[8];
   dirichlet_w(d, X2, Xs, wd);
@@ -341,29 +347,31 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
   for (int q = 0; q < 33; ++q) f[q] = 0.0;
   f[0] = wG;
   // phi_s = (phi_G - sum_k wd_k phi_k) / wd_s
-  f[1] = 1.0 / wd[7];
+  double rws = 1.0 / wd[7];
+  f[1] = rws;
   const int K = stencil_k(d);
-  for (int k = 0; k < K; ++k) f[2 + k] = -wd[k] / wd[7];
-  // gradient at S, local coordinates (x_1 = 0)
-  double fx0 = (X2[0] - Xs[0]) / X2[0], fx1 = Xs[0] / X2[0];
-  double fy0 = (X2[1] - Xs[1]) / X2[1], fy1 = Xs[1] / X2[1];
+  for (int k = 0; k < K; ++k) f[2 + k] = -wd[k] * rws;
+  // gradient at S, local coordinates (x_1 = 0): fx0 = (x_2 - x_s)/(x_2 - x_1),
+  // fx1 = (x_s - x_1)/(x_2 - x_1), divided differences over h = x_2 - x_1
+  double fx0 = (X2[0] - Xs[0]) * r2[0], fx1 = Xs[0] * r2[0];
+  double fy0 = (X2[1] - Xs[1]) * r2[1], fy1 = Xs[1] * r2[1];
   double* bx = f + 9;
   double* by = f + 17;
   double* bz = f + 25;
   if (d == 2) {
-    double hx = X2[0], hy = X2[1];
-    bx[0] = -fy0 / hx; bx[1] = fy0 / hx; bx[2] = -fy1 / hx; bx[3] = fy1 / hx;
-    by[0] = -fx0 / hy; by[1] = -fx1 / hy; by[2] = fx0 / hy; by[3] = fx1 / hy;
+    double ix = r2[0], iy = r2[1];
+    bx[0] = -fy0 * ix; bx[1] = fy0 * ix; bx[2] = -fy1 * ix; bx[3] = fy1 * ix;
+    by[0] = -fx0 * iy; by[1] = -fx1 * iy; by[2] = fx0 * iy; by[3] = fx1 * iy;
   } else {
-    double fz0 = (X2[2] - Xs[2]) / X2[2], fz1 = Xs[2] / X2[2];
-    double hx = X2[0], hy = X2[1], hz = X2[2];
+    double fz0 = (X2[2] - Xs[2]) * r2[2], fz1 = Xs[2] * r2[2];
+    double ix = r2[0], iy = r2[1], iz = r2[2];
     // slots: 0 G, 1 P1, 2 P2, 3 P3, 4 P4, 5 P5, 6 P6, 7 P7
-    bx[0] = -fy0 * fz0 / hx; bx[1] = fy0 * fz0 / hx; bx[2] = -fy1 * fz0 / hx; bx[4] = fy1 * fz0 / hx;
-    bx[3] = -fy0 * fz1 / hx; bx[6] = fy0 * fz1 / hx; bx[5] = -fy1 * fz1 / hx; bx[7] = fy1 * fz1 / hx;
-    by[0] = -fx0 * fz0 / hy; by[2] = fx0 * fz0 / hy; by[1] = -fx1 * fz0 / hy; by[4] = fx1 * fz0 / hy;
-    by[3] = -fx0 * fz1 / hy; by[5] = fx0 * fz1 / hy; by[6] = -fx1 * fz1 / hy; by[7] = fx1 * fz1 / hy;
-    bz[0] = -fx0 * fy0 / hz; bz[3] = fx0 * fy0 / hz; bz[1] = -fx1 * fy0 / hz; bz[6] = fx1 * fy0 / hz;
-    bz[2] = -fx0 * fy1 / hz; bz[5] = fx0 * fy1 / hz; bz[4] = -fx1 * fy1 / hz; bz[7] = fx1 * fy1 / hz;
+    bx[0] = -fy0 * fz0 * ix; bx[1] = fy0 * fz0 * ix; bx[2] = -fy1 * fz0 * ix; bx[4] = fy1 * fz0 * ix;
+    bx[3] = -fy0 * fz1 * ix; bx[6] = fy0 * fz1 * ix; bx[5] = -fy1 * fz1 * ix; bx[7] = fy1 * fz1 * ix;
+    by[0] = -fx0 * fz0 * iy; by[2] = fx0 * fz0 * iy; by[1] = -fx1 * fz0 * iy; by[4] = fx1 * fz0 * iy;
+    by[3] = -fx0 * fz1 * iy; by[5] = fx0 * fz1 * iy; by[6] = -fx1 * fz1 * iy; by[7] = fx1 * fz1 * iy;
+    bz[0] = -fx0 * fy0 * iz; bz[3] = fx0 * fy0 * iz; bz[1] = -fx1 * fy0 * iz; bz[6] = fx1 * fy0 * iz;
+    bz[2] = -fx0 * fy1 * iz; bz[5] = fx0 * fy1 * iz; bz[4] = -fx1 * fy1 * iz; bz[7] = fx1 * fy1 * iz;
   }
   for (int q = 0; q < 33; ++q) ftab[(size_t)q * ng + p] = f[q];
 }
