@@ -270,15 +270,18 @@ int64_t ebr_launch_count(const void* ctx);
 
 /* enable != 0: from now on every kernel launch of the context is bracketed by
  * two CUDA events recorded on the launching stream (adds a small gap between
- * kernels).  Clears earlier records.  enable = 0 turns it off. */
+ * kernels).  Inside a stream capture the events become event-record nodes of
+ * the graph and are re-recorded at every replay.  Clears earlier records.
+ * enable = 0 stops adding records (existing ones stay readable). */
 ebr_status ebr_profile(void* ctx, int32_t enable);
 /* Synchronise the recorded events and aggregate them by kernel name:
  * h_names [max_entries][32] (NUL-terminated), h_ms [max_entries] total
  * milliseconds, h_count [max_entries] launches.  Returns the number of
- * distinct names (may exceed max_entries) or a negative ebr_status; clears
- * the records.  Any output pointer may be NULL. */
+ * distinct names (may exceed max_entries) or a negative ebr_status.  keep = 0
+ * clears the records; keep != 0 keeps them (to read a replayed graph again).
+ * Any output pointer may be NULL. */
 int32_t ebr_profile_read(void* ctx, int32_t max_entries, char* h_names, double* h_ms,
-                         int64_t* h_count);
+                         int64_t* h_count, int32_t keep);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free classification of one grid (the paper has no counterpart)

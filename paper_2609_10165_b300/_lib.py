@@ -61,7 +61,7 @@ _SIGS = {
     "ebr_diagnostics": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_int32, c_void_p]),
     "ebr_launch_count": (c_int64, [c_void_p]),
     "ebr_profile": (c_int32, [c_void_p, c_int32]),
-    "ebr_profile_read": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "ebr_profile_read": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32]),
     "ebr_classify_cells_static": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Body), c_void_p,
                                             c_void_p, c_void_p]),
 }

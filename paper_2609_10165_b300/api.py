@@ -181,11 +181,11 @@ class Reconstructor:
     def profile(self, enable=True):
         self._check(self.lib.ebr_profile(self.ctx, 1 if enable else 0))
 
-    def profile_read(self, max_entries=64):
+    def profile_read(self, max_entries=64, keep=False):
         names = ctypes.create_string_buffer(32 * max_entries)
         ms = (ctypes.c_double * max_entries)()
         cnt = (ctypes.c_int64 * max_entries)()
-        n = self.lib.ebr_profile_read(self.ctx, max_entries, names, ms, cnt)
+        n = self.lib.ebr_profile_read(self.ctx, max_entries, names, ms, cnt, 1 if keep else 0)
         if n < 0:
             self._check(n)
         out = {}

@@ -119,17 +119,27 @@ cudaEvent_t take_event(Ctx* c) {
   return c->pool[c->pool_used++];
 }
 
+// Inside a stream capture the events become event-record nodes of the graph
+// (re-recorded at every replay), so a captured step can be timed per kernel
+// without the host launch gaps of an eager step.
+void prof_record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &st);
+  if (st == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
+}
+
 void prof_begin(Ctx* c, cudaStream_t s, const char* name) {
   if (!c->prof) return;
   Ctx::ProfRec r{name, take_event(c), nullptr};
-  if (r.a) cudaEventRecord(r.a, s);
+  if (r.a) prof_record(r.a, s);
   c->recs.push_back(r);
 }
 
 void prof_end(Ctx* c, cudaStream_t s) {
   if (!c->prof || c->recs.empty()) return;
   c->recs.back().b = take_event(c);
-  if (c->recs.back().b) cudaEventRecord(c->recs.back().b, s);
+  if (c->recs.back().b) prof_record(c->recs.back().b, s);
 }
 
 ebr_status fail(Ctx* c, ebr_status s, const char* fmt, ...) {
@@ -856,13 +866,15 @@ ebr_status ebr_profile(void* ctx, int32_t enable) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
   c->prof = enable != 0;
-  c->recs.clear();
-  c->pool_used = 0;
+  if (c->prof) {
+    c->recs.clear();
+    c->pool_used = 0;
+  }
   return EBR_OK;
 }
 
 int32_t ebr_profile_read(void* ctx, int32_t max_entries, char* h_names, double* h_ms,
-                         int64_t* h_count) {
+                         int64_t* h_count, int32_t keep) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
   std::vector<std::string> names;
@@ -888,8 +900,10 @@ int32_t ebr_profile_read(void* ctx, int32_t max_entries, char* h_names, double* 
     if (h_ms) h_ms[k] = ms[k];
     if (h_count) h_count[k] = cnt[k];
   }
-  c->recs.clear();
-  c->pool_used = 0;
+  if (!keep) {
+    c->recs.clear();
+    c->pool_used = 0;
+  }
   return n;
 }
 
