@@ -37,7 +37,7 @@ UNIT = "updates/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--geoms", type=int, default=256)
@@ -150,9 +150,13 @@ def setup(geoms, device, dtype):
 
 
 class Step:
-    """The timed hot path on resident device buffers."""
+    """The timed hot path on resident device buffers.
 
-    def __init__(self, R, fields, bcs, geoms, mode, adjoint=True):
+    With `overlap`, the adjoint (which needs the coefficients but not the
+    filled values: the path is linear) runs on a second stream beside the
+    fill and the forces, joined at the end of the step."""
+
+    def __init__(self, R, fields, bcs, geoms, mode, adjoint=True, overlap=False):
         import torch
         self.R, self.fields, self.bcs, self.mode, self.adjoint = R, fields, bcs, mode, adjoint
         self.kinds = geoms[0]["bc"]
@@ -166,16 +170,28 @@ class Step:
         self.seed = torch.ones(R.B, 2, dtype=torch.float64, device=dev)
         self.gf = [torch.zeros_like(f) for f in fields]
         self.gb = [torch.zeros_like(b) for b in bcs]
+        self.side = torch.cuda.Stream(dev) if (overlap and adjoint) else None
+
+    def _adjoint(self):
+        self.R.adjoint(self.kinds, self.vel, self.p, self.mu, self.dirs, self.seed, self.gf, self.gb,
+                       mode=self.mode)
 
     def __call__(self):
+        import torch
         R = self.R
         R.classify()
         R.build_levels()
+        if self.side is not None:
+            main = torch.cuda.current_stream()
+            self.side.wait_stream(main)
+            with torch.cuda.stream(self.side):
+                self._adjoint()
         R.reconstruct(self.fields, self.kinds, self.bcs, mode=self.mode)
         R.forces([self.fields[i] for i in self.vel], self.fields[self.p], self.mu, self.dirs, out=self.out)
-        if self.adjoint:
-            R.adjoint(self.kinds, self.vel, self.p, self.mu, self.dirs, self.seed, self.gf, self.gb,
-                      mode=self.mode)
+        if self.side is not None:
+            torch.cuda.current_stream().wait_stream(self.side)
+        elif self.adjoint:
+            self._adjoint()
 
 
 def reduce_over_ranks(ms, updates, device):
@@ -280,6 +296,43 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# Algorithmic bytes per step of every kernel (2D: K = 3 stencil members, FP32
+# fields, s = 4 B; FP64 coefficients).  A kernel's minimum HBM traffic: the
+# records it must read once and the outputs it must write once.
+def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
+    K = 3 if dim == 2 else 7
+    s = 4
+    return {
+        "rows": n_cells * 1 + rows * 8,                          # tags + row runs
+        "iface": 2 * rows * 12 + ni * 9,                         # runs + counts / offsets; cell, geo, side
+        "scan": 8 * (rows + ni + ng),                            # three exclusive scans
+        "place": ni * 10,                                        # interface record + tag
+        "reclassify": 2 * ni * 9,                                # two passes over the interface
+        "ghost_flags": ni * 13,
+        "ghost_write": ni * 13 + ng * (12 + 12 + 8 + 8 * dim + 4),   # compaction + psi, n, meta
+        "poscell": 2 * ng * 12,
+        "deps": ng * (12 + 8 * dim + K + 4 * K + 4 * K + 4),
+        "levels": ng * (4 * K + 12),
+        "reorder": ng * 2 * (4 + 4 + 8 + 8 * dim + 4 + 4 * K + 4),
+        "tables": ng * (4 + 4 + 8 + 8 * dim + 4 + 2 * dim + 16 * 8 + (1 + (1 + K) + dim * (K + 1)) * 8),
+        "gsrc": ng * 32 + n_gsrc * 4,
+        "fill_chain": ng * F * (K * s + s + s) + ng * (4 + 4 + 4 * K + 2 * (K + 1) * 8),
+        "fill_level": ng * F * (K * s + s + s) + ng * (4 + 4 + 2 * (K + 1) * 8),
+        "forces": ng * (4 + 4 + 8 * dim + 4 + (2 + K + dim * (K + 1)) * 8 + s * (dim + 1) * (K + 1)),
+        "adj_seed": ng * (4 + 8 * dim + (2 + K + dim * (K + 1)) * 8 + F * (K + 1) * 8),
+        "adj_chain": ng * (4 + s * F) + n_gsrc * (4 + 4 + F * 8 + 16),
+        "adj_level": ng * (4 + s * F) + n_gsrc * (4 + 4 + F * 8 + 16),
+        "adj_fluid": ng * 12 + ng * K * (F * 8 + 8 + F * s) + ng * K * F * s,
+        "adj_bc": ng * (4 + 4 + 16 + 3 * F * s),
+    }
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from an ncu capture
+# of the same kernel on this workload (None until captured for the current
+# kernel version).
+TRAFFIC_PER_LAUNCH = {}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -303,7 +356,7 @@ def main():
     counts = R.counts()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
 
-    step = Step(R, fields, bcs, geoms, "persistent", adjoint=True)
+    step = Step(R, fields, bcs, geoms, "persistent", adjoint=True, overlap=True)
     for _ in range(max(args.warmup, 3)):
         step()
     R.sync_status()
@@ -341,7 +394,10 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     R.sync_status()
-    ms_step, total_updates = reduce_over_ranks(float(np.mean(ms)), updates, dev)
+    ms_med = float(np.median(ms))
+    ms_stats = {"mean": float(np.mean(ms)), "median": ms_med, "p10": float(np.percentile(ms, 10)),
+                "p90": float(np.percentile(ms, 90))}
+    ms_step, total_updates = reduce_over_ranks(ms_med, updates, dev)
     value = total_updates / (ms_step * 1e-3)
 
     # forward only (same graph construction)
@@ -353,7 +409,7 @@ def main():
         with torch.cuda.graph(gf, stream=side, capture_error_mode="relaxed"):
             step_f()
     torch.cuda.synchronize()
-    ms_f = float(np.mean(time_steps(gf.replay, max(5, args.steps // 2), stream, flush)))
+    ms_f = float(np.median(time_steps(gf.replay, max(5, args.steps // 2), stream, flush)))
 
     diag = R.diagnostics()
 
@@ -389,7 +445,7 @@ def main():
         step64 = Step(R, fields64, bcs64, geoms, "level", adjoint=True)
         step64()
         torch.cuda.synchronize()
-        ms64 = float(np.mean(time_steps(step64, max(3, args.steps // 5), stream, flush)))
+        ms64 = float(np.median(time_steps(step64, max(3, args.steps // 5), stream, flush)))
         del fields64, bcs64, step64
     except StopIteration:
         pass
@@ -418,32 +474,29 @@ def main():
         e2e_step()
         torch.cuda.synchronize()
         e2e_ms = time_steps(e2e_step, max(5, args.steps // 3), stream, flush)
-        e2e_val = total_updates / (np.mean(e2e_ms) * 1e-3)
+        e2e_val = total_updates / (np.median(e2e_ms) * 1e-3)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / duration
     peak, peak_kind = measured_peaks()
     n_cells = R.n_cells
     rows = sum(c2["n_cells"] // geoms[b]["grid"]["n"][0] for b, c2 in enumerate(counts))
     ni = sum(c2["n_interface"] for c2 in counts)
-    K = 3
-    algo = {
-        # tag stream: 1 byte per cell written + 8 B per row run
-        "rows": n_cells * 1 + rows * 8,
-        # fill: per update 3 stencil reads + BC + write (FP32), per ghost the
-        # record (cell 4, meta 4) and the weights (8 doubles per kind used)
-        "fill_chain": updates * 20 + ng * (8 + 2 * 8 * 8 + 4 * K),
-        "adj_chain": ng * (F * 4 + 8 * 8 * F) + ng * 4,
-        "place": ni * (4 + 4 + 1 + 8 + 24 + 1),
-    }
-    tb = algo.get(top)
-    if tb:
-        tb = tb / prof_n[top]                       # bytes per launch
-    achieved = (tb / (prof_ms[top] / prof_n[top] * 1e-3) / 1e9) if tb else None
-    roof = {"kernel": top, "bound": "hbm" if tb else "latency",
-            "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None,
-            "traffic": None, "peak_source": peak_kind,
-            "kernel_ms": {k: round(v, 5) for k, v in sorted(prof_ms.items(), key=lambda kv: -kv[1])}}
+    algo = algorithmic_bytes(n_cells, rows, ni, ng, diag["n_gsrc"], F, dim=2)
+    top = max(prof_ms, key=prof_ms.get)
+    per_kernel = {}
+    for k, v in sorted(prof_ms.items(), key=lambda kv: -kv[1]):
+        gbs = algo[k] / (v * 1e-3) / 1e9 if k in algo else None
+        per_kernel[k] = {"ms": round(v, 5), "launches": prof_n[k],
+                         "algo_bytes": algo.get(k), "gbs": round(gbs, 1) if gbs else None}
+    tb = algo[top] / prof_n[top]                      # bytes per launch
+    achieved = tb / (prof_ms[top] / prof_n[top] * 1e-3) / 1e9
+    roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(top),
+            "peak_source": peak_kind, "algo_bytes_per_launch": tb,
+            "timing": "CUDA events recorded as nodes of the captured step graph, mean of 5 replays, L2 flushed",
+            "step_algo_bytes": sum(algo.values()),
+            "step_frac": sum(algo.values()) / (ms_step * 1e-3) / 1e9 / peak,
+            "per_kernel": per_kernel}
 
     baseline = None
     if rank == 0 and not args.no_baseline and not args.lite:
@@ -451,7 +504,7 @@ def main():
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_step, "ms_stats_rank0": ms_stats, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 fields, f64 coefficients", "data": "synthetic",
         "config": {"workload": WORKLOAD, "geometries": args.geoms, "cells": n_cells, "ghosts": ng,
                    "fields": F, "placement": "HGC", "max_levels": max(c2["n_levels"] for c2 in counts),
@@ -462,7 +515,7 @@ def main():
         "plain_fp64_updates_per_s": total_updates / (ms64 * 1e-3) if ms64 == ms64 else None,
         "plain_fp64_ms_per_step": ms64,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": float(np.mean(e2e_ms))},
+                "ms_per_step": float(np.median(e2e_ms))},
         "gpu_launches": int(launches_per_step * args.steps),
         "graph_kernel_nodes_per_step": graph_kernels,
         "roofline": roof,

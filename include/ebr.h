@@ -160,7 +160,11 @@ ebr_status ebr_counts(const void* ctx, ebr_geom_counts* h_counts);
  * order (geometry, level, linear index).  Also validates every stencil member
  * (EBR_ESTENCIL_OOB / EBR_ESTENCIL_SOLID) and detects cycles (EBR_ECYCLE),
  * and builds the transposed incidence lists used by the adjoint.
- * Device-side failures are reported through the status word. */
+ * Device-side failures are reported through the status word.  After the first
+ * call the incidence lists are built on a second, library-owned stream that
+ * forks from and joins back into `stream` by events inside this call, so the
+ * call stays ordered on `stream` (and a stream capture records the two
+ * branches as parallel graph nodes). */
 ebr_status ebr_build_levels(void* ctx, ebr_stream stream);
 
 /* Ghost records in canonical order, copied to host arrays sized by the total
@@ -249,6 +253,43 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
                                    ebr_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Many fields in the field-minor layout (Sec. 3.2 fill and its transpose)
+ *
+ * One device array holds all n_fields values of a cell contiguously:
+ * element (cell c, field f) at index c * n_fields + f, c the flat cell index of
+ * ebr_layout().  This is the layout for a solver that carries many fields per
+ * cell (several velocity sets, species, ensemble members): the stencil gather
+ * of one ghost then reads n_fields consecutive values per member.
+ * 1 <= n_fields <= 1024; h_bc_kind: host int32 [n_fields], EBR_DIRICHLET or
+ * EBR_NEUMANN per field.  Same ghost set, levels and weights as
+ * ebr_reconstruct (closed forms of Secs. 4-5, one pass per ghost in level
+ * order); FP32 fields combine with the weights rounded to float.
+ * ------------------------------------------------------------------------- */
+
+/* Fill the ghost entries of d_fields (device, dtype, [total cells][n_fields])
+ * in place from the fluid entries and d_bc (device, dtype,
+ * [total ghosts][n_fields], canonical ghost order).  Other entries are not
+ * written.  A non-finite result sets EBR_ENONFINITE in the status word. */
+ebr_status ebr_reconstruct_packed(void* ctx, int32_t n_fields, void* d_fields,
+                                  const int32_t* h_bc_kind, const void* d_bc, int32_t dtype,
+                                  ebr_stream stream);
+
+/* Transpose of ebr_reconstruct_packed (vector-Jacobian product).
+ * d_cot (device, dtype, [total cells][n_fields], in/out): on entry dJ/dy for
+ * the filled field y; on exit dJ/dx for the field x before the fill: ghost
+ * entries set to 0 (the fill overwrites them), each fluid entry read by a
+ * ghost stencil incremented by sum_G w lambda_G, other entries unchanged.
+ * d_grad_bc (device, dtype, [total ghosts][n_fields]): written with dJ/d(bc).
+ * lambda (dJ/d ghost value, reverse level order) lives in library scratch of
+ * total ghosts * n_fields elements, allocated by the first call with a
+ * larger n_fields; that call must not be inside a stream capture (it returns
+ * EBR_EINVAL there).  Every output element is written by one thread in a
+ * fixed summation order: bitwise deterministic, no atomics. */
+ebr_status ebr_reconstruct_packed_adjoint(void* ctx, int32_t n_fields, const int32_t* h_bc_kind,
+                                          void* d_cot, void* d_grad_bc, int32_t dtype,
+                                          ebr_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Status
  * ------------------------------------------------------------------------- */
 
@@ -258,7 +299,9 @@ ebr_status ebr_sync_status(void* ctx, ebr_stream stream);
 /* Diagnostics (synchronises the stream): h_out[0] = x-rows whose solid run
  * the 4-cell windows could not confirm, so that the whole row was swept with
  * the exact predicate, accumulated since ebr_plan; h_out[1] = largest stencil
- * multiplier r_i; h_out[2] = kernel launches so far.  n = entries wanted. */
+ * multiplier r_i; h_out[2] = kernel launches so far; h_out[3] = entries of
+ * the ghost-target source lists of the adjoint (after ebr_build_levels).
+ * n = entries wanted. */
 ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stream);
 
 /* Number of kernel launches this context has issued since creation. */

@@ -57,6 +57,10 @@ _SIGS = {
                                           ctypes.POINTER(c_double), c_void_p,
                                           ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                                           c_int32, c_int32, c_int32, c_void_p]),
+    "ebr_reconstruct_packed": (c_int32, [c_void_p, c_int32, c_void_p, ctypes.POINTER(c_int32),
+                                         c_void_p, c_int32, c_void_p]),
+    "ebr_reconstruct_packed_adjoint": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32), c_void_p,
+                                                 c_void_p, c_int32, c_void_p]),
     "ebr_sync_status": (c_int32, [c_void_p, c_void_p]),
     "ebr_diagnostics": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_int32, c_void_p]),
     "ebr_launch_count": (c_int64, [c_void_p]),

@@ -170,13 +170,44 @@ class Reconstructor:
             1 if accumulate else 0, MODE[mode], self._stream()))
         return grad_fields, grad_bc
 
+    # -- many fields, field-minor layout [cells][F] ----------------------------
+    def reconstruct_packed(self, fields, bc_kinds, bc):
+        """Fill the ghost entries of `fields` ([cells, F], contiguous) in place;
+        `bc` is [ghosts, F] in canonical ghost order."""
+        F = int(fields.shape[1])
+        self._packed_check(fields, F, self.n_cells)
+        self._packed_check(bc, F, self.n_ghosts)
+        kinds = (ctypes.c_int32 * F)(*[int(k) for k in bc_kinds])
+        self._check(self.lib.ebr_reconstruct_packed(self.ctx, F, _ptr(fields), kinds, _ptr(bc),
+                                                    DTYPE[fields.dtype], self._stream()))
+        return fields
+
+    def reconstruct_packed_adjoint(self, bc_kinds, cot, grad_bc):
+        """Transpose of reconstruct_packed, in place on `cot` ([cells, F]):
+        dJ/d(filled field) in, dJ/d(field before the fill) out; `grad_bc`
+        ([ghosts, F]) receives dJ/d(boundary data)."""
+        F = int(cot.shape[1])
+        self._packed_check(cot, F, self.n_cells)
+        self._packed_check(grad_bc, F, self.n_ghosts)
+        kinds = (ctypes.c_int32 * F)(*[int(k) for k in bc_kinds])
+        self._check(self.lib.ebr_reconstruct_packed_adjoint(self.ctx, F, kinds, _ptr(cot), _ptr(grad_bc),
+                                                            DTYPE[cot.dtype], self._stream()))
+        return cot, grad_bc
+
+    def _packed_check(self, t, F, rows):
+        if t.dim() != 2 or not t.is_contiguous() or int(t.shape[1]) != F or t.device != self.device:
+            raise ValueError("packed arrays are contiguous [rows, F] tensors on %s" % self.device)
+        if rows is not None and int(t.shape[0]) != rows:
+            raise ValueError("packed field array needs %d rows (cells), got %d" % (rows, int(t.shape[0])))
+
     def sync_status(self):
         self._check(self.lib.ebr_sync_status(self.ctx, self._stream()))
 
     def diagnostics(self):
-        out = (ctypes.c_int64 * 3)()
-        self._check(self.lib.ebr_diagnostics(self.ctx, out, 3, self._stream()))
-        return {"row_fallbacks": int(out[0]), "r_max": int(out[1]), "launches": int(out[2])}
+        out = (ctypes.c_int64 * 4)()
+        self._check(self.lib.ebr_diagnostics(self.ctx, out, 4, self._stream()))
+        return {"row_fallbacks": int(out[0]), "r_max": int(out[1]), "launches": int(out[2]),
+                "n_gsrc": int(out[3])}
 
     def profile(self, enable=True):
         self._check(self.lib.ebr_profile(self.ctx, 1 if enable else 0))

@@ -7,7 +7,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libebr.so")
-SOURCES = ["api.cu", "classify.cu", "levels.cu", "scan.cu", "fill.cu", "forces.cu", "adjoint.cu"]
+SOURCES = ["api.cu", "classify.cu", "levels.cu", "scan.cu", "fill.cu", "forces.cu", "adjoint.cu",
+           "packed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

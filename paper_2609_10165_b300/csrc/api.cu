@@ -97,6 +97,10 @@ struct Ctx {
   void* lam = nullptr;
 
   std::vector<int> order_by_size;            // geometries, largest ghost count first
+  int* d_deep_list = nullptr;                // geometries with ghosts, deepest chain first
+  int n_deep = 0;
+  void* lamP = nullptr;                      // packed adjoint scratch [ng][F]
+  size_t lamP_bytes = 0;
   std::map<long long, ChainPlan> chain_plans;
 
   // optional per-kernel timing: events recorded on the launching stream
@@ -108,6 +112,11 @@ struct Ctx {
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
+
+  // second stream for independent branches inside one call (fork / join by
+  // events, so that a stream capture records them as parallel graph branches)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 cudaEvent_t take_event(Ctx* c) {
@@ -208,11 +217,31 @@ void free_all(Ctx* c) {
   c->recs.clear();
   for (auto& b : c->bufs) cudaFree(b.p);
   c->bufs.clear();
+  c->lamP = nullptr;
+  c->lamP_bytes = 0;
+  c->d_deep_list = nullptr;
+  c->n_deep = 0;
   for (auto& kv : c->chain_plans) (void)kv;
   c->chain_plans.clear();
 }
 
 cudaStream_t S(ebr_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+ebr_status ensure_side(Ctx* c) {
+  if (c->side) return EBR_OK;
+  CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  return EBR_OK;
+}
+
+void destroy_side(Ctx* c) {
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
+  c->side = nullptr;
+  c->ev_fork = c->ev_join = nullptr;
+}
 
 // k_check: compare scanned offsets at geometry boundaries with the plan
 __global__ void k_check(const Geom* G, int B, const int* row_ptr, const int* gpos, int n_iface,
@@ -420,18 +449,29 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   prof_begin(c, s, "poscell");
   launch_poscell(c->dG, ng, c->g_cell, c->g_geo, nullptr, c->pos_of_cell, s);
   prof_end(c, s);
+  // The coefficient tables and the ghost-target source lists (adjoint only)
+  // are independent: outside planning the source lists run on the second
+  // stream, joined before the call returns.
+  cudaStream_t sg = s;
+  if (!planning) {
+    ebr_status st = ensure_side(c);
+    if (st) return st;
+    CK(cudaEventRecord(c->ev_fork, s));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    sg = c->side;
+  }
   prof_begin(c, s, "tables");
   launch_tables(c->dG, ng, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->tags, c->wtab,
                 c->ftab, s);
   prof_end(c, s);
   // ghost-target sources
-  prof_begin(c, s, "gsrc");
+  prof_begin(c, sg, "gsrc");
   launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax, nullptr,
-              c->gsrc_cnt, 0, s);
-  prof_end(c, s);
-  prof_begin(c, s, "scan");
-  launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, s);
-  prof_end(c, s);
+              c->gsrc_cnt, 0, sg);
+  prof_end(c, sg);
+  prof_begin(c, sg, "scan");
+  launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, sg);
+  prof_end(c, sg);
   c->launches += 7;
   CKL();
   if (planning) {
@@ -446,12 +486,16 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     }
     AL(c->gsrc, c->n_gsrc);
   }
-  prof_begin(c, s, "gsrc");
+  prof_begin(c, sg, "gsrc");
   launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
-              c->gsrc_ptr, c->gsrc, 1, s);
-  prof_end(c, s);
+              c->gsrc_ptr, c->gsrc, 1, sg);
+  prof_end(c, sg);
   c->launches += 1;
   CKL();
+  if (!planning) {
+    CK(cudaEventRecord(c->ev_join, c->side));
+    CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+  }
   if (planning) {
     // force chunks (<= 256 ghosts, never straddling geometries)
     std::vector<int4> ch;
@@ -473,6 +517,18 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     for (int b = 0; b < c->B; ++b) c->order_by_size[b] = b;
     std::stable_sort(c->order_by_size.begin(), c->order_by_size.end(),
                      [&](int a, int b) { return c->hG[a].n_ghost > c->hG[b].n_ghost; });
+    // packed kernels: one CTA row per geometry, longest dependency chain first
+    std::vector<int> deep;
+    for (int b = 0; b < c->B; ++b)
+      if (c->hG[b].n_ghost > 0) deep.push_back(b);
+    std::stable_sort(deep.begin(), deep.end(), [&](int a, int b) {
+      const Geom &A = c->hG[a], &Bg = c->hG[b];
+      return A.n_levels != Bg.n_levels ? A.n_levels > Bg.n_levels : A.n_ghost > Bg.n_ghost;
+    });
+    c->n_deep = (int)deep.size();
+    AL(c->d_deep_list, std::max<size_t>(deep.size(), 1));
+    if (!deep.empty())
+      CK(cudaMemcpy(c->d_deep_list, deep.data(), sizeof(int) * deep.size(), cudaMemcpyHostToDevice));
   }
   return EBR_OK;
 }
@@ -529,6 +585,7 @@ void ebr_destroy(void* ctx) {
   if (!ctx) return;
   Ctx* c = static_cast<Ctx*>(ctx);
   free_all(c);
+  destroy_side(c);
   delete c;
 }
 
@@ -862,6 +919,84 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
   return EBR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// many fields, field-minor layout
+// ---------------------------------------------------------------------------
+static ebr_status packed_args(Ctx* c, const char* who, int32_t n_fields, const int32_t* h_bc_kind,
+                              int32_t dtype, KindBits* kb) {
+  if (!c->levelled) return fail(c, EBR_EINVAL, "%s: build the levels first", who);
+  if (n_fields < 1 || n_fields > PACKED_MAX_FIELDS || !h_bc_kind)
+    return fail(c, EBR_EINVAL, "%s: 1..%d fields with kinds required", who, PACKED_MAX_FIELDS);
+  if (dtype != EBR_F32 && dtype != EBR_F64) return fail(c, EBR_EINVAL, "%s: bad dtype", who);
+  std::memset(kb, 0, sizeof(KindBits));
+  for (int f = 0; f < n_fields; ++f) {
+    if (h_bc_kind[f] != 0 && h_bc_kind[f] != 1) return fail(c, EBR_EINVAL, "%s: bad bc kind", who);
+    if (h_bc_kind[f]) kb->w[f >> 5] |= 1u << (f & 31);
+  }
+  return EBR_OK;
+}
+
+ebr_status ebr_reconstruct_packed(void* ctx, int32_t n_fields, void* d_fields,
+                                  const int32_t* h_bc_kind, const void* d_bc, int32_t dtype,
+                                  ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  KindBits kb;
+  ebr_status st = packed_args(c, "ebr_reconstruct_packed", n_fields, h_bc_kind, dtype, &kb);
+  if (st) return st;
+  if (!d_fields || !d_bc) return fail(c, EBR_EINVAL, "ebr_reconstruct_packed: null field or boundary data");
+  cudaStream_t s = S(stream);
+  prof_begin(c, s, "pfill");
+  launch_pfill(dtype, n_fields, d_fields, d_bc, kb, c->dG, c->d_deep_list, c->n_deep, c->g_cell,
+               c->g_meta, c->lev_ptr, c->wtab, c->ng, c->d_status, s);
+  prof_end(c, s);
+  c->launches += c->n_deep > 0 ? 1 : 0;
+  CKL();
+  return EBR_OK;
+}
+
+ebr_status ebr_reconstruct_packed_adjoint(void* ctx, int32_t n_fields, const int32_t* h_bc_kind,
+                                          void* d_cot, void* d_grad_bc, int32_t dtype,
+                                          ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  KindBits kb;
+  ebr_status st = packed_args(c, "ebr_reconstruct_packed_adjoint", n_fields, h_bc_kind, dtype, &kb);
+  if (st) return st;
+  if (!d_cot || !d_grad_bc) return fail(c, EBR_EINVAL, "ebr_reconstruct_packed_adjoint: null cotangent or gradient");
+  cudaStream_t s = S(stream);
+  size_t need = (size_t)std::max(c->ng, 1) * n_fields * (dtype == EBR_F32 ? 4 : 8);
+  if (need > c->lamP_bytes) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(c, EBR_EINVAL, "ebr_reconstruct_packed_adjoint: first call with %d fields must precede stream capture (it sizes scratch)", n_fields);
+    void* q = nullptr;
+    st = balloc(c, &q, need);
+    if (st) return st;
+    c->lamP = q;
+    c->lamP_bytes = need;
+  }
+  const int dim = c->hG[0].dim;
+  for (int b = 1; b < c->B; ++b)
+    if (c->hG[b].dim != dim) return fail(c, EBR_EINVAL, "ebr_reconstruct_packed_adjoint: mixed dimensions");
+  prof_begin(c, s, "padj_chain");
+  launch_padj(dtype, n_fields, d_cot, c->lamP, d_grad_bc, kb, c->dG, c->d_deep_list, c->n_deep, c->ng,
+              stencil_k(dim), c->g_geo, c->g_cell, c->g_meta, c->lev_ptr, c->gsrc_ptr, c->gsrc, c->tags,
+              c->pos_of_cell, c->rmax, c->wtab, s, 0);
+  prof_end(c, s);
+  prof_begin(c, s, "padj_fluid");
+  launch_padj(dtype, n_fields, d_cot, c->lamP, d_grad_bc, kb, c->dG, c->d_deep_list, c->n_deep, c->ng,
+              stencil_k(dim), c->g_geo, c->g_cell, c->g_meta, c->lev_ptr, c->gsrc_ptr, c->gsrc, c->tags,
+              c->pos_of_cell, c->rmax, c->wtab, s, 1);
+  prof_end(c, s);
+  c->launches += c->ng > 0 ? 2 : 0;
+  CKL();
+  return EBR_OK;
+}
+
 ebr_status ebr_profile(void* ctx, int32_t enable) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
@@ -918,6 +1053,7 @@ ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stre
   if (n > 0) h_out[0] = st[0];
   if (n > 1) h_out[1] = c->rmax;
   if (n > 2) h_out[2] = c->launches;
+  if (n > 3) h_out[3] = c->n_gsrc;
   return EBR_OK;
 }
 

@@ -62,13 +62,14 @@ __host__ __device__ inline uint32_t meta_depmask(uint32_t m) { return (m >> 23) 
 // Offsets of P_1..P_K in units of r_a e_a h_a (Secs. 4 and 5, Appendix A).
 __host__ __device__ inline int stencil_k(int dim) { return dim == 2 ? 3 : 7; }
 __host__ __device__ inline void stencil_off(int dim, int k, int o[3]) {
-  if (dim == 2) {
-    const int t[3][2] = {{1, 0}, {0, 1}, {1, 1}};
-    o[0] = t[k][0]; o[1] = t[k][1]; o[2] = 0;
-  } else {
-    const int t[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 1}};
-    o[0] = t[k][0]; o[1] = t[k][1]; o[2] = t[k][2];
-  }
+  // 3 bits (x, y, z) per member: 2D P1..P3 = (1,0), (0,1), (1,1);
+  // 3D P1..P7 = (1,0,0), (0,1,0), (0,0,1), (1,1,0), (0,1,1), (1,0,1), (1,1,1)
+  const unsigned code = dim == 2 ? (1u | 2u << 3 | 3u << 6)
+                                 : (1u | 2u << 3 | 4u << 6 | 3u << 9 | 6u << 12 | 5u << 15 | 7u << 18);
+  unsigned v = code >> (3 * k);
+  o[0] = v & 1u;
+  o[1] = (v >> 1) & 1u;
+  o[2] = (v >> 2) & 1u;
 }
 
 // Cell centre along axis a, evaluated without contraction.

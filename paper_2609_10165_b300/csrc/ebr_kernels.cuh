@@ -18,6 +18,12 @@ __device__ inline int find_seg(const int* off, int B, int x) {
   return lo;
 }
 
+// kind (0 Dirichlet, 1 Neumann) of field f of a packed field array: bit f
+struct KindBits {
+  uint32_t w[32];
+};
+constexpr int PACKED_MAX_FIELDS = 1024;
+
 // ---- classify.cu
 void launch_rows(const Geom* G, const int* row_off, int B, int total_rows, int2* runs,
                  int8_t* tags, int* status, int* stats, cudaStream_t s);
@@ -100,5 +106,17 @@ void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* 
 void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                    const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,
                    void* const* grad, int accumulate, cudaStream_t s);
+
+// ---- packed.cu (field-minor layout [cells][F])
+void launch_pfill(int dtype, int F, void* fld, const void* bc, const KindBits& kb, const Geom* G,
+                  const int* geo_list, int n_list, const int* g_cell, const uint32_t* g_meta,
+                  const int* lev_ptr, const double* wtab, int ng, int* status, cudaStream_t s);
+// phase 0: reverse-level chain (lambda, boundary-data gradients, ghost
+// cotangents cleared); phase 1: fluid targets
+void launch_padj(int dtype, int F, void* cot, void* lamP, void* gbc, const KindBits& kb,
+                 const Geom* G, const int* geo_list, int n_list, int ng, int kmax, const int* g_geo,
+                 const int* g_cell, const uint32_t* g_meta, const int* lev_ptr, const int* gsrc_ptr,
+                 const int* gsrc, const int8_t* tags, const int* pos_of_cell, int R,
+                 const double* wtab, cudaStream_t s, int phase);
 
 }  // namespace ebr
