@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--geoms", type=int, default=256)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--sets", type=int, default=32, help="field sets of the throughput mode (0: skip)")
     ap.add_argument("--lite", action="store_true",
                     help="headline step only (no plain FP64 path, no e2e, no CPU baseline), for profilers")
     return ap.parse_args()
@@ -333,6 +334,136 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
 TRAFFIC_PER_LAUNCH = {}
 
 
+def unique_fluid_targets(R, info, dim=2):
+    """Active (ghost, member) incidences whose member is a fluid cell, and the
+    number of distinct such cells (host count from the ghost records: member
+    k is active when n_a != 0 on every axis it is offset along)."""
+    tags = R.tags.cpu().numpy()
+    off = np.asarray(R.cell_offset)
+    geom, cell, r, nrm = info["geom"], info["cell"], info["r"], info["normal"]
+    nx = np.array([R._grids[b].n[0] for b in range(R.B)], dtype=np.int64)[geom]
+    e = np.where(nrm[:, :dim] < 0.0, -1, 1)
+    offs = [(1, 0), (0, 1), (1, 1)]
+    targets, n_inc = [], 0
+    for ox, oy in offs:
+        act = np.ones(cell.size, bool)
+        if ox:
+            act &= nrm[:, 0] != 0.0
+        if oy:
+            act &= nrm[:, 1] != 0.0
+        t = off[geom] + cell + ox * r[:, 0] * e[:, 0] + nx * (oy * r[:, 1] * e[:, 1])
+        fl = act & (tags[np.clip(t, 0, tags.size - 1)] == 0)
+        n_inc += int(fl.sum())
+        targets.append(t[fl])
+    return n_inc, int(np.unique(np.concatenate(targets)).size)
+
+
+def throughput_mode(R, info, fields, bcs, kinds3, flush, stream, steps, warmup, peak, n_sets=32):
+    """Many fields per cell in the field-minor layout: n_sets copies of the
+    (u, v, p) set (scaled), 3 n_sets FP32 fields, fill + transpose of the fill
+    per step on the classified batch (the geometry part is not repeated)."""
+    import torch
+    dev = R.device
+    F = 3 * n_sets
+    kinds = list(kinds3) * n_sets
+    scale = torch.tensor([1.0 + 0.01 * k for k in range(n_sets) for _ in range(3)], device=dev)
+    P = torch.stack([fields[f % 3] for f in range(F)], dim=1).mul_(scale)
+    Pbc = torch.stack([bcs[f % 3] for f in range(F)], dim=1).mul_(scale)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2609)
+    C = torch.randn((R.n_cells, F), generator=gen, device=dev, dtype=torch.float32)
+    Gbc = torch.empty((Pbc.shape[0], F), device=dev, dtype=torch.float32)
+    side = torch.cuda.Stream(dev)
+
+    def step(adjoint=True):
+        if adjoint:
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                R.reconstruct_packed_adjoint(kinds, C, Gbc)
+        R.reconstruct_packed(P, kinds, Pbc)
+        if adjoint:
+            torch.cuda.current_stream().wait_stream(side)
+
+    graphs = {}
+    cap = torch.cuda.Stream(dev)
+    for adj in (True, False):
+        step(adj)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(g, stream=cap, capture_error_mode="relaxed"):
+                step(adj)
+        torch.cuda.synchronize()
+        graphs[adj] = g
+    for _ in range(warmup):
+        graphs[True].replay()
+    torch.cuda.synchronize()
+    R.sync_status()
+    ms = time_steps(graphs[True].replay, steps, stream, flush)
+    ms_f = time_steps(graphs[False].replay, max(5, steps // 2), stream, flush)
+    R.sync_status()
+    # per-kernel device times inside a captured step
+    R.profile(True)
+    gp = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(gp, stream=cap, capture_error_mode="relaxed"):
+            step(True)
+    torch.cuda.synchronize()
+    R.profile(False)
+    prof = {}
+    for _ in range(5):
+        flush.zero_()
+        gp.replay()
+        torch.cuda.synchronize()
+        for k, (v, n) in R.profile_read(keep=True).items():
+            prof[k] = (prof.get(k, (0.0, n))[0] + v / 5, n)
+    R.profile_read(keep=False)
+    del gp, graphs
+    ng = int(Pbc.shape[0])
+    n_inc, n_tgt = unique_fluid_targets(R, info)
+    diag = R.diagnostics()
+    s = 4
+    K = 3
+    # algorithmic bytes per call (2D, FP32): forward per update K stencil
+    # reads + boundary datum + ghost write, per ghost its record (cell, meta)
+    # and the weights of both kinds; adjoint per update the ghost cotangent
+    # read and cleared and dJ/db written, every fluid target read and written
+    # once per field, per ghost the record and the weights
+    algo = {
+        "pfill": ng * F * (K * s + s + s) + ng * (8 + 2 * (K + 1) * 8),
+        "padj": ng * F * 3 * s + n_tgt * F * 2 * s + ng * (8 + 2 * (K + 1) * 8) + diag["n_gsrc"] * 4,
+    }
+    groups = {"pfill": ("pfill_part", "pfill_lvl", "pfill_tail"),
+              "padj": ("padj_tail", "padj_lvl", "padj_fluid")}
+    med = float(np.median(ms))
+    med_f = float(np.median(ms_f))
+    per = {k: {"ms": round(v, 5), "launches": n} for k, (v, n) in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    call_ms = {gname: sum(prof[k][0] for k in ks if k in prof) for gname, ks in groups.items()}
+    for gname in algo:
+        per[gname] = {"ms": round(call_ms[gname], 5), "algo_bytes": algo[gname],
+                      "gbs": round(algo[gname] / (call_ms[gname] * 1e-3) / 1e9, 1) if call_ms[gname] else None}
+    top = max(algo, key=lambda k: call_ms[k])
+    ach = algo[top] / (call_ms[top] * 1e-3) / 1e9
+    step_bytes = sum(algo.values())
+    out = {
+        "fields": F, "field_sets": n_sets, "layout": "field-minor [cells][fields], FP32",
+        "updates_per_step": ng * F, "value": ng * F / (med * 1e-3), "unit": "updates/s",
+        "ms_per_step": med, "p10_ms": float(np.percentile(ms, 10)), "p90_ms": float(np.percentile(ms, 90)),
+        "fwd_value": ng * F / (med_f * 1e-3), "fwd_ms_per_step": med_f,
+        "step_algo_bytes": step_bytes, "step_gbs": step_bytes / (med * 1e-3) / 1e9,
+        "step_frac": step_bytes / (med * 1e-3) / 1e9 / peak,
+        "fluid_incidences": n_inc, "unique_fluid_targets": n_tgt, "schedule": diag["packed"],
+        "roofline": {"kernel": top, "launches": "all launches of the call", "bound": "hbm",
+                     "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": TRAFFIC_PER_LAUNCH.get(top), "algo_bytes_per_call": algo[top]},
+        "per_kernel": per,
+        "l2": "flushed before every timed step (512 MB write)",
+    }
+    del P, Pbc, C, Gbc
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -435,6 +566,12 @@ def main():
     del gp
     top = max(prof_ms, key=prof_ms.get)
 
+    # throughput mode: many fields per cell, field-minor layout
+    tput = None
+    if args.sets > 0:
+        tput = throughput_mode(R, info, fields, bcs, geoms[0]["bc"], flush, stream, args.steps,
+                               max(args.warmup, 3), measured_peaks()[0], n_sets=args.sets)
+
     # plain FP64 path: one launch per level per geometry, FP64 fields, no graph
     ms64 = float("nan")
     try:
@@ -519,6 +656,7 @@ def main():
         "gpu_launches": int(launches_per_step * args.steps),
         "graph_kernel_nodes_per_step": graph_kernels,
         "roofline": roof,
+        "throughput_mode": tput,
         "clocks": clk,
         "cpu_baseline": baseline,
         "wall_s_timed": t_wall,

@@ -300,7 +300,10 @@ ebr_status ebr_sync_status(void* ctx, ebr_stream stream);
  * the 4-cell windows could not confirm, so that the whole row was swept with
  * the exact predicate, accumulated since ebr_plan; h_out[1] = largest stencil
  * multiplier r_i; h_out[2] = kernel launches so far; h_out[3] = entries of
- * the ghost-target source lists of the adjoint (after ebr_build_levels).
+ * the ghost-target source lists of the adjoint (after ebr_build_levels);
+ * h_out[4..10] = schedule of the field-minor kernels (0 before their first
+ * call): last grid-wide level of the fill and of its transpose, geometries
+ * with a level tail in each, largest tail of each (ghosts), fluid targets.
  * n = entries wanted. */
 ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stream);
 

@@ -26,8 +26,9 @@ Reconstruction: A Non-Iterative Approach for Embedded-Boundary Methods"):
                       normal_derivative_trilinear, derivative_trilinear_x/y/z)
                       and the pressure / viscous force sums.
 * ``adjoint``      -- gradient of (drag, lift) with respect to the fluid field
-                      values and the boundary data, from the explicit sparse
-                      matrix of the (linear) map.
+                      values and the boundary data, and the vector-Jacobian
+                      product of the fill, from the explicit sparse matrix of
+                      the (linear) map.
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
 the force quadrature weights, which the paper does not specify ("parity
@@ -40,7 +41,7 @@ from .levels import build_levels, Levels
 from .reconstruct import (fill, ghost_weights, ghost_value, vandermonde_ghost_value,
                           DIRICHLET, NEUMANN)
 from .surface import boundary_quantities, forces, face_weights
-from .adjoint import adjoint_gradient, linear_map
+from .adjoint import adjoint_gradient, fill_vjp, linear_map
 
 __all__ = [
     "Grid", "Body", "closest_point", "inside",
@@ -49,5 +50,5 @@ __all__ = [
     "fill", "ghost_weights", "ghost_value", "vandermonde_ghost_value",
     "DIRICHLET", "NEUMANN",
     "boundary_quantities", "forces", "face_weights",
-    "adjoint_gradient", "linear_map",
+    "adjoint_gradient", "fill_vjp", "linear_map",
 ]

@@ -102,6 +102,39 @@ def force_coefficients(cls, lev, n_fields, p_id, vel_ids, mu, dirs, seed):
     return cgv, cxv
 
 
+def fill_vjp(cls, lev, bc_kinds, ybar):
+    """Vector-Jacobian product of the in-place fill (Sec. 3.2 with the closed
+    forms of Secs. 4-5): the fill maps (x, b) to y with y = x on non-ghost
+    cells and y_g = g on ghost cells, g = (I - A_gg)^-1 (A_gx x + A_gb b).
+    Given ybar [F][N] (dJ/dy) returns (xbar [F][N], bbar [F][N_g] canonical):
+        (I - A_gg)^T lambda = ybar on the ghosts,
+        xbar = ybar + A_gx^T lambda, with xbar = 0 on the ghost cells,
+        bbar = A_gb^T lambda."""
+    kinds = sorted(set(int(k) for k in bc_kinds))
+    by_kind = dict(zip(kinds, linear_map(cls, lev, kinds)))
+    ng = cls.n_ghosts
+    pos = lev.position()
+    cells = np.zeros(ng, dtype=np.int64)
+    cells[pos] = cls.idx                      # ghost cell of canonical position q
+    I = sp.identity(ng, format="csc")
+    xbar, bbar = [], []
+    for f, kind in enumerate(bc_kinds):
+        Agg, Agx, Agb = by_kind[int(kind)]
+        y = np.asarray(ybar[f], dtype=np.float64)
+        yg = y[cells]
+        if ng > 1:
+            lam = np.atleast_1d(spla.spsolve((I - Agg).T.tocsc(), yg))
+        elif ng == 1:
+            lam = yg / (1.0 - Agg.toarray()[0, 0])
+        else:
+            lam = np.zeros(0)
+        xb = y + Agx.T @ lam
+        xb[cells] = 0.0
+        xbar.append(xb)
+        bbar.append(Agb.T @ lam)
+    return xbar, bbar
+
+
 def adjoint_gradient(cls, lev, bc_kinds, p_id, vel_ids, mu, dirs, seed):
     """(grad_fields [F][N], grad_bc [F][N_g] canonical order) of
     J = seed[0] drag + seed[1] lift."""

@@ -204,10 +204,14 @@ class Reconstructor:
         self._check(self.lib.ebr_sync_status(self.ctx, self._stream()))
 
     def diagnostics(self):
-        out = (ctypes.c_int64 * 4)()
-        self._check(self.lib.ebr_diagnostics(self.ctx, out, 4, self._stream()))
+        out = (ctypes.c_int64 * 11)()
+        self._check(self.lib.ebr_diagnostics(self.ctx, out, 11, self._stream()))
         return {"row_fallbacks": int(out[0]), "r_max": int(out[1]), "launches": int(out[2]),
-                "n_gsrc": int(out[3])}
+                "n_gsrc": int(out[3]),
+                "packed": {"grid_levels_fill": int(out[4]), "grid_levels_adjoint": int(out[5]),
+                           "tail_geometries_fill": int(out[6]), "tail_geometries_adjoint": int(out[7]),
+                           "largest_tail_fill": int(out[8]), "largest_tail_adjoint": int(out[9]),
+                           "fluid_targets": int(out[10])}}
 
     def profile(self, enable=True):
         self._check(self.lib.ebr_profile(self.ctx, 1 if enable else 0))

@@ -97,8 +97,7 @@ struct Ctx {
   void* lam = nullptr;
 
   std::vector<int> order_by_size;            // geometries, largest ghost count first
-  int* d_deep_list = nullptr;                // geometries with ghosts, deepest chain first
-  int n_deep = 0;
+  PackedPlan pplan;                          // schedule of the packed kernels
   void* lamP = nullptr;                      // packed adjoint scratch [ng][F]
   size_t lamP_bytes = 0;
   std::map<long long, ChainPlan> chain_plans;
@@ -219,8 +218,7 @@ void free_all(Ctx* c) {
   c->bufs.clear();
   c->lamP = nullptr;
   c->lamP_bytes = 0;
-  c->d_deep_list = nullptr;
-  c->n_deep = 0;
+  c->pplan = PackedPlan();
   for (auto& kv : c->chain_plans) (void)kv;
   c->chain_plans.clear();
 }
@@ -517,18 +515,6 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     for (int b = 0; b < c->B; ++b) c->order_by_size[b] = b;
     std::stable_sort(c->order_by_size.begin(), c->order_by_size.end(),
                      [&](int a, int b) { return c->hG[a].n_ghost > c->hG[b].n_ghost; });
-    // packed kernels: one CTA row per geometry, longest dependency chain first
-    std::vector<int> deep;
-    for (int b = 0; b < c->B; ++b)
-      if (c->hG[b].n_ghost > 0) deep.push_back(b);
-    std::stable_sort(deep.begin(), deep.end(), [&](int a, int b) {
-      const Geom &A = c->hG[a], &Bg = c->hG[b];
-      return A.n_levels != Bg.n_levels ? A.n_levels > Bg.n_levels : A.n_ghost > Bg.n_ghost;
-    });
-    c->n_deep = (int)deep.size();
-    AL(c->d_deep_list, std::max<size_t>(deep.size(), 1));
-    if (!deep.empty())
-      CK(cudaMemcpy(c->d_deep_list, deep.data(), sizeof(int) * deep.size(), cudaMemcpyHostToDevice));
   }
   return EBR_OK;
 }
@@ -922,12 +908,142 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
 // ---------------------------------------------------------------------------
 // many fields, field-minor layout
 // ---------------------------------------------------------------------------
+// Packed schedule: L0 = the last level in which some geometry has more than
+// PACKED_TAIL_MAX ghosts; levels 1..L0 become grid-wide ghost lists, the
+// geometries with more levels form the tail (deepest first).
+static ebr_status packed_plan(Ctx* c, cudaStream_t s, const char* who) {
+  if (c->pplan.built) return EBR_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(c, EBR_EINVAL, "%s: the first packed call must precede stream capture (it plans the schedule)", who);
+  PackedPlan pp;
+  int maxlev = 0;
+  for (int b = 0; b < c->B; ++b) maxlev = std::max(maxlev, c->hG[b].n_levels);
+  std::vector<int> mx(maxlev + 2, 0);
+  for (int b = 0; b < c->B; ++b) {
+    const Geom& g = c->hG[b];
+    for (int lv = 1; lv <= g.n_levels; ++lv)
+      mx[lv] = std::max(mx[lv], c->h_lev_ptr[g.lev_off + lv] - c->h_lev_ptr[g.lev_off + lv - 1]);
+  }
+  pp.L0 = 1;
+  pp.L0a = 1;
+  for (int lv = 2; lv <= maxlev; ++lv) {
+    if (mx[lv] > PACKED_TAIL_MAX) pp.L0 = lv;
+    if (mx[lv] > PACKED_TAIL_MAX_ADJ) pp.L0a = lv;
+  }
+  const int Lmax = std::max(pp.L0, pp.L0a);
+  std::vector<int> lst;
+  pp.h_lvl_off.assign(Lmax + 1, 0);
+  for (int lv = 1; lv <= Lmax; ++lv) {
+    for (int b = 0; b < c->B; ++b) {
+      const Geom& g = c->hG[b];
+      if (lv > g.n_levels) continue;
+      for (int q = c->h_lev_ptr[g.lev_off + lv - 1]; q < c->h_lev_ptr[g.lev_off + lv]; ++q) lst.push_back(q);
+    }
+    pp.h_lvl_off[lv] = (int)lst.size();
+  }
+  std::vector<int> tail, tail_a;
+  for (int b = 0; b < c->B; ++b) {
+    if (c->hG[b].n_levels > pp.L0) tail.push_back(b);
+    if (c->hG[b].n_levels > pp.L0a) tail_a.push_back(b);
+  }
+  auto deeper = [&](int a, int b) { return c->hG[a].n_levels > c->hG[b].n_levels; };
+  std::stable_sort(tail.begin(), tail.end(), deeper);
+  std::stable_sort(tail_a.begin(), tail_a.end(), deeper);
+  pp.n_tail = (int)tail.size();
+  pp.n_tail_a = (int)tail_a.size();
+  AL(pp.d_tail_a, std::max<size_t>(tail_a.size(), 1));
+  if (!tail_a.empty())
+    CK(cudaMemcpy(pp.d_tail_a, tail_a.data(), sizeof(int) * tail_a.size(), cudaMemcpyHostToDevice));
+  AL(pp.d_lvl, std::max<size_t>(lst.size(), 1));
+  AL(pp.d_tail, std::max<size_t>(tail.size(), 1));
+  if (!lst.empty()) CK(cudaMemcpy(pp.d_lvl, lst.data(), sizeof(int) * lst.size(), cudaMemcpyHostToDevice));
+  if (!tail.empty()) CK(cudaMemcpy(pp.d_tail, tail.data(), sizeof(int) * tail.size(), cudaMemcpyHostToDevice));
+  const int ng = c->ng;
+  const int kmax = stencil_k(c->hG[0].dim);
+  // consumer lists of the ghosts
+  AL(pp.cons_ptr, ng + 1);
+  int* tmp_cnt = nullptr;
+  AL(tmp_cnt, std::max<long long>((long long)ng * kmax, 1) + 1);
+  launch_packed_plan_cons(ng, c->gsrc_ptr, c->gsrc, c->g_meta, nullptr, tmp_cnt, s);
+  launch_scan(tmp_cnt, pp.cons_ptr, ng, c->scan_tmp, s);
+  CKL();
+  int n_cons = 0;
+  CK(cudaMemcpyAsync(&n_cons, pp.cons_ptr + ng, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  AL(pp.cons, std::max(n_cons, 1));
+  launch_packed_plan_cons(ng, c->gsrc_ptr, c->gsrc, c->g_meta, pp.cons_ptr, pp.cons, s);
+  // fluid targets: owner flags and source counts per incidence, two scans
+  const long long ninc = (long long)ng * kmax;
+  if (ninc >= (1LL << 26)) return fail(c, EBR_EINVAL, "%s: too many ghost incidences for the packed plan", who);
+  int *flag = nullptr, *tpos = nullptr, *epos = nullptr;
+  AL(flag, ninc + 1);
+  AL(tpos, ninc + 1);
+  AL(epos, ninc + 1);
+  launch_packed_plan_ftgt(ng, kmax, c->dG, c->g_geo, c->g_cell, c->g_meta, c->tags, c->pos_of_cell,
+                          c->rmax, flag, tmp_cnt, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+  launch_scan(flag, tpos, (int)ninc, c->scan_tmp, s);
+  launch_scan(tmp_cnt, epos, (int)ninc, c->scan_tmp, s);
+  CKL();
+  int tot[2] = {0, 0};
+  CK(cudaMemcpyAsync(&tot[0], tpos + ninc, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&tot[1], epos + ninc, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  pp.n_ft = tot[0];
+  AL(pp.ft_cell, std::max(tot[0], 1));
+  AL(pp.ft_ptr, tot[0] + 1);
+  AL(pp.ft_src, std::max(tot[1], 1));
+  launch_packed_plan_ftgt(ng, kmax, c->dG, c->g_geo, c->g_cell, c->g_meta, c->tags, c->pos_of_cell,
+                          c->rmax, nullptr, nullptr, tpos, epos, pp.ft_cell, pp.ft_ptr, pp.ft_src, s);
+  CKL();
+  CK(cudaMemcpyAsync(pp.ft_ptr + tot[0], &tot[1], sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  pp.built = true;
+  c->pplan = pp;
+  return EBR_OK;
+}
+
+// item records of the packed kernels for one field type (once per plan)
+static ebr_status packed_records(Ctx* c, cudaStream_t s, int dtype, const char* who) {
+  PackedPlan& pp = c->pplan;
+  if (pp.rec_built[dtype]) return EBR_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(c, EBR_EINVAL, "%s: the first packed call of a field type must precede stream capture", who);
+  const int dim = c->hG[0].dim, ng = c->ng;
+  AL(pp.rec_fwd[dtype], std::max<size_t>((size_t)ng * packed_rec_words(dtype, dim, 0), 1));
+  AL(pp.rec_adj[dtype], std::max<size_t>((size_t)ng * packed_rec_words(dtype, dim, 1), 1));
+  AL(pp.rec_fl[dtype], std::max<size_t>((size_t)pp.n_ft * packed_rec_words(dtype, dim, 1), 1));
+  launch_packed_records(dtype, dim, c->dG, ng, c->g_geo, c->g_cell, c->g_meta, c->g_dep, c->wtab, pp,
+                        pp.rec_fwd[dtype], pp.rec_adj[dtype], pp.rec_fl[dtype], s);
+  int max_nt = 0, max_nta = 0;
+  for (int b = 0; b < c->B; ++b) {
+    const Geom& g = c->hG[b];
+    const int end = c->h_lev_ptr[g.lev_off + g.n_levels];
+    if (g.n_levels > pp.L0) max_nt = std::max(max_nt, end - c->h_lev_ptr[g.lev_off + pp.L0]);
+    if (g.n_levels > pp.L0a) max_nta = std::max(max_nta, end - c->h_lev_ptr[g.lev_off + pp.L0a]);
+  }
+  pp.tail_max = max_nt;
+  pp.tail_max_a = max_nta;
+  pp.tail_smem[0][dtype] = packed_tail_smem(dtype, dim, 0, max_nt, max_smem_optin());
+  pp.tail_smem[1][dtype] = packed_tail_smem(dtype, dim, 1, max_nta, max_smem_optin());
+  CKL();
+  CK(cudaStreamSynchronize(s));
+  pp.rec_built[dtype] = true;
+  return EBR_OK;
+}
+
 static ebr_status packed_args(Ctx* c, const char* who, int32_t n_fields, const int32_t* h_bc_kind,
                               int32_t dtype, KindBits* kb) {
   if (!c->levelled) return fail(c, EBR_EINVAL, "%s: build the levels first", who);
   if (n_fields < 1 || n_fields > PACKED_MAX_FIELDS || !h_bc_kind)
     return fail(c, EBR_EINVAL, "%s: 1..%d fields with kinds required", who, PACKED_MAX_FIELDS);
   if (dtype != EBR_F32 && dtype != EBR_F64) return fail(c, EBR_EINVAL, "%s: bad dtype", who);
+  for (int b = 1; b < c->B; ++b)
+    if (c->hG[b].dim != c->hG[0].dim) return fail(c, EBR_EINVAL, "%s: mixed dimensions", who);
+  if (c->total_cells >= (1LL << 31)) return fail(c, EBR_EINVAL, "%s: more than 2^31 cells", who);
   std::memset(kb, 0, sizeof(KindBits));
   for (int f = 0; f < n_fields; ++f) {
     if (h_bc_kind[f] != 0 && h_bc_kind[f] != 1) return fail(c, EBR_EINVAL, "%s: bad bc kind", who);
@@ -947,11 +1063,18 @@ ebr_status ebr_reconstruct_packed(void* ctx, int32_t n_fields, void* d_fields,
   if (st) return st;
   if (!d_fields || !d_bc) return fail(c, EBR_EINVAL, "ebr_reconstruct_packed: null field or boundary data");
   cudaStream_t s = S(stream);
-  prof_begin(c, s, "pfill");
-  launch_pfill(dtype, n_fields, d_fields, d_bc, kb, c->dG, c->d_deep_list, c->n_deep, c->g_cell,
-               c->g_meta, c->lev_ptr, c->wtab, c->ng, c->d_status, s);
-  prof_end(c, s);
-  c->launches += c->n_deep > 0 ? 1 : 0;
+  st = packed_plan(c, s, "ebr_reconstruct_packed");
+  if (st) return st;
+  st = packed_records(c, s, dtype, "ebr_reconstruct_packed");
+  if (st) return st;
+  static const char* names[3] = {"pfill_part", "pfill_lvl", "pfill_tail"};
+  for (int ph = 0; ph < 3; ++ph) {
+    prof_begin(c, s, names[ph]);
+    launch_pfill(dtype, c->hG[0].dim, n_fields, d_fields, d_bc, kb, c->dG, c->lev_ptr, c->ng, c->pplan,
+                 c->pplan.rec_fwd[dtype], c->d_status, s, ph);
+    prof_end(c, s);
+  }
+  c->launches += pfill_launches(c->pplan, c->ng);
   CKL();
   return EBR_OK;
 }
@@ -967,6 +1090,10 @@ ebr_status ebr_reconstruct_packed_adjoint(void* ctx, int32_t n_fields, const int
   if (st) return st;
   if (!d_cot || !d_grad_bc) return fail(c, EBR_EINVAL, "ebr_reconstruct_packed_adjoint: null cotangent or gradient");
   cudaStream_t s = S(stream);
+  st = packed_plan(c, s, "ebr_reconstruct_packed_adjoint");
+  if (st) return st;
+  st = packed_records(c, s, dtype, "ebr_reconstruct_packed_adjoint");
+  if (st) return st;
   size_t need = (size_t)std::max(c->ng, 1) * n_fields * (dtype == EBR_F32 ? 4 : 8);
   if (need > c->lamP_bytes) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -982,17 +1109,14 @@ ebr_status ebr_reconstruct_packed_adjoint(void* ctx, int32_t n_fields, const int
   const int dim = c->hG[0].dim;
   for (int b = 1; b < c->B; ++b)
     if (c->hG[b].dim != dim) return fail(c, EBR_EINVAL, "ebr_reconstruct_packed_adjoint: mixed dimensions");
-  prof_begin(c, s, "padj_chain");
-  launch_padj(dtype, n_fields, d_cot, c->lamP, d_grad_bc, kb, c->dG, c->d_deep_list, c->n_deep, c->ng,
-              stencil_k(dim), c->g_geo, c->g_cell, c->g_meta, c->lev_ptr, c->gsrc_ptr, c->gsrc, c->tags,
-              c->pos_of_cell, c->rmax, c->wtab, s, 0);
-  prof_end(c, s);
-  prof_begin(c, s, "padj_fluid");
-  launch_padj(dtype, n_fields, d_cot, c->lamP, d_grad_bc, kb, c->dG, c->d_deep_list, c->n_deep, c->ng,
-              stencil_k(dim), c->g_geo, c->g_cell, c->g_meta, c->lev_ptr, c->gsrc_ptr, c->gsrc, c->tags,
-              c->pos_of_cell, c->rmax, c->wtab, s, 1);
-  prof_end(c, s);
-  c->launches += c->ng > 0 ? 2 : 0;
+  static const char* names[3] = {"padj_tail", "padj_lvl", "padj_fluid"};
+  for (int ph = 0; ph < 3; ++ph) {
+    prof_begin(c, s, names[ph]);
+    launch_padj(dtype, n_fields, d_cot, c->lamP, d_grad_bc, kb, c->dG, c->ng, c->lev_ptr, c->wtab,
+                c->pplan, c->pplan.rec_adj[dtype], c->pplan.rec_fl[dtype], c->d_status, s, ph);
+    prof_end(c, s);
+  }
+  c->launches += padj_launches(c->pplan, c->ng);
   CKL();
   return EBR_OK;
 }
@@ -1054,6 +1178,10 @@ ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stre
   if (n > 1) h_out[1] = c->rmax;
   if (n > 2) h_out[2] = c->launches;
   if (n > 3) h_out[3] = c->n_gsrc;
+  // packed schedule (zeros before the first packed call)
+  const PackedPlan& pp = c->pplan;
+  const long long pk[7] = {pp.L0, pp.L0a, pp.n_tail, pp.n_tail_a, pp.tail_max, pp.tail_max_a, pp.n_ft};
+  for (int k = 0; k < 7 && 4 + k < n; ++k) h_out[4 + k] = pp.built ? pk[k] : 0;
   return EBR_OK;
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "ebr_device.cuh"
 
 namespace ebr {
@@ -108,15 +110,69 @@ void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, 
                    void* const* grad, int accumulate, cudaStream_t s);
 
 // ---- packed.cu (field-minor layout [cells][F])
-void launch_pfill(int dtype, int F, void* fld, const void* bc, const KindBits& kb, const Geom* G,
-                  const int* geo_list, int n_list, const int* g_cell, const uint32_t* g_meta,
-                  const int* lev_ptr, const double* wtab, int ng, int* status, cudaStream_t s);
-// phase 0: reverse-level chain (lambda, boundary-data gradients, ghost
-// cotangents cleared); phase 1: fluid targets
+// Schedule of the packed kernels, planned once per levelled geometry set:
+// forward levels 1..L0 (adjoint 1..L0a) run grid-wide from the ghost lists
+// d_lvl[h_lvl_off[l - 1] .. h_lvl_off[l]); the levels above (at most
+// PACKED_TAIL_MAX, resp. PACKED_TAIL_MAX_ADJ, ghosts per geometry and level)
+// run in one CTA per geometry of d_tail (d_tail_a).
+constexpr int PACKED_TAIL_MAX = 128;       // forward tail (shared memory)
+constexpr int PACKED_TAIL_MAX_ADJ = 128;   // adjoint tail (shared memory; else global memory)
+constexpr int PACKED_MAX_SOURCES = 64;   // sources of one item (consumers / fluid sources)
+struct PackedPlan {
+  bool built = false;
+  int L0 = 1;
+  int* d_lvl = nullptr;
+  std::vector<int> h_lvl_off;
+  int* d_tail = nullptr;
+  int n_tail = 0;
+  int L0a = 1;
+  int* d_tail_a = nullptr;
+  int n_tail_a = 0;
+  int* cons_ptr = nullptr;     // [ng + 1] active consumers of each ghost (q << 3 | slot)
+  int* cons = nullptr;
+  int n_ft = 0;                // fluid targets
+  int* ft_cell = nullptr;      // [n_ft] global cell
+  int* ft_ptr = nullptr;       // [n_ft + 1]
+  int* ft_src = nullptr;       // sources (q << 3 | slot), fixed probe order
+  // per field type (0 FP32, 1 FP64): item records (forward, adjoint, fluid)
+  bool rec_built[2] = {false, false};
+  uint32_t* rec_fwd[2] = {nullptr, nullptr};
+  uint32_t* rec_adj[2] = {nullptr, nullptr};
+  uint32_t* rec_fl[2] = {nullptr, nullptr};
+  // dynamic shared memory of the tail kernels [forward, adjoint][type];
+  // 0 = the largest tail does not fit, the global-memory tail kernels run
+  size_t tail_smem[2][2] = {{0, 0}, {0, 0}};
+  int tail_max = 0;            // largest forward tail (ghosts of levels > L0 in one geometry)
+  int tail_max_a = 0;          // largest adjoint tail (levels > L0a)
+};
+size_t packed_tail_smem(int dtype, int dim, int which, int max_nt, int limit);
+// words per record: which = 0 forward, 1 adjoint / fluid
+size_t packed_rec_words(int dtype, int dim, int which);
+void launch_packed_records(int dtype, int dim, const Geom* G, int ng, const int* g_geo,
+                           const int* g_cell, const uint32_t* g_meta, const int* g_dep,
+                           const double* wtab, const PackedPlan& pp, uint32_t* fwd, uint32_t* adj,
+                           uint32_t* fl, cudaStream_t s);
+// forward phases: 0 partial sums of every ghost, 1 levels 2..L0 grid-wide,
+// 2 the tail CTAs.  Adjoint phases (lambda in reverse level order, with the
+// boundary-data gradients and the ghost cotangents cleared): 0 the tail CTAs,
+// 1 levels L0..1 grid-wide; 2 the fluid targets.
+void launch_pfill(int dtype, int dim, int F, void* fld, const void* bc, const KindBits& kb,
+                  const Geom* G, const int* lev_ptr, int ng, const PackedPlan& pp,
+                  const uint32_t* rec, int* status, cudaStream_t s, int phase);
+int pfill_launches(const PackedPlan& pp, int ng);
 void launch_padj(int dtype, int F, void* cot, void* lamP, void* gbc, const KindBits& kb,
-                 const Geom* G, const int* geo_list, int n_list, int ng, int kmax, const int* g_geo,
-                 const int* g_cell, const uint32_t* g_meta, const int* lev_ptr, const int* gsrc_ptr,
-                 const int* gsrc, const int8_t* tags, const int* pos_of_cell, int R,
-                 const double* wtab, cudaStream_t s, int phase);
+                 const Geom* G, int ng, const int* lev_ptr, const double* wtab,
+                 const PackedPlan& pp, const uint32_t* rec_adj, const uint32_t* rec_fl,
+                 int* status, cudaStream_t s, int phase);
+int padj_launches(const PackedPlan& pp, int ng);
+// plan kernels: ptr == null counts (out = counts), else writes the lists
+void launch_packed_plan_cons(int ng, const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
+                             const int* ptr, int* out, cudaStream_t s);
+// tpos == null: flag / count per (ghost, member) incidence; else writes the
+// target cells, offsets and sources
+void launch_packed_plan_ftgt(int ng, int kmax, const Geom* G, const int* g_geo, const int* g_cell,
+                             const uint32_t* g_meta, const int8_t* tags, const int* pos_of_cell,
+                             int R, int* flag, int* cnt, const int* tpos, const int* epos,
+                             int* ft_cell, int* ft_ptr, int* ft_src, cudaStream_t s);
 
 }  // namespace ebr

@@ -195,3 +195,37 @@ def test_adjoint_dot_product_identity():
         # and the linear map equals the level-by-level fill
         xin = x.copy()
         out = O.fill(c, lev, [xin], [O.DIRICHLET if Agb.diagonal().min() > 0 else O.NEUMANN], [b])
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
+def test_fill_vjp_against_the_level_walk(case, placement):
+    # <ybar, fill(x, b)> = <xbar, x> + <bbar, b> for the level-by-level fill
+    # (an algorithm independent of the sparse solve inside fill_vjp), and the
+    # ghost entries of x have zero gradient
+    gd, bd = CASES[case]
+    c = O.classify(gd, bd, placement)
+    lev = O.build_levels(c)
+    rng = np.random.default_rng(50 + case)
+    kinds = [O.DIRICHLET, O.NEUMANN, O.NEUMANN]
+    N, ng = c.grid.N, c.n_ghosts
+    ybar = [rng.normal(size=N) for _ in kinds]
+    xbar, bbar = O.fill_vjp(c, lev, kinds, ybar)
+    for f in range(len(kinds)):
+        assert np.all(xbar[f][c.idx] == 0.0)
+        # non-stencil, non-ghost cells pass the cotangent through unchanged
+        touched = set(int(m) for g in range(ng) for k in range(lev.midx.shape[1])
+                      if lev.active[g, k] for m in [lev.midx[g, k]])
+        other = np.ones(N, bool)
+        other[c.idx] = False
+        other[list(touched)] = False
+        assert np.array_equal(xbar[f][other], ybar[f][other])
+    for trial in range(2):
+        x = [rng.normal(size=N) for _ in kinds]
+        b = [rng.normal(size=ng) for _ in kinds]
+        y = O.fill(c, lev, [a.copy() for a in x], kinds, b)
+        for f in range(len(kinds)):
+            lhs = float(ybar[f] @ y[f])
+            rhs = float(xbar[f] @ x[f] + bbar[f] @ b[f])
+            scale = float(np.abs(ybar[f]) @ np.abs(y[f])) + 1.0
+            assert abs(lhs - rhs) < 1e-12 * scale, (f, lhs, rhs)
