@@ -328,10 +328,16 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
     }
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from an ncu capture
-# of the same kernel on this workload (None until captured for the current
-# kernel version).
-TRAFFIC_PER_LAUNCH = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# of the same kernel version on this workload (profiles/
+# dram_traffic_batch_256.md; L2 write-back hides most writes of a short
+# kernel).  The many-field calls were captured on 32 geometries and scaled by
+# the ghost count.  A kernel changed since its capture is left out (None).
+TRAFFIC_PER_LAUNCH = {
+    "adj_fluid": 27.44e6, "fill_chain": 28.36e6, "forces": 34.96e6, "adj_chain": 6.41e6,
+    "levels": 1.11e6, "rows": 0.57e6,
+    "pfill": 123.0e6, "padj": 153.0e6,
+}
 
 
 def unique_fluid_targets(R, info, dim=2):

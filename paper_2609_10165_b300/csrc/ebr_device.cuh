@@ -162,28 +162,37 @@ __device__ inline void ellipse_closest(double a, double b, double p, double q,
   double t = (double)tf;
   if (!(t > tmin)) t = 0.0;
   for (int it = 0; it < 12; ++it) {
-    double rua = 1.0 / (a2 + t), rub = 1.0 / (b2 + t);
-    double fx = a * p * rua, fy = b * q * rub;
-    double F = fx * fx + fy * fy - 1.0;
-    double dF = -2.0 * (fx * fx * rua + fy * fy * rub);
+    // one double reciprocal per iteration: 1/(a^2+t) and 1/(b^2+t) from
+    // 1/((a^2+t)(b^2+t))
+    const double ua = a2 + t, ub = b2 + t;
+    const double r = 1.0 / (ua * ub);
+    const double rua = ub * r, rub = ua * r;
+    const double fx = a * p * rua, fy = b * q * rub;
+    const double F = fx * fx + fy * fy - 1.0;
+    const double dF = -2.0 * (fx * fx * rua + fy * fy * rub);
     if (F == 0.0 || dF == 0.0) break;
-    double tn = t - F / dF;
+    // Newton increment in float: its relative error (6e-8) times the step
+    // leaves an error far below the next step, which converges it
+    // quadratically; F stays in double
+    double tn = t - (double)((float)F / (float)dF);
     if (!(tn > tmin)) tn = 0.5 * (t + tmin);
-    double dt = fabs(tn - t);
+    const double dt = fabs(tn - t);
     t = tn;
     // quadratic convergence: once a step is 1e-12 relative, the error left
     // after it is far below the rounding level
     if (dt <= 1e-12 * fabs(t)) break;
   }
-  double ua = a2 + t, ub = b2 + t;
-  // G - S = (p t / ua, q t / ub): no cancellation
-  double ex = p * t / ua, ey = q * t / ub;
+  const double ua = a2 + t, ub = b2 + t;
+  const double r = 1.0 / (ua * ub);
+  const double rua = ub * r, rub = ua * r;
+  // G - S = (p t / ua, q t / ub): no cancellation; the outward normal at S is
+  // along (X / a^2, Y / b^2) = (p / ua, q / ub)
+  const double ex = p * t * rua, ey = q * t * rub;
   dist = sqrt(ex * ex + ey * ey);
-  double X = a2 * p / ua, Y = b2 * q / ub;
-  double mx = X / a2, my = Y / b2;
-  double mn = sqrt(mx * mx + my * my);
-  nx = mx / mn;
-  ny = my / mn;
+  const double mx = p * rua, my = q * rub;
+  const double inv = rsqrt(mx * mx + my * my);
+  nx = mx * inv;
+  ny = my * inv;
 }
 
 // Upper airfoil surface as polynomials in u = sqrt(x / c).
@@ -275,15 +284,17 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
       double gv, dg;
       g(u, gv, dg);
       if (gv == 0.0) break;
+      // Newton increment in float (g in double): see ellipse_closest
+      const double st = dg > 0.0 ? (double)((float)gv / (float)dg) : 0.0;
       // converged: a Newton step of 1e-12 (relative) leaves an error below the
       // rounding level; accept it before the safeguard, which would otherwise
       // bisect once the step rounds onto the bracket end
-      if (dg > 0.0 && fabs(gv / dg) <= 1e-12 * fmax(u, 1e-3)) {
-        u = fmin(fmax(u - gv / dg, lo), hi);
+      if (dg > 0.0 && fabs(st) <= 1e-12 * fmax(u, 1e-3)) {
+        u = fmin(fmax(u - st, lo), hi);
         break;
       }
       if (gv < 0.0) lo = u; else hi = u;
-      double un = u - gv / dg;
+      double un = u - st;
       if (!(un > lo && un < hi) || dg <= 0.0) un = 0.5 * (lo + hi);
       u = un;
     }
@@ -291,8 +302,8 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
   double x, y, dx, dy, ddx, ddy;
   airfoil_u(t, c, u, x, y, dx, dy, ddx, ddy);
   double d2u = (x - qx) * (x - qx) + (y - qy) * (y - qy);
-  double yte, tmp1, tmp2, tmp3, tmp4, tmp5;
-  airfoil_u(t, c, 1.0, tmp1, yte, tmp2, tmp3, tmp4, tmp5);
+  // half thickness at the trailing edge: the polynomial at u = 1
+  const double yte = 5.0 * t * c * (0.2969 + -0.1260 + -0.3516 + 0.2843 + -0.1015);
   double by = fmin(qy, yte);
   double d2b = (qx - c) * (qx - c) + (qy - by) * (qy - by);
   double sx, sy;
@@ -301,16 +312,16 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
     sx = c; sy = by; nx = 1.0; ny = 0.0;
   } else {
     sx = x; sy = y;
-    double fn = sqrt(dx * dx + dy * dy);
-    nx = -dy / fn;
-    ny = dx / fn;
+    const double inv = rsqrt(dx * dx + dy * dy);
+    nx = -dy * inv;
+    ny = dx * inv;
   }
   bool corner = !inside && ((base && qy > yte) || (!base && u == 1.0));
   if (corner) {
     sx = c; sy = yte;
-    double vx = qx - c, vy = qy - yte, vn = sqrt(vx * vx + vy * vy);
-    nx = vx / vn;
-    ny = vy / vn;
+    const double vx = qx - c, vy = qy - yte, inv = rsqrt(vx * vx + vy * vy);
+    nx = vx * inv;
+    ny = vy * inv;
   }
   dist = sqrt((qx - sx) * (qx - sx) + (qy - sy) * (qy - sy));
   if (py < 0.0) ny = -ny;
@@ -444,7 +455,8 @@ __device__ inline bool closest_point(const Geom& g, double x, double y, double z
       double rho = __dsqrt_rn(__dadd_rn(__dadd_rn(sq(dx), sq(dy)), sq(dz)));
       if (rho == 0.0) return false;
       dist = fabs(g.radii[0] - rho);
-      n[0] = dx / rho; n[1] = dy / rho; n[2] = dz / rho;
+      const double ir = 1.0 / rho;
+      n[0] = dx * ir; n[1] = dy * ir; n[2] = dz * ir;
       break;
     }
     case ELLIPSE:
