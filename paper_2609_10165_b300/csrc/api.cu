@@ -1,6 +1,7 @@
 // C ABI (include/ebr.h): context, planning, and the orchestration of the
 // classification, level, fill, force and adjoint kernels.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -626,6 +627,27 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const eb
     for (int q = 0; q < 9; ++q) g.rot[q] = bd.rot[q];
     g.t = bd.thickness;
     g.c = bd.chord;
+    // float copies and the margin of the float HGC decision: it covers the
+    // float rounding of cell centres, body-frame coordinates, the float
+    // closest point and dn/2 by a wide factor (1e-4 of the finest width plus
+    // 4e-6 of the largest coordinate magnitude)
+    {
+      float hmin = 3.4e38f, ext = 1.0f;
+      for (int a = 0; a < 3; ++a) {
+        g.flo[a] = (float)g.lo[a];
+        g.fh[a] = (float)g.h[a];
+        g.fcentre[a] = (float)g.centre[a];
+        g.fradii[a] = (float)g.radii[a];
+        if (a < g.dim) {
+          hmin = std::min(hmin, (float)g.h[a]);
+          ext = std::max(ext, std::max(std::fabs((float)g.lo[a]), std::fabs((float)(g.lo[a] + g.n[a] * g.h[a]))));
+        }
+      }
+      for (int q = 0; q < 9; ++q) g.frot[q] = (float)g.rot[q];
+      g.ft = (float)g.t;
+      g.fc = (float)g.c;
+      g.hgc_mrg = 1e-4f * hmin + 4e-6f * ext;
+    }
     if ((bd.kind == EBR_CIRCLE || bd.kind == EBR_SPHERE) && !(bd.radii[0] > 0))
       return fail(c, EBR_EINVAL, "geometry %d: radius must be positive", b);
     if (bd.kind == EBR_ELLIPSE && !(bd.radii[0] > 0 && bd.radii[1] > 0))

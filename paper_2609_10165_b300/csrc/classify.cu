@@ -468,22 +468,24 @@ __global__ void k_place(const Geom* __restrict__ G, int n_iface, const int* __re
     double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
     // Eq. HGC_criterion decided in float where the float psi and dn/2 are
     // clearly apart; the few cells within the safety margin use double
+    const float xf = g.flo[0] + ((float)i + 0.5f) * g.fh[0];
+    const float yf = g.flo[1] + ((float)j + 0.5f) * g.fh[1];
+    const float zf = g.dim == 3 ? g.flo[2] + ((float)k + 0.5f) * g.fh[2] : 0.0f;
     float n32[3];
-    float psi32 = closest_point_f32(g, x, y, z, solid, n32);
-    float s32 = 0.0f, hmin = 3.4e38f, ext = 1.0f;
+    float psi32 = closest_point_f32(g, xf, yf, zf, solid, n32);
+    float s32 = 0.0f;
     for (int a = 0; a < g.dim; ++a) {
-      float q = n32[a] / (float)g.h[a];
+      float q = n32[a] / g.fh[a];
       s32 += q * q;
-      hmin = fminf(hmin, (float)g.h[a]);
-      ext = fmaxf(ext, fmaxf(fabsf((float)g.lo[a]), fabsf((float)(g.lo[a] + g.n[a] * g.h[a]))));
     }
     float half32 = 0.5f / sqrtf(s32);
-    float mrg = 1e-4f * hmin + 4e-6f * ext;
     float gap = fabsf(psi32) - half32;
     bool cand;
-    if (fabsf(gap) > mrg) {
+    if (fabsf(gap) > g.hgc_mrg) {
       cand = gap <= 0.0f;
     } else {
+      double x = centre_of(g, 0, i), y = centre_of(g, 1, j);
+      double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
       double psi, nv[3];
       if (!closest_point(g, x, y, z, solid, psi, nv)) { set_status(status, S_EINVAL); return; }
       double half = 0.5 * delta_n(g, nv);

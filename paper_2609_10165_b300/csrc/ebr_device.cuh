@@ -42,7 +42,9 @@ struct Geom {
   int iface_off, n_iface;
   int ghost_off, n_ghost;
   int lev_off, n_levels;     // level pointers at lev_ptr[lev_off .. lev_off + n_levels]
-  int ftgt_off, n_ftgt;      // fluid adjoint targets
+  // float copies for the float pre-decisions (no double work or conversions
+  // per cell); hgc_mrg = safety margin of the float HGC decision
+  float flo[3], fh[3], fcentre[3], fradii[3], frot[9], ft, fc, hgc_mrg;
 };
 
 // ---------------------------------------------------------------------------
@@ -332,25 +334,25 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
 // thresholds (a cell whose float decision is within a safety margin of a
 // threshold is decided with the double closest point instead)
 // ---------------------------------------------------------------------------
-__device__ inline float closest_point_f32(const Geom& g, double x, double y, double z, bool solid,
+__device__ inline float closest_point_f32(const Geom& g, float x, float y, float z, bool solid,
                                           float n[3]) {
   n[0] = n[1] = n[2] = 0.0f;
   float dist = 0.0f;
   switch (g.kind) {
     case CIRCLE:
     case SPHERE: {
-      float dx = (float)(x - g.centre[0]), dy = (float)(y - g.centre[1]);
-      float dz = g.kind == SPHERE ? (float)(z - g.centre[2]) : 0.0f;
+      float dx = x - g.fcentre[0], dy = y - g.fcentre[1];
+      float dz = g.kind == SPHERE ? z - g.fcentre[2] : 0.0f;
       float rho = sqrtf(dx * dx + dy * dy + dz * dz);
       float r = 1.0f / fmaxf(rho, 1e-30f);
-      dist = fabsf((float)g.radii[0] - rho);
+      dist = fabsf(g.fradii[0] - rho);
       n[0] = dx * r; n[1] = dy * r; n[2] = dz * r;
       break;
     }
     case ELLIPSE: {
-      double pd, qd;
-      to_body2(g, x, y, pd, qd);
-      float a = (float)g.radii[0], b = (float)g.radii[1], p = (float)pd, q = (float)qd;
+      const float wx = x - g.fcentre[0], wy = y - g.fcentre[1];
+      const float p = g.frot[0] * wx + g.frot[3] * wy, q = g.frot[1] * wx + g.frot[4] * wy;
+      const float a = g.fradii[0], b = g.fradii[1];
       float a2 = a * a, b2 = b * b, tmin = -fminf(a2, b2), t = 0.0f;
       for (int it = 0; it < 16; ++it) {
         float rua = 1.0f / (a2 + t), rub = 1.0f / (b2 + t);
@@ -370,14 +372,14 @@ __device__ inline float closest_point_f32(const Geom& g, double x, double y, dou
       float mx = p * rua, my = q * rub;           // (X / a^2, Y / b^2)
       float mn = 1.0f / sqrtf(mx * mx + my * my);
       float bx = mx * mn, by = my * mn;
-      n[0] = (float)g.rot[0] * bx + (float)g.rot[1] * by;
-      n[1] = (float)g.rot[3] * bx + (float)g.rot[4] * by;
+      n[0] = g.frot[0] * bx + g.frot[1] * by;
+      n[1] = g.frot[3] * bx + g.frot[4] * by;
       break;
     }
     default: {  // AIRFOIL4
-      double pd, qd;
-      to_body2(g, x, y, pd, qd);
-      float c = (float)g.c, t = (float)g.t, qx = (float)pd, qy = fabsf((float)qd);
+      const float wx = x - g.fcentre[0], wy = y - g.fcentre[1];
+      const float qd = g.frot[1] * wx + g.frot[4] * wy;
+      const float c = g.fc, t = g.ft, qx = g.frot[0] * wx + g.frot[3] * wy, qy = fabsf(qd);
       const int NS = 64;
       int best = 0;
       float bd = 3.4e38f;
@@ -432,9 +434,9 @@ __device__ inline float closest_point_f32(const Geom& g, double x, double y, dou
         float fn = 1.0f / sqrtf(dx * dx + dy * dy);
         bx = -dy * fn; by = dx * fn;
       }
-      if (qd < 0.0) by = -by;
-      n[0] = (float)g.rot[0] * bx + (float)g.rot[1] * by;
-      n[1] = (float)g.rot[3] * bx + (float)g.rot[4] * by;
+      if (qd < 0.0f) by = -by;
+      n[0] = g.frot[0] * bx + g.frot[1] * by;
+      n[1] = g.frot[3] * bx + g.frot[4] * by;
       break;
     }
   }

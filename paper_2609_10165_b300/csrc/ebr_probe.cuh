@@ -36,9 +36,55 @@ __device__ inline void member_ijk(const Geom& g, const int ijk[3], uint32_t m, i
 // member_slot(H) = T, found by probing H = T - delta over the box |delta_a| <= R
 // in a fixed order.  Slot 0 (H = T itself) is listed first for ghost targets.
 // ---------------------------------------------------------------------------
+// One z-slab (dz fixed) of the reach-1 probe, in three rounds of independent
+// loads (tags; positions; metas) before the ordered visit.  Returns false when
+// the visitor stopped the probe.
+template <typename Visit>
+__device__ __forceinline__ bool probe_slab_r1(const Geom& g, const int tijk[3], int dz, const int8_t* tg,
+                                              const int* pcell, const uint32_t* g_meta, Visit& visit) {
+  const int K = stencil_k(g.dim);
+  int hc[9], q[9];
+  uint32_t m[9];
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const int dx = b % 3 - 1, dy = b / 3 - 1;
+    const int h[3] = {tijk[0] - dx, tijk[1] - dy, tijk[2] - dz};
+    const bool ok = !(dx == 0 && dy == 0 && dz == 0) && in_grid(g, h);
+    hc[b] = ok ? cell_lin(g, h) : -1;
+  }
+  int8_t t[9];
+#pragma unroll
+  for (int b = 0; b < 9; ++b) t[b] = hc[b] >= 0 ? tg[hc[b]] : (int8_t)0;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) q[b] = (t[b] == 2 || t[b] == -2) ? pcell[hc[b]] : -1;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) m[b] = q[b] >= 0 ? g_meta[q[b]] : 0u;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    if (q[b] < 0) continue;
+    const int dd[3] = {b % 3 - 1, b / 3 - 1, dz};
+    for (int k = 0; k < K; ++k) {
+      int o[3];
+      stencil_off(g.dim, k, o);
+      bool hit = true;
+      for (int a = 0; a < g.dim; ++a)
+        if (o[a] * meta_r(m[b], a) * meta_e(m[b], a) != dd[a]) hit = false;
+      if (hit) { if (!visit(q[b], k + 1)) return false; }
+    }
+  }
+  return true;
+}
+
 template <typename Visit>
 __device__ inline void probe_sources(const Geom& g, const int tijk[3], const int8_t* tg,
                                      const int* pcell, const uint32_t* g_meta, int R, Visit visit) {
+  if (R == 1) {
+    // the usual reach: the 8 (2D) or 26 (3D) neighbours, same order as below
+    if (g.dim == 3 && !probe_slab_r1(g, tijk, -1, tg, pcell, g_meta, visit)) return;
+    if (!probe_slab_r1(g, tijk, 0, tg, pcell, g_meta, visit)) return;
+    if (g.dim == 3) probe_slab_r1(g, tijk, 1, tg, pcell, g_meta, visit);
+    return;
+  }
   const int K = stencil_k(g.dim);
   int Rz = g.dim == 3 ? R : 0;
   for (int dz = -Rz; dz <= Rz; ++dz)
