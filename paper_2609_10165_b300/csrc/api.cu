@@ -647,6 +647,11 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const eb
       g.ft = (float)g.t;
       g.fc = (float)g.c;
       g.hgc_mrg = 1e-4f * hmin + 4e-6f * ext;
+      float extc = 1.0f;
+      for (int a = 0; a < g.dim; ++a)
+        extc = std::max(extc, std::max(std::fabs((float)(g.lo[a] - g.centre[a])),
+                                       std::fabs((float)(g.lo[a] + g.n[a] * g.h[a] - g.centre[a]))));
+      g.fext = extc;
     }
     if ((bd.kind == EBR_CIRCLE || bd.kind == EBR_SPHERE) && !(bd.radii[0] > 0))
       return fail(c, EBR_EINVAL, "geometry %d: radius must be positive", b);

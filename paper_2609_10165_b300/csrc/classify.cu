@@ -277,78 +277,305 @@ __device__ void exact_run(const Geom& g, int j, int k, int& s, int& t, int* stat
   }
 }
 
+// ---------------------------------------------------------------------------
+// rows, RG = 8 lanes per row (4 rows per warp).  The search for the run is
+// parallel inside the group: 8 samples per round instead of one lane walking
+// dozens of dependent iterations, so that many more rows are in flight.
+// Every shuffle and ballot names the group's lanes only, and control flow is
+// uniform inside a group (all its lanes hold the same row).
+// ---------------------------------------------------------------------------
+constexpr int RG = 8;
+
+struct RowGrp {
+  unsigned mask;   // the group's lanes
+  int sl;          // lane within the group
+  int shift;       // first lane of the group
+  __device__ __forceinline__ unsigned ballot(bool p) const {
+    return (__ballot_sync(mask, p) >> shift) & 0xFFu;
+  }
+  // group arg-max; ties go to the smaller index (all lanes get the result)
+  __device__ __forceinline__ int arg_max(float v) const {
+    int a = sl;
+    for (int o = 1; o < RG; o <<= 1) {
+      const float ov = __shfl_xor_sync(mask, v, o, RG);
+      const int oa = __shfl_xor_sync(mask, a, o, RG);
+      if (ov > v || (ov == v && oa < a)) { v = ov; a = oa; }
+    }
+    return a;
+  }
+  __device__ __forceinline__ int min_i(int v) const {
+    for (int o = 1; o < RG; o <<= 1) v = min(v, __shfl_xor_sync(mask, v, o, RG));
+    return v;
+  }
+  __device__ __forceinline__ int max_i(int v) const {
+    for (int o = 1; o < RG; o <<= 1) v = max(v, __shfl_xor_sync(mask, v, o, RG));
+    return v;
+  }
+};
+
+// float row constants from the float copies of the geometry (the margins of
+// solid_f32 cover the float rounding of the cell centres by a wide factor)
+__device__ inline void row_consts_f(const Geom& g, int j, int k, RowF& R) {
+  const float dy = g.flo[1] + ((float)j + 0.5f) * g.fh[1] - g.fcentre[1];
+  const float dz = g.dim == 3 ? g.flo[2] + ((float)k + 0.5f) * g.fh[2] - g.fcentre[2] : 0.0f;
+  const float ext = g.fext;
+  R.ox = g.flo[0] - g.fcentre[0];
+  R.hx = g.fh[0];
+  R.ia = R.ib = 1.0f;
+  R.r00 = g.frot[0];
+  R.r01 = g.frot[1];
+  if (g.kind == CIRCLE || g.kind == SPHERE) {
+    const float r = g.fradii[0];
+    R.c0 = dy * dy + (g.kind == SPHERE ? dz * dz : 0.0f);
+    R.c1 = r * r;
+    R.m = 1e-5f * (3.0f * ext * ext + r * r);
+  } else if (g.kind == ELLIPSE) {
+    const float a = g.fradii[0], b = g.fradii[1];
+    R.c0 = g.frot[3] * dy;
+    R.c1 = g.frot[4] * dy;
+    R.ia = 1.0f / a;
+    R.ib = 1.0f / b;
+    const float mn = fminf(a, b);
+    R.m = 1e-5f * (1.0f + 2.0f * ext * ext / (mn * mn));
+  } else {
+    R.c0 = g.frot[3] * dy;
+    R.c1 = g.frot[4] * dy;
+    R.m = 2e-5f * (1.0f + ext);
+  }
+}
+
+// Estimate of the solid run of row (j, k) by the group (same result in every
+// lane); same states as estimate_row.
+__device__ void estimate_row_grp(const Geom& g, int j, int k, const RowGrp& Gp, int& state, int& ia,
+                                 int& ib, int& iv) {
+  const int n = g.n[0];
+  const float y = g.flo[1] + ((float)j + 0.5f) * g.fh[1] - g.fcentre[1];
+  const float z = g.dim == 3 ? g.flo[2] + ((float)k + 0.5f) * g.fh[2] - g.fcentre[2] : 0.0f;
+  const float lo0 = g.flo[0] - g.fcentre[0], h0 = g.fh[0];
+  auto frac = [&](float xr) { return (xr - lo0) / h0 - 0.5f; };   // body-relative x -> cell
+  state = ROW_EMPTY; ia = 0; ib = -1; iv = 0;
+  float cx, xa, xb;
+  if (g.kind == CIRCLE || g.kind == SPHERE) {
+    const float r2 = g.fradii[0] * g.fradii[0];
+    const float yz = y * y + (g.kind == SPHERE ? z * z : 0.0f);
+    const float D = r2 - yz;
+    cx = 0.0f;
+    if (D < -(1e-4f * r2 + 1e-6f * yz)) return;
+    if (D <= 0.0f) { state = ROW_TANGENT; iv = (int)lrintf(frac(cx)); return; }
+    const float sD = sqrtf(D);
+    xa = -sD; xb = sD;
+  } else if (g.kind == ELLIPSE) {
+    const float r00 = g.frot[0], r01 = g.frot[1], r10 = g.frot[3], r11 = g.frot[4];
+    const float ia2 = 1.0f / (g.fradii[0] * g.fradii[0]), ib2 = 1.0f / (g.fradii[1] * g.fradii[1]);
+    const float A = r00 * r00 * ia2 + r01 * r01 * ib2;
+    const float Bq = 2.0f * y * (r00 * r10 * ia2 + r01 * r11 * ib2);
+    const float C = y * y * (r10 * r10 * ia2 + r11 * r11 * ib2) - 1.0f;
+    const float disc = Bq * Bq - 4.0f * A * C;
+    cx = -Bq / (2.0f * A);
+    const float scale = Bq * Bq + 4.0f * A * fabsf(C);
+    if (disc < -1e-4f * scale) return;
+    if (disc <= 0.0f) { state = ROW_TANGENT; iv = (int)lrintf(frac(cx)); return; }
+    const float sd = sqrtf(disc) / (2.0f * A);
+    xa = cx - sd; xb = cx + sd;
+  } else {  // AIRFOIL4: maximum of the concave depth, then the two roots
+    const float r00 = g.frot[0], r01 = g.frot[1];
+    const float bx = g.frot[3] * y, byy = g.frot[4] * y;
+    const float c = g.fc, t = g.ft;
+    if (!(r00 > 0.0f)) { state = -1; return; }
+    const float X0 = (0.0f - bx) / r00, X1 = (c - bx) / r00;
+    // quick reject: |y'| along the segment exceeds the maximum half thickness
+    float ymin = fminf(fabsf(r01 * X0 + byy), fabsf(r01 * X1 + byy));
+    if ((r01 * X0 + byy) * (r01 * X1 + byy) < 0.0f) ymin = 0.0f;
+    if (ymin > 0.6f * t * c + 1e-4f * c) return;
+    // maximum: 8 samples per round; for a concave depth the maximum lies
+    // within one spacing of the best sample, so the bracket shrinks 4x
+    float lo = X0, hi = X1;
+    for (int r = 0; r < 8; ++r) {
+      const float w = (hi - lo) * (1.0f / RG);
+      const int bi = Gp.arg_max(airfoil_f32(t, c, r00, r01, bx, byy, lo + ((float)Gp.sl + 0.5f) * w));
+      const float xbest = lo + ((float)bi + 0.5f) * w;
+      lo = fmaxf(X0, xbest - w);
+      hi = fminf(X1, xbest + w);
+    }
+    const float xm = 0.5f * (lo + hi);
+    const float fm = airfoil_f32(t, c, r00, r01, bx, byy, xm);
+    const float tol = 1e-4f * c;
+    cx = xm;
+    if (fm < -tol) return;
+    // a grazing row whose maximum depth rounds to <= 0 holds at most a few
+    // cells around the maximum; any positive depth gets bracketed roots
+    if (fm <= 0.0f) { state = ROW_TANGENT; iv = (int)lrintf(frac(cx)); return; }
+    // roots on either side of the maximum (8-way refinement, depth monotone
+    // there); where the depth is still >= 0 at the segment end the run ends
+    // there (x' = 0 or x' = c)
+    float xa_f = X0, xb_f = X1;
+    if (airfoil_f32(t, c, r00, r01, bx, byy, X0) < 0.0f) {
+      float a = X0, b = xm;                        // depth(a) < 0 <= depth(b)
+      for (int r = 0; r < 6; ++r) {
+        const float w = (b - a) * (1.0f / RG);
+        const float xs = a + ((float)Gp.sl + 1.0f) * w;
+        const unsigned pos = Gp.ballot(Gp.sl == RG - 1 || airfoil_f32(t, c, r00, r01, bx, byy, xs) >= 0.0f);
+        const int i0 = __ffs(pos) - 1;
+        b = a + (float)(i0 + 1) * w;
+        a = a + (float)i0 * w;
+      }
+      xa_f = 0.5f * (a + b);
+    }
+    if (airfoil_f32(t, c, r00, r01, bx, byy, X1) < 0.0f) {
+      float a = xm, b = X1;                        // depth(a) >= 0 > depth(b)
+      for (int r = 0; r < 6; ++r) {
+        const float w = (b - a) * (1.0f / RG);
+        const float xs = a + ((float)Gp.sl + 1.0f) * w;
+        const unsigned neg = Gp.ballot(Gp.sl == RG - 1 || airfoil_f32(t, c, r00, r01, bx, byy, xs) < 0.0f);
+        const int i0 = __ffs(neg) - 1;
+        b = a + (float)(i0 + 1) * w;
+        a = a + (float)i0 * w;
+      }
+      xb_f = 0.5f * (a + b);
+    }
+    xa = xa_f; xb = xb_f;
+  }
+  const float fa = frac(xa), fb = frac(xb);
+  if (fb < -2.0f || fa > n + 1.0f) return;
+  ia = (int)ceilf(fmaxf(fa, -4.0f));
+  ib = (int)floorf(fminf(fb, (float)n + 3.0f));
+  if (ia > ib) { state = ROW_TANGENT; iv = (int)lrintf(frac(cx)); return; }
+  state = ROW_RUN;
+}
+
+// exact run [s, t] of a row by the group: windows of the estimate confirmed
+// with the exact predicate (one cell per lane), exact 8-way search or sweep
+// as the fallback; counts fallbacks in stats[0]
+__device__ void exact_run_grp(const Geom& g, int j, int k, const RowGrp& Gp, int& s, int& t,
+                              int* status, int* stats) {
+  const int n = g.n[0];
+  int state, ia, ib, iv;
+  estimate_row_grp(g, j, k, Gp, state, ia, ib, iv);
+  s = 0; t = -1;
+  if (state < 0) { if (Gp.sl == 0) set_status(status, S_EINVAL); return; }
+  if (state == ROW_EMPTY) return;
+  RowF R;
+  row_consts_f(g, j, k, R);
+  bool ok = true;
+  if (state == ROW_RUN) {
+    const int cell = Gp.sl < 4 ? ia - 2 + Gp.sl : ib - 1 + (Gp.sl - 4);
+    const unsigned w = Gp.ballot(pred_cell(g, R, cell, j, k));
+    const unsigned bl = w & 0xFu, bu = w >> 4;
+    if (bl == 0 || bu == 0) ok = false;
+    else {
+      const int m0 = __ffs(bl) - 1, m1 = 31 - __clz(bu);
+      s = ia - 2 + m0;
+      t = ib - 1 + m1;
+      if (m0 == 0 && s > 0) ok = false;
+      if (m1 == 3 && t < n - 1) ok = false;
+      if (s > t) ok = false;
+    }
+  } else {  // tangent: a short run (or none) around the vertex
+    const unsigned bw = Gp.ballot(pred_cell(g, R, iv - 3 + Gp.sl, j, k));
+    if (bw == 0) { s = 0; t = -1; return; }
+    const int m0 = __ffs(bw) - 1, m1 = 31 - __clz(bw);
+    s = iv - 3 + m0;
+    t = iv - 3 + m1;
+    if ((m0 == 0 && s > 0) || (m1 == 7 && t < n - 1)) ok = false;
+    const unsigned run = bw >> m0;
+    if ((run & (run + 1)) != 0) ok = false;     // not contiguous
+  }
+  if (ok) return;
+  if (Gp.sl == 0) atomicAdd(&stats[0], 1);
+  // fallback 1: a solid seed inside the estimated run; the run is an
+  // interval (convex body), so search both ends with the exact predicate
+  const int seed = state == ROW_RUN ? (ia + ib) / 2 : iv;
+  if (seed >= 0 && seed < n && solid_cell(g, seed, j, k)) {
+    int lo = -1, hi = seed;              // pred(lo) false (virtual), pred(hi) true
+    while (hi - lo > 1) {
+      const int step = (hi - lo + RG - 1) / RG;
+      const int x = min(lo + (Gp.sl + 1) * step, hi);
+      const unsigned p = Gp.ballot(x >= hi || solid_cell(g, x, j, k));
+      const int i0 = __ffs(p) - 1;
+      hi = min(lo + (i0 + 1) * step, hi);
+      lo = lo + i0 * step;
+    }
+    s = hi;
+    lo = seed; hi = n;                   // pred(lo) true, pred(hi) false (virtual)
+    while (hi - lo > 1) {
+      const int step = (hi - lo + RG - 1) / RG;
+      const int x = min(lo + (Gp.sl + 1) * step, hi);
+      const unsigned p = Gp.ballot(x >= hi || !solid_cell(g, x, j, k));
+      const int i0 = __ffs(p) - 1;
+      hi = min(lo + (i0 + 1) * step, hi);
+      lo = lo + i0 * step;
+    }
+    t = lo;
+  } else {
+    // fallback 2: sweep the whole row with the exact predicate
+    int mn = n, mx = -1;
+    for (int i = Gp.sl; i < n; i += RG)
+      if (solid_cell(g, i, j, k)) { mn = min(mn, i); mx = max(mx, i); }
+    mn = Gp.min_i(mn);
+    mx = Gp.max_i(mx);
+    if (mx < 0) { s = 0; t = -1; } else { s = mn; t = mx; }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_rows(const Geom* __restrict__ G, const int* __restrict__ row_off,
                                               int B, int total_rows, int2* __restrict__ runs,
                                               int8_t* __restrict__ tags, int* status, int* stats) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int base = warp * 32; base < total_rows; base += nwarps * 32) {
-    int row = base + lane;
-    int s = 0, t = -1, nx = 0;
-    long long start = 0;
-    if (row < total_rows) {
-      int b = find_seg(row_off, B, row);
-      const Geom& g = G[b];
-      int local = row - g.row_off;
-      int j = local % g.n[1];
-      int k = local / g.n[1];
-      exact_run(g, j, k, s, t, status, stats);
-      runs[row] = make_int2(s, t);
-      nx = g.n[0];
-      start = g.cell_off + (long long)local * nx;
-    }
-    // the warp streams the tags of its rows
-    int nvalid = min(32, total_rows - base);
-    for (int r = 0; r < nvalid; ++r) {
-      int rs = __shfl_sync(0xffffffffu, s, r);
-      int rt = __shfl_sync(0xffffffffu, t, r);
-      int rn = __shfl_sync(0xffffffffu, nx, r);
-      long long rst = __shfl_sync(0xffffffffu, start, r);
-      long long end = rst + rn;
-      // 16-byte alignment of the actual addresses (the caller's buffer may be offset)
-      long long mis = (long long)(reinterpret_cast<uintptr_t>(tags) & 15u);
-      long long a0 = ((rst + mis + 15) & ~15LL) - mis;
-      long long a1 = ((end + mis) & ~15LL) - mis;
-      if (a0 > end) a0 = end;
-      if (a1 < a0) a1 = a0;
-      // head bytes [rst, a0) and tail bytes [a1, end)
-      long long nh = a0 - rst, nt = end - a1;
-      if (lane < nh) {
-        long long i = lane;
-        tags[rst + i] = (int8_t)(i >= rs && i <= rt);
-      }
-      if (lane < nt) {
-        long long i = a1 + lane - rst;
-        tags[a1 + lane] = (int8_t)(i >= rs && i <= rt);
-      }
-      // aligned middle: 16 cells per lane per step.  Bytes [lo, hi) of the
-      // chunk lie inside the run; each 32-bit word is a difference of two
-      // prefix masks of 0x01 bytes.
-      for (long long c = a0 + 16LL * lane; c < a1; c += 16LL * 32) {
-        int i0 = (int)(c - rst);
-        int lo = min(max(rs - i0, 0), 16);
-        int hi = min(max(rt + 1 - i0, 0), 16);
-        uint32_t w[4];
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) / RG;
+  if (row >= total_rows) return;                 // the whole group leaves together
+  RowGrp Gp;
+  Gp.sl = lane & (RG - 1);
+  Gp.shift = lane & ~(RG - 1);
+  Gp.mask = 0xFFu << Gp.shift;
+  const int b = find_seg(row_off, B, row);
+  const Geom& g = G[b];
+  const int local = row - g.row_off;
+  const int j = local % g.n[1];
+  const int k = local / g.n[1];
+  int s, t;
+  exact_run_grp(g, j, k, Gp, s, t, status, stats);
+  if (Gp.sl == 0) runs[row] = make_int2(s, t);
+  // the group streams the tags of its row
+  const int nx = g.n[0];
+  const long long rst = g.cell_off + (long long)local * nx, end = rst + nx;
+  // 16-byte alignment of the actual addresses (the caller's buffer may be offset)
+  const long long mis = (long long)(reinterpret_cast<uintptr_t>(tags) & 15u);
+  long long a0 = ((rst + mis + 15) & ~15LL) - mis;
+  long long a1 = ((end + mis) & ~15LL) - mis;
+  if (a0 > end) a0 = end;
+  if (a1 < a0) a1 = a0;
+  for (long long q = rst + Gp.sl; q < a0; q += RG) {
+    const long long i = q - rst;
+    tags[q] = (int8_t)(i >= s && i <= t);
+  }
+  for (long long q = a1 + Gp.sl; q < end; q += RG) {
+    const long long i = q - rst;
+    tags[q] = (int8_t)(i >= s && i <= t);
+  }
+  // aligned middle: 16 cells per lane per step.  Bytes [lo, hi) of the chunk
+  // lie inside the run; each 32-bit word is a difference of two prefix masks
+  // of 0x01 bytes.
+  for (long long c = a0 + 16LL * Gp.sl; c < a1; c += 16LL * RG) {
+    const int i0 = (int)(c - rst);
+    const int lo = min(max(s - i0, 0), 16);
+    const int hi = min(max(t + 1 - i0, 0), 16);
+    uint32_t w[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          int l = min(max(lo - 4 * q, 0), 4), h = min(max(hi - 4 * q, 0), 4);
-          uint32_t ph = h ? (0x01010101u >> (8 * (4 - h))) : 0u;
-          uint32_t pl = l ? (0x01010101u >> (8 * (4 - l))) : 0u;
-          w[q] = h > l ? (ph & ~pl) : 0u;
-        }
-        *reinterpret_cast<uint4*>(tags + c) = make_uint4(w[0], w[1], w[2], w[3]);
-      }
+    for (int q = 0; q < 4; ++q) {
+      const int l = min(max(lo - 4 * q, 0), 4), h = min(max(hi - 4 * q, 0), 4);
+      const uint32_t ph = h ? (0x01010101u >> (8 * (4 - h))) : 0u;
+      const uint32_t pl = l ? (0x01010101u >> (8 * (4 - l))) : 0u;
+      w[q] = h > l ? (ph & ~pl) : 0u;
     }
+    *reinterpret_cast<uint4*>(tags + c) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
 void launch_rows(const Geom* G, const int* row_off, int B, int total_rows, int2* runs,
                  int8_t* tags, int* status, int* stats, cudaStream_t s) {
   if (total_rows <= 0) return;
-  int warps = (total_rows + 31) / 32;
-  int blocks = (warps + 7) / 8;
-  k_rows<<<blocks, 256, 0, s>>>(G, row_off, B, total_rows, runs, tags, status, stats);
+  const long long threads = (long long)total_rows * RG;
+  k_rows<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(G, row_off, B, total_rows, runs, tags, status, stats);
 }
 
 // ---------------------------------------------------------------------------

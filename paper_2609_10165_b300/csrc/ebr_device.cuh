@@ -45,6 +45,7 @@ struct Geom {
   // float copies for the float pre-decisions (no double work or conversions
   // per cell); hgc_mrg = safety margin of the float HGC decision
   float flo[3], fh[3], fcentre[3], fradii[3], frot[9], ft, fc, hgc_mrg;
+  float fext;                // max(1, largest |grid corner - centre| over the axes)
 };
 
 // ---------------------------------------------------------------------------
