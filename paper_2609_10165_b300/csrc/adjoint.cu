@@ -25,41 +25,51 @@ struct AdjSet {
   void* gbc[8];
 };
 
-__global__ void k_adj_seed(int dim, int F, AdjSet roles_unused, int4 role, double mu, double dd0,
-                           double dd1, double dd2, double dl0, double dl1, double dl2,
-                           const double* __restrict__ seed, int ng, const int* __restrict__ g_geo,
-                           const double* __restrict__ g_n, const double* __restrict__ ftab,
-                           double* __restrict__ sv) {
-  (void)roles_unused;
+template <int D>
+__global__ void k_adj_seed(int F, int4 role, double mu, double dd0, double dd1, double dd2,
+                           double dl0, double dl1, double dl2, const double* __restrict__ seed,
+                           int ng, const int* __restrict__ g_geo, const double* __restrict__ g_n,
+                           const double* __restrict__ ftab, double* __restrict__ sv) {
+  constexpr int K = D == 2 ? 3 : 7;
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
   int b = g_geo[p];
-  double s0 = seed[2 * b], s1 = seed[2 * b + 1];
-  double q[3] = {s0 * dd0 + s1 * dl0, s0 * dd1 + s1 * dl1, s0 * dd2 + s1 * dl2};
-  double n[3] = {g_n[p], g_n[ng + p], g_n[2 * (size_t)ng + p]};
-  double wG = ftab[p];
+  const double s0 = seed[2 * b], s1 = seed[2 * b + 1];
+  const double dd[3] = {dd0, dd1, dd2}, dl[3] = {dl0, dl1, dl2};
+  double q[D], n[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    q[a] = s0 * dd[a] + s1 * dl[a];
+    n[a] = g_n[(size_t)a * ng + p];
+  }
+  const double wG = ftab[p];
   double qn = 0.0;
-  for (int a = 0; a < dim; ++a) qn += q[a] * n[a];
+#pragma unroll
+  for (int a = 0; a < D; ++a) qn += q[a] * n[a];
   const int vel[3] = {role.x, role.y, role.z};
   const int pidx = role.w;
-  const int K = stencil_k(dim);
   for (int f = 0; f < F; ++f) {
-    int m = -1;
-    for (int a = 0; a < dim; ++a)
-      if (vel[a] == f) m = a;
+    // velocity component of field f (if any), selected without indexing
+    bool isv = false;
+    double qm = 0.0, nm = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (vel[a] == f) { isv = true; qm = q[a]; nm = n[a]; }
+#pragma unroll
     for (int s = 0; s < 8; ++s) {
       double c = 0.0;
       if (s <= K) {
         if (f == pidx) {
           c = -wG * qn * ftab[(size_t)(1 + s) * ng + p];
-        } else if (m >= 0) {
+        } else if (isv) {
           double bn = 0.0, qb = 0.0;
-          for (int a = 0; a < dim; ++a) {
-            double beta = ftab[(size_t)(9 + 8 * a + s) * ng + p];
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            const double beta = ftab[(size_t)(9 + 8 * a + s) * ng + p];
             bn += beta * n[a];
             qb += beta * q[a];
           }
-          c = wG * mu * (q[m] * bn + n[m] * qb);
+          c = wG * mu * (qm * bn + nm * qb);
         }
       }
       sv[(size_t)(f * 8 + s) * ng + p] = c;
@@ -71,12 +81,15 @@ void launch_adj_seed(int dim, int F, const int* role, double mu, const double* d
                      const double* seed, int ng, const int* g_geo, const double* g_n,
                      const double* ftab, double* sv, cudaStream_t s) {
   if (ng <= 0) return;
-  AdjSet dummy{};
   int4 r = make_int4(role[0], role[1], role[2], role[3]);
   double dd[3] = {0, 0, 0}, dl[3] = {0, 0, 0};
   for (int a = 0; a < dim; ++a) { dd[a] = dirs[a]; dl[a] = dirs[dim + a]; }
-  k_adj_seed<<<(ng + 127) / 128, 128, 0, s>>>(dim, F, dummy, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1],
-                                              dl[2], seed, ng, g_geo, g_n, ftab, sv);
+  if (dim == 2)
+    k_adj_seed<2><<<(ng + 127) / 128, 128, 0, s>>>(F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
+                                                   seed, ng, g_geo, g_n, ftab, sv);
+  else
+    k_adj_seed<3><<<(ng + 127) / 128, 128, 0, s>>>(F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
+                                                   seed, ng, g_geo, g_n, ftab, sv);
 }
 
 template <typename T>

@@ -394,7 +394,8 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     AL(c->g_meta, ng);
     AL(c->lev_ptr, ng + c->B + 1);
     {
-      size_t cap = (size_t)max_smem_optin(), need = 0;
+      // the level kernel also holds ~9 KB of static shared memory
+      size_t cap = (size_t)max_smem_optin() - 12 * 1024, need = 0;
       for (int b = 0; b < c->B; ++b) {
         size_t q = levels_smem(c->hG[b].dim, c->hG[b].n_ghost);
         if (q <= cap) need = std::max(need, q);

@@ -246,20 +246,33 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
     float d = (x - fqx) * (x - fqx) + (y - fqy) * (y - fqy);
     if (d < bd) { bd = d; best = s; }
   }
-  double lo = fmax(0.0, (double)(best - 1) / NS), hi = fmin(1.0, (double)(best + 1) / NS);
+  double lo = fmax(0.0, (double)(best - 1) * (1.0 / NS)), hi = fmin(1.0, (double)(best + 1) * (1.0 / NS));
+  // surface point, first and second derivatives at the last evaluated u
+  double x = 0.0, y = 0.0, dx = 0.0, dy = 0.0, ddx = 0.0, ddy = 0.0;
   auto g = [&](double u, double& gv, double& dg) {
-    double x, y, dx, dy, ddx, ddy;
     airfoil_u(t, c, u, x, y, dx, dy, ddx, ddy);
     gv = (x - qx) * dx + (y - qy) * dy;
     dg = dx * dx + dy * dy + (x - qx) * ddx + (y - qy) * ddy;
   };
-  double glo, dlo, ghi, dhi;
-  g(lo, glo, dlo);
-  g(hi, ghi, dhi);
+  // sign of g at a bracket end: in float where it is clearly away from zero
+  // (the margin bounds the float rounding of both products by a wide
+  // factor), in double otherwise
+  auto end_sign = [&](double ue) -> int {
+    float xf, yf, dxf, dyf, ddxf, ddyf;
+    airfoil_u32(ft, fc, (float)ue, xf, yf, dxf, dyf, ddxf, ddyf);
+    const float gf = (xf - fqx) * dxf + (yf - fqy) * dyf;
+    const float m = 1e-5f * (1.0f + fabsf(xf) + fabsf(fqx) + fabsf(yf) + fabsf(fqy)) * (fabsf(dxf) + fabsf(dyf));
+    if (gf > m) return 1;
+    if (gf < -m) return -1;
+    double gv, dg;
+    g(ue, gv, dg);
+    return gv > 0.0 ? 1 : (gv < 0.0 ? -1 : 0);
+  };
   double u;
-  if (glo >= 0.0) {
+  bool have = false;           // x .. ddy hold the values at u
+  if (end_sign(lo) >= 0) {
     u = lo;                    // distance increases from lo on (lo == 0 here)
-  } else if (ghi <= 0.0) {
+  } else if (end_sign(hi) <= 0) {
     u = hi;                    // distance decreases up to hi (hi == 1 here)
   } else {
     // float Newton inside the bracket
@@ -286,14 +299,22 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
     for (int it = 0; it < 40; ++it) {
       double gv, dg;
       g(u, gv, dg);
-      if (gv == 0.0) break;
+      if (gv == 0.0) { have = true; break; }
       // Newton increment in float (g in double): see ellipse_closest
       const double st = dg > 0.0 ? (double)((float)gv / (float)dg) : 0.0;
       // converged: a Newton step of 1e-12 (relative) leaves an error below the
       // rounding level; accept it before the safeguard, which would otherwise
-      // bisect once the step rounds onto the bracket end
+      // bisect once the step rounds onto the bracket end.  The point and the
+      // tangent at the new u follow from the last evaluation to first order
+      // (the neglected terms are ~step^2, far below the rounding level).
       if (dg > 0.0 && fabs(st) <= 1e-12 * fmax(u, 1e-3)) {
-        u = fmin(fmax(u - st, lo), hi);
+        const double un = fmin(fmax(u - st, lo), hi), du = un - u;
+        x += dx * du;
+        y += dy * du;
+        dx += ddx * du;
+        dy += ddy * du;
+        u = un;
+        have = true;
         break;
       }
       if (gv < 0.0) lo = u; else hi = u;
@@ -302,8 +323,7 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
       u = un;
     }
   }
-  double x, y, dx, dy, ddx, ddy;
-  airfoil_u(t, c, u, x, y, dx, dy, ddx, ddy);
+  if (!have) airfoil_u(t, c, u, x, y, dx, dy, ddx, ddy);
   double d2u = (x - qx) * (x - qx) + (y - qy) * (y - qy);
   // half thickness at the trailing edge: the polynomial at u = 1
   const double yte = 5.0 * t * c * (0.2969 + -0.1260 + -0.3516 + 0.2843 + -0.1015);

@@ -19,7 +19,8 @@ struct VelSet {
   double dirs[6];
 };
 
-template <typename T>
+// D (2 or 3) fixed at compile time keeps the per-ghost arrays in registers
+template <typename T, int D>
 __global__ void __launch_bounds__(FC_T) k_forces_chunk(VelSet V, double mu, const Geom* __restrict__ G,
                                                        const int4* __restrict__ chunks,
                                                        const int* __restrict__ g_cell,
@@ -28,59 +29,72 @@ __global__ void __launch_bounds__(FC_T) k_forces_chunk(VelSet V, double mu, cons
                                                        const uint32_t* __restrict__ g_meta,
                                                        const double* __restrict__ ftab, int ng,
                                                        double* __restrict__ partial) {
+  constexpr int K = D == 2 ? 3 : 7;
   __shared__ double red[FC_T][8];
   int4 ch = chunks[blockIdx.x];        // (geometry, p0, p1, -)
   const Geom& g = G[ch.x];
-  const int d = g.dim, K = stencil_k(d), nx = g.n[0], ny = g.n[1];
+  const int nx = g.n[0], ny = g.n[1];
   int p = ch.y + threadIdx.x;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (p < ch.z) {
     int cell = g_cell[p];
     uint32_t m = g_meta[p];
-    int slots[8];
+    int slots[K + 1];
     slots[0] = cell;
+#pragma unroll
     for (int k = 0; k < K; ++k) {
       int o[3];
-      stencil_off(d, k, o);
+      stencil_off(D, k, o);
       int off = o[0] * meta_r(m, 0) * meta_e(m, 0) + nx * (o[1] * meta_r(m, 1) * meta_e(m, 1));
-      if (d == 3) off += nx * ny * (o[2] * meta_r(m, 2) * meta_e(m, 2));
+      if (D == 3) off += nx * ny * (o[2] * meta_r(m, 2) * meta_e(m, 2));
       slots[k + 1] = cell + off;
     }
-    double n[3] = {g_n[p], g_n[ng + p], g_n[2 * (size_t)ng + p]};
+    double n[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) n[a] = g_n[(size_t)a * ng + p];
     double wG = ftab[p];
     const T* pp = static_cast<const T*>(V.p) + g.cell_off;
     double ps = 0.0;
+#pragma unroll
     for (int s = 0; s <= K; ++s) ps += ftab[(size_t)(1 + s) * ng + p] * (double)pp[slots[s]];
-    double Gm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // Gm[i][a] = d u_i / d x_a
-    for (int i = 0; i < d; ++i) {
+    double Gm[D][D];                                        // Gm[i][a] = d u_i / d x_a
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int a = 0; a < D; ++a) Gm[i][a] = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
       if (!V.u[i]) continue;
       const T* ui = static_cast<const T*>(V.u[i]) + g.cell_off;
+#pragma unroll
       for (int s = 0; s <= K; ++s) {
         double v = (double)ui[slots[s]];
-        for (int a = 0; a < d; ++a) Gm[i][a] += ftab[(size_t)(9 + 8 * a + s) * ng + p] * v;
+#pragma unroll
+        for (int a = 0; a < D; ++a) Gm[i][a] += ftab[(size_t)(9 + 8 * a + s) * ng + p] * v;
       }
     }
-    double fp[3], fv[3];
-    for (int i = 0; i < d; ++i) {
-      fp[i] = -ps * n[i] * wG;
-      double t = 0.0;
-      for (int a = 0; a < d; ++a) t += (Gm[i][a] + Gm[a][i]) * n[a];
-      fv[i] = mu * t * wG;
-    }
     double dr = 0.0, li = 0.0;
-    for (int i = 0; i < d; ++i) {
-      acc[i] = fp[i];
-      acc[d + i] = fv[i];
-      dr += (fp[i] + fv[i]) * V.dirs[i];
-      li += (fp[i] + fv[i]) * V.dirs[d + i];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const double fp = -ps * n[i] * wG;
+      double t = 0.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) t += (Gm[i][a] + Gm[a][i]) * n[a];
+      const double fv = mu * t * wG;
+      acc[i] = fp;
+      acc[D + i] = fv;
+      dr += (fp + fv) * V.dirs[i];
+      li += (fp + fv) * V.dirs[D + i];
     }
-    acc[2 * d] = dr;
-    acc[2 * d + 1] = li;
+    acc[2 * D] = dr;
+    acc[2 * D + 1] = li;
   }
+#pragma unroll
   for (int q = 0; q < 8; ++q) red[threadIdx.x][q] = acc[q];
   __syncthreads();
   for (int w = FC_T / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
+#pragma unroll
       for (int q = 0; q < 8; ++q) red[threadIdx.x][q] += red[threadIdx.x + w][q];
     __syncthreads();
   }
@@ -108,10 +122,14 @@ void launch_forces(int dtype, int dim, const void* const* vel, const void* p, do
   V.p = p;
   for (int q = 0; q < 6; ++q) V.dirs[q] = q < 2 * dim ? dirs[q] : 0.0;
   if (n_chunks > 0) {
-    if (dtype == 0)
-      k_forces_chunk<float><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+    if (dtype == 0 && dim == 2)
+      k_forces_chunk<float, 2><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+    else if (dtype == 0)
+      k_forces_chunk<float, 3><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+    else if (dim == 2)
+      k_forces_chunk<double, 2><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
     else
-      k_forces_chunk<double><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+      k_forces_chunk<double, 3><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
   }
   k_forces_final<<<(B + 127) / 128, 128, 0, s>>>(B, G, chunk_ptr, partial, out);
 }

@@ -78,6 +78,7 @@ void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, u
 // in one pass (warps in order, __match_any_sync within a warp); larger ones
 // work on global memory with one block scan per level.
 constexpr int LV_T = 1024;
+constexpr int LV_NL = 64;        // levels ranked with per-warp counts (more: warp by warp)
 
 size_t levels_smem(int dim, int n) {
   return ((size_t)(stencil_k(dim) + 2) * n + 1) * sizeof(int) + 64;
@@ -89,8 +90,10 @@ __global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int
                                                  int* __restrict__ lev_ptr, int* __restrict__ n_levels,
                                                  int smem_ints, int* status) {
   extern __shared__ int sm[];
-  __shared__ int sh_cnt;
+  __shared__ int sh_cnt3[3];
   __shared__ int sh_warp[32];
+  __shared__ int sh_wl[LV_T / 32][LV_NL];     // per-warp counts of each level (ranking)
+  __shared__ int sh_tot[LV_NL];               // chunk total of each level
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
     const Geom& g = G[b];
@@ -108,13 +111,17 @@ __global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int
           dl[(size_t)k * n + s] = d >= 0 ? d - g0 : -1;
         }
     }
-    if (threadIdx.x == 0) lp[0] = g0;
+    if (threadIdx.x == 0) {
+      lp[0] = g0;
+      sh_cnt3[0] = sh_cnt3[1] = sh_cnt3[2] = 0;
+    }
     __syncthreads();
+    // one barrier per sweep: the count of sweep L lives in sh_cnt3[L % 3];
+    // thread 0 clears the slot of sweep L + 1, last read in sweep L - 2
     int remaining = n, L = 0;
     while (remaining > 0) {
       ++L;
-      if (threadIdx.x == 0) sh_cnt = 0;
-      __syncthreads();
+      if (threadIdx.x == 0) sh_cnt3[(L + 1) % 3] = 0;
       int mine = 0;
       for (int s = threadIdx.x; s < n; s += LV_T) {
         if (lvl[s] != 0) continue;
@@ -128,24 +135,56 @@ __global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int
         }
         if (ok) { lvl[s] = L; ++mine; }
       }
-      if (mine) atomicAdd(&sh_cnt, mine);
+      if (mine) atomicAdd(&sh_cnt3[L % 3], mine);
       __syncthreads();
-      int cnt = sh_cnt;
-      __syncthreads();
+      const int cnt = sh_cnt3[L % 3];
       if (cnt == 0) {
         if (threadIdx.x == 0) set_status(status, S_ECYCLE);
         break;
       }
       remaining -= cnt;
       if (threadIdx.x == 0) lp[L] = lp[L - 1] + cnt;
-      __syncthreads();
     }
+    __syncthreads();
     int nl = remaining > 0 ? 0 : L;
     if (threadIdx.x == 0) n_levels[b] = nl;
     __syncthreads();
     if (remaining > 0) continue;
-    if (fast) {
-      // pos[L] = next free canonical slot of level L (the dependency area is free now)
+    if (fast && nl < LV_NL) {
+      // stable counting sort by level: pos[L] = next free canonical slot of
+      // level L (the dependency area is free now); per chunk of LV_T ghosts,
+      // slot = pos[L] + (same-level ghosts of earlier warps in the chunk) +
+      // (same-level lanes before it in its warp)
+      int* pos = sm + n;
+      for (int q = threadIdx.x; q < nl; q += LV_T) pos[q + 1] = lp[q];
+      for (int base = 0; base < n; base += LV_T) {
+        for (int q = threadIdx.x; q < (LV_T / 32) * LV_NL; q += LV_T) (&sh_wl[0][0])[q] = 0;
+        __syncthreads();
+        const int s = base + threadIdx.x;
+        const int L2 = s < n ? lvl[s] : 0;
+        const unsigned peers = __match_any_sync(0xffffffffu, L2);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (s < n && lane == __ffs(peers) - 1) sh_wl[w][L2] = __popc(peers);
+        __syncthreads();
+        // exclusive prefix over the warps, one thread per level
+        for (int q = threadIdx.x; q <= nl; q += LV_T) {
+          int acc = 0;
+          for (int ww = 0; ww < LV_T / 32; ++ww) {
+            const int v = sh_wl[ww][q];
+            sh_wl[ww][q] = acc;
+            acc += v;
+          }
+          sh_tot[q] = acc;
+        }
+        __syncthreads();
+        if (s < n) order_pos[g0 + s] = pos[L2] + sh_wl[w][L2] + rank;
+        __syncthreads();
+        for (int q = threadIdx.x + 1; q <= nl; q += LV_T) pos[q] += sh_tot[q];
+      }
+      __syncthreads();
+      for (int s = threadIdx.x; s < n; s += LV_T) level[g0 + s] = lvl[s];
+    } else if (fast) {
+      // more than LV_NL - 1 levels: warps in order, one at a time
       int* pos = sm + n;
       for (int q = threadIdx.x; q < nl; q += LV_T) pos[q + 1] = lp[q];
       __syncthreads();
