@@ -334,8 +334,8 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
 # kernel).  The many-field calls were captured on 32 geometries and scaled by
 # the ghost count.  A kernel changed since its capture is left out (None).
 TRAFFIC_PER_LAUNCH = {
-    "adj_fluid": 27.44e6, "fill_chain": 28.36e6, "forces": 34.96e6, "adj_chain": 6.41e6,
-    "levels": 1.11e6, "rows": 0.57e6,
+    "adj_fluid": 33.85e6, "fill_chain": 28.37e6, "forces": 32.54e6, "adj_chain": 6.40e6,
+    "levels": 1.11e6, "rows": 0.25e6, "place": 1.77e6, "gsrc": 14.11e6,
     "pfill": 123.0e6, "padj": 153.0e6,
 }
 
