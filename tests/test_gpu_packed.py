@@ -2,8 +2,9 @@
 its transpose) against the oracle's level-walk fill and its vector-Jacobian
 product, on seeded random fields.  FP64 within 1e-12 of the magnitude of the
 terms, FP32 within 1e-5 of the largest magnitude (tests/parity.py); the
-packed fill must equal the per-field-array fill bit for bit, and the
-transpose must be bitwise reproducible."""
+packed fill must equal the per-field-array fill bit for bit, the two packed
+kernels must satisfy the adjoint identity, and the transpose must be bitwise
+reproducible."""
 
 import numpy as np
 import pytest
@@ -150,6 +151,30 @@ def test_packed_fill_equals_field_arrays_bitwise(dtype):
     R.sync_status()
     for f in range(3):
         assert torch.equal(ft[:, f], fa[f])
+
+
+def test_packed_adjoint_identity_fp64():
+    """<ybar, fill(x, b)> = <xbar, x> + <bbar, b> for the GPU fill and the GPU
+    transpose: the two kernels are transposes of one linear map (the ghost
+    entries of the filled field depend only on fluid entries and boundary
+    data, every other entry passes through)."""
+    for cases, F in ((MIXED_2D, 7), (SPHERE_3D, 5)):
+        R, info, x, b = _setup(cases, "HGC", F, torch.float64, 17)
+        kinds = _kinds(F)
+        rng = np.random.default_rng(18)
+        ybar = rng.normal(size=(R.n_cells, F))
+        y = torch.tensor(x, device=R.device)
+        R.reconstruct_packed(y, kinds, torch.tensor(b, device=R.device))
+        cot = torch.tensor(ybar, device=R.device)
+        gb = torch.empty((info["cell"].size, F), dtype=torch.float64, device=R.device)
+        R.reconstruct_packed_adjoint(kinds, cot, gb)
+        R.sync_status()
+        yb = torch.tensor(ybar, device=R.device)
+        xt, bt = torch.tensor(x, device=R.device), torch.tensor(b, device=R.device)
+        lhs = float((yb * y).sum())
+        rhs = float((cot * xt).sum() + (gb * bt).sum())
+        scale = float((yb.abs() * y.abs()).sum())
+        assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
