@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--geoms", type=int, default=256)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--sets", type=int, default=32, help="field sets of the throughput mode (0: skip)")
     ap.add_argument("--lite", action="store_true",
                     help="headline step only (no plain FP64 path, no e2e, no CPU baseline), for profilers")
@@ -241,34 +242,112 @@ def time_steps(fn, steps, stream, flush):
     return [a.elapsed_time(b) for a, b in ts]
 
 
-def cpu_baseline(geoms_all, budget_s=15.0):
-    """The oracle as it stands on a bounded sample of the batch: classify,
-    levels, fill of 3 fields, forces and the explicit-matrix adjoint."""
+def _oracle_geometry(g):
+    """The oracle's whole path on one geometry; seconds per phase and the
+    updates (ghosts x 3 fields) it produced."""
     import oracle as O
     from paper_2609_10165_b300 import inputs as I
 
+    t = [time.perf_counter()]
+    c = O.classify(g["grid"], g["body"], "HGC")
+    lev = O.build_levels(c)
+    t.append(time.perf_counter())
+    X = c.grid.centre(c.grid.unlin(c.idx))
+    S = (X + c.psi[:, None] * c.n)[lev.order]
+    nn = c.n[lev.order]
+    arrays = [f.on_grid(g["grid"], np.float32).astype(np.float64) for f in g["fields"]]
+    bcs = [I.bc_values(f, k, S, nn) for f, k in zip(g["fields"], g["bc"])]
+    t.append(time.perf_counter())
+    out = O.fill(c, lev, arrays, g["bc"], bcs)
+    t.append(time.perf_counter())
+    O.forces(c, lev, out[2], [out[0], out[1]], g["mu"], I.DRAG_LIFT_DIRS_2D)
+    t.append(time.perf_counter())
+    O.adjoint_gradient(c, lev, g["bc"], 2, [0, 1], g["mu"], I.DRAG_LIFT_DIRS_2D, (1.0, 1.0))
+    t.append(time.perf_counter())
+    phases = {"classify_levels": t[1] - t[0], "inputs": t[2] - t[1], "fill": t[3] - t[2],
+              "forces": t[4] - t[3], "adjoint": t[5] - t[4]}
+    return c.n_ghosts * 3, phases
+
+
+def _oracle_geometry_index(args):
+    """Pool worker: rebuild the seeded batch (parameters only) and run one
+    geometry."""
+    n_geoms, gi = args
+    from paper_2609_10165_b300 import inputs as I
+    return _oracle_geometry(I.batch(n_geoms)[gi])
+
+
+# the step's kernels by phase of the method (the serial per-kernel profile;
+# "scan" holds all three exclusive scans, counted under classify)
+PHASES = {
+    "classify": ("rows", "iface", "scan", "place", "reclassify", "ghost_flags", "ghost_write"),
+    "levels": ("poscell", "deps", "levels", "reorder", "tables", "gsrc"),
+    "fill": ("fill_chain",),
+    "forces": ("forces",),
+    "adjoint": ("adj_seed", "adj_chain", "adj_fluid", "adj_bc"),
+}
+
+
+def phase_sums(prof_ms):
+    out = {ph: round(sum(prof_ms.get(k, 0.0) for k in ks), 5) for ph, ks in PHASES.items()}
+    named = {k for ks in PHASES.values() for k in ks}
+    rest = sum(v for k, v in prof_ms.items() if k not in named)
+    if rest:
+        out["other"] = round(rest, 5)
+    return out
+
+
+def cpu_baseline(geoms_all, budget_s=15.0):
+    """The oracle as it stands on a bounded sample of the batch, one thread:
+    classify, levels, fill of 3 fields, forces and the explicit-matrix
+    adjoint, with the seconds of each phase."""
     t0 = time.perf_counter()
     updates = 0
     done = 0
+    phases = {}
     for g in geoms_all:
-        c = O.classify(g["grid"], g["body"], "HGC")
-        lev = O.build_levels(c)
-        X = c.grid.centre(c.grid.unlin(c.idx))
-        S = (X + c.psi[:, None] * c.n)[lev.order]
-        nn = c.n[lev.order]
-        arrays = [f.on_grid(g["grid"], np.float32).astype(np.float64) for f in g["fields"]]
-        bcs = [I.bc_values(f, k, S, nn) for f, k in zip(g["fields"], g["bc"])]
-        out = O.fill(c, lev, arrays, g["bc"], bcs)
-        O.forces(c, lev, out[2], [out[0], out[1]], g["mu"], I.DRAG_LIFT_DIRS_2D)
-        O.adjoint_gradient(c, lev, g["bc"], 2, [0, 1], g["mu"], I.DRAG_LIFT_DIRS_2D, (1.0, 1.0))
-        updates += c.n_ghosts * 3
+        u, ph = _oracle_geometry(g)
+        updates += u
         done += 1
+        for k, v in ph.items():
+            phases[k] = phases.get(k, 0.0) + v
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
     return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d of %d geometries of %s (classify, levels, fill of 3 fields, forces, "
-                      "explicit-matrix adjoint), %.1f s" % (done, len(geoms_all), WORKLOAD, dt)}
+                      "explicit-matrix adjoint), %.1f s" % (done, len(geoms_all), WORKLOAD, dt),
+            "phases_s": {k: round(v, 3) for k, v in phases.items()}}
+
+
+def cpu_baseline_all_cores(n_geoms, budget_s=15.0):
+    """The same oracle path over all host cores: a process pool (spawn, so
+    that no worker inherits a CUDA context) runs geometries in parallel,
+    largest first, until the budget is spent; the sample is the geometries
+    finished by then."""
+    import multiprocessing as mp
+    from paper_2609_10165_b300 import inputs as I
+
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    geoms = I.batch(n_geoms)
+    order = sorted(range(n_geoms), key=lambda i: -geoms[i]["grid"]["n"][0])
+    ctx = mp.get_context("spawn")
+    updates = done = 0
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        for u, _ in pool.imap_unordered(_oracle_geometry_index, [(n_geoms, i) for i in order]):
+            updates += u
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+        pool.terminate()
+    return {"value": updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d geometries of %s, largest first, on a %d-process pool, %.1f s "
+                      "(worker start-up included)" % (done, n_geoms, WORKLOAD, cores, dt)}
 
 
 def run_reference(args):
@@ -497,6 +576,14 @@ def main():
     for _ in range(max(args.warmup, 3)):
         step()
     R.sync_status()
+    # launch shapes of the one-thread-per-item kernels, tuned on this workload
+    # (eager serial steps, per-launch events, L2 flushed) before any capture
+    tuned, tune_rep = None, None
+    if not args.no_autotune:
+        from paper_2609_10165_b300.autotune import autotune
+        tuned, tune_rep = autotune(R, Step(R, fields, bcs, geoms, "persistent", adjoint=True, overlap=False),
+                                   reps=5, flush=flush.zero_)
+        R.sync_status()
     l0 = R.launches
     step()
     torch.cuda.synchronize()
@@ -644,11 +731,13 @@ def main():
             "timing": "CUDA events recorded as nodes of a captured graph of the step without the two-stream overlap, mean of 5 replays, L2 flushed",
             "step_algo_bytes": sum(algo.values()),
             "step_frac": sum(algo.values()) / (ms_step * 1e-3) / 1e9 / peak,
-            "per_kernel": per_kernel}
+            "per_kernel": per_kernel,
+            "phases_ms": phase_sums(prof_ms)}
 
     baseline = None
     if rank == 0 and not args.no_baseline and not args.lite:
         baseline = cpu_baseline(geoms, budget_s=15.0)
+        baseline["all_cores"] = cpu_baseline_all_cores(args.geoms, budget_s=15.0)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -658,7 +747,9 @@ def main():
                    "fields": F, "placement": "HGC", "max_levels": max(c2["n_levels"] for c2 in counts),
                    "l2": "flushed before every timed step (512 MB write)", "graph": True,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "row_fallbacks_since_plan": diag["row_fallbacks"]},
+                   "row_fallbacks_since_plan": diag["row_fallbacks"],
+                   "block_sizes": tuned if tuned is not None else "defaults (128)"},
+        "autotune": tune_rep,
         "fwd_updates_per_s": total_updates / (ms_f * 1e-3), "fwd_ms_per_step": ms_f,
         "plain_fp64_updates_per_s": total_updates / (ms64 * 1e-3) if ms64 == ms64 else None,
         "plain_fp64_ms_per_step": ms64,

@@ -311,6 +311,31 @@ ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stre
 int64_t ebr_launch_count(const void* ctx);
 
 /* ---------------------------------------------------------------------------
+ * Launch shapes (tuning; the paper has no counterpart)
+ *
+ * Threads per block of the kernels that run one thread per item (interface
+ * cell, ghost, fluid target): "iface", "place", "ghost_write" (the per-ghost
+ * closest-point kernel of that step), "deps", "tables", "gsrc", "adj_seed",
+ * "adj_fluid", "adj_bc" -- the names under which ebr_profile_read reports
+ * them.  The block size changes scheduling only: every result is bitwise the
+ * same for every allowed value.  A launch reads the context's value when it
+ * is issued, so a graph captured earlier keeps the shapes it was captured
+ * with.  The Python autotuner (paper_2609_10165_b300/autotune.py) times the
+ * candidates with ebr_profile and sets the fastest.
+ * ------------------------------------------------------------------------- */
+
+/* Number of tunable kernels; writes up to max_entries names into h_names
+ * [max_entries][32] (NUL-terminated) when h_names is not NULL. */
+int32_t ebr_tunable_kernels(char* h_names, int32_t max_entries);
+/* Set the threads per block of one tunable kernel of this context: a
+ * multiple of 32 in 32..256 (default 128).  EBR_EINVAL for an unknown name
+ * or value (the old value stays). */
+ebr_status ebr_set_block_size(void* ctx, const char* kernel, int32_t threads);
+/* Current threads per block of a tunable kernel, or EBR_EINVAL (negative)
+ * for an unknown name. */
+int32_t ebr_get_block_size(const void* ctx, const char* kernel);
+
+/* ---------------------------------------------------------------------------
  * Timing (diagnostics; the paper has no counterpart)
  * ------------------------------------------------------------------------- */
 

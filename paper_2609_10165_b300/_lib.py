@@ -66,6 +66,9 @@ _SIGS = {
     "ebr_launch_count": (c_int64, [c_void_p]),
     "ebr_profile": (c_int32, [c_void_p, c_int32]),
     "ebr_profile_read": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32]),
+    "ebr_tunable_kernels": (c_int32, [c_void_p, c_int32]),
+    "ebr_set_block_size": (c_int32, [c_void_p, ctypes.c_char_p, c_int32]),
+    "ebr_get_block_size": (c_int32, [c_void_p, ctypes.c_char_p]),
     "ebr_classify_cells_static": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Body), c_void_p,
                                             c_void_p, c_void_p]),
 }

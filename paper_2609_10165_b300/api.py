@@ -229,6 +229,22 @@ class Reconstructor:
             out[nm] = (float(ms[k]), int(cnt[k]))
         return out
 
+    # -- launch shapes ----------------------------------------------------------
+    def tunable_kernels(self):
+        n = int(self.lib.ebr_tunable_kernels(None, 0))
+        names = ctypes.create_string_buffer(32 * n)
+        self.lib.ebr_tunable_kernels(names, n)
+        return [names.raw[32 * k: 32 * k + 32].split(b"\0", 1)[0].decode() for k in range(n)]
+
+    def set_block_size(self, kernel, threads):
+        self._check(self.lib.ebr_set_block_size(self.ctx, kernel.encode(), int(threads)))
+
+    def block_size(self, kernel):
+        v = int(self.lib.ebr_get_block_size(self.ctx, kernel.encode()))
+        if v < 0:
+            raise ValueError("no tunable kernel named %r" % kernel)
+        return v
+
     @property
     def launches(self):
         return int(self.lib.ebr_launch_count(self.ctx))

@@ -79,16 +79,16 @@ __global__ void k_adj_seed(int F, int4 role, double mu, double dd0, double dd1, 
 
 void launch_adj_seed(int dim, int F, const int* role, double mu, const double* dirs,
                      const double* seed, int ng, const int* g_geo, const double* g_n,
-                     const double* ftab, double* sv, cudaStream_t s) {
+                     const double* ftab, double* sv, cudaStream_t s, int T) {
   if (ng <= 0) return;
   int4 r = make_int4(role[0], role[1], role[2], role[3]);
   double dd[3] = {0, 0, 0}, dl[3] = {0, 0, 0};
   for (int a = 0; a < dim; ++a) { dd[a] = dirs[a]; dl[a] = dirs[dim + a]; }
   if (dim == 2)
-    k_adj_seed<2><<<(ng + 127) / 128, 128, 0, s>>>(F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
+    k_adj_seed<2><<<(ng + T - 1) / T, T, 0, s>>>(F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
                                                    seed, ng, g_geo, g_n, ftab, sv);
   else
-    k_adj_seed<3><<<(ng + 127) / 128, 128, 0, s>>>(F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
+    k_adj_seed<3><<<(ng + T - 1) / T, T, 0, s>>>(F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
                                                    seed, ng, g_geo, g_n, ftab, sv);
 }
 
@@ -328,16 +328,16 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
 void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                       const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
                       const int* pos_of_cell, int rmax, const double* wtab, const double* sv,
-                      const void* lam, void* const* grad, int accumulate, int kmax, cudaStream_t s) {
+                      const void* lam, void* const* grad, int accumulate, int kmax, cudaStream_t s, int T) {
   if (ng <= 0) return;
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.grad[f] = grad[f]; }
   // one thread per (ghost, member): K = 3 in 2D, 7 in 3D (kmax covers both)
   int n = ng * kmax;
   if (dtype == 0)
-    k_adj_fluid<float><<<(n + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const float*)lam, accumulate, kmax);
+    k_adj_fluid<float><<<(n + T - 1) / T, T, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const float*)lam, accumulate, kmax);
   else
-    k_adj_fluid<double><<<(n + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const double*)lam, accumulate, kmax);
+    k_adj_fluid<double><<<(n + T - 1) / T, T, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const double*)lam, accumulate, kmax);
 }
 
 template <typename T>
@@ -357,14 +357,14 @@ __global__ void k_adj_bc(AdjSet A, int F, int ng, const Geom* __restrict__ G,
 
 void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                    const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,
-                   void* const* grad, int accumulate, cudaStream_t s) {
+                   void* const* grad, int accumulate, cudaStream_t s, int T) {
   if (ng <= 0) return;
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.gbc[f] = grad_bc[f]; A.grad[f] = grad[f]; }
   if (dtype == 0)
-    k_adj_bc<float><<<(ng + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, wtab, (const float*)lam, accumulate);
+    k_adj_bc<float><<<(ng + T - 1) / T, T, 0, s>>>(A, F, ng, G, g_geo, g_cell, wtab, (const float*)lam, accumulate);
   else
-    k_adj_bc<double><<<(ng + 127) / 128, 128, 0, s>>>(A, F, ng, G, g_geo, g_cell, wtab, (const double*)lam, accumulate);
+    k_adj_bc<double><<<(ng + T - 1) / T, T, 0, s>>>(A, F, ng, G, g_geo, g_cell, wtab, (const double*)lam, accumulate);
 }
 
 }  // namespace ebr

@@ -28,6 +28,23 @@ struct ChainPlan {
   std::vector<int> fallback;   // geometries served by level launches
 };
 
+// Launch shapes a caller may tune: threads per block of the kernels that run
+// one thread per item (interface cell, ghost or fluid target), where the
+// block size changes scheduling only, never a result.  Names are those of
+// the kernels' profiling records (ebr_profile_read).
+enum TuneId { TU_IFACE, TU_PLACE, TU_GHOST, TU_DEPS, TU_TABLES, TU_GSRC, TU_ADJ_SEED, TU_ADJ_FLUID, TU_ADJ_BC, TU_N };
+static const char* const kTuneNames[TU_N] = {"iface", "place", "ghost_write", "deps", "tables",
+                                             "gsrc", "adj_seed", "adj_fluid", "adj_bc"};
+constexpr int TUNE_DEFAULT = 128;
+constexpr int TUNE_MAX = 256;     // every kernel fits at 256 threads (<= 255 registers each)
+
+static int tune_id(const char* name) {
+  if (!name) return -1;
+  for (int i = 0; i < TU_N; ++i)
+    if (std::strcmp(name, kTuneNames[i]) == 0) return i;
+  return -1;
+}
+
 struct Ctx {
   int device = 0;
   std::string err;
@@ -98,6 +115,8 @@ struct Ctx {
   void* lam = nullptr;
 
   std::vector<int> order_by_size;            // geometries, largest ghost count first
+  int tb[TU_N] = {TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT,
+                  TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT};   // threads per block
   PackedPlan pplan;                          // schedule of the packed kernels
   void* lamP = nullptr;                      // packed adjoint scratch [ng][F]
   size_t lamP_bytes = 0;
@@ -283,7 +302,7 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   CKL();
   prof_begin(c, s, "iface");
   launch_iface(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, c->row_cnt, nullptr, nullptr,
-               nullptr, nullptr, 0, 0, c->d_status, s);
+               nullptr, nullptr, 0, 0, c->d_status, s, c->tb[TU_IFACE]);
   prof_end(c, s);
   prof_begin(c, s, "scan");
   launch_scan(c->row_cnt, c->row_ptr, c->total_rows, c->scan_tmp, s);
@@ -310,11 +329,11 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   }
   prof_begin(c, s, "iface");
   launch_iface(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, nullptr, c->row_ptr,
-               c->iface_cell, c->iface_geo, c->iface_solid, 1, c->n_iface, c->d_status, s);
+               c->iface_cell, c->iface_geo, c->iface_solid, 1, c->n_iface, c->d_status, s, c->tb[TU_IFACE]);
   prof_end(c, s);
   prof_begin(c, s, "place");
   launch_place(c->dG, c->n_iface, c->iface_cell, c->iface_geo, c->iface_solid, c->placement,
-               d_tags, c->iface_psi, c->iface_n, c->d_status, s);
+               d_tags, c->iface_psi, c->iface_n, c->d_status, s, c->tb[TU_PLACE]);
   prof_end(c, s);
   c->launches += 2;
   if (c->placement == EBR_HGC) {
@@ -362,7 +381,7 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   prof_begin(c, s, "ghost_write");
   launch_ghost_write(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->iface_psi,
                      c->iface_n, c->gpos, c->placement, c->ng, c->gs_cell, c->gs_geo, c->gs_psi,
-                     c->gs_n, c->gs_meta, c->d_stats + 1, c->d_status, s);
+                     c->gs_n, c->gs_meta, c->d_stats + 1, c->d_status, s, c->tb[TU_GHOST]);
   prof_end(c, s);
   c->launches += 2;
   CKL();
@@ -417,7 +436,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   prof_end(c, s);
   prof_begin(c, s, "deps");
   launch_deps(c->dG, ng, c->gs_cell, c->gs_geo, c->gs_meta, c->gs_n, c->tags, c->pos_of_cell,
-              c->dep, c->d_status, s);
+              c->dep, c->d_status, s, c->tb[TU_DEPS]);
   prof_end(c, s);
   prof_begin(c, s, "levels");
   launch_levels(c->dG, c->B, c->dep, ng, c->level, c->order_pos, c->lev_ptr, c->d_nlev,
@@ -462,12 +481,12 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   }
   prof_begin(c, s, "tables");
   launch_tables(c->dG, ng, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->tags, c->wtab,
-                c->ftab, s);
+                c->ftab, s, c->tb[TU_TABLES]);
   prof_end(c, s);
   // ghost-target sources
   prof_begin(c, sg, "gsrc");
   launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax, nullptr,
-              c->gsrc_cnt, 0, sg);
+              c->gsrc_cnt, 0, sg, c->tb[TU_GSRC]);
   prof_end(c, sg);
   prof_begin(c, sg, "scan");
   launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, sg);
@@ -488,7 +507,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   }
   prof_begin(c, sg, "gsrc");
   launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
-              c->gsrc_ptr, c->gsrc, 1, sg);
+              c->gsrc_ptr, c->gsrc, 1, sg, c->tb[TU_GSRC]);
   prof_end(c, sg);
   c->launches += 1;
   CKL();
@@ -886,7 +905,7 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
   int kinds[8];
   for (int f = 0; f < n_fields; ++f) kinds[f] = h_bc_kind[f];
   prof_begin(c, s, "adj_seed");
-  launch_adj_seed(dim, n_fields, role, mu, h_dirs, d_seed, c->ng, c->g_geo, c->g_n, c->ftab, c->sv, s);
+  launch_adj_seed(dim, n_fields, role, mu, h_dirs, d_seed, c->ng, c->g_geo, c->g_n, c->ftab, c->sv, s, c->tb[TU_ADJ_SEED]);
   prof_end(c, s);
   c->launches += 1;
   std::vector<int> level_geoms;
@@ -921,12 +940,12 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
   prof_begin(c, s, "adj_fluid");
   launch_adj_fluid(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->g_meta, c->tags,
                    c->pos_of_cell, c->rmax, c->wtab, c->sv, c->lam, d_grad_fields, accumulate,
-                   stencil_k(dim), s);
+                   stencil_k(dim), s, c->tb[TU_ADJ_FLUID]);
   prof_end(c, s);
   c->launches += 1;
   prof_begin(c, s, "adj_bc");
   launch_adj_bc(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->wtab, c->lam, d_grad_bc,
-                d_grad_fields, accumulate, s);
+                d_grad_fields, accumulate, s, c->tb[TU_ADJ_BC]);
   prof_end(c, s);
   c->launches += 1;
   CKL();
@@ -1147,6 +1166,34 @@ ebr_status ebr_reconstruct_packed_adjoint(void* ctx, int32_t n_fields, const int
   c->launches += padj_launches(c->pplan, c->ng);
   CKL();
   return EBR_OK;
+}
+
+int32_t ebr_tunable_kernels(char* h_names, int32_t max_entries) {
+  for (int i = 0; i < TU_N && i < max_entries; ++i) {
+    if (!h_names) break;
+    std::strncpy(h_names + 32 * i, kTuneNames[i], 31);
+    h_names[32 * i + 31] = 0;
+  }
+  return TU_N;
+}
+
+ebr_status ebr_set_block_size(void* ctx, const char* kernel, int32_t threads) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  const int id = tune_id(kernel);
+  if (id < 0) return fail(c, EBR_EINVAL, "ebr_set_block_size: no tunable kernel named '%s'", kernel ? kernel : "(null)");
+  if (threads < 32 || threads > TUNE_MAX || threads % 32 != 0)
+    return fail(c, EBR_EINVAL, "ebr_set_block_size: %d threads (a multiple of 32 in 32..%d)", threads, TUNE_MAX);
+  c->tb[id] = threads;
+  return EBR_OK;
+}
+
+int32_t ebr_get_block_size(const void* ctx, const char* kernel) {
+  const Ctx* c = static_cast<const Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  const int id = tune_id(kernel);
+  return id < 0 ? EBR_EINVAL : c->tb[id];
 }
 
 ebr_status ebr_profile(void* ctx, int32_t enable) {

@@ -657,9 +657,9 @@ __global__ void k_iface(const Geom* __restrict__ G, const int* __restrict__ row_
 
 void launch_iface(const Geom* G, const int* row_off, int B, int total_rows, const int2* runs,
                   int* row_cnt, const int* row_ptr, int* iface_cell, int* iface_geo,
-                  int8_t* iface_solid, int write, int iface_cap, int* status, cudaStream_t s) {
+                  int8_t* iface_solid, int write, int iface_cap, int* status, cudaStream_t s, int T) {
   if (total_rows <= 0) return;
-  k_iface<<<(total_rows + 127) / 128, 128, 0, s>>>(G, row_off, B, total_rows, runs, row_cnt,
+  k_iface<<<(total_rows + T - 1) / T, T, 0, s>>>(G, row_off, B, total_rows, runs, row_cnt,
                                                    row_ptr, iface_cell, iface_geo, iface_solid,
                                                    write, iface_cap, status);
 }
@@ -725,9 +725,9 @@ __global__ void k_place(const Geom* __restrict__ G, int n_iface, const int* __re
 
 void launch_place(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                   const int8_t* iface_solid, int placement, int8_t* tags, double* iface_psi,
-                  double* iface_n, int* status, cudaStream_t s) {
+                  double* iface_n, int* status, cudaStream_t s, int T) {
   if (n_iface <= 0) return;
-  k_place<<<(n_iface + 127) / 128, 128, 0, s>>>(G, n_iface, iface_cell, iface_geo, iface_solid,
+  k_place<<<(n_iface + T - 1) / T, T, 0, s>>>(G, n_iface, iface_cell, iface_geo, iface_solid,
                                                 placement, tags, iface_psi, iface_n, status);
 }
 
@@ -843,14 +843,14 @@ void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const
                         const int8_t* tags, const double* iface_psi, const double* iface_n,
                         const int* gpos, int placement, int ng_cap, int* gs_cell, int* gs_geo,
                         double* gs_psi, double* gs_n, uint32_t* gs_meta, int* rmax,
-                        int* status, cudaStream_t s) {
+                        int* status, cudaStream_t s, int T) {
   (void)iface_psi;
   (void)iface_n;
   if (n_iface <= 0) return;
   k_ghost_write<<<(n_iface + 255) / 256, 256, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, gpos,
                                                       ng_cap, gs_cell, gs_geo, gs_meta, status);
   if (ng_cap <= 0) return;
-  k_ghost_geom<<<(ng_cap + 127) / 128, 128, 0, s>>>(G, ng_cap, placement, gs_cell, gs_geo, gs_psi,
+  k_ghost_geom<<<(ng_cap + T - 1) / T, T, 0, s>>>(G, ng_cap, placement, gs_cell, gs_geo, gs_psi,
                                                     gs_n, gs_meta, rmax, status);
 }
 

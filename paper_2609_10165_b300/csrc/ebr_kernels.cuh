@@ -31,10 +31,10 @@ void launch_rows(const Geom* G, const int* row_off, int B, int total_rows, int2*
                  int8_t* tags, int* status, int* stats, cudaStream_t s);
 void launch_iface(const Geom* G, const int* row_off, int B, int total_rows, const int2* runs,
                   int* row_cnt, const int* row_ptr, int* iface_cell, int* iface_geo,
-                  int8_t* iface_solid, int write, int iface_cap, int* status, cudaStream_t s);
+                  int8_t* iface_solid, int write, int iface_cap, int* status, cudaStream_t s, int T = 128);
 void launch_place(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                   const int8_t* iface_solid, int placement, int8_t* tags, double* iface_psi,
-                  double* iface_n, int* status, cudaStream_t s);
+                  double* iface_n, int* status, cudaStream_t s, int T = 128);
 void launch_reclassify(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                        int8_t* tags, int pass, cudaStream_t s);
 void launch_ghost_flags(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
@@ -43,7 +43,7 @@ void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const
                         const int8_t* tags, const double* iface_psi, const double* iface_n,
                         const int* gpos, int placement, int ng_cap, int* gs_cell, int* gs_geo,
                         double* gs_psi, double* gs_n, uint32_t* gs_meta, int* rmax,
-                        int* status, cudaStream_t s);
+                        int* status, cudaStream_t s, int T = 128);
 
 // ---- scan.cu : exclusive scan of n int32 values into out[0..n]; out[n] = total
 size_t scan_temp_bytes(int n);
@@ -54,7 +54,7 @@ void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, cons
                     int* pos_of_cell, cudaStream_t s);
 void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, uint32_t* gs_meta,
                  const double* gs_n, const int8_t* tags, const int* pos_of_cell, int* dep,
-                 int* status, cudaStream_t s);
+                 int* status, cudaStream_t s, int T = 128);
 size_t levels_smem(int dim, int n_ghost);
 void launch_levels(const Geom* G, int B, const int* dep, int ng_total, int* level, int* order_pos,
                    int* lev_ptr, int* n_levels, size_t smem, int* status, cudaStream_t s);
@@ -64,10 +64,10 @@ void launch_reorder(int ng, const int* order_pos, const int* gs_cell, const int*
                     double* g_n, uint32_t* g_meta, int* g_dep, int* g_level, cudaStream_t s);
 void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, const double* g_psi,
                    const double* g_n, const uint32_t* g_meta, const int8_t* tags, double* wtab,
-                   double* ftab, cudaStream_t s);
+                   double* ftab, cudaStream_t s, int T = 128);
 void launch_gsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
                  const int8_t* tags, const int* pos_of_cell, int rmax, const int* ptr,
-                 int* cnt_or_src, int write, cudaStream_t s);
+                 int* cnt_or_src, int write, cudaStream_t s, int T = 128);
 
 
 // ---- fill.cu
@@ -92,7 +92,7 @@ void launch_forces(int dtype, int dim, const void* const* vel, const void* p, do
 // ---- adjoint.cu
 void launch_adj_seed(int dim, int F, const int* role, double mu, const double* dirs,
                      const double* seed, int ng, const int* g_geo, const double* g_n,
-                     const double* ftab, double* sv, cudaStream_t s);
+                     const double* ftab, double* sv, cudaStream_t s, int T = 128);
 void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int p1,
                       const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
                       const double* wtab, const double* sv, int ng_total, void* lam, cudaStream_t s);
@@ -104,10 +104,10 @@ void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom*
 void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                       const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
                       const int* pos_of_cell, int rmax, const double* wtab, const double* sv,
-                      const void* lam, void* const* grad, int accumulate, int kmax, cudaStream_t s);
+                      const void* lam, void* const* grad, int accumulate, int kmax, cudaStream_t s, int T = 128);
 void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                    const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,
-                   void* const* grad, int accumulate, cudaStream_t s);
+                   void* const* grad, int accumulate, cudaStream_t s, int T = 128);
 
 // ---- packed.cu (field-minor layout [cells][F])
 // Schedule of the packed kernels, planned once per levelled geometry set:

@@ -63,9 +63,9 @@ __global__ void k_deps(const Geom* __restrict__ G, int ng, const int* __restrict
 
 void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, uint32_t* gs_meta,
                  const double* gs_n, const int8_t* tags, const int* pos_of_cell, int* dep,
-                 int* status, cudaStream_t s) {
+                 int* status, cudaStream_t s, int T) {
   if (ng <= 0) return;
-  k_deps<<<(ng + 127) / 128, 128, 0, s>>>(G, ng, gs_cell, gs_geo, gs_meta, gs_n, tags,
+  k_deps<<<(ng + T - 1) / T, T, 0, s>>>(G, ng, gs_cell, gs_geo, gs_meta, gs_n, tags,
                                           pos_of_cell, dep, status);
 }
 
@@ -417,9 +417,9 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
 
 void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, const double* g_psi,
                    const double* g_n, const uint32_t* g_meta, const int8_t* tags, double* wtab,
-                   double* ftab, cudaStream_t s) {
+                   double* ftab, cudaStream_t s, int T) {
   if (ng <= 0) return;
-  k_tables<<<(ng + 127) / 128, 128, 0, s>>>(G, ng, g_cell, g_geo, g_psi, g_n, g_meta, tags, wtab, ftab);
+  k_tables<<<(ng + T - 1) / T, T, 0, s>>>(G, ng, g_cell, g_geo, g_psi, g_n, g_meta, tags, wtab, ftab);
 }
 
 // ghost targets: write = 0 counts, write = 1 writes sources (self first)
@@ -447,9 +447,9 @@ __global__ void k_gsrc(const Geom* __restrict__ G, int ng, const int* __restrict
 
 void launch_gsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
                  const int8_t* tags, const int* pos_of_cell, int rmax, const int* ptr,
-                 int* cnt_or_src, int write, cudaStream_t s) {
+                 int* cnt_or_src, int write, cudaStream_t s, int T) {
   if (ng <= 0) return;
-  k_gsrc<<<(ng + 127) / 128, 128, 0, s>>>(G, ng, g_cell, g_geo, g_meta, tags, pos_of_cell, rmax,
+  k_gsrc<<<(ng + T - 1) / T, T, 0, s>>>(G, ng, g_cell, g_geo, g_meta, tags, pos_of_cell, rmax,
                                           ptr, cnt_or_src, write);
 }
 
