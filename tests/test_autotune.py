@@ -63,6 +63,10 @@ COST = {
 }
 
 
+def test_default_candidates_are_allowed_block_sizes():
+    assert all(t % 32 == 0 and 32 <= t <= 256 for t in A.DEFAULT_CANDIDATES)
+
+
 def test_choose_takes_the_minimum_and_breaks_ties_small():
     assert A.choose({64: 2.0, 128: 1.0, 256: 3.0}) == 128
     assert A.choose({256: 1.0, 64: 1.0, 128: 1.0}) == 64
@@ -73,7 +77,7 @@ def test_choose_takes_the_minimum_and_breaks_ties_small():
 def test_search_finds_each_minimum_and_skips_unlaunched_kernels():
     R = FakeCtx(COST, launched=["place", "tables", "adj_fluid"])
     R.set_block_size("gsrc", 96)
-    shapes, rep = A.autotune(R, R.step, reps=5)
+    shapes, rep = A.autotune(R, R.step, candidates=(64, 128, 256), reps=5)
     assert shapes == {"place": 64, "tables": 128, "adj_fluid": 256, "gsrc": 96}
     assert R.shape == shapes
     assert rep["source"] == "search"
@@ -85,10 +89,10 @@ def test_cache_round_trip(tmp_path):
     path = str(tmp_path / "shapes.json")
     R = FakeCtx(COST, launched=list(COST))
     key = A.workload_key(R, "f32", 3, "fake-gpu")
-    shapes, rep = A.autotune(R, R.step, reps=3, cache_path=path, key=key)
+    shapes, rep = A.autotune(R, R.step, candidates=(64, 128, 256), reps=3, cache_path=path, key=key)
     assert rep["source"] == "search"
     R2 = FakeCtx(COST, launched=list(COST))
-    shapes2, rep2 = A.autotune(R2, R2.step, reps=3, cache_path=path, key=key)
+    shapes2, rep2 = A.autotune(R2, R2.step, candidates=(64, 128, 256), reps=3, cache_path=path, key=key)
     assert rep2["source"] == "cache" and shapes2 == shapes and R2.shape == shapes
     # another workload misses the cache
     R3 = FakeCtx(COST, launched=list(COST))
