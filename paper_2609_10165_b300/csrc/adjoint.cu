@@ -301,8 +301,10 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
   const int* pc = pos_of_cell + g.cell_off;
   if (!in_grid(g, tijk) || tg[cell_lin(g, tijk)] != 0) return;
   // one pass: the first source met decides ownership; a non-owner stops there
+  // fields up to 8: fixed-trip loops keep acc[] in registers
   T acc[8];
-  for (int f = 0; f < F; ++f) acc[f] = T(0);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) acc[f] = T(0);
   bool first = true, owner = false;
   probe_sources(g, tijk, tg, pc, g_meta, rmax, [&](int q, int slot) {
     if (first) {
@@ -311,17 +313,23 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
       if (!owner) return false;
     }
     bool act = meta_active(g_meta[q]) >> (slot - 1) & 1u;
-    for (int f = 0; f < F; ++f) {
-      acc[f] += (T)sv[(size_t)(f * 8 + slot) * ng + q];
-      if (act) acc[f] += (T)wtab[(size_t)(A.kind[f] * 8 + slot - 1) * ng + q] * lam[(size_t)f * ng + q];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      if (f < F) {
+        acc[f] += (T)sv[(size_t)(f * 8 + slot) * ng + q];
+        if (act) acc[f] += (T)wtab[(size_t)(A.kind[f] * 8 + slot - 1) * ng + q] * lam[(size_t)f * ng + q];
+      }
     }
     return true;
   });
   if (!owner) return;
   long long c = g.cell_off + cell_lin(g, tijk);
-  for (int f = 0; f < F; ++f) {
-    T* gr = static_cast<T*>(A.grad[f]);
-    if (accumulate) gr[c] += acc[f]; else gr[c] = acc[f];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    if (f < F) {
+      T* gr = static_cast<T*>(A.grad[f]);
+      if (accumulate) gr[c] += acc[f]; else gr[c] = acc[f];
+    }
   }
 }
 

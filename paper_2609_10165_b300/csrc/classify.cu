@@ -701,7 +701,9 @@ __global__ void k_place(const Geom* __restrict__ G, int n_iface, const int* __re
     float n32[3];
     float psi32 = closest_point_f32(g, xf, yf, zf, solid, n32);
     float s32 = 0.0f;
-    for (int a = 0; a < g.dim; ++a) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= g.dim) continue;
       float q = n32[a] / g.fh[a];
       s32 += q * q;
     }
@@ -751,7 +753,9 @@ __global__ void k_reclassify(const Geom* __restrict__ G, int n_iface, const int*
   int ijk[3] = {i, j, k};
   int stride[3] = {1, g.n[0], g.n[0] * g.n[1]};
   bool found = false;
-  for (int a = 0; a < g.dim && !found; ++a) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.dim || found) continue;
     if (ijk[a] > 0 && tg[cell - stride[a]] == look) found = true;
     if (ijk[a] < g.n[a] - 1 && tg[cell + stride[a]] == look) found = true;
   }
@@ -819,7 +823,9 @@ __global__ void k_ghost_geom(const Geom* __restrict__ G, int ng, int placement,
   double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
   if (!closest_point(g, x, y, z, solid, psi, nv)) { set_status(status, S_EINVAL); return; }
   int rloc = 1;
-  for (int a = 0; a < g.dim; ++a) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.dim) continue;
     if (nv[a] < 0.0) meta |= 1u << a;
     int r = 1;
     if (placement == CGC_ES) {

@@ -500,7 +500,9 @@ __device__ inline bool closest_point(const Geom& g, double x, double y, double z
 // Eq. delta_n with the ghost's own widths.
 __device__ inline double delta_n(const Geom& g, const double n[3]) {
   double s = 0.0;
-  for (int a = 0; a < g.dim; ++a) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.dim) continue;
     double q = n[a] / g.h[a];
     s += q * q;
   }

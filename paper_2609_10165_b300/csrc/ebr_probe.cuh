@@ -18,16 +18,21 @@ __device__ inline int cell_lin(const Geom& g, const int ijk[3]) {
   return ijk[0] + g.n[0] * (ijk[1] + g.n[1] * ijk[2]);
 }
 
+// fixed-trip loops over the three axes (predicated on the dimension) keep
+// every index static, so the small arrays stay in registers
 __device__ inline bool in_grid(const Geom& g, const int ijk[3]) {
-  for (int a = 0; a < g.dim; ++a)
-    if (ijk[a] < 0 || ijk[a] >= g.n[a]) return false;
-  return true;
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < g.dim && (ijk[a] < 0 || ijk[a] >= g.n[a])) ok = false;
+  return ok;
 }
 
 // member k of a ghost at ijk with meta m
 __device__ inline void member_ijk(const Geom& g, const int ijk[3], uint32_t m, int k, int out[3]) {
   int o[3];
   stencil_off(g.dim, k, o);
+#pragma unroll
   for (int a = 0; a < 3; ++a) out[a] = ijk[a] + (a < g.dim ? o[a] * meta_r(m, a) * meta_e(m, a) : 0);
 }
 
@@ -67,8 +72,9 @@ __device__ __forceinline__ bool probe_slab_r1(const Geom& g, const int tijk[3], 
       int o[3];
       stencil_off(g.dim, k, o);
       bool hit = true;
-      for (int a = 0; a < g.dim; ++a)
-        if (o[a] * meta_r(m[b], a) * meta_e(m[b], a) != dd[a]) hit = false;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a < g.dim && o[a] * meta_r(m[b], a) * meta_e(m[b], a) != dd[a]) hit = false;
       if (hit) { if (!visit(q[b], k + 1)) return false; }
     }
   }
@@ -103,8 +109,9 @@ __device__ inline void probe_sources(const Geom& g, const int tijk[3], const int
           int o[3];
           stencil_off(g.dim, k, o);
           bool hit = true;
-          for (int a = 0; a < g.dim; ++a)
-            if (o[a] * meta_r(m, a) * meta_e(m, a) != dd[a]) hit = false;
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            if (a < g.dim && o[a] * meta_r(m, a) * meta_e(m, a) != dd[a]) hit = false;
           if (hit) { if (!visit(q, k + 1)) return; }
         }
       }

@@ -44,8 +44,9 @@ __global__ void k_deps(const Geom* __restrict__ G, int ng, const int* __restrict
         set_status(status, S_ESTENCIL_OOB);
       } else {
         bool act = true;
-        for (int a = 0; a < g.dim; ++a)
-          if (o[a] && nv[a] == 0.0) act = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (a < g.dim && o[a] && nv[a] == 0.0) act = false;
         long long mc = g.cell_off + cell_lin(g, mijk);
         int8_t t = tags[mc];
         if (t == 1) set_status(status, S_ESTENCIL_SOLID);
@@ -296,8 +297,10 @@ void launch_reorder(int ng, const int* order_pos, const int* gs_cell, const int*
 // ---------------------------------------------------------------------------
 __device__ void dirichlet_w(int dim, const double X2[3], const double Xs[3], double w[8]) {
   // w_a = (x_1 - x_s) / (x_2 - x_s) with x_1 = 0 (Eqs. phi_G_Dir_2d / _3d)
-  double om[3];
-  for (int a = 0; a < dim; ++a) om[a] = -Xs[a] / (X2[a] - Xs[a]);
+  double om[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < dim) om[a] = -Xs[a] / (X2[a] - Xs[a]);
   for (int q = 0; q < 8; ++q) w[q] = 0.0;
   if (dim == 2) {
     w[0] = om[0]; w[1] = om[1]; w[2] = -om[0] * om[1];
@@ -354,10 +357,15 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
   double psi = g_psi[p];
   double n[3] = {g_n[p], g_n[ng + p], g_n[2 * (size_t)ng + p]};
   double X2[3] = {1, 1, 1}, Xs[3] = {0, 0, 0}, r2[3] = {1, 1, 1};
-  for (int a = 0; a < d; ++a) {
-    X2[a] = meta_r(m, a) * meta_e(m, a) * g.h[a];
-    Xs[a] = psi * n[a];
-    r2[a] = 1.0 / X2[a];
+  // fixed-trip axis loops predicated on the dimension: static indices keep
+  // the small arrays in registers
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < d) {
+      X2[a] = meta_r(m, a) * meta_e(m, a) * g.h[a];
+      Xs[a] = psi * n[a];
+      r2[a] = 1.0 / X2[a];
+    }
   }
   double wd[8], wn[8];
   dirichlet_w(d, X2, Xs, wd);
@@ -371,10 +379,14 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
   cell_ijk3(g, g_cell[p], ijk);
   const int8_t* tg = tags + g.cell_off;
   double wG = 0.0;
-  for (int a = 0; a < d; ++a) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= d) continue;
     double area = 1.0;
-    for (int b = 0; b < d; ++b)
-      if (b != a) area *= g.h[b];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      if (b < d && b != a) area *= g.h[b];
+#pragma unroll
     for (int sgn = -1; sgn <= 1; sgn += 2) {
       int nb[3] = {ijk[0], ijk[1], ijk[2]};
       nb[a] += sgn;
@@ -389,7 +401,9 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
   double rws = 1.0 / wd[7];
   f[1] = rws;
   const int K = stencil_k(d);
-  for (int k = 0; k < K; ++k) f[2 + k] = -wd[k] * rws;
+#pragma unroll
+  for (int k = 0; k < 7; ++k)
+    if (k < K) f[2 + k] = -wd[k] * rws;
   // gradient at S, local coordinates (x_1 = 0): fx0 = (x_2 - x_s)/(x_2 - x_1),
   // fx1 = (x_s - x_1)/(x_2 - x_1), divided differences over h = x_2 - x_1
   double fx0 = (X2[0] - Xs[0]) * r2[0], fx1 = Xs[0] * r2[0];
