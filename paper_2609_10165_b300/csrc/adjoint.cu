@@ -236,16 +236,29 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
   }
   __syncthreads();
   // phase 2: reverse levels
-  for (int lv = g.n_levels; lv >= 1; --lv) {
-    int a = lps[lv - 1], b = lps[lv];
-    for (int s = a + threadIdx.x; s < b; s += AC_T) {
-      for (int f = 0; f < F; ++f) {
-        int kind = A.kind[f];
-        T v = L[(size_t)f * n + s];
-        for (int o = cptr[s]; o < cptr[s + 1]; ++o) v += cw[(size_t)kind * nsrc + o] * L[(size_t)f * n + cq[o]];
-        L[(size_t)f * n + s] = v;
-      }
+  auto relax = [&](int s) {
+    for (int f = 0; f < F; ++f) {
+      int kind = A.kind[f];
+      T v = L[(size_t)f * n + s];
+      for (int o = cptr[s]; o < cptr[s + 1]; ++o) v += cw[(size_t)kind * nsrc + o] * L[(size_t)f * n + cq[o]];
+      L[(size_t)f * n + s] = v;
     }
+  };
+  // the deepest levels (lw.., at most 32 ghosts each) come first: one warp
+  // walks them with warp barriers, then the block takes the wide levels
+  int lw = g.n_levels + 1;
+  while (lw > 1 && lps[lw - 1] - lps[lw - 2] <= 32) --lw;
+  if (threadIdx.x < 32) {
+    for (int lv = g.n_levels; lv >= lw; --lv) {
+      const int s = lps[lv - 1] + threadIdx.x;
+      if (s < lps[lv]) relax(s);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int lv = lw - 1; lv >= 1; --lv) {
+    int a = lps[lv - 1], b = lps[lv];
+    for (int s = a + threadIdx.x; s < b; s += AC_T) relax(s);
     __syncthreads();
   }
   for (int s = threadIdx.x; s < n; s += AC_T)

@@ -134,23 +134,35 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
   }
   __syncthreads();
   // phase 2: the dependency chain, level by level, on shared memory only
-  for (int lv = 1; lv <= g.n_levels; ++lv) {
-    int a = lps[lv - 1], b = lps[lv];
-    for (int s = a + threadIdx.x; s < b; s += CH_T) {
-      int cell = cellv[s];
-      for (int f = 0; f < F; ++f) {
-        int kind = P.kind[f];
-        T v = vals[(size_t)f * n + s];
-        for (int k = 0; k < K; ++k) {
-          int d = dpos[(size_t)k * n + s];
-          if (d >= 0) v += wdep[(size_t)(kind * K + k) * n + s] * vals[(size_t)f * n + d];
-        }
-        vals[(size_t)f * n + s] = v;
-        static_cast<T*>(P.f[f])[g.cell_off + cell] = v;
-        if (!isfinite((double)v)) set_status(status, S_ENONFINITE);
+  auto relax = [&](int s) {
+    int cell = cellv[s];
+    for (int f = 0; f < F; ++f) {
+      int kind = P.kind[f];
+      T v = vals[(size_t)f * n + s];
+      for (int k = 0; k < K; ++k) {
+        int d = dpos[(size_t)k * n + s];
+        if (d >= 0) v += wdep[(size_t)(kind * K + k) * n + s] * vals[(size_t)f * n + d];
       }
+      vals[(size_t)f * n + s] = v;
+      static_cast<T*>(P.f[f])[g.cell_off + cell] = v;
+      if (!isfinite(v)) set_status(status, S_ENONFINITE);
     }
+  };
+  // levels lw.. hold at most 32 ghosts each (the thin end of the chains):
+  // one warp walks them with warp barriers instead of block barriers
+  int lw = g.n_levels + 1;
+  while (lw > 1 && lps[lw - 1] - lps[lw - 2] <= 32) --lw;
+  for (int lv = 1; lv < lw; ++lv) {
+    int a = lps[lv - 1], b = lps[lv];
+    for (int s = a + threadIdx.x; s < b; s += CH_T) relax(s);
     __syncthreads();
+  }
+  if (threadIdx.x < 32) {
+    for (int lv = lw; lv <= g.n_levels; ++lv) {
+      const int s = lps[lv - 1] + threadIdx.x;
+      if (s < lps[lv]) relax(s);
+      __syncwarp();
+    }
   }
 }
 
