@@ -70,22 +70,30 @@ void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, u
                                           pos_of_cell, dep, status);
 }
 
-// One CTA per geometry: integer frontier sweep.  In sweep L a ghost whose
-// dependencies all carry levels in [1, L-1] receives level L; a level written in
-// the same sweep reads as "not ready", so the result does not depend on the
-// thread schedule.  Then a stable counting sort by level gives the canonical
-// position (level, index) of every ghost.  Geometries whose levels and
-// dependencies fit in shared memory run the sweep there and rank each level
-// in one pass (warps in order, __match_any_sync within a warp); larger ones
-// work on global memory with one block scan per level.
+// One CTA per geometry, integer arithmetic only.  Geometries whose arrays fit
+// in shared memory run a layered topological sort there: consumer lists from
+// the dependencies, in-degree counters, and one frontier per level (a ghost
+// enters level L + 1 when the last of its dependencies is placed in level L,
+// so its level is 1 + the largest level among its dependencies, whatever the
+// thread schedule); each level touches only its frontier.  Larger geometries
+// sweep on global memory: in sweep L a ghost whose dependencies all carry
+// levels in [1, L-1] receives level L (a level written in the same sweep
+// reads as "not ready").  Then a stable counting sort by level gives the
+// canonical position (level, index) of every ghost: in shared memory one
+// pass per chunk (warps in order, __match_any_sync within a warp), else one
+// block scan per level.
 constexpr int LV_T = 1024;
 constexpr int LV_NL = 64;        // levels ranked with per-warp counts (more: warp by warp)
 
+// shared-memory ints of the fast path: levels, local dependencies [K][n],
+// in-degrees, consumer offsets [n + 1], consumers [K][n], two frontiers
+__host__ __device__ inline long long levels_smem_ints(int K, int n) { return (long long)(2 * K + 5) * n + 1; }
+
 size_t levels_smem(int dim, int n) {
-  return ((size_t)(stencil_k(dim) + 2) * n + 1) * sizeof(int) + 64;
+  return (size_t)levels_smem_ints(stencil_k(dim), n) * sizeof(int) + 64;
 }
 
-__global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int B,
+__global__ void __launch_bounds__(LV_T, 2) k_levels(const Geom* __restrict__ G, int B,
                                                  const int* __restrict__ dep, int ng_total,
                                                  int* __restrict__ level, int* __restrict__ order_pos,
                                                  int* __restrict__ lev_ptr, int* __restrict__ n_levels,
@@ -100,7 +108,7 @@ __global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int
     const Geom& g = G[b];
     const int g0 = g.ghost_off, n = g.n_ghost;
     const int K = stencil_k(g.dim);
-    const bool fast = (long long)(K + 2) * n + 1 <= smem_ints;
+    const bool fast = levels_smem_ints(K, n) <= smem_ints;
     int* lp = lev_ptr + g.lev_off;
     int* lvl = fast ? sm : level + g0;
     int* dl = sm + n;                          // [K][n] local dependencies (fast path)
@@ -117,34 +125,137 @@ __global__ void __launch_bounds__(LV_T) k_levels(const Geom* __restrict__ G, int
       sh_cnt3[0] = sh_cnt3[1] = sh_cnt3[2] = 0;
     }
     __syncthreads();
-    // one barrier per sweep: the count of sweep L lives in sh_cnt3[L % 3];
-    // thread 0 clears the slot of sweep L + 1, last read in sweep L - 2
-    int remaining = n, L = 0;
-    while (remaining > 0) {
-      ++L;
-      if (threadIdx.x == 0) sh_cnt3[(L + 1) % 3] = 0;
-      int mine = 0;
-      for (int s = threadIdx.x; s < n; s += LV_T) {
-        if (lvl[s] != 0) continue;
-        bool ok = true;
-        for (int k = 0; k < K && ok; ++k) {
-          int d = fast ? dl[(size_t)k * n + s] : dep[(size_t)k * ng_total + g0 + s] - g0;
-          if (d >= 0) {
-            int lv = ((volatile int*)lvl)[d];
-            if (lv == 0 || lv >= L) ok = false;
+    int remaining = n, L = 0, run = 0;     // run: ghosts levelled so far (register, not lp[])
+    if (fast) {
+      // layered topological sort: a ghost joins level L + 1 when its last
+      // dependency is placed in level L, i.e. level = 1 + max over its
+      // dependencies (Sec. 3.2); each level touches only its own frontier
+      int* indeg = dl + (size_t)K * n;         // [n]
+      int* cptr = indeg + n;                   // [n + 1] consumer offsets
+      int* cons = cptr + n + 1;                // [K][n] consumers
+      int* fr0 = cons + (size_t)K * n;         // [n] frontiers of odd levels
+      int* fr1 = fr0 + n;                      // [n] frontiers of even levels (first: cursors)
+      for (int q = threadIdx.x; q <= n; q += LV_T) cptr[q] = 0;
+      __syncthreads();
+      for (int q = threadIdx.x; q < n; q += LV_T) {
+        int c = 0;
+        for (int k = 0; k < K; ++k) {
+          const int d = dl[(size_t)k * n + q];
+          if (d >= 0) { ++c; atomicAdd(&cptr[d], 1); }
+        }
+        indeg[q] = c;
+      }
+      __syncthreads();
+      {
+        // exclusive scan of the consumer counts, a contiguous segment per thread
+        const int per = (n + LV_T - 1) / LV_T;
+        const int q0 = min(n, (int)threadIdx.x * per), q1 = min(n, q0 + per);
+        int loc = 0;
+        for (int q = q0; q < q1; ++q) loc += cptr[q];
+        int x = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (lane == 31) sh_warp[w] = x;
+        __syncthreads();
+        if (w == 0) {
+          int v = sh_warp[lane];
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+          }
+          sh_warp[lane] = v;
+        }
+        __syncthreads();
+        int ex = (w > 0 ? sh_warp[w - 1] : 0) + x - loc;
+        for (int q = q0; q < q1; ++q) {
+          const int c = cptr[q];
+          cptr[q] = ex;
+          ex += c;
+        }
+        if (threadIdx.x == LV_T - 1) cptr[n] = sh_warp[31];
+        __syncthreads();
+      }
+      for (int q = threadIdx.x; q < n; q += LV_T) fr1[q] = cptr[q];
+      __syncthreads();
+      for (int q = threadIdx.x; q < n; q += LV_T)
+        for (int k = 0; k < K; ++k) {
+          const int d = dl[(size_t)k * n + q];
+          if (d >= 0) cons[atomicAdd(&fr1[d], 1)] = q;
+        }
+      __syncthreads();
+      for (int q = threadIdx.x; q < n; q += LV_T)
+        if (indeg[q] == 0) {
+          lvl[q] = 1;
+          fr0[atomicAdd(&sh_cnt3[1], 1)] = q;
+        }
+      __syncthreads();
+      // frontier counts: level L in sh_cnt3[L % 3]; thread 0 clears the slot
+      // of level L + 2 while level L is processed (last read two levels ago)
+      int nf = sh_cnt3[1];
+      if (nf > 0) {
+        L = 1;
+        run = nf;
+        if (threadIdx.x == 0) lp[1] = g0 + run;
+      }
+      while (nf > 0) {
+        if (threadIdx.x == 0) sh_cnt3[(L + 2) % 3] = 0;
+        const int* cur = (L & 1) ? fr0 : fr1;
+        int* nxt = (L & 1) ? fr1 : fr0;
+        for (int i = threadIdx.x; i < nf; i += LV_T) {
+          const int q = cur[i];
+          for (int e = cptr[q]; e < cptr[q + 1]; ++e) {
+            const int c = cons[e];
+            if (atomicSub(&indeg[c], 1) == 1) {
+              lvl[c] = L + 1;
+              nxt[atomicAdd(&sh_cnt3[(L + 1) % 3], 1)] = c;
+            }
           }
         }
-        if (ok) { lvl[s] = L; ++mine; }
+        __syncthreads();
+        nf = sh_cnt3[(L + 1) % 3];
+        if (nf == 0) break;
+        ++L;
+        run += nf;
+        if (threadIdx.x == 0) lp[L] = g0 + run;
       }
-      if (mine) atomicAdd(&sh_cnt3[L % 3], mine);
-      __syncthreads();
-      const int cnt = sh_cnt3[L % 3];
-      if (cnt == 0) {
-        if (threadIdx.x == 0) set_status(status, S_ECYCLE);
-        break;
+      remaining = n - run;
+      if (remaining > 0 && threadIdx.x == 0) set_status(status, S_ECYCLE);
+    } else {
+      // one barrier per sweep: the count of sweep L lives in sh_cnt3[L % 3];
+      // thread 0 clears the slot of sweep L + 1, last read in sweep L - 2
+      while (remaining > 0) {
+        ++L;
+        if (threadIdx.x == 0) sh_cnt3[(L + 1) % 3] = 0;
+        int mine = 0;
+        for (int s = threadIdx.x; s < n; s += LV_T) {
+          if (lvl[s] != 0) continue;
+          bool ok = true;
+          for (int k = 0; k < K && ok; ++k) {
+            int d = fast ? dl[(size_t)k * n + s] : dep[(size_t)k * ng_total + g0 + s] - g0;
+            if (d >= 0) {
+              int lv = ((volatile int*)lvl)[d];
+              if (lv == 0 || lv >= L) ok = false;
+            }
+          }
+          if (ok) { lvl[s] = L; ++mine; }
+        }
+        // one shared-memory atomic per warp (same-address atomics serialise)
+        mine = __reduce_add_sync(0xffffffffu, mine);
+        if (lane == 0 && mine) atomicAdd(&sh_cnt3[L % 3], mine);
+        __syncthreads();
+        const int cnt = sh_cnt3[L % 3];
+        if (cnt == 0) {
+          if (threadIdx.x == 0) set_status(status, S_ECYCLE);
+          break;
+        }
+        remaining -= cnt;
+        run += cnt;
+        if (threadIdx.x == 0) lp[L] = g0 + run;
       }
-      remaining -= cnt;
-      if (threadIdx.x == 0) lp[L] = lp[L - 1] + cnt;
     }
     __syncthreads();
     int nl = remaining > 0 ? 0 : L;
