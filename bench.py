@@ -282,7 +282,7 @@ def _oracle_geometry_index(args):
 PHASES = {
     "classify": ("rows", "iface", "scan", "place", "reclassify", "ghost_flags", "ghost_write"),
     "levels": ("poscell", "deps", "levels", "reorder", "tables", "gsrc"),
-    "fill": ("fill_chain",),
+    "fill": ("fill_part", "fill_chain"),
     "forces": ("forces",),
     "adjoint": ("adj_seed", "adj_chain", "adj_fluid", "adj_bc"),
 }
@@ -396,7 +396,12 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
         "reorder": ng * 2 * (4 + 4 + 8 + 8 * dim + 4 + 4 * K + 4),
         "tables": ng * (4 + 4 + 8 + 8 * dim + 4 + 2 * dim + 16 * 8 + (1 + (1 + K) + dim * (K + 1)) * 8),
         "gsrc": ng * 32 + n_gsrc * 4,
-        "fill_chain": ng * F * (K * s + s + s) + ng * (4 + 4 + 4 * K + 2 * (K + 1) * 8),
+        # partial sums: per update the boundary datum and the fluid members
+        # read, the sum written; per ghost geometry, cell, meta and weights
+        "fill_part": ng * F * (K * s + s + s) + ng * (4 + 4 + 4 + (K + 1) * 8),
+        # chain: per update the partial read and the ghost written; per ghost
+        # cell, meta, dependency positions and weights of both kinds
+        "fill_chain": ng * F * (s + s) + ng * (4 + 4 + 4 * K + 2 * K * 8),
         "fill_level": ng * F * (K * s + s + s) + ng * (4 + 4 + 2 * (K + 1) * 8),
         "forces": ng * (4 + 4 + 8 * dim + 4 + (2 + K + dim * (K + 1)) * 8 + s * (dim + 1) * (K + 1)),
         "adj_seed": ng * (4 + 8 * dim + (2 + K + dim * (K + 1)) * 8 + F * (K + 1) * 8),

@@ -32,9 +32,10 @@ struct ChainPlan {
 // one thread per item (interface cell, ghost or fluid target), where the
 // block size changes scheduling only, never a result.  Names are those of
 // the kernels' profiling records (ebr_profile_read).
-enum TuneId { TU_IFACE, TU_PLACE, TU_GHOST, TU_DEPS, TU_TABLES, TU_GSRC, TU_ADJ_SEED, TU_ADJ_FLUID, TU_ADJ_BC, TU_N };
-static const char* const kTuneNames[TU_N] = {"iface", "place", "ghost_write", "deps", "tables",
-                                             "gsrc", "adj_seed", "adj_fluid", "adj_bc"};
+enum TuneId { TU_IFACE, TU_PLACE, TU_GHOST, TU_DEPS, TU_TABLES, TU_GSRC, TU_FILL_PART, TU_ADJ_SEED,
+              TU_ADJ_FLUID, TU_ADJ_BC, TU_N };
+static const char* const kTuneNames[TU_N] = {"iface", "place", "ghost_write", "deps", "tables", "gsrc",
+                                             "fill_part", "adj_seed", "adj_fluid", "adj_bc"};
 constexpr int TUNE_DEFAULT = 128;
 constexpr int TUNE_MAX = 256;     // every kernel fits at 256 threads (<= 255 registers each)
 
@@ -113,10 +114,11 @@ struct Ctx {
   // adjoint scratch
   double* sv = nullptr;
   void* lam = nullptr;
+  void* fpart = nullptr;       // fill partial sums [F <= 8][ng] (field type)
 
   std::vector<int> order_by_size;            // geometries, largest ghost count first
   int tb[TU_N] = {TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT,
-                  TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT};   // threads per block
+                  TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT};   // threads per block
   PackedPlan pplan;                          // schedule of the packed kernels
   void* lamP = nullptr;                      // packed adjoint scratch [ng][F]
   size_t lamP_bytes = 0;
@@ -428,6 +430,8 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     AL(c->sv, 64 * (size_t)ng);
     {
       ebr_status st = balloc(c, &c->lam, 8 * 8 * (size_t)ng);   // [F <= 8][ng] doubles
+      if (st) return st;
+      st = balloc(c, &c->fpart, 8 * 8 * (size_t)ng);
       if (st) return st;
     }
   }
@@ -828,12 +832,16 @@ ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
     ebr_status st = chain_plan(c, 0, dtype, n_fields, &cp);
     if (st) return st;
     if (cp->n_list > 0) {
+      prof_begin(c, s, "fill_part");
+      launch_fill_partial(dtype, n_fields, d_fields, kinds, d_bc, c->dG, c->g_geo, c->g_cell, c->g_meta,
+                          c->wtab, c->ng, c->fpart, s, c->tb[TU_FILL_PART]);
+      prof_end(c, s);
       prof_begin(c, s, "fill_chain");
       launch_fill_chain(dtype, 0, n_fields, d_fields, kinds, d_bc, c->dG, cp->d_list, cp->n_list,
                         c->g_cell, c->g_meta, c->g_dep, c->lev_ptr, c->wtab, c->ng, cp->smem,
-                        c->d_status, s);
+                        c->fpart, c->d_status, s);
       prof_end(c, s);
-      c->launches += 1;
+      c->launches += 2;
       CKL();
     }
     level_geoms = cp->fallback;

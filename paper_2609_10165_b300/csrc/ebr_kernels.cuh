@@ -80,7 +80,12 @@ void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int
                        const void* const* bc, const Geom* G, const int* geo_list, int n_list,
                        const int* g_cell, const uint32_t* g_meta, const int* g_dep,
                        const int* lev_ptr, const double* wtab, int ng_total, size_t smem,
-                       int* status, cudaStream_t s);
+                       const void* part, int* status, cudaStream_t s);
+// partial sums [F][ng] (boundary term + fluid members) of every ghost, read
+// by the chain kernel
+void launch_fill_partial(int dtype, int F, void* const* fields, const int* bc_kind, const void* const* bc,
+                         const Geom* G, const int* g_geo, const int* g_cell, const uint32_t* g_meta,
+                         const double* wtab, int ng, void* part, cudaStream_t s, int T = 128);
 
 // ---- forces.cu
 void launch_forces(int dtype, int dim, const void* const* vel, const void* p, double mu,

@@ -3,12 +3,14 @@
 //
 // Two schedules:
 //  * k_fill_level: one grid-wide launch per level of one geometry.
-//  * k_fill_chain: one CTA per geometry.  Everything that does not depend on
+//  * k_fill_partial + k_fill_chain: everything that does not depend on
 //    another ghost -- the boundary term and the fluid members of every ghost,
-//    for every field -- is gathered first, in parallel, into shared memory;
-//    the dependency chain then runs level by level on shared memory only,
-//    separated by block barriers.  Long chains (an airfoil has ~60 levels)
-//    cost a few hundred cycles per level instead of a kernel launch each.
+//    for every field -- is summed first by a grid-wide kernel (one thread per
+//    ghost, all SMs); then one CTA per geometry loads those partial sums into
+//    shared memory and runs the dependency chain level by level there,
+//    separated by block barriers (warp barriers for the thin end).  Long
+//    chains (an airfoil has ~60 levels) cost a few hundred cycles per level
+//    instead of a kernel launch each.
 // FP32 fields are combined in float with the weights rounded to float.
 #include "ebr_kernels.cuh"
 
@@ -76,6 +78,54 @@ void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int
     k_fill_level<double><<<(n + T - 1) / T, T, 0, s>>>(P, F, dim, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
 }
 
+// Partial sum of every ghost and field: w_s b_G plus the fluid (non-
+// dependency) members, in member order -- the first terms of the level fill,
+// in the same order, so the chain that adds the dependency terms gives the
+// same bits as summing everything in one place.
+template <typename T>
+__global__ void k_fill_partial(FieldSet P, int F, const Geom* __restrict__ G, const int* __restrict__ g_geo,
+                               const int* __restrict__ g_cell, const uint32_t* __restrict__ g_meta,
+                               const double* __restrict__ wtab, int ng, T* __restrict__ part) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ng) return;
+  const Geom& g = G[g_geo[p]];
+  const int dim = g.dim, K = stencil_k(dim), nx = g.n[0], ny = g.n[1];
+  const int cell = g_cell[p];
+  const uint32_t m = g_meta[p];
+  const uint32_t act = meta_active(m), dm = meta_depmask(m);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    if (f >= F) break;
+    const T* fld = static_cast<const T*>(P.f[f]) + g.cell_off;
+    const T* bc = static_cast<const T*>(P.bc[f]);
+    const int kind = P.kind[f];
+    T acc = wload<T>(wtab, ng, kind, 7, p) * bc[p];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      if (k >= K) break;
+      if (!(act >> k & 1u) || (dm >> k & 1u)) continue;
+      acc += wload<T>(wtab, ng, kind, k, p) * fld[member_cell(dim, cell, nx, ny, m, k)];
+    }
+    part[(size_t)f * ng + p] = acc;
+  }
+}
+
+void launch_fill_partial(int dtype, int F, void* const* fields, const int* bc_kind, const void* const* bc,
+                         const Geom* G, const int* g_geo, const int* g_cell, const uint32_t* g_meta,
+                         const double* wtab, int ng, void* part, cudaStream_t s, int T) {
+  if (ng <= 0) return;
+  FieldSet P;
+  for (int f = 0; f < 8; ++f) {
+    P.f[f] = f < F ? fields[f] : nullptr;
+    P.bc[f] = f < F ? bc[f] : nullptr;
+    P.kind[f] = f < F ? bc_kind[f] : 0;
+  }
+  if (dtype == 0)
+    k_fill_partial<float><<<(ng + T - 1) / T, T, 0, s>>>(P, F, G, g_geo, g_cell, g_meta, wtab, ng, (float*)part);
+  else
+    k_fill_partial<double><<<(ng + T - 1) / T, T, 0, s>>>(P, F, G, g_geo, g_cell, g_meta, wtab, ng, (double*)part);
+}
+
 constexpr int CH_T = 512;
 
 size_t fill_chain_smem(int dtype, int dim, int F, int n) {
@@ -94,12 +144,11 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
                                                      const int* __restrict__ g_dep,
                                                      const int* __restrict__ lev_ptr,
                                                      const double* __restrict__ wtab, int ng,
-                                                     int* status) {
+                                                     const T* __restrict__ part, int* status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom& g = G[geo_list[blockIdx.x]];
   const int n = g.n_ghost, g0 = g.ghost_off, dim = g.dim;
   const int K = stencil_k(dim);
-  const int nx = g.n[0], ny = g.n[1];
   T* vals = reinterpret_cast<T*>(smem);                 // [F][n]
   T* wdep = vals + (size_t)F * n;                       // [2][K][n]
   int* dpos = reinterpret_cast<int*>(wdep + (size_t)2 * K * n);  // [K][n]
@@ -107,24 +156,14 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
   int* lps = cellv + n;                                          // [n_levels + 1]
   const int* lp = lev_ptr + g.lev_off;
   for (int q = threadIdx.x; q <= g.n_levels; q += CH_T) lps[q] = lp[q] - g0;
-  // phase 1: boundary term + fluid members; dependency weights and positions
+  // phase 1: the partial sums (boundary term + fluid members) of the
+  // geometry's ghosts; dependency weights and positions
   for (int s = threadIdx.x; s < n; s += CH_T) {
     int p = g0 + s;
-    int cell = g_cell[p];
-    cellv[s] = cell;
+    cellv[s] = g_cell[p];
     uint32_t m = g_meta[p];
-    uint32_t act = meta_active(m), dm = meta_depmask(m);
-    for (int f = 0; f < F; ++f) {
-      const T* fld = static_cast<const T*>(P.f[f]) + g.cell_off;
-      const T* bc = static_cast<const T*>(P.bc[f]);
-      int kind = P.kind[f];
-      T acc = wload<T>(wtab, ng, kind, 7, p) * bc[p];
-      for (int k = 0; k < K; ++k) {
-        if (!(act >> k & 1u) || (dm >> k & 1u)) continue;
-        acc += wload<T>(wtab, ng, kind, k, p) * fld[member_cell(dim, cell, nx, ny, m, k)];
-      }
-      vals[(size_t)f * n + s] = acc;
-    }
+    uint32_t dm = meta_depmask(m);
+    for (int f = 0; f < F; ++f) vals[(size_t)f * n + s] = part[(size_t)f * ng + p];
     for (int k = 0; k < K; ++k) {
       bool d = dm >> k & 1u;
       dpos[(size_t)k * n + s] = d ? g_dep[(size_t)k * ng + p] - g0 : -1;
@@ -170,7 +209,7 @@ void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int
                        const void* const* bc, const Geom* G, const int* geo_list, int n_list,
                        const int* g_cell, const uint32_t* g_meta, const int* g_dep,
                        const int* lev_ptr, const double* wtab, int ng_total, size_t smem,
-                       int* status, cudaStream_t s) {
+                       const void* part, int* status, cudaStream_t s) {
   (void)dim;
   if (n_list <= 0) return;
   FieldSet P;
@@ -185,14 +224,14 @@ void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int
       cudaFuncSetAttribute(k_fill_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       set_float = smem;
     }
-    k_fill_chain<float><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, status);
+    k_fill_chain<float><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, (const float*)part, status);
   } else {
     static size_t set_double = 0;
     if (smem > set_double) {
       cudaFuncSetAttribute(k_fill_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       set_double = smem;
     }
-    k_fill_chain<double><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, status);
+    k_fill_chain<double><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, (const double*)part, status);
   }
 }
 
