@@ -284,7 +284,7 @@ PHASES = {
     "levels": ("poscell", "deps", "levels", "reorder", "tables", "gsrc"),
     "fill": ("fill_part", "fill_chain"),
     "forces": ("forces",),
-    "adjoint": ("adj_seed", "adj_chain", "adj_fluid", "adj_bc"),
+    "adjoint": ("adj_seed", "adj_part", "adj_chain", "adj_fluid", "adj_bc"),
 }
 
 
@@ -405,7 +405,13 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
         "fill_level": ng * F * (K * s + s + s) + ng * (4 + 4 + 2 * (K + 1) * 8),
         "forces": ng * (4 + 4 + 8 * dim + 4 + (2 + K + dim * (K + 1)) * 8 + s * (dim + 1) * (K + 1)),
         "adj_seed": ng * (4 + 8 * dim + (2 + K + dim * (K + 1)) * 8 + F * (K + 1) * 8),
-        "adj_chain": ng * (4 + s * F) + n_gsrc * (4 + 4 + F * 8 + 16),
+        # start values and incidence records: per source entry its word,
+        # F force coefficients, the consumer's meta and two weights read, a
+        # record (consumer, two weights) written; per update lambda0 written
+        "adj_part": ng * (4 + s * F) + n_gsrc * (4 + F * 8 + 4 + 16 + 4 + 2 * s),
+        # chain: per update lambda0 read and lambda written; per source entry
+        # its record read
+        "adj_chain": ng * (4 + 2 * s * F) + n_gsrc * (4 + 2 * s),
         "adj_level": ng * (4 + s * F) + n_gsrc * (4 + 4 + F * 8 + 16),
         "adj_fluid": ng * 12 + ng * K * (F * 8 + 8 + F * s) + ng * K * F * s,
         "adj_bc": ng * (4 + 4 + 16 + 3 * F * s),
@@ -418,8 +424,7 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
 # kernel).  The many-field calls were captured on 32 geometries and scaled by
 # the ghost count.  A kernel changed since its capture is left out (None).
 TRAFFIC_PER_LAUNCH = {
-    "adj_fluid": 33.85e6, "fill_chain": 28.37e6, "forces": 32.54e6, "adj_chain": 6.40e6,
-    "levels": 1.11e6, "rows": 0.25e6, "place": 1.77e6, "gsrc": 14.11e6,
+    "forces": 32.54e6, "rows": 0.25e6,
     "pfill": 123.0e6, "padj": 153.0e6,
 }
 

@@ -316,8 +316,10 @@ int64_t ebr_launch_count(const void* ctx);
  * Threads per block of the kernels that run one thread per item (interface
  * cell, ghost, fluid target): "iface", "place", "ghost_write" (the per-ghost
  * closest-point kernel of that step), "deps", "tables", "gsrc", "fill_part"
- * (the partial sums of the persistent fill), "adj_seed", "adj_fluid",
- * "adj_bc" -- the names under which ebr_profile_read reports them.  The block size changes scheduling only: every result is bitwise the
+ * (the partial sums of the persistent fill), "adj_seed", "adj_part" (the
+ * start values and incidence records of the persistent adjoint chain),
+ * "adj_fluid", "adj_bc" -- the names under which ebr_profile_read reports
+ * them.  The block size changes scheduling only: every result is bitwise the
  * same for every allowed value.  A launch reads the context's value when it
  * is issued, so a graph captured earlier keeps the shapes it was captured
  * with.  The Python autotuner (paper_2609_10165_b300/autotune.py) times the

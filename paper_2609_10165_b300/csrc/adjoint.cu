@@ -133,10 +133,55 @@ void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int
     k_adj_level<double><<<(n + T - 1) / T, T, 0, s>>>(A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (double*)lam);
 }
 
-// One CTA per geometry.  Phase 1 (parallel): lambda starts as the sum of the
-// force coefficients of all incidences, and the consumer incidences (active
-// members) are packed into shared memory with their weights.  Phase 2: reverse
-// levels on shared memory only.
+// Per ghost, grid-wide (one thread per ghost): lambda's start value, the sum
+// of the force coefficients of all incidences (in source-list order), and,
+// per incidence of the source list, the consumer it stands for (global ghost
+// position, -1 when it is the ghost itself or an inactive member) with its
+// weights of both kinds.
+template <typename T>
+__global__ void k_adj_part(int F, int ng, const int* __restrict__ gsrc_ptr, const int* __restrict__ gsrc,
+                           const uint32_t* __restrict__ g_meta, const double* __restrict__ wtab,
+                           const double* __restrict__ sv, T* __restrict__ lpart, int* __restrict__ cq_g,
+                           T* __restrict__ cw_g, int n_src) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ng) return;
+  const int j0 = gsrc_ptr[p], j1 = gsrc_ptr[p + 1];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    if (f >= F) break;
+    T acc = T(0);
+    for (int j = j0; j < j1; ++j) {
+      const int e = gsrc[j];
+      acc += (T)sv[(size_t)(f * 8 + (e & 7)) * ng + (e >> 3)];
+    }
+    lpart[(size_t)f * ng + p] = acc;
+  }
+  for (int j = j0; j < j1; ++j) {
+    const int e = gsrc[j];
+    const int q = e >> 3, sl = e & 7;
+    const bool c = sl > 0 && (meta_active(g_meta[q]) >> (sl - 1) & 1u);
+    cq_g[j] = c ? q : -1;
+    cw_g[j] = c ? (T)wtab[(size_t)(sl - 1) * ng + q] : T(0);
+    cw_g[(size_t)n_src + j] = c ? (T)wtab[(size_t)(8 + sl - 1) * ng + q] : T(0);
+  }
+}
+
+void launch_adj_part(int dtype, int F, int ng, const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
+                     const double* wtab, const double* sv, void* lpart, int* cq_g, void* cw_g, int n_src,
+                     cudaStream_t s, int T) {
+  if (ng <= 0) return;
+  if (dtype == 0)
+    k_adj_part<float><<<(ng + T - 1) / T, T, 0, s>>>(F, ng, gsrc_ptr, gsrc, g_meta, wtab, sv, (float*)lpart,
+                                                     cq_g, (float*)cw_g, n_src);
+  else
+    k_adj_part<double><<<(ng + T - 1) / T, T, 0, s>>>(F, ng, gsrc_ptr, gsrc, g_meta, wtab, sv, (double*)lpart,
+                                                      cq_g, (double*)cw_g, n_src);
+}
+
+// One CTA per geometry.  Phase 1: lambda's start values and the geometry's
+// slice of the incidence records (from k_adj_part) are copied into shared
+// memory.  Phase 2: reverse levels on shared memory only, each ghost adding
+// w lambda over its consumers in source-list order.
 constexpr int AC_T = 512;
 
 size_t adj_chain_smem(int dtype, int F, int n, int n_src) {
@@ -149,90 +194,36 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
                                                     const int* __restrict__ geo_list,
                                                     const int* __restrict__ lev_ptr,
                                                     const int* __restrict__ gsrc_ptr,
-                                                    const int* __restrict__ gsrc,
-                                                    const uint32_t* __restrict__ g_meta,
-                                                    const double* __restrict__ wtab,
-                                                    const double* __restrict__ sv, int ng,
+                                                    const T* __restrict__ lpart,
+                                                    const int* __restrict__ cq_g,
+                                                    const T* __restrict__ cw_g, int n_src, int ng,
                                                     T* __restrict__ lam) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int sh_warp[32];
-  __shared__ int sh_carry;
   const Geom& g = G[geo_list[blockIdx.x]];
   const int n = g.n_ghost, g0 = g.ghost_off;
-  const int nsrc = gsrc_ptr[g0 + n] - gsrc_ptr[g0];
+  const int j0g = gsrc_ptr[g0];
+  const int nsrc = gsrc_ptr[g0 + n] - j0g;
   T* L = reinterpret_cast<T*>(smem);                         // [F][n]
   T* cw = L + (size_t)F * n;                                 // [2][nsrc]
-  int* cq = reinterpret_cast<int*>(cw + (size_t)2 * nsrc);   // [nsrc]
+  int* cq = reinterpret_cast<int*>(cw + (size_t)2 * nsrc);   // [nsrc] local consumer or -1
   int* cptr = cq + nsrc;                                     // [n + 1]
   int* lps = cptr + n + 1;                                   // [n_levels + 1]
   {
     const int* lp = lev_ptr + g.lev_off;
     for (int q = threadIdx.x; q <= g.n_levels; q += AC_T) lps[q] = lp[q] - g0;
   }
-  // phase 1a: force-coefficient sums, consumer counts
-  if (threadIdx.x == 0) sh_carry = 0;
-  __syncthreads();
-  for (int base = 0; base < n; base += AC_T) {
-    int s = base + threadIdx.x;
-    int cnt = 0;
-    if (s < n) {
-      int p = g0 + s;
-      int j0 = gsrc_ptr[p], j1 = gsrc_ptr[p + 1];
-      for (int f = 0; f < F; ++f) {
-        T acc = T(0);
-        for (int j = j0; j < j1; ++j) {
-          int e = gsrc[j];
-          acc += (T)sv[(size_t)(f * 8 + (e & 7)) * ng + (e >> 3)];
-        }
-        L[(size_t)f * n + s] = acc;
-      }
-      for (int j = j0; j < j1; ++j) {
-        int e = gsrc[j];
-        int q = e >> 3, sl = e & 7;
-        if (sl > 0 && (meta_active(g_meta[q]) >> (sl - 1) & 1u)) ++cnt;
-      }
-    }
-    // block exclusive scan of cnt
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) sh_warp[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      int v = lane < (AC_T / 32) ? sh_warp[lane] : 0;
-      for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-      }
-      if (lane < AC_T / 32) sh_warp[lane] = v;
-    }
-    __syncthreads();
-    int ex = sh_carry + (w > 0 ? sh_warp[w - 1] : 0) + x - cnt;
-    if (s < n) cptr[s] = ex;
-    int tot = sh_warp[AC_T / 32 - 1];
-    __syncthreads();
-    if (threadIdx.x == 0) sh_carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) cptr[n] = sh_carry;
-  __syncthreads();
-  // phase 1b: pack consumers
+  // phase 1: start values, source offsets and the incidence records
   for (int s = threadIdx.x; s < n; s += AC_T) {
-    int p = g0 + s;
-    int o = cptr[s];
-    for (int j = gsrc_ptr[p]; j < gsrc_ptr[p + 1]; ++j) {
-      int e = gsrc[j];
-      int q = e >> 3, sl = e & 7;
-      if (sl > 0 && (meta_active(g_meta[q]) >> (sl - 1) & 1u)) {
-        cq[o] = q - g0;
-        cw[o] = (T)wtab[(size_t)(sl - 1) * ng + q];
-        cw[nsrc + o] = (T)wtab[(size_t)(8 + sl - 1) * ng + q];
-        ++o;
-      }
-    }
+    const int p = g0 + s;
+    cptr[s] = gsrc_ptr[p] - j0g;
+    for (int f = 0; f < F; ++f) L[(size_t)f * n + s] = lpart[(size_t)f * ng + p];
+  }
+  if (threadIdx.x == 0) cptr[n] = nsrc;
+  for (int o = threadIdx.x; o < nsrc; o += AC_T) {
+    const int q = cq_g[j0g + o];
+    cq[o] = q >= 0 ? q - g0 : -1;
+    cw[o] = cw_g[j0g + o];
+    cw[nsrc + o] = cw_g[(size_t)n_src + j0g + o];
   }
   __syncthreads();
   // phase 2: reverse levels
@@ -240,7 +231,10 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
     for (int f = 0; f < F; ++f) {
       int kind = A.kind[f];
       T v = L[(size_t)f * n + s];
-      for (int o = cptr[s]; o < cptr[s + 1]; ++o) v += cw[(size_t)kind * nsrc + o] * L[(size_t)f * n + cq[o]];
+      for (int o = cptr[s]; o < cptr[s + 1]; ++o) {
+        const int q = cq[o];
+        if (q >= 0) v += cw[(size_t)kind * nsrc + o] * L[(size_t)f * n + q];
+      }
       L[(size_t)f * n + s] = v;
     }
   };
@@ -267,7 +261,7 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
 
 void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom* G,
                       const int* geo_list, int n_list, const int* lev_ptr, const int* gsrc_ptr,
-                      const int* gsrc, const uint32_t* g_meta, const double* wtab, const double* sv,
+                      const void* lpart, const int* cq_g, const void* cw_g, int n_src,
                       int ng_total, void* lam, size_t smem, cudaStream_t s) {
   (void)dim;
   if (n_list <= 0) return;
@@ -279,14 +273,16 @@ void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom*
       cudaFuncSetAttribute(k_adj_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       set_float = smem;
     }
-    k_adj_chain<float><<<n_list, AC_T, smem, s>>>(A, F, G, geo_list, lev_ptr, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (float*)lam);
+    k_adj_chain<float><<<n_list, AC_T, smem, s>>>(A, F, G, geo_list, lev_ptr, gsrc_ptr, (const float*)lpart, cq_g,
+                                                  (const float*)cw_g, n_src, ng_total, (float*)lam);
   } else {
     static size_t set_double = 0;
     if (smem > set_double) {
       cudaFuncSetAttribute(k_adj_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       set_double = smem;
     }
-    k_adj_chain<double><<<n_list, AC_T, smem, s>>>(A, F, G, geo_list, lev_ptr, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (double*)lam);
+    k_adj_chain<double><<<n_list, AC_T, smem, s>>>(A, F, G, geo_list, lev_ptr, gsrc_ptr, (const double*)lpart,
+                                                   cq_g, (const double*)cw_g, n_src, ng_total, (double*)lam);
   }
 }
 

@@ -33,9 +33,9 @@ struct ChainPlan {
 // block size changes scheduling only, never a result.  Names are those of
 // the kernels' profiling records (ebr_profile_read).
 enum TuneId { TU_IFACE, TU_PLACE, TU_GHOST, TU_DEPS, TU_TABLES, TU_GSRC, TU_FILL_PART, TU_ADJ_SEED,
-              TU_ADJ_FLUID, TU_ADJ_BC, TU_N };
+              TU_ADJ_PART, TU_ADJ_FLUID, TU_ADJ_BC, TU_N };
 static const char* const kTuneNames[TU_N] = {"iface", "place", "ghost_write", "deps", "tables", "gsrc",
-                                             "fill_part", "adj_seed", "adj_fluid", "adj_bc"};
+                                             "fill_part", "adj_seed", "adj_part", "adj_fluid", "adj_bc"};
 constexpr int TUNE_DEFAULT = 128;
 constexpr int TUNE_MAX = 256;     // every kernel fits at 256 threads (<= 255 registers each)
 
@@ -115,9 +115,12 @@ struct Ctx {
   double* sv = nullptr;
   void* lam = nullptr;
   void* fpart = nullptr;       // fill partial sums [F <= 8][ng] (field type)
+  void* apart = nullptr;       // adjoint start values [F <= 8][ng] (field type)
+  int* acq = nullptr;          // adjoint incidence records: consumer [n_gsrc]
+  void* acw = nullptr;         //   and weights [2][n_gsrc] (field type)
 
   std::vector<int> order_by_size;            // geometries, largest ghost count first
-  int tb[TU_N] = {TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT,
+  int tb[TU_N] = {TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT,
                   TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT};   // threads per block
   PackedPlan pplan;                          // schedule of the packed kernels
   void* lamP = nullptr;                      // packed adjoint scratch [ng][F]
@@ -433,6 +436,8 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
       if (st) return st;
       st = balloc(c, &c->fpart, 8 * 8 * (size_t)ng);
       if (st) return st;
+      st = balloc(c, &c->apart, 8 * 8 * (size_t)ng);
+      if (st) return st;
     }
   }
   prof_begin(c, s, "poscell");
@@ -508,6 +513,9 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
       c->h_gsrc_geo[b] = hp[g.ghost_off + g.n_ghost] - hp[g.ghost_off];
     }
     AL(c->gsrc, c->n_gsrc);
+    AL(c->acq, c->n_gsrc);
+    ebr_status st = balloc(c, &c->acw, 2 * 8 * std::max<size_t>((size_t)c->n_gsrc, 1));
+    if (st) return st;
   }
   prof_begin(c, sg, "gsrc");
   launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
@@ -922,11 +930,15 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
     ebr_status st = chain_plan(c, 1, dtype, n_fields, &cp);
     if (st) return st;
     if (cp->n_list > 0) {
+      prof_begin(c, s, "adj_part");
+      launch_adj_part(dtype, n_fields, c->ng, c->gsrc_ptr, c->gsrc, c->g_meta, c->wtab, c->sv, c->apart,
+                      c->acq, c->acw, c->n_gsrc, s, c->tb[TU_ADJ_PART]);
+      prof_end(c, s);
       prof_begin(c, s, "adj_chain");
       launch_adj_chain(dtype, dim, n_fields, kinds, c->dG, cp->d_list, cp->n_list, c->lev_ptr,
-                       c->gsrc_ptr, c->gsrc, c->g_meta, c->wtab, c->sv, c->ng, c->lam, cp->smem, s);
+                       c->gsrc_ptr, c->apart, c->acq, c->acw, c->n_gsrc, c->ng, c->lam, cp->smem, s);
       prof_end(c, s);
-      c->launches += 1;
+      c->launches += 2;
     }
     level_geoms = cp->fallback;
   } else if (mode == EBR_MODE_LEVEL_LAUNCH) {

@@ -102,9 +102,14 @@ void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int
                       const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
                       const double* wtab, const double* sv, int ng_total, void* lam, cudaStream_t s);
 size_t adj_chain_smem(int dtype, int F, int n_ghost, int n_src);
+// lambda's start values [F][ng] and the incidence records of the source
+// lists (consumer position or -1, weights [2][n_src]) for the chain kernel
+void launch_adj_part(int dtype, int F, int ng, const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
+                     const double* wtab, const double* sv, void* lpart, int* cq_g, void* cw_g, int n_src,
+                     cudaStream_t s, int T = 128);
 void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom* G,
                       const int* geo_list, int n_list, const int* lev_ptr, const int* gsrc_ptr,
-                      const int* gsrc, const uint32_t* g_meta, const double* wtab, const double* sv,
+                      const void* lpart, const int* cq_g, const void* cw_g, int n_src,
                       int ng_total, void* lam, size_t smem, cudaStream_t s);
 void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                       const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
