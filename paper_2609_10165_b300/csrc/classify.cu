@@ -552,22 +552,33 @@ __global__ void __launch_bounds__(256) k_rows(const Geom* __restrict__ G, const 
     const long long i = q - rst;
     tags[q] = (int8_t)(i >= s && i <= t);
   }
-  // aligned middle: 16 cells per lane per step.  Bytes [lo, hi) of the chunk
-  // lie inside the run; each 32-bit word is a difference of two prefix masks
-  // of 0x01 bytes.
-  for (long long c = a0 + 16LL * Gp.sl; c < a1; c += 16LL * RG) {
-    const int i0 = (int)(c - rst);
-    const int lo = min(max(s - i0, 0), 16);
-    const int hi = min(max(t + 1 - i0, 0), 16);
-    uint32_t w[4];
+  // aligned middle: 16 cells per lane per step, offsets from the row start in
+  // 32-bit.  A chunk wholly outside or inside the run is a constant; only the
+  // (at most two) chunks that hold an end of the run build their bytes: bytes
+  // [lo, hi) lie inside, each 32-bit word a difference of two prefix masks of
+  // 0x01 bytes.
+  int8_t* const rowp = tags + rst;
+  const int ia0 = (int)(a0 - rst), ia1 = (int)(a1 - rst);
+  for (int i0 = ia0 + 16 * Gp.sl; i0 < ia1; i0 += 16 * RG) {
+    uint4 v;
+    if (i0 + 15 < s || i0 > t) {
+      v = make_uint4(0u, 0u, 0u, 0u);
+    } else if (i0 >= s && i0 + 15 <= t) {
+      v = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+    } else {
+      const int lo = min(max(s - i0, 0), 16);
+      const int hi = min(max(t + 1 - i0, 0), 16);
+      uint32_t w[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int l = min(max(lo - 4 * q, 0), 4), h = min(max(hi - 4 * q, 0), 4);
-      const uint32_t ph = h ? (0x01010101u >> (8 * (4 - h))) : 0u;
-      const uint32_t pl = l ? (0x01010101u >> (8 * (4 - l))) : 0u;
-      w[q] = h > l ? (ph & ~pl) : 0u;
+      for (int q = 0; q < 4; ++q) {
+        const int l = min(max(lo - 4 * q, 0), 4), h = min(max(hi - 4 * q, 0), 4);
+        const uint32_t ph = h ? (0x01010101u >> (8 * (4 - h))) : 0u;
+        const uint32_t pl = l ? (0x01010101u >> (8 * (4 - l))) : 0u;
+        w[q] = h > l ? (ph & ~pl) : 0u;
+      }
+      v = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    *reinterpret_cast<uint4*>(tags + c) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(rowp + i0) = v;
   }
 }
 
