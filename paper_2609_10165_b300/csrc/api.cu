@@ -312,7 +312,7 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   prof_begin(c, s, "scan");
   launch_scan(c->row_cnt, c->row_ptr, c->total_rows, c->scan_tmp, s);
   prof_end(c, s);
-  c->launches += 4;
+  c->launches += 3;
   CKL();
   if (planning) {
     std::vector<int> hp(c->total_rows + 1);
@@ -356,7 +356,7 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   prof_begin(c, s, "scan");
   launch_scan(c->gflag, c->gpos, c->n_iface, c->scan_tmp, s);
   prof_end(c, s);
-  c->launches += 4;
+  c->launches += 3;
   CKL();
   if (planning) {
     std::vector<int> hp(c->n_iface + 1);
@@ -500,7 +500,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   prof_begin(c, sg, "scan");
   launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, sg);
   prof_end(c, sg);
-  c->launches += 7;
+  c->launches += 6;
   CKL();
   if (planning) {
     CK(cudaMemcpyAsync(&c->n_gsrc, c->gsrc_ptr + ng, sizeof(int), cudaMemcpyDeviceToHost, s));

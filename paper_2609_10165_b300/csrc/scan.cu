@@ -1,6 +1,7 @@
 // Device-wide exclusive scan of int32 counts (stream compaction offsets).
-// Three launches: per-block scan, scan of the block totals, add-back.
-// out has n + 1 entries; out[n] is the total.
+// Two launches: per-tile scan (writing the tile totals), then add-back, where
+// every tile sums the totals of the tiles before it (integer sums: exact in
+// any order).  out has n + 1 entries; out[n] is the total.
 #include "ebr_kernels.cuh"
 
 namespace ebr {
@@ -75,13 +76,30 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ tile_sum
 }
 
 __global__ void __launch_bounds__(SCAN_T) k_scan_add(int* __restrict__ out, int n,
-                                                     const int* __restrict__ tile_sum) {
+                                                     const int* __restrict__ tile_sum, int ntiles) {
+  __shared__ int sh[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // offset of this tile: the totals of the tiles before it (one more for the
+  // last tile, whose sum is the grand total out[n])
+  const int upto = blockIdx.x == ntiles - 1 ? ntiles : blockIdx.x;
+  int part = 0;
+  for (int i = threadIdx.x; i < upto; i += SCAN_T) part += tile_sum[i];
+  part = __reduce_add_sync(0xffffffffu, part);
+  if (lane == 0) sh[w] = part;
+  __syncthreads();
+  int before = 0, total = 0;
+  for (int q = 0; q < SCAN_T / 32; ++q) total += sh[q];
+  if (blockIdx.x == ntiles - 1) {
+    before = total - tile_sum[ntiles - 1];
+    if (threadIdx.x == 0) out[n] = total;
+  } else {
+    before = total;
+  }
   long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
-  int add = tile_sum[blockIdx.x];
 #pragma unroll
   for (int q = 0; q < SCAN_ITEMS; ++q) {
     long long i = base + q;
-    if (i < n) out[i] += add;
+    if (i < n) out[i] += before;
   }
 }
 
@@ -98,8 +116,7 @@ void launch_scan(const int* in, int* out, int n, void* temp, cudaStream_t s) {
     return;
   }
   k_scan_tiles<<<ntiles, SCAN_T, 0, s>>>(in, out, n, ts);
-  k_scan_sums<<<1, SCAN_T, 0, s>>>(ts, ntiles, out, n);
-  k_scan_add<<<ntiles, SCAN_T, 0, s>>>(out, n, ts);
+  k_scan_add<<<ntiles, SCAN_T, 0, s>>>(out, n, ts, ntiles);
 }
 
 }  // namespace ebr
