@@ -284,7 +284,7 @@ PHASES = {
     "levels": ("poscell", "deps", "levels", "reorder", "tables", "gsrc"),
     "fill": ("fill_part", "fill_chain"),
     "forces": ("forces",),
-    "adjoint": ("adj_seed", "adj_part", "adj_chain", "adj_fluid", "adj_bc"),
+    "adjoint": ("adj_seed", "adj_part", "adj_chain", "adj_probe", "adj_fluid", "adj_bc"),
 }
 
 
@@ -413,6 +413,10 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
         # its record read
         "adj_chain": ng * (4 + 2 * s * F) + n_gsrc * (4 + 2 * s),
         "adj_level": ng * (4 + s * F) + n_gsrc * (4 + 4 + F * 8 + 16),
+        # fluid targets' sources: per ghost its record, per incidence the
+        # member's tag, the neighbours' tags, its count and cell written, about
+        # two source words
+        "adj_probe": ng * 12 + ng * K * (1 + 8 + 8 + 2 * 4),
         "adj_fluid": ng * 12 + ng * K * (F * 8 + 8 + F * s) + ng * K * F * s,
         "adj_bc": ng * (4 + 4 + 16 + 3 * F * s),
     }

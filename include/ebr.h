@@ -318,8 +318,9 @@ int64_t ebr_launch_count(const void* ctx);
  * closest-point kernel of that step), "deps", "tables", "gsrc", "fill_part"
  * (the partial sums of the persistent fill), "adj_seed", "adj_part" (the
  * start values and incidence records of the persistent adjoint chain),
- * "adj_fluid", "adj_bc" -- the names under which ebr_profile_read reports
- * them.  The block size changes scheduling only: every result is bitwise the
+ * "adj_probe" (the fluid targets' sources at reach 1, found beside the
+ * chain), "adj_fluid", "adj_bc" -- the names under which ebr_profile_read
+ * reports them.  The block size changes scheduling only: every result is bitwise the
  * same for every allowed value.  A launch reads the context's value when it
  * is issued, so a graph captured earlier keeps the shapes it was captured
  * with.  The Python autotuner (paper_2609_10165_b300/autotune.py) times the

@@ -357,6 +357,115 @@ void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* 
     k_adj_fluid<double><<<(n + T - 1) / T, T, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const double*)lam, accumulate, kmax);
 }
 
+// Fluid targets in two passes at reach 1: the probe needs no lambda, so it
+// can run beside the seed and chain kernels; the pull then sums in the
+// probe's order, which gives the same bits as the one-pass kernel above.
+// Per incidence i = (ghost p, member k): fcnt[i] = sources recorded when the
+// incidence owns its target (the first source in probe order), else 0;
+// fcell[i] = the target's global cell; fsrc[i * cap + e] = q << 4 | slot << 1
+// | active, in probe order.
+__global__ void k_adj_fprobe(int ng, const Geom* __restrict__ G, const int* __restrict__ g_geo,
+                             const int* __restrict__ g_cell, const uint32_t* __restrict__ g_meta,
+                             const int8_t* __restrict__ tags, const int* __restrict__ pos_of_cell, int kmax,
+                             int cap, int* __restrict__ fcnt, int* __restrict__ fcell, int* __restrict__ fsrc,
+                             int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = i / kmax, k = i - p * kmax;
+  if (p >= ng) return;
+  const Geom& g = G[g_geo[p]];
+  int n = 0;
+  if (k < stencil_k(g.dim)) {
+    int gijk[3], tijk[3];
+    cell_ijk3(g, g_cell[p], gijk);
+    member_ijk(g, gijk, g_meta[p], k, tijk);
+    const int8_t* tg = tags + g.cell_off;
+    const int* pc = pos_of_cell + g.cell_off;
+    if (in_grid(g, tijk) && tg[cell_lin(g, tijk)] == 0) {
+      bool first = true, owner = false;
+      int* out = fsrc + (size_t)i * cap;
+      probe_sources(g, tijk, tg, pc, g_meta, 1, [&](int q, int slot) {
+        if (first) {
+          first = false;
+          owner = (q == p && slot == k + 1);
+          if (!owner) return false;
+        }
+        const int act = (int)((meta_active(g_meta[q]) >> (slot - 1)) & 1u);
+        if (n < cap) out[n] = (q << 4) | (slot << 1) | act;
+        ++n;
+        return true;
+      });
+      if (!owner) n = 0;
+      if (n > cap) {
+        set_status(status, S_EINVAL);
+        n = cap;
+      }
+      if (n > 0) fcell[i] = (int)(g.cell_off + cell_lin(g, tijk));
+    }
+  }
+  fcnt[i] = n;
+}
+
+template <typename T>
+__global__ void k_adj_fpull(AdjSet A, int F, int ng, int n_inc, int cap, const int* __restrict__ fcnt,
+                            const int* __restrict__ fcell, const int* __restrict__ fsrc,
+                            const double* __restrict__ wtab, const double* __restrict__ sv,
+                            const T* __restrict__ lam, int accumulate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inc) return;
+  const int n = fcnt[i];
+  if (n <= 0) return;
+  T acc[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) acc[f] = T(0);
+  const int* src = fsrc + (size_t)i * cap;
+  for (int e = 0; e < n; ++e) {
+    const int w = src[e];
+    const int q = w >> 4, slot = (w >> 1) & 7;
+    const bool act = w & 1;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      if (f < F) {
+        acc[f] += (T)sv[(size_t)(f * 8 + slot) * ng + q];
+        if (act) acc[f] += (T)wtab[(size_t)(A.kind[f] * 8 + slot - 1) * ng + q] * lam[(size_t)f * ng + q];
+      }
+    }
+  }
+  const long long c = fcell[i];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    if (f < F) {
+      T* gr = static_cast<T*>(A.grad[f]);
+      if (accumulate) gr[c] += acc[f]; else gr[c] = acc[f];
+    }
+  }
+}
+
+int adj_fluid_cap(int dim) { return dim == 2 ? 8 : 26; }
+
+void launch_adj_fprobe(int ng, const Geom* G, const int* g_geo, const int* g_cell, const uint32_t* g_meta,
+                       const int8_t* tags, const int* pos_of_cell, int kmax, int cap, int* fcnt, int* fcell,
+                       int* fsrc, int* status, cudaStream_t s, int T) {
+  if (ng <= 0) return;
+  const int n = ng * kmax;
+  k_adj_fprobe<<<(n + T - 1) / T, T, 0, s>>>(ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, kmax, cap, fcnt,
+                                             fcell, fsrc, status);
+}
+
+void launch_adj_fpull(int dtype, int F, const int* bc_kind, int ng, int kmax, int cap, const int* fcnt,
+                      const int* fcell, const int* fsrc, const double* wtab, const double* sv, const void* lam,
+                      void* const* grad, int accumulate, cudaStream_t s, int T) {
+  if (ng <= 0) return;
+  AdjSet A{};
+  for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.grad[f] = grad[f]; }
+  const int n = ng * kmax;
+  if (dtype == 0)
+    k_adj_fpull<float><<<(n + T - 1) / T, T, 0, s>>>(A, F, ng, n, cap, fcnt, fcell, fsrc, wtab, sv,
+                                                     (const float*)lam, accumulate);
+  else
+    k_adj_fpull<double><<<(n + T - 1) / T, T, 0, s>>>(A, F, ng, n, cap, fcnt, fcell, fsrc, wtab, sv,
+                                                      (const double*)lam, accumulate);
+}
+
 template <typename T>
 __global__ void k_adj_bc(AdjSet A, int F, int ng, const Geom* __restrict__ G,
                          const int* __restrict__ g_geo, const int* __restrict__ g_cell,

@@ -33,9 +33,10 @@ struct ChainPlan {
 // block size changes scheduling only, never a result.  Names are those of
 // the kernels' profiling records (ebr_profile_read).
 enum TuneId { TU_IFACE, TU_PLACE, TU_GHOST, TU_DEPS, TU_TABLES, TU_GSRC, TU_FILL_PART, TU_ADJ_SEED,
-              TU_ADJ_PART, TU_ADJ_FLUID, TU_ADJ_BC, TU_N };
+              TU_ADJ_PART, TU_ADJ_PROBE, TU_ADJ_FLUID, TU_ADJ_BC, TU_N };
 static const char* const kTuneNames[TU_N] = {"iface", "place", "ghost_write", "deps", "tables", "gsrc",
-                                             "fill_part", "adj_seed", "adj_part", "adj_fluid", "adj_bc"};
+                                             "fill_part", "adj_seed", "adj_part", "adj_probe", "adj_fluid",
+                                             "adj_bc"};
 constexpr int TUNE_DEFAULT = 128;
 constexpr int TUNE_MAX = 256;     // every kernel fits at 256 threads (<= 255 registers each)
 
@@ -118,10 +119,15 @@ struct Ctx {
   void* apart = nullptr;       // adjoint start values [F <= 8][ng] (field type)
   int* acq = nullptr;          // adjoint incidence records: consumer [n_gsrc]
   void* acw = nullptr;         //   and weights [2][n_gsrc] (field type)
+  // fluid targets of the adjoint at reach 1, per (ghost, member) incidence:
+  // source count when it owns its target, target cell, sources [cap]
+  int *af_cnt = nullptr, *af_cell = nullptr, *af_src = nullptr;
+  int af_cap = 0;
 
   std::vector<int> order_by_size;            // geometries, largest ghost count first
   int tb[TU_N] = {TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT,
-                  TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT};   // threads per block
+                  TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT, TUNE_DEFAULT,
+                  TUNE_DEFAULT};   // threads per block
   PackedPlan pplan;                          // schedule of the packed kernels
   void* lamP = nullptr;                      // packed adjoint scratch [ng][F]
   size_t lamP_bytes = 0;
@@ -438,6 +444,13 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
       if (st) return st;
       st = balloc(c, &c->apart, 8 * 8 * (size_t)ng);
       if (st) return st;
+    }
+    {
+      const int kmax = stencil_k(c->hG[0].dim);
+      c->af_cap = adj_fluid_cap(c->hG[0].dim);
+      AL(c->af_cnt, (size_t)ng * kmax);
+      AL(c->af_cell, (size_t)ng * kmax);
+      AL(c->af_src, (size_t)ng * kmax * c->af_cap);
     }
   }
   prof_begin(c, s, "poscell");
@@ -920,6 +933,23 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
   cudaStream_t s = S(stream);
   int kinds[8];
   for (int f = 0; f < n_fields; ++f) kinds[f] = h_bc_kind[f];
+  // at reach 1 the fluid targets' probe (which needs no lambda) runs on the
+  // second stream beside the seed and chain kernels; the pull joins it
+  const int kmax = stencil_k(dim);
+  const bool split = c->rmax == 1 && c->ng > 0 && c->total_cells < (1LL << 31) && c->ng < (1 << 27) &&
+                     c->af_cap > 0;
+  if (split) {
+    ebr_status st = ensure_side(c);
+    if (st) return st;
+    CK(cudaEventRecord(c->ev_fork, s));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    prof_begin(c, c->side, "adj_probe");
+    launch_adj_fprobe(c->ng, c->dG, c->g_geo, c->g_cell, c->g_meta, c->tags, c->pos_of_cell, kmax, c->af_cap,
+                      c->af_cnt, c->af_cell, c->af_src, c->d_status, c->side, c->tb[TU_ADJ_PROBE]);
+    prof_end(c, c->side);
+    CK(cudaEventRecord(c->ev_join, c->side));
+    c->launches += 1;
+  }
   prof_begin(c, s, "adj_seed");
   launch_adj_seed(dim, n_fields, role, mu, h_dirs, d_seed, c->ng, c->g_geo, c->g_n, c->ftab, c->sv, s, c->tb[TU_ADJ_SEED]);
   prof_end(c, s);
@@ -957,11 +987,19 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
       c->launches += 1;
     }
   }
-  prof_begin(c, s, "adj_fluid");
-  launch_adj_fluid(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->g_meta, c->tags,
-                   c->pos_of_cell, c->rmax, c->wtab, c->sv, c->lam, d_grad_fields, accumulate,
-                   stencil_k(dim), s, c->tb[TU_ADJ_FLUID]);
-  prof_end(c, s);
+  if (split) {
+    CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+    prof_begin(c, s, "adj_fluid");
+    launch_adj_fpull(dtype, n_fields, kinds, c->ng, kmax, c->af_cap, c->af_cnt, c->af_cell, c->af_src, c->wtab,
+                     c->sv, c->lam, d_grad_fields, accumulate, s, c->tb[TU_ADJ_FLUID]);
+    prof_end(c, s);
+  } else {
+    prof_begin(c, s, "adj_fluid");
+    launch_adj_fluid(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->g_meta, c->tags,
+                     c->pos_of_cell, c->rmax, c->wtab, c->sv, c->lam, d_grad_fields, accumulate, kmax, s,
+                     c->tb[TU_ADJ_FLUID]);
+    prof_end(c, s);
+  }
   c->launches += 1;
   prof_begin(c, s, "adj_bc");
   launch_adj_bc(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->wtab, c->lam, d_grad_bc,

@@ -111,6 +111,14 @@ void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom*
                       const int* geo_list, int n_list, const int* lev_ptr, const int* gsrc_ptr,
                       const void* lpart, const int* cq_g, const void* cw_g, int n_src,
                       int ng_total, void* lam, size_t smem, cudaStream_t s);
+// fluid targets in two passes at reach 1: probe (no lambda needed) and pull
+int adj_fluid_cap(int dim);
+void launch_adj_fprobe(int ng, const Geom* G, const int* g_geo, const int* g_cell, const uint32_t* g_meta,
+                       const int8_t* tags, const int* pos_of_cell, int kmax, int cap, int* fcnt, int* fcell,
+                       int* fsrc, int* status, cudaStream_t s, int T = 128);
+void launch_adj_fpull(int dtype, int F, const int* bc_kind, int ng, int kmax, int cap, const int* fcnt,
+                      const int* fcell, const int* fsrc, const double* wtab, const double* sv, const void* lam,
+                      void* const* grad, int accumulate, cudaStream_t s, int T = 128);
 void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                       const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
                       const int* pos_of_cell, int rmax, const double* wtab, const double* sv,

@@ -68,7 +68,7 @@ def test_results_bitwise_equal_at_every_block_size():
     R, geoms, fields, bcs = _setup()
     ref = _step(R, geoms, fields, bcs)
     names = R.tunable_kernels()
-    assert len(names) == 11 and all(R.block_size(n) == 128 for n in names)
+    assert len(names) == 12 and all(R.block_size(n) == 128 for n in names)
     for T in (32, 64, 96, 256):
         for n in names:
             R.set_block_size(n, T)
