@@ -428,9 +428,9 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
 # kernel).  The many-field calls were captured on 32 geometries and scaled by
 # the ghost count.  A kernel changed since its capture is left out (None).
 TRAFFIC_PER_LAUNCH = {
-    "adj_fluid": 27.58e6, "fill_part": 27.85e6, "fill_chain": 6.04e6, "forces": 32.54e6,
-    "adj_part": 6.34e6, "adj_chain": 3.13e6, "levels": 1.13e6, "rows": 0.34e6, "place": 1.74e6,
-    "gsrc": 13.97e6, "tables": 9.84e6,
+    "adj_fluid": 23.61e6, "adj_probe": 13.95e6, "adj_seed": 10.62e6, "fill_part": 27.85e6,
+    "fill_chain": 6.04e6, "forces": 32.54e6, "adj_part": 6.34e6, "adj_chain": 3.13e6, "levels": 1.13e6,
+    "rows": 0.34e6, "place": 1.74e6, "gsrc": 13.97e6, "tables": 9.84e6,
     "pfill": 123.0e6, "padj": 153.0e6,
 }
 
