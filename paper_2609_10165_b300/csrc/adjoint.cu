@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom& g = G[geo_list[blockIdx.x]];
   const int n = g.n_ghost, g0 = g.ghost_off;
+  const int n_levels = g.n_levels;     // in a register: the kernel stores to global memory
   const int j0g = gsrc_ptr[g0];
   const int nsrc = gsrc_ptr[g0 + n] - j0g;
   T* L = reinterpret_cast<T*>(smem);                         // [F][n]
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
   int* lps = cptr + n + 1;                                   // [n_levels + 1]
   {
     const int* lp = lev_ptr + g.lev_off;
-    for (int q = threadIdx.x; q <= g.n_levels; q += AC_T) lps[q] = lp[q] - g0;
+    for (int q = threadIdx.x; q <= n_levels; q += AC_T) lps[q] = lp[q] - g0;
   }
   // phase 1: start values, source offsets and the incidence records
   for (int s = threadIdx.x; s < n; s += AC_T) {
@@ -240,10 +241,10 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
   };
   // the deepest levels (lw.., at most 32 ghosts each) come first: one warp
   // walks them with warp barriers, then the block takes the wide levels
-  int lw = g.n_levels + 1;
+  int lw = n_levels + 1;
   while (lw > 1 && lps[lw - 1] - lps[lw - 2] <= 32) --lw;
   if (threadIdx.x < 32) {
-    for (int lv = g.n_levels; lv >= lw; --lv) {
+    for (int lv = n_levels; lv >= lw; --lv) {
       const int s = lps[lv - 1] + threadIdx.x;
       if (s < lps[lv]) relax(s);
       __syncwarp();

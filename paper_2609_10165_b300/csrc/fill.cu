@@ -148,6 +148,10 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom& g = G[geo_list[blockIdx.x]];
   const int n = g.n_ghost, g0 = g.ghost_off, dim = g.dim;
+  // geometry fields in registers: the loops below store to global memory,
+  // after which a read through g would have to be repeated
+  const int n_levels = g.n_levels;
+  const long long cell_off = g.cell_off;
   const int K = stencil_k(dim);
   T* vals = reinterpret_cast<T*>(smem);                 // [F][n]
   T* wdep = vals + (size_t)F * n;                       // [2][K][n]
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
   int* cellv = dpos + (size_t)K * n;                             // [n]
   int* lps = cellv + n;                                          // [n_levels + 1]
   const int* lp = lev_ptr + g.lev_off;
-  for (int q = threadIdx.x; q <= g.n_levels; q += CH_T) lps[q] = lp[q] - g0;
+  for (int q = threadIdx.x; q <= n_levels; q += CH_T) lps[q] = lp[q] - g0;
   // phase 1: the partial sums (boundary term + fluid members) of the
   // geometry's ghosts; dependency weights and positions
   for (int s = threadIdx.x; s < n; s += CH_T) {
@@ -183,13 +187,13 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
         if (d >= 0) v += wdep[(size_t)(kind * K + k) * n + s] * vals[(size_t)f * n + d];
       }
       vals[(size_t)f * n + s] = v;
-      static_cast<T*>(P.f[f])[g.cell_off + cell] = v;
+      static_cast<T*>(P.f[f])[cell_off + cell] = v;
       if (!isfinite(v)) set_status(status, S_ENONFINITE);
     }
   };
   // levels lw.. hold at most 32 ghosts each (the thin end of the chains):
   // one warp walks them with warp barriers instead of block barriers
-  int lw = g.n_levels + 1;
+  int lw = n_levels + 1;
   while (lw > 1 && lps[lw - 1] - lps[lw - 2] <= 32) --lw;
   for (int lv = 1; lv < lw; ++lv) {
     int a = lps[lv - 1], b = lps[lv];
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
     __syncthreads();
   }
   if (threadIdx.x < 32) {
-    for (int lv = lw; lv <= g.n_levels; ++lv) {
+    for (int lv = lw; lv <= n_levels; ++lv) {
       const int s = lps[lv - 1] + threadIdx.x;
       if (s < lps[lv]) relax(s);
       __syncwarp();

@@ -262,10 +262,11 @@ __global__ void __launch_bounds__(PK_CT) k_pf_tail(T* __restrict__ fld, int F,
                                                    int* status) {
   const Geom& g = G[geo_list[blockIdx.x]];
   const int* lp = lev_ptr + g.lev_off;
+  const int n_levels = g.n_levels;     // in a register: the kernel stores to global memory
   const int warp = threadIdx.x >> 5, nw = PK_CT / 32;
   const int nch = (F + 31) / 32;
   bool bad = false;
-  for (int lv = L0 + 1; lv <= g.n_levels; ++lv) {
+  for (int lv = L0 + 1; lv <= n_levels; ++lv) {
     const int a = lp[lv - 1], b = lp[lv];
     for (int t = warp; t < (b - a) * nch; t += nw) {
       const int p = a + t / nch, c = t % nch;
@@ -300,7 +301,8 @@ __global__ void __launch_bounds__(PK_CT, 2) k_pf_tail_s(T* __restrict__ fld, int
   constexpr int V = WPV<T>::v;
   const Geom& g = G[geo_list[blockIdx.y]];   // chunks of one geometry launch together
   const int* lp = lev_ptr + g.lev_off;
-  const int t0 = lp[L0], nt = lp[g.n_levels] - t0;
+  const int n_levels = g.n_levels;     // in a register: the kernel stores to global memory
+  const int t0 = lp[L0], nt = lp[n_levels] - t0;
   // the plan sized the shared memory for `cap` tail ghosts
   if (nt < 0 || nt > cap || t0 < 0 || t0 + nt > ng) {
     if (threadIdx.x == 0) set_status(status, S_ESHAPE);
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(PK_CT, 2) k_pf_tail_s(T* __restrict__ fld, int
   }
   __syncthreads();
   bool bad = false;
-  for (int lv = L0 + 1; lv <= g.n_levels; ++lv) {
+  for (int lv = L0 + 1; lv <= n_levels; ++lv) {
     const int a = max(lp[lv - 1] - t0, 0), b = min(lp[lv] - t0, nt);
     for (int s = a + warp; s < b; s += nw) {
       T v = vals[s * 32 + lane];
@@ -405,7 +407,8 @@ __global__ void __launch_bounds__(PK_CT, 2) k_pa_tail_s(T* __restrict__ cot, T* 
   constexpr int V = WPV<T>::v;
   const Geom& g = G[geo_list[blockIdx.y]];   // chunks of one geometry launch together
   const int* lp = lev_ptr + g.lev_off;
-  const int t0 = lp[L0], nt = lp[g.n_levels] - t0;
+  const int n_levels = g.n_levels;     // in a register: the kernel stores to global memory
+  const int t0 = lp[L0], nt = lp[n_levels] - t0;
   // the plan sized the shared memory for `cap` tail ghosts
   if (nt < 0 || nt > cap || t0 < 0 || t0 + nt > ng) {
     if (threadIdx.x == 0) set_status(status, S_ESHAPE);
@@ -472,7 +475,7 @@ __global__ void __launch_bounds__(PK_CT, 2) k_pa_tail_s(T* __restrict__ cot, T* 
     }
   }
   __syncthreads();
-  for (int lv = g.n_levels; lv > L0; --lv) {
+  for (int lv = n_levels; lv > L0; --lv) {
     const int a = max(lp[lv - 1] - t0, 0), b = min(lp[lv] - t0, nt);
     for (int s = a + warp; s < b; s += nw) {
       T v = lam[s * 32 + lane];
@@ -602,10 +605,11 @@ __global__ void __launch_bounds__(PK_CA, 2) k_pa_tail(T* __restrict__ cot, T* __
   const Geom& g = G[geo_list[blockIdx.x]];
   const int warp = threadIdx.x >> 5, nw = PK_CA / 32;
   const int* lp = lev_ptr + g.lev_off;
+  const int n_levels = g.n_levels;     // in a register: the kernel stores to global memory
   // bring every tail record and ghost-cotangent row into L2 up front (the
   // rows of one ghost are F consecutive values, 128-byte lines)
   {
-    const int t0 = lp[L0], t1 = lp[g.n_levels];
+    const int t0 = lp[L0], t1 = lp[n_levels];
     const int lines = (int)((F * sizeof(T) + 127) / 128);
     for (int i = threadIdx.x; i < (t1 - t0) * (lines + 1); i += PK_CA) {
       const int p = t0 + i / (lines + 1), l = i % (lines + 1);
@@ -620,9 +624,9 @@ __global__ void __launch_bounds__(PK_CA, 2) k_pa_tail(T* __restrict__ cot, T* __
     }
   }
   Rec nxt{0u, 0u};
-  if (g.n_levels > L0 && lp[g.n_levels - 1] + warp < lp[g.n_levels])
-    nxt = load_rec(rec, lp[g.n_levels - 1] + warp, rec_src_words<T>());
-  for (int lv = g.n_levels; lv > L0; --lv) {
+  if (n_levels > L0 && lp[n_levels - 1] + warp < lp[n_levels])
+    nxt = load_rec(rec, lp[n_levels - 1] + warp, rec_src_words<T>());
+  for (int lv = n_levels; lv > L0; --lv) {
     const int a = lp[lv - 1], b = lp[lv];
     for (int p = a + warp; p < b; p += nw) {
       const Rec R = p == a + warp ? nxt : load_rec(rec, p, rec_src_words<T>());
