@@ -269,19 +269,11 @@ void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom*
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) A.kind[f] = bc_kind[f];
   if (dtype == 0) {
-    static size_t set_float = 0;
-    if (smem > set_float) {
-      cudaFuncSetAttribute(k_adj_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set_float = smem;
-    }
+    smem_raise<k_adj_chain<float>>(smem);
     k_adj_chain<float><<<n_list, AC_T, smem, s>>>(A, F, G, geo_list, lev_ptr, gsrc_ptr, (const float*)lpart, cq_g,
                                                   (const float*)cw_g, n_src, ng_total, (float*)lam);
   } else {
-    static size_t set_double = 0;
-    if (smem > set_double) {
-      cudaFuncSetAttribute(k_adj_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set_double = smem;
-    }
+    smem_raise<k_adj_chain<double>>(smem);
     k_adj_chain<double><<<n_list, AC_T, smem, s>>>(A, F, G, geo_list, lev_ptr, gsrc_ptr, (const double*)lpart,
                                                    cq_g, (const double*)cw_g, n_src, ng_total, (double*)lam);
   }

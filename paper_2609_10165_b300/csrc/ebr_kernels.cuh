@@ -20,6 +20,19 @@ __device__ inline int find_seg(const int* off, int B, int x) {
   return lo;
 }
 
+// Raise (never lower) the dynamic shared-memory opt-in of kernel K on the
+// current device to `bytes`: the opt-in is per function and per device, and a
+// graph captured earlier may still hold a launch with a larger size.
+template <auto K>
+inline void smem_raise(size_t bytes) {
+  static size_t seen[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && bytes <= seen[dev]) return;
+  cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (dev >= 0 && dev < 64) seen[dev] = bytes;
+}
+
 // kind (0 Dirichlet, 1 Neumann) of field f of a packed field array: bit f
 struct KindBits {
   uint32_t w[32];

@@ -223,18 +223,10 @@ void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int
     P.kind[f] = f < F ? bc_kind[f] : 0;
   }
   if (dtype == 0) {
-    static size_t set_float = 0;
-    if (smem > set_float) {
-      cudaFuncSetAttribute(k_fill_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set_float = smem;
-    }
+    smem_raise<k_fill_chain<float>>(smem);
     k_fill_chain<float><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, (const float*)part, status);
   } else {
-    static size_t set_double = 0;
-    if (smem > set_double) {
-      cudaFuncSetAttribute(k_fill_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set_double = smem;
-    }
+    smem_raise<k_fill_chain<double>>(smem);
     k_fill_chain<double><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, (const double*)part, status);
   }
 }

@@ -354,11 +354,7 @@ __global__ void __launch_bounds__(LV_T, 2) k_levels(const Geom* __restrict__ G, 
 void launch_levels(const Geom* G, int B, const int* dep, int ng_total, int* level, int* order_pos,
                    int* lev_ptr, int* n_levels, size_t smem, int* status, cudaStream_t s) {
   if (B <= 0) return;
-  static size_t set = 0;
-  if (smem > set) {
-    cudaFuncSetAttribute(k_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    set = smem;
-  }
+  smem_raise<k_levels>(smem);
   k_levels<<<B, LV_T, smem, s>>>(G, B, dep, ng_total, level, order_pos, lev_ptr, n_levels,
                                  (int)(smem / sizeof(int)) - 16, status);
 }

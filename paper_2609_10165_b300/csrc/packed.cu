@@ -794,11 +794,6 @@ size_t packed_tail_smem(int dtype, int dim, int which, int max_nt, int limit) {
   return b <= (size_t)limit ? b : 0;
 }
 
-template <typename Kern>
-static void smem_optin(Kern k, size_t bytes) {
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 template <typename T, int K>
 static void pfill_t(int F, void* fld, const void* bc, const KindBits& kb, const Geom* G,
                     const int* lev_ptr, int ng, const PackedPlan& pp, const uint32_t* rec,
@@ -815,7 +810,7 @@ static void pfill_t(int F, void* fld, const void* bc, const KindBits& kb, const 
   if (phase == 2 && pp.n_tail > 0) {
     const size_t sm = pp.tail_smem[0][sizeof(T) == 4 ? 0 : 1];
     if (sm > 0) {
-      smem_optin(k_pf_tail_s<T, K>, sm);
+      smem_raise<k_pf_tail_s<T, K>>(sm);
       k_pf_tail_s<T, K><<<dim3((F + 31) / 32, pp.n_tail), PK_CT, sm, s>>>((T*)fld, F, kb, G, pp.d_tail, rec,
                                                                          lev_ptr, pp.L0, pp.tail_max, ng,
                                                                          status);
@@ -850,7 +845,7 @@ static void padj_t(int F, void* cot, void* lamP, void* gbc, const KindBits& kb, 
   if (phase == 0 && pp.n_tail_a > 0) {
     const size_t sm = pp.tail_smem[1][sizeof(T) == 4 ? 0 : 1];
     if (sm > 0) {
-      smem_optin(k_pa_tail_s<T>, sm);
+      smem_raise<k_pa_tail_s<T>>(sm);
       k_pa_tail_s<T><<<dim3((F + 31) / 32, pp.n_tail_a), PK_CT, sm, s>>>((T*)cot, (T*)lamP, (T*)gbc, F, kb,
                                                                         G, pp.d_tail_a, rec_adj, lev_ptr,
                                                                         pp.L0a, pp.cons, wtab, ng,
