@@ -164,30 +164,47 @@ __device__ inline void ellipse_closest(double a, double b, double p, double q,
   }
   double t = (double)tf;
   if (!(t > tmin)) t = 0.0;
+  // Halley steps in double (cubic convergence; the increment in float): from
+  // the float solution one step leaves an error of about the float rounding of
+  // the increment (~1e-14 relative), so a step of <= 1e-6 relative is final;
+  // the reciprocals at the new t follow from the last ones to second order,
+  // 1/(u + d) = (1/u)(1 - e + e^2), e = d/u, error O(e^3)
+  double rua = 0.0, rub = 0.0;
+  bool have = false;
   for (int it = 0; it < 12; ++it) {
     // one double reciprocal per iteration: 1/(a^2+t) and 1/(b^2+t) from
     // 1/((a^2+t)(b^2+t))
     const double ua = a2 + t, ub = b2 + t;
     const double r = 1.0 / (ua * ub);
-    const double rua = ub * r, rub = ua * r;
+    rua = ub * r;
+    rub = ua * r;
     const double fx = a * p * rua, fy = b * q * rub;
-    const double F = fx * fx + fy * fy - 1.0;
-    const double dF = -2.0 * (fx * fx * rua + fy * fy * rub);
-    if (F == 0.0 || dF == 0.0) break;
-    // Newton increment in float: its relative error (6e-8) times the step
-    // leaves an error far below the next step, which converges it
-    // quadratically; F stays in double
-    double tn = t - (double)((float)F / (float)dF);
+    const double fx2 = fx * fx, fy2 = fy * fy;
+    const double F = fx2 + fy2 - 1.0;
+    const double dF = -2.0 * (fx2 * rua + fy2 * rub);
+    if (F == 0.0 || dF == 0.0) { have = true; break; }
+    const double d2F = 6.0 * (fx2 * rua * rua + fy2 * rub * rub);
+    const float Ff = (float)F, dFf = (float)dF, d2Ff = (float)d2F;
+    const float den = 2.0f * dFf * dFf - Ff * d2Ff;
+    const float step = den > 0.0f ? 2.0f * Ff * dFf / den : Ff / dFf;
+    double tn = t - (double)step;
     if (!(tn > tmin)) tn = 0.5 * (t + tmin);
-    const double dt = fabs(tn - t);
+    const double d = tn - t;
     t = tn;
-    // quadratic convergence: once a step is 1e-12 relative, the error left
-    // after it is far below the rounding level
-    if (dt <= 1e-12 * fabs(t)) break;
+    if (fabs(d) <= 1e-6 * fabs(t)) {
+      const double ea = d * rua, eb = d * rub;
+      rua = rua * (1.0 - ea + ea * ea);
+      rub = rub * (1.0 - eb + eb * eb);
+      have = true;
+      break;
+    }
   }
-  const double ua = a2 + t, ub = b2 + t;
-  const double r = 1.0 / (ua * ub);
-  const double rua = ub * r, rub = ua * r;
+  if (!have) {
+    const double ua = a2 + t, ub = b2 + t;
+    const double r = 1.0 / (ua * ub);
+    rua = ub * r;
+    rub = ua * r;
+  }
   // G - S = (p t / ua, q t / ub): no cancellation; the outward normal at S is
   // along (X / a^2, Y / b^2) = (p / ua, q / ub)
   const double ex = p * t * rua, ey = q * t * rub;
