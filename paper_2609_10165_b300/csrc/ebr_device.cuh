@@ -232,6 +232,13 @@ __device__ inline void airfoil_u(double t, double c, double u, double& x, double
   ddy = k * fma(u2, fma(u2, fma(u2, 56.0 * a4, 30.0 * a3), 12.0 * a2), 2.0 * a1);
 }
 
+// d^3 y / du^3 of the upper surface (x is quadratic in u: its third derivative is 0)
+__device__ inline double airfoil_dddy(double t, double c, double u) {
+  const double a2 = -0.3516, a3 = 0.2843, a4 = -0.1015;
+  const double u2 = u * u;
+  return 5.0 * t * c * u * fma(u2, fma(u2, 336.0 * a4, 120.0 * a3), 24.0 * a2);
+}
+
 __device__ inline void airfoil_u32(float t, float c, float u, float& x, float& y, float& dx,
                                    float& dy, float& ddx, float& ddy) {
   const float a0 = 0.2969f, a1 = -0.1260f, a2 = -0.3516f, a3 = 0.2843f, a4 = -0.1015f;
@@ -314,25 +321,32 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
       uf = un;
     }
     u = fmin(fmax((double)uf, lo), hi);
-    // double polish: safeguarded Newton inside [lo, hi]; a step of 1e-12
-    // relative leaves an error below the rounding level (quadratic convergence)
+    // double polish: safeguarded Halley steps inside [lo, hi] (cubic
+    // convergence; the increment in float).  From the float solution one step
+    // leaves an error of about the float rounding of the increment (~1e-14
+    // relative), so a step of <= 1e-6 relative is final: the point and its
+    // tangent at the new u follow from the last evaluation by Taylor
+    // expansion -- x exactly (it is quadratic in u), y and y' to third order
+    // (the neglected terms are ~step^4 and ~step^3).
     for (int it = 0; it < 40; ++it) {
       double gv, dg;
       g(u, gv, dg);
       if (gv == 0.0) { have = true; break; }
-      // Newton increment in float (g in double): see ellipse_closest
-      const double st = dg > 0.0 ? (double)((float)gv / (float)dg) : 0.0;
-      // converged: a Newton step of 1e-12 (relative) leaves an error below the
-      // rounding level; accept it before the safeguard, which would otherwise
-      // bisect once the step rounds onto the bracket end.  The point and the
-      // tangent at the new u follow from the last evaluation to first order
-      // (the neglected terms are ~step^2, far below the rounding level).
-      if (dg > 0.0 && fabs(st) <= 1e-12 * fmax(u, 1e-3)) {
+      const double dddy = airfoil_dddy(t, c, u);
+      const double d2g = 3.0 * (dx * ddx + dy * ddy) + (y - qy) * dddy;
+      double st = 0.0;
+      if (dg > 0.0) {
+        const float gf = (float)gv, dgf = (float)dg, d2f = (float)d2g;
+        const float den = 2.0f * dgf * dgf - gf * d2f;
+        st = den > 0.0f ? (double)(2.0f * gf * dgf / den) : (double)(gf / dgf);
+      }
+      if (dg > 0.0 && fabs(st) <= 1e-6 * fmax(u, 1e-3)) {
         const double un = fmin(fmax(u - st, lo), hi), du = un - u;
-        x += dx * du;
-        y += dy * du;
+        const double h2 = 0.5 * du * du;
+        x += dx * du + ddx * h2;
+        y += dy * du + ddy * h2 + dddy * h2 * du * (1.0 / 3.0);
         dx += ddx * du;
-        dy += ddy * du;
+        dy += ddy * du + dddy * h2;
         u = un;
         have = true;
         break;
