@@ -45,6 +45,9 @@ def _gpu_grad(run, w, seed, dtype, mode):
 @pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
 @pytest.mark.parametrize("mode", ["level", "persistent"])
 def test_adjoint_matches_oracle(kind, placement, mode):
+    # HGC and CGC stencils reach 1 cell (the fluid targets' two-pass probe +
+    # pull); the CGC_ES cases here reach r = 2 (the one-pass kernel): both
+    # paths of the fluid-target gradient are compared with the oracle
     w = _case(kind)
     run = GPURun([w], placement)
     seed = (0.7, -1.3)

@@ -213,3 +213,14 @@ def test_max_alpha_near_paper_cylinder_values():
     ac = _alphas(O.classify(gd, bd, "CGC")).max()
     assert 0.4 < ah <= 0.5
     assert 0.85 < ac < 1.0
+
+
+def test_adjoint_cases_cover_both_stencil_reaches():
+    """The GPU adjoint cases span both fluid-target paths of the library: HGC
+    stencils reach one cell, the CGC_ES cases reach two (Sec. 7's r_i)."""
+    import numpy as np
+    from tests.test_gpu_adjoint import _case
+    for kind in ("ellipse", "airfoil", "sphere"):
+        w = _case(kind)
+        assert int(np.max(O.classify(w["grid"], w["body"], "HGC").r)) == 1
+        assert int(np.max(O.classify(w["grid"], w["body"], "CGC_ES").r)) == 2
