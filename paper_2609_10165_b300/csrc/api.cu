@@ -484,11 +484,9 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     c->launches += 1;
   }
   prof_begin(c, s, "reorder");
-  launch_reorder(ng, c->order_pos, c->gs_cell, c->gs_geo, c->gs_psi, c->gs_n, c->gs_meta, c->dep,
-                 c->level, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->g_dep, c->g_level, s);
-  prof_end(c, s);
-  prof_begin(c, s, "poscell");
-  launch_poscell(c->dG, ng, c->g_cell, c->g_geo, nullptr, c->pos_of_cell, s);
+  launch_reorder(c->dG, c->pos_of_cell, ng, c->order_pos, c->gs_cell, c->gs_geo, c->gs_psi, c->gs_n,
+                 c->gs_meta, c->dep, c->level, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->g_dep,
+                 c->g_level, s);
   prof_end(c, s);
   // The coefficient tables and the ghost-target source lists (adjoint only)
   // are independent: outside planning the source lists run on the second
@@ -513,7 +511,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   prof_begin(c, sg, "scan");
   launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, sg);
   prof_end(c, sg);
-  c->launches += 6;
+  c->launches += 5;   // reorder, tables, source counts, scan (2)
   CKL();
   if (planning) {
     CK(cudaMemcpyAsync(&c->n_gsrc, c->gsrc_ptr + ng, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -71,7 +71,10 @@ void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, u
 size_t levels_smem(int dim, int n_ghost);
 void launch_levels(const Geom* G, int B, const int* dep, int ng_total, int* level, int* order_pos,
                    int* lev_ptr, int* n_levels, size_t smem, int* status, cudaStream_t s);
-void launch_reorder(int ng, const int* order_pos, const int* gs_cell, const int* gs_geo,
+// canonical reorder of the ghost records; writes pos_of_cell (canonical
+// position of each ghost cell) as well
+void launch_reorder(const Geom* G, int* pos_of_cell, int ng, const int* order_pos, const int* gs_cell,
+                    const int* gs_geo,
                     const double* gs_psi, const double* gs_n, const uint32_t* gs_meta,
                     const int* dep, const int* level, int* g_cell, int* g_geo, double* g_psi,
                     double* g_n, uint32_t* g_meta, int* g_dep, int* g_level, cudaStream_t s);

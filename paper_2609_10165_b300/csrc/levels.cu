@@ -359,7 +359,10 @@ void launch_levels(const Geom* G, int B, const int* dep, int ng_total, int* leve
                                  (int)(smem / sizeof(int)) - 16, status);
 }
 
-__global__ void k_reorder(int ng, const int* __restrict__ order_pos, const int* __restrict__ gs_cell,
+// canonical reorder of the ghost records; also the position of each ghost
+// cell in the canonical order (pos_of_cell; no kernel of this launch reads it)
+__global__ void k_reorder(const Geom* __restrict__ G, int* __restrict__ pos_of_cell, int ng,
+                          const int* __restrict__ order_pos, const int* __restrict__ gs_cell,
                           const int* __restrict__ gs_geo, const double* __restrict__ gs_psi,
                           const double* __restrict__ gs_n, const uint32_t* __restrict__ gs_meta,
                           const int* __restrict__ dep, const int* __restrict__ level,
@@ -379,14 +382,16 @@ __global__ void k_reorder(int ng, const int* __restrict__ order_pos, const int* 
     int d = dep[(size_t)k * ng + s];
     g_dep[(size_t)k * ng + p] = d >= 0 ? order_pos[d] : -1;
   }
+  pos_of_cell[G[gs_geo[s]].cell_off + gs_cell[s]] = p;
 }
 
-void launch_reorder(int ng, const int* order_pos, const int* gs_cell, const int* gs_geo,
+void launch_reorder(const Geom* G, int* pos_of_cell, int ng, const int* order_pos, const int* gs_cell,
+                    const int* gs_geo,
                     const double* gs_psi, const double* gs_n, const uint32_t* gs_meta,
                     const int* dep, const int* level, int* g_cell, int* g_geo, double* g_psi,
                     double* g_n, uint32_t* g_meta, int* g_dep, int* g_level, cudaStream_t s) {
   if (ng <= 0) return;
-  k_reorder<<<(ng + 255) / 256, 256, 0, s>>>(ng, order_pos, gs_cell, gs_geo, gs_psi, gs_n, gs_meta,
+  k_reorder<<<(ng + 255) / 256, 256, 0, s>>>(G, pos_of_cell, ng, order_pos, gs_cell, gs_geo, gs_psi, gs_n, gs_meta,
                                              dep, level, g_cell, g_geo, g_psi, g_n, g_meta, g_dep,
                                              g_level);
 }
