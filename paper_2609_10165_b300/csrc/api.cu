@@ -279,9 +279,9 @@ __global__ void k_check(const Geom* G, int B, const int* row_ptr, const int* gpo
   if (b >= B) return;
   const Geom& g = G[b];
   if (stage == 0) {
+    // interface offsets of the rows, then ghost offsets of the interface list
     if (row_ptr[g.row_off] != g.iface_off) set_status(status, S_ESHAPE);
     if (b == B - 1 && row_ptr[g.row_off + g.n_rows] != n_iface) set_status(status, S_ESHAPE);
-  } else if (stage == 1) {
     if (gpos[g.iface_off] != g.ghost_off) set_status(status, S_ESHAPE);
     if (b == B - 1 && gpos[n_iface] != ng) set_status(status, S_ESHAPE);
   } else {
@@ -385,9 +385,7 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   } else {
     k_check<<<(c->B + 127) / 128, 128, 0, s>>>(c->dG, c->B, c->row_ptr, c->gpos, c->n_iface, c->ng,
                                                c->d_nlev, 0, c->d_status);
-    k_check<<<(c->B + 127) / 128, 128, 0, s>>>(c->dG, c->B, c->row_ptr, c->gpos, c->n_iface, c->ng,
-                                               c->d_nlev, 1, c->d_status);
-    c->launches += 2;
+    c->launches += 1;
   }
   prof_begin(c, s, "ghost_write");
   launch_ghost_write(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->iface_psi,
@@ -480,7 +478,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     if (st) return st;
   } else {
     k_check<<<(c->B + 127) / 128, 128, 0, s>>>(c->dG, c->B, c->row_ptr, c->gpos, c->n_iface, c->ng,
-                                               c->d_nlev, 2, c->d_status);
+                                               c->d_nlev, 1, c->d_status);
     c->launches += 1;
   }
   prof_begin(c, s, "reorder");
