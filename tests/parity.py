@@ -21,7 +21,7 @@ from paper_2609_10165_b300.api import Reconstructor
 U32 = 2.0 ** -24
 
 
-class GPURun:
+class DeviceRun:
     def __init__(self, geoms, placement, mode="persistent", dtype=torch.float64):
         """geoms: list of workload dicts (grid, body, fields, bc, roles, mu)."""
         self.geoms = geoms

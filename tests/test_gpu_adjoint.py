@@ -9,7 +9,7 @@ import torch
 
 import oracle as O
 from paper_2609_10165_b300 import inputs as I
-from tests.parity import GPURun
+from tests.parity import DeviceRun
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,7 @@ def test_adjoint_matches_oracle(kind, placement, mode):
     # pull); the CGC_ES cases here reach r = 2 (the one-pass kernel): both
     # paths of the fluid-target gradient are compared with the oracle
     w = _case(kind)
-    run = GPURun([w], placement)
+    run = DeviceRun([w], placement)
     seed = (0.7, -1.3)
     d = w["grid"]["dim"]
     dirs = I.DRAG_LIFT_DIRS_2D if d == 2 else I.DRAG_LIFT_DIRS_3D
@@ -80,7 +80,7 @@ def test_adjoint_finite_differences(name):
         w = _case("airfoil")
     else:
         w = I.WORKLOADS[name]()
-    run = GPURun([w], "HGC", dtype=torch.float64)
+    run = DeviceRun([w], "HGC", dtype=torch.float64)
     seed = (1.0, 0.5)
     rng = np.random.default_rng(5)
     arrays = run.field_arrays()
@@ -103,7 +103,7 @@ def test_adjoint_finite_differences(name):
 
 def test_autograd_function():
     w = _case("ellipse")
-    run = GPURun([w], "HGC", dtype=torch.float64)
+    run = DeviceRun([w], "HGC", dtype=torch.float64)
     dev = run.R.device
     arrays = run.field_arrays()
     bcs = run.bc_arrays()
@@ -122,7 +122,7 @@ def test_autograd_function():
 
 def test_adjoint_bitwise_reproducible():
     w = _case("airfoil")
-    run = GPURun([w], "HGC")
+    run = DeviceRun([w], "HGC")
     for dtype in (torch.float32, torch.float64):
         a = _gpu_grad(run, w, (1.0, 1.0), dtype, "persistent")
         b = _gpu_grad(run, w, (1.0, 1.0), dtype, "persistent")

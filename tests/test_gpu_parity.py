@@ -11,7 +11,7 @@ import torch
 
 import oracle as O
 from paper_2609_10165_b300 import inputs as I
-from tests.parity import GPURun, oracle_run, term_magnitude, compare_structure, U32
+from tests.parity import DeviceRun, oracle_run, term_magnitude, compare_structure, U32
 
 pytestmark = pytest.mark.gpu
 
@@ -84,7 +84,7 @@ def _check_values(run, geoms, placement, dtype):
 def test_small_cases_all_bodies(placement, mode, dtype):
     for k, case in enumerate(_small_cases()):
         g = _with_fields(case, 50 + 10 * k)
-        run = GPURun([g], placement, mode=mode, dtype=dtype)
+        run = DeviceRun([g], placement, mode=mode, dtype=dtype)
         compare_structure(run, [g], placement)
         _check_values(run, [g], placement, dtype)
 
@@ -94,7 +94,7 @@ def test_small_cases_batched_together():
     # forces, but classification / levels / fill are per geometry
     cases = [_with_fields(c, 90 + 10 * k) for k, c in enumerate(_small_cases()) if c["grid"]["dim"] == 2]
     for placement in ("HGC", "CGC_ES"):
-        run = GPURun(cases, placement, mode="persistent")
+        run = DeviceRun(cases, placement, mode="persistent")
         compare_structure(run, cases, placement)
         _check_values(run, cases, placement, torch.float64)
 
@@ -102,7 +102,7 @@ def test_small_cases_batched_together():
 @pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
 def test_cylinder_128(placement):
     w = I.cylinder(128, 1)
-    run = GPURun([w], placement, mode="level")
+    run = DeviceRun([w], placement, mode="level")
     res = compare_structure(run, [w], placement)
     c, lev = res[0]
     assert c.n_ghosts == run.info["cell"].size
@@ -112,7 +112,7 @@ def test_cylinder_128(placement):
 
 
 def _forces_case(w, placement, dtype, mode="persistent"):
-    run = GPURun([w], placement, mode=mode, dtype=dtype)
+    run = DeviceRun([w], placement, mode=mode, dtype=dtype)
     arrays = run.field_arrays()
     if dtype == torch.float32:
         arrays = [a.astype(np.float32).astype(np.float64) for a in arrays]
@@ -143,7 +143,7 @@ def test_cylinder_forces_fp64(placement):
 @pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
 def test_airfoil_2048(placement):
     w = I.airfoil_2048()
-    run = GPURun([w], placement, mode="persistent")
+    run = DeviceRun([w], placement, mode="persistent")
     compare_structure(run, [w], placement)
     _check_values(run, [w], placement, torch.float64)
     run.dtype = torch.float32
@@ -160,7 +160,7 @@ def test_airfoil_forces():
 
 def test_batch_subset_both_modes():
     geoms = I.batch()[:24]
-    run = GPURun(geoms, "HGC", mode="persistent", dtype=torch.float32)
+    run = DeviceRun(geoms, "HGC", mode="persistent", dtype=torch.float32)
     compare_structure(run, geoms, "HGC")
     _check_values(run, geoms, "HGC", torch.float32)
     run.mode = "level"
@@ -170,7 +170,7 @@ def test_batch_subset_both_modes():
 
 def test_reclassify_is_deterministic_and_sync_free():
     w = I.airfoil_2048()
-    run = GPURun([w], "HGC")
+    run = DeviceRun([w], "HGC")
     t0 = run.R.tags.clone()
     info0 = run.R.ghost_info()
     for _ in range(3):
@@ -211,7 +211,7 @@ def test_invalid_arguments():
 @pytest.mark.parametrize("name", ["sphere_256", "sphere_512"])
 def test_sphere_fp32(name):
     w = I.WORKLOADS[name]()
-    run = GPURun([w], "HGC", mode="persistent", dtype=torch.float32)
+    run = DeviceRun([w], "HGC", mode="persistent", dtype=torch.float32)
     compare_structure(run, [w], "HGC")
     _check_values(run, [w], "HGC", torch.float32)
 
@@ -230,7 +230,7 @@ def test_nonfinite_boundary_data_is_reported(mode):
     # word reports it at the next synchronising query, and is cleared by it
     from paper_2609_10165_b300._lib import EBRError
     w = _with_fields(_small_cases()[0], 300)
-    run = GPURun([w], "HGC", mode=mode, dtype=torch.float64)
+    run = DeviceRun([w], "HGC", mode=mode, dtype=torch.float64)
     arrays = run.field_arrays()
     bcs = run.bc_arrays()
     bcs[0][3] = np.nan
