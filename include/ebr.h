@@ -244,7 +244,11 @@ ebr_status ebr_boundary_forces(void* ctx, const void* const* d_vel, const void* 
  *   (canonical order), written (or added when accumulate = 1).
  * The pull form over transposed incidence lists makes the result bitwise
  * deterministic.  The geometry must have been planned and levelled.  The
- * field values themselves are not needed (the map is linear). */
+ * field values themselves are not needed (the map is linear).  When every
+ * stencil reaches one cell (HGC, CGC), the search for the fluid targets'
+ * sources runs on the context's second stream, forked from and joined back
+ * into `stream` by events inside this call (a stream capture records it as
+ * a parallel branch); the call's work is complete in `stream` order. */
 ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h_bc_kind,
                                    const int32_t* h_vel_index, int32_t p_index, double mu,
                                    const double* h_dirs, const double* d_seed,
