@@ -428,6 +428,7 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
 # kernel).  The many-field calls were captured on 32 geometries and scaled by
 # the ghost count.  A kernel changed since its capture is left out (None).
 TRAFFIC_PER_LAUNCH = {
+    "ghost_write": 9.15e6,       # k_ghost_write 7.98 MB + k_ghost_geom 1.17 MB
     "adj_fluid": 23.61e6, "adj_probe": 13.95e6, "adj_seed": 10.62e6, "fill_part": 27.85e6,
     "fill_chain": 6.04e6, "forces": 32.54e6, "adj_part": 6.34e6, "adj_chain": 3.13e6, "levels": 1.13e6,
     "rows": 0.34e6, "place": 1.74e6, "gsrc": 13.97e6, "tables": 9.84e6,
