@@ -3,6 +3,7 @@ classification threshold (psi = 0, |psi| = dn/2, an r_i ceiling, n_i = 0),
 where two correct FP64 implementations could round to different tags.  The
 workloads are checked here so the bit-exact GPU comparison is meaningful."""
 
+import numpy as np
 import pytest
 
 import oracle as O
@@ -18,10 +19,24 @@ def test_workload_has_no_ties(name, placement):
     O.build_levels(c)     # acyclic, stencils valid
 
 
-def test_batch_subset_has_no_ties():
-    for k, gm in enumerate(I.batch()):
-        if k % 8:
-            continue
-        c = O.classify(gm["grid"], gm["body"], "HGC")
-        assert c.ties == [], k
-        O.build_levels(c)
+def test_whole_batch_has_no_ties():
+    # all 256 geometries, in a spawn pool (the same worker the full-batch
+    # GPU test uses for its bit-exact structure comparison)
+    from tests.oracle_pool import batch_structure, start_pool
+    n = 256
+    with start_pool(n) as pool:
+        res = pool.map_async(batch_structure, [(n, gi, "HGC") for gi in range(n)]).get(timeout=1200)
+    assert [r[0] for r in res] == list(range(n))
+    assert [r[0] for r in res if not r[1]] == []
+
+
+def test_pool_worker_matches_a_direct_call():
+    from tests.oracle_pool import batch_structure, start_pool
+    args = [(256, 120, "HGC"), (256, 171, "CGC")]      # two of the smallest grids
+    with start_pool(len(args)) as pool:
+        got = pool.map_async(batch_structure, args).get(timeout=600)
+    for a, r in zip(args, got):
+        direct = batch_structure(a)
+        assert r[0] == direct[0] and r[1] == direct[1]
+        for x, y in zip(r[2:], direct[2:]):
+            assert np.array_equal(x, y)
