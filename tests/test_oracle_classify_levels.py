@@ -224,3 +224,15 @@ def test_adjoint_cases_cover_both_stencil_reaches():
         w = _case(kind)
         assert int(np.max(O.classify(w["grid"], w["body"], "HGC").r)) == 1
         assert int(np.max(O.classify(w["grid"], w["body"], "CGC_ES").r)) == 2
+
+
+@pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
+def test_bodies_missing_or_covering_the_grid_have_no_ghosts(placement):
+    # degenerate sets of the GPU edge-case tests: no cell of another tag
+    # shares a face, so no interface and no ghost; tags all 0 or all 1
+    from tests.test_gpu_edge_cases import _empty_cases
+    for case in _empty_cases():
+        c = O.classify(case["grid"], case["body"], placement)
+        lev = O.build_levels(c)
+        assert c.n_ghosts == 0 and c.ties == [] and lev.order.size == 0
+        assert np.unique(c.tags).size == 1 and c.tags[0] in (0, 1)
