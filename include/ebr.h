@@ -200,6 +200,7 @@ typedef enum {
  * h_bc_kind: host [n_fields] of ebr_bc.
  * d_bc: host array [n_fields] of device pointers, each [total ghosts] of dtype
  *   in canonical order: phi at S (Dirichlet) or dphi/dn at S (Neumann).
+ *   A pointer may be null when the geometry set has no ghost cell.
  * Weights are evaluated in double (Eqs. phi_G_*), once per ghost; FP32 fields
  * are combined in float with the weights rounded to float. */
 ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
@@ -242,6 +243,7 @@ ebr_status ebr_boundary_forces(void* ctx, const void* const* d_vel, const void* 
  *   fill); all other entries are left untouched.
  * d_grad_bc: host array [n_fields] of device pointers [total ghosts] of dtype
  *   (canonical order), written (or added when accumulate = 1).
+ *   A pointer may be null when the geometry set has no ghost cell.
  * The pull form over transposed incidence lists makes the result bitwise
  * deterministic.  The geometry must have been planned and levelled.  The
  * field values themselves are not needed (the map is linear).  When every

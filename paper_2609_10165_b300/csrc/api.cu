@@ -837,7 +837,8 @@ ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
     return fail(c, EBR_EINVAL, "ebr_reconstruct: 1..8 fields with kinds and boundary data required");
   if (dtype != EBR_F32 && dtype != EBR_F64) return fail(c, EBR_EINVAL, "ebr_reconstruct: bad dtype");
   for (int f = 0; f < n_fields; ++f) {
-    if (!d_fields[f] || !d_bc[f]) return fail(c, EBR_EINVAL, "ebr_reconstruct: null field %d", f);
+    if (!d_fields[f] || (!d_bc[f] && c->ng > 0))
+      return fail(c, EBR_EINVAL, "ebr_reconstruct: null field %d", f);
     if (h_bc_kind[f] != 0 && h_bc_kind[f] != 1) return fail(c, EBR_EINVAL, "ebr_reconstruct: bad bc kind");
   }
   cudaStream_t s = S(stream);
@@ -923,7 +924,8 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
   int role[4] = {-1, -1, -1, p_index};
   for (int a = 0; a < dim; ++a) role[a] = h_vel_index[a];
   for (int f = 0; f < n_fields; ++f) {
-    if (!d_grad_fields[f] || !d_grad_bc[f]) return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: null gradient %d", f);
+    if (!d_grad_fields[f] || (!d_grad_bc[f] && c->ng > 0))
+      return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: null gradient %d", f);
     if (h_bc_kind[f] != 0 && h_bc_kind[f] != 1) return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: bad bc kind");
   }
   cudaStream_t s = S(stream);

@@ -99,17 +99,17 @@ def test_empty_ghost_set(which):
         c = O.classify(case["grid"], case["body"], "HGC")
         assert np.array_equal(tags[R.cell_offset[b]:R.cell_offset[b + 1]], c.tags)
     dev = R.device
-    # the boundary-data and gradient pointers must be valid even for zero
-    # ghosts: one-element buffers
+    # zero ghosts: the boundary data and its gradient are empty tensors (null
+    # pointers, which the ABI accepts for an empty ghost set)
     fields = [torch.randn(R.n_cells, dtype=torch.float64, device=dev) for _ in range(3)]
     before = [f.clone() for f in fields]
-    bc = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in range(3)]
+    bc = [torch.zeros(0, dtype=torch.float64, device=dev) for _ in range(3)]
     kinds = cases[0]["bc"]
     for mode in ("level", "persistent"):
         R.reconstruct(fields, kinds, bc, mode=mode)
     out = R.forces([fields[0], fields[1]], fields[2], 0.01, I.DRAG_LIFT_DIRS_2D)
     gf = [torch.zeros(R.n_cells, dtype=torch.float64, device=dev) for _ in range(3)]
-    gb = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in range(3)]
+    gb = [torch.zeros(0, dtype=torch.float64, device=dev) for _ in range(3)]
     seed = torch.ones(R.B, 2, dtype=torch.float64, device=dev)
     R.adjoint(kinds, [0, 1], 2, 0.01, I.DRAG_LIFT_DIRS_2D, seed, gf, gb)
     R.sync_status()
