@@ -65,6 +65,18 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def measured_sm_mhz():
+    """Maximum SM clock recorded beside the measured peaks (2032 MHz on B300
+    when the file is absent)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("sm_max_mhz"):
+            return float(d["sm_max_mhz"])
+    return 2032.0
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -436,6 +448,58 @@ TRAFFIC_PER_LAUNCH = {
 }
 
 
+# FP64 flops per launch (DADD + DMUL + 2 x DFMA thread instructions, one ncu
+# capture on this workload: profiles/fp64_ops_batch_256.md) of the kernels
+# bound by the FP64 pipe.  "ghost_write" is the compaction + closest-point
+# pair; only the closest-point kernel does FP64 work.
+FP64_FLOPS_PER_LAUNCH = {
+    "ghost_write": 11_876_551, "tables": 10_419_154, "adj_seed": 9_582_272, "forces": 6_864_204,
+}
+# the FP64 pipe of one SM issues two double FMAs per clock (the counter's
+# sustained peak), i.e. 4 flops per SM per clock
+FP64_FLOPS_PER_SM_CLK = 4
+
+
+def fp64_peak_tflops(n_sm, sm_mhz):
+    return n_sm * FP64_FLOPS_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+
+
+def roofline_object(prof_ms, prof_n, algo, hbm_peak, hbm_peak_kind, n_sm, sm_mhz):
+    """The dominant kernel of the serial per-kernel profile against its bound:
+    the FP64 pipe (flops per launch / event-timed duration vs. the peak from
+    the SM count and clock) for the kernels in FP64_FLOPS_PER_LAUNCH, HBM
+    (algorithmic bytes per launch / duration vs. the measured copy bandwidth)
+    otherwise.  The HBM figures are kept for every kernel."""
+    top = max(prof_ms, key=prof_ms.get)
+    per_kernel = {}
+    for k, v in sorted(prof_ms.items(), key=lambda kv: -kv[1]):
+        gbs = algo[k] / (v * 1e-3) / 1e9 if k in algo else None
+        per_kernel[k] = {"ms": round(v, 5), "launches": prof_n[k],
+                         "algo_bytes": algo.get(k), "gbs": round(gbs, 1) if gbs else None}
+        if k in FP64_FLOPS_PER_LAUNCH:
+            per_kernel[k]["fp64_tflops"] = round(FP64_FLOPS_PER_LAUNCH[k] / (v / prof_n[k] * 1e-3) / 1e12, 4)
+    t_launch = prof_ms[top] / prof_n[top] * 1e-3      # seconds per launch
+    tb = algo[top] / prof_n[top]                      # bytes per launch
+    gbs = tb / t_launch / 1e9
+    hbm = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+           "peak_source": hbm_peak_kind, "algo_bytes_per_launch": tb}
+    fp64_peak = fp64_peak_tflops(n_sm, sm_mhz)
+    roof = {"kernel": top, "traffic": TRAFFIC_PER_LAUNCH.get(top)}
+    if top in FP64_FLOPS_PER_LAUNCH:
+        ach = FP64_FLOPS_PER_LAUNCH[top] / t_launch / 1e12
+        roof.update({"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": ach / fp64_peak, "flops_per_launch": FP64_FLOPS_PER_LAUNCH[top],
+                     "peak_source": "derived: %d SMs x %d FP64 flops per SM per clock x %.0f MHz"
+                                    % (n_sm, FP64_FLOPS_PER_SM_CLK, sm_mhz),
+                     "hbm": hbm})
+    else:
+        roof.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": gbs / hbm_peak, "peak_source": hbm_peak_kind, "algo_bytes_per_launch": tb})
+    roof["fp64_peak_tflops"] = fp64_peak
+    roof["per_kernel"] = per_kernel
+    roof["phases_ms"] = phase_sums(prof_ms)
+    return roof
+
 def unique_fluid_targets(R, info, dim=2):
     """Active (ghost, member) incidences whose member is a fluid cell, and the
     number of distinct such cells (host count from the ghost records: member
@@ -734,22 +798,12 @@ def main():
     rows = sum(c2["n_cells"] // geoms[b]["grid"]["n"][0] for b, c2 in enumerate(counts))
     ni = sum(c2["n_interface"] for c2 in counts)
     algo = algorithmic_bytes(n_cells, rows, ni, ng, diag["n_gsrc"], F, dim=2)
-    top = max(prof_ms, key=prof_ms.get)
-    per_kernel = {}
-    for k, v in sorted(prof_ms.items(), key=lambda kv: -kv[1]):
-        gbs = algo[k] / (v * 1e-3) / 1e9 if k in algo else None
-        per_kernel[k] = {"ms": round(v, 5), "launches": prof_n[k],
-                         "algo_bytes": algo.get(k), "gbs": round(gbs, 1) if gbs else None}
-    tb = algo[top] / prof_n[top]                      # bytes per launch
-    achieved = tb / (prof_ms[top] / prof_n[top] * 1e-3) / 1e9
-    roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(top),
-            "peak_source": peak_kind, "algo_bytes_per_launch": tb,
-            "timing": "CUDA events recorded as nodes of a captured graph of the step without the two-stream overlap, mean of 5 replays, L2 flushed",
-            "step_algo_bytes": sum(algo.values()),
-            "step_frac": sum(algo.values()) / (ms_step * 1e-3) / 1e9 / peak,
-            "per_kernel": per_kernel,
-            "phases_ms": phase_sums(prof_ms)}
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = roofline_object(prof_ms, prof_n, algo, peak, peak_kind, n_sm, measured_sm_mhz())
+    roof.update({
+        "timing": "CUDA events recorded as nodes of a captured graph of the step without the two-stream overlap, mean of 5 replays, L2 flushed",
+        "step_algo_bytes": sum(algo.values()),
+        "step_frac": sum(algo.values()) / (ms_step * 1e-3) / 1e9 / peak})
 
     baseline = None
     if rank == 0 and not args.no_baseline and not args.lite:

@@ -58,3 +58,45 @@ def test_algorithmic_bytes_grow_with_the_workload():
         assert b[k] == pytest.approx(2 * a[k]), k
     # the tag stream is one byte per cell plus the row runs
     assert a["rows"] == 1_000_000 + 8 * 2000
+
+
+def _profile(top_ms):
+    prof_ms = {"ghost_write": 0.0438, "fill_chain": 0.0418, "rows": 0.0400, "tables": 0.0235, "forces": 0.0377,
+               "scan": 0.0270}
+    prof_ms.update(top_ms)
+    prof_n = {k: (3 if k == "scan" else 1) for k in prof_ms}
+    algo = bench.algorithmic_bytes(48_250_166, 126_000, 171_700, 85_556, 160_000, 3)
+    return prof_ms, prof_n, algo
+
+
+def test_fp64_peak_from_unit_counts_and_clock():
+    # 148 SMs x 2 double FMAs (4 flops) per SM per clock x 2032 MHz
+    assert bench.fp64_peak_tflops(148, 2032.0) == pytest.approx(1.202944)
+
+
+def test_roofline_of_an_fp64_bound_dominant_kernel():
+    prof_ms, prof_n, algo = _profile({})
+    r = bench.roofline_object(prof_ms, prof_n, algo, 6495.6, "measured", 148, 2032.0)
+    assert r["kernel"] == "ghost_write" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    ach = bench.FP64_FLOPS_PER_LAUNCH["ghost_write"] / 0.0438e-3 / 1e12
+    assert r["achieved"] == pytest.approx(ach)
+    assert r["frac"] == pytest.approx(ach / bench.fp64_peak_tflops(148, 2032.0))
+    assert r["traffic"] == bench.TRAFFIC_PER_LAUNCH["ghost_write"]
+    assert r["hbm"]["unit"] == "GB/s" and r["hbm"]["frac"] == pytest.approx(
+        algo["ghost_write"] / 0.0438e-3 / 1e9 / 6495.6)
+    assert r["per_kernel"]["tables"]["fp64_tflops"] > 0
+    assert "fp64_tflops" not in r["per_kernel"]["fill_chain"]
+    assert set(r["phases_ms"]) >= {"classify", "levels", "fill", "forces"}
+
+
+def test_roofline_of_a_memory_bound_dominant_kernel():
+    prof_ms, prof_n, algo = _profile({"fill_chain": 0.09, "scan": 0.03})
+    r = bench.roofline_object(prof_ms, prof_n, algo, 6495.6, "measured", 148, 2032.0)
+    assert r["kernel"] == "fill_chain" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(algo["fill_chain"] / 0.09e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6495.6)
+    # per-launch figures divide by the launch count
+    prof_ms, prof_n, algo = _profile({"scan": 0.3})
+    r = bench.roofline_object(prof_ms, prof_n, algo, 6495.6, "measured", 148, 2032.0)
+    assert r["kernel"] == "scan" and r["algo_bytes_per_launch"] == pytest.approx(algo["scan"] / 3)
+    assert r["achieved"] == pytest.approx(algo["scan"] / 3 / (0.1e-3) / 1e9)
