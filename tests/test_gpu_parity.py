@@ -199,6 +199,32 @@ def test_stencil_out_of_grid_is_reported():
     assert eo.value.code == "ESTENCIL_OOB"
 
 
+
+def test_solid_stencil_member_is_reported():
+    # host-side fault injection: after classification a fluid stencil member
+    # of one ghost is overwritten with the solid tag in the caller's tag
+    # buffer; building the levels reports EBR_ESTENCIL_SOLID (and the oracle,
+    # given the same tags, raises ESTENCIL_SOLID)
+    from paper_2609_10165_b300.api import Reconstructor
+    from paper_2609_10165_b300._lib import EBRError
+    case = _small_cases()[0]
+    c = O.classify(case["grid"], case["body"], "HGC")
+    lev = O.build_levels(c)
+    g = int(lev.order[0])
+    fluid = [int(m) for m in lev.midx[g] if c.tags[int(m)] == 0]
+    assert fluid
+    R = Reconstructor(case["grid"], case["body"], "HGC")
+    R.sync_status()
+    R.tags[fluid[0]] = 1
+    with pytest.raises(EBRError) as ei:
+        R.build_levels()
+        R.sync_status()
+    assert ei.value.name == "EBR_ESTENCIL_SOLID"
+    c.tags[fluid[0]] = 1
+    with pytest.raises(O.EBRError) as eo:
+        O.build_levels(c)
+    assert eo.value.code == "ESTENCIL_SOLID"
+
 def test_invalid_arguments():
     from paper_2609_10165_b300.api import Reconstructor
     from paper_2609_10165_b300._lib import EBRError
