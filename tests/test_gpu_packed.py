@@ -107,7 +107,7 @@ def _term_bound(c, mats, xa, ba):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("F", [1, 5, 40, 130])
+@pytest.mark.parametrize("F", [1, 5, 40, 130, 1024])   # 1024: the ABI maximum
 def test_packed_fill_matches_oracle(dtype, F):
     R, info, x, b = _setup(MIXED_2D, "HGC", F, dtype, 7 + F)
     compare_structure(R_run(R, info), MIXED_2D, "HGC")

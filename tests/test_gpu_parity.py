@@ -90,6 +90,23 @@ def test_small_cases_all_bodies(placement, mode, dtype):
         _check_values(run, [g], placement, dtype)
 
 
+
+@pytest.mark.parametrize("mode", ["level", "persistent"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_eight_fields_the_abi_maximum(mode, dtype):
+    # the per-field-array calls take at most 8 fields: all 8, with mixed
+    # kinds, on the 2D small cases
+    geoms = []
+    for k, case in enumerate(c for c in _small_cases() if c["grid"]["dim"] == 2):
+        g = dict(case)
+        fs = [I.FourierField(2, 4, case["grid"]["lo"], case["grid"]["hi"], 600 + 10 * k + f) for f in range(8)]
+        g.update({"fields": fs, "bc": [I.NEUMANN if f % 3 == 2 else I.DIRICHLET for f in range(8)],
+                  "roles": {"p": 2, "vel": [0, 1]}, "mu": 0.01})
+        geoms.append(g)
+    run = DeviceRun(geoms, "HGC", mode=mode, dtype=dtype)
+    compare_structure(run, geoms, "HGC")
+    _check_values(run, geoms, "HGC", dtype)
+
 def test_small_cases_batched_together():
     # the five small geometries in one 2D/3D-mixed set is not allowed for
     # forces, but classification / levels / fill are per geometry
