@@ -90,7 +90,6 @@ def test_small_cases_all_bodies(placement, mode, dtype):
         _check_values(run, [g], placement, dtype)
 
 
-
 @pytest.mark.parametrize("mode", ["level", "persistent"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_eight_fields_the_abi_maximum(mode, dtype):
@@ -106,6 +105,7 @@ def test_eight_fields_the_abi_maximum(mode, dtype):
     run = DeviceRun(geoms, "HGC", mode=mode, dtype=dtype)
     compare_structure(run, geoms, "HGC")
     _check_values(run, geoms, "HGC", dtype)
+
 
 def test_small_cases_batched_together():
     # the five small geometries in one 2D/3D-mixed set is not allowed for
@@ -241,6 +241,7 @@ def test_solid_stencil_member_is_reported():
     with pytest.raises(O.EBRError) as eo:
         O.build_levels(c)
     assert eo.value.code == "ESTENCIL_SOLID"
+
 
 def test_invalid_arguments():
     from paper_2609_10165_b300.api import Reconstructor
