@@ -59,7 +59,8 @@ typedef enum {
   EBR_ESTENCIL_SOLID = -6,  /* a stencil member is a solid (tag 1) cell: value undefined  */
   EBR_ETIMEOUT = -7,        /* a bounded device-side wait gave up                          */
   EBR_ENONFINITE = -8,      /* non-finite value met where the path needs a finite one     */
-  EBR_ESHAPE = -9           /* a re-run produced other counts than the planned geometry   */
+  EBR_ESHAPE = -9           /* the geometry differs from the plan (counts of a re-run, or
+                               ghost tags in the tag buffer that the plan does not hold)  */
 } ebr_status;
 
 typedef enum { EBR_HGC = 0, EBR_CGC = 1, EBR_CGC_ES = 2 } ebr_placement;
@@ -159,7 +160,11 @@ ebr_status ebr_counts(const void* ctx, ebr_geom_counts* h_counts);
  * of its dependencies, 1 without any.  Ghosts are then stored in the canonical
  * order (geometry, level, linear index).  Also validates every stencil member
  * (EBR_ESTENCIL_OOB / EBR_ESTENCIL_SOLID) and detects cycles (EBR_ECYCLE),
- * and builds the transposed incidence lists used by the adjoint.
+ * and builds the transposed incidence lists used by the adjoint.  The tags
+ * are read from the buffer last given to ebr_plan / ebr_classify; a member
+ * tagged +-2 there that is not a ghost of the plan (the buffer was edited)
+ * adds no dependency and sets EBR_ESHAPE -- every position the kernels look
+ * up through a ghost tag is checked against the plan's ghost records.
  * Device-side failures are reported through the status word.  After the first
  * call the incidence lists are built on a second, library-owned stream that
  * forks from and joins back into `stream` by events inside this call, so the
@@ -379,17 +384,24 @@ int32_t ebr_profile_read(void* ctx, int32_t max_entries, char* h_names, double* 
  *                  (solid, centre in the closed body) -- the tags before
  *                  ghost placement; same layout as the other calls.
  *   d_n_interface  caller-owned device int64, receives the number of cells
- *                  with a face neighbour on the other side of the boundary.
+ *                  with a face neighbour on the other side of the boundary,
+ *                  or, when the device recorded a failure (a row whose solid
+ *                  run the row kernel could not determine, left all fluid),
+ *                  that negative ebr_status instead of the count.  The host
+ *                  checks on the body make that failure unreachable for the
+ *                  bodies of this header; the value is the only channel by
+ *                  which a device-side failure of this call is reported.
  * The per-row solid runs needed between the two kernels live in a fixed
  * device array inside the library (EBR_STATIC_MAX_ROWS rows, 2 MiB, held by
  * every device that loads the library until the process exits).  Grids with
  * more rows are rejected with EBR_EINVAL before any GPU work, as are invalid
- * grids or bodies (no message: there is no context).  The first call on a
- * device looks the array's device address up (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the array and it
- * keeps the last call's contents: the call clears what must start at zero
- * itself, and calls that overlap on the GPU (other streams, other threads)
- * race on it.  Asynchronous on the stream. */
+ * grids or bodies (no message: there is no context).  Every call looks the
+ * array's device address up in the current context (cudaGetSymbolAddress);
+ * the first call in a context may load the library's device code, so make
+ * it before any stream capture.  All calls share the array and it keeps the
+ * last call's contents: the call clears what must start at zero itself, and
+ * calls that overlap on the GPU (other streams, other threads) race on it.
+ * Asynchronous on the stream. */
 ebr_status ebr_classify_cells_static(const ebr_grid* h_grid, const ebr_body* h_body,
                                      int8_t* d_tags, int64_t* d_n_interface, ebr_stream stream);
 

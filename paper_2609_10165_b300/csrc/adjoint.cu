@@ -308,7 +308,7 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
 #pragma unroll
   for (int f = 0; f < 8; ++f) acc[f] = T(0);
   bool first = true, owner = false;
-  probe_sources(g, tijk, tg, pc, g_meta, rmax, [&](int q, int slot) {
+  probe_sources(g, tijk, tg, pc, g_cell, g_meta, rmax, [&](int q, int slot) {
     if (first) {
       first = false;
       owner = (q == p && slot == k + 1);
@@ -376,7 +376,7 @@ __global__ void k_adj_fprobe(int ng, const Geom* __restrict__ G, const int* __re
     if (in_grid(g, tijk) && tg[cell_lin(g, tijk)] == 0) {
       bool first = true, owner = false;
       int* out = fsrc + (size_t)i * cap;
-      probe_sources(g, tijk, tg, pc, g_meta, 1, [&](int q, int slot) {
+      probe_sources(g, tijk, tg, pc, g_cell, g_meta, 1, [&](int q, int slot) {
         if (first) {
           first = false;
           owner = (q == p && slot == k + 1);

@@ -510,7 +510,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, sg);
   prof_end(c, sg);
   c->launches += 5;   // reorder, tables, source counts, scan (2)
-  CKL();
+  if (planning) CKL();   // outside planning: checked after the join below
   if (planning) {
     CK(cudaMemcpyAsync(&c->n_gsrc, c->gsrc_ptr + ng, sizeof(int), cudaMemcpyDeviceToHost, s));
     std::vector<int> hp(ng + 1);
@@ -531,11 +531,11 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
               c->gsrc_ptr, c->gsrc, 1, sg, c->tb[TU_GSRC]);
   prof_end(c, sg);
   c->launches += 1;
-  CKL();
   if (!planning) {
     CK(cudaEventRecord(c->ev_join, c->side));
     CK(cudaStreamWaitEvent(s, c->ev_join, 0));
   }
+  CKL();
   if (planning) {
     // force chunks (<= 256 ghosts, never straddling geometries)
     std::vector<int4> ch;
@@ -928,9 +928,19 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
       return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: null gradient %d", f);
     if (h_bc_kind[f] != 0 && h_bc_kind[f] != 1) return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: bad bc kind");
   }
+  if (mode != EBR_MODE_PERSISTENT && mode != EBR_MODE_LEVEL_LAUNCH)
+    return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: bad mode %d", mode);
   cudaStream_t s = S(stream);
   int kinds[8];
   for (int f = 0; f < n_fields; ++f) kinds[f] = h_bc_kind[f];
+  // everything that can fail runs before the fork below, so that an error
+  // return never leaves the side stream unjoined (a stream capture would be
+  // invalidated by the dangling branch)
+  ChainPlan* cp = nullptr;
+  if (mode == EBR_MODE_PERSISTENT) {
+    ebr_status st = chain_plan(c, 1, dtype, n_fields, &cp);
+    if (st) return st;
+  }
   // at reach 1 the fluid targets' probe (which needs no lambda) runs on the
   // second stream beside the seed and chain kernels; the pull joins it
   const int kmax = stencil_k(dim);
@@ -954,9 +964,6 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
   c->launches += 1;
   std::vector<int> level_geoms;
   if (mode == EBR_MODE_PERSISTENT) {
-    ChainPlan* cp = nullptr;
-    ebr_status st = chain_plan(c, 1, dtype, n_fields, &cp);
-    if (st) return st;
     if (cp->n_list > 0) {
       prof_begin(c, s, "adj_part");
       launch_adj_part(dtype, n_fields, c->ng, c->gsrc_ptr, c->gsrc, c->g_meta, c->wtab, c->sv, c->apart,
@@ -969,10 +976,8 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
       c->launches += 2;
     }
     level_geoms = cp->fallback;
-  } else if (mode == EBR_MODE_LEVEL_LAUNCH) {
-    for (int b = 0; b < c->B; ++b) level_geoms.push_back(b);
   } else {
-    return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: bad mode %d", mode);
+    for (int b = 0; b < c->B; ++b) level_geoms.push_back(b);
   }
   for (int b : level_geoms) {
     const Geom& g = c->hG[b];

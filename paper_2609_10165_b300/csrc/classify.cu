@@ -882,20 +882,14 @@ void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const
 // device that loads the library until the process exits).  Every call shares
 // that array: calls that overlap on the GPU race on it.
 // ===========================================================================
-#include <mutex>
-
 #include "../../include/ebr.h"
 
 namespace {
 
 constexpr int kStaticMaxRows = EBR_STATIC_MAX_ROWS;
-constexpr int kStaticMaxDevices = 64;
 
 // [0, 2 * rows): int2 row runs; then the status word and the fallback counter
 static __device__ __align__(256) int g_static_scratch[2 * kStaticMaxRows + 64];
-
-std::mutex g_static_mutex;
-int* g_static_addr[kStaticMaxDevices] = {};
 
 __global__ void __launch_bounds__(256) k_rows_static(ebr::Geom g, int2* __restrict__ runs,
                                                      int8_t* __restrict__ tags, int* status,
@@ -950,6 +944,14 @@ __global__ void __launch_bounds__(256) k_rows_static(ebr::Geom g, int2* __restri
       }
     }
   }
+}
+
+// After the count: a device-side failure recorded by the row kernel (a row
+// whose solid run could not be determined leaves that row all fluid) replaces
+// the count by the negative status, so the caller sees it.
+__global__ void k_static_status(const int* __restrict__ status, long long* __restrict__ count) {
+  const int st = *status;
+  if (st != 0) *count = st;
 }
 
 // interface cells per row from the runs (same interval algebra as k_iface),
@@ -1033,20 +1035,18 @@ extern "C" ebr_status ebr_classify_cells_static(const ebr_grid* h_grid, const eb
   g.row_off = 0;
   g.n_rows = (int)rows;
 
-  // device address of the fixed scratch, looked up once per device (the
-  // array's name is only a host-side stand-in)
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return EBR_ECUDA;
-  int* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_addr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) return EBR_ECUDA;
-      g_static_addr[dev] = static_cast<int*>(p);
-    }
-    base = g_static_addr[dev];
+  // Device address of the fixed scratch in the current context (the array's
+  // name is only a host-side stand-in).  Looked up on every call: the address
+  // belongs to the module as loaded in the current context, so a cached value
+  // would dangle after a device reset or name another context's copy.  Once
+  // the module is loaded in the context this is a table lookup; the first call
+  // in a context may load it, so it should come before any stream capture.
+  void* sym = nullptr;
+  if (cudaGetSymbolAddress(&sym, g_static_scratch) != cudaSuccess) {
+    cudaGetLastError();
+    return EBR_ECUDA;
   }
+  int* base = static_cast<int*>(sym);
   int2* runs = reinterpret_cast<int2*>(base);
   int* status = base + 2 * kStaticMaxRows;
   int* stats = status + 1;
@@ -1057,6 +1057,7 @@ extern "C" ebr_status ebr_classify_cells_static(const ebr_grid* h_grid, const eb
   k_rows_static<<<(warps + 7) / 8, 256, 0, s>>>(g, runs, d_tags, status, stats);
   k_iface_count_static<<<(int)((rows + 127) / 128), 128, 0, s>>>(
       g, runs, reinterpret_cast<unsigned long long*>(d_n_interface));
+  k_static_status<<<1, 1, 0, s>>>(status, reinterpret_cast<long long*>(d_n_interface));
   if (cudaGetLastError() != cudaSuccess) return EBR_ECUDA;
   return EBR_OK;
 }

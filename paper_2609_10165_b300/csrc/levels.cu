@@ -20,7 +20,11 @@ void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, cons
 }
 
 // Stencil members: validate (inside the grid, not tag 1), active mask
-// (n_i != 0 along every offset axis), dependencies on ghost members.
+// (n_i != 0 along every offset axis), dependencies on ghost members.  A
+// member tagged +-2 in the caller's tag buffer is a dependency only when it
+// is a ghost of this plan (ghost_slot_of); any other +-2 tag (the buffer was
+// edited after planning) sets EBR_ESHAPE and adds no edge, so no position
+// read from pos_of_cell is used unchecked.
 __global__ void k_deps(const Geom* __restrict__ G, int ng, const int* __restrict__ gs_cell,
                        const int* __restrict__ gs_geo, uint32_t* __restrict__ gs_meta,
                        const double* __restrict__ gs_n, const int8_t* __restrict__ tags,
@@ -52,8 +56,9 @@ __global__ void k_deps(const Geom* __restrict__ G, int ng, const int* __restrict
         if (t == 1) set_status(status, S_ESTENCIL_SOLID);
         if (act) active |= 1u << k;
         if (act && (t == 2 || t == -2)) {
-          d = pos_of_cell[mc];
-          depm |= 1u << k;
+          d = ghost_slot_of(g, cell_lin(g, mijk), pos_of_cell + g.cell_off, gs_cell);
+          if (d >= 0) depm |= 1u << k;
+          else set_status(status, S_ESHAPE);
         }
       }
     }
@@ -116,8 +121,12 @@ __global__ void __launch_bounds__(LV_T, 2) k_levels(const Geom* __restrict__ G, 
       lvl[s] = 0;
       if (fast)
         for (int k = 0; k < K; ++k) {
+          // k_deps only writes positions of this geometry's ghosts; the range
+          // check keeps every shared-memory index in [0, n) regardless
           int d = dep[(size_t)k * ng_total + g0 + s];
-          dl[(size_t)k * n + s] = d >= 0 ? d - g0 : -1;
+          const bool in = d >= g0 && d < g0 + n;
+          if (d >= 0 && !in) set_status(status, S_ESHAPE);
+          dl[(size_t)k * n + s] = in ? d - g0 : -1;
         }
     }
     if (threadIdx.x == 0) {
@@ -236,6 +245,7 @@ __global__ void __launch_bounds__(LV_T, 2) k_levels(const Geom* __restrict__ G, 
           bool ok = true;
           for (int k = 0; k < K && ok; ++k) {
             int d = fast ? dl[(size_t)k * n + s] : dep[(size_t)k * ng_total + g0 + s] - g0;
+            if (d >= n) d = -1;              // outside the geometry (never written by k_deps)
             if (d >= 0) {
               int lv = ((volatile int*)lvl)[d];
               if (lv == 0 || lv >= L) ok = false;
@@ -562,12 +572,12 @@ __global__ void k_gsrc(const Geom* __restrict__ G, int ng, const int* __restrict
   const int* pc = pos_of_cell + g.cell_off;
   if (!write) {
     int cnt = 1;
-    probe_sources(g, tijk, tg, pc, g_meta, R, [&](int, int) { ++cnt; return true; });
+    probe_sources(g, tijk, tg, pc, g_cell, g_meta, R, [&](int, int) { ++cnt; return true; });
     out[p] = cnt;
   } else {
     int o = ptr[p];
     out[o++] = (p << 3) | 0;
-    probe_sources(g, tijk, tg, pc, g_meta, R, [&](int q, int slot) { out[o++] = (q << 3) | slot; return true; });
+    probe_sources(g, tijk, tg, pc, g_cell, g_meta, R, [&](int q, int slot) { out[o++] = (q << 3) | slot; return true; });
   }
 }
 

@@ -709,7 +709,7 @@ __global__ void k_ftgt(int ng, int kmax, const Geom* __restrict__ G, const int* 
   if (!in_grid(g, tijk) || tg[cell_lin(g, tijk)] != 0) return;
   bool first = true, owner = false;
   int n = 0, o = write ? epos[i] : 0;
-  probe_sources(g, tijk, tg, pc, g_meta, R, [&](int q, int slot) {
+  probe_sources(g, tijk, tg, pc, g_cell, g_meta, R, [&](int q, int slot) {
     if (!(meta_active(g_meta[q]) >> (slot - 1) & 1u)) return true;
     if (first) {
       first = false;

@@ -11,13 +11,17 @@ from paper_2609_10165_b300 import inputs as I
 
 
 def batch_structure(args):
-    """(gi, tie-free, tags, canonical ghost cells, their levels, their r) of
+    """(gi, tie-free, tags, canonical ghost cells, their levels, their r,
+    their psi, normals and boundary points S, the smallest cell width) of
     geometry gi of the n_geoms-geometry batch, placed with `placement`."""
     n_geoms, gi, placement = args
     g = I.batch(n_geoms)[gi]
     c = O.classify(g["grid"], g["body"], placement)
     lev = O.build_levels(c)
-    return gi, c.ties == [], c.tags, c.idx[lev.order], lev.level[lev.order], c.r[lev.order]
+    X = c.grid.centre(c.grid.unlin(c.idx))
+    S = X + c.psi[:, None] * c.n
+    return (gi, c.ties == [], c.tags, c.idx[lev.order], lev.level[lev.order], c.r[lev.order],
+            c.psi[lev.order], c.n[lev.order], S[lev.order], min(c.grid.h))
 
 
 def start_pool(n_tasks):

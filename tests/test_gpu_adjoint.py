@@ -9,7 +9,7 @@ import torch
 
 import oracle as O
 from paper_2609_10165_b300 import inputs as I
-from tests.parity import DeviceRun
+from tests.parity import DeviceRun, compare_structure, note_worst
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +63,28 @@ def test_adjoint_matches_oracle(kind, placement, mode):
             sc = max(np.abs(gx[f]).max(), np.abs(gbo[f]).max(), 1e-300)
             assert np.max(np.abs(gf[f] - gx[f])) <= rtol * sc, (dtype, f, np.max(np.abs(gf[f] - gx[f])) / sc)
             assert np.max(np.abs(gb[f] - gbo[f])) <= rtol * sc, (dtype, f)
+
+
+@pytest.mark.parametrize("name", ["cylinder_1024", "sphere_256"])
+def test_adjoint_full_size_matches_oracle(name):
+    # the adjoint configurations at their full sizes (1024^2 cylinder, 256^3
+    # sphere), FP64 and FP32 fields with FP64 coefficients, against the
+    # oracle's explicit-matrix gradient
+    w = I.WORKLOADS[name]()
+    run = DeviceRun([w], "HGC")
+    res = compare_structure(run, [w], "HGC")
+    c, lev = res[0]
+    d = w["grid"]["dim"]
+    dirs = I.DRAG_LIFT_DIRS_2D if d == 2 else I.DRAG_LIFT_DIRS_3D
+    seed = (1.0, 0.5)
+    gx, gbo = O.adjoint_gradient(c, lev, w["bc"], w["roles"]["p"], w["roles"]["vel"], w["mu"], dirs, seed)
+    for dtype, rtol in ((torch.float64, 1e-11), (torch.float32, 2e-5)):
+        gf, gb = _gpu_grad(run, w, seed, dtype, "persistent")
+        for f in range(len(w["fields"])):
+            sc = max(np.abs(gx[f]).max(), np.abs(gbo[f]).max(), 1e-300)
+            e = max(np.max(np.abs(gf[f] - gx[f])), np.max(np.abs(gb[f] - gbo[f]))) / sc
+            assert e <= rtol, (name, dtype, f, e)
+            note_worst("adjoint %s %s" % ("FP64" if dtype == torch.float64 else "FP32", name), e / rtol, e)
 
 
 def _J_gpu(run, w, arrays, bcs, seed):

@@ -12,7 +12,7 @@ import torch
 import oracle as O
 from paper_2609_10165_b300 import inputs as I
 from paper_2609_10165_b300.api import Reconstructor
-from tests.parity import DeviceRun, compare_structure
+from tests.parity import DeviceRun, compare_structure, oracle_bcs
 from tests.test_gpu_parity import _check_values, _small_cases, _with_fields
 
 pytestmark = pytest.mark.gpu
@@ -69,7 +69,7 @@ def test_empty_geometries_forces_and_adjoint():
         sel = info["geom"] == b
         c = O.classify(g["grid"], g["body"], "HGC")
         lev = O.build_levels(c)
-        filled = O.fill(c, lev, [a[o0:o1] for a in arrays], g["bc"], [x[sel] for x in bcs])
+        filled = O.fill(c, lev, [a[o0:o1] for a in arrays], g["bc"], oracle_bcs(g, c, lev))
         ref, scale = O.forces(c, lev, filled[p], [filled[i] for i in vel], mu, dirs)
         assert np.all(np.abs(out[b] - ref) <= 1e-12 * scale + 1e-300), (b, out[b], ref)
         gx, gbo = O.adjoint_gradient(c, lev, g["bc"], p, vel, mu, dirs, (0.7, -1.3))

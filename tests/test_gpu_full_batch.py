@@ -20,6 +20,7 @@ import torch
 import oracle as O
 from paper_2609_10165_b300 import inputs as I
 from tests.oracle_pool import batch_structure, start_pool
+from tests.parity import GEOM_TOL, NORMAL_TOL, oracle_bcs
 
 pytestmark = pytest.mark.gpu
 
@@ -91,7 +92,7 @@ def _bench_step_outputs(geoms, dev):
 
 def _check_structure(dev_out, structure):
     tags, info, off = dev_out["tags"], dev_out["info"], dev_out["offset"]
-    for gi, tie_free, c_tags, cells, levels, r in structure:
+    for gi, tie_free, c_tags, cells, levels, r, psi, nrm, S, h in structure:
         assert tie_free, gi
         o0, o1 = off[gi], off[gi + 1]
         assert np.array_equal(tags[o0:o1], c_tags), (gi, int(np.sum(tags[o0:o1] != c_tags)))
@@ -99,6 +100,10 @@ def _check_structure(dev_out, structure):
         assert np.array_equal(info["cell"][sel], cells), gi
         assert np.array_equal(info["level"][sel], levels), gi
         assert np.array_equal(info["r"][sel][:, :2], r), gi
+        # the GPU's closest points against the oracle's own
+        assert np.max(np.abs(info["psi"][sel] - psi), initial=0.0) <= GEOM_TOL * h, gi
+        assert np.max(np.abs(info["S"][sel][:, :2] - S), initial=0.0) <= GEOM_TOL * h, gi
+        assert np.max(np.abs(info["normal"][sel][:, :2] - nrm), initial=0.0) <= NORMAL_TOL, gi
 
 
 def _check_properties(dev_out, host_fields, n_geoms):
@@ -128,12 +133,12 @@ def _check_sample(dev_out, geoms, host_fields, host_bcs, sample):
         g = geoms[gi]
         o0, o1 = off[gi], off[gi + 1]
         sel = info["geom"] == gi
-        # the oracle on exactly the uploaded inputs: FP32 fields and FP32 boundary data
+        # the oracle on the uploaded FP32 field values, with FP32-rounded
+        # boundary data evaluated at its own S
         arrays = [np.asarray(a[o0:o1], dtype=np.float64) for a in host_fields]
-        bcs = [b[sel].astype(np.float32).astype(np.float64) for b in host_bcs]
         c = O.classify(g["grid"], g["body"], "HGC")
         lev = O.build_levels(c)
-        filled = O.fill(c, lev, arrays, g["bc"], bcs)
+        filled = O.fill(c, lev, arrays, g["bc"], oracle_bcs(g, c, lev, f32=True))
         cells = c.idx[lev.order]
         for f in range(3):
             got = dev_out["fields"][f][o0:o1][cells]

@@ -11,7 +11,7 @@ import torch
 
 import oracle as O
 from paper_2609_10165_b300 import inputs as I
-from tests.parity import DeviceRun, oracle_run, term_magnitude, compare_structure, U32
+from tests.parity import DeviceRun, oracle_bcs, term_magnitude, compare_structure, note_worst, U32
 
 pytestmark = pytest.mark.gpu
 
@@ -37,24 +37,24 @@ def _with_fields(case, seed):
 
 
 def _check_values(run, geoms, placement, dtype):
+    f32 = dtype == torch.float32
     arrays = run.field_arrays()
-    if dtype == torch.float32:
+    if f32:
         arrays = [a.astype(np.float32).astype(np.float64) for a in arrays]
+    # the GPU's boundary data at its own S and normals
     bcs = run.bc_arrays()
-    if dtype == torch.float32:
+    if f32:
         bcs = [b.astype(np.float32).astype(np.float64) for b in bcs]
     ft, _ = run.fill(arrays, bcs)
     got = [t.double().cpu().numpy() for t in ft]
-    info = run.info
     worst = 0.0
     for b, g in enumerate(geoms):
         o0, o1 = run.R.cell_offset[b], run.R.cell_offset[b + 1]
-        sel = info["geom"] == b
-        # oracle on the same inputs, with the GPU's boundary data (same order)
+        # the oracle on the same field values, with boundary data at its own S
         c = O.classify(g["grid"], g["body"], placement)
         lev = O.build_levels(c)
         loc = [a[o0:o1] for a in arrays]
-        bl = [bb[sel] for bb in bcs]
+        bl = oracle_bcs(g, c, lev, f32)
         out = O.fill(c, lev, loc, g["bc"], bl)
         T = term_magnitude(c, lev, loc, bl, g["bc"])
         cells = c.idx[lev.order]
@@ -71,7 +71,11 @@ def _check_values(run, geoms, placement, dtype):
             bad = diff > tol
             assert not np.any(bad), (b, f, int(bad.sum()), float(diff.max()), float(tol[np.argmax(diff - tol)]))
             if diff.size:
-                worst = max(worst, float(np.max(diff / np.maximum(tol, 1e-300))))
+                r = float(np.max(diff / np.maximum(tol, 1e-300)))
+                worst = max(worst, r)
+                key = "values %s %s" % ("FP32" if f32 else "FP64", placement)
+                rel = float(diff.max() / (np.abs(loc[f]).max() if f32 else max(T[f].max(), 1e-300)))
+                note_worst(key, r, rel)
             # non-ghost cells untouched
             mask = np.ones(o1 - o0, bool)
             mask[cells] = False
@@ -142,13 +146,16 @@ def _forces_case(w, placement, dtype, mode="persistent"):
     dirs = I.DRAG_LIFT_DIRS_2D if d == 2 else I.DRAG_LIFT_DIRS_3D
     vel = [None if i is None else ft[i] for i in w["roles"]["vel"]]
     out = run.R.forces(vel, ft[w["roles"]["p"]], w["mu"], dirs).cpu().numpy()[0]
-    # oracle on the GPU-filled values?  No: on its own fill of the same inputs
+    # the oracle on its own fill of the same field values, with boundary data
+    # at its own S
     c = O.classify(w["grid"], w["body"], placement)
     lev = O.build_levels(c)
-    sel = run.info["geom"] == 0
-    filled = O.fill(c, lev, arrays, w["bc"], [b[sel] for b in bcs])
+    filled = O.fill(c, lev, arrays, w["bc"], oracle_bcs(w, c, lev, dtype == torch.float32))
     vel_o = [None if i is None else filled[i] for i in w["roles"]["vel"]]
     ref, scale = O.forces(c, lev, filled[w["roles"]["p"]], vel_o, w["mu"], dirs)
+    key = "forces %s %s" % ("FP32" if dtype == torch.float32 else "FP64", placement)
+    note_worst(key, float(np.max(np.abs(out - ref) / np.maximum(scale, 1e-300))),
+               float(np.max(np.abs(out - ref) / np.maximum(scale, 1e-300))))
     return out, ref, scale
 
 
@@ -168,12 +175,23 @@ def test_airfoil_2048(placement):
     _check_values(run, [w], placement, torch.float32)
 
 
-def test_airfoil_forces():
+# FP32 forces: the GPU sums the traction terms in double from FP32 field
+# values; the error comes from the FP32 ghost values (within 1e-5 of the field
+# maximum, measured below 1e-6) divided by the stencil spacing in the
+# boundary gradients.  1e-4 of the terms' magnitude for HGC and CGC_ES, whose
+# weights are bounded by the alpha <= 1/2 placement; CGC's weights grow like
+# 1/(1 - alpha) (about 12 at alpha = 0.92), so it is allowed 1e-3.
+F32_FORCE_TOL = {"HGC": 1e-4, "CGC_ES": 1e-4, "CGC": 1e-3}
+
+
+@pytest.mark.parametrize("placement", ["HGC", "CGC", "CGC_ES"])
+def test_airfoil_forces(placement):
+    # drag and lift of the 2048x1024 airfoil under each placement
     w = I.airfoil_2048()
-    out, ref, scale = _forces_case(w, "HGC", torch.float64)
+    out, ref, scale = _forces_case(w, placement, torch.float64)
     assert np.all(np.abs(out - ref) <= 1e-12 * scale), (out, ref, scale)
-    out, ref, scale = _forces_case(w, "HGC", torch.float32)
-    assert np.all(np.abs(out - ref) <= 1e-4 * scale), (out, ref, scale)
+    out, ref, scale = _forces_case(w, placement, torch.float32)
+    assert np.all(np.abs(out - ref) <= F32_FORCE_TOL[placement] * scale), (out, ref, scale)
 
 
 def test_batch_subset_both_modes():
@@ -261,12 +279,16 @@ def test_sphere_fp32(name):
     _check_values(run, [w], "HGC", torch.float32)
 
 
-def test_sphere_256_forces():
-    w = I.WORKLOADS["sphere_256"]()
-    out, ref, scale = _forces_case(w, "HGC", torch.float64)
-    assert np.all(np.abs(out - ref) <= 1e-12 * scale), (out, ref, scale)
+@pytest.mark.parametrize("name", ["sphere_256", "sphere_512"])
+def test_sphere_forces(name):
+    # boundary pressure and shear forces of the sphere; sphere_512 is the
+    # 512^3 configuration (FP32 fields, FP64 coefficients) at full size
+    w = I.WORKLOADS[name]()
+    if name == "sphere_256":
+        out, ref, scale = _forces_case(w, "HGC", torch.float64)
+        assert np.all(np.abs(out - ref) <= 1e-12 * scale), (out, ref, scale)
     out, ref, scale = _forces_case(w, "HGC", torch.float32)
-    assert np.all(np.abs(out - ref) <= 1e-4 * scale), (out, ref, scale)
+    assert np.all(np.abs(out - ref) <= F32_FORCE_TOL["HGC"] * scale), (out, ref, scale)
 
 
 @pytest.mark.parametrize("mode", ["level", "persistent"])

@@ -4,8 +4,12 @@ It serves callers that cannot let the library allocate device memory (their
 own memory pool or budget, or no cudaMalloc while other work runs).  It is
 called here through the C ABI on buffers the test owns, twice in a row, and
 its fluid / solid tags and interface count must equal those of the planned
-path (ebr_plan): tags bit for bit, counts exactly.  The file sorts last so a
-run that stops at the first failure has already run every other test."""
+path (ebr_plan): tags bit for bit, counts exactly.  On the small cases the
+tags are also compared with the oracle's solid set and the count with a
+brute-force count over the oracle's tags.  One case has exactly
+EBR_STATIC_MAX_ROWS rows, where the last row run sits next to the status word
+of the fixed array.  The file sorts last so a run that stops at the first
+failure has already run every other test."""
 
 import ctypes
 
@@ -19,7 +23,12 @@ from paper_2609_10165_b300.api import Reconstructor, _grid_struct, _body_struct
 
 pytestmark = pytest.mark.gpu
 
+MAX_ROWS = 1 << 18                         # EBR_STATIC_MAX_ROWS
+
 CASES = {
+    # n_y n_z == EBR_STATIC_MAX_ROWS exactly
+    "max_rows_sphere": lambda: {"grid": I.grid(3, [8, 512, 512], [-1.0] * 3, [1.0] * 3),
+                                "body": I.sphere(0.013, -0.007, 0.011, 0.6)},
     "cylinder_128": lambda: I.cylinder(128, 1),
     "airfoil_2048": lambda: I.airfoil_2048(),
     "sphere_256": lambda: I.sphere_cfg(256, 5),
@@ -38,6 +47,29 @@ def _call(lib, g, b, tags, count):
                                          ctypes.c_void_p(count.data_ptr()), stream)
 
 
+ORACLE_CASES = ("cylinder_128", "ragged_ellipse", "batch_geometry_7")
+
+
+def _oracle_solid_and_count(g, b):
+    """Solid set (centre in the closed body) and brute-force interface count
+    (cells with a face neighbour on the other side) from the oracle."""
+    import oracle as O
+    c = O.classify(g, b, "HGC")
+    solid = ((c.tags == 1) | (c.tags == 2)).astype(np.int8)
+    n = [int(v) for v in g["n"]][: g["dim"]]
+    sv = solid.reshape(n[::-1])                 # [.., y, x]: x fastest
+    iface = np.zeros(sv.shape, bool)
+    for ax in range(sv.ndim):
+        diff = np.diff(sv, axis=ax) != 0
+        lo = [slice(None)] * sv.ndim
+        hi = [slice(None)] * sv.ndim
+        lo[ax] = slice(0, -1)
+        hi[ax] = slice(1, None)
+        iface[tuple(lo)] |= diff
+        iface[tuple(hi)] |= diff
+    return solid, int(iface.sum())
+
+
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_static_entry_point_matches_planned_path(name):
     lib = _lib.load()
@@ -48,6 +80,11 @@ def test_static_entry_point_matches_planned_path(name):
     ref_solid = ((ref_tags == 1) | (ref_tags == 2)).astype(np.int8)
     ref_count = R.counts()[0]["n_interface"]
     n = R.n_cells
+    if name in ORACLE_CASES:
+        o_solid, o_count = _oracle_solid_and_count(g, b)
+        assert np.array_equal(o_solid, ref_solid) and o_count == ref_count, name
+    if name == "max_rows_sphere":
+        assert g["n"][1] * g["n"][2] == MAX_ROWS
     for call in range(2):
         tags = torch.full((n,), 7, dtype=torch.int8, device="cuda")
         count = torch.full((1,), -5, dtype=torch.int64, device="cuda")
