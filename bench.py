@@ -15,6 +15,7 @@ scaling, no collective on the data path).
 """
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -170,9 +171,10 @@ class Step:
     filled values: the path is linear) runs on a second stream beside the
     fill and the forces, joined at the end of the step."""
 
-    def __init__(self, R, fields, bcs, geoms, mode, adjoint=True, overlap=False):
+    def __init__(self, R, fields, bcs, geoms, mode, adjoint=True, overlap=False, geometry=True):
         import torch
         self.R, self.fields, self.bcs, self.mode, self.adjoint = R, fields, bcs, mode, adjoint
+        self.geometry = geometry     # False: a stationary body, classified and levelled once
         self.kinds = geoms[0]["bc"]
         self.vel = geoms[0]["roles"]["vel"]
         self.p = geoms[0]["roles"]["p"]
@@ -193,8 +195,9 @@ class Step:
     def __call__(self):
         import torch
         R = self.R
-        R.classify()
-        R.build_levels()
+        if self.geometry:
+            R.classify()
+            R.build_levels()
         if self.side is not None:
             main = torch.cuda.current_stream()
             self.side.wait_stream(main)
@@ -254,9 +257,11 @@ def time_steps(fn, steps, stream, flush):
     return [a.elapsed_time(b) for a, b in ts]
 
 
-def _oracle_geometry(g):
+def _oracle_geometry(g, keep=False):
     """The oracle's whole path on one geometry; seconds per phase and the
-    updates (ghosts x 3 fields) it produced."""
+    updates (ghosts x 3 fields) it produced (and, with keep, its results:
+    canonical ghost cells, ghost values, forces with their term magnitudes,
+    gradients)."""
     import oracle as O
     from paper_2609_10165_b300 import inputs as I
 
@@ -272,13 +277,18 @@ def _oracle_geometry(g):
     t.append(time.perf_counter())
     out = O.fill(c, lev, arrays, g["bc"], bcs)
     t.append(time.perf_counter())
-    O.forces(c, lev, out[2], [out[0], out[1]], g["mu"], I.DRAG_LIFT_DIRS_2D)
+    fo, fscale = O.forces(c, lev, out[2], [out[0], out[1]], g["mu"], I.DRAG_LIFT_DIRS_2D)
     t.append(time.perf_counter())
-    O.adjoint_gradient(c, lev, g["bc"], 2, [0, 1], g["mu"], I.DRAG_LIFT_DIRS_2D, (1.0, 1.0))
+    gx, gb = O.adjoint_gradient(c, lev, g["bc"], 2, [0, 1], g["mu"], I.DRAG_LIFT_DIRS_2D, (1.0, 1.0))
     t.append(time.perf_counter())
     phases = {"classify_levels": t[1] - t[0], "inputs": t[2] - t[1], "fill": t[3] - t[2],
               "forces": t[4] - t[3], "adjoint": t[5] - t[4]}
-    return c.n_ghosts * 3, phases
+    if not keep:
+        return c.n_ghosts * 3, phases
+    cells = c.idx[lev.order]
+    res = {"cells": cells, "values": [o[cells] for o in out], "fmax": [float(np.abs(a).max()) for a in arrays],
+           "forces": fo, "fscale": fscale, "gx": gx, "gb": gb}
+    return c.n_ghosts * 3, phases, res
 
 
 def _oracle_geometry_index(args):
@@ -309,27 +319,74 @@ def phase_sums(prof_ms):
     return out
 
 
-def cpu_baseline(geoms_all, budget_s=15.0):
+def sample_order(n, seed=2609):
+    """A seeded permutation of the geometry indices: the CPU samples draw
+    from the whole batch, not from its first geometries."""
+    return [int(i) for i in np.random.default_rng(seed).permutation(n)]
+
+
+def accuracy(gpu, res_by_geom, offsets, info):
+    """Worst error of the FP32 GPU path against the FP64 oracle (which ran on
+    the same FP32 field values, with FP64 boundary data at its own boundary
+    points) over the sampled geometries: ghost values relative to the field's
+    maximum, forces relative to the magnitude of their terms, gradients
+    relative to their maximum."""
+    ev = ef = eg = 0.0
+    for b, r in res_by_geom.items():
+        o0 = int(offsets[b])
+        sel = info["geom"] == b
+        cells = r["cells"]
+        for f in range(3):
+            if cells.size:
+                d = np.abs(gpu["fields"][f][o0 + cells].astype(np.float64) - r["values"][f])
+                ev = max(ev, float(d.max()) / max(r["fmax"][f], 1e-300))
+        d = np.abs(gpu["forces"][b] - r["forces"]) / np.maximum(r["fscale"], 1e-300)
+        ef = max(ef, float(d.max()))
+        o1 = o0 + r["gx"].shape[1]
+        for f in range(3):
+            sc = max(np.abs(r["gx"][f]).max(), np.abs(r["gb"][f]).max(), 1e-300)
+            d1 = np.abs(gpu["gf"][f][o0:o1].astype(np.float64) - r["gx"][f]).max()
+            d2 = np.abs(gpu["gb"][f][sel].astype(np.float64) - r["gb"][f]).max() if sel.any() else 0.0
+            eg = max(eg, float(max(d1, d2)) / sc)
+    return {"against": "FP64 oracle on the same FP32 field values, boundary data at its own S (FP64)",
+            "geometries": len(res_by_geom),
+            "ghost_values_rel_field_max": ev, "forces_rel_terms": ef, "gradients_rel_max": eg,
+            "test_tolerances": {"ghost_values_rel_field_max": 1e-5, "forces_rel_terms": 1e-4,
+                                "gradients_rel_max": 2e-5}}
+
+
+def cpu_baseline(geoms_all, budget_s=15.0, gpu=None, offsets=None, info=None):
     """The oracle as it stands on a bounded sample of the batch, one thread:
     classify, levels, fill of 3 fields, forces and the explicit-matrix
-    adjoint, with the seconds of each phase."""
+    adjoint, with the seconds of each phase.  Geometries are taken in a
+    seeded random order over the whole batch until the budget is spent.
+    With the GPU results of the step (gpu), the oracle's results on the same
+    sample also give the `accuracy` of the FP32 path (compared after the
+    timing)."""
     t0 = time.perf_counter()
     updates = 0
-    done = 0
+    done = []
     phases = {}
-    for g in geoms_all:
-        u, ph = _oracle_geometry(g)
-        updates += u
-        done += 1
-        for k, v in ph.items():
+    kept = {}
+    for b in sample_order(len(geoms_all)):
+        r = _oracle_geometry(geoms_all[b], keep=gpu is not None)
+        updates += r[0]
+        done.append(b)
+        for k, v in r[1].items():
             phases[k] = phases.get(k, 0.0) + v
+        if gpu is not None:
+            kept[b] = r[2]
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d of %d geometries of %s (classify, levels, fill of 3 fields, forces, "
-                      "explicit-matrix adjoint), %.1f s" % (done, len(geoms_all), WORKLOAD, dt),
-            "phases_s": {k: round(v, 3) for k, v in phases.items()}}
+    out = {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d of %d geometries of %s in a seeded random order (classify, levels, fill of 3 "
+                     "fields, forces, explicit-matrix adjoint), %.1f s" % (len(done), len(geoms_all), WORKLOAD, dt),
+           "sample_geometries": sorted(done),
+           "phases_s": {k: round(v, 3) for k, v in phases.items()}}
+    if gpu is not None:
+        out["accuracy"] = accuracy(gpu, kept, offsets, info)
+    return out
 
 
 def cpu_baseline_all_cores(n_geoms, budget_s=15.0):
@@ -368,22 +425,26 @@ def run_reference(args):
         return
     geoms = make_batch(args.geoms)
     ts = []
-    base = None
+    covered = set()
     for s in range(args.warmup + args.steps):
-        # each step a bounded sample: a rotating window of geometries
-        k = s % len(geoms)
-        sample = geoms[k:k + 2] or geoms[:2]
-        r = cpu_baseline(sample, budget_s=2.0)
+        # each step a bounded sample: 2 geometries drawn (seeded, without
+        # replacement) from the whole batch
+        pick = [int(i) for i in np.random.default_rng(2609 + s).choice(len(geoms), 2, replace=False)]
+        t0 = time.perf_counter()
+        u = sum(_oracle_geometry(geoms[i])[0] for i in pick)
+        dt = time.perf_counter() - t0
         if s >= args.warmup:
-            ts.append(r)
-        base = r
-    val = float(np.mean([r["value"] for r in ts]))
+            ts.append(u / dt)
+            covered.update(pick)
+    val = float(np.mean(ts))
+    sample = ("per step 2 geometries of %s drawn at random (seeded) from all %d; the timed steps covered "
+              "%d distinct geometries" % (WORKLOAD, len(geoms), len(covered)))
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "impl": "reference",
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": "2 geometries per step"},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": val,
-                             "sample": "per step 2 geometries of %s; last: %s" % (WORKLOAD, base["sample"])},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": val, "sample": sample,
+                             "sample_geometries": sorted(covered)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -434,27 +495,57 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
     }
 
 
+# Source file of each kernel group's device code; with the shared headers it
+# keys the counters below to the code they were measured on.
+CSRC = os.path.join(ROOT, "paper_2609_10165_b300", "csrc")
+KERNEL_SOURCE = {
+    "rows": "classify.cu", "iface": "classify.cu", "place": "classify.cu", "reclassify": "classify.cu",
+    "ghost_flags": "classify.cu", "ghost_write": "classify.cu", "scan": "scan.cu",
+    "poscell": "levels.cu", "deps": "levels.cu", "levels": "levels.cu", "reorder": "levels.cu",
+    "tables": "levels.cu", "gsrc": "levels.cu", "fill_part": "fill.cu", "fill_chain": "fill.cu",
+    "fill_level": "fill.cu", "forces": "forces.cu", "adj_seed": "adjoint.cu", "adj_part": "adjoint.cu",
+    "adj_chain": "adjoint.cu", "adj_level": "adjoint.cu", "adj_probe": "adjoint.cu",
+    "adj_fluid": "adjoint.cu", "adj_bc": "adjoint.cu", "pfill": "packed.cu", "padj": "packed.cu",
+}
+SHARED_HEADERS = ("ebr_device.cuh", "ebr_probe.cuh", "ebr_kernels.cuh")
+
+
+def kernel_source_hash(kernel):
+    """First 16 hex digits of the SHA-256 of the kernel's source file and the
+    shared device headers (None for an unknown kernel)."""
+    f = KERNEL_SOURCE.get(kernel)
+    if f is None:
+        return None
+    h = hashlib.sha256()
+    for name in (f,) + SHARED_HEADERS:
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
-# of the same kernel version on this workload (profiles/
-# dram_traffic_batch_256.md; L2 write-back hides most writes of a short
-# kernel).  The many-field calls were captured on 32 geometries and scaled by
-# the ghost count.  A kernel changed since its capture is left out (None).
-TRAFFIC_PER_LAUNCH = {
-    "ghost_write": 9.15e6,       # k_ghost_write 7.98 MB + k_ghost_geom 1.17 MB
-    "adj_fluid": 23.61e6, "adj_probe": 13.95e6, "adj_seed": 10.62e6, "fill_part": 27.85e6,
-    "fill_chain": 6.04e6, "forces": 32.54e6, "adj_part": 6.34e6, "adj_chain": 3.13e6, "levels": 1.13e6,
-    "rows": 0.34e6, "place": 1.74e6, "gsrc": 13.97e6, "tables": 9.84e6,
-    "pfill": 123.0e6, "padj": 153.0e6,
-}
+# on this workload, with the source hash of the kernel version captured (L2
+# write-back hides most writes of a short kernel).  A figure whose hash no
+# longer matches the source is reported as null, with the reason.
+TRAFFIC_PER_LAUNCH = {}
+
+# FP64 flops per launch (DADD + DMUL + 2 x DFMA thread instructions from one
+# ncu capture on this workload) of the kernels bound by the FP64 pipe, with
+# the source hash of the captured version.  "ghost_write" is the compaction +
+# closest-point pair; only the closest-point kernel does FP64 work.
+FP64_FLOPS_PER_LAUNCH = {}
 
 
-# FP64 flops per launch (DADD + DMUL + 2 x DFMA thread instructions, one ncu
-# capture on this workload: profiles/fp64_ops_batch_256.md) of the kernels
-# bound by the FP64 pipe.  "ghost_write" is the compaction + closest-point
-# pair; only the closest-point kernel does FP64 work.
-FP64_FLOPS_PER_LAUNCH = {
-    "ghost_write": 11_876_551, "tables": 10_419_154, "adj_seed": 9_582_272, "forces": 6_864_204,
-}
+def counter(table, kernel):
+    """(value, None) when the table holds a figure measured on the current
+    source of the kernel, else (None, reason)."""
+    if kernel not in table:
+        return None, "no ncu capture of this kernel on this workload"
+    value, h = table[kernel]
+    cur = kernel_source_hash(kernel)
+    if cur != h:
+        return None, "kernel source changed since the capture (captured %s, now %s)" % (h, cur)
+    return value, None
 # the FP64 pipe of one SM issues two double FMAs per clock (the counter's
 # sustained peak), i.e. 4 flops per SM per clock
 FP64_FLOPS_PER_SM_CLK = 4
@@ -476,25 +567,32 @@ def roofline_object(prof_ms, prof_n, algo, hbm_peak, hbm_peak_kind, n_sm, sm_mhz
         gbs = algo[k] / (v * 1e-3) / 1e9 if k in algo else None
         per_kernel[k] = {"ms": round(v, 5), "launches": prof_n[k],
                          "algo_bytes": algo.get(k), "gbs": round(gbs, 1) if gbs else None}
-        if k in FP64_FLOPS_PER_LAUNCH:
-            per_kernel[k]["fp64_tflops"] = round(FP64_FLOPS_PER_LAUNCH[k] / (v / prof_n[k] * 1e-3) / 1e12, 4)
+        fl, _ = counter(FP64_FLOPS_PER_LAUNCH, k)
+        if fl is not None:
+            per_kernel[k]["fp64_tflops"] = round(fl / (v / prof_n[k] * 1e-3) / 1e12, 4)
     t_launch = prof_ms[top] / prof_n[top] * 1e-3      # seconds per launch
     tb = algo[top] / prof_n[top]                      # bytes per launch
     gbs = tb / t_launch / 1e9
     hbm = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
            "peak_source": hbm_peak_kind, "algo_bytes_per_launch": tb}
     fp64_peak = fp64_peak_tflops(n_sm, sm_mhz)
-    roof = {"kernel": top, "traffic": TRAFFIC_PER_LAUNCH.get(top)}
-    if top in FP64_FLOPS_PER_LAUNCH:
-        ach = FP64_FLOPS_PER_LAUNCH[top] / t_launch / 1e12
+    traffic, why = counter(TRAFFIC_PER_LAUNCH, top)
+    roof = {"kernel": top, "traffic": traffic, "source_hash": kernel_source_hash(top)}
+    if why:
+        roof["traffic_null_because"] = why
+    flops, why_f = counter(FP64_FLOPS_PER_LAUNCH, top)
+    if flops is not None:
+        ach = flops / t_launch / 1e12
         roof.update({"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": ach / fp64_peak, "flops_per_launch": FP64_FLOPS_PER_LAUNCH[top],
+                     "frac": ach / fp64_peak, "flops_per_launch": flops,
                      "peak_source": "derived: %d SMs x %d FP64 flops per SM per clock x %.0f MHz"
                                     % (n_sm, FP64_FLOPS_PER_SM_CLK, sm_mhz),
                      "hbm": hbm})
     else:
         roof.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": gbs / hbm_peak, "peak_source": hbm_peak_kind, "algo_bytes_per_launch": tb})
+        if top in ("ghost_write", "tables", "adj_seed", "forces"):
+            roof["fp64_flops_null_because"] = why_f
     roof["fp64_peak_tflops"] = fp64_peak
     roof["per_kernel"] = per_kernel
     roof["phases_ms"] = phase_sums(prof_ms)
@@ -621,7 +719,8 @@ def throughput_mode(R, info, fields, bcs, kinds3, flush, stream, steps, warmup, 
         "fluid_incidences": n_inc, "unique_fluid_targets": n_tgt, "schedule": diag["packed"],
         "roofline": {"kernel": top, "launches": "all launches of the call", "bound": "hbm",
                      "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                     "traffic": TRAFFIC_PER_LAUNCH.get(top), "algo_bytes_per_call": algo[top]},
+                     "traffic": counter(TRAFFIC_PER_LAUNCH, top)[0],
+                     "source_hash": kernel_source_hash(top), "algo_bytes_per_call": algo[top]},
         "per_kernel": per,
         "l2": "flushed before every timed step (512 MB write)",
     }
@@ -716,6 +815,21 @@ def main():
     torch.cuda.synchronize()
     ms_f = float(np.median(time_steps(gf.replay, max(5, args.steps // 2), stream, flush)))
 
+    # reconstruction only: a stationary body (Sec. 7: the classification is
+    # redone only when the body moves), planned and levelled once; per step
+    # the fill, the forces and the adjoint (same graph construction)
+    step_r = Step(R, fields, bcs, geoms, "persistent", adjoint=True, overlap=True, geometry=False)
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        step_r()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(gr, stream=side, capture_error_mode="relaxed"):
+            step_r()
+    torch.cuda.synchronize()
+    ms_r_all = time_steps(gr.replay, max(5, args.steps // 2), stream, flush)
+    ms_r = float(np.median(ms_r_all))
+    del gr
+
     diag = R.diagnostics()
 
     # per-kernel device times: the step captured once more, without the
@@ -805,9 +919,24 @@ def main():
         "step_algo_bytes": sum(algo.values()),
         "step_frac": sum(algo.values()) / (ms_step * 1e-3) / 1e9 / peak})
 
+    recon_keys = [k for k in PHASES["fill"] + PHASES["forces"] + PHASES["adjoint"] if k in algo]
+    recon_bytes = sum(algo[k] for k in recon_keys)
+    reconstruction = {
+        "what": "fill (3 FP32 fields) + forces + adjoint per step on a geometry planned and levelled "
+                "once (stationary body); CUDA graph, adjoint on a second stream, L2 flushed",
+        "value": total_updates / (ms_r * 1e-3), "unit": UNIT, "ms_per_step": ms_r,
+        "p10_ms": float(np.percentile(ms_r_all, 10)), "p90_ms": float(np.percentile(ms_r_all, 90)),
+        "step_algo_bytes": recon_bytes,
+        "step_frac": recon_bytes / (ms_r * 1e-3) / 1e9 / peak,
+        "phases_ms_serial": {ph: phase_sums(prof_ms)[ph] for ph in ("fill", "forces", "adjoint")},
+    }
+
     baseline = None
     if rank == 0 and not args.no_baseline and not args.lite:
-        baseline = cpu_baseline(geoms, budget_s=15.0)
+        gpu_out = {"fields": [f.cpu().numpy() for f in fields], "forces": step.out.view(R.B, 6).cpu().numpy(),
+                   "gf": [t.cpu().numpy() for t in step.gf], "gb": [t.cpu().numpy() for t in step.gb]}
+        baseline = cpu_baseline(geoms, budget_s=15.0, gpu=gpu_out, offsets=R.cell_offset, info=info)
+        del gpu_out
         baseline["all_cores"] = cpu_baseline_all_cores(args.geoms, budget_s=15.0)
 
     line = {
@@ -822,6 +951,8 @@ def main():
                    "block_sizes": tuned if tuned is not None else "defaults (128)"},
         "autotune": tune_rep,
         "fwd_updates_per_s": total_updates / (ms_f * 1e-3), "fwd_ms_per_step": ms_f,
+        "reconstruction_only": reconstruction,
+        "accuracy": baseline.get("accuracy") if baseline else None,
         "plain_fp64_updates_per_s": total_updates / (ms64 * 1e-3) if ms64 == ms64 else None,
         "plain_fp64_ms_per_step": ms64,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),

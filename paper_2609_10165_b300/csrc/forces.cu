@@ -30,7 +30,9 @@ __global__ void __launch_bounds__(FC_T) k_forces_chunk(VelSet V, double mu, cons
                                                        const double* __restrict__ ftab, int ng,
                                                        double* __restrict__ partial) {
   constexpr int K = D == 2 ? 3 : 7;
-  __shared__ double red[FC_T][8];
+  // [quantity][thread]: a warp's 32 doubles of one quantity are contiguous
+  // (no bank conflicts in the tree below)
+  __shared__ double red[8][FC_T];
   int4 ch = chunks[blockIdx.x];        // (geometry, p0, p1, -)
   const Geom& g = G[ch.x];
   const int nx = g.n[0], ny = g.n[1];
@@ -89,16 +91,31 @@ __global__ void __launch_bounds__(FC_T) k_forces_chunk(VelSet V, double mu, cons
     acc[2 * D] = dr;
     acc[2 * D + 1] = li;
   }
+  // fixed tree: at level w, element i < w becomes element i + element i + w
+  // (w = 128, 64 in shared memory; 32 by warp 0 from shared memory; 16 .. 1
+  // by shuffles, which add the same pairs in the same order)
 #pragma unroll
-  for (int q = 0; q < 8; ++q) red[threadIdx.x][q] = acc[q];
+  for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = acc[q];
   __syncthreads();
-  for (int w = FC_T / 2; w > 0; w >>= 1) {
+#pragma unroll
+  for (int w = FC_T / 2; w > 32; w >>= 1) {
     if (threadIdx.x < w)
 #pragma unroll
-      for (int q = 0; q < 8; ++q) red[threadIdx.x][q] += red[threadIdx.x + w][q];
+      for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x < 8) partial[(size_t)blockIdx.x * 8 + threadIdx.x] = red[0][threadIdx.x];
+  if (threadIdx.x < 32) {
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = red[q][threadIdx.x] + red[q][threadIdx.x + 32];
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], w);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) partial[(size_t)blockIdx.x * 8 + q] = v[q];
+  }
 }
 
 __global__ void k_forces_final(int B, const Geom* __restrict__ G, const int* __restrict__ chunk_ptr,

@@ -74,14 +74,18 @@ def test_fp64_peak_from_unit_counts_and_clock():
     assert bench.fp64_peak_tflops(148, 2032.0) == pytest.approx(1.202944)
 
 
-def test_roofline_of_an_fp64_bound_dominant_kernel():
+def test_roofline_of_an_fp64_bound_dominant_kernel(monkeypatch):
+    h = bench.kernel_source_hash
+    monkeypatch.setattr(bench, "FP64_FLOPS_PER_LAUNCH", {"ghost_write": (11_876_551, h("ghost_write")),
+                                                         "tables": (10_419_154, h("tables"))})
+    monkeypatch.setattr(bench, "TRAFFIC_PER_LAUNCH", {"ghost_write": (9.15e6, h("ghost_write"))})
     prof_ms, prof_n, algo = _profile({})
     r = bench.roofline_object(prof_ms, prof_n, algo, 6495.6, "measured", 148, 2032.0)
     assert r["kernel"] == "ghost_write" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    ach = bench.FP64_FLOPS_PER_LAUNCH["ghost_write"] / 0.0438e-3 / 1e12
+    ach = 11_876_551 / 0.0438e-3 / 1e12
     assert r["achieved"] == pytest.approx(ach)
     assert r["frac"] == pytest.approx(ach / bench.fp64_peak_tflops(148, 2032.0))
-    assert r["traffic"] == bench.TRAFFIC_PER_LAUNCH["ghost_write"]
+    assert r["traffic"] == 9.15e6
     assert r["hbm"]["unit"] == "GB/s" and r["hbm"]["frac"] == pytest.approx(
         algo["ghost_write"] / 0.0438e-3 / 1e9 / 6495.6)
     assert r["per_kernel"]["tables"]["fp64_tflops"] > 0
@@ -100,3 +104,26 @@ def test_roofline_of_a_memory_bound_dominant_kernel():
     r = bench.roofline_object(prof_ms, prof_n, algo, 6495.6, "measured", 148, 2032.0)
     assert r["kernel"] == "scan" and r["algo_bytes_per_launch"] == pytest.approx(algo["scan"] / 3)
     assert r["achieved"] == pytest.approx(algo["scan"] / 3 / (0.1e-3) / 1e9)
+
+
+def test_counters_measured_on_other_source_are_null(monkeypatch):
+    # a counter keyed to another version of the kernel's source is not used:
+    # traffic null with the reason, and an FP64-bound kernel falls back to
+    # the HBM roofline
+    monkeypatch.setattr(bench, "FP64_FLOPS_PER_LAUNCH", {"ghost_write": (11_876_551, "0" * 16)})
+    monkeypatch.setattr(bench, "TRAFFIC_PER_LAUNCH", {"ghost_write": (9.15e6, "0" * 16)})
+    prof_ms, prof_n, algo = _profile({})
+    r = bench.roofline_object(prof_ms, prof_n, algo, 6495.6, "measured", 148, 2032.0)
+    assert r["traffic"] is None and "changed" in r["traffic_null_because"]
+    assert r["bound"] == "hbm" and "changed" in r["fp64_flops_null_because"]
+    assert r["source_hash"] == bench.kernel_source_hash("ghost_write")
+    # every profiled kernel name has a source file
+    for ks in bench.PHASES.values():
+        for k in ks:
+            assert bench.kernel_source_hash(k) is not None, k
+
+
+def test_cpu_samples_cover_the_whole_batch():
+    order = bench.sample_order(256)
+    assert sorted(order) == list(range(256))
+    assert order[:20] != list(range(20))
