@@ -25,6 +25,10 @@ Reconstruction: A Non-Iterative Approach for Embedded-Boundary Methods"):
                       at S (Sec. 6, Eqs. derivative_bilinear,
                       normal_derivative_trilinear, derivative_trilinear_x/y/z)
                       and the pressure / viscous force sums.
+* ``tiles``        -- the fill run by rectangular tiles (subdomains) that
+                      exchange, after each level, only the ghosts of that level
+                      read by another tile's stencil (Sec. 3.2, distributed
+                      memory), and the halo volume of a conventional exchange.
 * ``adjoint``      -- gradient of (drag, lift) with respect to the fluid field
                       values and the boundary data, and the vector-Jacobian
                       product of the fill, from the explicit sparse matrix of
@@ -42,6 +46,7 @@ from .reconstruct import (fill, ghost_weights, ghost_value, vandermonde_ghost_va
                           DIRICHLET, NEUMANN)
 from .surface import boundary_quantities, forces, face_weights
 from .adjoint import adjoint_gradient, fill_vjp, linear_map
+from . import tiles
 
 __all__ = [
     "Grid", "Body", "closest_point", "inside",

@@ -517,170 +517,76 @@ __device__ void exact_run_grp(const Geom& g, int j, int k, const RowGrp& Gp, int
   }
 }
 
-// Airfoil rows that cannot meet the body: |y'| along the chord segment stays
-// above the largest half thickness (0.6 t c bounds it with a wide margin), so
-// the row is empty.  Returns 1 for such a row, 0 when it may meet the body,
-// -1 for an airfoil whose chord is not inclined by less than 90 degrees.
-__device__ inline int airfoil_row_rejected(const Geom& g, int j) {
-  const float y = g.flo[1] + ((float)j + 0.5f) * g.fh[1] - g.fcentre[1];
-  const float r00 = g.frot[0], r01 = g.frot[1];
-  const float bx = g.frot[3] * y, byy = g.frot[4] * y;
-  const float c = g.fc, t = g.ft;
-  if (!(r00 > 0.0f)) return -1;
-  const float X0 = (0.0f - bx) / r00, X1 = (c - bx) / r00;
-  float ymin = fminf(fabsf(r01 * X0 + byy), fabsf(r01 * X1 + byy));
-  if ((r01 * X0 + byy) * (r01 * X1 + byy) < 0.0f) ymin = 0.0f;
-  return ymin > 0.6f * t * c + 1e-4f * c ? 1 : 0;
-}
-
-// Tag value (0 / 1) of 16 consecutive cells [i0, i0 + 16) of a row whose
-// solid run is [s, t], as four little-endian words: a chunk wholly outside or
-// inside the run is a constant; a chunk holding an end of the run builds its
-// bytes [lo, hi) from two prefix masks of 0x01 bytes per word.
-__device__ __forceinline__ uint4 run_chunk(int i0, int s, int t) {
-  if (i0 + 15 < s || i0 > t) return make_uint4(0u, 0u, 0u, 0u);
-  if (i0 >= s && i0 + 15 <= t) return make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
-  const int lo = min(max(s - i0, 0), 16);
-  const int hi = min(max(t + 1 - i0, 0), 16);
-  uint32_t w[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int l = min(max(lo - 4 * q, 0), 4), h = min(max(hi - 4 * q, 0), 4);
-    const uint32_t ph = h ? (0x01010101u >> (8 * (4 - h))) : 0u;
-    const uint32_t pl = l ? (0x01010101u >> (8 * (4 - l))) : 0u;
-    w[q] = h > l ? (ph & ~pl) : 0u;
-  }
-  return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-// One warp per 32 consecutive rows of the flat row list (rows of all
-// geometries back to back, so the warp's tags are one contiguous byte range).
-//  1. Runs, one lane per row: circle, sphere and ellipse rows take the closed
-//     form estimate and the exact 4-cell windows in their own lane; airfoil
-//     rows that may meet the body (the others are empty) go to 8-lane groups,
-//     four rows at a time, for the parallel search of the concave depth.
-//  2. Tags: the warp streams its whole byte range with 16-byte stores, lane l
-//     taking chunks l, l + 32, ... (512 contiguous bytes per warp store); a
-//     chunk that straddles two rows builds its bytes one by one.
-// The runs are exact either way (every estimate is confirmed or replaced by
-// the exact predicate), so the result does not depend on which lane or group
-// computed a row.
-constexpr int ROWS_WARPS = 8;        // warps per block (256 threads)
-
 __global__ void __launch_bounds__(256) k_rows(const Geom* __restrict__ G, const int* __restrict__ row_off,
                                               int B, int total_rows, int2* __restrict__ runs,
                                               int8_t* __restrict__ tags, int* status, int* stats) {
-  __shared__ long long sh_rs[ROWS_WARPS][33];   // flat start of each row of the warp, then the end
-  __shared__ int2 sh_run[ROWS_WARPS][32];
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int r0 = (blockIdx.x * ROWS_WARPS + wib) * 32;
-  if (r0 >= total_rows) return;                 // the whole warp leaves together
-  const int nrow = min(32, total_rows - r0);
-  const int row = r0 + lane;
-  const bool mine = lane < nrow;
-  int b = 0, local = 0, j = 0, k = 0;
-  int s = 0, t = -1;
-  bool grp = false;
-  if (mine) {
-    b = find_seg(row_off, B, row);
-    const Geom& g = G[b];
-    local = row - g.row_off;
-    j = local % g.n[1];
-    k = local / g.n[1];
-    if (g.kind == AIRFOIL4) {
-      const int q = airfoil_row_rejected(g, j);
-      if (q < 0) set_status(status, S_EINVAL);
-      grp = q == 0;
-    } else {
-      exact_run(g, j, k, s, t, status, stats);
-    }
-    sh_rs[wib][lane] = g.cell_off + (long long)local * g.n[0];
-    if (lane == nrow - 1) sh_rs[wib][nrow] = g.cell_off + (long long)(local + 1) * g.n[0];
-  }
-  // airfoil rows that may meet the body: four per round, one per 8-lane group
-  unsigned pend = __ballot_sync(FULL, grp);
-  while (pend) {
-    const int gi = lane >> 3;
-    unsigned m = pend;
-    for (int q = 0; q < gi && m; ++q) m &= m - 1;
-    const int src = m ? __ffs(m) - 1 : -1;       // the row of this group (uniform in the group)
-    for (int q = 0; q < 4 && pend; ++q) pend &= pend - 1;
-    const int sb = __shfl_sync(FULL, b, src < 0 ? 0 : src);
-    const int sj = __shfl_sync(FULL, j, src < 0 ? 0 : src);
-    const int sk = __shfl_sync(FULL, k, src < 0 ? 0 : src);
-    if (src >= 0) {
-      RowGrp Gp;
-      Gp.sl = lane & (RG - 1);
-      Gp.shift = lane & ~(RG - 1);
-      Gp.mask = 0xFFu << Gp.shift;
-      int s2, t2;
-      exact_run_grp(G[sb], sj, sk, Gp, s2, t2, status, stats);
-      if (Gp.sl == 0) sh_run[wib][src] = make_int2(s2, t2);
-    }
-    __syncwarp();
-  }
-  if (grp) {
-    const int2 r = sh_run[wib][lane];
-    s = r.x;
-    t = r.y;
-  }
-  if (mine) {
-    runs[row] = make_int2(s, t);
-    sh_run[wib][lane] = make_int2(s, t);
-  }
-  __syncwarp();
-  // the warp's contiguous byte range [A, E): head and tail bytes up to the
-  // 16-byte boundaries of the actual addresses (the caller's buffer may be
-  // offset), the aligned middle in 16-byte chunks
-  const long long A = sh_rs[wib][0], E = sh_rs[wib][nrow];
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) / RG;
+  if (row >= total_rows) return;                 // the whole group leaves together
+  RowGrp Gp;
+  Gp.sl = lane & (RG - 1);
+  Gp.shift = lane & ~(RG - 1);
+  Gp.mask = 0xFFu << Gp.shift;
+  const int b = find_seg(row_off, B, row);
+  const Geom& g = G[b];
+  const int local = row - g.row_off;
+  const int j = local % g.n[1];
+  const int k = local / g.n[1];
+  int s, t;
+  exact_run_grp(g, j, k, Gp, s, t, status, stats);
+  if (Gp.sl == 0) runs[row] = make_int2(s, t);
+  // the group streams the tags of its row
+  const int nx = g.n[0];
+  const long long rst = g.cell_off + (long long)local * nx, end = rst + nx;
+  // 16-byte alignment of the actual addresses (the caller's buffer may be offset)
   const long long mis = (long long)(reinterpret_cast<uintptr_t>(tags) & 15u);
-  long long a0 = ((A + mis + 15) & ~15LL) - mis;
-  long long a1 = ((E + mis) & ~15LL) - mis;
-  if (a0 > E) a0 = E;
+  long long a0 = ((rst + mis + 15) & ~15LL) - mis;
+  long long a1 = ((end + mis) & ~15LL) - mis;
+  if (a0 > end) a0 = end;
   if (a1 < a0) a1 = a0;
-  {
-    // lanes 0..15: head bytes, lanes 16..31: tail bytes
-    const long long x = lane < 16 ? A + lane : a1 + (lane - 16);
-    const long long lim = lane < 16 ? a0 : E;
-    if (x < lim) {
-      int r = 0;
-      while (x >= sh_rs[wib][r + 1]) ++r;
-      const int i = (int)(x - sh_rs[wib][r]);
-      const int2 R = sh_run[wib][r];
-      tags[x] = (int8_t)(i >= R.x && i <= R.y);
-    }
+  for (long long q = rst + Gp.sl; q < a0; q += RG) {
+    const long long i = q - rst;
+    tags[q] = (int8_t)(i >= s && i <= t);
   }
-  int r = 0;
-  for (long long x = a0 + 16LL * lane; x < a1; x += 16LL * 32) {
-    while (x >= sh_rs[wib][r + 1]) ++r;
+  for (long long q = a1 + Gp.sl; q < end; q += RG) {
+    const long long i = q - rst;
+    tags[q] = (int8_t)(i >= s && i <= t);
+  }
+  // aligned middle: 16 cells per lane per step, offsets from the row start in
+  // 32-bit.  A chunk wholly outside or inside the run is a constant; only the
+  // (at most two) chunks that hold an end of the run build their bytes: bytes
+  // [lo, hi) lie inside, each 32-bit word a difference of two prefix masks of
+  // 0x01 bytes.
+  int8_t* const rowp = tags + rst;
+  const int ia0 = (int)(a0 - rst), ia1 = (int)(a1 - rst);
+  for (int i0 = ia0 + 16 * Gp.sl; i0 < ia1; i0 += 16 * RG) {
     uint4 v;
-    if (x + 16 <= sh_rs[wib][r + 1]) {
-      const int2 R = sh_run[wib][r];
-      v = run_chunk((int)(x - sh_rs[wib][r]), R.x, R.y);
+    if (i0 + 15 < s || i0 > t) {
+      v = make_uint4(0u, 0u, 0u, 0u);
+    } else if (i0 >= s && i0 + 15 <= t) {
+      v = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
     } else {
-      // the chunk straddles rows: byte by byte
-      uint32_t w[4] = {0u, 0u, 0u, 0u};
-      int rr = r;
+      const int lo = min(max(s - i0, 0), 16);
+      const int hi = min(max(t + 1 - i0, 0), 16);
+      uint32_t w[4];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        while (x + q >= sh_rs[wib][rr + 1]) ++rr;
-        const int i = (int)(x + q - sh_rs[wib][rr]);
-        const int2 R = sh_run[wib][rr];
-        w[q >> 2] |= (uint32_t)(i >= R.x && i <= R.y) << (8 * (q & 3));
+      for (int q = 0; q < 4; ++q) {
+        const int l = min(max(lo - 4 * q, 0), 4), h = min(max(hi - 4 * q, 0), 4);
+        const uint32_t ph = h ? (0x01010101u >> (8 * (4 - h))) : 0u;
+        const uint32_t pl = l ? (0x01010101u >> (8 * (4 - l))) : 0u;
+        w[q] = h > l ? (ph & ~pl) : 0u;
       }
       v = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    *reinterpret_cast<uint4*>(tags + x) = v;
+    *reinterpret_cast<uint4*>(rowp + i0) = v;
   }
 }
 
 void launch_rows(const Geom* G, const int* row_off, int B, int total_rows, int2* runs,
                  int8_t* tags, int* status, int* stats, cudaStream_t s) {
   if (total_rows <= 0) return;
-  const long long warps = ((long long)total_rows + 31) / 32;
-  k_rows<<<(unsigned)((warps + ROWS_WARPS - 1) / ROWS_WARPS), 32 * ROWS_WARPS, 0, s>>>(
-      G, row_off, B, total_rows, runs, tags, status, stats);
+  const long long threads = (long long)total_rows * RG;
+  k_rows<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(G, row_off, B, total_rows, runs, tags, status, stats);
 }
 
 // ---------------------------------------------------------------------------
