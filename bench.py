@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--sets", type=int, default=32, help="field sets of the throughput mode (0: skip)")
+    ap.add_argument("--no-single-grid", dest="single_grid", action="store_false",
+                    help="skip the 512^3 single-grid tiled fill")
     ap.add_argument("--lite", action="store_true",
                     help="headline step only (no plain FP64 path, no e2e, no CPU baseline), for profilers")
     return ap.parse_args()
@@ -506,6 +508,7 @@ KERNEL_SOURCE = {
     "fill_level": "fill.cu", "forces": "forces.cu", "adj_seed": "adjoint.cu", "adj_part": "adjoint.cu",
     "adj_chain": "adjoint.cu", "adj_level": "adjoint.cu", "adj_probe": "adjoint.cu",
     "adj_fluid": "adjoint.cu", "adj_bc": "adjoint.cu", "pfill": "packed.cu", "padj": "packed.cu",
+    "tiled_fill": "tiled.cu",
 }
 SHARED_HEADERS = ("ebr_device.cuh", "ebr_probe.cuh", "ebr_kernels.cuh")
 
@@ -729,6 +732,85 @@ def throughput_mode(R, info, fields, bcs, kinds3, flush, stream, steps, warmup, 
     return out
 
 
+def single_grid_mode(dev, stream, flush, steps, warmup, peak, tiles=((16, 16, 16), (32, 32, 32), (64, 64, 64))):
+    """One large grid: the 512^3 sphere, 4 FP32 fields (u, v, w Dirichlet, p
+    Neumann), planned and levelled once.  Times the tiled fill (persistent
+    cooperative launch, per-level exchange between tiles, Sec. 3.2) for a few
+    tile sizes against the level-launch fill (one launch per level), each
+    captured in a CUDA graph, the L2 flushed before every step."""
+    import torch
+    from paper_2609_10165_b300 import inputs as I
+    from paper_2609_10165_b300.api import Reconstructor
+
+    w = I.sphere_cfg(512, 3)
+    R = Reconstructor(w["grid"], w["body"], "HGC", device=dev)
+    R.build_levels()
+    R.sync_status()
+    info = R.ghost_info()
+    F = len(w["fields"])
+    fields = [torch.tensor(f.on_grid(w["grid"], np.float32), device=dev) for f in w["fields"]]
+    bcs = [torch.tensor(I.bc_values(f, k, info["S"], info["normal"]), dtype=torch.float32, device=dev)
+           for f, k in zip(w["fields"], w["bc"])]
+    ng = int(info["cell"].size)
+    K, sz = 7, 4
+    algo = ng * F * (K * sz + 2 * sz) + ng * (4 + 4 + 2 * (K + 1) * 8)
+    cap = torch.cuda.Stream(dev)
+
+    how = {}
+
+    def timed(fn, key):
+        fn()
+        torch.cuda.synchronize()
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(cap):
+                with torch.cuda.graph(g, stream=cap, capture_error_mode="relaxed"):
+                    fn()
+            torch.cuda.synchronize()
+            run, how[key] = g.replay, "graph"
+        except Exception as e:  # reported: timed eagerly instead
+            torch.cuda.synchronize()
+            run, how[key] = fn, "eager (capture failed: %s)" % str(e)[:80]
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        ms = float(np.median(time_steps(run, steps, stream, flush)))
+        R.sync_status()
+        return ms
+
+    out = {"workload": "sphere_512 (512^3 cells, r = 0.5 in [-2, 2]^3, HGC), 4 FP32 fields, FP64 coefficients",
+           "ghosts": ng, "levels": int(info["level"].max()), "updates_per_step": ng * F,
+           "algo_bytes": algo, "l2": "flushed before every timed step (512 MB write)"}
+    ms_lv = timed(lambda: R.reconstruct(fields, w["bc"], bcs, mode="level"), "level_launch")
+    out["level_launch"] = {"ms": ms_lv, "value": ng * F / (ms_lv * 1e-3), "launches": int(info["level"].max())}
+    best = None
+    out["tiled"] = {}
+    for tile in tiles:
+        R.tiled_plan(list(tile))
+        ti = R.tiled_info()
+        key = "x".join(str(t) for t in tile)
+        ms = timed(lambda: R.reconstruct_tiled(fields, w["bc"], bcs), key)
+        out["tiled"][key] = {"ms": ms, "value": ng * F / (ms * 1e-3), "active_tiles": ti["active_tiles"],
+                             "ctas": ti["grid_f32"], "sent_ghosts": ti["sent_ghosts"],
+                             "values_exchanged": ti["values_exchanged"], "halo_values": ti["halo_values"],
+                             "sent_per_level": ti["sent_per_level"]}
+        if best is None or ms < out["tiled"][best]["ms"]:
+            best = key
+    b = out["tiled"][best]
+    out["timing"] = how
+    out["best_tile"] = best
+    out["value"] = b["value"]
+    out["unit"] = UNIT
+    out["roofline"] = {"kernel": "tiled_fill", "bound": "hbm", "achieved": algo / (b["ms"] * 1e-3) / 1e9,
+                       "peak": peak, "unit": "GB/s", "frac": algo / (b["ms"] * 1e-3) / 1e9 / peak,
+                       "algo_bytes_per_launch": algo,
+                       "traffic": counter(TRAFFIC_PER_LAUNCH, "tiled_fill")[0],
+                       "source_hash": kernel_source_hash("tiled_fill")}
+    del fields, bcs, R
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -865,6 +947,12 @@ def main():
         tput = throughput_mode(R, info, fields, bcs, geoms[0]["bc"], flush, stream, args.steps,
                                max(args.warmup, 3), measured_peaks()[0], n_sets=args.sets)
 
+    # one large grid: the tiled fill with its per-level exchange
+    single = None
+    if args.single_grid and rank == 0 and not args.lite:
+        single = single_grid_mode(dev, stream, flush, max(5, args.steps // 4), max(args.warmup, 3),
+                                  measured_peaks()[0])
+
     # plain FP64 path: one launch per level per geometry, FP64 fields, no graph
     ms64 = float("nan")
     try:
@@ -961,6 +1049,7 @@ def main():
         "graph_kernel_nodes_per_step": graph_kernels,
         "roofline": roof,
         "throughput_mode": tput,
+        "single_grid": single,
         "clocks": clk,
         "cpu_baseline": baseline,
         "wall_s_timed": t_wall,

@@ -301,6 +301,58 @@ ebr_status ebr_reconstruct_packed_adjoint(void* ctx, int32_t n_fields, const int
                                           ebr_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Tiled fill with a per-level exchange (Sec. 3.2, distributed memory)
+ *
+ * The grids are cut into rectangular tiles (subdomains) and a ghost belongs
+ * to the tile of its cell.  The fill runs as one persistent cooperative
+ * launch: each CTA owns tiles; for every level L_k it fills the ghosts of
+ * its tiles in L_k, reading fluid values and its own tiles' ghosts from the
+ * fields and other tiles' ghosts only from an exchange buffer, writes to that
+ * buffer the ghosts of L_k that other tiles' stencils read (only those: the
+ * level-wise exchange of Sec. 3.2), and meets all CTAs at a device-wide
+ * barrier before L_{k+1}.  Same closed forms and summation order as
+ * EBR_MODE_LEVEL_LAUNCH: the results are the same bits.
+ * ------------------------------------------------------------------------- */
+
+/* Plan the tiles of the levelled geometry set: h_tile [dim] cells per tile
+ * along x, y (, z), each >= 1.  Tile t of cell (i, j, k) of geometry b is
+ * tile_offset[b] + i / T_x + n_tx (j / T_y + n_ty (k / T_z)), n_ta = ceil(n_a /
+ * T_a), tile offsets accumulated over the geometries in order.  Plans on the
+ * host (synchronises the stream; not inside a stream capture) and allocates
+ * the schedule and the exchange buffer (released by the next tiled plan,
+ * ebr_plan or ebr_destroy).  Plan again after ebr_build_levels re-plans. */
+ebr_status ebr_tiled_plan(void* ctx, const int32_t* h_tile, ebr_stream stream);
+
+/* Fill the ghost entries in place, tiled (same arguments and layouts as
+ * ebr_reconstruct, 1..8 fields).  Every wait at the device-wide barrier is
+ * bounded: a wait that gives up sets EBR_ETIMEOUT in the status word and the
+ * launch ends (ghosts of the levels not reached are left unwritten). */
+ebr_status ebr_reconstruct_tiled(void* ctx, int32_t n_fields, void* const* d_fields,
+                                 const int32_t* h_bc_kind, const void* const* d_bc, int32_t dtype,
+                                 ebr_stream stream);
+
+/* Schedule statistics, h_out[0 .. n): [0] tiles owning a ghost, [1] tiles in
+ * all, [2] sent ghosts (ghosts read by another tile's stencil), [3] values
+ * exchanged ((sent ghost, receiving tile) pairs, all levels), [4] values a
+ * conventional halo exchange would send (every sweep, the ghosts within the
+ * stencil reach of a face of their tile, one sweep per level), [5] levels,
+ * [6] / [7] CTAs of the FP32 / FP64 launch, [8 + k - 1] sent ghosts of level
+ * k.  Host values; no synchronisation. */
+ebr_status ebr_tiled_info(void* ctx, int64_t* h_out, int32_t n);
+
+/* Per ghost (canonical order), host arrays [total ghosts]: h_tile receives
+ * its tile (numbering of ebr_tiled_plan), h_slot its slot in the exchange
+ * buffer or -1 when no other tile reads it.  Either pointer may be NULL. */
+ebr_status ebr_tiled_lists(void* ctx, int32_t* h_tile, int32_t* h_slot);
+
+/* Failure test of the bounded barrier (the paper has no counterpart): the
+ * next ebr_reconstruct_tiled waits at its first barrier for one arrival more
+ * than its CTAs provide and gives up after `spins` polls (1 .. 2^24): it
+ * reports EBR_ETIMEOUT through ebr_sync_status, and the context stays usable.
+ * No GPU fault is involved: the wait is a bounded loop. */
+ebr_status ebr_tiled_wait_test(void* ctx, int32_t spins);
+
+/* ---------------------------------------------------------------------------
  * Status
  * ------------------------------------------------------------------------- */
 

@@ -61,6 +61,12 @@ _SIGS = {
                                          c_void_p, c_int32, c_void_p]),
     "ebr_reconstruct_packed_adjoint": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32), c_void_p,
                                                  c_void_p, c_int32, c_void_p]),
+    "ebr_tiled_plan": (c_int32, [c_void_p, ctypes.POINTER(c_int32), c_void_p]),
+    "ebr_reconstruct_tiled": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_int32),
+                                        ctypes.POINTER(c_void_p), c_int32, c_void_p]),
+    "ebr_tiled_info": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_int32]),
+    "ebr_tiled_lists": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "ebr_tiled_wait_test": (c_int32, [c_void_p, c_int32]),
     "ebr_sync_status": (c_int32, [c_void_p, c_void_p]),
     "ebr_diagnostics": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_int32, c_void_p]),
     "ebr_launch_count": (c_int64, [c_void_p]),

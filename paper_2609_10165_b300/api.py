@@ -200,6 +200,40 @@ class Reconstructor:
         if rows is not None and int(t.shape[0]) != rows:
             raise ValueError("packed field array needs %d rows (cells), got %d" % (rows, int(t.shape[0])))
 
+    # -- tiled fill with a per-level exchange -----------------------------------
+    def tiled_plan(self, tile):
+        """Plan tiles of `tile` cells per axis (host step; before any capture)."""
+        t = (ctypes.c_int32 * 3)(*([int(v) for v in tile] + [1] * (3 - len(tile))))
+        self._check(self.lib.ebr_tiled_plan(self.ctx, t, self._stream()))
+
+    def reconstruct_tiled(self, fields, bc_kinds, bc):
+        F = len(fields)
+        kinds = (ctypes.c_int32 * F)(*[int(k) for k in bc_kinds])
+        self._check(self.lib.ebr_reconstruct_tiled(self.ctx, F, _ptr_array(fields), kinds, _ptr_array(bc),
+                                                   DTYPE[fields[0].dtype], self._stream()))
+        return fields
+
+    def tiled_info(self):
+        n = 8 + 256
+        out = (ctypes.c_int64 * n)()
+        self._check(self.lib.ebr_tiled_info(self.ctx, out, n))
+        L = int(out[5])
+        return {"active_tiles": int(out[0]), "tiles": int(out[1]), "sent_ghosts": int(out[2]),
+                "values_exchanged": int(out[3]), "halo_values": int(out[4]), "levels": L,
+                "grid_f32": int(out[6]), "grid_f64": int(out[7]),
+                "sent_per_level": [int(out[8 + k]) for k in range(min(L, 256))]}
+
+    def tiled_lists(self):
+        ng = self.n_ghosts
+        tile = np.zeros(ng, np.int32)
+        slot = np.zeros(ng, np.int32)
+        self._check(self.lib.ebr_tiled_lists(self.ctx, tile.ctypes.data_as(ctypes.c_void_p),
+                                             slot.ctypes.data_as(ctypes.c_void_p)))
+        return tile, slot
+
+    def tiled_wait_test(self, spins):
+        self._check(self.lib.ebr_tiled_wait_test(self.ctx, int(spins)))
+
     def sync_status(self):
         self._check(self.lib.ebr_sync_status(self.ctx, self._stream()))
 

@@ -1,6 +1,7 @@
 // C ABI (include/ebr.h): context, planning, and the orchestration of the
 // classification, level, fill, force and adjoint kernels.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -133,6 +134,23 @@ struct Ctx {
   size_t lamP_bytes = 0;
   std::map<long long, ChainPlan> chain_plans;
 
+  // tile schedule of the tiled fill (ebr_tiled_plan); its device buffers are
+  // its own (freed by the next tiled plan, ebr_plan or ebr_destroy)
+  struct Tiled {
+    bool built = false;
+    int tile[3] = {0, 0, 0};
+    TiledPlanDev dev;
+    int grid[2] = {0, 0};
+    void* xbuf = nullptr;
+    unsigned* bar = nullptr;
+    std::vector<void*> mem;
+    std::vector<int> h_tile_global;       // per ghost (canonical): geometry tile offset + tile id
+    std::vector<int> h_slot;              // per ghost: exchange slot or -1
+    std::vector<long long> sent_per_level;
+    long long total_tiles = 0, pairs = 0, halo = 0;
+    int extra_once = 0, spin_once = 0;    // bounded-wait test of the next launch
+  } tiled;
+
   // optional per-kernel timing: events recorded on the launching stream
   struct ProfRec {
     const char* name;
@@ -240,7 +258,13 @@ ebr_status balloc(Ctx* c, void** p, size_t bytes) {
     if (s_ != EBR_OK) return s_;                                 \
   } while (0)
 
+void tiled_free(Ctx* c) {
+  for (void* q : c->tiled.mem) cudaFree(q);
+  c->tiled = Ctx::Tiled();
+}
+
 void free_all(Ctx* c) {
+  tiled_free(c);
   for (auto& e : c->pool) cudaEventDestroy(e);
   c->pool.clear();
   c->pool_used = 0;
@@ -1226,6 +1250,238 @@ ebr_status ebr_reconstruct_packed_adjoint(void* ctx, int32_t n_fields, const int
   }
   c->launches += padj_launches(c->pplan, c->ng);
   CKL();
+  return EBR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tiled fill with per-level exchange (Sec. 3.2, distributed memory)
+// ---------------------------------------------------------------------------
+static ebr_status tiled_alloc(Ctx* c, void** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, EBR_ENOMEM, "ebr_tiled_plan: cudaMalloc of %zu bytes failed", bytes);
+  }
+  c->tiled.mem.push_back(q);
+  *p = q;
+  return EBR_OK;
+}
+
+ebr_status ebr_tiled_plan(void* ctx, const int32_t* h_tile, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_tiled_plan: build the levels first");
+  if (!h_tile) return fail(c, EBR_EINVAL, "ebr_tiled_plan: null tile sizes");
+  const int dim = c->hG[0].dim;
+  int T[3] = {1, 1, 1};
+  for (int a = 0; a < dim; ++a) {
+    if (h_tile[a] < 1) return fail(c, EBR_EINVAL, "ebr_tiled_plan: tile size %d along axis %d", h_tile[a], a);
+    T[a] = h_tile[a];
+  }
+  cudaStream_t s = S(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(c, EBR_EINVAL, "ebr_tiled_plan: plans on the host; call it outside stream capture");
+  tiled_free(c);
+  Ctx::Tiled& tp = c->tiled;
+  const int ng = c->ng;
+  std::vector<int> geo(ng), cell(ng), lev(ng), dep((size_t)MAXK * ng);
+  if (ng > 0) {
+    CK(cudaMemcpyAsync(geo.data(), c->g_geo, sizeof(int) * ng, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(cell.data(), c->g_cell, sizeof(int) * ng, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(lev.data(), c->g_level, sizeof(int) * ng, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(dep.data(), c->g_dep, sizeof(int) * MAXK * (size_t)ng, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  // tiles of every geometry, numbered after those of the geometries before it
+  std::vector<long long> toff(c->B + 1, 0);
+  std::vector<std::array<int, 3>> ntile(c->B);
+  for (int b = 0; b < c->B; ++b) {
+    long long nt = 1;
+    for (int a = 0; a < 3; ++a) {
+      ntile[b][a] = a < dim ? (c->hG[b].n[a] + T[a] - 1) / T[a] : 1;
+      nt *= ntile[b][a];
+    }
+    toff[b + 1] = toff[b] + nt;
+  }
+  if (toff[c->B] >= (1LL << 31)) return fail(c, EBR_EINVAL, "ebr_tiled_plan: more than 2^31 tiles");
+  tp.total_tiles = toff[c->B];
+  tp.h_tile_global.assign(ng, 0);
+  for (int p = 0; p < ng; ++p) {
+    const Geom& g = c->hG[geo[p]];
+    const int i = cell[p] % g.n[0], j = (cell[p] / g.n[0]) % g.n[1], k = cell[p] / (g.n[0] * g.n[1]);
+    const long long t = i / T[0] + (long long)ntile[geo[p]][0] * (j / T[1] + (long long)ntile[geo[p]][1] * (k / T[2]));
+    tp.h_tile_global[p] = (int)(toff[geo[p]] + t);
+  }
+  // active tiles (those owning a ghost), in tile order
+  std::vector<int> act(tp.h_tile_global);
+  std::sort(act.begin(), act.end());
+  act.erase(std::unique(act.begin(), act.end()), act.end());
+  const int NT = (int)act.size();
+  std::vector<int> tile_of(ng);
+  for (int p = 0; p < ng; ++p)
+    tile_of[p] = (int)(std::lower_bound(act.begin(), act.end(), tp.h_tile_global[p]) - act.begin());
+  int Lmax = 0;
+  for (int b = 0; b < c->B; ++b) Lmax = std::max(Lmax, c->hG[b].n_levels);
+  const int W = Lmax + 1;
+  // ghosts of each (tile, level), in canonical order: level L (1-based) of
+  // active tile i is bucket i W + L - 1, [t_ptr[i W + L - 1], t_ptr[i W + L])
+  std::vector<int> t_ptr((size_t)NT * W + 1, 0), t_list(ng);
+  for (int p = 0; p < ng; ++p) {
+    if (lev[p] < 1 || lev[p] > Lmax) return fail(c, EBR_EINVAL, "ebr_tiled_plan: ghost %d without a level", p);
+    ++t_ptr[(size_t)tile_of[p] * W + lev[p] - 1];
+  }
+  {
+    int run = 0;
+    for (size_t q = 0; q < t_ptr.size(); ++q) {
+      const int v = t_ptr[q];
+      t_ptr[q] = run;
+      run += v;
+    }
+  }
+  {
+    std::vector<int> cur(t_ptr.begin(), t_ptr.end() - 1);
+    for (int p = 0; p < ng; ++p) t_list[cur[(size_t)tile_of[p] * W + lev[p] - 1]++] = p;
+  }
+  // sent ghosts: a dependency of a ghost of another tile; (ghost, receiving
+  // tile) pairs for the statistics
+  std::vector<char> sent(ng, 0);
+  std::vector<long long> pairs;
+  for (int p = 0; p < ng; ++p)
+    for (int k = 0; k < MAXK; ++k) {
+      const int d = dep[(size_t)k * ng + p];
+      if (d >= 0 && tile_of[d] != tile_of[p]) {
+        sent[d] = 1;
+        pairs.push_back((long long)d * (long long)(NT + 1) + tile_of[p]);
+      }
+    }
+  std::sort(pairs.begin(), pairs.end());
+  tp.pairs = (long long)(std::unique(pairs.begin(), pairs.end()) - pairs.begin());
+  tp.h_slot.assign(ng, -1);
+  tp.sent_per_level.assign(Lmax, 0);
+  int n_slots = 0;
+  for (int p = 0; p < ng; ++p)
+    if (sent[p]) {
+      tp.h_slot[p] = n_slots++;
+      ++tp.sent_per_level[lev[p] - 1];
+    }
+  // conventional comparison: every sweep exchanges the ghosts within the
+  // stencil reach of a tile face (to the tile across it); n_levels sweeps
+  tp.halo = 0;
+  {
+    const int R = std::max(c->rmax, 1);
+    std::vector<long long> per(c->B, 0);
+    for (int p = 0; p < ng; ++p) {
+      const Geom& g = c->hG[geo[p]];
+      const int ijk[3] = {cell[p] % g.n[0], (cell[p] / g.n[0]) % g.n[1], cell[p] / (g.n[0] * g.n[1])};
+      for (int a = 0; a < dim; ++a) {
+        const int r = ijk[a] % T[a], base = ijk[a] - r;
+        if (r < R && base > 0) ++per[geo[p]];
+        if (T[a] - 1 - r < R && base + T[a] < g.n[a]) ++per[geo[p]];
+      }
+    }
+    for (int b = 0; b < c->B; ++b) tp.halo += per[b] * c->hG[b].n_levels;
+  }
+  // upload
+  int *d_ptr = nullptr, *d_list = nullptr, *d_tile = nullptr, *d_slot = nullptr;
+  ebr_status st;
+  if ((st = tiled_alloc(c, (void**)&d_ptr, sizeof(int) * t_ptr.size()))) return st;
+  if ((st = tiled_alloc(c, (void**)&d_list, sizeof(int) * std::max(ng, 1)))) return st;
+  if ((st = tiled_alloc(c, (void**)&d_tile, sizeof(int) * std::max(ng, 1)))) return st;
+  if ((st = tiled_alloc(c, (void**)&d_slot, sizeof(int) * std::max(ng, 1)))) return st;
+  if ((st = tiled_alloc(c, &tp.xbuf, (size_t)8 * 8 * std::max(n_slots, 1)))) return st;   // [F <= 8][slots] doubles
+  if ((st = tiled_alloc(c, (void**)&tp.bar, 2 * sizeof(unsigned)))) return st;
+  CK(cudaMemcpy(d_ptr, t_ptr.data(), sizeof(int) * t_ptr.size(), cudaMemcpyHostToDevice));
+  if (ng > 0) {
+    CK(cudaMemcpy(d_list, t_list.data(), sizeof(int) * ng, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_tile, tile_of.data(), sizeof(int) * ng, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_slot, tp.h_slot.data(), sizeof(int) * ng, cudaMemcpyHostToDevice));
+  }
+  tp.dev.n_tiles = NT;
+  tp.dev.Lmax = Lmax;
+  tp.dev.n_slots = std::max(n_slots, 1);
+  tp.dev.spin_limit = 1 << 21;
+  tp.dev.t_ptr = d_ptr;
+  tp.dev.t_list = d_list;
+  tp.dev.tile_of = d_tile;
+  tp.dev.slot_of = d_slot;
+  for (int a = 0; a < 3; ++a) tp.tile[a] = T[a];
+  for (int dt = 0; dt < 2; ++dt) tp.grid[dt] = tiled_grid(dt, NT);
+  CKL();
+  tp.built = true;
+  return EBR_OK;
+}
+
+ebr_status ebr_reconstruct_tiled(void* ctx, int32_t n_fields, void* const* d_fields,
+                                 const int32_t* h_bc_kind, const void* const* d_bc, int32_t dtype,
+                                 ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  if (!c->tiled.built) return fail(c, EBR_EINVAL, "ebr_reconstruct_tiled: call ebr_tiled_plan first");
+  if (n_fields < 1 || n_fields > 8 || !d_fields || !h_bc_kind || !d_bc)
+    return fail(c, EBR_EINVAL, "ebr_reconstruct_tiled: 1..8 fields with kinds and boundary data required");
+  if (dtype != EBR_F32 && dtype != EBR_F64) return fail(c, EBR_EINVAL, "ebr_reconstruct_tiled: bad dtype");
+  for (int f = 0; f < n_fields; ++f) {
+    if (!d_fields[f] || (!d_bc[f] && c->ng > 0))
+      return fail(c, EBR_EINVAL, "ebr_reconstruct_tiled: null field %d", f);
+    if (h_bc_kind[f] != 0 && h_bc_kind[f] != 1) return fail(c, EBR_EINVAL, "ebr_reconstruct_tiled: bad bc kind");
+  }
+  Ctx::Tiled& tp = c->tiled;
+  if (tp.dev.n_tiles == 0 || tp.dev.Lmax == 0) return EBR_OK;
+  cudaStream_t s = S(stream);
+  TiledPlanDev A = tp.dev;
+  const int extra = tp.extra_once;
+  if (tp.spin_once > 0) A.spin_limit = tp.spin_once;
+  tp.extra_once = tp.spin_once = 0;
+  prof_begin(c, s, "tiled_fill");
+  cudaError_t e = launch_tiled_fill(dtype, n_fields, d_fields, h_bc_kind, d_bc, c->dG, A, tp.grid[dtype],
+                                    c->g_geo, c->g_cell, c->g_meta, c->g_dep, c->wtab, c->ng, tp.xbuf, tp.bar,
+                                    extra, c->d_status, s);
+  prof_end(c, s);
+  c->launches += 1;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, EBR_ECUDA, "ebr_reconstruct_tiled: launch failed: %s", cudaGetErrorString(e));
+  }
+  return EBR_OK;
+}
+
+ebr_status ebr_tiled_info(void* ctx, int64_t* h_out, int32_t n) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !h_out || n < 1) return EBR_EINVAL;
+  if (!c->tiled.built) return fail(c, EBR_EINVAL, "ebr_tiled_info: call ebr_tiled_plan first");
+  const Ctx::Tiled& tp = c->tiled;
+  long long nsent = 0;
+  for (long long q : tp.sent_per_level) nsent += q;
+  const long long v[8] = {tp.dev.n_tiles, tp.total_tiles, nsent, tp.pairs, tp.halo, tp.dev.Lmax,
+                          tp.grid[0], tp.grid[1]};
+  for (int k = 0; k < n; ++k)
+    h_out[k] = k < 8 ? v[k] : (k - 8 < (int)tp.sent_per_level.size() ? tp.sent_per_level[k - 8] : 0);
+  return EBR_OK;
+}
+
+ebr_status ebr_tiled_lists(void* ctx, int32_t* h_tile, int32_t* h_slot) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  if (!c->tiled.built) return fail(c, EBR_EINVAL, "ebr_tiled_lists: call ebr_tiled_plan first");
+  for (int p = 0; p < c->ng; ++p) {
+    if (h_tile) h_tile[p] = c->tiled.h_tile_global[p];
+    if (h_slot) h_slot[p] = c->tiled.h_slot[p];
+  }
+  return EBR_OK;
+}
+
+ebr_status ebr_tiled_wait_test(void* ctx, int32_t spins) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  if (!c->tiled.built) return fail(c, EBR_EINVAL, "ebr_tiled_wait_test: call ebr_tiled_plan first");
+  if (spins < 1 || spins > (1 << 24)) return fail(c, EBR_EINVAL, "ebr_tiled_wait_test: spins in 1..2^24");
+  c->tiled.extra_once = 1;
+  c->tiled.spin_once = spins;
   return EBR_OK;
 }
 

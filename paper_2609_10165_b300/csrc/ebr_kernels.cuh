@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ebr_device.cuh"
@@ -142,6 +143,32 @@ void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* 
 void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                    const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,
                    void* const* grad, int accumulate, cudaStream_t s, int T = 128);
+
+// ---- tiled.cu (Sec. 3.2, distributed memory: tiles with a per-level exchange)
+// Device view of a tile schedule: the ghosts of active tile i in level L are
+// t_list[t_ptr[i (Lmax + 1) + L - 1] .. t_ptr[i (Lmax + 1) + L]) (canonical
+// positions); tile_of[p] is the active tile of ghost p, slot_of[p] its slot in
+// the exchange buffer ([F][n_slots]) when another tile's stencil reads it, else -1.
+struct TiledPlanDev {
+  int n_tiles = 0;
+  int Lmax = 0;
+  int n_slots = 0;
+  int spin_limit = 0;
+  const int* t_ptr = nullptr;
+  const int* t_list = nullptr;
+  const int* tile_of = nullptr;
+  const int* slot_of = nullptr;
+};
+// CTAs of the cooperative tiled fill: all tiles, at most the resident CTAs
+int tiled_grid(int dtype, int n_tiles);
+// zeroes the barrier words and launches the cooperative fill; extra_arrivals
+// > 0 makes the first barrier wait for arrivals that never come (the bounded
+// wait then reports EBR_ETIMEOUT)
+cudaError_t launch_tiled_fill(int dtype, int F, void* const* fields, const int* bc_kind, const void* const* bc,
+                              const Geom* G, const TiledPlanDev& A, int grid, const int* g_geo,
+                              const int* g_cell, const uint32_t* g_meta, const int* g_dep, const double* wtab,
+                              int ng, void* xbuf, unsigned* bar, int extra_arrivals, int* status,
+                              cudaStream_t s);
 
 // ---- packed.cu (field-minor layout [cells][F])
 // Schedule of the packed kernels, planned once per levelled geometry set:
