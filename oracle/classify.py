@@ -21,6 +21,17 @@ or -2 (centre in the fluid).
   (the paper lists both without an order); it reproduces Fig. 3(c).
 * CGC_ES (Sec. 7, Eq. stencil_anisotropic): the CGC ghost set with the stencil
   multipliers r_i = max(1, ceil(2 |n_i psi| / dx_i)); CGC and HGC use r_i = 1.
+* Second ghost layer (Sec. 7, "Additional ghost-cell layers", layers=2): after
+  the first layer is placed (and, for HGC, reclassified), every remaining
+  solid cell (tag 1) with psi <= 1.5 dn joins the ghost set (+2), and every
+  ghost takes the multipliers of Eq. stencil_anisotropic (which leave HGC's
+  first layer at r = 1, since there |n_i psi| / dx_i <= psi / dn <= 1/2).
+  Readings: the layer is added after the first layer's reclassification (the
+  passes act on the first layer only), dn is that of Eq. delta_n with the
+  cell's own normal and widths, and the rule is offered with HGC and CGC_ES.
+  Candidates are the solid cells with a fluid cell within `layer_reach` cells
+  along every axis (a box); the reach bounds the index distance from a solid
+  cell with psi <= 1.5 dn to a fluid cell (see layer_reach).
 
 Only cells with a face neighbour on the other side of the boundary can end as
 ghosts: a fluid cell without a solid neighbour has no neighbour tagged 1 and
@@ -119,9 +130,44 @@ def delta_n(grid, n):
     return 1.0 / np.sqrt(s)
 
 
-def classify(grid, body, placement=HGC, tie_rel=1e-9, cells=None):
+def layer_reach(grid):
+    """Box reach (cells per axis) that holds a fluid cell for every solid cell
+    with psi <= 1.5 dn.  For such a cell G with boundary point S and unit
+    normal n, the point X = G + (psi + D/2 + eps) n, D = sqrt(sum_a h_a^2),
+    lies at distance D/2 + eps from the convex body (its closest point is S),
+    so the cell containing X has its centre outside: a fluid cell.  Along axis
+    a that centre is at most psi + D/2 + h_a/2 from G, and psi <= 1.5 dn <=
+    1.5 max_a h_a, hence at most ceil((1.5 max h + D/2) / h_a + 1/2) cells."""
+    h = grid.h
+    D = float(np.sqrt(sum(v * v for v in h)))
+    hm = max(h)
+    return [int(np.ceil((1.5 * hm + 0.5 * D) / h[a] + 0.5)) for a in range(grid.dim)]
+
+
+def _box_neighbour_any(grid, flag, reach):
+    """For each cell: does any in-grid cell within `reach[a]` cells along every
+    axis a (a box) have ``flag`` set?"""
+    f = flag.reshape(grid.n[::-1])
+    nd = grid.dim
+    out = f.copy()
+    for a in range(nd):
+        ax = nd - 1 - a
+        cur = out.copy()
+        for s_ in range(1, reach[a] + 1):
+            sl_lo = [slice(None)] * nd
+            sl_hi = [slice(None)] * nd
+            sl_lo[ax] = slice(0, -s_)
+            sl_hi[ax] = slice(s_, None)
+            cur[tuple(sl_lo)] |= out[tuple(sl_hi)]
+            cur[tuple(sl_hi)] |= out[tuple(sl_lo)]
+        out = cur
+    return out.reshape(-1)
+
+
+def classify(grid, body, placement=HGC, tie_rel=1e-9, cells=None, layers=1, layer_cells=None):
     """Tags and ghost records.  ``cells`` (optional, for the brute-force test)
-    evaluates psi on the given cell set instead of the interface cells."""
+    evaluates psi on the given cell set instead of the interface cells;
+    ``layer_cells`` likewise replaces the second layer's candidates."""
     if isinstance(grid, dict):
         grid = Grid.from_dict(grid)
     if isinstance(body, dict):
@@ -169,6 +215,34 @@ def classify(grid, body, placement=HGC, tie_rel=1e-9, cells=None):
     else:
         raise ValueError("unknown placement %r" % placement)
 
+    if layers == 2:
+        if placement not in (HGC, CGC_ES):
+            raise ValueError("a second ghost layer goes with HGC or CGC_ES")
+        # second layer: remaining solid cells with psi <= 1.5 dn
+        if layer_cells is None:
+            near = _box_neighbour_any(grid, ~solid, layer_reach(grid))
+            layer_cells = np.nonzero((tags == 1) & near)[0]
+        layer_cells = np.setdiff1d(np.asarray(layer_cells, dtype=np.int64), cells)
+        layer_cells = layer_cells[tags[layer_cells] == 1]
+        psi_l, n_l = closest_point(body, grid.centre(grid.unlin(layer_cells)))
+        if not np.all(psi_l >= 0):
+            raise AssertionError("second-layer candidate outside the body")
+        # the first layer's interface cells left solid are candidates too
+        back = (tags[cells] == 1)
+        cand = np.concatenate([cells[back], layer_cells])
+        psi_k = np.concatenate([psi_c[back], psi_l])
+        n_k = np.concatenate([n_c[back], n_l])
+        dn = delta_n(grid, n_k)
+        add = psi_k <= 1.5 * dn
+        for k in np.nonzero(np.abs(psi_k - 1.5 * dn) < tol)[0]:
+            ties.append((int(cand[k]), "psi~1.5dn", float(psi_k[k] - 1.5 * dn[k])))
+        tags[cand[add]] = 2
+        cells = np.concatenate([cells, layer_cells])
+        psi_c = np.concatenate([psi_c, psi_l])
+        n_c = np.concatenate([n_c, n_l])
+    elif layers != 1:
+        raise ValueError("layers must be 1 or 2")
+
     gmask = np.abs(tags[cells]) == 2
     g_cells = cells[gmask]
     order = np.argsort(g_cells)
@@ -177,7 +251,7 @@ def classify(grid, body, placement=HGC, tie_rel=1e-9, cells=None):
     n = n_c[gmask][order]
     e = np.where(n >= 0, 1, -1).astype(np.int64)          # sgn(n), 0 -> +1
     r = np.ones_like(e)
-    if placement == CGC_ES:
+    if placement == CGC_ES or layers == 2:
         for a in range(d):
             q = 2.0 * np.abs(psi * n[:, a]) / grid.h[a]
             r[:, a] = np.maximum(1, np.ceil(q)).astype(np.int64)
