@@ -64,6 +64,9 @@ typedef enum {
 } ebr_status;
 
 typedef enum { EBR_HGC = 0, EBR_CGC = 1, EBR_CGC_ES = 2 } ebr_placement;
+/* OR'ed into the placement of ebr_plan: a second ghost layer (Sec. 7,
+ * "Additional ghost-cell layers"), with EBR_HGC or EBR_CGC_ES. */
+#define EBR_SECOND_LAYER 16
 typedef enum { EBR_F32 = 0, EBR_F64 = 1 } ebr_dtype;
 typedef enum { EBR_DIRICHLET = 0, EBR_NEUMANN = 1 } ebr_bc;
 typedef enum { EBR_CIRCLE = 0, EBR_SPHERE = 1, EBR_ELLIPSE = 2, EBR_AIRFOIL4 = 3 } ebr_body_kind;
@@ -132,6 +135,13 @@ const char* ebr_last_error(const void* ctx);
  * a -2 cell without a tag-1 face neighbour becomes 0 and (afterwards) a +2
  * cell without a tag-0 face neighbour becomes 1; EBR_CGC_ES -- the CGC set with
  * the stencil multipliers of Eq. stencil_anisotropic.
+ * placement | EBR_SECOND_LAYER (EBR_HGC or EBR_CGC_ES): after the first
+ * layer is placed and reclassified, every remaining solid cell with
+ * psi <= 1.5 dn (Eq. delta_n, its own normal and widths) becomes a ghost
+ * (+2) too, and every ghost takes the multipliers of Eq. stencil_anisotropic
+ * (HGC's first layer keeps r = 1).  The interface list then also holds the
+ * solid cells within a box reach of a fluid cell (the candidates), and
+ * ebr_counts' n_interface counts them.
  * d_tags: caller-owned int8 [total cells] receiving 0, 1, +2, -2.
  * This call synchronises the stream (it sizes the context's buffers) and
  * must come first; later calls reuse the plan until the next ebr_plan. */
@@ -144,6 +154,19 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids,
  * context's ghost records; a count that differs from the plan sets EBR_ESHAPE
  * in the device status. */
 ebr_status ebr_classify(void* ctx, int8_t* d_tags, ebr_stream stream);
+
+/* Move the bodies of the planned geometry set (Sec. 7: a moving body is
+ * classified anew every step): h_bodies [n_geom] (host, copied) replace the
+ * bodies of ebr_plan, same kinds and grids; the geometry set is re-planned
+ * and classified into d_tags as by ebr_plan, and must be levelled again
+ * (ebr_build_levels) before the next fill.  Device buffers are reused: every
+ * buffer sized by the counts is grow-only (a buffer that is too small is
+ * replaced by one 25 % larger than needed), so a body that moves a little
+ * settles into the capacity after a few steps and its steps then allocate
+ * nothing (ebr_diagnostics h_out[11] counts allocations).  Synchronises the
+ * stream; not inside a stream capture; graphs captured before refer to the
+ * old plan and must be captured again.  On an invalid body nothing changes. */
+ebr_status ebr_move(void* ctx, const ebr_body* h_bodies, int8_t* d_tags, ebr_stream stream);
 
 /* Flat layout: h_cell_offset [n_geom + 1] (host) receives the cell offsets. */
 ebr_status ebr_layout(const void* ctx, int64_t* h_cell_offset);
@@ -366,7 +389,8 @@ ebr_status ebr_sync_status(void* ctx, ebr_stream stream);
  * the ghost-target source lists of the adjoint (after ebr_build_levels);
  * h_out[4..10] = schedule of the field-minor kernels (0 before their first
  * call): last grid-wide level of the fill and of its transpose, geometries
- * with a level tail in each, largest tail of each (ghosts), fluid targets.
+ * with a level tail in each, largest tail of each (ghosts), fluid targets;
+ * h_out[11] = device allocations the context has made so far.
  * n = entries wanted. */
 ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stream);
 

@@ -42,6 +42,7 @@ _SIGS = {
     "ebr_plan": (c_int32, [c_void_p, c_int32, ctypes.POINTER(Grid), ctypes.POINTER(Body), c_int32,
                            c_void_p, c_void_p]),
     "ebr_classify": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "ebr_move": (c_int32, [c_void_p, ctypes.POINTER(Body), c_void_p, c_void_p]),
     "ebr_layout": (c_int32, [c_void_p, ctypes.POINTER(c_int64)]),
     "ebr_counts": (c_int32, [c_void_p, ctypes.POINTER(GeomCounts)]),
     "ebr_build_levels": (c_int32, [c_void_p, c_void_p]),

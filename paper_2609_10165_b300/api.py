@@ -17,6 +17,7 @@ KIND = {"circle": 0, "sphere": 1, "ellipse": 2, "airfoil": 3}
 PLACEMENT = {"HGC": 0, "CGC": 1, "CGC_ES": 2}
 MODE = {"level": 0, "persistent": 1}
 DTYPE = {torch.float32: 0, torch.float64: 1}
+SECOND_LAYER = 16          # EBR_SECOND_LAYER
 
 
 def _grid_struct(g):
@@ -59,7 +60,7 @@ def _ptr_array(ts):
 class Reconstructor:
     """One planned geometry set (B >= 1 grids with bodies) on one device."""
 
-    def __init__(self, grids, bodies, placement="HGC", device=None):
+    def __init__(self, grids, bodies, placement="HGC", device=None, layers=1):
         self.lib = _lib.load()
         if isinstance(grids, dict):
             grids, bodies = [grids], [bodies]
@@ -74,8 +75,12 @@ class Reconstructor:
         self._bodies = (_lib.Body * self.B)(*[_body_struct(b) for b in bodies])
         ncell = sum(int(np.prod([g["n"][a] for a in range(int(g["dim"]))])) for g in grids)
         self.tags = torch.empty(ncell, dtype=torch.int8, device=self.device)
+        if layers not in (1, 2):
+            raise ValueError("layers must be 1 or 2")
+        self.layers = layers
+        flags = PLACEMENT[placement] | (SECOND_LAYER if layers == 2 else 0)
         self._check(self.lib.ebr_plan(self.ctx, self.B, self._grids, self._bodies,
-                                      PLACEMENT[placement], _ptr(self.tags), self._stream()))
+                                      flags, _ptr(self.tags), self._stream()))
         off = (ctypes.c_int64 * (self.B + 1))()
         self._check(self.lib.ebr_layout(self.ctx, off))
         self.cell_offset = np.array(list(off), dtype=np.int64)
@@ -109,6 +114,17 @@ class Reconstructor:
         t = self.tags if tags is None else tags
         self._check(self.lib.ebr_classify(self.ctx, _ptr(t), self._stream()))
         return t
+
+    def move(self, bodies):
+        """Move the bodies (same kinds and grids) and re-plan the geometry
+        set; levels must be built again before the next fill."""
+        if isinstance(bodies, dict):
+            bodies = [bodies]
+        if len(bodies) != self.B:
+            raise ValueError("move needs %d bodies" % self.B)
+        self._bodies = (_lib.Body * self.B)(*[_body_struct(b) for b in bodies])
+        self._check(self.lib.ebr_move(self.ctx, self._bodies, _ptr(self.tags), self._stream()))
+        self.levelled = False
 
     def build_levels(self):
         self._check(self.lib.ebr_build_levels(self.ctx, self._stream()))
@@ -238,14 +254,15 @@ class Reconstructor:
         self._check(self.lib.ebr_sync_status(self.ctx, self._stream()))
 
     def diagnostics(self):
-        out = (ctypes.c_int64 * 11)()
-        self._check(self.lib.ebr_diagnostics(self.ctx, out, 11, self._stream()))
+        out = (ctypes.c_int64 * 12)()
+        self._check(self.lib.ebr_diagnostics(self.ctx, out, 12, self._stream()))
         return {"row_fallbacks": int(out[0]), "r_max": int(out[1]), "launches": int(out[2]),
                 "n_gsrc": int(out[3]),
                 "packed": {"grid_levels_fill": int(out[4]), "grid_levels_adjoint": int(out[5]),
                            "tail_geometries_fill": int(out[6]), "tail_geometries_adjoint": int(out[7]),
                            "largest_tail_fill": int(out[8]), "largest_tail_adjoint": int(out[9]),
-                           "fluid_targets": int(out[10])}}
+                           "fluid_targets": int(out[10])},
+                "allocations": int(out[11])}
 
     def profile(self, enable=True):
         self._check(self.lib.ebr_profile(self.ctx, 1 if enable else 0))

@@ -52,10 +52,16 @@ struct Ctx {
   int device = 0;
   std::string err;
   long long launches = 0;
-  std::vector<DevBuf> bufs;    // every library allocation, freed at destroy
+  std::vector<DevBuf> bufs;    // allocations of the derived plans, freed at the next plan
+  struct Slot {
+    void* p = nullptr;
+    size_t cap = 0;
+  };
+  std::map<const void*, Slot> slots;   // grow-only buffers of the context's pointer members
+  long long n_alloc = 0;               // device allocations made so far
 
   // geometry set
-  int B = 0, placement = 0;
+  int B = 0, placement = 0, layers = 1;
   bool planned = false, levelled = false;
   std::vector<Geom> hG;
   std::vector<int> h_row_off;
@@ -225,9 +231,34 @@ ebr_status fail(Ctx* c, ebr_status s, const char* fmt, ...) {
                   __FILE__, __LINE__);                                                        \
   } while (0)
 
-template <typename T>
-ebr_status dalloc(Ctx* c, T** p, size_t count) {
-  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+// Device allocations.  A buffer held by a pointer member of the context is a
+// grow-only slot: a later plan of the same context (ebr_move, the next plan
+// of a moving body) reuses it when it is large enough and otherwise replaces
+// it with one 25 % larger than asked, so that the counts of a body that
+// moves a little settle into the capacity after a few steps.  Buffers of the
+// derived plans (chain, field-minor, temporaries) are listed in c->bufs and
+// released with them.
+ebr_status balloc(Ctx* c, void** p, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 16);
+  const char* a = reinterpret_cast<const char*>(p);
+  const bool member = a >= reinterpret_cast<const char*>(c) && a < reinterpret_cast<const char*>(c + 1);
+  if (member) {
+    Ctx::Slot& sl = c->slots[p];
+    if (sl.p && sl.cap >= bytes) { *p = sl.p; return EBR_OK; }
+    const size_t want = sl.p ? bytes + bytes / 4 : bytes;
+    if (sl.p) { cudaFree(sl.p); sl.p = nullptr; sl.cap = 0; }
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, EBR_ENOMEM, "cudaMalloc of %zu bytes failed: %s", want, cudaGetErrorString(e));
+    }
+    sl.p = q;
+    sl.cap = want;
+    ++c->n_alloc;
+    *p = q;
+    return EBR_OK;
+  }
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, bytes);
   if (e != cudaSuccess) {
@@ -235,21 +266,14 @@ ebr_status dalloc(Ctx* c, T** p, size_t count) {
     return fail(c, EBR_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
   }
   c->bufs.push_back({q, bytes});
-  *p = static_cast<T*>(q);
+  ++c->n_alloc;
+  *p = q;
   return EBR_OK;
 }
 
-ebr_status balloc(Ctx* c, void** p, size_t bytes) {
-  bytes = std::max<size_t>(bytes, 16);
-  void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(c, EBR_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
-  }
-  c->bufs.push_back({q, bytes});
-  *p = q;
-  return EBR_OK;
+template <typename T>
+ebr_status dalloc(Ctx* c, T** p, size_t count) {
+  return balloc(c, reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
 }
 
 #define AL(ptr, count)                                           \
@@ -263,19 +287,26 @@ void tiled_free(Ctx* c) {
   c->tiled = Ctx::Tiled();
 }
 
-void free_all(Ctx* c) {
+// the plans derived from the levels (chain, field-minor, tiled) and their buffers
+void release_derived(Ctx* c) {
   tiled_free(c);
-  for (auto& e : c->pool) cudaEventDestroy(e);
-  c->pool.clear();
-  c->pool_used = 0;
-  c->recs.clear();
   for (auto& b : c->bufs) cudaFree(b.p);
   c->bufs.clear();
   c->lamP = nullptr;
   c->lamP_bytes = 0;
   c->pplan = PackedPlan();
-  for (auto& kv : c->chain_plans) (void)kv;
   c->chain_plans.clear();
+}
+
+void free_all(Ctx* c) {
+  release_derived(c);
+  for (auto& e : c->pool) cudaEventDestroy(e);
+  c->pool.clear();
+  c->pool_used = 0;
+  c->recs.clear();
+  for (auto& kv : c->slots)
+    if (kv.second.p) cudaFree(kv.second.p);
+  c->slots.clear();
 }
 
 cudaStream_t S(ebr_stream s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -379,6 +410,12 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
     launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 1, s);
     prof_end(c, s);
     c->launches += 2;
+  }
+  if (c->layers == 2) {
+    prof_begin(c, s, "layer2");
+    launch_layer2(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->d_status, s);
+    prof_end(c, s);
+    c->launches += 1;
   }
   prof_begin(c, s, "ghost_flags");
   launch_ghost_flags(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->gflag, s);
@@ -586,6 +623,51 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
 }
 
 
+// Body of geometry b (kind, centre, radii or semi-axes, rotation, airfoil
+// parameters) and the float copies and margins derived from it; the grid
+// fields of g (dim, n, lo, h) are set already.
+ebr_status set_body(Ctx* c, Geom& g, const ebr_body& bd, int b) {
+  if (bd.kind < 0 || bd.kind > 3) return fail(c, EBR_EINVAL, "geometry %d: bad body kind", b);
+  const int want_dim = bd.kind == EBR_SPHERE ? 3 : 2;
+  if (want_dim != g.dim) return fail(c, EBR_EINVAL, "geometry %d: body kind needs dim %d", b, want_dim);
+  if ((bd.kind == EBR_CIRCLE || bd.kind == EBR_SPHERE) && !(bd.radii[0] > 0))
+    return fail(c, EBR_EINVAL, "geometry %d: radius must be positive", b);
+  if (bd.kind == EBR_ELLIPSE && !(bd.radii[0] > 0 && bd.radii[1] > 0))
+    return fail(c, EBR_EINVAL, "geometry %d: semi-axes must be positive", b);
+  if (bd.kind == EBR_AIRFOIL4 && !(bd.thickness > 0 && bd.chord > 0 && bd.rot[0] > 0))
+    return fail(c, EBR_EINVAL, "geometry %d: airfoil needs t > 0, chord > 0, |angle| < 90 deg", b);
+  g.kind = bd.kind;
+  for (int a = 0; a < 3; ++a) { g.centre[a] = bd.centre[a]; g.radii[a] = bd.radii[a]; }
+  for (int q = 0; q < 9; ++q) g.rot[q] = bd.rot[q];
+  g.t = bd.thickness;
+  g.c = bd.chord;
+  // float copies and the margin of the float HGC decision: it covers the
+  // float rounding of cell centres, body-frame coordinates, the float
+  // closest point and dn/2 by a wide factor (1e-4 of the finest width plus
+  // 4e-6 of the largest coordinate magnitude)
+  float hmin = 3.4e38f, ext = 1.0f;
+  for (int a = 0; a < 3; ++a) {
+    g.flo[a] = (float)g.lo[a];
+    g.fh[a] = (float)g.h[a];
+    g.fcentre[a] = (float)g.centre[a];
+    g.fradii[a] = (float)g.radii[a];
+    if (a < g.dim) {
+      hmin = std::min(hmin, (float)g.h[a]);
+      ext = std::max(ext, std::max(std::fabs((float)g.lo[a]), std::fabs((float)(g.lo[a] + g.n[a] * g.h[a]))));
+    }
+  }
+  for (int q = 0; q < 9; ++q) g.frot[q] = (float)g.rot[q];
+  g.ft = (float)g.t;
+  g.fc = (float)g.c;
+  g.hgc_mrg = 1e-4f * hmin + 4e-6f * ext;
+  float extc = 1.0f;
+  for (int a = 0; a < g.dim; ++a)
+    extc = std::max(extc, std::max(std::fabs((float)(g.lo[a] - g.centre[a])),
+                                   std::fabs((float)(g.lo[a] + g.n[a] * g.h[a] - g.centre[a]))));
+  g.fext = extc;
+  return EBR_OK;
+}
+
 // Chain plan for (kind of pass, dtype, F): geometries whose state fits in one
 // CTA's shared memory, largest first; the rest use level launches.
 ebr_status chain_plan(Ctx* c, int which, int dtype, int F, ChainPlan** out) {
@@ -657,10 +739,15 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const eb
   c->err.clear();
   if (n_geom < 1 || !h_grids || !h_bodies || !d_tags)
     return fail(c, EBR_EINVAL, "ebr_plan: n_geom >= 1 and non-null grids, bodies, tags required");
+  const int layers = (placement & EBR_SECOND_LAYER) ? 2 : 1;
+  placement &= ~EBR_SECOND_LAYER;
   if (placement < 0 || placement > 2) return fail(c, EBR_EINVAL, "ebr_plan: bad placement %d", placement);
+  if (layers == 2 && placement == EBR_CGC)
+    return fail(c, EBR_EINVAL, "ebr_plan: the second ghost layer goes with EBR_HGC or EBR_CGC_ES");
   free_all(c);
   c->B = n_geom;
   c->placement = placement;
+  c->layers = layers;
   c->planned = c->levelled = false;
   c->hG.assign(n_geom, Geom{});
   c->h_row_off.assign(n_geom + 1, 0);
@@ -671,9 +758,6 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const eb
     const ebr_body& bd = h_bodies[b];
     Geom& g = c->hG[b];
     if (gr.dim != 2 && gr.dim != 3) return fail(c, EBR_EINVAL, "geometry %d: dim must be 2 or 3", b);
-    int want_dim = bd.kind == EBR_SPHERE ? 3 : 2;
-    if (bd.kind < 0 || bd.kind > 3) return fail(c, EBR_EINVAL, "geometry %d: bad body kind", b);
-    if (want_dim != gr.dim) return fail(c, EBR_EINVAL, "geometry %d: body kind needs dim %d", b, want_dim);
     g.dim = gr.dim;
     long long n3 = 1;
     for (int a = 0; a < 3; ++a) {
@@ -686,44 +770,26 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const eb
       n3 *= na;
     }
     if (n3 > (1LL << 31) - 1) return fail(c, EBR_EINVAL, "geometry %d: more than 2^31-1 cells", b);
-    g.kind = bd.kind;
     g.placement = placement;
-    for (int a = 0; a < 3; ++a) { g.centre[a] = bd.centre[a]; g.radii[a] = bd.radii[a]; }
-    for (int q = 0; q < 9; ++q) g.rot[q] = bd.rot[q];
-    g.t = bd.thickness;
-    g.c = bd.chord;
-    // float copies and the margin of the float HGC decision: it covers the
-    // float rounding of cell centres, body-frame coordinates, the float
-    // closest point and dn/2 by a wide factor (1e-4 of the finest width plus
-    // 4e-6 of the largest coordinate magnitude)
+    // second layer: box reach per axis that holds a fluid cell for every
+    // solid cell with psi <= 1.5 dn: ceil((1.5 max h + |h| / 2) / h_a + 1/2)
+    g.layers = layers;
     {
-      float hmin = 3.4e38f, ext = 1.0f;
-      for (int a = 0; a < 3; ++a) {
-        g.flo[a] = (float)g.lo[a];
-        g.fh[a] = (float)g.h[a];
-        g.fcentre[a] = (float)g.centre[a];
-        g.fradii[a] = (float)g.radii[a];
-        if (a < g.dim) {
-          hmin = std::min(hmin, (float)g.h[a]);
-          ext = std::max(ext, std::max(std::fabs((float)g.lo[a]), std::fabs((float)(g.lo[a] + g.n[a] * g.h[a]))));
-        }
+      double hm = 0.0, D2 = 0.0;
+      for (int a = 0; a < gr.dim; ++a) {
+        const double ha = (gr.hi[a] - gr.lo[a]) / (double)gr.n[a];
+        hm = std::max(hm, ha);
+        D2 += ha * ha;
       }
-      for (int q = 0; q < 9; ++q) g.frot[q] = (float)g.rot[q];
-      g.ft = (float)g.t;
-      g.fc = (float)g.c;
-      g.hgc_mrg = 1e-4f * hmin + 4e-6f * ext;
-      float extc = 1.0f;
-      for (int a = 0; a < g.dim; ++a)
-        extc = std::max(extc, std::max(std::fabs((float)(g.lo[a] - g.centre[a])),
-                                       std::fabs((float)(g.lo[a] + g.n[a] * g.h[a] - g.centre[a]))));
-      g.fext = extc;
+      for (int a = 0; a < 3; ++a) {
+        const double ha = a < gr.dim ? (gr.hi[a] - gr.lo[a]) / (double)gr.n[a] : 1.0;
+        g.reach[a] = a < gr.dim ? (int)std::ceil((1.5 * hm + 0.5 * std::sqrt(D2)) / ha + 0.5) : 0;
+      }
     }
-    if ((bd.kind == EBR_CIRCLE || bd.kind == EBR_SPHERE) && !(bd.radii[0] > 0))
-      return fail(c, EBR_EINVAL, "geometry %d: radius must be positive", b);
-    if (bd.kind == EBR_ELLIPSE && !(bd.radii[0] > 0 && bd.radii[1] > 0))
-      return fail(c, EBR_EINVAL, "geometry %d: semi-axes must be positive", b);
-    if (bd.kind == EBR_AIRFOIL4 && !(bd.thickness > 0 && bd.chord > 0 && bd.rot[0] > 0))
-      return fail(c, EBR_EINVAL, "geometry %d: airfoil needs t > 0, chord > 0, |angle| < 90 deg", b);
+    {
+      ebr_status st = set_body(c, g, bd, b);
+      if (st) return st;
+    }
     g.cell_off = cells;
     g.row_off = rows;
     g.n_rows = g.n[1] * g.n[2];
@@ -774,6 +840,45 @@ ebr_status ebr_classify(void* ctx, int8_t* d_tags, ebr_stream stream) {
   if (!c->planned) return fail(c, EBR_EINVAL, "ebr_classify: call ebr_plan first");
   if (!d_tags) return fail(c, EBR_EINVAL, "ebr_classify: null tags");
   return run_classify(c, d_tags, S(stream), false);
+}
+
+ebr_status ebr_move(void* ctx, const ebr_body* h_bodies, int8_t* d_tags, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  c->err.clear();
+  if (c->B == 0 || c->hG.empty()) return fail(c, EBR_EINVAL, "ebr_move: call ebr_plan first");
+  if (!h_bodies || !d_tags) return fail(c, EBR_EINVAL, "ebr_move: null bodies or tags");
+  cudaStream_t s = S(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(c, EBR_EINVAL, "ebr_move: re-plans on the host; call it outside stream capture");
+  // every body first: on an error nothing changes
+  std::vector<Geom> hg = c->hG;
+  for (int b = 0; b < c->B; ++b) {
+    ebr_status st = set_body(c, hg[b], h_bodies[b], b);
+    if (st) return st;
+  }
+  CK(cudaStreamSynchronize(s));
+  if (c->side) CK(cudaStreamSynchronize(c->side));
+  release_derived(c);
+  c->hG = hg;
+  c->planned = c->levelled = false;
+  ebr_status st = upload_geoms(c);
+  if (st) return st;
+  CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(c->d_stats, 0, 4 * sizeof(int), s));
+  st = run_classify(c, d_tags, s, true);
+  if (st) return st;
+  int hs = 0;
+  CK(cudaMemcpyAsync(&hs, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hs != 0) {
+    CK(cudaMemset(c->d_status, 0, sizeof(int)));
+    return fail(c, (ebr_status)hs, "device status %d during classification", hs);
+  }
+  c->planned = true;
+  return EBR_OK;
 }
 
 ebr_status ebr_layout(const void* ctx, int64_t* h_cell_offset) {
@@ -1430,6 +1535,8 @@ ebr_status ebr_reconstruct_tiled(void* ctx, int32_t n_fields, void* const* d_fie
       return fail(c, EBR_EINVAL, "ebr_reconstruct_tiled: null field %d", f);
     if (h_bc_kind[f] != 0 && h_bc_kind[f] != 1) return fail(c, EBR_EINVAL, "ebr_reconstruct_tiled: bad bc kind");
   }
+  for (int b = 1; b < c->B; ++b)
+    if (c->hG[b].dim != c->hG[0].dim) return fail(c, EBR_EINVAL, "ebr_reconstruct_tiled: mixed dimensions");
   Ctx::Tiled& tp = c->tiled;
   if (tp.dev.n_tiles == 0 || tp.dev.Lmax == 0) return EBR_OK;
   cudaStream_t s = S(stream);
@@ -1438,7 +1545,7 @@ ebr_status ebr_reconstruct_tiled(void* ctx, int32_t n_fields, void* const* d_fie
   if (tp.spin_once > 0) A.spin_limit = tp.spin_once;
   tp.extra_once = tp.spin_once = 0;
   prof_begin(c, s, "tiled_fill");
-  cudaError_t e = launch_tiled_fill(dtype, n_fields, d_fields, h_bc_kind, d_bc, c->dG, A, tp.grid[dtype],
+  cudaError_t e = launch_tiled_fill(dtype, c->hG[0].dim, n_fields, d_fields, h_bc_kind, d_bc, c->dG, A, tp.grid[dtype],
                                     c->g_geo, c->g_cell, c->g_meta, c->g_dep, c->wtab, c->ng, tp.xbuf, tp.bar,
                                     extra, c->d_status, s);
   prof_end(c, s);
@@ -1574,6 +1681,7 @@ ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stre
   const PackedPlan& pp = c->pplan;
   const long long pk[7] = {pp.L0, pp.L0a, pp.n_tail, pp.n_tail_a, pp.tail_max, pp.tail_max_a, pp.n_ft};
   for (int k = 0; k < 7 && 4 + k < n; ++k) h_out[4 + k] = pp.built ? pk[k] : 0;
+  if (n > 11) h_out[11] = c->n_alloc;
   return EBR_OK;
 }
 

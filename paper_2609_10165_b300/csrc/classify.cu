@@ -635,6 +635,32 @@ __global__ void k_iface(const Geom* __restrict__ G, const int* __restrict__ row_
     add_diff(v, m, R, Q, n);
     add_diff(v, m, Q, R, n);
   }
+  // second ghost layer: the solid cells of the row with a fluid cell within
+  // the box reach (the run minus its erosion by the box: a cell stays out
+  // only when every in-grid row of the box has a run covering it with the
+  // reach to spare, a run end at the grid edge counting as covered), listed
+  // as band cells (flag 2)
+  int bandA = 1, bandB = 0, bandC = 1, bandD = 0;
+  if (g.layers == 2 && R.x <= R.y) {
+    int elo = 0, ehi = n - 1;
+    const int ry = g.reach[1], rz = g.dim == 3 ? g.reach[2] : 0, rx = g.reach[0];
+    for (int dk2 = -rz; dk2 <= rz && elo <= ehi; ++dk2)
+      for (int dj2 = -ry; dj2 <= ry && elo <= ehi; ++dj2) {
+        const int jj = j + dj2, kk = k + dk2;
+        if (jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
+        const int2 Q = (dj2 == 0 && dk2 == 0) ? R : runs[g.row_off + jj + ny * kk];
+        if (Q.x > Q.y) { elo = 1; ehi = 0; break; }
+        elo = max(elo, Q.x == 0 ? 0 : Q.x + rx);
+        ehi = min(ehi, Q.y == n - 1 ? n - 1 : Q.y - rx);
+      }
+    if (elo > ehi) { bandA = R.x; bandB = R.y; }
+    else {
+      bandA = R.x; bandB = min(R.y, elo - 1);
+      bandC = max(R.x, ehi + 1); bandD = R.y;
+    }
+    add_iv(v, m, bandA, bandB, n);
+    add_iv(v, m, bandC, bandD, n);
+  }
   // sort by start, merge
   for (int x = 1; x < m; ++x) {
     Iv key = v[x];
@@ -655,12 +681,29 @@ __global__ void k_iface(const Geom* __restrict__ G, const int* __restrict__ row_
   }
   int o = row_ptr[row];
   int rowbase = n * (j + ny * k);
+  // interface cells of the row: the run's ends and the cells across them,
+  // and the cells that differ from a face-neighbour row (the same sets as
+  // above); the rest of the list (second layer only) are band cells
   for (int x = 0; x < w; ++x) {
     for (int i = v[x].a; i <= v[x].b; ++i) {
       if (o >= cap) { set_status(status, S_ESHAPE); return; }
+      const bool sol = i >= R.x && i <= R.y;
+      int8_t flag = (int8_t)sol;
+      if (g.layers == 2 && sol && ((i >= bandA && i <= bandB) || (i >= bandC && i <= bandD))) {
+        // a band cell is an interface cell too when a face neighbour is fluid
+        bool face = i == R.x && R.x > 0;
+        face = face || (i == R.y && R.y < n - 1);
+        for (int q = 0; q < 4 && !face; ++q) {
+          const int jj = j + dj[q], kk = k + dk[q];
+          if (jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
+          const int2 Q = runs[g.row_off + jj + ny * kk];
+          if (!(i >= Q.x && i <= Q.y)) face = true;
+        }
+        if (!face) flag = 2;
+      }
       iface_cell[o] = rowbase + i;
       iface_geo[o] = b;
-      iface_solid[o] = (int8_t)(i >= R.x && i <= R.y);
+      iface_solid[o] = flag;
       ++o;
     }
   }
@@ -697,6 +740,12 @@ __global__ void k_place(const Geom* __restrict__ G, int n_iface, const int* __re
   int cell = iface_cell[m];
   bool solid = iface_solid[m] != 0;
   int8_t tag = solid ? 1 : 0;
+  if (iface_solid[m] == 2) {
+    // a band cell of the second layer (solid, no fluid face neighbour): the
+    // first layer leaves it solid; k_layer2 decides it after reclassification
+    tags[g.cell_off + cell] = 1;
+    return;
+  }
   if (placement != HGC) {
     tag = solid ? 2 : 0;   // solid interface cell = solid cell with a fluid face neighbour
   } else {
@@ -779,6 +828,54 @@ void launch_reclassify(const Geom* G, int n_iface, const int* iface_cell, const 
   k_reclassify<<<(n_iface + 127) / 128, 128, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, pass);
 }
 
+// Second ghost layer (Sec. 7): after the first layer's placement and
+// reclassification every listed cell still solid (tag 1) with psi <= 1.5 dn
+// (Eq. delta_n with its own normal and widths) becomes a ghost (+2).  Decided
+// in float where psi and 1.5 dn are clearly apart (three times the HGC
+// margin), in double otherwise.
+__global__ void k_layer2(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
+                         const int* __restrict__ iface_geo, int8_t* __restrict__ tags, int* status) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_iface) return;
+  const Geom& g = G[iface_geo[m]];
+  if (g.layers != 2) return;
+  const int cell = iface_cell[m];
+  int8_t* t = tags + g.cell_off + cell;
+  if (*t != 1) return;
+  int i, j, k;
+  cell_ijk(g, cell, i, j, k);
+  const float xf = g.flo[0] + ((float)i + 0.5f) * g.fh[0];
+  const float yf = g.flo[1] + ((float)j + 0.5f) * g.fh[1];
+  const float zf = g.dim == 3 ? g.flo[2] + ((float)k + 0.5f) * g.fh[2] : 0.0f;
+  float n32[3];
+  const float psi32 = closest_point_f32(g, xf, yf, zf, true, n32);
+  float s32 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.dim) continue;
+    const float q = n32[a] / g.fh[a];
+    s32 += q * q;
+  }
+  const float gap = fabsf(psi32) - 1.5f / sqrtf(s32);
+  bool add;
+  if (fabsf(gap) > 3.0f * g.hgc_mrg) {
+    add = gap <= 0.0f;
+  } else {
+    const double x = centre_of(g, 0, i), y = centre_of(g, 1, j);
+    const double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
+    double psi, nv[3];
+    if (!closest_point(g, x, y, z, true, psi, nv)) { set_status(status, S_EINVAL); return; }
+    add = psi <= 1.5 * delta_n(g, nv);
+  }
+  if (add) *t = 2;
+}
+
+void launch_layer2(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo, int8_t* tags,
+                   int* status, cudaStream_t s) {
+  if (n_iface <= 0) return;
+  k_layer2<<<(n_iface + 127) / 128, 128, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, status);
+}
+
 __global__ void k_ghost_flags(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
                               const int* __restrict__ iface_geo, const int8_t* __restrict__ tags,
                               int* __restrict__ flags) {
@@ -839,7 +936,7 @@ __global__ void k_ghost_geom(const Geom* __restrict__ G, int ng, int placement,
     if (a >= g.dim) continue;
     if (nv[a] < 0.0) meta |= 1u << a;
     int r = 1;
-    if (placement == CGC_ES) {
+    if (placement == CGC_ES || g.layers == 2) {
       // Eq. stencil_anisotropic: r_i = max(1, ceil(2 |n_i psi| / dx_i))
       double q = 2.0 * fabs(psi * nv[a]) / g.h[a];
       r = max(1, (int)ceil(q));

@@ -46,6 +46,10 @@ struct Geom {
   // per cell); hgc_mrg = safety margin of the float HGC decision
   float flo[3], fh[3], fcentre[3], fradii[3], frot[9], ft, fc, hgc_mrg;
   float fext;                // max(1, largest |grid corner - centre| over the axes)
+  // second ghost layer (Sec. 7): layers = 2 adds the solid cells with
+  // psi <= 1.5 dn; reach = box (cells per axis) holding a fluid cell for each
+  int layers;
+  int reach[3];
 };
 
 // ---------------------------------------------------------------------------

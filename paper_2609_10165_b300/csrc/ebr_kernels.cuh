@@ -51,6 +51,9 @@ void launch_place(const Geom* G, int n_iface, const int* iface_cell, const int* 
                   double* iface_n, int* status, cudaStream_t s, int T = 128);
 void launch_reclassify(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                        int8_t* tags, int pass, cudaStream_t s);
+// second ghost layer (geometries with layers == 2), after the reclassification
+void launch_layer2(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo, int8_t* tags,
+                   int* status, cudaStream_t s);
 void launch_ghost_flags(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                         const int8_t* tags, int* flags, cudaStream_t s);
 void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
@@ -164,7 +167,7 @@ int tiled_grid(int dtype, int n_tiles);
 // zeroes the barrier words and launches the cooperative fill; extra_arrivals
 // > 0 makes the first barrier wait for arrivals that never come (the bounded
 // wait then reports EBR_ETIMEOUT)
-cudaError_t launch_tiled_fill(int dtype, int F, void* const* fields, const int* bc_kind, const void* const* bc,
+cudaError_t launch_tiled_fill(int dtype, int dim, int F, void* const* fields, const int* bc_kind, const void* const* bc,
                               const Geom* G, const TiledPlanDev& A, int grid, const int* g_geo,
                               const int* g_cell, const uint32_t* g_meta, const int* g_dep, const double* wtab,
                               int ng, void* xbuf, unsigned* bar, int extra_arrivals, int* status,

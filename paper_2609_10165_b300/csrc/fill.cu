@@ -35,26 +35,52 @@ __device__ inline int member_cell(int dim, int cell, int nx, int ny, uint32_t m,
   return cell + off;
 }
 
-template <typename T>
-__global__ void k_fill_level(FieldSet P, int F, int dim, long long cell_off, int p0, int p1,
+// All loads of a ghost (weights, boundary data, member values of every
+// field) are issued before its stores: the members of a level-L ghost are
+// fluid cells or ghosts of lower levels, never written in this launch, so
+// the loads may run ahead of the stores; the sums keep the order boundary
+// term, then active members in member order.
+template <typename T, int D>
+__global__ void k_fill_level(FieldSet P, int F, long long cell_off, int p0, int p1,
                              const int* __restrict__ g_cell, const uint32_t* __restrict__ g_meta,
                              const double* __restrict__ wtab, int ng, int nx, int ny, int* status) {
+  constexpr int K = D == 2 ? 3 : 7;
   int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= p1) return;
-  const int K = stencil_k(dim);
-  int cell = g_cell[p];
-  uint32_t m = g_meta[p];
-  uint32_t act = meta_active(m);
-  for (int f = 0; f < F; ++f) {
-    T* fld = static_cast<T*>(P.f[f]) + cell_off;
-    const T* bc = static_cast<const T*>(P.bc[f]);
-    int kind = P.kind[f];
-    T acc = wload<T>(wtab, ng, kind, 7, p) * bc[p];
-    for (int k = 0; k < K; ++k) {
-      if (!(act >> k & 1u)) continue;
-      acc += wload<T>(wtab, ng, kind, k, p) * fld[member_cell(dim, cell, nx, ny, m, k)];
-    }
-    fld[cell] = acc;
+  const int cell = g_cell[p];
+  const uint32_t m = g_meta[p];
+  const uint32_t act = meta_active(m);
+  int mc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) mc[k] = member_cell(D, cell, nx, ny, m, k);
+  // weights of both boundary-condition kinds (selected per field below
+  // without a dynamic index, so that they stay in registers)
+  T w0[K + 1], w1[K + 1];
+  w0[K] = wload<T>(wtab, ng, 0, 7, p);
+  w1[K] = wload<T>(wtab, ng, 1, 7, p);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    w0[k] = wload<T>(wtab, ng, 0, k, p);
+    w1[k] = wload<T>(wtab, ng, 1, k, p);
+  }
+  T val[8][K + 1];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    if (f >= F) break;
+    const T* fld = static_cast<const T*>(P.f[f]) + cell_off;
+    val[f][K] = static_cast<const T*>(P.bc[f])[p];
+#pragma unroll
+    for (int k = 0; k < K; ++k) val[f][k] = (act >> k & 1u) ? fld[mc[k]] : T(0);
+  }
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    if (f >= F) break;
+    const bool neu = P.kind[f] != 0;
+    T acc = (neu ? w1[K] : w0[K]) * val[f][K];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (act >> k & 1u) acc += (neu ? w1[k] : w0[k]) * val[f][k];
+    static_cast<T*>(P.f[f])[cell_off + cell] = acc;
     if (!isfinite((double)acc)) set_status(status, S_ENONFINITE);
   }
 }
@@ -72,10 +98,15 @@ void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int
   }
   int n = p1 - p0;
   int T = n < 128 ? 64 : 128;
-  if (dtype == 0)
-    k_fill_level<float><<<(n + T - 1) / T, T, 0, s>>>(P, F, dim, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+  const unsigned nb = (unsigned)((n + T - 1) / T);
+  if (dtype == 0 && dim == 2)
+    k_fill_level<float, 2><<<nb, T, 0, s>>>(P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+  else if (dtype == 0)
+    k_fill_level<float, 3><<<nb, T, 0, s>>>(P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+  else if (dim == 2)
+    k_fill_level<double, 2><<<nb, T, 0, s>>>(P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
   else
-    k_fill_level<double><<<(n + T - 1) / T, T, 0, s>>>(P, F, dim, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+    k_fill_level<double, 3><<<nb, T, 0, s>>>(P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
 }
 
 // Partial sum of every ghost and field: w_s b_G plus the fluid (non-

@@ -66,7 +66,7 @@ __device__ bool tiled_barrier(unsigned* bar, unsigned target, int spin_limit, in
   return s_ok != 0;
 }
 
-template <typename T>
+template <typename T, int D>
 __global__ void __launch_bounds__(TL_T) k_tiled_fill(TiledFields P, int F, const Geom* __restrict__ G,
                                                      TiledPlanDev A, const int* __restrict__ g_geo,
                                                      const int* __restrict__ g_cell,
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(TL_T) k_tiled_fill(TiledFields P, int F, const
                                                      const double* __restrict__ wtab, int ng,
                                                      T* __restrict__ xbuf, unsigned* bar,
                                                      int extra_arrivals, int* status) {
+  constexpr int K = D == 2 ? 3 : 7;
   const int W = A.Lmax + 1;
   for (int L = 1; L <= A.Lmax; ++L) {
     for (int i = blockIdx.x; i < A.n_tiles; i += gridDim.x) {
@@ -82,35 +83,67 @@ __global__ void __launch_bounds__(TL_T) k_tiled_fill(TiledFields P, int F, const
       for (int e = a + threadIdx.x; e < b; e += TL_T) {
         const int p = A.t_list[e];
         const Geom& g = G[g_geo[p]];
-        const int dim = g.dim, K = stencil_k(dim), nx = g.n[0], ny = g.n[1];
+        const int nx = g.n[0], ny = g.n[1];
+        const long long cell_off = g.cell_off;
         const int cell = g_cell[p];
         const uint32_t m = g_meta[p];
         const uint32_t act = meta_active(m), dm = meta_depmask(m);
         const int tp = A.tile_of[p];
         const int slot = A.slot_of[p];
-        for (int f = 0; f < F; ++f) {
-          T* fld = static_cast<T*>(P.f[f]) + g.cell_off;
-          const T* bc = static_cast<const T*>(P.bc[f]);
-          const int kind = P.kind[f];
-          T acc = (T)wtab[(size_t)(kind * 8 + 7) * ng + p] * bc[p];
-          for (int k = 0; k < K; ++k) {
-            if (!(act >> k & 1u)) continue;
-            int o[3];
-            stencil_off(dim, k, o);
-            int off = o[0] * meta_r(m, 0) * meta_e(m, 0) + nx * (o[1] * meta_r(m, 1) * meta_e(m, 1));
-            if (dim == 3) off += nx * ny * (o[2] * meta_r(m, 2) * meta_e(m, 2));
-            T v;
-            if (dm >> k & 1u) {
-              // a ghost written during this launch: its own tile's from the
-              // field, another tile's from the exchange buffer (L2 reads)
-              const int d = g_dep[(size_t)k * ng + p];
-              v = A.tile_of[d] == tp ? __ldcg(fld + cell + off) : __ldcg(xbuf + (size_t)f * A.n_slots + A.slot_of[d]);
-            } else {
-              v = fld[cell + off];
-            }
-            acc += (T)wtab[(size_t)(kind * 8 + k) * ng + p] * v;
+        // where each member's value comes from: the field (fluid cells and
+        // this tile's ghosts, written at lower levels) or the exchange
+        // buffer (another tile's ghosts)
+        int mc[K], xs[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          int o[3];
+          stencil_off(D, k, o);
+          int off = o[0] * meta_r(m, 0) * meta_e(m, 0) + nx * (o[1] * meta_r(m, 1) * meta_e(m, 1));
+          if (D == 3) off += nx * ny * (o[2] * meta_r(m, 2) * meta_e(m, 2));
+          mc[k] = cell + off;
+          xs[k] = -1;
+          if (dm >> k & 1u) {
+            const int d = g_dep[(size_t)k * ng + p];
+            if (A.tile_of[d] != tp) xs[k] = A.slot_of[d];
           }
-          fld[cell] = acc;
+        }
+        T w0[K + 1], w1[K + 1];
+        w0[K] = (T)wtab[(size_t)7 * ng + p];
+        w1[K] = (T)wtab[(size_t)15 * ng + p];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          w0[k] = (T)wtab[(size_t)k * ng + p];
+          w1[k] = (T)wtab[(size_t)(8 + k) * ng + p];
+        }
+        // every load of the ghost before its stores (its members are never
+        // in its own level); values written during this launch are read
+        // through L2
+        T val[8][K + 1];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+          if (f >= F) break;
+          const T* fld = static_cast<const T*>(P.f[f]) + cell_off;
+          val[f][K] = static_cast<const T*>(P.bc[f])[p];
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            T v = T(0);
+            if (act >> k & 1u) {
+              if (xs[k] >= 0) v = __ldcg(xbuf + (size_t)f * A.n_slots + xs[k]);
+              else if (dm >> k & 1u) v = __ldcg(fld + mc[k]);
+              else v = fld[mc[k]];
+            }
+            val[f][k] = v;
+          }
+        }
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+          if (f >= F) break;
+          const bool neu = P.kind[f] != 0;
+          T acc = (neu ? w1[K] : w0[K]) * val[f][K];
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+            if (act >> k & 1u) acc += (neu ? w1[k] : w0[k]) * val[f][k];
+          static_cast<T*>(P.f[f])[cell_off + cell] = acc;
           if (slot >= 0) xbuf[(size_t)f * A.n_slots + slot] = acc;
           if (!isfinite((double)acc)) set_status(status, S_ENONFINITE);
         }
@@ -127,15 +160,16 @@ int tiled_grid(int dtype, int n_tiles) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // the 3D instances use the most registers: their residency bounds both
   if (dtype == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tiled_fill<float>, TL_T, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tiled_fill<float, 3>, TL_T, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tiled_fill<double>, TL_T, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tiled_fill<double, 3>, TL_T, 0);
   const long long cap = (long long)std::max(per, 1) * std::max(sms, 1);
   return (int)std::max<long long>(1, std::min<long long>(n_tiles, cap));
 }
 
-cudaError_t launch_tiled_fill(int dtype, int F, void* const* fields, const int* bc_kind, const void* const* bc,
+cudaError_t launch_tiled_fill(int dtype, int dim, int F, void* const* fields, const int* bc_kind, const void* const* bc,
                               const Geom* G, const TiledPlanDev& A, int grid, const int* g_geo,
                               const int* g_cell, const uint32_t* g_meta, const int* g_dep, const double* wtab,
                               int ng, void* xbuf, unsigned* bar, int extra_arrivals, int* status,
@@ -158,10 +192,16 @@ cudaError_t launch_tiled_fill(int dtype, int F, void* const* fields, const int* 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (dtype == 0)
-    return cudaLaunchKernelEx(&cfg, k_tiled_fill<float>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, wtab, ng,
+  if (dtype == 0 && dim == 2)
+    return cudaLaunchKernelEx(&cfg, k_tiled_fill<float, 2>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, wtab, ng,
                               static_cast<float*>(xbuf), bar, extra_arrivals, status);
-  return cudaLaunchKernelEx(&cfg, k_tiled_fill<double>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, wtab, ng,
+  if (dtype == 0)
+    return cudaLaunchKernelEx(&cfg, k_tiled_fill<float, 3>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, wtab, ng,
+                              static_cast<float*>(xbuf), bar, extra_arrivals, status);
+  if (dim == 2)
+    return cudaLaunchKernelEx(&cfg, k_tiled_fill<double, 2>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, wtab, ng,
+                              static_cast<double*>(xbuf), bar, extra_arrivals, status);
+  return cudaLaunchKernelEx(&cfg, k_tiled_fill<double, 3>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, wtab, ng,
                             static_cast<double*>(xbuf), bar, extra_arrivals, status);
 }
 

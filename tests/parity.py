@@ -47,11 +47,12 @@ def note_worst(key, ratio, value):
 
 
 class DeviceRun:
-    def __init__(self, geoms, placement, mode="persistent", dtype=torch.float64):
+    def __init__(self, geoms, placement, mode="persistent", dtype=torch.float64, layers=1):
         """geoms: list of workload dicts (grid, body, fields, bc, roles, mu)."""
         self.geoms = geoms
         self.dtype = dtype
-        self.R = Reconstructor([g["grid"] for g in geoms], [g["body"] for g in geoms], placement)
+        self.layers = layers
+        self.R = Reconstructor([g["grid"] for g in geoms], [g["body"] for g in geoms], placement, layers=layers)
         self.R.build_levels()
         self.R.sync_status()
         self.info = self.R.ghost_info()
@@ -101,10 +102,10 @@ def oracle_bcs(g, c, lev, f32=False):
     return out
 
 
-def oracle_run(g, placement, arrays, f32=False):
+def oracle_run(g, placement, arrays, f32=False, layers=1):
     """Oracle classification, levels and fill of one geometry, with the
     boundary data at the oracle's own S."""
-    c = O.classify(g["grid"], g["body"], placement)
+    c = O.classify(g["grid"], g["body"], placement, layers=layers)
     lev = O.build_levels(c)
     bcs = oracle_bcs(g, c, lev, f32)
     out = O.fill(c, lev, arrays, g["bc"], bcs)
@@ -165,7 +166,7 @@ def compare_structure(run, geoms, placement):
     info = run.info
     res = []
     for b, g in enumerate(geoms):
-        c = O.classify(g["grid"], g["body"], placement)
+        c = O.classify(g["grid"], g["body"], placement, layers=getattr(run, "layers", 1))
         assert c.ties == [], c.ties[:5]
         lev = O.build_levels(c)
         o0, o1 = run.R.cell_offset[b], run.R.cell_offset[b + 1]
