@@ -58,6 +58,7 @@ struct Ctx {
     size_t cap = 0;
   };
   std::map<const void*, Slot> slots;   // grow-only buffers of the context's pointer members
+  std::map<long long, Slot> chain_slots;  // grow-only geometry lists of the chain plans, by key
   long long n_alloc = 0;               // device allocations made so far
 
   // geometry set
@@ -238,27 +239,29 @@ ebr_status fail(Ctx* c, ebr_status s, const char* fmt, ...) {
 // moves a little settle into the capacity after a few steps.  Buffers of the
 // derived plans (chain, field-minor, temporaries) are listed in c->bufs and
 // released with them.
+ebr_status slot_alloc(Ctx* c, Ctx::Slot& sl, void** p, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 16);
+  if (sl.p && sl.cap >= bytes) { *p = sl.p; return EBR_OK; }
+  const size_t want = sl.p ? bytes + bytes / 4 : bytes;
+  if (sl.p) { cudaFree(sl.p); sl.p = nullptr; sl.cap = 0; }
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, EBR_ENOMEM, "cudaMalloc of %zu bytes failed: %s", want, cudaGetErrorString(e));
+  }
+  sl.p = q;
+  sl.cap = want;
+  ++c->n_alloc;
+  *p = q;
+  return EBR_OK;
+}
+
 ebr_status balloc(Ctx* c, void** p, size_t bytes) {
   bytes = std::max<size_t>(bytes, 16);
   const char* a = reinterpret_cast<const char*>(p);
   const bool member = a >= reinterpret_cast<const char*>(c) && a < reinterpret_cast<const char*>(c + 1);
-  if (member) {
-    Ctx::Slot& sl = c->slots[p];
-    if (sl.p && sl.cap >= bytes) { *p = sl.p; return EBR_OK; }
-    const size_t want = sl.p ? bytes + bytes / 4 : bytes;
-    if (sl.p) { cudaFree(sl.p); sl.p = nullptr; sl.cap = 0; }
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, want);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(c, EBR_ENOMEM, "cudaMalloc of %zu bytes failed: %s", want, cudaGetErrorString(e));
-    }
-    sl.p = q;
-    sl.cap = want;
-    ++c->n_alloc;
-    *p = q;
-    return EBR_OK;
-  }
+  if (member) return slot_alloc(c, c->slots[p], p, bytes);
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, bytes);
   if (e != cudaSuccess) {
@@ -307,6 +310,9 @@ void free_all(Ctx* c) {
   for (auto& kv : c->slots)
     if (kv.second.p) cudaFree(kv.second.p);
   c->slots.clear();
+  for (auto& kv : c->chain_slots)
+    if (kv.second.p) cudaFree(kv.second.p);
+  c->chain_slots.clear();
 }
 
 cudaStream_t S(ebr_stream s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -690,7 +696,11 @@ ebr_status chain_plan(Ctx* c, int which, int dtype, int F, ChainPlan** out) {
     }
   }
   cp.n_list = (int)list.size();
-  AL(cp.d_list, std::max<size_t>(list.size(), 1));
+  {
+    ebr_status st = slot_alloc(c, c->chain_slots[key], reinterpret_cast<void**>(&cp.d_list),
+                               sizeof(int) * std::max<size_t>(list.size(), 1));
+    if (st) return st;
+  }
   if (!list.empty())
     CK(cudaMemcpy(cp.d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice));
   c->chain_plans[key] = cp;
