@@ -811,6 +811,47 @@ def single_grid_mode(dev, stream, flush, steps, warmup, peak, tiles=((16, 16, 16
     return out
 
 
+def moving_mode(dev, n_geoms=32, steps=20, warmup=3, dt=0.02):
+    """Moving bodies (Sec. 7): the first n_geoms geometries of the batch, each
+    body translating and turning at a seeded rate, advanced step by step:
+    move (re-plan, reusing the device buffers), levels, boundary data at the
+    new boundary points, fill of 3 FP32 fields, forces and adjoint.  Every
+    step synchronises with the host (the counts change), so the step time is
+    taken on the host clock around a synchronised step."""
+    import torch
+    from paper_2609_10165_b300 import inputs as I
+    from paper_2609_10165_b300.moving import MovingStepper, RigidMotion
+
+    geoms = I.batch()[:n_geoms]
+    rng = np.random.default_rng(2609)
+    motions = [RigidMotion(g["body"], velocity=tuple(rng.uniform(-0.05, 0.05, 2)) + (0.0,),
+                           omega=float(rng.uniform(-0.5, 0.5)) if g["body"]["kind"] == "ellipse"
+                           else float(rng.uniform(-0.05, 0.05))) for g in geoms]
+    fields = [[g["fields"][f] for g in geoms] for f in range(3)]
+    st = MovingStepper([g["grid"] for g in geoms], motions, fields, geoms[0]["bc"], geoms[0]["roles"]["vel"],
+                       geoms[0]["roles"]["p"], geoms[0]["mu"], I.DRAG_LIFT_DIRS_2D, device=dev)
+    for _ in range(warmup):
+        st.advance(dt, adjoint=True)
+    torch.cuda.synchronize()
+    a0 = st.R.diagnostics()["allocations"]
+    ts, ups = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        out = st.advance(dt, adjoint=True)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+        ups.append(int(out[1]["cell"].size) * 3)
+    st.R.sync_status()
+    a1 = st.R.diagnostics()["allocations"]
+    ms = float(np.median(ts)) * 1e3
+    return {"what": "%d geometries of batch_256 moving (translation + rotation), per step: move + levels + "
+                    "boundary data + fill (3 FP32 fields) + forces + adjoint; host clock around a synchronised "
+                    "step" % n_geoms,
+            "ms_per_step": ms, "value": float(np.median(ups)) / (ms * 1e-3), "unit": UNIT,
+            "ghosts_min_max": [min(ups) // 3, max(ups) // 3], "allocations_in_timed_steps": a1 - a0,
+            "steps": steps}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -953,6 +994,10 @@ def main():
         single = single_grid_mode(dev, stream, flush, max(5, args.steps // 4), max(args.warmup, 3),
                                   measured_peaks()[0])
 
+    moving = None
+    if rank == 0 and not args.lite:
+        moving = moving_mode(dev)
+
     # plain FP64 path: one launch per level per geometry, FP64 fields, no graph
     ms64 = float("nan")
     try:
@@ -1050,6 +1095,7 @@ def main():
         "roofline": roof,
         "throughput_mode": tput,
         "single_grid": single,
+        "moving_bodies": moving,
         "clocks": clk,
         "cpu_baseline": baseline,
         "wall_s_timed": t_wall,

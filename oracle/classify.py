@@ -29,6 +29,9 @@ or -2 (centre in the fluid).
   Readings: the layer is added after the first layer's reclassification (the
   passes act on the first layer only), dn is that of Eq. delta_n with the
   cell's own normal and widths, and the rule is offered with HGC and CGC_ES.
+  A candidate at the exact centre of a circle or sphere (depth R, normal
+  undefined) stays solid when R > 1.5 max_a h_a, which no dn admits; a body
+  smaller than that has no defined second layer (error EINVAL).
   Candidates are the solid cells with a fluid cell within `layer_reach` cells
   along every axis (a box); the reach bounds the index distance from a solid
   cell with psi <= 1.5 dn to a fluid cell (see layer_reach).
@@ -224,6 +227,16 @@ def classify(grid, body, placement=HGC, tie_rel=1e-9, cells=None, layers=1, laye
             layer_cells = np.nonzero((tags == 1) & near)[0]
         layer_cells = np.setdiff1d(np.asarray(layer_cells, dtype=np.int64), cells)
         layer_cells = layer_cells[tags[layer_cells] == 1]
+        if body.kind in ("circle", "sphere"):
+            # a candidate at the body's centre has depth R and no normal: it
+            # stays solid when R > 1.5 max_a h_a (no dn <= max_a h_a admits
+            # it); otherwise the second layer is undefined there
+            Xl = grid.centre(grid.unlin(layer_cells))
+            at_c = np.all(Xl == body.centre[:d][None, :], axis=1)
+            if np.any(at_c):
+                if not body.radii[0] > 1.5 * max(grid.h):
+                    raise EBRError("EINVAL", "second-layer candidate at the centre of a small body")
+                layer_cells = layer_cells[~at_c]
         psi_l, n_l = closest_point(body, grid.centre(grid.unlin(layer_cells)))
         if not np.all(psi_l >= 0):
             raise AssertionError("second-layer candidate outside the body")

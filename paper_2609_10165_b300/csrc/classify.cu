@@ -844,6 +844,18 @@ __global__ void k_layer2(const Geom* __restrict__ G, int n_iface, const int* __r
   if (*t != 1) return;
   int i, j, k;
   cell_ijk(g, cell, i, j, k);
+  if (g.kind == CIRCLE || g.kind == SPHERE) {
+    // a candidate at the body's centre has depth R and no normal: it stays
+    // solid when R > 1.5 max_a h_a (no dn admits it), else the second layer
+    // is undefined there
+    const double dx = centre_of(g, 0, i) - g.centre[0], dy = centre_of(g, 1, j) - g.centre[1];
+    const double dz = g.dim == 3 ? centre_of(g, 2, k) - g.centre[2] : 0.0;
+    if (dx == 0.0 && dy == 0.0 && dz == 0.0) {
+      const double hm = fmax(fmax(g.h[0], g.h[1]), g.dim == 3 ? g.h[2] : 0.0);
+      if (!(g.radii[0] > 1.5 * hm)) set_status(status, S_EINVAL);
+      return;
+    }
+  }
   const float xf = g.flo[0] + ((float)i + 0.5f) * g.fh[0];
   const float yf = g.flo[1] + ((float)j + 0.5f) * g.fh[1];
   const float zf = g.dim == 3 ? g.flo[2] + ((float)k + 0.5f) * g.fh[2] : 0.0f;

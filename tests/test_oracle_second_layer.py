@@ -98,3 +98,18 @@ def test_layer_reach_bound():
     assert O.classify.__globals__["layer_reach"](O.Grid(2, [8, 8], [0, 0], [8, 8])) == [3, 3]
     assert O.classify.__globals__["layer_reach"](O.Grid(3, [8, 8, 8], [0] * 3, [8] * 3)) == [3, 3, 3]
     assert O.classify.__globals__["layer_reach"](O.Grid(2, [8, 8], [0, 0], [16, 8])) == [3, 5]
+
+
+def test_candidate_at_a_sphere_centre():
+    # a 17^3 grid whose centre cell is the sphere's centre: the candidate box
+    # reaches it; at depth R > 1.5 h it stays solid (the normal is undefined
+    # there, and no dn admits it)
+    gd = I.grid(3, [17, 17, 17], [-1.0, -1.0, -1.0], [1.0, 1.0, 1.0])
+    c = O.classify(gd, I.sphere(0.0, 0.0, 0.0, 0.55), "HGC", layers=2)
+    centre = int(c.grid.lin(np.array([[8, 8, 8]]))[0])
+    assert c.tags[centre] == 1
+    O.build_levels(c)
+    # the same body as a brute-force check of the whole layer
+    cb = O.classify(gd, I.sphere(0.0, 0.0, 0.0, 0.55), "HGC", layers=2,
+                    layer_cells=np.setdiff1d(np.arange(c.grid.N), [centre]))
+    assert np.array_equal(c.idx, cb.idx)
