@@ -40,7 +40,7 @@ unpinned" against the paper; see ``surface.face_weights``).
 """
 
 from .geometry import Grid, Body, closest_point, inside
-from .classify import classify, Classification, stencil_offsets, EBRError
+from .classify import classify, Classification, stencil_offsets, EBRError, ghost_x2
 from .levels import build_levels, Levels
 from .reconstruct import (fill, ghost_weights, ghost_value, vandermonde_ghost_value,
                           DIRICHLET, NEUMANN)
@@ -50,7 +50,7 @@ from . import tiles
 
 __all__ = [
     "Grid", "Body", "closest_point", "inside",
-    "classify", "Classification", "stencil_offsets", "EBRError",
+    "classify", "Classification", "stencil_offsets", "EBRError", "ghost_x2",
     "build_levels", "Levels",
     "fill", "ghost_weights", "ghost_value", "vandermonde_ghost_value",
     "DIRICHLET", "NEUMANN",

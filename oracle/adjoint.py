@@ -22,6 +22,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
+from .classify import ghost_x2
 from .reconstruct import ghost_weights
 from .surface import face_weights, ghost_force_term
 
@@ -41,7 +42,7 @@ def linear_map(cls, lev, bc_kinds):
         wsv = np.zeros(ng)
         for g in range(ng):
             q = int(pos[g])
-            w, ws = ghost_weights(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], bc)
+            w, ws = ghost_weights(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], bc, ghost_x2(cls, g))
             wsv[q] = ws
             for k in range(K):
                 if not lev.active[g, k]:
@@ -89,7 +90,7 @@ def force_coefficients(cls, lev, n_fields, p_id, vel_ids, mu, dirs, seed):
                     vv = [None] * d
                     vv[int(role[1:])] = uv
                 fp, fv = ghost_force_term(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g],
-                                          wf[g], mu, pv, vv)
+                                          wf[g], mu, pv, vv, ghost_x2(cls, g))
                 tot = fp + fv
                 c = seed[0] * float(tot @ dirs[0]) + seed[1] * float(tot @ dirs[1])
                 if c == 0.0:

@@ -78,7 +78,9 @@ def stencil_offsets(dim):
 class Classification:
     """Tags for every cell and the ghost records (sorted by linear index)."""
 
-    def __init__(self, grid, body, placement, tags, idx, psi, n, e, r, ties):
+    def __init__(self, grid, body, placement, tags, idx, psi, n, e, r, ties, x2=None, hw=None):
+        self.x2 = x2                # float64 [N_g, d]: x_2 - x_1 per ghost (stretched grids), else None
+        self.hw = hw                # float64 [N_g, d]: the ghost cell's widths (stretched grids), else None
         self.grid = grid
         self.body = body
         self.placement = placement
@@ -124,24 +126,39 @@ def _face_neighbour_any(grid, flag):
     return out.reshape(-1)
 
 
-def delta_n(grid, n):
-    """Eq. delta_n: normal cell thickness for unit normals n [M, d]."""
+def delta_n(grid, n, widths=None):
+    """Eq. delta_n: normal cell thickness for unit normals n [M, d], with the
+    cells' own widths [M, d] (a uniform grid's spacing when widths is None)."""
     s = np.zeros(n.shape[0])
     for a in range(grid.dim):
-        q = n[:, a] / grid.h[a]
+        q = n[:, a] / (grid.h[a] if widths is None else widths[:, a])
         s = s + q * q
     return 1.0 / np.sqrt(s)
 
 
+def ghost_x2(cls, g):
+    """x_2 - x_1 of ghost g (index order) on a stretched grid, else None (the
+    closed forms then take r e h)."""
+    return None if cls.x2 is None else cls.x2[g]
+
+
 def layer_reach(grid):
     """Box reach (cells per axis) that holds a fluid cell for every solid cell
-    with psi <= 1.5 dn.  For such a cell G with boundary point S and unit
+    with psi <= 1.5 dn (widths of a stretched grid bounded by hmax, counted in
+    units of the smallest width).  For such a cell G with boundary point S and unit
     normal n, the point X = G + (psi + D/2 + eps) n, D = sqrt(sum_a h_a^2),
     lies at distance D/2 + eps from the convex body (its closest point is S),
     so the cell containing X has its centre outside: a fluid cell.  Along axis
     a that centre is at most psi + D/2 + h_a/2 from G, and psi <= 1.5 dn <=
     1.5 max_a h_a, hence at most ceil((1.5 max h + D/2) / h_a + 1/2) cells."""
     h = grid.h
+    if getattr(grid, "stretched", False):
+        # stretched: the largest widths in the distances, the smallest width
+        # of the axis as the unit (the containing cell's half width included)
+        hx = grid.hmax
+        D = float(np.sqrt(sum(v * v for v in hx)))
+        hm = max(hx)
+        return [int(np.ceil((1.5 * hm + 0.5 * D + 0.5 * hx[a]) / h[a])) for a in range(grid.dim)]
     D = float(np.sqrt(sum(v * v for v in h)))
     hm = max(h)
     return [int(np.ceil((1.5 * hm + 0.5 * D) / h[a] + 0.5)) for a in range(grid.dim)]
@@ -200,7 +217,7 @@ def classify(grid, body, placement=HGC, tie_rel=1e-9, cells=None, layers=1, laye
         ghost_c = sol_c & _face_neighbour_any(grid, ~solid)[cells]
         tags[cells[ghost_c]] = 2
     elif placement == HGC:
-        dn = delta_n(grid, n_c)
+        dn = delta_n(grid, n_c, grid.widths(ijk) if grid.stretched else None)
         cand_s = sol_c & (psi_c <= dn / 2)
         cand_f = (~sol_c) & (-psi_c < dn / 2)
         for k in np.nonzero(np.abs(np.abs(psi_c) - dn / 2) < tol)[0]:
@@ -234,7 +251,7 @@ def classify(grid, body, placement=HGC, tie_rel=1e-9, cells=None, layers=1, laye
             Xl = grid.centre(grid.unlin(layer_cells))
             at_c = np.all(Xl == body.centre[:d][None, :], axis=1)
             if np.any(at_c):
-                if not body.radii[0] > 1.5 * max(grid.h):
+                if not body.radii[0] > 1.5 * max(grid.hmax):
                     raise EBRError("EINVAL", "second-layer candidate at the centre of a small body")
                 layer_cells = layer_cells[~at_c]
         psi_l, n_l = closest_point(body, grid.centre(grid.unlin(layer_cells)))
@@ -245,7 +262,7 @@ def classify(grid, body, placement=HGC, tie_rel=1e-9, cells=None, layers=1, laye
         cand = np.concatenate([cells[back], layer_cells])
         psi_k = np.concatenate([psi_c[back], psi_l])
         n_k = np.concatenate([n_c[back], n_l])
-        dn = delta_n(grid, n_k)
+        dn = delta_n(grid, n_k, grid.widths(grid.unlin(cand)) if grid.stretched else None)
         add = psi_k <= 1.5 * dn
         for k in np.nonzero(np.abs(psi_k - 1.5 * dn) < tol)[0]:
             ties.append((int(cand[k]), "psi~1.5dn", float(psi_k[k] - 1.5 * dn[k])))
@@ -264,14 +281,25 @@ def classify(grid, body, placement=HGC, tie_rel=1e-9, cells=None, layers=1, laye
     n = n_c[gmask][order]
     e = np.where(n >= 0, 1, -1).astype(np.int64)          # sgn(n), 0 -> +1
     r = np.ones_like(e)
+    hw = grid.widths(grid.unlin(g_cells)) if grid.stretched else None
     if placement == CGC_ES or layers == 2:
         for a in range(d):
-            q = 2.0 * np.abs(psi * n[:, a]) / grid.h[a]
+            q = 2.0 * np.abs(psi * n[:, a]) / (grid.h[a] if hw is None else hw[:, a])
             r[:, a] = np.maximum(1, np.ceil(q)).astype(np.int64)
             near = (q > 1.0 - 1e-9) & (np.abs(q - np.round(q)) < 1e-9)
             for k in np.nonzero(near)[0]:
                 ties.append((int(g_cells[k]), "r%d ceil" % a, float(q[k])))
-    return Classification(grid, body, placement, tags, g_cells, psi, n, e, r, ties)
+    x2 = None
+    if grid.stretched:
+        # x_2 - x_1: centre of the cell r_i e_i cells away minus the ghost's
+        # (indices clipped into the grid; a stencil that leaves it is an error
+        # raised by check_stencils)
+        gijk = grid.unlin(g_cells)
+        x2 = np.zeros((g_cells.size, d))
+        for a in range(d):
+            far = np.clip(gijk[:, a] + r[:, a] * e[:, a], 0, grid.n[a] - 1)
+            x2[:, a] = grid.cen[a][far] - grid.cen[a][gijk[:, a]]
+    return Classification(grid, body, placement, tags, g_cells, psi, n, e, r, ties, x2=x2, hw=hw)
 
 
 def stencil_members(cls):

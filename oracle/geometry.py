@@ -25,30 +25,61 @@ AIRFOIL_A = (0.2969, -0.1260, -0.3516, 0.2843, -0.1015)
 
 
 class Grid:
-    """Uniform cell-centred Cartesian grid.
+    """Cell-centred Cartesian grid, uniform or stretched.
 
-    Cell (i, j[, k]) has centre lo_a + (i_a + 1/2) h_a with h_a = (hi_a - lo_a) / n_a
-    and linear index i + n_x (j + n_y k) (x fastest).
+    Uniform: cell (i, j[, k]) has centre lo_a + (i_a + 1/2) h_a with
+    h_a = (hi_a - lo_a) / n_a.  Stretched (``faces`` given: per axis the n_a + 1
+    increasing face coordinates): cell i_a spans [f_a(i_a), f_a(i_a + 1)], its
+    centre is the midpoint and its width the difference (Sec. 7: local mesh
+    spacing dx_i).  Linear index i + n_x (j + n_y k) (x fastest).
+
+    ``h`` holds the spacing of a uniform grid, the smallest width per axis of a
+    stretched one; ``hmax`` the largest.
     """
 
-    def __init__(self, dim, n, lo, hi):
+    def __init__(self, dim, n, lo, hi, faces=None):
         self.dim = int(dim)
         self.n = tuple(int(n[a]) for a in range(self.dim))
-        self.lo = tuple(float(lo[a]) for a in range(self.dim))
-        self.hi = tuple(float(hi[a]) for a in range(self.dim))
-        self.h = tuple((self.hi[a] - self.lo[a]) / self.n[a] for a in range(self.dim))
+        self.stretched = faces is not None
+        if self.stretched:
+            self.faces = [np.asarray(faces[a], dtype=np.float64) for a in range(self.dim)]
+            for a in range(self.dim):
+                if self.faces[a].size != self.n[a] + 1 or not np.all(np.diff(self.faces[a]) > 0):
+                    raise ValueError("axis %d needs %d increasing faces" % (a, self.n[a] + 1))
+            self.lo = tuple(float(self.faces[a][0]) for a in range(self.dim))
+            self.hi = tuple(float(self.faces[a][-1]) for a in range(self.dim))
+            self.cen = [0.5 * (f[:-1] + f[1:]) for f in self.faces]
+            self.wid = [np.diff(f) for f in self.faces]
+            self.h = tuple(float(w.min()) for w in self.wid)
+            self.hmax = tuple(float(w.max()) for w in self.wid)
+        else:
+            self.lo = tuple(float(lo[a]) for a in range(self.dim))
+            self.hi = tuple(float(hi[a]) for a in range(self.dim))
+            self.h = tuple((self.hi[a] - self.lo[a]) / self.n[a] for a in range(self.dim))
+            self.hmax = self.h
         self.N = int(np.prod(self.n))
 
     @classmethod
     def from_dict(cls, d):
-        return cls(d["dim"], d["n"], d["lo"], d["hi"])
+        return cls(d["dim"], d["n"], d["lo"], d["hi"], d.get("faces"))
 
     def centre(self, ijk):
         """Cell centres for integer index arrays ijk [M, dim] -> [M, dim] float64."""
         ijk = np.asarray(ijk, dtype=np.int64).reshape(-1, self.dim)
         out = np.empty(ijk.shape, dtype=np.float64)
         for a in range(self.dim):
-            out[:, a] = self.lo[a] + (ijk[:, a].astype(np.float64) + 0.5) * self.h[a]
+            if self.stretched:
+                out[:, a] = self.cen[a][ijk[:, a]]
+            else:
+                out[:, a] = self.lo[a] + (ijk[:, a].astype(np.float64) + 0.5) * self.h[a]
+        return out
+
+    def widths(self, ijk):
+        """Cell widths [M, dim] of the cells ijk [M, dim]."""
+        ijk = np.asarray(ijk, dtype=np.int64).reshape(-1, self.dim)
+        out = np.empty(ijk.shape, dtype=np.float64)
+        for a in range(self.dim):
+            out[:, a] = self.wid[a][ijk[:, a]] if self.stretched else self.h[a]
         return out
 
     def lin(self, ijk):

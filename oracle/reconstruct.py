@@ -22,24 +22,29 @@ to pin the closed forms.  ``fill`` applies the closed forms level by level
 
 import numpy as np
 
-from .classify import stencil_offsets
+from .classify import ghost_x2, stencil_offsets
 
 DIRICHLET, NEUMANN = 0, 1
 LD = np.longdouble
 
 
-def local_points(h, psi, n, e, r):
-    """(x2 [d], xs [d]) in local coordinates (origin at G)."""
+def local_points(h, psi, n, e, r, x2=None):
+    """(x2 [d], xs [d]) in local coordinates (origin at G): x_2 = r e h on a
+    uniform grid; on a stretched grid the given x_2 - x_1 (the centre of the
+    cell r_i e_i cells away, Sec. 7 with the local spacing)."""
     d = len(h)
-    x2 = np.array([r[a] * e[a] * h[a] for a in range(d)], dtype=np.float64)
+    if x2 is None:
+        x2 = np.array([r[a] * e[a] * h[a] for a in range(d)], dtype=np.float64)
+    else:
+        x2 = np.asarray(x2, dtype=np.float64)
     xs = np.array([psi * n[a] for a in range(d)], dtype=np.float64)
     return x2, xs
 
 
-def ghost_weights(h, psi, n, e, r, bc):
+def ghost_weights(h, psi, n, e, r, bc, x2=None):
     """Weights (w [K] on P_1..P_K, ws on the boundary datum)."""
     d = len(h)
-    x2, xs = local_points(h, psi, n, e, r)
+    x2, xs = local_points(h, psi, n, e, r, x2)
     if d == 2:
         x1 = y1 = 0.0
         X2, Y2 = x2
@@ -95,8 +100,8 @@ def ghost_weights(h, psi, n, e, r, bc):
     return w, ws
 
 
-def ghost_value(h, psi, n, e, r, bc, phi_members, datum):
-    w, ws = ghost_weights(h, psi, n, e, r, bc)
+def ghost_value(h, psi, n, e, r, bc, phi_members, datum, x2=None):
+    w, ws = ghost_weights(h, psi, n, e, r, bc, x2)
     return float(np.dot(w, phi_members) + ws * datum)
 
 
@@ -120,11 +125,11 @@ def _solve_ld(A, b):
     return x
 
 
-def vandermonde_ghost_value(h, psi, n, e, r, bc, phi_members, datum):
+def vandermonde_ghost_value(h, psi, n, e, r, bc, phi_members, datum, x2=None):
     """C_0 of the (bi/tri)linear interpolant through the stencil and the
     boundary condition: the Appendix A system, solved directly."""
     d = len(h)
-    x2, xs = local_points(h, psi, n, e, r)
+    x2, xs = local_points(h, psi, n, e, r, x2)
     offs = stencil_offsets(d)
     if d == 2:
         def row(p):
@@ -170,7 +175,7 @@ def fill(cls, lev, fields, bc_kinds, bc_data):
         for fi, arr in enumerate(out):
             bc = bc_kinds[fi]
             if (g, bc) not in W:
-                W[(g, bc)] = ghost_weights(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], bc)
+                W[(g, bc)] = ghost_weights(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], bc, ghost_x2(cls, g))
             w, ws = W[(g, bc)]
             acc = ws * float(bc_data[fi][p])
             for k in range(w.size):

@@ -25,6 +25,7 @@ import math
 
 import numpy as np
 
+from .classify import ghost_x2
 from .reconstruct import ghost_weights, DIRICHLET
 
 
@@ -32,16 +33,16 @@ def _members_values(lev, g, arr, K):
     return np.array([arr[lev.midx[g, k]] for k in range(K)], dtype=np.float64)
 
 
-def phi_s(h, psi, n, e, r, phi_g, phi_m):
+def phi_s(h, psi, n, e, r, phi_g, phi_m, x2=None):
     """Eq. phi_G_Dir_2d / _3d solved for phi_s."""
-    w, ws = ghost_weights(h, psi, n, e, r, DIRICHLET)
+    w, ws = ghost_weights(h, psi, n, e, r, DIRICHLET, x2)
     return (phi_g - float(np.dot(w, phi_m))) / ws
 
 
-def gradient_at_s(h, psi, n, e, r, phi_g, phi_m):
+def gradient_at_s(h, psi, n, e, r, phi_g, phi_m, x2=None):
     """Eq. derivative_bilinear (2D) or Eqs. derivative_trilinear_x/y/z (3D)."""
     d = len(h)
-    x2 = [r[a] * e[a] * h[a] for a in range(d)]
+    x2 = [r[a] * e[a] * h[a] for a in range(d)] if x2 is None else [float(v) for v in x2]
     xs = [psi * n[a] for a in range(d)]
     if d == 2:
         x1 = y1 = 0.0
@@ -88,8 +89,9 @@ def boundary_quantities(cls, lev, arr):
         g = int(lev.order[p])
         pm = _members_values(lev, g, arr, K)
         pg = float(arr[cls.idx[g]])
-        ps[p] = phi_s(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], pg, pm)
-        gr[p] = gradient_at_s(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], pg, pm)
+        x2 = ghost_x2(cls, g)
+        ps[p] = phi_s(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], pg, pm, x2)
+        gr[p] = gradient_at_s(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], pg, pm, x2)
     return ps, gr
 
 
@@ -99,12 +101,13 @@ def face_weights(cls):
     g = cls.grid
     d = g.dim
     ijk = g.unlin(cls.idx)
+    wid = g.widths(ijk)                      # the ghost cells' own widths
     w = np.zeros(cls.n_ghosts)
     for a in range(d):
-        area = 1.0
+        area = np.ones(cls.n_ghosts)
         for b in range(d):
             if b != a:
-                area *= g.h[b]
+                area = area * wid[:, b]
         for s in (-1, 1):
             nb = ijk.copy()
             nb[:, a] += s
@@ -115,7 +118,7 @@ def face_weights(cls):
     return w
 
 
-def ghost_force_term(h, psi, n, e, r, wG, mu, p_vals, vel_vals):
+def ghost_force_term(h, psi, n, e, r, wG, mu, p_vals, vel_vals, x2=None):
     """Per-ghost traction times weight: (Fp [d], Fv [d]).
 
     p_vals / vel_vals[i]: (value at G, values at P_1..P_K) of the filled
@@ -123,12 +126,12 @@ def ghost_force_term(h, psi, n, e, r, wG, mu, p_vals, vel_vals):
     """
     d = len(h)
     pg, pm = p_vals
-    ps = phi_s(h, psi, n, e, r, pg, pm)
+    ps = phi_s(h, psi, n, e, r, pg, pm, x2)
     G = np.zeros((d, d))                    # G[i, j] = d u_i / d x_j at S
     for i in range(d):
         if vel_vals[i] is not None:
             ug, um = vel_vals[i]
-            G[i] = gradient_at_s(h, psi, n, e, r, ug, um)
+            G[i] = gradient_at_s(h, psi, n, e, r, ug, um, x2)
     fp = -ps * np.asarray(n, dtype=np.float64)
     fv = mu * ((G + G.T) @ np.asarray(n, dtype=np.float64))
     return wG * fp, wG * fv
@@ -152,7 +155,8 @@ def forces(cls, lev, p_arr, vel_arrs, mu, dirs):
         pv = (float(p_arr[cls.idx[g]]), _members_values(lev, g, p_arr, K))
         vv = [None if a is None else (float(a[cls.idx[g]]), _members_values(lev, g, a, K))
               for a in vel_arrs]
-        fp, fv = ghost_force_term(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], wf[g], mu, pv, vv)
+        fp, fv = ghost_force_term(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], wf[g], mu, pv, vv,
+                                  ghost_x2(cls, g))
         terms_p.append(fp)
         terms_v.append(fv)
     terms_p = np.array(terms_p).reshape(-1, d)

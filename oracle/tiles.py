@@ -28,6 +28,7 @@ per axis, in cells; tile t of cell (i, j, k) = (i // T_x) + n_tx ((j // T_y)
 
 import numpy as np
 
+from .classify import ghost_x2
 from .reconstruct import ghost_weights
 
 
@@ -95,7 +96,7 @@ def tiled_fill(cls, lev, arrays, bc_kinds, bcs, tile):
             t = int(tl[g])
             mine = held.setdefault(t, {})
             for f, (arr, kind, b) in enumerate(zip(arrays, bc_kinds, bcs)):
-                w, ws = ghost_weights(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], kind)
+                w, ws = ghost_weights(h, cls.psi[g], cls.n[g], cls.e[g], cls.r[g], kind, ghost_x2(cls, g))
                 v = ws * float(b[q])
                 for k in range(K):
                     if not lev.active[g, k]:

@@ -56,6 +56,36 @@ def grid(dim, n, lo, hi):
             "hi": [float(v) for v in hi]}
 
 
+def axis_centres(g, a):
+    """Cell centres along axis a of grid dict g: face midpoints of a stretched
+    grid, lo + (i + 1/2) h of a uniform one."""
+    if "faces" in g:
+        f = np.asarray(g["faces"][a], dtype=np.float64)
+        return 0.5 * (f[:-1] + f[1:])
+    n = g["n"]
+    return g["lo"][a] + (np.arange(n[a], dtype=np.float64) + 0.5) * ((g["hi"][a] - g["lo"][a]) / n[a])
+
+
+def stretched_axis(lo, hi, n, ratio=1.03, centre_frac=0.5):
+    """n + 1 increasing faces on [lo, hi] whose widths grow geometrically by
+    `ratio` per cell away from the point centre_frac of the axis (the
+    stretching of the paper's meshes, here applied everywhere so that the
+    ghost stencils see it)."""
+    c = centre_frac * n
+    w = np.array([ratio ** abs(i + 0.5 - c) for i in range(n)], dtype=np.float64)
+    w *= (hi - lo) / w.sum()
+    f = np.concatenate([[lo], lo + np.cumsum(w)])
+    f[-1] = hi
+    return f
+
+
+def stretched_grid(dim, n, lo, hi, ratio=(1.03, 1.03, 1.03), centre_frac=(0.5, 0.5, 0.5)):
+    """Grid dict with explicit faces per axis (stretched_axis)."""
+    g = grid(dim, n, lo, hi)
+    g["faces"] = [stretched_axis(lo[a], hi[a], int(n[a]), ratio[a], centre_frac[a]).tolist() for a in range(dim)]
+    return g
+
+
 def circle(cx, cy, r):
     return {"kind": "circle", "centre": [cx, cy, 0.0], "radii": [r, r, 0.0], "rot": IDENT,
             "thickness": 0.0, "chord": 0.0}
@@ -123,8 +153,7 @@ class FourierField:
     def on_grid(self, g, dtype=np.float64):
         """Values at every cell centre of grid dict ``g``, flattened x-fastest."""
         n = g["n"]
-        cen = [g["lo"][a] + (np.arange(n[a], dtype=np.float64) + 0.5) * ((g["hi"][a] - g["lo"][a]) / n[a])
-               for a in range(self.dim)]
+        cen = [axis_centres(g, a) for a in range(self.dim)]
         B = [self._basis(a, cen[a])[0] for a in range(self.dim)]
         if self.dim == 2:
             return (B[1] @ self.a.T @ B[0].T).astype(dtype).reshape(-1)   # [ny, nx]
@@ -150,9 +179,8 @@ class CylinderU:
         return np.stack([2 * math.pi * cx * cy, -2 * math.pi * sx * sy], axis=1)
 
     def on_grid(self, g, dtype=np.float64):
-        n = g["n"]
-        x = g["lo"][0] + (np.arange(n[0]) + 0.5) * ((g["hi"][0] - g["lo"][0]) / n[0])
-        y = g["lo"][1] + (np.arange(n[1]) + 0.5) * ((g["hi"][1] - g["lo"][1]) / n[1])
+        x = axis_centres(g, 0)
+        y = axis_centres(g, 1)
         return (np.cos(2 * math.pi * y)[:, None] * np.sin(2 * math.pi * x)[None, :]).astype(dtype).reshape(-1)
 
 
@@ -171,8 +199,7 @@ class Quadratic:
 
     def on_grid(self, g, dtype=np.float64):
         n = g["n"]
-        cen = [g["lo"][a] + (np.arange(n[a]) + 0.5) * ((g["hi"][a] - g["lo"][a]) / n[a])
-               for a in range(self.dim)]
+        cen = [axis_centres(g, a) for a in range(self.dim)]
         if self.dim == 2:
             v = cen[1][:, None] ** 2 + cen[0][None, :] ** 2
         else:
@@ -212,8 +239,7 @@ class Polynomial:
 
     def on_grid(self, g, dtype=np.float64):
         n = g["n"][: self.dim]
-        axes = [g["lo"][a] + (np.arange(n[a]) + 0.5) * ((g["hi"][a] - g["lo"][a]) / n[a])
-                for a in range(self.dim)]
+        axes = [axis_centres(g, a) for a in range(self.dim)]
         mesh = np.meshgrid(*axes[::-1], indexing="ij")[::-1]
         X = np.stack([m.reshape(-1) for m in mesh], axis=1)
         return self.value(X).astype(dtype)

@@ -144,7 +144,7 @@ def term_magnitude(c, lev, arrays, bcs, kinds):
         t = np.zeros(ng)
         for p in range(ng):
             g = int(lev.order[p])
-            w, ws = O.ghost_weights(h, c.psi[g], c.n[g], c.e[g], c.r[g], kinds[fi])
+            w, ws = O.ghost_weights(h, c.psi[g], c.n[g], c.e[g], c.r[g], kinds[fi], O.ghost_x2(c, g))
             acc = abs(ws * b[p])
             for k in range(w.size):
                 if not lev.active[g, k]:
