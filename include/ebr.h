@@ -149,6 +149,20 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids,
                     const ebr_body* h_bodies, int32_t placement, int8_t* d_tags,
                     ebr_stream stream);
 
+/* ebr_plan on stretched grids (Sec. 7: the local mesh spacing; the meshes of
+ * Secs. 8.1 and 8.2 are stretched away from the body).  h_faces: host array
+ * [n_geom] of host pointers; h_faces[b] holds the cell faces of geometry b,
+ * n_x + 1 strictly increasing x-faces, then n_y + 1 y-faces (then n_z + 1
+ * z-faces), copied; NULL makes that grid uniform (its lo, hi).  For a
+ * stretched grid lo and hi are taken from the first and last faces.  Cell
+ * centres are the face midpoints, widths the face differences; Eq. delta_n
+ * and Eq. stencil_anisotropic use the ghost cell's own widths, the closed
+ * forms the stencil's actual x_2 - x_1 (the centre of the cell r_i e_i cells
+ * away minus the ghost's), the surface weights the ghost cell's face areas.
+ * Everything else as ebr_plan. */
+ebr_status ebr_plan_faces(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const double* const* h_faces,
+                          const ebr_body* h_bodies, int32_t placement, int8_t* d_tags, ebr_stream stream);
+
 /* Re-run the classification of the planned geometry set without host
  * synchronisation (capturable in a CUDA graph).  Writes d_tags and the
  * context's ghost records; a count that differs from the plan sets EBR_ESHAPE

@@ -41,6 +41,8 @@ _SIGS = {
     "ebr_last_error": (ctypes.c_char_p, [c_void_p]),
     "ebr_plan": (c_int32, [c_void_p, c_int32, ctypes.POINTER(Grid), ctypes.POINTER(Body), c_int32,
                            c_void_p, c_void_p]),
+    "ebr_plan_faces": (c_int32, [c_void_p, c_int32, ctypes.POINTER(Grid), ctypes.POINTER(c_void_p),
+                                 ctypes.POINTER(Body), c_int32, c_void_p, c_void_p]),
     "ebr_classify": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "ebr_move": (c_int32, [c_void_p, ctypes.POINTER(Body), c_void_p, c_void_p]),
     "ebr_layout": (c_int32, [c_void_p, ctypes.POINTER(c_int64)]),

@@ -79,8 +79,17 @@ class Reconstructor:
             raise ValueError("layers must be 1 or 2")
         self.layers = layers
         flags = PLACEMENT[placement] | (SECOND_LAYER if layers == 2 else 0)
-        self._check(self.lib.ebr_plan(self.ctx, self.B, self._grids, self._bodies,
-                                      flags, _ptr(self.tags), self._stream()))
+        if any("faces" in g for g in grids):
+            # stretched grids: the faces of every axis, concatenated per geometry
+            self._faces = [np.ascontiguousarray(np.concatenate([np.asarray(g["faces"][a], dtype=np.float64)
+                                                                for a in range(int(g["dim"]))]))
+                           if "faces" in g else None for g in grids]
+            fp = (ctypes.c_void_p * self.B)(*[f.ctypes.data if f is not None else 0 for f in self._faces])
+            self._check(self.lib.ebr_plan_faces(self.ctx, self.B, self._grids, fp, self._bodies,
+                                                flags, _ptr(self.tags), self._stream()))
+        else:
+            self._check(self.lib.ebr_plan(self.ctx, self.B, self._grids, self._bodies,
+                                          flags, _ptr(self.tags), self._stream()))
         off = (ctypes.c_int64 * (self.B + 1))()
         self._check(self.lib.ebr_layout(self.ctx, off))
         self.cell_offset = np.array(list(off), dtype=np.int64)

@@ -63,6 +63,11 @@ struct Ctx {
 
   // geometry set
   int B = 0, placement = 0, layers = 1;
+  // stretched grids: per geometry and axis the host cell centres; device
+  // centres + widths (doubles) and float centres of all stretched geometries
+  std::vector<std::array<std::vector<double>, 3>> h_cen;
+  double* coord_d = nullptr;
+  float* coord_f = nullptr;
   bool planned = false, levelled = false;
   std::vector<Geom> hG;
   std::vector<int> h_row_off;
@@ -651,7 +656,12 @@ ebr_status set_body(Ctx* c, Geom& g, const ebr_body& bd, int b) {
   // float rounding of cell centres, body-frame coordinates, the float
   // closest point and dn/2 by a wide factor (1e-4 of the finest width plus
   // 4e-6 of the largest coordinate magnitude)
+  // (on a stretched grid h holds the smallest widths; the far end of axis a
+  // is then the last face, kept in far[a])
   float hmin = 3.4e38f, ext = 1.0f;
+  double far[3];
+  for (int a = 0; a < 3; ++a)
+    far[a] = g.stretched && a < g.dim ? g.lo[a] + g.span[a] : g.lo[a] + g.n[a] * g.h[a];
   for (int a = 0; a < 3; ++a) {
     g.flo[a] = (float)g.lo[a];
     g.fh[a] = (float)g.h[a];
@@ -659,7 +669,7 @@ ebr_status set_body(Ctx* c, Geom& g, const ebr_body& bd, int b) {
     g.fradii[a] = (float)g.radii[a];
     if (a < g.dim) {
       hmin = std::min(hmin, (float)g.h[a]);
-      ext = std::max(ext, std::max(std::fabs((float)g.lo[a]), std::fabs((float)(g.lo[a] + g.n[a] * g.h[a]))));
+      ext = std::max(ext, std::max(std::fabs((float)g.lo[a]), std::fabs((float)far[a])));
     }
   }
   for (int q = 0; q < 9; ++q) g.frot[q] = (float)g.rot[q];
@@ -669,7 +679,7 @@ ebr_status set_body(Ctx* c, Geom& g, const ebr_body& bd, int b) {
   float extc = 1.0f;
   for (int a = 0; a < g.dim; ++a)
     extc = std::max(extc, std::max(std::fabs((float)(g.lo[a] - g.centre[a])),
-                                   std::fabs((float)(g.lo[a] + g.n[a] * g.h[a] - g.centre[a]))));
+                                   std::fabs((float)(far[a] - g.centre[a]))));
   g.fext = extc;
   return EBR_OK;
 }
@@ -742,10 +752,13 @@ int64_t ebr_launch_count(const void* ctx) {
   return ctx ? static_cast<const Ctx*>(ctx)->launches : 0;
 }
 
-ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const ebr_body* h_bodies,
-                    int32_t placement, int8_t* d_tags, ebr_stream stream) {
-  Ctx* c = static_cast<Ctx*>(ctx);
-  if (!c) return EBR_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// ebr_plan and ebr_plan_faces (h_faces null: every grid uniform)
+ebr_status plan_impl(Ctx* c, int32_t n_geom, const ebr_grid* h_grids, const double* const* h_faces,
+                     const ebr_body* h_bodies, int32_t placement, int8_t* d_tags, ebr_stream stream) {
   c->err.clear();
   if (n_geom < 1 || !h_grids || !h_bodies || !d_tags)
     return fail(c, EBR_EINVAL, "ebr_plan: n_geom >= 1 and non-null grids, bodies, tags required");
@@ -761,39 +774,79 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const eb
   c->planned = c->levelled = false;
   c->hG.assign(n_geom, Geom{});
   c->h_row_off.assign(n_geom + 1, 0);
-  long long cells = 0;
+  c->h_cen.assign(n_geom, {});
+  long long cells = 0, n_coord = 0;
   int rows = 0;
+  std::vector<std::array<std::vector<double>, 3>> h_wid(n_geom);
   for (int b = 0; b < n_geom; ++b) {
     const ebr_grid& gr = h_grids[b];
     const ebr_body& bd = h_bodies[b];
     Geom& g = c->hG[b];
     if (gr.dim != 2 && gr.dim != 3) return fail(c, EBR_EINVAL, "geometry %d: dim must be 2 or 3", b);
     g.dim = gr.dim;
+    const double* faces = h_faces ? h_faces[b] : nullptr;
+    g.stretched = faces != nullptr;
     long long n3 = 1;
+    const double* fa = faces;
     for (int a = 0; a < 3; ++a) {
       long long na = a < gr.dim ? gr.n[a] : 1;
       if (na < 2 && a < gr.dim) return fail(c, EBR_EINVAL, "geometry %d: n[%d] < 2", b, a);
-      if (a < gr.dim && !(gr.hi[a] > gr.lo[a])) return fail(c, EBR_EINVAL, "geometry %d: hi <= lo", b);
       g.n[a] = (int)na;
-      g.lo[a] = a < gr.dim ? gr.lo[a] : 0.0;
-      g.h[a] = a < gr.dim ? (gr.hi[a] - gr.lo[a]) / (double)na : 1.0;
+      if (a < gr.dim && faces) {
+        // faces of axis a: na + 1 strictly increasing values
+        std::vector<double>& cen = c->h_cen[b][a];
+        std::vector<double>& wid = h_wid[b][a];
+        cen.resize(na);
+        wid.resize(na);
+        double wmin = 1e300;
+        for (long long i = 0; i < na; ++i) {
+          if (!(fa[i + 1] > fa[i])) return fail(c, EBR_EINVAL, "geometry %d: faces of axis %d not increasing", b, a);
+          cen[i] = 0.5 * (fa[i] + fa[i + 1]);
+          wid[i] = fa[i + 1] - fa[i];
+          wmin = std::min(wmin, wid[i]);
+        }
+        g.lo[a] = fa[0];
+        g.h[a] = wmin;
+        g.span[a] = fa[na] - fa[0];
+        fa += na + 1;
+        n_coord += na;
+      } else {
+        if (a < gr.dim && !(gr.hi[a] > gr.lo[a])) return fail(c, EBR_EINVAL, "geometry %d: hi <= lo", b);
+        g.lo[a] = a < gr.dim ? gr.lo[a] : 0.0;
+        g.h[a] = a < gr.dim ? (gr.hi[a] - gr.lo[a]) / (double)na : 1.0;
+        g.span[a] = a < gr.dim ? gr.hi[a] - gr.lo[a] : 1.0;
+      }
       n3 *= na;
     }
     if (n3 > (1LL << 31) - 1) return fail(c, EBR_EINVAL, "geometry %d: more than 2^31-1 cells", b);
     g.placement = placement;
+    // largest width of each axis (the spacing of a uniform grid)
+    double hx[3] = {1.0, 1.0, 1.0};
+    g.hmax = 0.0;
+    for (int a = 0; a < gr.dim; ++a) {
+      hx[a] = g.stretched ? *std::max_element(h_wid[b][a].begin(), h_wid[b][a].end()) : g.h[a];
+      g.hmax = std::max(g.hmax, hx[a]);
+    }
     // second layer: box reach per axis that holds a fluid cell for every
-    // solid cell with psi <= 1.5 dn: ceil((1.5 max h + |h| / 2) / h_a + 1/2)
+    // solid cell with psi <= 1.5 dn: ceil((1.5 max h + |h| / 2) / h_a + 1/2);
+    // stretched: the largest widths in the distances, the axis' smallest
+    // width as the unit, the containing cell's half width included
     g.layers = layers;
     {
       double hm = 0.0, D2 = 0.0;
       for (int a = 0; a < gr.dim; ++a) {
-        const double ha = (gr.hi[a] - gr.lo[a]) / (double)gr.n[a];
+        const double ha = g.stretched ? hx[a] : (gr.hi[a] - gr.lo[a]) / (double)gr.n[a];
         hm = std::max(hm, ha);
         D2 += ha * ha;
       }
       for (int a = 0; a < 3; ++a) {
-        const double ha = a < gr.dim ? (gr.hi[a] - gr.lo[a]) / (double)gr.n[a] : 1.0;
-        g.reach[a] = a < gr.dim ? (int)std::ceil((1.5 * hm + 0.5 * std::sqrt(D2)) / ha + 0.5) : 0;
+        if (a >= gr.dim) { g.reach[a] = 0; continue; }
+        if (g.stretched) {
+          g.reach[a] = (int)std::ceil((1.5 * hm + 0.5 * std::sqrt(D2) + 0.5 * hx[a]) / g.h[a]);
+        } else {
+          const double ha = (gr.hi[a] - gr.lo[a]) / (double)gr.n[a];
+          g.reach[a] = (int)std::ceil((1.5 * hm + 0.5 * std::sqrt(D2)) / ha + 0.5);
+        }
       }
     }
     {
@@ -810,6 +863,32 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const eb
   c->h_row_off[n_geom] = rows;
   c->total_cells = cells;
   c->total_rows = rows;
+  if (n_coord > 0) {
+    // device centres, widths and float centres of the stretched grids
+    AL(c->coord_d, 2 * (size_t)n_coord);
+    AL(c->coord_f, (size_t)n_coord);
+    std::vector<double> hd(2 * (size_t)n_coord);
+    std::vector<float> hf((size_t)n_coord);
+    size_t o = 0;
+    for (int b = 0; b < n_geom; ++b) {
+      Geom& g = c->hG[b];
+      if (!g.stretched) continue;
+      for (int a = 0; a < g.dim; ++a) {
+        const size_t na = (size_t)g.n[a];
+        for (size_t i = 0; i < na; ++i) {
+          hd[o + i] = c->h_cen[b][a][i];
+          hd[(size_t)n_coord + o + i] = h_wid[b][a][i];
+          hf[o + i] = (float)c->h_cen[b][a][i];
+        }
+        g.cen[a] = c->coord_d + o;
+        g.wid[a] = c->coord_d + n_coord + o;
+        g.fcen[a] = c->coord_f + o;
+        o += na;
+      }
+    }
+    CK(cudaMemcpy(c->coord_d, hd.data(), sizeof(double) * hd.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->coord_f, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice));
+  }
   AL(c->dG, n_geom);
   AL(c->d_row_off, n_geom + 1);
   AL(c->d_status, 1);
@@ -841,6 +920,25 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const eb
   }
   c->planned = true;
   return EBR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const ebr_body* h_bodies,
+                    int32_t placement, int8_t* d_tags, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  return plan_impl(c, n_geom, h_grids, nullptr, h_bodies, placement, d_tags, stream);
+}
+
+ebr_status ebr_plan_faces(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const double* const* h_faces,
+                          const ebr_body* h_bodies, int32_t placement, int8_t* d_tags, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  if (!h_faces) return fail(c, EBR_EINVAL, "ebr_plan_faces: null face array");
+  return plan_impl(c, n_geom, h_grids, h_faces, h_bodies, placement, d_tags, stream);
 }
 
 ebr_status ebr_classify(void* ctx, int8_t* d_tags, ebr_stream stream) {
@@ -956,7 +1054,8 @@ ebr_status ebr_ghost_info(void* ctx, int32_t* h_geom, int64_t* h_cell, int32_t* 
       double na = n[(size_t)a * ng + p];
       if (h_normal) h_normal[3 * (size_t)p + a] = na;
       if (h_S) {
-        double x = a < g.dim ? g.lo[a] + ((double)ijk[a] + 0.5) * g.h[a] : 0.0;
+        double x = a >= g.dim ? 0.0
+                   : g.stretched ? c->h_cen[geo[p]][a][ijk[a]] : g.lo[a] + ((double)ijk[a] + 0.5) * g.h[a];
         h_S[3 * (size_t)p + a] = a < g.dim ? x + psi[p] * na : 0.0;
       }
       if (h_r) h_r[3 * (size_t)p + a] = a < g.dim ? meta_r(meta[p], a) : 0;

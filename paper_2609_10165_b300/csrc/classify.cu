@@ -47,7 +47,7 @@ struct RowF {
 // The margins bound the float rounding of every quantity by a wide factor;
 // a cell within the margin of the boundary is decided by the double predicate.
 __device__ inline int solid_f32(const Geom& g, const RowF& R, int i) {
-  float x = R.ox + ((float)i + 0.5f) * R.hx;
+  float x = g.stretched ? g.fcen[0][i] - g.fcentre[0] : R.ox + ((float)i + 0.5f) * R.hx;
   switch (g.kind) {
     case CIRCLE:
     case SPHERE: {
@@ -316,8 +316,8 @@ struct RowGrp {
 // float row constants from the float copies of the geometry (the margins of
 // solid_f32 cover the float rounding of the cell centres by a wide factor)
 __device__ inline void row_consts_f(const Geom& g, int j, int k, RowF& R) {
-  const float dy = g.flo[1] + ((float)j + 0.5f) * g.fh[1] - g.fcentre[1];
-  const float dz = g.dim == 3 ? g.flo[2] + ((float)k + 0.5f) * g.fh[2] - g.fcentre[2] : 0.0f;
+  const float dy = fcentre_of(g, 1, j) - g.fcentre[1];
+  const float dz = g.dim == 3 ? fcentre_of(g, 2, k) - g.fcentre[2] : 0.0f;
   const float ext = g.fext;
   R.ox = g.flo[0] - g.fcentre[0];
   R.hx = g.fh[0];
@@ -349,10 +349,25 @@ __device__ inline void row_consts_f(const Geom& g, int j, int k, RowF& R) {
 __device__ void estimate_row_grp(const Geom& g, int j, int k, const RowGrp& Gp, int& state, int& ia,
                                  int& ib, int& iv) {
   const int n = g.n[0];
-  const float y = g.flo[1] + ((float)j + 0.5f) * g.fh[1] - g.fcentre[1];
-  const float z = g.dim == 3 ? g.flo[2] + ((float)k + 0.5f) * g.fh[2] - g.fcentre[2] : 0.0f;
+  const float y = fcentre_of(g, 1, j) - g.fcentre[1];
+  const float z = g.dim == 3 ? fcentre_of(g, 2, k) - g.fcentre[2] : 0.0f;
   const float lo0 = g.flo[0] - g.fcentre[0], h0 = g.fh[0];
-  auto frac = [&](float xr) { return (xr - lo0) / h0 - 0.5f; };   // body-relative x -> cell
+  // body-relative x -> fractional cell index (cell i has its centre at i);
+  // on a stretched grid by bisection over the float centres, linear between
+  // neighbouring centres (beyond the end centres: half widths of the end cells)
+  auto frac = [&](float xr) {
+    if (!g.stretched) return (xr - lo0) / h0 - 0.5f;
+    const float x = xr + g.fcentre[0];
+    const float* c = g.fcen[0];
+    if (x <= c[0]) return (x - c[0]) / (float)g.wid[0][0];
+    if (x >= c[n - 1]) return (float)(n - 1) + (x - c[n - 1]) / (float)g.wid[0][n - 1];
+    int lo = 0, hi = n - 1;            // c[lo] <= x < c[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (c[mid] <= x) lo = mid; else hi = mid;
+    }
+    return (float)lo + (x - c[lo]) / (c[hi] - c[lo]);
+  };
   state = ROW_EMPTY; ia = 0; ib = -1; iv = 0;
   float cx, xa, xb;
   if (g.kind == CIRCLE || g.kind == SPHERE) {
@@ -755,16 +770,17 @@ __global__ void k_place(const Geom* __restrict__ G, int n_iface, const int* __re
     double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
     // Eq. HGC_criterion decided in float where the float psi and dn/2 are
     // clearly apart; the few cells within the safety margin use double
-    const float xf = g.flo[0] + ((float)i + 0.5f) * g.fh[0];
-    const float yf = g.flo[1] + ((float)j + 0.5f) * g.fh[1];
-    const float zf = g.dim == 3 ? g.flo[2] + ((float)k + 0.5f) * g.fh[2] : 0.0f;
+    const float xf = fcentre_of(g, 0, i);
+    const float yf = fcentre_of(g, 1, j);
+    const float zf = g.dim == 3 ? fcentre_of(g, 2, k) : 0.0f;
     float n32[3];
     float psi32 = closest_point_f32(g, xf, yf, zf, solid, n32);
     float s32 = 0.0f;
+    const int ijk[3] = {i, j, k};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (a >= g.dim) continue;
-      float q = n32[a] / g.fh[a];
+      float q = n32[a] / (g.stretched ? (float)g.wid[a][ijk[a]] : g.fh[a]);
       s32 += q * q;
     }
     float half32 = 0.5f / sqrtf(s32);
@@ -777,7 +793,7 @@ __global__ void k_place(const Geom* __restrict__ G, int n_iface, const int* __re
       double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
       double psi, nv[3];
       if (!closest_point(g, x, y, z, solid, psi, nv)) { set_status(status, S_EINVAL); return; }
-      double half = 0.5 * delta_n(g, nv);
+      double half = 0.5 * delta_n(g, nv, i, j, k);
       cand = solid ? (psi <= half) : (-psi < half);
     }
     if (cand) tag = solid ? 2 : -2;
@@ -851,21 +867,21 @@ __global__ void k_layer2(const Geom* __restrict__ G, int n_iface, const int* __r
     const double dx = centre_of(g, 0, i) - g.centre[0], dy = centre_of(g, 1, j) - g.centre[1];
     const double dz = g.dim == 3 ? centre_of(g, 2, k) - g.centre[2] : 0.0;
     if (dx == 0.0 && dy == 0.0 && dz == 0.0) {
-      const double hm = fmax(fmax(g.h[0], g.h[1]), g.dim == 3 ? g.h[2] : 0.0);
-      if (!(g.radii[0] > 1.5 * hm)) set_status(status, S_EINVAL);
+      if (!(g.radii[0] > 1.5 * g.hmax)) set_status(status, S_EINVAL);
       return;
     }
   }
-  const float xf = g.flo[0] + ((float)i + 0.5f) * g.fh[0];
-  const float yf = g.flo[1] + ((float)j + 0.5f) * g.fh[1];
-  const float zf = g.dim == 3 ? g.flo[2] + ((float)k + 0.5f) * g.fh[2] : 0.0f;
+  const float xf = fcentre_of(g, 0, i);
+  const float yf = fcentre_of(g, 1, j);
+  const float zf = g.dim == 3 ? fcentre_of(g, 2, k) : 0.0f;
   float n32[3];
   const float psi32 = closest_point_f32(g, xf, yf, zf, true, n32);
   float s32 = 0.0f;
+  const int ijk[3] = {i, j, k};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (a >= g.dim) continue;
-    const float q = n32[a] / g.fh[a];
+    const float q = n32[a] / (g.stretched ? (float)g.wid[a][ijk[a]] : g.fh[a]);
     s32 += q * q;
   }
   const float gap = fabsf(psi32) - 1.5f / sqrtf(s32);
@@ -877,7 +893,7 @@ __global__ void k_layer2(const Geom* __restrict__ G, int n_iface, const int* __r
     const double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
     double psi, nv[3];
     if (!closest_point(g, x, y, z, true, psi, nv)) { set_status(status, S_EINVAL); return; }
-    add = psi <= 1.5 * delta_n(g, nv);
+    add = psi <= 1.5 * delta_n(g, nv, i, j, k);
   }
   if (add) *t = 2;
 }
@@ -949,8 +965,10 @@ __global__ void k_ghost_geom(const Geom* __restrict__ G, int ng, int placement,
     if (nv[a] < 0.0) meta |= 1u << a;
     int r = 1;
     if (placement == CGC_ES || g.layers == 2) {
-      // Eq. stencil_anisotropic: r_i = max(1, ceil(2 |n_i psi| / dx_i))
-      double q = 2.0 * fabs(psi * nv[a]) / g.h[a];
+      // Eq. stencil_anisotropic: r_i = max(1, ceil(2 |n_i psi| / dx_i)),
+      // dx_i the ghost cell's width
+      const int ijk[3] = {i, j, k};
+      double q = 2.0 * fabs(psi * nv[a]) / width_of(g, a, ijk[a]);
       r = max(1, (int)ceil(q));
     }
     if (r > 15) { set_status(status, S_EINVAL); r = 15; }

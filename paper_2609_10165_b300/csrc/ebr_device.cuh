@@ -50,6 +50,16 @@ struct Geom {
   // psi <= 1.5 dn; reach = box (cells per axis) holding a fluid cell for each
   int layers;
   int reach[3];
+  // stretched grids (Sec. 7, local mesh spacing): per axis the cell centres,
+  // widths and float centres (device arrays of n_a entries, owned by the
+  // context); lo then holds the first face and h the smallest width per axis.
+  // stretched == 0: uniform, centres lo + (i + 1/2) h.
+  int stretched;
+  double hmax;               // largest cell width over the axes
+  double span[3];            // last face minus first face per axis (stretched grids)
+  const double* cen[3];
+  const double* wid[3];
+  const float* fcen[3];
 };
 
 // ---------------------------------------------------------------------------
@@ -79,9 +89,21 @@ __host__ __device__ inline void stencil_off(int dim, int k, int o[3]) {
   o[2] = (v >> 2) & 1u;
 }
 
-// Cell centre along axis a, evaluated without contraction.
+// Cell centre along axis a, evaluated without contraction (uniform grids).
 __device__ __forceinline__ double centre_of(const Geom& g, int a, int i) {
+  if (g.stretched) return g.cen[a][i];
   return __dadd_rn(g.lo[a], __dmul_rn((double)i + 0.5, g.h[a]));
+}
+
+// Width of cell i along axis a.
+__device__ __forceinline__ double width_of(const Geom& g, int a, int i) {
+  return g.stretched ? g.wid[a][i] : g.h[a];
+}
+
+// Float centre along axis a (the float pre-tests; their margins cover the
+// rounding of either form by a wide factor).
+__device__ __forceinline__ float fcentre_of(const Geom& g, int a, int i) {
+  return g.stretched ? g.fcen[a][i] : g.flo[a] + ((float)i + 0.5f) * g.fh[a];
 }
 
 // ---------------------------------------------------------------------------
@@ -535,13 +557,14 @@ __device__ inline bool closest_point(const Geom& g, double x, double y, double z
   return true;
 }
 
-// Eq. delta_n with the ghost's own widths.
-__device__ inline double delta_n(const Geom& g, const double n[3]) {
+// Eq. delta_n with the widths of the cell (i, j, k).
+__device__ inline double delta_n(const Geom& g, const double n[3], int i, int j, int k) {
+  const int ijk[3] = {i, j, k};
   double s = 0.0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (a >= g.dim) continue;
-    double q = n[a] / g.h[a];
+    double q = n[a] / width_of(g, a, ijk[a]);
     s += q * q;
   }
   return 1.0 / sqrt(s);

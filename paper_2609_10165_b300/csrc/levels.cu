@@ -479,12 +479,23 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
   double psi = g_psi[p];
   double n[3] = {g_n[p], g_n[ng + p], g_n[2 * (size_t)ng + p]};
   double X2[3] = {1, 1, 1}, Xs[3] = {0, 0, 0}, r2[3] = {1, 1, 1};
+  int ijk[3];
+  cell_ijk3(g, g_cell[p], ijk);
   // fixed-trip axis loops predicated on the dimension: static indices keep
-  // the small arrays in registers
+  // the small arrays in registers.  x_2 - x_1 = r e h on a uniform grid; on
+  // a stretched one the centre of the cell r_i e_i cells away minus the
+  // ghost's (the index clamped into the grid: a stencil that leaves it is
+  // reported by k_deps, and its weights are never used)
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (a < d) {
-      X2[a] = meta_r(m, a) * meta_e(m, a) * g.h[a];
+      const int step = meta_r(m, a) * meta_e(m, a);
+      if (g.stretched) {
+        const int far = min(max(ijk[a] + step, 0), g.n[a] - 1);
+        X2[a] = g.cen[a][far] - g.cen[a][ijk[a]];
+      } else {
+        X2[a] = step * g.h[a];
+      }
       Xs[a] = psi * n[a];
       r2[a] = 1.0 / X2[a];
     }
@@ -496,9 +507,8 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
     wtab[(size_t)q * ng + p] = wd[q];
     wtab[(size_t)(8 + q) * ng + p] = wn[q];
   }
-  // surface weight: faces shared with tag-0 cells, |n_face . n| times face area
-  int ijk[3];
-  cell_ijk3(g, g_cell[p], ijk);
+  // surface weight: faces shared with tag-0 cells, |n_face . n| times face
+  // area (the ghost cell's own widths)
   const int8_t* tg = tags + g.cell_off;
   double wG = 0.0;
 #pragma unroll
@@ -507,7 +517,7 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
     double area = 1.0;
 #pragma unroll
     for (int b = 0; b < 3; ++b)
-      if (b < d && b != a) area *= g.h[b];
+      if (b < d && b != a) area *= width_of(g, b, ijk[b]);
 #pragma unroll
     for (int sgn = -1; sgn <= 1; sgn += 2) {
       int nb[3] = {ijk[0], ijk[1], ijk[2]};
