@@ -390,6 +390,26 @@ ebr_status ebr_tiled_lists(void* ctx, int32_t* h_tile, int32_t* h_slot);
 ebr_status ebr_tiled_wait_test(void* ctx, int32_t spins);
 
 /* ---------------------------------------------------------------------------
+ * Stability diagnostics (Sec. 7, Eq. stability_alpha_max)
+ * ------------------------------------------------------------------------- */
+
+/* For every ghost and axis the normalized distance
+ *   alpha_i = (x_s,i - x_1,i) / (x_2,i - x_1,i)
+ * (x_1 the ghost centre, x_s its boundary point, x_2 the stencil point r_i e_i
+ * cells away; alpha_i < 0 for a ghost centre in the fluid).  Host outputs,
+ * any may be NULL:
+ *   h_alpha      [n_geom][6]: max alpha_x, y, z, then min alpha_x, y, z of the
+ *                geometry's ghosts (0 for absent axes and empty geometries);
+ *   h_alpha_hist [3][n_bins]: alpha_i of all ghosts in n_bins bins of equal
+ *                width over [-0.5, 1.0) (values outside go to the end bins);
+ *   h_level_hist [n_levels]: ghosts in level k at index k - 1 (all geometries);
+ *   h_r_hist     [3][16]: count of each stencil multiplier r_i.
+ * 1 <= n_bins <= 4096.  The geometry set must be levelled.  Synchronises the
+ * stream; counts and extrema do not depend on the schedule. */
+ebr_status ebr_stats(void* ctx, double* h_alpha, int64_t* h_alpha_hist, int32_t n_bins, int64_t* h_level_hist,
+                     int32_t n_levels, int64_t* h_r_hist, ebr_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Status
  * ------------------------------------------------------------------------- */
 

@@ -70,6 +70,7 @@ _SIGS = {
     "ebr_tiled_info": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_int32]),
     "ebr_tiled_lists": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "ebr_tiled_wait_test": (c_int32, [c_void_p, c_int32]),
+    "ebr_stats": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p]),
     "ebr_sync_status": (c_int32, [c_void_p, c_void_p]),
     "ebr_diagnostics": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_int32, c_void_p]),
     "ebr_launch_count": (c_int64, [c_void_p]),

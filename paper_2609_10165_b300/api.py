@@ -259,6 +259,20 @@ class Reconstructor:
     def tiled_wait_test(self, spins):
         self._check(self.lib.ebr_tiled_wait_test(self.ctx, int(spins)))
 
+    def stats(self, n_bins=60, n_levels=256):
+        """Stability diagnostics (Eq. stability_alpha_max): per geometry max and
+        min alpha per axis, alpha histogram over [-0.5, 1), level and r
+        histograms."""
+        alpha = np.zeros((self.B, 6))
+        ah = np.zeros((3, n_bins), np.int64)
+        lh = np.zeros(n_levels, np.int64)
+        rh = np.zeros((3, 16), np.int64)
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        self._check(self.lib.ebr_stats(self.ctx, P(alpha), P(ah), n_bins, P(lh), n_levels, P(rh), self._stream()))
+        d = self.dim
+        return {"alpha_max": alpha[:, :d], "alpha_min": alpha[:, 3:3 + d], "alpha_hist": ah[:d],
+                "bin_edges": np.linspace(-0.5, 1.0, n_bins + 1), "level_hist": lh, "r_hist": rh[:d]}
+
     def sync_status(self):
         self._check(self.lib.ebr_sync_status(self.ctx, self._stream()))
 

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libebr.so")
 OBJ = os.path.join(ROOT, "_build")
 SOURCES = ["api.cu", "classify.cu", "levels.cu", "scan.cu", "fill.cu", "forces.cu", "adjoint.cu",
-           "packed.cu", "tiled.cu"]
+           "packed.cu", "tiled.cu", "stats.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC"]
 

@@ -10,10 +10,19 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ebr.h"
 #include "ebr_kernels.cuh"
 
 using namespace ebr;
+
+// an NVTX range around every entry point (a no-op unless a profiler is
+// attached), so that a timeline shows the library's calls
+struct EbrRange {
+  explicit EbrRange(const char* name) { nvtxRangePushA(name); }
+  ~EbrRange() { nvtxRangePop(); }
+};
 
 namespace {
 
@@ -68,6 +77,7 @@ struct Ctx {
   std::vector<std::array<std::vector<double>, 3>> h_cen;
   double* coord_d = nullptr;
   float* coord_f = nullptr;
+  unsigned long long* stats_buf = nullptr;   // ebr_stats: extrema and histograms
   bool planned = false, levelled = false;
   std::vector<Geom> hG;
   std::vector<int> h_row_off;
@@ -930,6 +940,7 @@ ebr_status ebr_plan(void* ctx, int32_t n_geom, const ebr_grid* h_grids, const eb
                     int32_t placement, int8_t* d_tags, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_plan");
   return plan_impl(c, n_geom, h_grids, nullptr, h_bodies, placement, d_tags, stream);
 }
 
@@ -937,6 +948,7 @@ ebr_status ebr_plan_faces(void* ctx, int32_t n_geom, const ebr_grid* h_grids, co
                           const ebr_body* h_bodies, int32_t placement, int8_t* d_tags, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_plan_faces");
   if (!h_faces) return fail(c, EBR_EINVAL, "ebr_plan_faces: null face array");
   return plan_impl(c, n_geom, h_grids, h_faces, h_bodies, placement, d_tags, stream);
 }
@@ -944,6 +956,7 @@ ebr_status ebr_plan_faces(void* ctx, int32_t n_geom, const ebr_grid* h_grids, co
 ebr_status ebr_classify(void* ctx, int8_t* d_tags, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_classify");
   c->err.clear();
   if (!c->planned) return fail(c, EBR_EINVAL, "ebr_classify: call ebr_plan first");
   if (!d_tags) return fail(c, EBR_EINVAL, "ebr_classify: null tags");
@@ -953,6 +966,7 @@ ebr_status ebr_classify(void* ctx, int8_t* d_tags, ebr_stream stream) {
 ebr_status ebr_move(void* ctx, const ebr_body* h_bodies, int8_t* d_tags, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_move");
   c->err.clear();
   if (c->B == 0 || c->hG.empty()) return fail(c, EBR_EINVAL, "ebr_move: call ebr_plan first");
   if (!h_bodies || !d_tags) return fail(c, EBR_EINVAL, "ebr_move: null bodies or tags");
@@ -1014,6 +1028,7 @@ ebr_status ebr_counts(const void* ctx, ebr_geom_counts* h_counts) {
 ebr_status ebr_build_levels(void* ctx, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_build_levels");
   c->err.clear();
   if (!c->planned) return fail(c, EBR_EINVAL, "ebr_build_levels: call ebr_plan first");
   bool planning = !c->levelled;
@@ -1028,6 +1043,7 @@ ebr_status ebr_ghost_info(void* ctx, int32_t* h_geom, int64_t* h_cell, int32_t* 
                           int32_t* h_r, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_ghost_info");
   c->err.clear();
   if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_ghost_info: build the levels first");
   cudaStream_t s = S(stream);
@@ -1069,6 +1085,7 @@ ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
                            int32_t mode, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_reconstruct");
   c->err.clear();
   if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_reconstruct: build the levels first");
   if (n_fields < 1 || n_fields > 8 || !d_fields || !h_bc_kind || !d_bc)
@@ -1125,6 +1142,7 @@ ebr_status ebr_boundary_forces(void* ctx, const void* const* d_vel, const void* 
                                double mu, const double* h_dirs, double* d_out, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_boundary_forces");
   c->err.clear();
   if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_boundary_forces: build the levels first");
   if (!d_vel || !d_p || !h_dirs || !d_out) return fail(c, EBR_EINVAL, "ebr_boundary_forces: null argument");
@@ -1150,6 +1168,7 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
                                    int32_t accumulate, int32_t mode, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_reconstruct_adjoint");
   c->err.clear();
   if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_reconstruct_adjoint: build the levels first");
   if (n_fields < 1 || n_fields > 8 || !h_bc_kind || !h_vel_index || !h_dirs || !d_seed ||
@@ -1403,6 +1422,7 @@ ebr_status ebr_reconstruct_packed(void* ctx, int32_t n_fields, void* d_fields,
                                   ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_reconstruct_packed");
   c->err.clear();
   KindBits kb;
   ebr_status st = packed_args(c, "ebr_reconstruct_packed", n_fields, h_bc_kind, dtype, &kb);
@@ -1430,6 +1450,7 @@ ebr_status ebr_reconstruct_packed_adjoint(void* ctx, int32_t n_fields, const int
                                           ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_reconstruct_packed_adjoint");
   c->err.clear();
   KindBits kb;
   ebr_status st = packed_args(c, "ebr_reconstruct_packed_adjoint", n_fields, h_bc_kind, dtype, &kb);
@@ -1485,6 +1506,7 @@ static ebr_status tiled_alloc(Ctx* c, void** p, size_t bytes) {
 ebr_status ebr_tiled_plan(void* ctx, const int32_t* h_tile, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_tiled_plan");
   c->err.clear();
   if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_tiled_plan: build the levels first");
   if (!h_tile) return fail(c, EBR_EINVAL, "ebr_tiled_plan: null tile sizes");
@@ -1634,6 +1656,7 @@ ebr_status ebr_reconstruct_tiled(void* ctx, int32_t n_fields, void* const* d_fie
                                  ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_reconstruct_tiled");
   c->err.clear();
   if (!c->tiled.built) return fail(c, EBR_EINVAL, "ebr_reconstruct_tiled: call ebr_tiled_plan first");
   if (n_fields < 1 || n_fields > 8 || !d_fields || !h_bc_kind || !d_bc)
@@ -1698,6 +1721,63 @@ ebr_status ebr_tiled_wait_test(void* ctx, int32_t spins) {
   if (spins < 1 || spins > (1 << 24)) return fail(c, EBR_EINVAL, "ebr_tiled_wait_test: spins in 1..2^24");
   c->tiled.extra_once = 1;
   c->tiled.spin_once = spins;
+  return EBR_OK;
+}
+
+ebr_status ebr_stats(void* ctx, double* h_alpha, int64_t* h_alpha_hist, int32_t n_bins, int64_t* h_level_hist,
+                     int32_t n_levels, int64_t* h_r_hist, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_stats");
+  c->err.clear();
+  if (!c->levelled) return fail(c, EBR_EINVAL, "ebr_stats: build the levels first");
+  if (n_bins < 1 || n_bins > 4096 || n_levels < 0)
+    return fail(c, EBR_EINVAL, "ebr_stats: 1..4096 bins, n_levels >= 0");
+  cudaStream_t s = S(stream);
+  const size_t n_ext = 6 * (size_t)c->B, n_a = 3 * (size_t)n_bins, n_r = 48;
+  unsigned long long* buf = nullptr;
+  {
+    ebr_status st = dalloc(c, &c->stats_buf, n_ext + n_a + n_r);
+    if (st) return st;
+    buf = c->stats_buf;
+  }
+  // extrema start at the smallest ordered value, counts at zero
+  CK(cudaMemsetAsync(buf, 0, sizeof(unsigned long long) * (n_ext + n_a + n_r), s));
+  launch_stats(c->dG, c->ng, c->g_geo, c->g_cell, c->g_psi, c->g_n, c->g_meta, n_bins, buf, buf + n_ext,
+               buf + n_ext + n_a, s);
+  c->launches += c->ng > 0 ? 1 : 0;
+  CKL();
+  std::vector<unsigned long long> h(n_ext + n_a + n_r);
+  CK(cudaMemcpyAsync(h.data(), buf, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  auto unbits = [](unsigned long long u) {
+    const unsigned long long b = (u >> 63) ? (u & ~(1ull << 63)) : ~u;
+    double v;
+    std::memcpy(&v, &b, sizeof v);
+    return v;
+  };
+  for (int b = 0; b < c->B; ++b) {
+    const Geom& g = c->hG[b];
+    for (int a = 0; a < 3; ++a) {
+      const bool any = g.n_ghost > 0 && a < g.dim;
+      if (h_alpha) {
+        h_alpha[(size_t)b * 6 + a] = any ? unbits(h[(size_t)b * 6 + a]) : 0.0;
+        h_alpha[(size_t)b * 6 + 3 + a] = any ? -unbits(h[(size_t)b * 6 + 3 + a]) : 0.0;
+      }
+    }
+  }
+  if (h_alpha_hist)
+    for (size_t q = 0; q < n_a; ++q) h_alpha_hist[q] = (int64_t)h[n_ext + q];
+  if (h_r_hist)
+    for (size_t q = 0; q < n_r; ++q) h_r_hist[q] = (int64_t)h[n_ext + n_a + q];
+  if (h_level_hist) {
+    for (int k = 0; k < n_levels; ++k) h_level_hist[k] = 0;
+    for (int b = 0; b < c->B; ++b) {
+      const Geom& g = c->hG[b];
+      for (int lv = 1; lv <= g.n_levels && lv <= n_levels; ++lv)
+        h_level_hist[lv - 1] += c->h_lev_ptr[g.lev_off + lv] - c->h_lev_ptr[g.lev_off + lv - 1];
+    }
+  }
   return EBR_OK;
 }
 
@@ -1797,6 +1877,7 @@ ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stre
 ebr_status ebr_sync_status(void* ctx, ebr_stream stream) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_sync_status");
   if (!c->d_status) return EBR_OK;
   int hs = 0;
   cudaStream_t s = S(stream);

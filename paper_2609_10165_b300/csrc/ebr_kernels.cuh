@@ -147,6 +147,13 @@ void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, 
                    const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,
                    void* const* grad, int accumulate, cudaStream_t s, int T = 128);
 
+// ---- stats.cu (Sec. 7, Eq. stability_alpha_max): ext [B][6] ordered bits of
+// max alpha_x,y,z and max -alpha_x,y,z; ahist [3][n_bins] over [-0.5, 1);
+// rhist [3][16] multipliers
+void launch_stats(const Geom* G, int ng, const int* g_geo, const int* g_cell, const double* g_psi,
+                  const double* g_n, const uint32_t* g_meta, int n_bins, unsigned long long* ext,
+                  unsigned long long* ahist, unsigned long long* rhist, cudaStream_t s);
+
 // ---- tiled.cu (Sec. 3.2, distributed memory: tiles with a per-level exchange)
 // Device view of a tile schedule: the ghosts of active tile i in level L are
 // t_list[t_ptr[i (Lmax + 1) + L - 1] .. t_ptr[i (Lmax + 1) + L]) (canonical
