@@ -228,16 +228,25 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
   }
   __syncthreads();
   // phase 2: reverse levels
+  // every field's sum in registers, the sources walked once: the loads of
+  // all fields are issued together and no store intervenes (each field
+  // still sums its sources in the same order, so the bits are the same)
   auto relax = [&](int s) {
-    for (int f = 0; f < F; ++f) {
-      int kind = A.kind[f];
-      T v = L[(size_t)f * n + s];
-      for (int o = cptr[s]; o < cptr[s + 1]; ++o) {
-        const int q = cq[o];
-        if (q >= 0) v += cw[(size_t)kind * nsrc + o] * L[(size_t)f * n + q];
-      }
-      L[(size_t)f * n + s] = v;
+    T v[8];
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+      if (f < F) v[f] = L[(size_t)f * n + s];
+    for (int o = cptr[s]; o < cptr[s + 1]; ++o) {
+      const int q = cq[o];
+      if (q < 0) continue;
+      const T w0 = cw[o], w1 = cw[(size_t)nsrc + o];
+#pragma unroll
+      for (int f = 0; f < 8; ++f)
+        if (f < F) v[f] += (A.kind[f] ? w1 : w0) * L[(size_t)f * n + q];
     }
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+      if (f < F) L[(size_t)f * n + s] = v[f];
   };
   // the deepest levels (lw.., at most 32 ghosts each) come first: one warp
   // walks them with warp barriers, then the block takes the wide levels

@@ -208,18 +208,29 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
   }
   __syncthreads();
   // phase 2: the dependency chain, level by level, on shared memory only
+  // every field's sum in registers, the dependencies walked once: the loads
+  // of all fields are issued together and no store intervenes (each field
+  // still adds its dependencies in member order, so the bits are the same)
   auto relax = [&](int s) {
-    int cell = cellv[s];
-    for (int f = 0; f < F; ++f) {
-      int kind = P.kind[f];
-      T v = vals[(size_t)f * n + s];
-      for (int k = 0; k < K; ++k) {
-        int d = dpos[(size_t)k * n + s];
-        if (d >= 0) v += wdep[(size_t)(kind * K + k) * n + s] * vals[(size_t)f * n + d];
-      }
-      vals[(size_t)f * n + s] = v;
-      static_cast<T*>(P.f[f])[cell_off + cell] = v;
-      if (!isfinite(v)) set_status(status, S_ENONFINITE);
+    const int cell = cellv[s];
+    T v[8];
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+      if (f < F) v[f] = vals[(size_t)f * n + s];
+    for (int k = 0; k < K; ++k) {
+      const int d = dpos[(size_t)k * n + s];
+      if (d < 0) continue;
+      const T w0 = wdep[(size_t)k * n + s], w1 = wdep[(size_t)(K + k) * n + s];
+#pragma unroll
+      for (int f = 0; f < 8; ++f)
+        if (f < F) v[f] += (P.kind[f] ? w1 : w0) * vals[(size_t)f * n + d];
+    }
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      if (f >= F) break;
+      vals[(size_t)f * n + s] = v[f];
+      static_cast<T*>(P.f[f])[cell_off + cell] = v[f];
+      if (!isfinite(v[f])) set_status(status, S_ENONFINITE);
     }
   };
   // levels lw.. hold at most 32 ghosts each (the thin end of the chains):
