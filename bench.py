@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--geoms", type=int, default=256)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
-    ap.add_argument("--sets", type=int, default=32, help="field sets of the throughput mode (0: skip)")
+    ap.add_argument("--sets", type=int, default=64,
+                    help="field sets of the throughput mode (0: skip); 64 sets move about 6x L2 per step")
     ap.add_argument("--no-single-grid", dest="single_grid", action="store_false",
                     help="skip the 512^3 single-grid tiled fill")
     ap.add_argument("--lite", action="store_true",
@@ -548,13 +549,28 @@ def kernel_source_hash(kernel):
 # on this workload, with the source hash of the kernel version captured (L2
 # write-back hides most writes of a short kernel).  A figure whose hash no
 # longer matches the source is reported as null, with the reason.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    "ghost_write": (9.18e6, "0945db4c2bac33e6"),     # k_ghost_write 7.98 MB + k_ghost_geom 1.20 MB
+    "rows": (0.29e6, "0945db4c2bac33e6"), "place": (1.77e6, "0945db4c2bac33e6"),
+    "iface": (1.07e6, "0945db4c2bac33e6"),
+    "tables": (9.87e6, "a2a2fe273f557785"), "levels": (1.12e6, "a2a2fe273f557785"),
+    "gsrc": (13.98e6, "a2a2fe273f557785"), "deps": (13.17e6, "a2a2fe273f557785"),
+    "reorder": (7.28e6, "a2a2fe273f557785"),
+    "fill_part": (27.85e6, "e287727b2a525463"), "fill_chain": (6.10e6, "e287727b2a525463"),
+    "forces": (32.61e6, "ae821412f312bd2b"),         # k_forces_chunk 32.54 MB + k_forces_final 0.07 MB
+    "adj_seed": (10.62e6, "6d145a6cc4882f02"), "adj_part": (6.34e6, "6d145a6cc4882f02"),
+    "adj_chain": (3.13e6, "6d145a6cc4882f02"), "adj_probe": (13.96e6, "6d145a6cc4882f02"),
+    "adj_fluid": (23.61e6, "6d145a6cc4882f02"), "adj_bc": (6.12e6, "6d145a6cc4882f02"),
+}
 
 # FP64 flops per launch (DADD + DMUL + 2 x DFMA thread instructions from one
 # ncu capture on this workload) of the kernels bound by the FP64 pipe, with
 # the source hash of the captured version.  "ghost_write" is the compaction +
 # closest-point pair; only the closest-point kernel does FP64 work.
-FP64_FLOPS_PER_LAUNCH = {}
+FP64_FLOPS_PER_LAUNCH = {
+    "ghost_write": (11_920_293, "0945db4c2bac33e6"), "tables": (10_419_154, "a2a2fe273f557785"),
+    "adj_seed": (9_582_272, "6d145a6cc4882f02"), "forces": (7_335_675, "ae821412f312bd2b"),
+}
 
 
 def counter(table, kernel):
