@@ -225,7 +225,8 @@ class Step:
             with torch.cuda.stream(self.side):
                 self._adjoint()
         R.reconstruct(self.fields, self.kinds, self.bcs, mode=self.mode)
-        R.forces([self.fields[i] for i in self.vel], self.fields[self.p], self.mu, self.dirs, out=self.out)
+        R.forces([None if i is None else self.fields[i] for i in self.vel], self.fields[self.p], self.mu,
+                 self.dirs, out=self.out)
         if self.side is not None:
             torch.cuda.current_stream().wait_stream(self.side)
         elif self.adjoint:
@@ -321,9 +322,12 @@ def _oracle_geometry_index(args):
 
 
 # the step's kernels by phase of the method (the serial per-kernel profile;
-# "scan" holds all three exclusive scans, counted under classify)
+# a re-run has no separate scans: "iface", "ghost_compact" and "gsrc" scan in
+# the same launch; "scan", "ghost_flags" and "ghost_write" are the planning
+# path's kernels)
 PHASES = {
-    "classify": ("rows", "iface", "scan", "place", "reclassify", "ghost_flags", "ghost_write"),
+    "classify": ("rows", "iface", "scan", "place", "reclassify", "ghost_flags", "ghost_write", "ghost_compact",
+                 "ghost_geom"),
     "levels": ("poscell", "deps", "levels", "reorder", "tables", "gsrc"),
     "fill": ("fill_part", "fill_chain"),
     "forces": ("forces",),
@@ -478,18 +482,23 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
     s = 4
     return {
         "rows": n_cells * 1 + rows * 8,                          # tags + row runs
-        "iface": 2 * rows * 12 + ni * 9,                         # runs + counts / offsets; cell, geo, side
-        "scan": 8 * (rows + ni + ng),                            # three exclusive scans
+        "iface": rows * (8 + 4) + ni * 9,                        # runs, offsets; cell, geo, side
         "place": ni * 10,                                        # interface record + tag
-        "reclassify": 2 * ni * 9,                                # two passes over the interface
+        "reclassify": ni * 9,                                    # pass A over the interface
+        # pass B, flags, offsets and ghost records: interface record, tag,
+        # offset; per ghost cell, geometry, meta
+        "ghost_compact": ni * 13 + ng * 12,
+        "ghost_geom": ng * (12 + 8 + 8 * dim + 4),               # record in; psi, n, meta out
+        # the planning path's separate kernels (counts, scans, compaction)
+        "scan": 8 * (rows + ni + ng),
         "ghost_flags": ni * 13,
-        "ghost_write": ni * 13 + ng * (12 + 12 + 8 + 8 * dim + 4),   # compaction + psi, n, meta
+        "ghost_write": ni * 13 + ng * (12 + 12 + 8 + 8 * dim + 4),
         "poscell": 2 * ng * 12,
         "deps": ng * (12 + 8 * dim + K + 4 * K + 4 * K + 4),
         "levels": ng * (4 * K + 12),
         "reorder": ng * 2 * (4 + 4 + 8 + 8 * dim + 4 + 4 * K + 4),
         "tables": ng * (4 + 4 + 8 + 8 * dim + 4 + 2 * dim + 16 * 8 + (1 + (1 + K) + dim * (K + 1)) * 8),
-        "gsrc": ng * 32 + n_gsrc * 4,
+        "gsrc": ng * 32 + n_gsrc * 4,                            # probes, offsets, sources
         # partial sums: per update the boundary datum and the fluid members
         # read, the sum written; per ghost geometry, cell, meta and weights
         "fill_part": ng * F * (K * s + s + s) + ng * (4 + 4 + 4 + (K + 1) * 8),
@@ -521,7 +530,8 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
 CSRC = os.path.join(ROOT, "paper_2609_10165_b300", "csrc")
 KERNEL_SOURCE = {
     "rows": "classify.cu", "iface": "classify.cu", "place": "classify.cu", "reclassify": "classify.cu",
-    "ghost_flags": "classify.cu", "ghost_write": "classify.cu", "scan": "scan.cu",
+    "ghost_compact": "classify.cu", "ghost_geom": "classify.cu", "ghost_flags": "classify.cu",
+    "ghost_write": "classify.cu", "scan": "scan.cu",
     "poscell": "levels.cu", "deps": "levels.cu", "levels": "levels.cu", "reorder": "levels.cu",
     "tables": "levels.cu", "gsrc": "levels.cu", "fill_part": "fill.cu", "fill_chain": "fill.cu",
     "fill_level": "fill.cu", "forces": "forces.cu", "adj_seed": "adjoint.cu", "adj_part": "adjoint.cu",
@@ -529,7 +539,7 @@ KERNEL_SOURCE = {
     "adj_fluid": "adjoint.cu", "adj_bc": "adjoint.cu", "pfill": "packed.cu", "padj": "packed.cu",
     "tiled_fill": "tiled.cu",
 }
-SHARED_HEADERS = ("ebr_device.cuh", "ebr_probe.cuh", "ebr_kernels.cuh")
+SHARED_HEADERS = ("ebr_device.cuh", "ebr_probe.cuh", "ebr_kernels.cuh", "lookback.cuh", "traction.cuh")
 
 
 def kernel_source_hash(kernel):
@@ -550,7 +560,6 @@ def kernel_source_hash(kernel):
 # write-back hides most writes of a short kernel).  A figure whose hash no
 # longer matches the source is reported as null, with the reason.
 TRAFFIC_PER_LAUNCH = {
-    "ghost_write": (9.18e6, "0945db4c2bac33e6"),     # k_ghost_write 7.98 MB + k_ghost_geom 1.20 MB
     "rows": (0.29e6, "0945db4c2bac33e6"), "place": (1.77e6, "0945db4c2bac33e6"),
     "iface": (1.07e6, "0945db4c2bac33e6"),
     "tables": (9.87e6, "a2a2fe273f557785"), "levels": (1.12e6, "a2a2fe273f557785"),
@@ -565,10 +574,9 @@ TRAFFIC_PER_LAUNCH = {
 
 # FP64 flops per launch (DADD + DMUL + 2 x DFMA thread instructions from one
 # ncu capture on this workload) of the kernels bound by the FP64 pipe, with
-# the source hash of the captured version.  "ghost_write" is the compaction +
-# closest-point pair; only the closest-point kernel does FP64 work.
+# the source hash of the captured version.
 FP64_FLOPS_PER_LAUNCH = {
-    "ghost_write": (11_920_293, "0945db4c2bac33e6"), "tables": (10_419_154, "a2a2fe273f557785"),
+    "ghost_geom": (11_920_293, "0945db4c2bac33e6"), "tables": (10_419_154, "a2a2fe273f557785"),
     "adj_seed": (9_582_272, "6d145a6cc4882f02"), "forces": (7_335_675, "ae821412f312bd2b"),
 }
 
@@ -628,7 +636,7 @@ def roofline_object(prof_ms, prof_n, algo, hbm_peak, hbm_peak_kind, n_sm, sm_mhz
     else:
         roof.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": gbs / hbm_peak, "peak_source": hbm_peak_kind, "algo_bytes_per_launch": tb})
-        if top in ("ghost_write", "tables", "adj_seed", "forces"):
+        if top in ("ghost_geom", "tables", "adj_seed", "forces"):
             roof["fp64_flops_null_because"] = why_f
     roof["fp64_peak_tflops"] = fp64_peak
     roof["per_kernel"] = per_kernel
@@ -961,6 +969,23 @@ def main():
     ms_step, total_updates = reduce_over_ranks(ms_med, updates, dev)
     value = total_updates / (ms_step * 1e-3)
 
+    # the same step with plain launches (programmatic dependent launch off)
+    from paper_2609_10165_b300.api import set_pdl
+    set_pdl(False)
+    try:
+        g0 = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            step()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g0, stream=side, capture_error_mode="relaxed"):
+                step()
+        torch.cuda.synchronize()
+        ms_plain = float(np.median(time_steps(g0.replay, max(5, args.steps // 2), stream, flush)))
+        del g0
+    finally:
+        set_pdl(True)
+    R.sync_status()
+
     # forward only (same graph construction)
     step_f = Step(R, fields, bcs, geoms, "persistent", adjoint=False)
     gf = torch.cuda.CUDAGraph()
@@ -1119,6 +1144,8 @@ def main():
                    "block_sizes": tuned if tuned is not None else "defaults (128)"},
         "autotune": tune_rep,
         "fwd_updates_per_s": total_updates / (ms_f * 1e-3), "fwd_ms_per_step": ms_f,
+        "plain_launch": {"what": "the headline step captured with programmatic dependent launch off",
+                         "ms_per_step": ms_plain},
         "reconstruction_only": reconstruction,
         "accuracy": baseline.get("accuracy") if baseline else None,
         "plain_fp64_updates_per_s": total_updates / (ms64 * 1e-3) if ms64 == ms64 else None,

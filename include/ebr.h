@@ -166,7 +166,11 @@ ebr_status ebr_plan_faces(void* ctx, int32_t n_geom, const ebr_grid* h_grids, co
 /* Re-run the classification of the planned geometry set without host
  * synchronisation (capturable in a CUDA graph).  Writes d_tags and the
  * context's ghost records; a count that differs from the plan sets EBR_ESHAPE
- * in the device status. */
+ * in the device status.  The stream compactions (interface cells of the
+ * rows, ghosts of the interface list) count, scan and write in one launch
+ * each: a single-pass scan whose blocks wait, bounded (EBR_ETIMEOUT), on the
+ * prefixes of blocks already running; its state lives in the context, so two
+ * re-runs of one context must not overlap (one stream at a time). */
 ebr_status ebr_classify(void* ctx, int8_t* d_tags, ebr_stream stream);
 
 /* Move the bodies of the planned geometry set (Sec. 7: a moving body is
@@ -431,12 +435,26 @@ ebr_status ebr_diagnostics(void* ctx, int64_t* h_out, int32_t n, ebr_stream stre
 /* Number of kernel launches this context has issued since creation. */
 int64_t ebr_launch_count(const void* ctx);
 
+/* Programmatic dependent launch (process-wide; on by default).  enable != 0:
+ * kernels of the library are launched with the programmatic stream
+ * serialization attribute, so that a kernel's blocks may be scheduled while
+ * the kernel before it in the stream is still running; each of them waits
+ * (griddepcontrol.wait) for the preceding kernels to complete before it
+ * touches memory, so results and stream order are unchanged.  Inside a stream
+ * capture such launches become programmatic edges of the graph.  enable = 0:
+ * plain launches.  A launch reads the switch when it is issued, so a graph
+ * captured earlier keeps the mode it was captured with.  Not synchronised
+ * with launches issued concurrently from other host threads. */
+void ebr_set_pdl(int32_t enable);
+/* Current switch: 1 on, 0 off. */
+int32_t ebr_get_pdl(void);
+
 /* ---------------------------------------------------------------------------
  * Launch shapes (tuning; the paper has no counterpart)
  *
  * Threads per block of the kernels that run one thread per item (interface
- * cell, ghost, fluid target): "iface", "place", "ghost_write" (the per-ghost
- * closest-point kernel of that step), "deps", "tables", "gsrc", "fill_part"
+ * cell, ghost, fluid target): "iface", "place", "ghost_geom" (the per-ghost
+ * closest-point kernel), "deps", "tables", "gsrc", "fill_part"
  * (the partial sums of the persistent fill), "adj_seed", "adj_part" (the
  * start values and incidence records of the persistent adjoint chain),
  * "adj_probe" (the fluid targets' sources at reach 1, found beside the
@@ -444,8 +462,11 @@ int64_t ebr_launch_count(const void* ctx);
  * reports them.  The block size changes scheduling only: every result is bitwise the
  * same for every allowed value.  A launch reads the context's value when it
  * is issued, so a graph captured earlier keeps the shapes it was captured
- * with.  The Python autotuner (paper_2609_10165_b300/autotune.py) times the
- * candidates with ebr_profile and sets the fastest.
+ * with.  "iface" and "gsrc" shape the planning pass (ebr_plan,
+ * ebr_build_levels after a plan); a re-run (ebr_classify, ebr_build_levels on
+ * a levelled context) counts, scans and writes in one launch of 256 threads
+ * per block.  The Python autotuner (paper_2609_10165_b300/autotune.py) times
+ * the candidates with ebr_profile and sets the fastest.
  * ------------------------------------------------------------------------- */
 
 /* Number of tunable kernels; writes up to max_entries names into h_names
@@ -477,6 +498,13 @@ ebr_status ebr_profile(void* ctx, int32_t enable);
  * Any output pointer may be NULL. */
 int32_t ebr_profile_read(void* ctx, int32_t max_entries, char* h_names, double* h_ms,
                          int64_t* h_count, int32_t keep);
+/* The records one by one, in the order they were issued (launches on
+ * several streams interleave): name, start and end in milliseconds after the
+ * start of the first record (a launch on another stream may start earlier:
+ * negative).  Synchronises the events; keeps the records.  Returns the
+ * number of records (may exceed max_entries) or a negative ebr_status. */
+int32_t ebr_profile_timeline(void* ctx, int32_t max_entries, char* h_names, double* h_start_ms,
+                             double* h_end_ms);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free classification of one grid (the paper has no counterpart)

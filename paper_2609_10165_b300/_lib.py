@@ -74,8 +74,11 @@ _SIGS = {
     "ebr_sync_status": (c_int32, [c_void_p, c_void_p]),
     "ebr_diagnostics": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_int32, c_void_p]),
     "ebr_launch_count": (c_int64, [c_void_p]),
+    "ebr_set_pdl": (None, [c_int32]),
+    "ebr_get_pdl": (c_int32, []),
     "ebr_profile": (c_int32, [c_void_p, c_int32]),
     "ebr_profile_read": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32]),
+    "ebr_profile_timeline": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "ebr_tunable_kernels": (c_int32, [c_void_p, c_int32]),
     "ebr_set_block_size": (c_int32, [c_void_p, ctypes.c_char_p, c_int32]),
     "ebr_get_block_size": (c_int32, [c_void_p, ctypes.c_char_p]),

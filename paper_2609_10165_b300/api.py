@@ -57,6 +57,16 @@ def _ptr_array(ts):
     return arr
 
 
+def set_pdl(enable):
+    """Programmatic dependent launch of the library's kernels (process-wide,
+    on by default): ebr_set_pdl."""
+    _lib.load().ebr_set_pdl(1 if enable else 0)
+
+
+def get_pdl():
+    return bool(_lib.load().ebr_get_pdl())
+
+
 class Reconstructor:
     """One planned geometry set (B >= 1 grids with bodies) on one device."""
 
@@ -302,6 +312,18 @@ class Reconstructor:
             nm = names.raw[32 * k: 32 * k + 32].split(b"\0", 1)[0].decode()
             out[nm] = (float(ms[k]), int(cnt[k]))
         return out
+
+    def profile_timeline(self, max_entries=256):
+        """[(name, start_ms, end_ms)] of the kept records in issue order,
+        relative to the start of the first record."""
+        names = ctypes.create_string_buffer(32 * max_entries)
+        t0 = (ctypes.c_double * max_entries)()
+        t1 = (ctypes.c_double * max_entries)()
+        n = self.lib.ebr_profile_timeline(self.ctx, max_entries, names, t0, t1)
+        if n < 0:
+            self._check(n)
+        return [(names.raw[32 * k: 32 * k + 32].split(b"\0", 1)[0].decode(), float(t0[k]), float(t1[k]))
+                for k in range(min(n, max_entries))]
 
     # -- launch shapes ----------------------------------------------------------
     def tunable_kernels(self):

@@ -30,6 +30,7 @@ __global__ void k_adj_seed(int F, int4 role, double mu, double dd0, double dd1, 
                            double dl0, double dl1, double dl2, const double* __restrict__ seed,
                            int ng, const int* __restrict__ g_geo, const double* __restrict__ g_n,
                            const double* __restrict__ ftab, double* __restrict__ sv) {
+  pdl_enter();
   constexpr int K = D == 2 ? 3 : 7;
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
@@ -85,10 +86,10 @@ void launch_adj_seed(int dim, int F, const int* role, double mu, const double* d
   double dd[3] = {0, 0, 0}, dl[3] = {0, 0, 0};
   for (int a = 0; a < dim; ++a) { dd[a] = dirs[a]; dl[a] = dirs[dim + a]; }
   if (dim == 2)
-    k_adj_seed<2><<<(ng + T - 1) / T, T, 0, s>>>(F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
+    launch(k_adj_seed<2>, (ng + T - 1) / T, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
                                                    seed, ng, g_geo, g_n, ftab, sv);
   else
-    k_adj_seed<3><<<(ng + T - 1) / T, T, 0, s>>>(F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
+    launch(k_adj_seed<3>, (ng + T - 1) / T, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
                                                    seed, ng, g_geo, g_n, ftab, sv);
 }
 
@@ -112,6 +113,7 @@ __global__ void k_adj_level(AdjSet A, int F, int p0, int p1, const int* __restri
                             const int* __restrict__ gsrc, const uint32_t* __restrict__ g_meta,
                             const double* __restrict__ wtab, const double* __restrict__ sv, int ng,
                             T* __restrict__ lam) {
+  pdl_enter();
   int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= p1) return;
   for (int f = 0; f < F; ++f)
@@ -128,9 +130,9 @@ void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int
   for (int f = 0; f < F && f < 8; ++f) A.kind[f] = bc_kind[f];
   int n = p1 - p0, T = n < 128 ? 64 : 128;
   if (dtype == 0)
-    k_adj_level<float><<<(n + T - 1) / T, T, 0, s>>>(A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (float*)lam);
+    launch(k_adj_level<float>, (n + T - 1) / T, T, 0, s, A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (float*)lam);
   else
-    k_adj_level<double><<<(n + T - 1) / T, T, 0, s>>>(A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (double*)lam);
+    launch(k_adj_level<double>, (n + T - 1) / T, T, 0, s, A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (double*)lam);
 }
 
 // Per ghost, grid-wide (one thread per ghost): lambda's start value, the sum
@@ -143,6 +145,7 @@ __global__ void k_adj_part(int F, int ng, const int* __restrict__ gsrc_ptr, cons
                            const uint32_t* __restrict__ g_meta, const double* __restrict__ wtab,
                            const double* __restrict__ sv, T* __restrict__ lpart, int* __restrict__ cq_g,
                            T* __restrict__ cw_g, int n_src) {
+  pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
   const int j0 = gsrc_ptr[p], j1 = gsrc_ptr[p + 1];
@@ -171,10 +174,10 @@ void launch_adj_part(int dtype, int F, int ng, const int* gsrc_ptr, const int* g
                      cudaStream_t s, int T) {
   if (ng <= 0) return;
   if (dtype == 0)
-    k_adj_part<float><<<(ng + T - 1) / T, T, 0, s>>>(F, ng, gsrc_ptr, gsrc, g_meta, wtab, sv, (float*)lpart,
+    launch(k_adj_part<float>, (ng + T - 1) / T, T, 0, s, F, ng, gsrc_ptr, gsrc, g_meta, wtab, sv, (float*)lpart,
                                                      cq_g, (float*)cw_g, n_src);
   else
-    k_adj_part<double><<<(ng + T - 1) / T, T, 0, s>>>(F, ng, gsrc_ptr, gsrc, g_meta, wtab, sv, (double*)lpart,
+    launch(k_adj_part<double>, (ng + T - 1) / T, T, 0, s, F, ng, gsrc_ptr, gsrc, g_meta, wtab, sv, (double*)lpart,
                                                       cq_g, (double*)cw_g, n_src);
 }
 
@@ -198,6 +201,7 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
                                                     const int* __restrict__ cq_g,
                                                     const T* __restrict__ cw_g, int n_src, int ng,
                                                     T* __restrict__ lam) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom& g = G[geo_list[blockIdx.x]];
   const int n = g.n_ghost, g0 = g.ghost_off;
@@ -213,13 +217,18 @@ __global__ void __launch_bounds__(AC_T) k_adj_chain(AdjSet A, int F, const Geom*
     const int* lp = lev_ptr + g.lev_off;
     for (int q = threadIdx.x; q <= n_levels; q += AC_T) lps[q] = lp[q] - g0;
   }
-  // phase 1: start values, source offsets and the incidence records
+  // phase 1: start values, source offsets and the incidence records (the
+  // loops unrolled so that several items' loads are in flight together)
+#pragma unroll 4
   for (int s = threadIdx.x; s < n; s += AC_T) {
     const int p = g0 + s;
     cptr[s] = gsrc_ptr[p] - j0g;
-    for (int f = 0; f < F; ++f) L[(size_t)f * n + s] = lpart[(size_t)f * ng + p];
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+      if (f < F) L[(size_t)f * n + s] = lpart[(size_t)f * ng + p];
   }
   if (threadIdx.x == 0) cptr[n] = nsrc;
+#pragma unroll 4
   for (int o = threadIdx.x; o < nsrc; o += AC_T) {
     const int q = cq_g[j0g + o];
     cq[o] = q >= 0 ? q - g0 : -1;
@@ -279,11 +288,11 @@ void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom*
   for (int f = 0; f < F && f < 8; ++f) A.kind[f] = bc_kind[f];
   if (dtype == 0) {
     smem_raise<k_adj_chain<float>>(smem);
-    k_adj_chain<float><<<n_list, AC_T, smem, s>>>(A, F, G, geo_list, lev_ptr, gsrc_ptr, (const float*)lpart, cq_g,
+    launch(k_adj_chain<float>, n_list, AC_T, smem, s, A, F, G, geo_list, lev_ptr, gsrc_ptr, (const float*)lpart, cq_g,
                                                   (const float*)cw_g, n_src, ng_total, (float*)lam);
   } else {
     smem_raise<k_adj_chain<double>>(smem);
-    k_adj_chain<double><<<n_list, AC_T, smem, s>>>(A, F, G, geo_list, lev_ptr, gsrc_ptr, (const double*)lpart,
+    launch(k_adj_chain<double>, n_list, AC_T, smem, s, A, F, G, geo_list, lev_ptr, gsrc_ptr, (const double*)lpart,
                                                    cq_g, (const double*)cw_g, n_src, ng_total, (double*)lam);
   }
 }
@@ -300,6 +309,7 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
                             const int* __restrict__ pos_of_cell, int rmax,
                             const double* __restrict__ wtab, const double* __restrict__ sv,
                             const T* __restrict__ lam, int accumulate, int kmax) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int p = i / kmax, k = i - p * kmax;
   if (p >= ng) return;
@@ -354,9 +364,9 @@ void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* 
   // one thread per (ghost, member): K = 3 in 2D, 7 in 3D (kmax covers both)
   int n = ng * kmax;
   if (dtype == 0)
-    k_adj_fluid<float><<<(n + T - 1) / T, T, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const float*)lam, accumulate, kmax);
+    launch(k_adj_fluid<float>, (n + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const float*)lam, accumulate, kmax);
   else
-    k_adj_fluid<double><<<(n + T - 1) / T, T, 0, s>>>(A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const double*)lam, accumulate, kmax);
+    launch(k_adj_fluid<double>, (n + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const double*)lam, accumulate, kmax);
 }
 
 // Fluid targets in two passes at reach 1: the probe needs no lambda, so it
@@ -371,6 +381,7 @@ __global__ void k_adj_fprobe(int ng, const Geom* __restrict__ G, const int* __re
                              const int8_t* __restrict__ tags, const int* __restrict__ pos_of_cell, int kmax,
                              int cap, int* __restrict__ fcnt, int* __restrict__ fcell, int* __restrict__ fsrc,
                              int* status) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = i / kmax, k = i - p * kmax;
   if (p >= ng) return;
@@ -412,6 +423,7 @@ __global__ void k_adj_fpull(AdjSet A, int F, int ng, int n_inc, int cap, const i
                             const int* __restrict__ fcell, const int* __restrict__ fsrc,
                             const double* __restrict__ wtab, const double* __restrict__ sv,
                             const T* __restrict__ lam, int accumulate) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_inc) return;
   const int n = fcnt[i];
@@ -449,7 +461,7 @@ void launch_adj_fprobe(int ng, const Geom* G, const int* g_geo, const int* g_cel
                        int* fsrc, int* status, cudaStream_t s, int T) {
   if (ng <= 0) return;
   const int n = ng * kmax;
-  k_adj_fprobe<<<(n + T - 1) / T, T, 0, s>>>(ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, kmax, cap, fcnt,
+  launch(k_adj_fprobe, (n + T - 1) / T, T, 0, s, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, kmax, cap, fcnt,
                                              fcell, fsrc, status);
 }
 
@@ -461,10 +473,10 @@ void launch_adj_fpull(int dtype, int F, const int* bc_kind, int ng, int kmax, in
   for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.grad[f] = grad[f]; }
   const int n = ng * kmax;
   if (dtype == 0)
-    k_adj_fpull<float><<<(n + T - 1) / T, T, 0, s>>>(A, F, ng, n, cap, fcnt, fcell, fsrc, wtab, sv,
+    launch(k_adj_fpull<float>, (n + T - 1) / T, T, 0, s, A, F, ng, n, cap, fcnt, fcell, fsrc, wtab, sv,
                                                      (const float*)lam, accumulate);
   else
-    k_adj_fpull<double><<<(n + T - 1) / T, T, 0, s>>>(A, F, ng, n, cap, fcnt, fcell, fsrc, wtab, sv,
+    launch(k_adj_fpull<double>, (n + T - 1) / T, T, 0, s, A, F, ng, n, cap, fcnt, fcell, fsrc, wtab, sv,
                                                       (const double*)lam, accumulate);
 }
 
@@ -472,6 +484,7 @@ template <typename T>
 __global__ void k_adj_bc(AdjSet A, int F, int ng, const Geom* __restrict__ G,
                          const int* __restrict__ g_geo, const int* __restrict__ g_cell,
                          const double* __restrict__ wtab, const T* __restrict__ lam, int accumulate) {
+  pdl_enter();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
   long long c = G[g_geo[p]].cell_off + g_cell[p];
@@ -490,9 +503,9 @@ void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, 
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.gbc[f] = grad_bc[f]; A.grad[f] = grad[f]; }
   if (dtype == 0)
-    k_adj_bc<float><<<(ng + T - 1) / T, T, 0, s>>>(A, F, ng, G, g_geo, g_cell, wtab, (const float*)lam, accumulate);
+    launch(k_adj_bc<float>, (ng + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, wtab, (const float*)lam, accumulate);
   else
-    k_adj_bc<double><<<(ng + T - 1) / T, T, 0, s>>>(A, F, ng, G, g_geo, g_cell, wtab, (const double*)lam, accumulate);
+    launch(k_adj_bc<double>, (ng + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, wtab, (const double*)lam, accumulate);
 }
 
 }  // namespace ebr

@@ -17,6 +17,10 @@
 
 using namespace ebr;
 
+namespace ebr {
+int g_pdl = 1;
+}
+
 // an NVTX range around every entry point (a no-op unless a profiler is
 // attached), so that a timeline shows the library's calls
 struct EbrRange {
@@ -44,7 +48,7 @@ struct ChainPlan {
 // the kernels' profiling records (ebr_profile_read).
 enum TuneId { TU_IFACE, TU_PLACE, TU_GHOST, TU_DEPS, TU_TABLES, TU_GSRC, TU_FILL_PART, TU_ADJ_SEED,
               TU_ADJ_PART, TU_ADJ_PROBE, TU_ADJ_FLUID, TU_ADJ_BC, TU_N };
-static const char* const kTuneNames[TU_N] = {"iface", "place", "ghost_write", "deps", "tables", "gsrc",
+static const char* const kTuneNames[TU_N] = {"iface", "place", "ghost_geom", "deps", "tables", "gsrc",
                                              "fill_part", "adj_seed", "adj_part", "adj_probe", "adj_fluid",
                                              "adj_bc"};
 constexpr int TUNE_DEFAULT = 128;
@@ -105,6 +109,10 @@ struct Ctx {
   int* gpos = nullptr;
   void* scan_tmp = nullptr;
   int8_t* tags = nullptr;      // last tag array the caller gave
+  // single-pass scan states of a re-run (rows, interface cells, ghost
+  // targets): counters and tile words in one buffer, zeroed at every plan
+  unsigned* lb_mem = nullptr;
+  Lookback lb_rows{}, lb_iface{}, lb_gsrc{};
 
   // ghosts
   int ng = 0;
@@ -122,6 +130,7 @@ struct Ctx {
   double* wtab = nullptr;
   double* ftab = nullptr;
   int *gsrc_cnt = nullptr, *gsrc_ptr = nullptr, *gsrc = nullptr;
+  int* gsrc_mem = nullptr;     // ghost position of each stencil member [K][ng] (-1: not a ghost)
   int n_gsrc = 0;
   std::vector<int> h_gsrc_geo;   // sources per geometry
   int *own_flag = nullptr, *own_ptr = nullptr, *ft_cell = nullptr, *ft_geo = nullptr,
@@ -348,23 +357,6 @@ void destroy_side(Ctx* c) {
   c->ev_fork = c->ev_join = nullptr;
 }
 
-// k_check: compare scanned offsets at geometry boundaries with the plan
-__global__ void k_check(const Geom* G, int B, const int* row_ptr, const int* gpos, int n_iface,
-                        int ng, const int* nlev, int stage, int* status) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
-  const Geom& g = G[b];
-  if (stage == 0) {
-    // interface offsets of the rows, then ghost offsets of the interface list
-    if (row_ptr[g.row_off] != g.iface_off) set_status(status, S_ESHAPE);
-    if (b == B - 1 && row_ptr[g.row_off + g.n_rows] != n_iface) set_status(status, S_ESHAPE);
-    if (gpos[g.iface_off] != g.ghost_off) set_status(status, S_ESHAPE);
-    if (b == B - 1 && gpos[n_iface] != ng) set_status(status, S_ESHAPE);
-  } else {
-    if (nlev[b] != g.n_levels) set_status(status, S_ESHAPE);
-  }
-}
-
 int max_smem_optin() {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
@@ -374,6 +366,27 @@ int max_smem_optin() {
 
 ebr_status upload_geoms(Ctx* c) {
   CK(cudaMemcpy(c->dG, c->hG.data(), sizeof(Geom) * c->B, cudaMemcpyHostToDevice));
+  return EBR_OK;
+}
+
+// the single-pass scan states of the re-run kernels (sizes of the plan)
+constexpr int LB_SPIN_LIMIT = 1 << 20;
+
+ebr_status lookback_alloc(Ctx* c, cudaStream_t s) {
+  const size_t t[3] = {(size_t)(c->total_rows + LB_T - 1) / LB_T, (size_t)(c->n_iface + LB_T - 1) / LB_T,
+                       (size_t)(c->ng + LB_T - 1) / LB_T};
+  // 16 counter words (three used per state), then the tile words (8 bytes)
+  const size_t words = 16 + 2 * (t[0] + t[1] + t[2]);
+  AL(c->lb_mem, words);
+  CK(cudaMemsetAsync(c->lb_mem, 0, words * sizeof(unsigned), s));
+  unsigned long long* tiles = reinterpret_cast<unsigned long long*>(c->lb_mem + 16);
+  Lookback* L[3] = {&c->lb_rows, &c->lb_iface, &c->lb_gsrc};
+  for (int i = 0; i < 3; ++i) {
+    L[i]->ctr = c->lb_mem + 4 * i;
+    L[i]->tiles = tiles;
+    L[i]->spin_limit = LB_SPIN_LIMIT;
+    tiles += t[i];
+  }
   return EBR_OK;
 }
 
@@ -387,16 +400,17 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   prof_end(c, s);
   c->launches += 1;
   CKL();
-  prof_begin(c, s, "iface");
-  launch_iface(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, c->row_cnt, nullptr, nullptr,
-               nullptr, nullptr, 0, 0, c->d_status, s, c->tb[TU_IFACE]);
-  prof_end(c, s);
-  prof_begin(c, s, "scan");
-  launch_scan(c->row_cnt, c->row_ptr, c->total_rows, c->scan_tmp, s);
-  prof_end(c, s);
-  c->launches += 3;
-  CKL();
   if (planning) {
+    // counts, their scan, the sizes on the host, then the interface cells
+    prof_begin(c, s, "iface");
+    launch_iface(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, c->row_cnt, nullptr, nullptr,
+                 nullptr, nullptr, 0, 0, c->d_status, s, c->tb[TU_IFACE]);
+    prof_end(c, s);
+    prof_begin(c, s, "scan");
+    launch_scan(c->row_cnt, c->row_ptr, c->total_rows, c->scan_tmp, s);
+    prof_end(c, s);
+    c->launches += 3;
+    CKL();
     std::vector<int> hp(c->total_rows + 1);
     CK(cudaMemcpyAsync(hp.data(), c->row_ptr, sizeof(int) * (c->total_rows + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -413,30 +427,59 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
     AL(c->iface_n, 3 * (size_t)ni);
     AL(c->gflag, ni);
     AL(c->gpos, ni + 1);
+    prof_begin(c, s, "iface");
+    launch_iface(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, nullptr, c->row_ptr,
+                 c->iface_cell, c->iface_geo, c->iface_solid, 1, c->n_iface, c->d_status, s, c->tb[TU_IFACE]);
+    prof_end(c, s);
+    c->launches += 1;
+  } else {
+    // a re-run with the plan's sizes: counts, offsets and cells in one launch
+    prof_begin(c, s, "iface");
+    launch_iface_fused(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, c->row_ptr, c->iface_cell,
+                       c->iface_geo, c->iface_solid, c->n_iface, c->lb_rows, c->d_status, s);
+    prof_end(c, s);
+    c->launches += 1;
   }
-  prof_begin(c, s, "iface");
-  launch_iface(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, nullptr, c->row_ptr,
-               c->iface_cell, c->iface_geo, c->iface_solid, 1, c->n_iface, c->d_status, s, c->tb[TU_IFACE]);
-  prof_end(c, s);
   prof_begin(c, s, "place");
   launch_place(c->dG, c->n_iface, c->iface_cell, c->iface_geo, c->iface_solid, c->placement,
                d_tags, c->iface_psi, c->iface_n, c->d_status, s, c->tb[TU_PLACE]);
   prof_end(c, s);
-  c->launches += 2;
+  c->launches += 1;
+  // a re-run of one-layer HGC takes pass B of the reclassification into the
+  // compaction launch
+  const bool fuse_b = !planning && c->placement == EBR_HGC && c->layers == 1;
   if (c->placement == EBR_HGC) {
     prof_begin(c, s, "reclassify");
     launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 0, s);
     prof_end(c, s);
-    prof_begin(c, s, "reclassify");
-    launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 1, s);
-    prof_end(c, s);
-    c->launches += 2;
+    c->launches += 1;
+    if (!fuse_b) {
+      prof_begin(c, s, "reclassify");
+      launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 1, s);
+      prof_end(c, s);
+      c->launches += 1;
+    }
   }
   if (c->layers == 2) {
     prof_begin(c, s, "layer2");
     launch_layer2(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->d_status, s);
     prof_end(c, s);
     c->launches += 1;
+  }
+  if (!planning) {
+    prof_begin(c, s, "ghost_compact");
+    launch_ghost_compact(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, fuse_b ? 1 : 0, c->gpos,
+                         c->ng, c->gs_cell, c->gs_geo, c->gs_meta, c->lb_iface, c->d_status, s);
+    prof_end(c, s);
+    // the offsets against the plan: block 0 of the closest-point kernel
+    prof_begin(c, s, "ghost_geom");
+    launch_ghost_geom(c->dG, c->placement, c->ng, c->gs_cell, c->gs_geo, c->gs_psi, c->gs_n, c->gs_meta,
+                      c->d_stats + 1, c->d_status, s, c->tb[TU_GHOST],
+                      PlanCheck{c->row_ptr, c->gpos, c->d_nlev, c->B, c->n_iface, c->ng, 0});
+    prof_end(c, s);
+    c->launches += 2;
+    CKL();
+    return EBR_OK;
   }
   prof_begin(c, s, "ghost_flags");
   launch_ghost_flags(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->gflag, s);
@@ -446,7 +489,7 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   prof_end(c, s);
   c->launches += 3;
   CKL();
-  if (planning) {
+  {
     std::vector<int> hp(c->n_iface + 1);
     CK(cudaMemcpyAsync(hp.data(), c->gpos, sizeof(int) * (c->n_iface + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -464,10 +507,6 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
     AL(c->gs_n, 3 * (size_t)ng);
     AL(c->gs_meta, ng);
     CK(cudaMemsetAsync(c->d_stats + 1, 0, sizeof(int), s));
-  } else {
-    k_check<<<(c->B + 127) / 128, 128, 0, s>>>(c->dG, c->B, c->row_ptr, c->gpos, c->n_iface, c->ng,
-                                               c->d_nlev, 0, c->d_status);
-    c->launches += 1;
   }
   prof_begin(c, s, "ghost_write");
   launch_ghost_write(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->iface_psi,
@@ -476,14 +515,12 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   prof_end(c, s);
   c->launches += 2;
   CKL();
-  if (planning) {
-    CK(cudaMemcpyAsync(&c->rmax, c->d_stats + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (c->rmax < 1) c->rmax = 1;
-    ebr_status st = upload_geoms(c);
-    if (st) return st;
-  }
-  return EBR_OK;
+  CK(cudaMemcpyAsync(&c->rmax, c->d_stats + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (c->rmax < 1) c->rmax = 1;
+  ebr_status st = upload_geoms(c);
+  if (st) return st;
+  return lookback_alloc(c, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -516,6 +553,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     AL(c->ftab, 33 * (size_t)ng);
     AL(c->gsrc_cnt, ng);
     AL(c->gsrc_ptr, ng + 1);
+    AL(c->gsrc_mem, (size_t)stencil_k(c->hG[0].dim) * ng);
     AL(c->sv, 64 * (size_t)ng);
     {
       ebr_status st = balloc(c, &c->lam, 8 * 8 * (size_t)ng);   // [F <= 8][ng] doubles
@@ -534,7 +572,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     }
   }
   prof_begin(c, s, "poscell");
-  launch_poscell(c->dG, ng, c->gs_cell, c->gs_geo, nullptr, c->pos_of_cell, s);
+  launch_poscell(c->dG, ng, c->gs_cell, c->gs_geo, nullptr, c->pos_of_cell, c->gsrc_cnt, s);
   prof_end(c, s);
   prof_begin(c, s, "deps");
   launch_deps(c->dG, ng, c->gs_cell, c->gs_geo, c->gs_meta, c->gs_n, c->tags, c->pos_of_cell,
@@ -558,15 +596,13 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     CK(cudaMemcpy(c->h_lev_ptr.data(), c->lev_ptr, sizeof(int) * (ng + c->B + 1), cudaMemcpyDeviceToHost));
     ebr_status st = upload_geoms(c);
     if (st) return st;
-  } else {
-    k_check<<<(c->B + 127) / 128, 128, 0, s>>>(c->dG, c->B, c->row_ptr, c->gpos, c->n_iface, c->ng,
-                                               c->d_nlev, 1, c->d_status);
-    c->launches += 1;
   }
   prof_begin(c, s, "reorder");
+  // a re-run checks the level counts against the plan in block 0 of the reorder
   launch_reorder(c->dG, c->pos_of_cell, ng, c->order_pos, c->gs_cell, c->gs_geo, c->gs_psi, c->gs_n,
                  c->gs_meta, c->dep, c->level, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->g_dep,
-                 c->g_level, s);
+                 c->g_level, s, PlanCheck{c->row_ptr, c->gpos, c->d_nlev, c->B, c->n_iface, c->ng, planning ? -1 : 1},
+                 c->d_status);
   prof_end(c, s);
   // The coefficient tables and the ghost-target source lists (adjoint only)
   // are independent: outside planning the source lists run on the second
@@ -583,17 +619,18 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   launch_tables(c->dG, ng, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->tags, c->wtab,
                 c->ftab, s, c->tb[TU_TABLES]);
   prof_end(c, s);
-  // ghost-target sources
+  c->launches += 2;   // reorder, tables
+  // ghost-target sources by transposition: member positions and counts; when
+  // planning the scan, the sizes on the host and the lists; in a re-run the
+  // offsets in one single-pass launch, then the lists
+  const int kmax = stencil_k(c->hG[0].dim);
   prof_begin(c, sg, "gsrc");
-  launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax, nullptr,
-              c->gsrc_cnt, 0, sg, c->tb[TU_GSRC]);
-  prof_end(c, sg);
-  prof_begin(c, sg, "scan");
-  launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, sg);
-  prof_end(c, sg);
-  c->launches += 5;   // reorder, tables, source counts, scan (2)
-  if (planning) CKL();   // outside planning: checked after the join below
+  launch_gsrc_count(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, kmax, c->gsrc_mem,
+                    c->gsrc_cnt, sg, c->tb[TU_GSRC]);
   if (planning) {
+    launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, sg);
+    c->launches += 3;
+    CKL();
     CK(cudaMemcpyAsync(&c->n_gsrc, c->gsrc_ptr + ng, sizeof(int), cudaMemcpyDeviceToHost, s));
     std::vector<int> hp(ng + 1);
     CK(cudaMemcpyAsync(hp.data(), c->gsrc_ptr, sizeof(int) * (ng + 1), cudaMemcpyDeviceToHost, s));
@@ -607,12 +644,16 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     AL(c->acq, c->n_gsrc);
     ebr_status st = balloc(c, &c->acw, 2 * 8 * std::max<size_t>((size_t)c->n_gsrc, 1));
     if (st) return st;
+    launch_gsrc_lists(ng, kmax, c->gsrc_mem, c->gsrc_ptr, c->gsrc_cnt, c->gsrc, c->n_gsrc, c->d_status, true, sg,
+                      c->tb[TU_GSRC]);
+    c->launches += 3;
+  } else {
+    launch_gsrc_place(ng, c->gsrc_cnt, c->gsrc_ptr, c->gsrc, c->n_gsrc, c->lb_gsrc, c->d_status, sg);
+    launch_gsrc_lists(ng, kmax, c->gsrc_mem, c->gsrc_ptr, c->gsrc_cnt, c->gsrc, c->n_gsrc, c->d_status, false,
+                      sg, c->tb[TU_GSRC]);
+    c->launches += 4;
   }
-  prof_begin(c, sg, "gsrc");
-  launch_gsrc(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, c->rmax,
-              c->gsrc_ptr, c->gsrc, 1, sg, c->tb[TU_GSRC]);
   prof_end(c, sg);
-  c->launches += 1;
   if (!planning) {
     CK(cudaEventRecord(c->ev_join, c->side));
     CK(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -761,6 +802,10 @@ const char* ebr_last_error(const void* ctx) {
 int64_t ebr_launch_count(const void* ctx) {
   return ctx ? static_cast<const Ctx*>(ctx)->launches : 0;
 }
+
+void ebr_set_pdl(int32_t enable) { ebr::g_pdl = enable != 0; }
+
+int32_t ebr_get_pdl(void) { return ebr::g_pdl; }
 
 }  // extern "C"
 
@@ -1850,6 +1895,36 @@ int32_t ebr_profile_read(void* ctx, int32_t max_entries, char* h_names, double* 
   if (!keep) {
     c->recs.clear();
     c->pool_used = 0;
+  }
+  return n;
+}
+
+int32_t ebr_profile_timeline(void* ctx, int32_t max_entries, char* h_names, double* h_start_ms,
+                             double* h_end_ms) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  const Ctx::ProfRec* first = nullptr;
+  for (auto& r : c->recs)
+    if (r.a && r.b) { first = &r; break; }
+  if (!first) return 0;
+  int n = 0;
+  for (auto& r : c->recs) {
+    if (!r.a || !r.b) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return fail(c, EBR_ECUDA, "event synchronise failed");
+    if (n < max_entries) {
+      float t0 = 0.0f, t1 = 0.0f;
+      // a record that began before the first one reads as a negative start
+      if (cudaEventElapsedTime(&t0, first->a, r.a) != cudaSuccess ||
+          cudaEventElapsedTime(&t1, first->a, r.b) != cudaSuccess)
+        return fail(c, EBR_ECUDA, "event timing failed");
+      if (h_names) {
+        std::strncpy(h_names + 32 * n, r.name, 31);
+        h_names[32 * n + 31] = 0;
+      }
+      if (h_start_ms) h_start_ms[n] = t0;
+      if (h_end_ms) h_end_ms[n] = t1;
+    }
+    ++n;
   }
   return n;
 }

@@ -11,6 +11,7 @@
 // neighbour rows, so they are enumerated per row already sorted by linear
 // index, without re-reading the tag array.
 #include "ebr_kernels.cuh"
+#include "lookback.cuh"
 
 namespace ebr {
 
@@ -532,9 +533,10 @@ __device__ void exact_run_grp(const Geom& g, int j, int k, const RowGrp& Gp, int
   }
 }
 
-__global__ void __launch_bounds__(256) k_rows(const Geom* __restrict__ G, const int* __restrict__ row_off,
+__global__ void __launch_bounds__(256, 5) k_rows(const Geom* __restrict__ G, const int* __restrict__ row_off,
                                               int B, int total_rows, int2* __restrict__ runs,
                                               int8_t* __restrict__ tags, int* status, int* stats) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) / RG;
   if (row >= total_rows) return;                 // the whole group leaves together
@@ -567,41 +569,54 @@ __global__ void __launch_bounds__(256) k_rows(const Geom* __restrict__ G, const 
     const long long i = q - rst;
     tags[q] = (int8_t)(i >= s && i <= t);
   }
-  // aligned middle: 16 cells per lane per step, offsets from the row start in
-  // 32-bit.  A chunk wholly outside or inside the run is a constant; only the
-  // (at most two) chunks that hold an end of the run build their bytes: bytes
-  // [lo, hi) lie inside, each 32-bit word a difference of two prefix masks of
-  // 0x01 bytes.
+  // aligned middle: 16-byte chunks, chunk c holding cells [ia0 + 16 c,
+  // ia0 + 16 c + 15] (offsets from the row start in 32-bit).  Chunks [0, zb)
+  // lie before the run, [ib0, ib1) inside it, [za, nch) after it: constant
+  // words in tight store loops, lane sl taking the chunks c = sl (mod RG).
+  // Only the (at most two) chunks of [zb, ib0) and [ib1, za) hold an end of
+  // the run and build their bytes: bytes [lo, hi) lie inside, each 32-bit word
+  // a difference of two prefix masks of 0x01 bytes.
   int8_t* const rowp = tags + rst;
   const int ia0 = (int)(a0 - rst), ia1 = (int)(a1 - rst);
-  for (int i0 = ia0 + 16 * Gp.sl; i0 < ia1; i0 += 16 * RG) {
-    uint4 v;
-    if (i0 + 15 < s || i0 > t) {
-      v = make_uint4(0u, 0u, 0u, 0u);
-    } else if (i0 >= s && i0 + 15 <= t) {
-      v = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
-    } else {
-      const int lo = min(max(s - i0, 0), 16);
-      const int hi = min(max(t + 1 - i0, 0), 16);
-      uint32_t w[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int l = min(max(lo - 4 * q, 0), 4), h = min(max(hi - 4 * q, 0), 4);
-        const uint32_t ph = h ? (0x01010101u >> (8 * (4 - h))) : 0u;
-        const uint32_t pl = l ? (0x01010101u >> (8 * (4 - l))) : 0u;
-        w[q] = h > l ? (ph & ~pl) : 0u;
-      }
-      v = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    *reinterpret_cast<uint4*>(rowp + i0) = v;
+  const int nch = (ia1 - ia0) >> 4;
+  int zb = nch, ib0 = nch, ib1 = nch, za = nch;
+  if (s <= t) {
+    zb = min(max((s - ia0) >> 4, 0), nch);
+    ib0 = min(max((s - ia0 + 15) >> 4, 0), nch);
+    ib1 = max(min(max((t + 1 - ia0) >> 4, 0), nch), ib0);
+    za = min(max(((t - ia0) >> 4) + 1, 0), nch);
   }
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  const uint4 one4 = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+  uint4* const chunk = reinterpret_cast<uint4*>(rowp + ia0);
+  // first chunk index >= c0 that belongs to this lane
+  auto first = [&](int c0) { return c0 + ((Gp.sl - c0) & (RG - 1)); };
+  for (int c = first(0); c < zb; c += RG) chunk[c] = zero4;
+  for (int c = first(ib0); c < ib1; c += RG) chunk[c] = one4;
+  for (int c = first(za); c < nch; c += RG) chunk[c] = zero4;
+  auto edge = [&](int c) {
+    const int i0 = ia0 + 16 * c;
+    const int lo = min(max(s - i0, 0), 16);
+    const int hi = min(max(t + 1 - i0, 0), 16);
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int l = min(max(lo - 4 * q, 0), 4), h = min(max(hi - 4 * q, 0), 4);
+      const uint32_t ph = h ? (0x01010101u >> (8 * (4 - h))) : 0u;
+      const uint32_t pl = l ? (0x01010101u >> (8 * (4 - l))) : 0u;
+      w[q] = h > l ? (ph & ~pl) : 0u;
+    }
+    chunk[c] = make_uint4(w[0], w[1], w[2], w[3]);
+  };
+  for (int c = first(zb); c < ib0; c += RG) edge(c);
+  for (int c = first(ib1); c < za; c += RG) edge(c);
 }
 
 void launch_rows(const Geom* G, const int* row_off, int B, int total_rows, int2* runs,
                  int8_t* tags, int* status, int* stats, cudaStream_t s) {
   if (total_rows <= 0) return;
   const long long threads = (long long)total_rows * RG;
-  k_rows<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(G, row_off, B, total_rows, runs, tags, status, stats);
+  launch(k_rows, (unsigned)((threads + 255) / 256), 256, 0, s, G, row_off, B, total_rows, runs, tags, status, stats);
 }
 
 // ---------------------------------------------------------------------------
@@ -623,20 +638,23 @@ __device__ inline void add_diff(Iv* v, int& m, int2 R, int2 Q, int n) {
   add_iv(v, m, max(R.x, Q.y + 1), R.y, n);
 }
 
-__global__ void k_iface(const Geom* __restrict__ G, const int* __restrict__ row_off, int B,
-                        int total_rows, const int2* __restrict__ runs, int* __restrict__ row_cnt,
-                        const int* __restrict__ row_ptr, int* __restrict__ iface_cell,
-                        int* __restrict__ iface_geo, int8_t* __restrict__ iface_solid, int write,
-                        int cap, int* status) {
-  int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= total_rows) return;
-  int b = find_seg(row_off, B, row);
-  const Geom& g = G[b];
-  int local = row - g.row_off;
-  int ny = g.n[1], nz = g.dim == 3 ? g.n[2] : 1, n = g.n[0];
-  int j = local % ny, k = local / ny;
-  int2 R = runs[row];
+// interface intervals of one row (sorted, merged: v[0..w)), its run and the
+// band limits of the second layer
+struct RowIface {
   Iv v[24];
+  int w;
+  int2 R;
+  int bandA, bandB, bandC, bandD;
+  int j, k, ny, nz, n;
+};
+
+__device__ inline void row_iface(const Geom& g, int local, const int2* __restrict__ runs, RowIface& I) {
+  const int ny = g.n[1], nz = g.dim == 3 ? g.n[2] : 1, n = g.n[0];
+  const int j = local % ny, k = local / ny;
+  I.j = j; I.k = k; I.ny = ny; I.nz = nz; I.n = n;
+  const int2 R = runs[g.row_off + local];
+  I.R = R;
+  Iv* v = I.v;
   int m = 0;
   if (R.x <= R.y) {
     if (R.x > 0) { add_iv(v, m, R.x, R.x, n); add_iv(v, m, R.x - 1, R.x - 1, n); }
@@ -655,7 +673,7 @@ __global__ void k_iface(const Geom* __restrict__ G, const int* __restrict__ row_
   // only when every in-grid row of the box has a run covering it with the
   // reach to spare, a run end at the grid edge counting as covered), listed
   // as band cells (flag 2)
-  int bandA = 1, bandB = 0, bandC = 1, bandD = 0;
+  I.bandA = 1; I.bandB = 0; I.bandC = 1; I.bandD = 0;
   if (g.layers == 2 && R.x <= R.y) {
     int elo = 0, ehi = n - 1;
     const int ry = g.reach[1], rz = g.dim == 3 ? g.reach[2] : 0, rx = g.reach[0];
@@ -668,13 +686,13 @@ __global__ void k_iface(const Geom* __restrict__ G, const int* __restrict__ row_
         elo = max(elo, Q.x == 0 ? 0 : Q.x + rx);
         ehi = min(ehi, Q.y == n - 1 ? n - 1 : Q.y - rx);
       }
-    if (elo > ehi) { bandA = R.x; bandB = R.y; }
+    if (elo > ehi) { I.bandA = R.x; I.bandB = R.y; }
     else {
-      bandA = R.x; bandB = min(R.y, elo - 1);
-      bandC = max(R.x, ehi + 1); bandD = R.y;
+      I.bandA = R.x; I.bandB = min(R.y, elo - 1);
+      I.bandC = max(R.x, ehi + 1); I.bandD = R.y;
     }
-    add_iv(v, m, bandA, bandB, n);
-    add_iv(v, m, bandC, bandD, n);
+    add_iv(v, m, I.bandA, I.bandB, n);
+    add_iv(v, m, I.bandC, I.bandD, n);
   }
   // sort by start, merge
   for (int x = 1; x < m; ++x) {
@@ -688,23 +706,32 @@ __global__ void k_iface(const Geom* __restrict__ G, const int* __restrict__ row_
     if (w > 0 && v[x].a <= v[w - 1].b + 1) v[w - 1].b = max(v[w - 1].b, v[x].b);
     else v[w++] = v[x];
   }
-  if (!write) {
-    int cnt = 0;
-    for (int x = 0; x < w; ++x) cnt += v[x].b - v[x].a + 1;
-    row_cnt[row] = cnt;
-    return;
-  }
-  int o = row_ptr[row];
-  int rowbase = n * (j + ny * k);
-  // interface cells of the row: the run's ends and the cells across them,
-  // and the cells that differ from a face-neighbour row (the same sets as
-  // above); the rest of the list (second layer only) are band cells
-  for (int x = 0; x < w; ++x) {
-    for (int i = v[x].a; i <= v[x].b; ++i) {
-      if (o >= cap) { set_status(status, S_ESHAPE); return; }
+  I.w = w;
+}
+
+__device__ inline int row_iface_count(const RowIface& I) {
+  int cnt = 0;
+  for (int x = 0; x < I.w; ++x) cnt += I.v[x].b - I.v[x].a + 1;
+  return cnt;
+}
+
+// interface cells of the row from list position o: the run's ends and the
+// cells across them, and the cells that differ from a face-neighbour row
+// (the same sets as above); the rest of the list (second layer only) are band
+// cells.  Returns false (status EBR_ESHAPE) when the list would pass cap.
+__device__ inline bool row_iface_write(const Geom& g, int b, const int2* __restrict__ runs, const RowIface& I,
+                                       int o, int cap, int* __restrict__ iface_cell, int* __restrict__ iface_geo,
+                                       int8_t* __restrict__ iface_solid, int* status) {
+  const int dj[4] = {-1, 1, 0, 0}, dk[4] = {0, 0, -1, 1};
+  const int2 R = I.R;
+  const int n = I.n, j = I.j, k = I.k, ny = I.ny, nz = I.nz;
+  const int rowbase = n * (j + ny * k);
+  for (int x = 0; x < I.w; ++x) {
+    for (int i = I.v[x].a; i <= I.v[x].b; ++i) {
+      if (o >= cap) { set_status(status, S_ESHAPE); return false; }
       const bool sol = i >= R.x && i <= R.y;
       int8_t flag = (int8_t)sol;
-      if (g.layers == 2 && sol && ((i >= bandA && i <= bandB) || (i >= bandC && i <= bandD))) {
+      if (g.layers == 2 && sol && ((i >= I.bandA && i <= I.bandB) || (i >= I.bandC && i <= I.bandD))) {
         // a band cell is an interface cell too when a face neighbour is fluid
         bool face = i == R.x && R.x > 0;
         face = face || (i == R.y && R.y < n - 1);
@@ -722,15 +749,74 @@ __global__ void k_iface(const Geom* __restrict__ G, const int* __restrict__ row_
       ++o;
     }
   }
+  return true;
+}
+
+__global__ void k_iface(const Geom* __restrict__ G, const int* __restrict__ row_off, int B,
+                        int total_rows, const int2* __restrict__ runs, int* __restrict__ row_cnt,
+                        const int* __restrict__ row_ptr, int* __restrict__ iface_cell,
+                        int* __restrict__ iface_geo, int8_t* __restrict__ iface_solid, int write,
+                        int cap, int* status) {
+  pdl_enter();
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= total_rows) return;
+  int b = find_seg(row_off, B, row);
+  const Geom& g = G[b];
+  RowIface I;
+  row_iface(g, row - g.row_off, runs, I);
+  if (!write) {
+    row_cnt[row] = row_iface_count(I);
+    return;
+  }
+  row_iface_write(g, b, runs, I, row_ptr[row], cap, iface_cell, iface_geo, iface_solid, status);
+}
+
+// One launch instead of count + scan + write: the rows' counts, their
+// offsets by a single-pass scan in row order (the same offsets as the scan of
+// the counts), then the cells.  row_ptr[total_rows] = total.
+__global__ void k_iface_fused(const Geom* __restrict__ G, const int* __restrict__ row_off, int B,
+                              int total_rows, const int2* __restrict__ runs, int* __restrict__ row_ptr,
+                              int* __restrict__ iface_cell, int* __restrict__ iface_geo,
+                              int8_t* __restrict__ iface_solid, int cap, const Lookback L, int* status) {
+  pdl_enter();
+  __shared__ int sh[32];
+  const LbBlock blk = lb_begin(L);
+  const int row = blk.tile * blockDim.x + threadIdx.x;
+  const bool on = row < total_rows;
+  int b = 0, cnt = 0;
+  RowIface I;
+  if (on) {
+    b = find_seg(row_off, B, row);
+    row_iface(G[b], row - G[b].row_off, runs, I);
+    cnt = row_iface_count(I);
+  }
+  int agg;
+  const int ex = block_excl_scan(cnt, sh, agg);
+  const long long base = lb_prefix(L, blk, (unsigned)agg, status);
+  if (base >= 0) {
+    if (on) {
+      row_ptr[row] = (int)(base + ex);
+      row_iface_write(G[b], b, runs, I, (int)(base + ex), cap, iface_cell, iface_geo, iface_solid, status);
+    }
+    if (row == total_rows - 1) row_ptr[total_rows] = (int)(base + ex + cnt);
+  }
+  lb_end(L);
 }
 
 void launch_iface(const Geom* G, const int* row_off, int B, int total_rows, const int2* runs,
                   int* row_cnt, const int* row_ptr, int* iface_cell, int* iface_geo,
                   int8_t* iface_solid, int write, int iface_cap, int* status, cudaStream_t s, int T) {
   if (total_rows <= 0) return;
-  k_iface<<<(total_rows + T - 1) / T, T, 0, s>>>(G, row_off, B, total_rows, runs, row_cnt,
-                                                   row_ptr, iface_cell, iface_geo, iface_solid,
-                                                   write, iface_cap, status);
+  launch(k_iface, (total_rows + T - 1) / T, T, 0, s, G, row_off, B, total_rows, runs, row_cnt,
+         row_ptr, iface_cell, iface_geo, iface_solid, write, iface_cap, status);
+}
+
+void launch_iface_fused(const Geom* G, const int* row_off, int B, int total_rows, const int2* runs,
+                        int* row_ptr, int* iface_cell, int* iface_geo, int8_t* iface_solid, int iface_cap,
+                        const Lookback& L, int* status, cudaStream_t s) {
+  if (total_rows <= 0) return;
+  launch(k_iface_fused, (total_rows + LB_T - 1) / LB_T, LB_T, 0, s, G, row_off, B, total_rows, runs, row_ptr,
+         iface_cell, iface_geo, iface_solid, iface_cap, L, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -747,6 +833,7 @@ __global__ void k_place(const Geom* __restrict__ G, int n_iface, const int* __re
                         const int* __restrict__ iface_geo, const int8_t* __restrict__ iface_solid,
                         int placement, int8_t* __restrict__ tags, double* __restrict__ psi_out,
                         double* __restrict__ n_out, int* status) {
+  pdl_enter();
   (void)psi_out;
   (void)n_out;
   int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -805,7 +892,7 @@ void launch_place(const Geom* G, int n_iface, const int* iface_cell, const int* 
                   const int8_t* iface_solid, int placement, int8_t* tags, double* iface_psi,
                   double* iface_n, int* status, cudaStream_t s, int T) {
   if (n_iface <= 0) return;
-  k_place<<<(n_iface + T - 1) / T, T, 0, s>>>(G, n_iface, iface_cell, iface_geo, iface_solid,
+  launch(k_place, (n_iface + T - 1) / T, T, 0, s, G, n_iface, iface_cell, iface_geo, iface_solid,
                                                 placement, tags, iface_psi, iface_n, status);
 }
 
@@ -813,8 +900,25 @@ void launch_place(const Geom* G, int n_iface, const int* iface_cell, const int* 
 // pass 1 (B): +2 without a tag-0 face neighbour -> 1.  In place is safe: pass A
 // only turns -2 into 0 and tests for 1; pass B only turns +2 into 1 and tests
 // for 0; pass B runs after pass A has completed.
+// does cell `cell` of the grid have a face neighbour tagged `look`?
+__device__ inline bool has_face_tag(const Geom& g, const int8_t* tg, int cell, int8_t look) {
+  int i, j, k;
+  cell_ijk(g, cell, i, j, k);
+  const int ijk[3] = {i, j, k};
+  const int stride[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  bool found = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.dim || found) continue;
+    if (ijk[a] > 0 && tg[cell - stride[a]] == look) found = true;
+    if (ijk[a] < g.n[a] - 1 && tg[cell + stride[a]] == look) found = true;
+  }
+  return found;
+}
+
 __global__ void k_reclassify(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
                              const int* __restrict__ iface_geo, int8_t* __restrict__ tags, int pass) {
+  pdl_enter();
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_iface) return;
   const Geom& g = G[iface_geo[m]];
@@ -823,25 +927,13 @@ __global__ void k_reclassify(const Geom* __restrict__ G, int n_iface, const int*
   int8_t me = tg[cell];
   int8_t want_self = pass == 0 ? -2 : 2;
   if (me != want_self) return;
-  int8_t look = pass == 0 ? 1 : 0;
-  int i, j, k;
-  cell_ijk(g, cell, i, j, k);
-  int ijk[3] = {i, j, k};
-  int stride[3] = {1, g.n[0], g.n[0] * g.n[1]};
-  bool found = false;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (a >= g.dim || found) continue;
-    if (ijk[a] > 0 && tg[cell - stride[a]] == look) found = true;
-    if (ijk[a] < g.n[a] - 1 && tg[cell + stride[a]] == look) found = true;
-  }
-  if (!found) tg[cell] = pass == 0 ? 0 : 1;
+  if (!has_face_tag(g, tg, cell, pass == 0 ? 1 : 0)) tg[cell] = pass == 0 ? 0 : 1;
 }
 
 void launch_reclassify(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                        int8_t* tags, int pass, cudaStream_t s) {
   if (n_iface <= 0) return;
-  k_reclassify<<<(n_iface + 127) / 128, 128, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, pass);
+  launch(k_reclassify, (n_iface + 127) / 128, 128, 0, s, G, n_iface, iface_cell, iface_geo, tags, pass);
 }
 
 // Second ghost layer (Sec. 7): after the first layer's placement and
@@ -851,6 +943,7 @@ void launch_reclassify(const Geom* G, int n_iface, const int* iface_cell, const 
 // margin), in double otherwise.
 __global__ void k_layer2(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
                          const int* __restrict__ iface_geo, int8_t* __restrict__ tags, int* status) {
+  pdl_enter();
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_iface) return;
   const Geom& g = G[iface_geo[m]];
@@ -901,12 +994,13 @@ __global__ void k_layer2(const Geom* __restrict__ G, int n_iface, const int* __r
 void launch_layer2(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo, int8_t* tags,
                    int* status, cudaStream_t s) {
   if (n_iface <= 0) return;
-  k_layer2<<<(n_iface + 127) / 128, 128, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, status);
+  launch(k_layer2, (n_iface + 127) / 128, 128, 0, s, G, n_iface, iface_cell, iface_geo, tags, status);
 }
 
 __global__ void k_ghost_flags(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
                               const int* __restrict__ iface_geo, const int8_t* __restrict__ tags,
                               int* __restrict__ flags) {
+  pdl_enter();
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_iface) return;
   const Geom& g = G[iface_geo[m]];
@@ -917,7 +1011,7 @@ __global__ void k_ghost_flags(const Geom* __restrict__ G, int n_iface, const int
 void launch_ghost_flags(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                         const int8_t* tags, int* flags, cudaStream_t s) {
   if (n_iface <= 0) return;
-  k_ghost_flags<<<(n_iface + 255) / 256, 256, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, flags);
+  launch(k_ghost_flags, (n_iface + 255) / 256, 256, 0, s, G, n_iface, iface_cell, iface_geo, tags, flags);
 }
 
 // compaction of the ghosts (index order): cell, geometry, fluid-side flag
@@ -925,6 +1019,7 @@ __global__ void k_ghost_write(const Geom* __restrict__ G, int n_iface, const int
                               const int* __restrict__ iface_geo, const int8_t* __restrict__ tags,
                               const int* __restrict__ gpos, int cap, int* __restrict__ gs_cell,
                               int* __restrict__ gs_geo, uint32_t* __restrict__ gs_meta, int* status) {
+  pdl_enter();
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_iface) return;
   int b = iface_geo[m];
@@ -939,13 +1034,68 @@ __global__ void k_ghost_write(const Geom* __restrict__ G, int n_iface, const int
   gs_meta[s] = t == -2 ? (1u << 22) : 0u;
 }
 
+// Ghost compaction in one launch instead of flags + scan + write.  With
+// pass_b (HGC, one layer) the cell's reclassification pass B comes first: +2
+// without a tag-0 face neighbour becomes 1 (the test reads only 0s, which
+// pass B neither makes nor removes, so the cells of the launch may run in any
+// order).  Then the ghost flag (tag +-2) of every interface cell, the offsets
+// by a single-pass scan in list order (the scan of the flags) and the ghost
+// records (cell, geometry, fluid-side flag).  gpos[n_iface] = total.
+__global__ void k_ghost_compact(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
+                                const int* __restrict__ iface_geo, int8_t* __restrict__ tags, int pass_b,
+                                int* __restrict__ gpos, int cap, int* __restrict__ gs_cell,
+                                int* __restrict__ gs_geo, uint32_t* __restrict__ gs_meta, const Lookback L,
+                                int* status) {
+  pdl_enter();
+  __shared__ int sh[32];
+  const LbBlock blk = lb_begin(L);
+  const int m = blk.tile * blockDim.x + threadIdx.x;
+  const bool on = m < n_iface;
+  int b = 0, cell = 0;
+  int8_t t = 0;
+  if (on) {
+    b = iface_geo[m];
+    const Geom& g = G[b];
+    cell = iface_cell[m];
+    int8_t* tg = tags + g.cell_off;
+    t = tg[cell];
+    if (pass_b && t == 2 && !has_face_tag(g, tg, cell, 0)) {
+      t = 1;
+      tg[cell] = 1;
+    }
+  }
+  const int flag = (t == 2 || t == -2) ? 1 : 0;
+  int agg;
+  const int ex = block_excl_scan(flag, sh, agg);
+  const long long base = lb_prefix(L, blk, (unsigned)agg, status);
+  if (base >= 0) {
+    if (on) {
+      const int q = (int)(base + ex);
+      gpos[m] = q;
+      if (flag) {
+        if (q >= cap) {
+          set_status(status, S_ESHAPE);
+        } else {
+          gs_cell[q] = cell;
+          gs_geo[q] = b;
+          gs_meta[q] = t == -2 ? (1u << 22) : 0u;
+        }
+      }
+    }
+    if (m == n_iface - 1) gpos[n_iface] = (int)(base + ex + flag);
+  }
+  lb_end(L);
+}
+
 // psi, S and n in double for the compacted ghosts only (Eq. signed_distance),
 // one ghost per thread so that no lane idles through the FP64 work; sign
 // bits e and stencil multipliers r (Eq. stencil_anisotropic for CGC_ES)
 __global__ void k_ghost_geom(const Geom* __restrict__ G, int ng, int placement,
                              const int* __restrict__ gs_cell, const int* __restrict__ gs_geo,
                              double* __restrict__ gs_psi, double* __restrict__ gs_n,
-                             uint32_t* __restrict__ gs_meta, int* rmax, int* status) {
+                             uint32_t* __restrict__ gs_meta, int* rmax, int* status, const PlanCheck chk) {
+  pdl_enter();
+  plan_check(G, chk, status);
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ng) return;
   const Geom& g = G[gs_geo[s]];
@@ -983,6 +1133,23 @@ __global__ void k_ghost_geom(const Geom* __restrict__ G, int ng, int placement,
   if (rloc > 1) atomicMax(rmax, rloc);
 }
 
+void launch_ghost_compact(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
+                          int8_t* tags, int pass_b, int* gpos, int ng_cap, int* gs_cell, int* gs_geo,
+                          uint32_t* gs_meta, const Lookback& L, int* status, cudaStream_t s) {
+  if (n_iface <= 0) return;
+  launch(k_ghost_compact, (n_iface + LB_T - 1) / LB_T, LB_T, 0, s, G, n_iface, iface_cell, iface_geo, tags,
+         pass_b, gpos, ng_cap, gs_cell, gs_geo, gs_meta, L, status);
+}
+
+// psi, S, n and the meta words of the compacted ghosts
+void launch_ghost_geom(const Geom* G, int placement, int ng_cap, int* gs_cell, int* gs_geo, double* gs_psi,
+                       double* gs_n, uint32_t* gs_meta, int* rmax, int* status, cudaStream_t s, int T,
+                       const PlanCheck& chk) {
+  if (ng_cap <= 0) return;
+  launch(k_ghost_geom, (ng_cap + T - 1) / T, T, 0, s, G, ng_cap, placement, gs_cell, gs_geo, gs_psi,
+         gs_n, gs_meta, rmax, status, chk);
+}
+
 void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                         const int8_t* tags, const double* iface_psi, const double* iface_n,
                         const int* gpos, int placement, int ng_cap, int* gs_cell, int* gs_geo,
@@ -991,11 +1158,11 @@ void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const
   (void)iface_psi;
   (void)iface_n;
   if (n_iface <= 0) return;
-  k_ghost_write<<<(n_iface + 255) / 256, 256, 0, s>>>(G, n_iface, iface_cell, iface_geo, tags, gpos,
+  launch(k_ghost_write, (n_iface + 255) / 256, 256, 0, s, G, n_iface, iface_cell, iface_geo, tags, gpos,
                                                       ng_cap, gs_cell, gs_geo, gs_meta, status);
   if (ng_cap <= 0) return;
-  k_ghost_geom<<<(ng_cap + T - 1) / T, T, 0, s>>>(G, ng_cap, placement, gs_cell, gs_geo, gs_psi,
-                                                    gs_n, gs_meta, rmax, status);
+  launch(k_ghost_geom, (ng_cap + T - 1) / T, T, 0, s, G, ng_cap, placement, gs_cell, gs_geo, gs_psi,
+         gs_n, gs_meta, rmax, status, PlanCheck{nullptr, nullptr, nullptr, 0, 0, 0, -1});
 }
 
 }  // namespace ebr

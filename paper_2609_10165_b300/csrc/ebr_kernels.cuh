@@ -5,9 +5,11 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "ebr_device.cuh"
+#include "lookback.cuh"
 
 namespace ebr {
 
@@ -21,6 +23,37 @@ __device__ inline int find_seg(const int* off, int B, int x) {
   return lo;
 }
 
+// Programmatic dependent launch.  A kernel launched through launch() may be
+// launched before the kernel ahead of it in the stream has completed: once
+// every block of that kernel has exited, not after its completion has been
+// signalled.  Every such kernel therefore begins with pdl_enter():
+// griddepcontrol.wait returns once the preceding grids have completed and
+// their writes are visible, and no memory is touched before it.  No kernel
+// triggers its dependents early (griddepcontrol.launch_dependents): blocks of
+// the next kernel parked on the SMs took slots from the kernels of the other
+// stream of a step and made the step slower.  A no-op for a plain launch.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// process-wide switch (ebr_set_pdl), on by default
+extern int g_pdl;
+
+// Launch of a library kernel on stream s (errors surface through
+// cudaGetLastError like a <<< >>> launch).
+template <typename... P, typename... A>
+inline void launch(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = g_pdl ? at : nullptr;
+  cfg.numAttrs = g_pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
 // Raise (never lower) the dynamic shared-memory opt-in of kernel K on the
 // current device to `bytes`: the opt-in is per function and per device, and a
 // graph captured earlier may still hold a launch with a larger size.
@@ -32,6 +65,32 @@ inline void smem_raise(size_t bytes) {
   if (dev >= 0 && dev < 64 && bytes <= seen[dev]) return;
   cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (dev >= 0 && dev < 64) seen[dev] = bytes;
+}
+
+// Check of a re-run against the plan, done by block 0 of the next kernel:
+// stage 0 the interface offsets of the rows and the ghost offsets of the
+// interface list at the geometry boundaries, stage 1 the level count of every
+// geometry; stage -1 (planning) nothing.  A difference is EBR_ESHAPE.
+struct PlanCheck {
+  const int* row_ptr;
+  const int* gpos;
+  const int* nlev;
+  int B, n_iface, ng, stage;
+};
+
+__device__ inline void plan_check(const Geom* G, const PlanCheck& C, int* status) {
+  if (C.stage < 0 || blockIdx.x != 0) return;
+  for (int b = threadIdx.x; b < C.B; b += blockDim.x) {
+    const Geom& g = G[b];
+    if (C.stage == 0) {
+      if (C.row_ptr[g.row_off] != g.iface_off) set_status(status, S_ESHAPE);
+      if (b == C.B - 1 && C.row_ptr[g.row_off + g.n_rows] != C.n_iface) set_status(status, S_ESHAPE);
+      if (C.gpos[g.iface_off] != g.ghost_off) set_status(status, S_ESHAPE);
+      if (b == C.B - 1 && C.gpos[C.n_iface] != C.ng) set_status(status, S_ESHAPE);
+    } else if (C.nlev[b] != g.n_levels) {
+      set_status(status, S_ESHAPE);
+    }
+  }
 }
 
 // kind (0 Dirichlet, 1 Neumann) of field f of a packed field array: bit f
@@ -51,6 +110,19 @@ void launch_place(const Geom* G, int n_iface, const int* iface_cell, const int* 
                   double* iface_n, int* status, cudaStream_t s, int T = 128);
 void launch_reclassify(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                        int8_t* tags, int pass, cudaStream_t s);
+// single-pass variants for a classification re-run (sizes known from the
+// plan): interface cells with their row offsets in one launch; ghost flags,
+// offsets and records in one launch (pass_b: HGC reclassification pass B of
+// each cell first); the per-ghost geometry after either
+void launch_iface_fused(const Geom* G, const int* row_off, int B, int total_rows, const int2* runs,
+                        int* row_ptr, int* iface_cell, int* iface_geo, int8_t* iface_solid, int iface_cap,
+                        const Lookback& L, int* status, cudaStream_t s);
+void launch_ghost_compact(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
+                          int8_t* tags, int pass_b, int* gpos, int ng_cap, int* gs_cell, int* gs_geo,
+                          uint32_t* gs_meta, const Lookback& L, int* status, cudaStream_t s);
+void launch_ghost_geom(const Geom* G, int placement, int ng_cap, int* gs_cell, int* gs_geo, double* gs_psi,
+                       double* gs_n, uint32_t* gs_meta, int* rmax, int* status, cudaStream_t s, int T = 128,
+                       const PlanCheck& chk = PlanCheck{nullptr, nullptr, nullptr, 0, 0, 0, -1});
 // second ghost layer (geometries with layers == 2), after the reclassification
 void launch_layer2(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo, int8_t* tags,
                    int* status, cudaStream_t s);
@@ -68,7 +140,7 @@ void launch_scan(const int* in, int* out, int n, void* temp, cudaStream_t s);
 
 // ---- levels.cu
 void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, const int* pos_of,
-                    int* pos_of_cell, cudaStream_t s);
+                    int* pos_of_cell, int* src_cnt, cudaStream_t s);
 void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, uint32_t* gs_meta,
                  const double* gs_n, const int8_t* tags, const int* pos_of_cell, int* dep,
                  int* status, cudaStream_t s, int T = 128);
@@ -81,13 +153,23 @@ void launch_reorder(const Geom* G, int* pos_of_cell, int ng, const int* order_po
                     const int* gs_geo,
                     const double* gs_psi, const double* gs_n, const uint32_t* gs_meta,
                     const int* dep, const int* level, int* g_cell, int* g_geo, double* g_psi,
-                    double* g_n, uint32_t* g_meta, int* g_dep, int* g_level, cudaStream_t s);
+                    double* g_n, uint32_t* g_meta, int* g_dep, int* g_level, cudaStream_t s,
+                    const PlanCheck& chk = PlanCheck{nullptr, nullptr, nullptr, 0, 0, 0, -1},
+                    int* status = nullptr);
 void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, const double* g_psi,
                    const double* g_n, const uint32_t* g_meta, const int8_t* tags, double* wtab,
                    double* ftab, cudaStream_t s, int T = 128);
-void launch_gsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
-                 const int8_t* tags, const int* pos_of_cell, int rmax, const int* ptr,
-                 int* cnt_or_src, int write, cudaStream_t s, int T = 128);
+// ghost targets' source lists by transposition: member ghost positions
+// mem [MAXK][ng] and source counts (cnt preset to 1); offsets by a scan, then
+// the own entries (self, planning), the scattered sources and the sort; or
+// offsets + own entries in one single-pass launch (a re-run)
+void launch_gsrc_count(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
+                       const int8_t* tags, const int* pos_of_cell, int kmax, int* mem, int* cnt, cudaStream_t s,
+                       int T = 128);
+void launch_gsrc_lists(int ng, int kmax, const int* mem, const int* ptr, int* cursor, int* src, int cap,
+                       int* status, bool self, cudaStream_t s, int T = 128);
+void launch_gsrc_place(int ng, int* cnt_cursor, int* ptr, int* src, int cap, const Lookback& L, int* status,
+                       cudaStream_t s);
 
 
 // ---- fill.cu

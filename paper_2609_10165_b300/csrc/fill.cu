@@ -44,6 +44,7 @@ template <typename T, int D>
 __global__ void k_fill_level(FieldSet P, int F, long long cell_off, int p0, int p1,
                              const int* __restrict__ g_cell, const uint32_t* __restrict__ g_meta,
                              const double* __restrict__ wtab, int ng, int nx, int ny, int* status) {
+  pdl_enter();
   constexpr int K = D == 2 ? 3 : 7;
   int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= p1) return;
@@ -100,13 +101,13 @@ void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int
   int T = n < 128 ? 64 : 128;
   const unsigned nb = (unsigned)((n + T - 1) / T);
   if (dtype == 0 && dim == 2)
-    k_fill_level<float, 2><<<nb, T, 0, s>>>(P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+    launch(k_fill_level<float, 2>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
   else if (dtype == 0)
-    k_fill_level<float, 3><<<nb, T, 0, s>>>(P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+    launch(k_fill_level<float, 3>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
   else if (dim == 2)
-    k_fill_level<double, 2><<<nb, T, 0, s>>>(P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+    launch(k_fill_level<double, 2>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
   else
-    k_fill_level<double, 3><<<nb, T, 0, s>>>(P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+    launch(k_fill_level<double, 3>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
 }
 
 // Partial sum of every ghost and field: w_s b_G plus the fluid (non-
@@ -117,6 +118,7 @@ template <typename T>
 __global__ void k_fill_partial(FieldSet P, int F, const Geom* __restrict__ G, const int* __restrict__ g_geo,
                                const int* __restrict__ g_cell, const uint32_t* __restrict__ g_meta,
                                const double* __restrict__ wtab, int ng, T* __restrict__ part) {
+  pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
   const Geom& g = G[g_geo[p]];
@@ -152,9 +154,9 @@ void launch_fill_partial(int dtype, int F, void* const* fields, const int* bc_ki
     P.kind[f] = f < F ? bc_kind[f] : 0;
   }
   if (dtype == 0)
-    k_fill_partial<float><<<(ng + T - 1) / T, T, 0, s>>>(P, F, G, g_geo, g_cell, g_meta, wtab, ng, (float*)part);
+    launch(k_fill_partial<float>, (ng + T - 1) / T, T, 0, s, P, F, G, g_geo, g_cell, g_meta, wtab, ng, (float*)part);
   else
-    k_fill_partial<double><<<(ng + T - 1) / T, T, 0, s>>>(P, F, G, g_geo, g_cell, g_meta, wtab, ng, (double*)part);
+    launch(k_fill_partial<double>, (ng + T - 1) / T, T, 0, s, P, F, G, g_geo, g_cell, g_meta, wtab, ng, (double*)part);
 }
 
 constexpr int CH_T = 512;
@@ -167,17 +169,14 @@ size_t fill_chain_smem(int dtype, int dim, int F, int n) {
   return (size_t)n * (F * sz + 2 * K * sz + K * sizeof(int) + sizeof(int)) + (size_t)(n + 1) * sizeof(int) + 64;
 }
 
+// The dependency chain of geometry g in one CTA (CH_T threads), on the
+// dynamic shared memory of fill_chain_smem.
 template <typename T>
-__global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Geom* __restrict__ G,
-                                                     const int* __restrict__ geo_list,
-                                                     const int* __restrict__ g_cell,
-                                                     const uint32_t* __restrict__ g_meta,
-                                                     const int* __restrict__ g_dep,
-                                                     const int* __restrict__ lev_ptr,
-                                                     const double* __restrict__ wtab, int ng,
-                                                     const T* __restrict__ part, int* status) {
+__device__ inline void chain_walk(const FieldSet& P, int F, const Geom& g, const int* __restrict__ g_cell,
+                                  const uint32_t* __restrict__ g_meta, const int* __restrict__ g_dep,
+                                  const int* __restrict__ lev_ptr, const double* __restrict__ wtab, int ng,
+                                  const T* __restrict__ part, int* status) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const Geom& g = G[geo_list[blockIdx.x]];
   const int n = g.n_ghost, g0 = g.ghost_off, dim = g.dim;
   // geometry fields in registers: the loops below store to global memory,
   // after which a read through g would have to be repeated
@@ -192,18 +191,36 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
   const int* lp = lev_ptr + g.lev_off;
   for (int q = threadIdx.x; q <= n_levels; q += CH_T) lps[q] = lp[q] - g0;
   // phase 1: the partial sums (boundary term + fluid members) of the
-  // geometry's ghosts; dependency weights and positions
-  for (int s = threadIdx.x; s < n; s += CH_T) {
-    int p = g0 + s;
-    cellv[s] = g_cell[p];
-    uint32_t m = g_meta[p];
-    uint32_t dm = meta_depmask(m);
-    for (int f = 0; f < F; ++f) vals[(size_t)f * n + s] = part[(size_t)f * ng + p];
-    for (int k = 0; k < K; ++k) {
-      bool d = dm >> k & 1u;
-      dpos[(size_t)k * n + s] = d ? g_dep[(size_t)k * ng + p] - g0 : -1;
-      wdep[(size_t)k * n + s] = d ? wload<T>(wtab, ng, 0, k, p) : T(0);
-      wdep[(size_t)(K + k) * n + s] = d ? wload<T>(wtab, ng, 1, k, p) : T(0);
+  // geometry's ghosts; dependency weights and positions.  U ghosts per
+  // thread at a time: their cells, metas and partials are loaded together,
+  // then (the meta tells which members are dependencies) their dependency
+  // positions and weights
+  constexpr int U = 4;
+  for (int s0 = threadIdx.x; s0 < n; s0 += CH_T * U) {
+    uint32_t dm[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u * CH_T;
+      dm[u] = 0u;
+      if (s >= n) continue;
+      const int p = g0 + s;
+      cellv[s] = g_cell[p];
+      dm[u] = meta_depmask(g_meta[p]);
+#pragma unroll
+      for (int f = 0; f < 8; ++f)
+        if (f < F) vals[(size_t)f * n + s] = part[(size_t)f * ng + p];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u * CH_T;
+      if (s >= n) continue;
+      const int p = g0 + s;
+      for (int k = 0; k < K; ++k) {
+        const bool d = dm[u] >> k & 1u;
+        dpos[(size_t)k * n + s] = d ? g_dep[(size_t)k * ng + p] - g0 : -1;
+        wdep[(size_t)k * n + s] = d ? wload<T>(wtab, ng, 0, k, p) : T(0);
+        wdep[(size_t)(K + k) * n + s] = d ? wload<T>(wtab, ng, 1, k, p) : T(0);
+      }
     }
   }
   __syncthreads();
@@ -251,6 +268,20 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
   }
 }
 
+
+template <typename T>
+__global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Geom* __restrict__ G,
+                                                     const int* __restrict__ geo_list,
+                                                     const int* __restrict__ g_cell,
+                                                     const uint32_t* __restrict__ g_meta,
+                                                     const int* __restrict__ g_dep,
+                                                     const int* __restrict__ lev_ptr,
+                                                     const double* __restrict__ wtab, int ng,
+                                                     const T* __restrict__ part, int* status) {
+  pdl_enter();
+  chain_walk<T>(P, F, G[geo_list[blockIdx.x]], g_cell, g_meta, g_dep, lev_ptr, wtab, ng, part, status);
+}
+
 void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
                        const void* const* bc, const Geom* G, const int* geo_list, int n_list,
                        const int* g_cell, const uint32_t* g_meta, const int* g_dep,
@@ -266,10 +297,10 @@ void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int
   }
   if (dtype == 0) {
     smem_raise<k_fill_chain<float>>(smem);
-    k_fill_chain<float><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, (const float*)part, status);
+    launch(k_fill_chain<float>, n_list, CH_T, smem, s, P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, (const float*)part, status);
   } else {
     smem_raise<k_fill_chain<double>>(smem);
-    k_fill_chain<double><<<n_list, CH_T, smem, s>>>(P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, (const double*)part, status);
+    launch(k_fill_chain<double>, n_list, CH_T, smem, s, P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, (const double*)part, status);
   }
 }
 

@@ -1,23 +1,16 @@
 // Boundary quantities and forces (Sec. 6).
 //
-// Per ghost: p_s from the Dirichlet relation solved for phi_s, grad u at S from
-// Eq. derivative_bilinear / Eqs. derivative_trilinear_x/y/z (both through the
-// ftab coefficients), traction f = -p_s n + mu (grad u + grad u^T) n, weighted
-// by the ghost's surface element w_G.  Ghosts are cut into chunks of at most
+// Per ghost the traction of traction.cuh (p_s, grad u at S, f = -p_s n +
+// mu (grad u + grad u^T) n, weighted by w_G).  Ghosts are cut into chunks of at most
 // 256 that never straddle geometries; each CTA reduces its chunk with a fixed
 // tree, and a second kernel adds the chunk partials of each geometry in order,
 // so the sums are bitwise reproducible.
 #include "ebr_kernels.cuh"
+#include "traction.cuh"
 
 namespace ebr {
 
 constexpr int FC_T = 256;
-
-struct VelSet {
-  const void* u[3];
-  const void* p;
-  double dirs[6];
-};
 
 // D (2 or 3) fixed at compile time keeps the per-ghost arrays in registers
 template <typename T, int D>
@@ -29,68 +22,15 @@ __global__ void __launch_bounds__(FC_T) k_forces_chunk(VelSet V, double mu, cons
                                                        const uint32_t* __restrict__ g_meta,
                                                        const double* __restrict__ ftab, int ng,
                                                        double* __restrict__ partial) {
-  constexpr int K = D == 2 ? 3 : 7;
+  pdl_enter();
   // [quantity][thread]: a warp's 32 doubles of one quantity are contiguous
   // (no bank conflicts in the tree below)
   __shared__ double red[8][FC_T];
   int4 ch = chunks[blockIdx.x];        // (geometry, p0, p1, -)
   const Geom& g = G[ch.x];
-  const int nx = g.n[0], ny = g.n[1];
   int p = ch.y + threadIdx.x;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (p < ch.z) {
-    int cell = g_cell[p];
-    uint32_t m = g_meta[p];
-    int slots[K + 1];
-    slots[0] = cell;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      int o[3];
-      stencil_off(D, k, o);
-      int off = o[0] * meta_r(m, 0) * meta_e(m, 0) + nx * (o[1] * meta_r(m, 1) * meta_e(m, 1));
-      if (D == 3) off += nx * ny * (o[2] * meta_r(m, 2) * meta_e(m, 2));
-      slots[k + 1] = cell + off;
-    }
-    double n[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) n[a] = g_n[(size_t)a * ng + p];
-    double wG = ftab[p];
-    const T* pp = static_cast<const T*>(V.p) + g.cell_off;
-    double ps = 0.0;
-#pragma unroll
-    for (int s = 0; s <= K; ++s) ps += ftab[(size_t)(1 + s) * ng + p] * (double)pp[slots[s]];
-    double Gm[D][D];                                        // Gm[i][a] = d u_i / d x_a
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int a = 0; a < D; ++a) Gm[i][a] = 0.0;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      if (!V.u[i]) continue;
-      const T* ui = static_cast<const T*>(V.u[i]) + g.cell_off;
-#pragma unroll
-      for (int s = 0; s <= K; ++s) {
-        double v = (double)ui[slots[s]];
-#pragma unroll
-        for (int a = 0; a < D; ++a) Gm[i][a] += ftab[(size_t)(9 + 8 * a + s) * ng + p] * v;
-      }
-    }
-    double dr = 0.0, li = 0.0;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const double fp = -ps * n[i] * wG;
-      double t = 0.0;
-#pragma unroll
-      for (int a = 0; a < D; ++a) t += (Gm[i][a] + Gm[a][i]) * n[a];
-      const double fv = mu * t * wG;
-      acc[i] = fp;
-      acc[D + i] = fv;
-      dr += (fp + fv) * V.dirs[i];
-      li += (fp + fv) * V.dirs[D + i];
-    }
-    acc[2 * D] = dr;
-    acc[2 * D + 1] = li;
-  }
+  if (p < ch.z) ghost_traction<T, D>(V, mu, g, p, g_cell, g_n, g_meta, ftab, ng, acc);
   // fixed tree: at level w, element i < w becomes element i + element i + w
   // (w = 128, 64 in shared memory; 32 by warp 0 from shared memory; 16 .. 1
   // by shuffles, which add the same pairs in the same order)
@@ -120,6 +60,7 @@ __global__ void __launch_bounds__(FC_T) k_forces_chunk(VelSet V, double mu, cons
 
 __global__ void k_forces_final(int B, const Geom* __restrict__ G, const int* __restrict__ chunk_ptr,
                                const double* __restrict__ partial, double* __restrict__ out) {
+  pdl_enter();
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   int d = G[b].dim, W = 2 * d + 2;
@@ -140,15 +81,15 @@ void launch_forces(int dtype, int dim, const void* const* vel, const void* p, do
   for (int q = 0; q < 6; ++q) V.dirs[q] = q < 2 * dim ? dirs[q] : 0.0;
   if (n_chunks > 0) {
     if (dtype == 0 && dim == 2)
-      k_forces_chunk<float, 2><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+      launch(k_forces_chunk<float, 2>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
     else if (dtype == 0)
-      k_forces_chunk<float, 3><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+      launch(k_forces_chunk<float, 3>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
     else if (dim == 2)
-      k_forces_chunk<double, 2><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+      launch(k_forces_chunk<double, 2>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
     else
-      k_forces_chunk<double, 3><<<n_chunks, FC_T, 0, s>>>(V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+      launch(k_forces_chunk<double, 3>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
   }
-  k_forces_final<<<(B + 127) / 128, 128, 0, s>>>(B, G, chunk_ptr, partial, out);
+  launch(k_forces_final, (B + 127) / 128, 128, 0, s, B, G, chunk_ptr, partial, out);
 }
 
 }  // namespace ebr

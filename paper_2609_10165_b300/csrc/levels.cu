@@ -5,18 +5,22 @@
 
 namespace ebr {
 
+// position of every ghost cell in the ghost arrays; src_cnt (optional): the
+// ghost-source counts set to 1 (each ghost is its own first source)
 __global__ void k_poscell(const Geom* __restrict__ G, int ng, const int* __restrict__ cell,
                           const int* __restrict__ geo, const int* __restrict__ pos_of,
-                          int* __restrict__ pos_of_cell) {
+                          int* __restrict__ pos_of_cell, int* __restrict__ src_cnt) {
+  pdl_enter();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ng) return;
   pos_of_cell[G[geo[s]].cell_off + cell[s]] = pos_of ? pos_of[s] : s;
+  if (src_cnt) src_cnt[s] = 1;
 }
 
 void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, const int* pos_of,
-                    int* pos_of_cell, cudaStream_t s) {
+                    int* pos_of_cell, int* src_cnt, cudaStream_t s) {
   if (ng <= 0) return;
-  k_poscell<<<(ng + 255) / 256, 256, 0, s>>>(G, ng, cell, geo, pos_of, pos_of_cell);
+  launch(k_poscell, (ng + 255) / 256, 256, 0, s, G, ng, cell, geo, pos_of, pos_of_cell, src_cnt);
 }
 
 // Stencil members: validate (inside the grid, not tag 1), active mask
@@ -29,6 +33,7 @@ __global__ void k_deps(const Geom* __restrict__ G, int ng, const int* __restrict
                        const int* __restrict__ gs_geo, uint32_t* __restrict__ gs_meta,
                        const double* __restrict__ gs_n, const int8_t* __restrict__ tags,
                        const int* __restrict__ pos_of_cell, int* __restrict__ dep, int* status) {
+  pdl_enter();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ng) return;
   const Geom& g = G[gs_geo[s]];
@@ -71,7 +76,7 @@ void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, u
                  const double* gs_n, const int8_t* tags, const int* pos_of_cell, int* dep,
                  int* status, cudaStream_t s, int T) {
   if (ng <= 0) return;
-  k_deps<<<(ng + T - 1) / T, T, 0, s>>>(G, ng, gs_cell, gs_geo, gs_meta, gs_n, tags,
+  launch(k_deps, (ng + T - 1) / T, T, 0, s, G, ng, gs_cell, gs_geo, gs_meta, gs_n, tags,
                                           pos_of_cell, dep, status);
 }
 
@@ -103,6 +108,7 @@ __global__ void __launch_bounds__(LV_T, 2) k_levels(const Geom* __restrict__ G, 
                                                  int* __restrict__ level, int* __restrict__ order_pos,
                                                  int* __restrict__ lev_ptr, int* __restrict__ n_levels,
                                                  int smem_ints, int* status) {
+  pdl_enter();
   extern __shared__ int sm[];
   __shared__ int sh_cnt3[3];
   __shared__ int sh_warp[32];
@@ -365,7 +371,7 @@ void launch_levels(const Geom* G, int B, const int* dep, int ng_total, int* leve
                    int* lev_ptr, int* n_levels, size_t smem, int* status, cudaStream_t s) {
   if (B <= 0) return;
   smem_raise<k_levels>(smem);
-  k_levels<<<B, LV_T, smem, s>>>(G, B, dep, ng_total, level, order_pos, lev_ptr, n_levels,
+  launch(k_levels, B, LV_T, smem, s, G, B, dep, ng_total, level, order_pos, lev_ptr, n_levels,
                                  (int)(smem / sizeof(int)) - 16, status);
 }
 
@@ -378,7 +384,10 @@ __global__ void k_reorder(const Geom* __restrict__ G, int* __restrict__ pos_of_c
                           const int* __restrict__ dep, const int* __restrict__ level,
                           int* __restrict__ g_cell, int* __restrict__ g_geo, double* __restrict__ g_psi,
                           double* __restrict__ g_n, uint32_t* __restrict__ g_meta,
-                          int* __restrict__ g_dep, int* __restrict__ g_level) {
+                          int* __restrict__ g_dep, int* __restrict__ g_level, const PlanCheck chk,
+                          int* status) {
+  pdl_enter();
+  plan_check(G, chk, status);
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ng) return;
   int p = order_pos[s];
@@ -399,11 +408,11 @@ void launch_reorder(const Geom* G, int* pos_of_cell, int ng, const int* order_po
                     const int* gs_geo,
                     const double* gs_psi, const double* gs_n, const uint32_t* gs_meta,
                     const int* dep, const int* level, int* g_cell, int* g_geo, double* g_psi,
-                    double* g_n, uint32_t* g_meta, int* g_dep, int* g_level, cudaStream_t s) {
+                    double* g_n, uint32_t* g_meta, int* g_dep, int* g_level, cudaStream_t s,
+                    const PlanCheck& chk, int* status) {
   if (ng <= 0) return;
-  k_reorder<<<(ng + 255) / 256, 256, 0, s>>>(G, pos_of_cell, ng, order_pos, gs_cell, gs_geo, gs_psi, gs_n, gs_meta,
-                                             dep, level, g_cell, g_geo, g_psi, g_n, g_meta, g_dep,
-                                             g_level);
+  launch(k_reorder, (ng + 255) / 256, 256, 0, s, G, pos_of_cell, ng, order_pos, gs_cell, gs_geo, gs_psi, gs_n,
+         gs_meta, dep, level, g_cell, g_geo, g_psi, g_n, g_meta, g_dep, g_level, chk, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -471,6 +480,7 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
                          const double* __restrict__ g_n, const uint32_t* __restrict__ g_meta,
                          const int8_t* __restrict__ tags, double* __restrict__ wtab,
                          double* __restrict__ ftab) {
+  pdl_enter();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
   const Geom& g = G[g_geo[p]];
@@ -565,38 +575,148 @@ void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, c
                    const double* g_n, const uint32_t* g_meta, const int8_t* tags, double* wtab,
                    double* ftab, cudaStream_t s, int T) {
   if (ng <= 0) return;
-  k_tables<<<(ng + T - 1) / T, T, 0, s>>>(G, ng, g_cell, g_geo, g_psi, g_n, g_meta, tags, wtab, ftab);
+  launch(k_tables, (ng + T - 1) / T, T, 0, s, G, ng, g_cell, g_geo, g_psi, g_n, g_meta, tags, wtab, ftab);
 }
 
-// ghost targets: write = 0 counts, write = 1 writes sources (self first)
-__global__ void k_gsrc(const Geom* __restrict__ G, int ng, const int* __restrict__ g_cell,
-                       const int* __restrict__ g_geo, const uint32_t* __restrict__ g_meta,
-                       const int8_t* __restrict__ tags, const int* __restrict__ pos_of_cell, int R,
-                       const int* __restrict__ ptr, int* __restrict__ out, int write) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= ng) return;
-  const Geom& g = G[g_geo[p]];
-  int tijk[3];
-  cell_ijk3(g, g_cell[p], tijk);
-  const int8_t* tg = tags + g.cell_off;
-  const int* pc = pos_of_cell + g.cell_off;
-  if (!write) {
-    int cnt = 1;
-    probe_sources(g, tijk, tg, pc, g_cell, g_meta, R, [&](int, int) { ++cnt; return true; });
-    out[p] = cnt;
-  } else {
-    int o = ptr[p];
-    out[o++] = (p << 3) | 0;
-    probe_sources(g, tijk, tg, pc, g_cell, g_meta, R, [&](int q, int slot) { out[o++] = (q << 3) | slot; return true; });
+// ---------------------------------------------------------------------------
+// Ghost targets' source lists (the adjoint reads the dependency relation of
+// Sec. 3.2 backwards): ghost p's list is p itself (slot 0) followed by every
+// (q, k + 1) whose stencil member k is p -- active or not, since the Sec. 6
+// boundary-gradient stencils use every member -- in ascending (q, slot)
+// order.  Built by transposition, without probing neighbourhoods:
+//   k_gsrc_count    per ghost q: the ghost position of each member (mem[k][q],
+//                   -1 when the member is not a ghost of this plan) and one
+//                   more source for each such member (cnt starts at 1, set by
+//                   k_poscell)
+//   k_gsrc_self     offsets known: p's own entry first, the cursor after it
+//   k_gsrc_place    the same in one launch with the offsets (single-pass scan
+//                   of cnt; a re-run, checked against the planned total)
+//   k_gsrc_scatter  each (q, k) takes the next entry of its target's list
+//   k_gsrc_sort     each list after the own entry sorted (a list holds a few
+//                   entries), so the order does not depend on the scatter
+// ---------------------------------------------------------------------------
+__global__ void k_gsrc_count(const Geom* __restrict__ G, int ng, const int* __restrict__ g_cell,
+                             const int* __restrict__ g_geo, const uint32_t* __restrict__ g_meta,
+                             const int8_t* __restrict__ tags, const int* __restrict__ pos_of_cell, int kmax,
+                             int* __restrict__ mem, int* __restrict__ cnt) {
+  pdl_enter();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ng) return;
+  const Geom& g = G[g_geo[q]];
+  int ijk[3];
+  cell_ijk3(g, g_cell[q], ijk);
+  const uint32_t m = g_meta[q];
+  const int K = stencil_k(g.dim);
+  for (int k = 0; k < kmax; ++k) {
+    int p = -1;
+    if (k < K) {
+      int mijk[3];
+      member_ijk(g, ijk, m, k, mijk);
+      if (in_grid(g, mijk)) {
+        const int mc = cell_lin(g, mijk);
+        const int8_t t = tags[g.cell_off + mc];
+        if (t == 2 || t == -2) p = ghost_slot_of(g, mc, pos_of_cell + g.cell_off, g_cell);
+      }
+    }
+    mem[(size_t)k * ng + q] = p;
+    if (p >= 0) atomicAdd(&cnt[p], 1);
   }
 }
 
-void launch_gsrc(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
-                 const int8_t* tags, const int* pos_of_cell, int rmax, const int* ptr,
-                 int* cnt_or_src, int write, cudaStream_t s, int T) {
+__global__ void k_gsrc_self(int ng, const int* __restrict__ ptr, int* __restrict__ src, int* __restrict__ cursor) {
+  pdl_enter();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ng) return;
+  const int o = ptr[p];
+  src[o] = p << 3;
+  cursor[p] = o + 1;
+}
+
+__global__ void k_gsrc_place(int ng, int* __restrict__ cnt_cursor, int* __restrict__ ptr, int* __restrict__ src,
+                             int cap, const Lookback L, int* status) {
+  pdl_enter();
+  __shared__ int sh[32];
+  const LbBlock blk = lb_begin(L);
+  const int p = blk.tile * blockDim.x + threadIdx.x;
+  const bool on = p < ng;
+  const int cnt = on ? cnt_cursor[p] : 0;
+  int agg;
+  const int ex = block_excl_scan(cnt, sh, agg);
+  const long long base = lb_prefix(L, blk, (unsigned)agg, status);
+  if (base < 0 && on) cnt_cursor[p] = cap;   // gave up: the scatter writes nothing for p
+  if (base >= 0) {
+    if (on) {
+      const int o = (int)(base + ex);
+      ptr[p] = o;
+      if (o + cnt > cap) {
+        set_status(status, S_ESHAPE);
+        cnt_cursor[p] = cap;            // the scatter then writes nothing for p
+      } else {
+        src[o] = p << 3;
+        cnt_cursor[p] = o + 1;
+      }
+    }
+    if (p == ng - 1) {
+      const long long total = base + ex + cnt;
+      ptr[ng] = (int)min(total, (long long)cap);
+      if (total != cap) set_status(status, S_ESHAPE);
+    }
+  }
+  lb_end(L);
+}
+
+// entries outside [0, cap) are never written (a count that differs from the
+// plan has set EBR_ESHAPE already)
+__global__ void k_gsrc_scatter(int ng, int kmax, const int* __restrict__ mem, const int* __restrict__ ptr,
+                               int* __restrict__ cursor, int* __restrict__ src, int cap, int* status) {
+  pdl_enter();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ng) return;
+  for (int k = 0; k < kmax; ++k) {
+    const int p = mem[(size_t)k * ng + q];
+    if (p < 0 || p >= ng) continue;
+    const int o = atomicAdd(&cursor[p], 1);
+    if (o >= 0 && o < ptr[p + 1] && o < cap) src[o] = (q << 3) | (k + 1);
+    else set_status(status, S_ESHAPE);
+  }
+}
+
+__global__ void k_gsrc_sort(int ng, const int* __restrict__ ptr, int* __restrict__ src, int cap) {
+  pdl_enter();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ng) return;
+  const int a = max(ptr[p] + 1, 0), b = min(ptr[p + 1], cap);
+  for (int x = a + 1; x < b; ++x) {
+    const int key = src[x];
+    int y = x - 1;
+    while (y >= a && src[y] > key) {
+      src[y + 1] = src[y];
+      --y;
+    }
+    src[y + 1] = key;
+  }
+}
+
+void launch_gsrc_count(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
+                       const int8_t* tags, const int* pos_of_cell, int kmax, int* mem, int* cnt, cudaStream_t s,
+                       int T) {
   if (ng <= 0) return;
-  k_gsrc<<<(ng + T - 1) / T, T, 0, s>>>(G, ng, g_cell, g_geo, g_meta, tags, pos_of_cell, rmax,
-                                          ptr, cnt_or_src, write);
+  launch(k_gsrc_count, (ng + T - 1) / T, T, 0, s, G, ng, g_cell, g_geo, g_meta, tags, pos_of_cell, kmax, mem,
+         cnt);
+}
+
+void launch_gsrc_lists(int ng, int kmax, const int* mem, const int* ptr, int* cursor, int* src, int cap,
+                       int* status, bool self, cudaStream_t s, int T) {
+  if (ng <= 0) return;
+  if (self) launch(k_gsrc_self, (ng + T - 1) / T, T, 0, s, ng, ptr, src, cursor);
+  launch(k_gsrc_scatter, (ng + T - 1) / T, T, 0, s, ng, kmax, mem, ptr, cursor, src, cap, status);
+  launch(k_gsrc_sort, (ng + T - 1) / T, T, 0, s, ng, ptr, src, cap);
+}
+
+void launch_gsrc_place(int ng, int* cnt_cursor, int* ptr, int* src, int cap, const Lookback& L, int* status,
+                       cudaStream_t s) {
+  if (ng <= 0) return;
+  launch(k_gsrc_place, (ng + LB_T - 1) / LB_T, LB_T, 0, s, ng, cnt_cursor, ptr, src, cap, L, status);
 }
 
 }  // namespace ebr

@@ -110,6 +110,7 @@ __global__ void k_rec_fwd(int ng, const Geom* __restrict__ G, const int* __restr
                           const int* __restrict__ g_cell, const uint32_t* __restrict__ g_meta,
                           const int* __restrict__ g_dep, const double* __restrict__ wtab,
                           uint32_t* __restrict__ out) {
+  pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
   constexpr int S = rec_fwd_words<T, K>(), V = WPV<T>::v;
@@ -156,6 +157,7 @@ __global__ void k_rec_adj(int ng, const Geom* __restrict__ G, const int* __restr
                           const int* __restrict__ g_cell, const int* __restrict__ cons_ptr,
                           const int* __restrict__ cons, const double* __restrict__ wtab,
                           uint32_t* __restrict__ out) {
+  pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
   constexpr int S = rec_src_words<T>(), V = WPV<T>::v;
@@ -174,6 +176,7 @@ template <typename T>
 __global__ void k_rec_fluid(int n_ft, const int* __restrict__ ft_cell, const int* __restrict__ ft_ptr,
                             const int* __restrict__ ft_src, const double* __restrict__ wtab, int ng,
                             uint32_t* __restrict__ out) {
+  pdl_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_ft) return;
   constexpr int S = rec_src_words<T>(), V = WPV<T>::v;
@@ -241,6 +244,7 @@ __global__ void __launch_bounds__(PK_T) k_pf_grid(T* __restrict__ fld, const T* 
                                                   const uint32_t* __restrict__ rec,
                                                   const int* __restrict__ list, int n, int partial,
                                                   int* status) {
+  pdl_enter();
   const int i = (blockIdx.x * PK_T + threadIdx.x) >> 5;
   if (i >= n) return;
   const long long p = list ? list[i] : i;
@@ -260,6 +264,7 @@ __global__ void __launch_bounds__(PK_CT) k_pf_tail(T* __restrict__ fld, int F,
                                                    const uint32_t* __restrict__ rec,
                                                    const int* __restrict__ lev_ptr, int L0,
                                                    int* status) {
+  pdl_enter();
   const Geom& g = G[geo_list[blockIdx.x]];
   const int* lp = lev_ptr + g.lev_off;
   const int n_levels = g.n_levels;     // in a register: the kernel stores to global memory
@@ -297,6 +302,7 @@ __global__ void __launch_bounds__(PK_CT, 2) k_pf_tail_s(T* __restrict__ fld, int
                                                      const uint32_t* __restrict__ rec,
                                                      const int* __restrict__ lev_ptr, int L0,
                                                      int cap, int ng, int* status) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int V = WPV<T>::v;
   const Geom& g = G[geo_list[blockIdx.y]];   // chunks of one geometry launch together
@@ -403,6 +409,7 @@ __global__ void __launch_bounds__(PK_CT, 2) k_pa_tail_s(T* __restrict__ cot, T* 
                                                      const int* __restrict__ cons,
                                                      const double* __restrict__ wtab, int ng,
                                                      int cap, int* status) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int V = WPV<T>::v;
   const Geom& g = G[geo_list[blockIdx.y]];   // chunks of one geometry launch together
@@ -581,6 +588,7 @@ __global__ void __launch_bounds__(PK_T) k_pa_grid(T* __restrict__ cot, T* __rest
                                                   const int* __restrict__ cons,
                                                   const double* __restrict__ wtab, int ng,
                                                   const int* __restrict__ list, int n) {
+  pdl_enter();
   const int i = (blockIdx.x * PK_T + threadIdx.x) >> 5;
   if (i >= n) return;
   const long long p = list[i];
@@ -602,6 +610,7 @@ __global__ void __launch_bounds__(PK_CA, 2) k_pa_tail(T* __restrict__ cot, T* __
                                                    const int* __restrict__ lev_ptr, int L0,
                                                    const int* __restrict__ cons,
                                                    const double* __restrict__ wtab, int ng) {
+  pdl_enter();
   const Geom& g = G[geo_list[blockIdx.x]];
   const int warp = threadIdx.x >> 5, nw = PK_CA / 32;
   const int* lp = lev_ptr + g.lev_off;
@@ -645,6 +654,7 @@ __global__ void __launch_bounds__(PK_T) k_pa_fluid(T* __restrict__ cot, const T*
                                                    const uint32_t* __restrict__ rec,
                                                    const int* __restrict__ ft_src,
                                                    const double* __restrict__ wtab, int ng, int n) {
+  pdl_enter();
   constexpr int V = WPV<T>::v;
   const int i = (blockIdx.x * PK_T + threadIdx.x) >> 5;
   if (i >= n) return;
@@ -674,6 +684,7 @@ __global__ void __launch_bounds__(PK_T) k_pa_fluid(T* __restrict__ cot, const T*
 __global__ void k_cons(int ng, const int* __restrict__ gsrc_ptr, const int* __restrict__ gsrc,
                        const uint32_t* __restrict__ g_meta, const int* __restrict__ ptr,
                        int* __restrict__ out) {
+  pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
   int c = 0, o = ptr ? ptr[p] : 0;
@@ -692,6 +703,7 @@ __global__ void k_ftgt(int ng, int kmax, const Geom* __restrict__ G, const int* 
                        int* __restrict__ flag, int* __restrict__ cnt, const int* __restrict__ tpos,
                        const int* __restrict__ epos, int* __restrict__ ft_cell,
                        int* __restrict__ ft_ptr, int* __restrict__ ft_src) {
+  pdl_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)ng * kmax) return;
   const int p = (int)(i / kmax), k = (int)(i - (long long)p * kmax);
@@ -733,7 +745,7 @@ __global__ void k_ftgt(int ng, int kmax, const Geom* __restrict__ G, const int* 
 void launch_packed_plan_cons(int ng, const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
                              const int* ptr, int* out, cudaStream_t s) {
   if (ng <= 0) return;
-  k_cons<<<(ng + 127) / 128, 128, 0, s>>>(ng, gsrc_ptr, gsrc, g_meta, ptr, out);
+  launch(k_cons, (ng + 127) / 128, 128, 0, s, ng, gsrc_ptr, gsrc, g_meta, ptr, out);
 }
 
 void launch_packed_plan_ftgt(int ng, int kmax, const Geom* G, const int* g_geo, const int* g_cell,
@@ -742,7 +754,7 @@ void launch_packed_plan_ftgt(int ng, int kmax, const Geom* G, const int* g_geo, 
                              int* ft_cell, int* ft_ptr, int* ft_src, cudaStream_t s) {
   long long n = (long long)ng * kmax;
   if (n <= 0) return;
-  k_ftgt<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(ng, kmax, G, g_geo, g_cell, g_meta, tags,
+  launch(k_ftgt, (unsigned)((n + 127) / 128), 128, 0, s, ng, kmax, G, g_geo, g_cell, g_meta, tags,
                                                      pos_of_cell, R, flag, cnt, tpos, epos, ft_cell,
                                                      ft_ptr, ft_src);
 }
@@ -765,12 +777,12 @@ static void recs_t(int dim, const Geom* G, int ng, const int* g_geo, const int* 
                    const uint32_t* g_meta, const int* g_dep, const double* wtab, const PackedPlan& pp,
                    uint32_t* fwd, uint32_t* adj, uint32_t* fl, cudaStream_t s) {
   if (ng > 0) {
-    if (dim == 2) k_rec_fwd<T, 3><<<(ng + 127) / 128, 128, 0, s>>>(ng, G, g_geo, g_cell, g_meta, g_dep, wtab, fwd);
-    else k_rec_fwd<T, 7><<<(ng + 127) / 128, 128, 0, s>>>(ng, G, g_geo, g_cell, g_meta, g_dep, wtab, fwd);
-    k_rec_adj<T><<<(ng + 127) / 128, 128, 0, s>>>(ng, G, g_geo, g_cell, pp.cons_ptr, pp.cons, wtab, adj);
+    if (dim == 2) launch(k_rec_fwd<T, 3>, (ng + 127) / 128, 128, 0, s, ng, G, g_geo, g_cell, g_meta, g_dep, wtab, fwd);
+    else launch(k_rec_fwd<T, 7>, (ng + 127) / 128, 128, 0, s, ng, G, g_geo, g_cell, g_meta, g_dep, wtab, fwd);
+    launch(k_rec_adj<T>, (ng + 127) / 128, 128, 0, s, ng, G, g_geo, g_cell, pp.cons_ptr, pp.cons, wtab, adj);
   }
   if (pp.n_ft > 0)
-    k_rec_fluid<T><<<(pp.n_ft + 127) / 128, 128, 0, s>>>(pp.n_ft, pp.ft_cell, pp.ft_ptr, pp.ft_src, wtab,
+    launch(k_rec_fluid<T>, (pp.n_ft + 127) / 128, 128, 0, s, pp.n_ft, pp.ft_cell, pp.ft_ptr, pp.ft_src, wtab,
                                                          ng, fl);
 }
 
@@ -800,7 +812,7 @@ static void pfill_t(int F, void* fld, const void* bc, const KindBits& kb, const 
                     int* status, cudaStream_t s, int phase) {
   auto grid = [&](int n, const int* list, int partial) {
     if (n <= 0) return;
-    k_pf_grid<T, K><<<warp_blocks(n), PK_T, 0, s>>>((T*)fld, (const T*)bc, F, kb, rec, list, n,
+    launch(k_pf_grid<T, K>, warp_blocks(n), PK_T, 0, s, (T*)fld, (const T*)bc, F, kb, rec, list, n,
                                                     partial, status);
   };
   if (phase == 0) grid(ng, nullptr, 1);
@@ -811,11 +823,11 @@ static void pfill_t(int F, void* fld, const void* bc, const KindBits& kb, const 
     const size_t sm = pp.tail_smem[0][sizeof(T) == 4 ? 0 : 1];
     if (sm > 0) {
       smem_raise<k_pf_tail_s<T, K>>(sm);
-      k_pf_tail_s<T, K><<<dim3((F + 31) / 32, pp.n_tail), PK_CT, sm, s>>>((T*)fld, F, kb, G, pp.d_tail, rec,
+      launch(k_pf_tail_s<T, K>, dim3((F + 31) / 32, pp.n_tail), PK_CT, sm, s, (T*)fld, F, kb, G, pp.d_tail, rec,
                                                                          lev_ptr, pp.L0, pp.tail_max, ng,
                                                                          status);
     } else {
-      k_pf_tail<T, K><<<pp.n_tail, PK_CT, 0, s>>>((T*)fld, F, kb, G, pp.d_tail, rec, lev_ptr, pp.L0, status);
+      launch(k_pf_tail<T, K>, pp.n_tail, PK_CT, 0, s, (T*)fld, F, kb, G, pp.d_tail, rec, lev_ptr, pp.L0, status);
     }
   }
 }
@@ -846,12 +858,12 @@ static void padj_t(int F, void* cot, void* lamP, void* gbc, const KindBits& kb, 
     const size_t sm = pp.tail_smem[1][sizeof(T) == 4 ? 0 : 1];
     if (sm > 0) {
       smem_raise<k_pa_tail_s<T>>(sm);
-      k_pa_tail_s<T><<<dim3((F + 31) / 32, pp.n_tail_a), PK_CT, sm, s>>>((T*)cot, (T*)lamP, (T*)gbc, F, kb,
+      launch(k_pa_tail_s<T>, dim3((F + 31) / 32, pp.n_tail_a), PK_CT, sm, s, (T*)cot, (T*)lamP, (T*)gbc, F, kb,
                                                                         G, pp.d_tail_a, rec_adj, lev_ptr,
                                                                         pp.L0a, pp.cons, wtab, ng,
                                                                         pp.tail_max_a, status);
     } else {
-      k_pa_tail<T><<<pp.n_tail_a, PK_CA, 0, s>>>((T*)cot, (T*)lamP, (T*)gbc, F, kb, G, pp.d_tail_a,
+      launch(k_pa_tail<T>, pp.n_tail_a, PK_CA, 0, s, (T*)cot, (T*)lamP, (T*)gbc, F, kb, G, pp.d_tail_a,
                                                  rec_adj, lev_ptr, pp.L0a, pp.cons, wtab, ng);
     }
   }
@@ -859,11 +871,11 @@ static void padj_t(int F, void* cot, void* lamP, void* gbc, const KindBits& kb, 
     for (int lv = pp.L0a; lv >= 1; --lv) {
       const int n = pp.h_lvl_off[lv] - pp.h_lvl_off[lv - 1];
       if (n <= 0) continue;
-      k_pa_grid<T><<<warp_blocks(n), PK_T, 0, s>>>((T*)cot, (T*)lamP, (T*)gbc, F, kb, rec_adj, pp.cons,
+      launch(k_pa_grid<T>, warp_blocks(n), PK_T, 0, s, (T*)cot, (T*)lamP, (T*)gbc, F, kb, rec_adj, pp.cons,
                                                    wtab, ng, pp.d_lvl + pp.h_lvl_off[lv - 1], n);
     }
   if (phase == 2 && pp.n_ft > 0)
-    k_pa_fluid<T><<<warp_blocks(pp.n_ft), PK_T, 0, s>>>((T*)cot, (const T*)lamP, F, kb, rec_fl, pp.ft_src,
+    launch(k_pa_fluid<T>, warp_blocks(pp.n_ft), PK_T, 0, s, (T*)cot, (const T*)lamP, F, kb, rec_fl, pp.ft_src,
                                                         wtab, ng, pp.n_ft);
 }
 

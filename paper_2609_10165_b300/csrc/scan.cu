@@ -3,6 +3,7 @@
 // every tile sums the totals of the tiles before it (integer sums: exact in
 // any order).  out has n + 1 entries; out[n] is the total.
 #include "ebr_kernels.cuh"
+#include "lookback.cuh"
 
 namespace ebr {
 
@@ -10,35 +11,9 @@ constexpr int SCAN_T = 256;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_T * SCAN_ITEMS;
 
-__device__ inline int block_excl_scan(int v, int* sh_warp, int& total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) sh_warp[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    int nw = blockDim.x >> 5;
-    int s = lane < nw ? sh_warp[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < nw) sh_warp[lane] = s;
-  }
-  __syncthreads();
-  int before = w > 0 ? sh_warp[w - 1] : 0;
-  total = sh_warp[(blockDim.x >> 5) - 1];
-  __syncthreads();
-  return before + x - v;
-}
-
 __global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int* __restrict__ in, int* __restrict__ out,
                                                        int n, int* __restrict__ tile_sum) {
+  pdl_enter();
   __shared__ int sh[32];
   long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   int v[SCAN_ITEMS];
@@ -62,6 +37,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int* __restrict__ i
 
 __global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ tile_sum, int ntiles,
                                                       int* __restrict__ out, int n) {
+  pdl_enter();
   __shared__ int sh[32];
   int carry = 0;
   for (int base = 0; base < ntiles; base += SCAN_T) {
@@ -77,6 +53,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ tile_sum
 
 __global__ void __launch_bounds__(SCAN_T) k_scan_add(int* __restrict__ out, int n,
                                                      const int* __restrict__ tile_sum, int ntiles) {
+  pdl_enter();
   __shared__ int sh[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // offset of this tile: the totals of the tiles before it (one more for the
@@ -112,11 +89,11 @@ void launch_scan(const int* in, int* out, int n, void* temp, cudaStream_t s) {
   int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   int* ts = static_cast<int*>(temp);
   if (n <= 0) {
-    k_scan_sums<<<1, SCAN_T, 0, s>>>(ts, 0, out, 0);
+    launch(k_scan_sums, 1, SCAN_T, 0, s, ts, 0, out, 0);
     return;
   }
-  k_scan_tiles<<<ntiles, SCAN_T, 0, s>>>(in, out, n, ts);
-  k_scan_add<<<ntiles, SCAN_T, 0, s>>>(out, n, ts, ntiles);
+  launch(k_scan_tiles, ntiles, SCAN_T, 0, s, in, out, n, ts);
+  launch(k_scan_add, ntiles, SCAN_T, 0, s, out, n, ts, ntiles);
 }
 
 }  // namespace ebr

@@ -1,0 +1,82 @@
+// Boundary traction of one ghost (Sec. 6), shared by the force kernels.
+//
+// p_s from the Dirichlet relation solved for phi_s, grad u at S from Eq.
+// derivative_bilinear / Eqs. derivative_trilinear_x/y/z (both through the ftab
+// coefficients: ftab[0] the surface element w_G, ftab[1 + s] the p_s weights,
+// ftab[9 + 8 a + s] the d/dx_a weights of stencil value s, s = 0 the ghost),
+// traction f = -p_s n + mu (grad u + grad u^T) n, weighted by w_G.
+#pragma once
+
+#include "ebr_device.cuh"
+
+namespace ebr {
+
+struct VelSet {
+  const void* u[3];      // velocity components (null: not present)
+  const void* p;         // pressure
+  double dirs[6];        // drag direction [D], lift direction [D]
+};
+
+// Adds ghost p's pressure force [0, D), viscous force [D, 2D), drag (2D) and
+// lift (2D + 1) to acc.  The stencil values are read from the field arrays.
+template <typename T, int D>
+__device__ inline void ghost_traction(const VelSet& V, double mu, const Geom& g, int p,
+                                      const int* __restrict__ g_cell, const double* __restrict__ g_n,
+                                      const uint32_t* __restrict__ g_meta, const double* __restrict__ ftab,
+                                      int ng, double acc[8]) {
+  constexpr int K = D == 2 ? 3 : 7;
+  const int nx = g.n[0], ny = g.n[1];
+  const int cell = g_cell[p];
+  const uint32_t m = g_meta[p];
+  int slots[K + 1];
+  slots[0] = cell;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int o[3];
+    stencil_off(D, k, o);
+    int off = o[0] * meta_r(m, 0) * meta_e(m, 0) + nx * (o[1] * meta_r(m, 1) * meta_e(m, 1));
+    if (D == 3) off += nx * ny * (o[2] * meta_r(m, 2) * meta_e(m, 2));
+    slots[k + 1] = cell + off;
+  }
+  double n[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) n[a] = g_n[(size_t)a * ng + p];
+  const double wG = ftab[p];
+  const T* pp = static_cast<const T*>(V.p) + g.cell_off;
+  double ps = 0.0;
+#pragma unroll
+  for (int s = 0; s <= K; ++s) ps += ftab[(size_t)(1 + s) * ng + p] * (double)pp[slots[s]];
+  double Gm[D][D];                                        // Gm[i][a] = d u_i / d x_a
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int a = 0; a < D; ++a) Gm[i][a] = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    if (!V.u[i]) continue;
+    const T* ui = static_cast<const T*>(V.u[i]) + g.cell_off;
+#pragma unroll
+    for (int s = 0; s <= K; ++s) {
+      const double v = (double)ui[slots[s]];
+#pragma unroll
+      for (int a = 0; a < D; ++a) Gm[i][a] += ftab[(size_t)(9 + 8 * a + s) * ng + p] * v;
+    }
+  }
+  double dr = 0.0, li = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const double fp = -ps * n[i] * wG;
+    double t = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) t += (Gm[i][a] + Gm[a][i]) * n[a];
+    const double fv = mu * t * wG;
+    acc[i] += fp;
+    acc[D + i] += fv;
+    dr += (fp + fv) * V.dirs[i];
+    li += (fp + fv) * V.dirs[D + i];
+  }
+  acc[2 * D] += dr;
+  acc[2 * D + 1] += li;
+}
+
+}  // namespace ebr

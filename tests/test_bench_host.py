@@ -43,7 +43,8 @@ def test_phase_sums_cover_every_profiled_kernel():
     assert sum(ph.values()) == pytest.approx(sum(prof.values()))
     # every kernel name the library profiles belongs to a phase
     named = {k for ks in bench.PHASES.values() for k in ks}
-    for k in ("rows", "iface", "scan", "place", "reclassify", "ghost_flags", "ghost_write", "poscell",
+    for k in ("rows", "iface", "scan", "place", "reclassify", "ghost_flags", "ghost_write", "ghost_compact",
+              "ghost_geom", "poscell",
               "deps", "levels", "reorder", "tables", "gsrc", "fill_part", "fill_chain", "forces",
               "adj_seed", "adj_part", "adj_chain", "adj_probe", "adj_fluid", "adj_bc"):
         assert k in named, k
@@ -61,10 +62,10 @@ def test_algorithmic_bytes_grow_with_the_workload():
 
 
 def _profile(top_ms):
-    prof_ms = {"ghost_write": 0.0438, "fill_chain": 0.0418, "rows": 0.0400, "tables": 0.0235, "forces": 0.0377,
-               "scan": 0.0270}
+    prof_ms = {"ghost_geom": 0.0438, "fill_chain": 0.0418, "rows": 0.0400, "tables": 0.0235, "forces": 0.0377,
+               "gsrc": 0.0270}
     prof_ms.update(top_ms)
-    prof_n = {k: (3 if k == "scan" else 1) for k in prof_ms}
+    prof_n = {k: (2 if k == "gsrc" else 1) for k in prof_ms}
     algo = bench.algorithmic_bytes(48_250_166, 126_000, 171_700, 85_556, 160_000, 3)
     return prof_ms, prof_n, algo
 
@@ -76,47 +77,47 @@ def test_fp64_peak_from_unit_counts_and_clock():
 
 def test_roofline_of_an_fp64_bound_dominant_kernel(monkeypatch):
     h = bench.kernel_source_hash
-    monkeypatch.setattr(bench, "FP64_FLOPS_PER_LAUNCH", {"ghost_write": (11_876_551, h("ghost_write")),
+    monkeypatch.setattr(bench, "FP64_FLOPS_PER_LAUNCH", {"ghost_geom": (11_876_551, h("ghost_geom")),
                                                          "tables": (10_419_154, h("tables"))})
-    monkeypatch.setattr(bench, "TRAFFIC_PER_LAUNCH", {"ghost_write": (9.15e6, h("ghost_write"))})
+    monkeypatch.setattr(bench, "TRAFFIC_PER_LAUNCH", {"ghost_geom": (9.15e6, h("ghost_geom"))})
     prof_ms, prof_n, algo = _profile({})
     r = bench.roofline_object(prof_ms, prof_n, algo, 6495.6, "measured", 148, 2032.0)
-    assert r["kernel"] == "ghost_write" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["kernel"] == "ghost_geom" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     ach = 11_876_551 / 0.0438e-3 / 1e12
     assert r["achieved"] == pytest.approx(ach)
     assert r["frac"] == pytest.approx(ach / bench.fp64_peak_tflops(148, 2032.0))
     assert r["traffic"] == 9.15e6
     assert r["hbm"]["unit"] == "GB/s" and r["hbm"]["frac"] == pytest.approx(
-        algo["ghost_write"] / 0.0438e-3 / 1e9 / 6495.6)
+        algo["ghost_geom"] / 0.0438e-3 / 1e9 / 6495.6)
     assert r["per_kernel"]["tables"]["fp64_tflops"] > 0
     assert "fp64_tflops" not in r["per_kernel"]["fill_chain"]
     assert set(r["phases_ms"]) >= {"classify", "levels", "fill", "forces"}
 
 
 def test_roofline_of_a_memory_bound_dominant_kernel():
-    prof_ms, prof_n, algo = _profile({"fill_chain": 0.09, "scan": 0.03})
+    prof_ms, prof_n, algo = _profile({"fill_chain": 0.09, "gsrc": 0.03})
     r = bench.roofline_object(prof_ms, prof_n, algo, 6495.6, "measured", 148, 2032.0)
     assert r["kernel"] == "fill_chain" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(algo["fill_chain"] / 0.09e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6495.6)
     # per-launch figures divide by the launch count
-    prof_ms, prof_n, algo = _profile({"scan": 0.3})
+    prof_ms, prof_n, algo = _profile({"gsrc": 0.3})
     r = bench.roofline_object(prof_ms, prof_n, algo, 6495.6, "measured", 148, 2032.0)
-    assert r["kernel"] == "scan" and r["algo_bytes_per_launch"] == pytest.approx(algo["scan"] / 3)
-    assert r["achieved"] == pytest.approx(algo["scan"] / 3 / (0.1e-3) / 1e9)
+    assert r["kernel"] == "gsrc" and r["algo_bytes_per_launch"] == pytest.approx(algo["gsrc"] / 2)
+    assert r["achieved"] == pytest.approx(algo["gsrc"] / 2 / (0.15e-3) / 1e9)
 
 
 def test_counters_measured_on_other_source_are_null(monkeypatch):
     # a counter keyed to another version of the kernel's source is not used:
     # traffic null with the reason, and an FP64-bound kernel falls back to
     # the HBM roofline
-    monkeypatch.setattr(bench, "FP64_FLOPS_PER_LAUNCH", {"ghost_write": (11_876_551, "0" * 16)})
-    monkeypatch.setattr(bench, "TRAFFIC_PER_LAUNCH", {"ghost_write": (9.15e6, "0" * 16)})
+    monkeypatch.setattr(bench, "FP64_FLOPS_PER_LAUNCH", {"ghost_geom": (11_876_551, "0" * 16)})
+    monkeypatch.setattr(bench, "TRAFFIC_PER_LAUNCH", {"ghost_geom": (9.15e6, "0" * 16)})
     prof_ms, prof_n, algo = _profile({})
     r = bench.roofline_object(prof_ms, prof_n, algo, 6495.6, "measured", 148, 2032.0)
     assert r["traffic"] is None and "changed" in r["traffic_null_because"]
     assert r["bound"] == "hbm" and "changed" in r["fp64_flops_null_because"]
-    assert r["source_hash"] == bench.kernel_source_hash("ghost_write")
+    assert r["source_hash"] == bench.kernel_source_hash("ghost_geom")
     # every profiled kernel name has a source file
     for ks in bench.PHASES.values():
         for k in ks:
