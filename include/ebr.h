@@ -268,7 +268,11 @@ ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
  * d_vel: host array [dim] of device pointers to the filled velocity fields
  *   (an entry may be NULL: that component is identically zero); d_p: filled
  *   pressure field; d_out: device double [n_geom * (2 dim + 2)], written.
- * Sums are deterministic (fixed reduction tree) in double. */
+ * Per ghost the terms are evaluated in the field type (FP32 fields: the
+ * coefficients rounded to float, as in the fill); sums over ghosts in double,
+ * deterministic (a fixed tree per chunk of 256 ghosts, the chunks of a
+ * geometry in order).  The chunk partials and counters are context scratch:
+ * two force calls of one context must not overlap (one stream at a time). */
 ebr_status ebr_boundary_forces(void* ctx, const void* const* d_vel, const void* d_p,
                                int32_t dtype, double mu, const double* h_dirs,
                                double* d_out, ebr_stream stream);

@@ -25,26 +25,29 @@ struct AdjSet {
   void* gbc[8];
 };
 
-template <int D>
+// The force coefficients in the field type (FP32 fields: from the
+// coefficients rounded to float, as the forward forces take them).
+template <typename T, int D>
 __global__ void k_adj_seed(int F, int4 role, double mu, double dd0, double dd1, double dd2,
                            double dl0, double dl1, double dl2, const double* __restrict__ seed,
                            int ng, const int* __restrict__ g_geo, const double* __restrict__ g_n,
-                           const double* __restrict__ ftab, double* __restrict__ sv) {
+                           const double* __restrict__ ftab, T* __restrict__ sv) {
   pdl_enter();
   constexpr int K = D == 2 ? 3 : 7;
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
   int b = g_geo[p];
-  const double s0 = seed[2 * b], s1 = seed[2 * b + 1];
-  const double dd[3] = {dd0, dd1, dd2}, dl[3] = {dl0, dl1, dl2};
-  double q[D], n[D];
+  const T s0 = (T)seed[2 * b], s1 = (T)seed[2 * b + 1];
+  const T dd[3] = {(T)dd0, (T)dd1, (T)dd2}, dl[3] = {(T)dl0, (T)dl1, (T)dl2};
+  T q[D], n[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     q[a] = s0 * dd[a] + s1 * dl[a];
-    n[a] = g_n[(size_t)a * ng + p];
+    n[a] = (T)g_n[(size_t)a * ng + p];
   }
-  const double wG = ftab[p];
-  double qn = 0.0;
+  const T wG = (T)ftab[p];
+  const T muT = (T)mu;
+  T qn = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) qn += q[a] * n[a];
   const int vel[3] = {role.x, role.y, role.z};
@@ -52,25 +55,25 @@ __global__ void k_adj_seed(int F, int4 role, double mu, double dd0, double dd1, 
   for (int f = 0; f < F; ++f) {
     // velocity component of field f (if any), selected without indexing
     bool isv = false;
-    double qm = 0.0, nm = 0.0;
+    T qm = T(0), nm = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a)
       if (vel[a] == f) { isv = true; qm = q[a]; nm = n[a]; }
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      double c = 0.0;
+      T c = T(0);
       if (s <= K) {
         if (f == pidx) {
-          c = -wG * qn * ftab[(size_t)(1 + s) * ng + p];
+          c = -wG * qn * (T)ftab[(size_t)(1 + s) * ng + p];
         } else if (isv) {
-          double bn = 0.0, qb = 0.0;
+          T bn = T(0), qb = T(0);
 #pragma unroll
           for (int a = 0; a < D; ++a) {
-            const double beta = ftab[(size_t)(9 + 8 * a + s) * ng + p];
+            const T beta = (T)ftab[(size_t)(9 + 8 * a + s) * ng + p];
             bn += beta * n[a];
             qb += beta * q[a];
           }
-          c = wG * mu * (qm * bn + nm * qb);
+          c = wG * muT * (qm * bn + nm * qb);
         }
       }
       sv[(size_t)(f * 8 + s) * ng + p] = c;
@@ -78,30 +81,37 @@ __global__ void k_adj_seed(int F, int4 role, double mu, double dd0, double dd1, 
   }
 }
 
-void launch_adj_seed(int dim, int F, const int* role, double mu, const double* dirs,
+void launch_adj_seed(int dtype, int dim, int F, const int* role, double mu, const double* dirs,
                      const double* seed, int ng, const int* g_geo, const double* g_n,
-                     const double* ftab, double* sv, cudaStream_t s, int T) {
+                     const double* ftab, void* sv, cudaStream_t s, int T) {
   if (ng <= 0) return;
   int4 r = make_int4(role[0], role[1], role[2], role[3]);
   double dd[3] = {0, 0, 0}, dl[3] = {0, 0, 0};
   for (int a = 0; a < dim; ++a) { dd[a] = dirs[a]; dl[a] = dirs[dim + a]; }
-  if (dim == 2)
-    launch(k_adj_seed<2>, (ng + T - 1) / T, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
-                                                   seed, ng, g_geo, g_n, ftab, sv);
+  const unsigned nb = (unsigned)((ng + T - 1) / T);
+  if (dtype == 0 && dim == 2)
+    launch(k_adj_seed<float, 2>, nb, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2], seed, ng,
+           g_geo, g_n, ftab, (float*)sv);
+  else if (dtype == 0)
+    launch(k_adj_seed<float, 3>, nb, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2], seed, ng,
+           g_geo, g_n, ftab, (float*)sv);
+  else if (dim == 2)
+    launch(k_adj_seed<double, 2>, nb, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2], seed, ng,
+           g_geo, g_n, ftab, (double*)sv);
   else
-    launch(k_adj_seed<3>, (ng + T - 1) / T, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2],
-                                                   seed, ng, g_geo, g_n, ftab, sv);
+    launch(k_adj_seed<double, 3>, nb, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2], seed, ng,
+           g_geo, g_n, ftab, (double*)sv);
 }
 
 template <typename T>
 __device__ inline T pull_sum(int f, int kind, int j0, int j1, const int* __restrict__ src,
                              const uint32_t* __restrict__ g_meta, const double* __restrict__ wtab,
-                             const double* __restrict__ sv, int ng, const T* __restrict__ lam) {
+                             const T* __restrict__ sv, int ng, const T* __restrict__ lam) {
   T acc = T(0);
   for (int j = j0; j < j1; ++j) {
     int e = src[j];
     int q = e >> 3, s = e & 7;
-    acc += (T)sv[(size_t)(f * 8 + s) * ng + q];
+    acc += sv[(size_t)(f * 8 + s) * ng + q];
     if (s > 0 && (meta_active(g_meta[q]) >> (s - 1) & 1u))
       acc += (T)wtab[(size_t)(kind * 8 + s - 1) * ng + q] * lam[(size_t)f * ng + q];
   }
@@ -111,7 +121,7 @@ __device__ inline T pull_sum(int f, int kind, int j0, int j1, const int* __restr
 template <typename T>
 __global__ void k_adj_level(AdjSet A, int F, int p0, int p1, const int* __restrict__ gsrc_ptr,
                             const int* __restrict__ gsrc, const uint32_t* __restrict__ g_meta,
-                            const double* __restrict__ wtab, const double* __restrict__ sv, int ng,
+                            const double* __restrict__ wtab, const T* __restrict__ sv, int ng,
                             T* __restrict__ lam) {
   pdl_enter();
   int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -123,16 +133,16 @@ __global__ void k_adj_level(AdjSet A, int F, int p0, int p1, const int* __restri
 
 void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int p1,
                       const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
-                      const double* wtab, const double* sv, int ng_total, void* lam, cudaStream_t s) {
+                      const double* wtab, const void* sv, int ng_total, void* lam, cudaStream_t s) {
   (void)dim;
   if (p1 <= p0) return;
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) A.kind[f] = bc_kind[f];
   int n = p1 - p0, T = n < 128 ? 64 : 128;
   if (dtype == 0)
-    launch(k_adj_level<float>, (n + T - 1) / T, T, 0, s, A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (float*)lam);
+    launch(k_adj_level<float>, (n + T - 1) / T, T, 0, s, A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, (const float*)sv, ng_total, (float*)lam);
   else
-    launch(k_adj_level<double>, (n + T - 1) / T, T, 0, s, A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, sv, ng_total, (double*)lam);
+    launch(k_adj_level<double>, (n + T - 1) / T, T, 0, s, A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, (const double*)sv, ng_total, (double*)lam);
 }
 
 // Per ghost, grid-wide (one thread per ghost): lambda's start value, the sum
@@ -143,7 +153,7 @@ void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int
 template <typename T>
 __global__ void k_adj_part(int F, int ng, const int* __restrict__ gsrc_ptr, const int* __restrict__ gsrc,
                            const uint32_t* __restrict__ g_meta, const double* __restrict__ wtab,
-                           const double* __restrict__ sv, T* __restrict__ lpart, int* __restrict__ cq_g,
+                           const T* __restrict__ sv, T* __restrict__ lpart, int* __restrict__ cq_g,
                            T* __restrict__ cw_g, int n_src) {
   pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -155,7 +165,7 @@ __global__ void k_adj_part(int F, int ng, const int* __restrict__ gsrc_ptr, cons
     T acc = T(0);
     for (int j = j0; j < j1; ++j) {
       const int e = gsrc[j];
-      acc += (T)sv[(size_t)(f * 8 + (e & 7)) * ng + (e >> 3)];
+      acc += sv[(size_t)(f * 8 + (e & 7)) * ng + (e >> 3)];
     }
     lpart[(size_t)f * ng + p] = acc;
   }
@@ -170,14 +180,14 @@ __global__ void k_adj_part(int F, int ng, const int* __restrict__ gsrc_ptr, cons
 }
 
 void launch_adj_part(int dtype, int F, int ng, const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
-                     const double* wtab, const double* sv, void* lpart, int* cq_g, void* cw_g, int n_src,
+                     const double* wtab, const void* sv, void* lpart, int* cq_g, void* cw_g, int n_src,
                      cudaStream_t s, int T) {
   if (ng <= 0) return;
   if (dtype == 0)
-    launch(k_adj_part<float>, (ng + T - 1) / T, T, 0, s, F, ng, gsrc_ptr, gsrc, g_meta, wtab, sv, (float*)lpart,
+    launch(k_adj_part<float>, (ng + T - 1) / T, T, 0, s, F, ng, gsrc_ptr, gsrc, g_meta, wtab, (const float*)sv, (float*)lpart,
                                                      cq_g, (float*)cw_g, n_src);
   else
-    launch(k_adj_part<double>, (ng + T - 1) / T, T, 0, s, F, ng, gsrc_ptr, gsrc, g_meta, wtab, sv, (double*)lpart,
+    launch(k_adj_part<double>, (ng + T - 1) / T, T, 0, s, F, ng, gsrc_ptr, gsrc, g_meta, wtab, (const double*)sv, (double*)lpart,
                                                       cq_g, (double*)cw_g, n_src);
 }
 
@@ -307,7 +317,7 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
                             const int* __restrict__ g_geo, const int* __restrict__ g_cell,
                             const uint32_t* __restrict__ g_meta, const int8_t* __restrict__ tags,
                             const int* __restrict__ pos_of_cell, int rmax,
-                            const double* __restrict__ wtab, const double* __restrict__ sv,
+                            const double* __restrict__ wtab, const T* __restrict__ sv,
                             const T* __restrict__ lam, int accumulate, int kmax) {
   pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -337,7 +347,7 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
 #pragma unroll
     for (int f = 0; f < 8; ++f) {
       if (f < F) {
-        acc[f] += (T)sv[(size_t)(f * 8 + slot) * ng + q];
+        acc[f] += sv[(size_t)(f * 8 + slot) * ng + q];
         if (act) acc[f] += (T)wtab[(size_t)(A.kind[f] * 8 + slot - 1) * ng + q] * lam[(size_t)f * ng + q];
       }
     }
@@ -356,7 +366,7 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
 
 void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                       const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
-                      const int* pos_of_cell, int rmax, const double* wtab, const double* sv,
+                      const int* pos_of_cell, int rmax, const double* wtab, const void* sv,
                       const void* lam, void* const* grad, int accumulate, int kmax, cudaStream_t s, int T) {
   if (ng <= 0) return;
   AdjSet A{};
@@ -364,9 +374,9 @@ void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* 
   // one thread per (ghost, member): K = 3 in 2D, 7 in 3D (kmax covers both)
   int n = ng * kmax;
   if (dtype == 0)
-    launch(k_adj_fluid<float>, (n + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const float*)lam, accumulate, kmax);
+    launch(k_adj_fluid<float>, (n + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, (const float*)sv, (const float*)lam, accumulate, kmax);
   else
-    launch(k_adj_fluid<double>, (n + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, sv, (const double*)lam, accumulate, kmax);
+    launch(k_adj_fluid<double>, (n + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, (const double*)sv, (const double*)lam, accumulate, kmax);
 }
 
 // Fluid targets in two passes at reach 1: the probe needs no lambda, so it
@@ -421,7 +431,7 @@ __global__ void k_adj_fprobe(int ng, const Geom* __restrict__ G, const int* __re
 template <typename T>
 __global__ void k_adj_fpull(AdjSet A, int F, int ng, int n_inc, int cap, const int* __restrict__ fcnt,
                             const int* __restrict__ fcell, const int* __restrict__ fsrc,
-                            const double* __restrict__ wtab, const double* __restrict__ sv,
+                            const double* __restrict__ wtab, const T* __restrict__ sv,
                             const T* __restrict__ lam, int accumulate) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -439,7 +449,7 @@ __global__ void k_adj_fpull(AdjSet A, int F, int ng, int n_inc, int cap, const i
 #pragma unroll
     for (int f = 0; f < 8; ++f) {
       if (f < F) {
-        acc[f] += (T)sv[(size_t)(f * 8 + slot) * ng + q];
+        acc[f] += sv[(size_t)(f * 8 + slot) * ng + q];
         if (act) acc[f] += (T)wtab[(size_t)(A.kind[f] * 8 + slot - 1) * ng + q] * lam[(size_t)f * ng + q];
       }
     }
@@ -466,18 +476,18 @@ void launch_adj_fprobe(int ng, const Geom* G, const int* g_geo, const int* g_cel
 }
 
 void launch_adj_fpull(int dtype, int F, const int* bc_kind, int ng, int kmax, int cap, const int* fcnt,
-                      const int* fcell, const int* fsrc, const double* wtab, const double* sv, const void* lam,
+                      const int* fcell, const int* fsrc, const double* wtab, const void* sv, const void* lam,
                       void* const* grad, int accumulate, cudaStream_t s, int T) {
   if (ng <= 0) return;
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.grad[f] = grad[f]; }
   const int n = ng * kmax;
   if (dtype == 0)
-    launch(k_adj_fpull<float>, (n + T - 1) / T, T, 0, s, A, F, ng, n, cap, fcnt, fcell, fsrc, wtab, sv,
-                                                     (const float*)lam, accumulate);
+    launch(k_adj_fpull<float>, (n + T - 1) / T, T, 0, s, A, F, ng, n, cap, fcnt, fcell, fsrc, wtab,
+           (const float*)sv, (const float*)lam, accumulate);
   else
-    launch(k_adj_fpull<double>, (n + T - 1) / T, T, 0, s, A, F, ng, n, cap, fcnt, fcell, fsrc, wtab, sv,
-                                                      (const double*)lam, accumulate);
+    launch(k_adj_fpull<double>, (n + T - 1) / T, T, 0, s, A, F, ng, n, cap, fcnt, fcell, fsrc, wtab,
+           (const double*)sv, (const double*)lam, accumulate);
 }
 
 template <typename T>

@@ -142,10 +142,11 @@ struct Ctx {
   int n_chunks = 0;
   int4* chunks = nullptr;
   int* chunk_ptr = nullptr;
+  int* chunk_done = nullptr;   // finished chunks per geometry (zero between launches)
   double* partial = nullptr;
 
   // adjoint scratch
-  double* sv = nullptr;
+  double* sv = nullptr;        // force coefficients [F * 8][ng] in the field type (room for doubles)
   void* lam = nullptr;
   void* fpart = nullptr;       // fill partial sums [F <= 8][ng] (field type)
   void* apart = nullptr;       // adjoint start values [F <= 8][ng] (field type)
@@ -673,6 +674,8 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     c->n_chunks = (int)ch.size();
     AL(c->chunks, c->n_chunks);
     AL(c->chunk_ptr, c->B + 1);
+    AL(c->chunk_done, c->B);
+    CK(cudaMemset(c->chunk_done, 0, sizeof(int) * c->B));
     AL(c->partial, 8 * (size_t)std::max(c->n_chunks, 1));
     CK(cudaMemcpy(c->chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->chunk_ptr, cp.data(), sizeof(int) * cp.size(), cudaMemcpyHostToDevice));
@@ -1198,10 +1201,10 @@ ebr_status ebr_boundary_forces(void* ctx, const void* const* d_vel, const void* 
   cudaStream_t s = S(stream);
   prof_begin(c, s, "forces");
   launch_forces(dtype, dim, d_vel, d_p, mu, h_dirs, c->dG, c->n_chunks, c->chunks, c->g_cell,
-                c->g_geo, c->g_n, c->g_meta, c->ftab, c->ng, c->partial, c->B, d_out, c->chunk_ptr,
-                s);
+                c->g_geo, c->g_n, c->g_meta, c->ftab, c->ng, c->partial, c->chunk_done, c->B, d_out,
+                c->chunk_ptr, s);
   prof_end(c, s);
-  c->launches += c->n_chunks > 0 ? 2 : 1;
+  c->launches += 1;
   CKL();
   return EBR_OK;
 }
@@ -1261,7 +1264,8 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
     c->launches += 1;
   }
   prof_begin(c, s, "adj_seed");
-  launch_adj_seed(dim, n_fields, role, mu, h_dirs, d_seed, c->ng, c->g_geo, c->g_n, c->ftab, c->sv, s, c->tb[TU_ADJ_SEED]);
+  launch_adj_seed(dtype, dim, n_fields, role, mu, h_dirs, d_seed, c->ng, c->g_geo, c->g_n, c->ftab, c->sv, s,
+                  c->tb[TU_ADJ_SEED]);
   prof_end(c, s);
   c->launches += 1;
   std::vector<int> level_geoms;

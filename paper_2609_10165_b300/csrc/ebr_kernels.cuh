@@ -193,21 +193,22 @@ void launch_fill_partial(int dtype, int F, void* const* fields, const int* bc_ki
 void launch_forces(int dtype, int dim, const void* const* vel, const void* p, double mu,
                    const double* dirs, const Geom* G, int n_chunks, const int4* chunks,
                    const int* g_cell, const int* g_geo, const double* g_n, const uint32_t* g_meta,
-                   const double* ftab, int ng_total, double* partial, int B, double* out,
+                   const double* ftab, int ng_total, double* partial, int* done, int B, double* out,
                    const int* chunk_ptr, cudaStream_t s);
 
 // ---- adjoint.cu
-void launch_adj_seed(int dim, int F, const int* role, double mu, const double* dirs,
+// the force coefficients sv [F * 8][ng] in the field type (dtype)
+void launch_adj_seed(int dtype, int dim, int F, const int* role, double mu, const double* dirs,
                      const double* seed, int ng, const int* g_geo, const double* g_n,
-                     const double* ftab, double* sv, cudaStream_t s, int T = 128);
+                     const double* ftab, void* sv, cudaStream_t s, int T = 128);
 void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int p1,
                       const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
-                      const double* wtab, const double* sv, int ng_total, void* lam, cudaStream_t s);
+                      const double* wtab, const void* sv, int ng_total, void* lam, cudaStream_t s);
 size_t adj_chain_smem(int dtype, int F, int n_ghost, int n_src);
 // lambda's start values [F][ng] and the incidence records of the source
 // lists (consumer position or -1, weights [2][n_src]) for the chain kernel
 void launch_adj_part(int dtype, int F, int ng, const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
-                     const double* wtab, const double* sv, void* lpart, int* cq_g, void* cw_g, int n_src,
+                     const double* wtab, const void* sv, void* lpart, int* cq_g, void* cw_g, int n_src,
                      cudaStream_t s, int T = 128);
 void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom* G,
                       const int* geo_list, int n_list, const int* lev_ptr, const int* gsrc_ptr,
@@ -219,11 +220,11 @@ void launch_adj_fprobe(int ng, const Geom* G, const int* g_geo, const int* g_cel
                        const int8_t* tags, const int* pos_of_cell, int kmax, int cap, int* fcnt, int* fcell,
                        int* fsrc, int* status, cudaStream_t s, int T = 128);
 void launch_adj_fpull(int dtype, int F, const int* bc_kind, int ng, int kmax, int cap, const int* fcnt,
-                      const int* fcell, const int* fsrc, const double* wtab, const double* sv, const void* lam,
+                      const int* fcell, const int* fsrc, const double* wtab, const void* sv, const void* lam,
                       void* const* grad, int accumulate, cudaStream_t s, int T = 128);
 void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                       const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
-                      const int* pos_of_cell, int rmax, const double* wtab, const double* sv,
+                      const int* pos_of_cell, int rmax, const double* wtab, const void* sv,
                       const void* lam, void* const* grad, int accumulate, int kmax, cudaStream_t s, int T = 128);
 void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                    const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,

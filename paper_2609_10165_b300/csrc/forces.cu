@@ -3,8 +3,8 @@
 // Per ghost the traction of traction.cuh (p_s, grad u at S, f = -p_s n +
 // mu (grad u + grad u^T) n, weighted by w_G).  Ghosts are cut into chunks of at most
 // 256 that never straddle geometries; each CTA reduces its chunk with a fixed
-// tree, and a second kernel adds the chunk partials of each geometry in order,
-// so the sums are bitwise reproducible.
+// tree, and the last chunk of a geometry to finish adds the chunk partials of
+// the geometry in chunk order, so the sums are bitwise reproducible.
 #include "ebr_kernels.cuh"
 #include "traction.cuh"
 
@@ -21,7 +21,10 @@ __global__ void __launch_bounds__(FC_T) k_forces_chunk(VelSet V, double mu, cons
                                                        const double* __restrict__ g_n,
                                                        const uint32_t* __restrict__ g_meta,
                                                        const double* __restrict__ ftab, int ng,
-                                                       double* __restrict__ partial) {
+                                                       double* __restrict__ partial,
+                                                       const int* __restrict__ chunk_ptr,
+                                                       int* __restrict__ done, int B,
+                                                       double* __restrict__ out) {
   pdl_enter();
   // [quantity][thread]: a warp's 32 doubles of one quantity are contiguous
   // (no bank conflicts in the tree below)
@@ -52,44 +55,73 @@ __global__ void __launch_bounds__(FC_T) k_forces_chunk(VelSet V, double mu, cons
     for (int w = 16; w > 0; w >>= 1)
 #pragma unroll
       for (int q = 0; q < 8; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], w);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) partial[(size_t)blockIdx.x * 8 + q] = v[q];
+      // the last chunk of the geometry to finish adds the chunk partials in
+      // chunk order (the same sums whatever the order the chunks ran in) and
+      // resets the geometry's counter for the next launch
+      const int b = ch.x;
+      const int c0 = chunk_ptr[b], nch = chunk_ptr[b + 1] - c0;
+      __threadfence();
+      if (atomicAdd(&done[b], 1) == nch - 1) {
+        __threadfence();
+        constexpr int W = 2 * D + 2;
+        double sum[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) sum[q] = 0.0;
+        for (int c = c0; c < c0 + nch; ++c)
+#pragma unroll
+          for (int q = 0; q < W; ++q) sum[q] += __ldcg(&partial[(size_t)c * 8 + q]);
+#pragma unroll
+        for (int q = 0; q < W; ++q) out[(size_t)b * W + q] = sum[q];
+        atomicExch(&done[b], 0);
+      }
+    }
+  }
+  // geometries without ghosts have no chunk: zeros
+  if (blockIdx.x == 0) {
+    constexpr int W = 2 * D + 2;
+    for (int b = threadIdx.x; b < B; b += FC_T)
+      if (chunk_ptr[b + 1] == chunk_ptr[b])
+#pragma unroll
+        for (int q = 0; q < W; ++q) out[(size_t)b * W + q] = 0.0;
   }
 }
 
-__global__ void k_forces_final(int B, const Geom* __restrict__ G, const int* __restrict__ chunk_ptr,
-                               const double* __restrict__ partial, double* __restrict__ out) {
+// no ghost in the whole set: every output zero
+__global__ void k_forces_zero(int n, double* __restrict__ out) {
   pdl_enter();
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
-  int d = G[b].dim, W = 2 * d + 2;
-  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int c = chunk_ptr[b]; c < chunk_ptr[b + 1]; ++c)
-    for (int q = 0; q < W; ++q) s[q] += partial[(size_t)c * 8 + q];
-  for (int q = 0; q < W; ++q) out[(size_t)b * W + q] = s[q];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = 0.0;
 }
 
 void launch_forces(int dtype, int dim, const void* const* vel, const void* p, double mu,
                    const double* dirs, const Geom* G, int n_chunks, const int4* chunks,
                    const int* g_cell, const int* g_geo, const double* g_n, const uint32_t* g_meta,
-                   const double* ftab, int ng_total, double* partial, int B, double* out,
+                   const double* ftab, int ng_total, double* partial, int* done, int B, double* out,
                    const int* chunk_ptr, cudaStream_t s) {
   VelSet V;
   for (int i = 0; i < 3; ++i) V.u[i] = i < dim ? vel[i] : nullptr;
   V.p = p;
   for (int q = 0; q < 6; ++q) V.dirs[q] = q < 2 * dim ? dirs[q] : 0.0;
-  if (n_chunks > 0) {
-    if (dtype == 0 && dim == 2)
-      launch(k_forces_chunk<float, 2>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
-    else if (dtype == 0)
-      launch(k_forces_chunk<float, 3>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
-    else if (dim == 2)
-      launch(k_forces_chunk<double, 2>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
-    else
-      launch(k_forces_chunk<double, 3>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab, ng_total, partial);
+  if (n_chunks <= 0) {
+    const int n = B * (2 * dim + 2);
+    if (n > 0) launch(k_forces_zero, (n + 127) / 128, 128, 0, s, n, out);
+    return;
   }
-  launch(k_forces_final, (B + 127) / 128, 128, 0, s, B, G, chunk_ptr, partial, out);
+  if (dtype == 0 && dim == 2)
+    launch(k_forces_chunk<float, 2>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab,
+           ng_total, partial, chunk_ptr, done, B, out);
+  else if (dtype == 0)
+    launch(k_forces_chunk<float, 3>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab,
+           ng_total, partial, chunk_ptr, done, B, out);
+  else if (dim == 2)
+    launch(k_forces_chunk<double, 2>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab,
+           ng_total, partial, chunk_ptr, done, B, out);
+  else
+    launch(k_forces_chunk<double, 3>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab,
+           ng_total, partial, chunk_ptr, done, B, out);
 }
 
 }  // namespace ebr

@@ -4,7 +4,8 @@
 // derivative_bilinear / Eqs. derivative_trilinear_x/y/z (both through the ftab
 // coefficients: ftab[0] the surface element w_G, ftab[1 + s] the p_s weights,
 // ftab[9 + 8 a + s] the d/dx_a weights of stencil value s, s = 0 the ghost),
-// traction f = -p_s n + mu (grad u + grad u^T) n, weighted by w_G.
+// traction f = -p_s n + mu (grad u + grad u^T) n, weighted by w_G; the sums
+// over ghosts in double.
 #pragma once
 
 #include "ebr_device.cuh"
@@ -19,6 +20,9 @@ struct VelSet {
 
 // Adds ghost p's pressure force [0, D), viscous force [D, 2D), drag (2D) and
 // lift (2D + 1) to acc.  The stencil values are read from the field arrays.
+// The ghost's terms are computed in the field type (FP32 fields: the
+// coefficients rounded to float, as the fill does with its weights; FP64
+// fields: all in double) and added to acc in double.
 template <typename T, int D>
 __device__ inline void ghost_traction(const VelSet& V, double mu, const Geom& g, int p,
                                       const int* __restrict__ g_cell, const double* __restrict__ g_n,
@@ -38,45 +42,46 @@ __device__ inline void ghost_traction(const VelSet& V, double mu, const Geom& g,
     if (D == 3) off += nx * ny * (o[2] * meta_r(m, 2) * meta_e(m, 2));
     slots[k + 1] = cell + off;
   }
-  double n[D];
+  T n[D];
 #pragma unroll
-  for (int a = 0; a < D; ++a) n[a] = g_n[(size_t)a * ng + p];
-  const double wG = ftab[p];
+  for (int a = 0; a < D; ++a) n[a] = (T)g_n[(size_t)a * ng + p];
+  const T wG = (T)ftab[p];
   const T* pp = static_cast<const T*>(V.p) + g.cell_off;
-  double ps = 0.0;
+  T ps = T(0);
 #pragma unroll
-  for (int s = 0; s <= K; ++s) ps += ftab[(size_t)(1 + s) * ng + p] * (double)pp[slots[s]];
-  double Gm[D][D];                                        // Gm[i][a] = d u_i / d x_a
+  for (int s = 0; s <= K; ++s) ps += (T)ftab[(size_t)(1 + s) * ng + p] * pp[slots[s]];
+  T Gm[D][D];                                             // Gm[i][a] = d u_i / d x_a
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int a = 0; a < D; ++a) Gm[i][a] = 0.0;
+    for (int a = 0; a < D; ++a) Gm[i][a] = T(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     if (!V.u[i]) continue;
     const T* ui = static_cast<const T*>(V.u[i]) + g.cell_off;
 #pragma unroll
     for (int s = 0; s <= K; ++s) {
-      const double v = (double)ui[slots[s]];
+      const T v = ui[slots[s]];
 #pragma unroll
-      for (int a = 0; a < D; ++a) Gm[i][a] += ftab[(size_t)(9 + 8 * a + s) * ng + p] * v;
+      for (int a = 0; a < D; ++a) Gm[i][a] += (T)ftab[(size_t)(9 + 8 * a + s) * ng + p] * v;
     }
   }
-  double dr = 0.0, li = 0.0;
+  const T muT = (T)mu;
+  T dr = T(0), li = T(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    const double fp = -ps * n[i] * wG;
-    double t = 0.0;
+    const T fp = -ps * n[i] * wG;
+    T t = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) t += (Gm[i][a] + Gm[a][i]) * n[a];
-    const double fv = mu * t * wG;
-    acc[i] += fp;
-    acc[D + i] += fv;
-    dr += (fp + fv) * V.dirs[i];
-    li += (fp + fv) * V.dirs[D + i];
+    const T fv = muT * t * wG;
+    acc[i] += (double)fp;
+    acc[D + i] += (double)fv;
+    dr += (fp + fv) * (T)V.dirs[i];
+    li += (fp + fv) * (T)V.dirs[D + i];
   }
-  acc[2 * D] += dr;
-  acc[2 * D + 1] += li;
+  acc[2 * D] += (double)dr;
+  acc[2 * D + 1] += (double)li;
 }
 
 }  // namespace ebr
