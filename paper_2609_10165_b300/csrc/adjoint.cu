@@ -159,16 +159,21 @@ __global__ void k_adj_part(int F, int ng, const int* __restrict__ gsrc_ptr, cons
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
   const int j0 = gsrc_ptr[p], j1 = gsrc_ptr[p + 1];
+  // every field's sum in registers, each source word read once (each field
+  // still adds its sources in list order)
+  T acc[8];
 #pragma unroll
-  for (int f = 0; f < 8; ++f) {
-    if (f >= F) break;
-    T acc = T(0);
-    for (int j = j0; j < j1; ++j) {
-      const int e = gsrc[j];
-      acc += sv[(size_t)(f * 8 + (e & 7)) * ng + (e >> 3)];
-    }
-    lpart[(size_t)f * ng + p] = acc;
+  for (int f = 0; f < 8; ++f) acc[f] = T(0);
+  for (int j = j0; j < j1; ++j) {
+    const int e = gsrc[j];
+    const size_t col = (size_t)(e & 7) * ng + (e >> 3);
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+      if (f < F) acc[f] += sv[(size_t)f * 8 * ng + col];
   }
+#pragma unroll
+  for (int f = 0; f < 8; ++f)
+    if (f < F) lpart[(size_t)f * ng + p] = acc[f];
   for (int j = j0; j < j1; ++j) {
     const int e = gsrc[j];
     const int q = e >> 3, sl = e & 7;

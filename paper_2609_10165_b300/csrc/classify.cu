@@ -646,6 +646,12 @@ struct RowIface {
   int2 R;
   int bandA, bandB, bandC, bandD;
   int j, k, ny, nz, n;
+  // the usual row (non-empty run, every in-grid face-neighbour run non-empty
+  // and overlapping it, one layer): the intervals are the cells around the
+  // run's first cell and those around its last cell, two intervals (f0, f1),
+  // merged when they touch; v is not used then
+  bool fast;
+  Iv f0, f1;
 };
 
 __device__ inline void row_iface(const Geom& g, int local, const int2* __restrict__ runs, RowIface& I) {
@@ -654,26 +660,69 @@ __device__ inline void row_iface(const Geom& g, int local, const int2* __restric
   I.j = j; I.k = k; I.ny = ny; I.nz = nz; I.n = n;
   const int2 R = runs[g.row_off + local];
   I.R = R;
+  const int dj[4] = {-1, 1, 0, 0}, dk[4] = {0, 0, -1, 1};
+  int2 Qn[4];
+  bool qin[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int jj = j + dj[q], kk = k + dk[q];
+    qin[q] = !(jj < 0 || jj >= ny || kk < 0 || kk >= nz);
+    Qn[q] = qin[q] ? runs[g.row_off + jj + ny * kk] : make_int2(1, 0);
+  }
+  bool fast = g.layers != 2 && R.x <= R.y;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (qin[q] && !(Qn[q].x <= Qn[q].y && Qn[q].x <= R.y && Qn[q].y >= R.x)) fast = false;
+  I.fast = fast;
+  I.bandA = 1; I.bandB = 0; I.bandC = 1; I.bandD = 0;
+  if (fast) {
+    // every piece of R \ Q and Q \ R touches R.x - 1 / R.x or R.y / R.y + 1,
+    // as do the cells across the run's ends: their unions are one interval
+    // each side
+    constexpr int INF = 1 << 30;
+    int llo = INF, lhi = -INF, rlo = INF, rhi = -INF;
+    if (R.x > 0) { llo = R.x - 1; lhi = R.x; }
+    if (R.y < n - 1) { rlo = R.y; rhi = R.y + 1; }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!qin[q]) continue;
+      const int2 Q = Qn[q];
+      if (Q.x < R.x) { llo = min(llo, Q.x); lhi = max(lhi, R.x - 1); }
+      else if (Q.x > R.x) { llo = min(llo, R.x); lhi = max(lhi, Q.x - 1); }
+      if (Q.y < R.y) { rlo = min(rlo, Q.y + 1); rhi = max(rhi, R.y); }
+      else if (Q.y > R.y) { rlo = min(rlo, R.y + 1); rhi = max(rhi, Q.y); }
+    }
+    llo = max(llo, 0); lhi = min(lhi, n - 1);
+    rlo = max(rlo, 0); rhi = min(rhi, n - 1);
+    I.f0.a = llo; I.f0.b = lhi;
+    I.f1.a = rlo; I.f1.b = rhi;
+    if (llo <= lhi && rlo <= rhi && rlo <= lhi + 1) {   // they touch: one interval
+      I.f0.b = max(lhi, rhi);
+      I.f1.a = 1; I.f1.b = 0;
+    } else if (llo > lhi) {                             // only the right one
+      I.f0 = I.f1;
+      I.f1.a = 1; I.f1.b = 0;
+    }
+    I.w = 0;
+    return;
+  }
   Iv* v = I.v;
   int m = 0;
   if (R.x <= R.y) {
     if (R.x > 0) { add_iv(v, m, R.x, R.x, n); add_iv(v, m, R.x - 1, R.x - 1, n); }
     if (R.y < n - 1) { add_iv(v, m, R.y, R.y, n); add_iv(v, m, R.y + 1, R.y + 1, n); }
   }
-  const int dj[4] = {-1, 1, 0, 0}, dk[4] = {0, 0, -1, 1};
+#pragma unroll
   for (int q = 0; q < 4; ++q) {
-    int jj = j + dj[q], kk = k + dk[q];
-    if (jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
-    int2 Q = runs[g.row_off + jj + ny * kk];
-    add_diff(v, m, R, Q, n);
-    add_diff(v, m, Q, R, n);
+    if (!qin[q]) continue;
+    add_diff(v, m, R, Qn[q], n);
+    add_diff(v, m, Qn[q], R, n);
   }
   // second ghost layer: the solid cells of the row with a fluid cell within
   // the box reach (the run minus its erosion by the box: a cell stays out
   // only when every in-grid row of the box has a run covering it with the
   // reach to spare, a run end at the grid edge counting as covered), listed
   // as band cells (flag 2)
-  I.bandA = 1; I.bandB = 0; I.bandC = 1; I.bandD = 0;
   if (g.layers == 2 && R.x <= R.y) {
     int elo = 0, ehi = n - 1;
     const int ry = g.reach[1], rz = g.dim == 3 ? g.reach[2] : 0, rx = g.reach[0];
@@ -710,6 +759,7 @@ __device__ inline void row_iface(const Geom& g, int local, const int2* __restric
 }
 
 __device__ inline int row_iface_count(const RowIface& I) {
+  if (I.fast) return max(I.f0.b - I.f0.a + 1, 0) + max(I.f1.b - I.f1.a + 1, 0);
   int cnt = 0;
   for (int x = 0; x < I.w; ++x) cnt += I.v[x].b - I.v[x].a + 1;
   return cnt;
@@ -726,6 +776,20 @@ __device__ inline bool row_iface_write(const Geom& g, int b, const int2* __restr
   const int2 R = I.R;
   const int n = I.n, j = I.j, k = I.k, ny = I.ny, nz = I.nz;
   const int rowbase = n * (j + ny * k);
+  if (I.fast) {
+    // one layer: no band cells; the two intervals in order
+    for (int x = 0; x < 2; ++x) {
+      const Iv iv = x == 0 ? I.f0 : I.f1;
+      for (int i = iv.a; i <= iv.b; ++i) {
+        if (o >= cap) { set_status(status, S_ESHAPE); return false; }
+        iface_cell[o] = rowbase + i;
+        iface_geo[o] = b;
+        iface_solid[o] = (int8_t)(i >= R.x && i <= R.y);
+        ++o;
+      }
+    }
+    return true;
+  }
   for (int x = 0; x < I.w; ++x) {
     for (int i = I.v[x].a; i <= I.v[x].b; ++i) {
       if (o >= cap) { set_status(status, S_ESHAPE); return false; }
@@ -794,11 +858,64 @@ __global__ void k_iface_fused(const Geom* __restrict__ G, const int* __restrict_
   const int ex = block_excl_scan(cnt, sh, agg);
   const long long base = lb_prefix(L, blk, (unsigned)agg, status);
   if (base >= 0) {
+    const int o = (int)(base + ex);
     if (on) {
-      row_ptr[row] = (int)(base + ex);
-      row_iface_write(G[b], b, runs, I, (int)(base + ex), cap, iface_cell, iface_geo, iface_solid, status);
+      row_ptr[row] = o;
+      // rows off the two-interval form write their own cells
+      if (!I.fast)
+        row_iface_write(G[b], b, runs, I, o, cap, iface_cell, iface_geo, iface_solid, status);
     }
     if (row == total_rows - 1) row_ptr[total_rows] = (int)(base + ex + cnt);
+    // the warp writes the cells of its two-interval rows together: output
+    // position t of the warp's flattened list belongs to the lane r with the
+    // largest exclusive prefix <= t (a row of a few hundred cells no longer
+    // holds its warp for as many serial stores); every lane takes part in
+    // every shuffle
+    const int lane = threadIdx.x & 31;
+    const int cf = (on && I.fast) ? cnt : 0;
+    int incl = cf;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int excl = incl - cf;
+    const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+    const int len0 = (on && I.fast) ? max(I.f0.b - I.f0.a + 1, 0) : 0;
+    const int a0 = (on && I.fast) ? I.f0.a : 0, a1 = (on && I.fast) ? I.f1.a : 0;
+    const int rx = on ? I.R.x : 0, ry = on ? I.R.y : 0;
+    const int rowbase = on ? I.n * (I.j + I.ny * I.k) : 0;
+    for (int t0 = 0; t0 < wtot; t0 += 32) {
+      const int t = t0 + lane;
+      int r = 0;
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        const int c = r + d;
+        const int v = __shfl_sync(0xffffffffu, excl, c);
+        if (v <= t) r = c;
+      }
+      const int ex_r = __shfl_sync(0xffffffffu, excl, r);
+      const int o_r = __shfl_sync(0xffffffffu, o, r);
+      const int l0 = __shfl_sync(0xffffffffu, len0, r);
+      const int s0 = __shfl_sync(0xffffffffu, a0, r);
+      const int s1 = __shfl_sync(0xffffffffu, a1, r);
+      const int x0 = __shfl_sync(0xffffffffu, rx, r);
+      const int x1 = __shfl_sync(0xffffffffu, ry, r);
+      const int rb = __shfl_sync(0xffffffffu, rowbase, r);
+      const int br = __shfl_sync(0xffffffffu, b, r);
+      if (t < wtot) {
+        const int pidx = t - ex_r;
+        const int i = pidx < l0 ? s0 + pidx : s1 + (pidx - l0);
+        const int q = o_r + pidx;
+        if (q >= cap) {
+          set_status(status, S_ESHAPE);
+        } else {
+          iface_cell[q] = rb + i;
+          iface_geo[q] = br;
+          iface_solid[q] = (int8_t)(i >= x0 && i <= x1);
+        }
+      }
+    }
   }
   lb_end(L);
 }
@@ -829,7 +946,7 @@ __device__ inline void cell_ijk(const Geom& g, int cell, int& i, int& j, int& k)
   k = r / g.n[1];
 }
 
-__global__ void k_place(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
+__global__ void __launch_bounds__(256, 5) k_place(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
                         const int* __restrict__ iface_geo, const int8_t* __restrict__ iface_solid,
                         int placement, int8_t* __restrict__ tags, double* __restrict__ psi_out,
                         double* __restrict__ n_out, int* status) {

@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(LV_T, 2) k_levels(const Geom* __restrict__ G, 
     int* lp = lev_ptr + g.lev_off;
     int* lvl = fast ? sm : level + g0;
     int* dl = sm + n;                          // [K][n] local dependencies (fast path)
+#pragma unroll 4
     for (int s = threadIdx.x; s < n; s += LV_T) {
       lvl[s] = 0;
       if (fast)
