@@ -626,8 +626,8 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   // offsets in one single-pass launch, then the lists
   const int kmax = stencil_k(c->hG[0].dim);
   prof_begin(c, sg, "gsrc");
-  launch_gsrc_count(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->tags, c->pos_of_cell, kmax, c->gsrc_mem,
-                    c->gsrc_cnt, sg, c->tb[TU_GSRC]);
+  launch_gsrc_count(c->dG, ng, c->g_cell, c->g_geo, c->g_meta, c->g_dep, c->tags, c->pos_of_cell, kmax,
+                    c->gsrc_mem, c->gsrc_cnt, sg, c->tb[TU_GSRC]);
   if (planning) {
     launch_scan(c->gsrc_cnt, c->gsrc_ptr, ng, c->scan_tmp, sg);
     c->launches += 3;

@@ -164,8 +164,8 @@ void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, c
 // the own entries (self, planning), the scattered sources and the sort; or
 // offsets + own entries in one single-pass launch (a re-run)
 void launch_gsrc_count(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
-                       const int8_t* tags, const int* pos_of_cell, int kmax, int* mem, int* cnt, cudaStream_t s,
-                       int T = 128);
+                       const int* g_dep, const int8_t* tags, const int* pos_of_cell, int kmax, int* mem, int* cnt,
+                       cudaStream_t s, int T = 128);
 void launch_gsrc_lists(int ng, int kmax, const int* mem, const int* ptr, int* cursor, int* src, int cap,
                        int* status, bool self, cudaStream_t s, int T = 128);
 void launch_gsrc_place(int ng, int* cnt_cursor, int* ptr, int* src, int cap, const Lookback& L, int* status,

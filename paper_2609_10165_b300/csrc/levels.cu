@@ -596,29 +596,42 @@ void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, c
 //   k_gsrc_sort     each list after the own entry sorted (a list holds a few
 //                   entries), so the order does not depend on the scatter
 // ---------------------------------------------------------------------------
+// An active member is a ghost exactly when it is a dependency (k_deps), whose
+// position g_dep holds already; only inactive members (n_a = 0 along an
+// offset axis) are looked up through the tags.
 __global__ void k_gsrc_count(const Geom* __restrict__ G, int ng, const int* __restrict__ g_cell,
                              const int* __restrict__ g_geo, const uint32_t* __restrict__ g_meta,
-                             const int8_t* __restrict__ tags, const int* __restrict__ pos_of_cell, int kmax,
-                             int* __restrict__ mem, int* __restrict__ cnt) {
+                             const int* __restrict__ g_dep, const int8_t* __restrict__ tags,
+                             const int* __restrict__ pos_of_cell, int kmax, int* __restrict__ mem,
+                             int* __restrict__ cnt) {
   pdl_enter();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= ng) return;
-  const Geom& g = G[g_geo[q]];
-  int ijk[3];
-  cell_ijk3(g, g_cell[q], ijk);
   const uint32_t m = g_meta[q];
-  const int K = stencil_k(g.dim);
+  const uint32_t act = meta_active(m), dm = meta_depmask(m);
+  const Geom* gp = nullptr;
+  int ijk[3] = {0, 0, 0};
   for (int k = 0; k < kmax; ++k) {
     int p = -1;
-    if (k < K) {
+    if (dm >> k & 1u) {
+      p = g_dep[(size_t)k * ng + q];
+    } else if (!(act >> k & 1u)) {
+      if (!gp) {
+        gp = &G[g_geo[q]];
+        cell_ijk3(*gp, g_cell[q], ijk);
+      }
+      const Geom& g = *gp;
       int mijk[3];
-      member_ijk(g, ijk, m, k, mijk);
-      if (in_grid(g, mijk)) {
-        const int mc = cell_lin(g, mijk);
-        const int8_t t = tags[g.cell_off + mc];
-        if (t == 2 || t == -2) p = ghost_slot_of(g, mc, pos_of_cell + g.cell_off, g_cell);
+      if (k < stencil_k(g.dim)) {
+        member_ijk(g, ijk, m, k, mijk);
+        if (in_grid(g, mijk)) {
+          const int mc = cell_lin(g, mijk);
+          const int8_t t = tags[g.cell_off + mc];
+          if (t == 2 || t == -2) p = ghost_slot_of(g, mc, pos_of_cell + g.cell_off, g_cell);
+        }
       }
     }
+    if (p >= ng) p = -1;
     mem[(size_t)k * ng + q] = p;
     if (p >= 0) atomicAdd(&cnt[p], 1);
   }
@@ -699,11 +712,11 @@ __global__ void k_gsrc_sort(int ng, const int* __restrict__ ptr, int* __restrict
 }
 
 void launch_gsrc_count(const Geom* G, int ng, const int* g_cell, const int* g_geo, const uint32_t* g_meta,
-                       const int8_t* tags, const int* pos_of_cell, int kmax, int* mem, int* cnt, cudaStream_t s,
-                       int T) {
+                       const int* g_dep, const int8_t* tags, const int* pos_of_cell, int kmax, int* mem, int* cnt,
+                       cudaStream_t s, int T) {
   if (ng <= 0) return;
-  launch(k_gsrc_count, (ng + T - 1) / T, T, 0, s, G, ng, g_cell, g_geo, g_meta, tags, pos_of_cell, kmax, mem,
-         cnt);
+  launch(k_gsrc_count, (ng + T - 1) / T, T, 0, s, G, ng, g_cell, g_geo, g_meta, g_dep, tags, pos_of_cell, kmax,
+         mem, cnt);
 }
 
 void launch_gsrc_lists(int ng, int kmax, const int* mem, const int* ptr, int* cursor, int* src, int cap,
