@@ -560,24 +560,34 @@ def kernel_source_hash(kernel):
 # write-back hides most writes of a short kernel).  A figure whose hash no
 # longer matches the source is reported as null, with the reason.
 TRAFFIC_PER_LAUNCH = {
-    "rows": (0.29e6, "0945db4c2bac33e6"), "place": (1.77e6, "0945db4c2bac33e6"),
-    "iface": (1.07e6, "0945db4c2bac33e6"),
-    "tables": (9.87e6, "a2a2fe273f557785"), "levels": (1.12e6, "a2a2fe273f557785"),
-    "gsrc": (13.98e6, "a2a2fe273f557785"), "deps": (13.17e6, "a2a2fe273f557785"),
-    "reorder": (7.28e6, "a2a2fe273f557785"),
-    "fill_part": (27.85e6, "e287727b2a525463"), "fill_chain": (6.10e6, "e287727b2a525463"),
-    "forces": (32.61e6, "ae821412f312bd2b"),         # k_forces_chunk 32.54 MB + k_forces_final 0.07 MB
-    "adj_seed": (10.62e6, "6d145a6cc4882f02"), "adj_part": (6.34e6, "6d145a6cc4882f02"),
-    "adj_chain": (3.13e6, "6d145a6cc4882f02"), "adj_probe": (13.96e6, "6d145a6cc4882f02"),
-    "adj_fluid": (23.61e6, "6d145a6cc4882f02"), "adj_bc": (6.12e6, "6d145a6cc4882f02"),
+    "rows": (0.88e6, "24ebace65ebb6311"),
+    "iface": (1.25e6, "24ebace65ebb6311"),
+    "place": (1.77e6, "24ebace65ebb6311"),
+    "reclassify": (7.40e6, "24ebace65ebb6311"),
+    "ghost_compact": (7.36e6, "24ebace65ebb6311"),
+    "ghost_geom": (1.28e6, "24ebace65ebb6311"),
+    "poscell": (0.80e6, "fa0a8eb5e01b2102"),
+    "deps": (13.17e6, "fa0a8eb5e01b2102"),
+    "levels": (1.13e6, "fa0a8eb5e01b2102"),
+    "reorder": (7.29e6, "fa0a8eb5e01b2102"),
+    "tables": (9.87e6, "fa0a8eb5e01b2102"),
+    "gsrc": (3.44e6, "fa0a8eb5e01b2102"),
+    "fill_part": (27.85e6, "c3872033bc21d552"),
+    "fill_chain": (6.16e6, "c3872033bc21d552"),
+    "forces": (32.55e6, "c64d33658b142d14"),
+    "adj_seed": (10.62e6, "001f2684c5abf787"),
+    "adj_part": (4.52e6, "001f2684c5abf787"),
+    "adj_chain": (3.13e6, "001f2684c5abf787"),
+    "adj_probe": (14.01e6, "001f2684c5abf787"),
+    "adj_fluid": (20.95e6, "001f2684c5abf787"),
+    "adj_bc": (6.12e6, "001f2684c5abf787"),
 }
 
 # FP64 flops per launch (DADD + DMUL + 2 x DFMA thread instructions from one
 # ncu capture on this workload) of the kernels bound by the FP64 pipe, with
 # the source hash of the captured version.
 FP64_FLOPS_PER_LAUNCH = {
-    "ghost_geom": (11_920_293, "0945db4c2bac33e6"), "tables": (10_419_154, "a2a2fe273f557785"),
-    "adj_seed": (9_582_272, "6d145a6cc4882f02"), "forces": (7_335_675, "ae821412f312bd2b"),
+    "ghost_geom": (11_876_551, "24ebace65ebb6311"), "tables": (10_419_154, "fa0a8eb5e01b2102"),
 }
 
 
@@ -636,7 +646,7 @@ def roofline_object(prof_ms, prof_n, algo, hbm_peak, hbm_peak_kind, n_sm, sm_mhz
     else:
         roof.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": gbs / hbm_peak, "peak_source": hbm_peak_kind, "algo_bytes_per_launch": tb})
-        if top in ("ghost_geom", "tables", "adj_seed", "forces"):
+        if top in ("ghost_geom", "tables"):
             roof["fp64_flops_null_because"] = why_f
     roof["fp64_peak_tflops"] = fp64_peak
     roof["per_kernel"] = per_kernel
