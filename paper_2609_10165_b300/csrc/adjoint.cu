@@ -31,7 +31,7 @@ template <typename T, int D>
 __global__ void k_adj_seed(int F, int4 role, double mu, double dd0, double dd1, double dd2,
                            double dl0, double dl1, double dl2, const double* __restrict__ seed,
                            int ng, const int* __restrict__ g_geo, const double* __restrict__ g_n,
-                           const double* __restrict__ ftab, T* __restrict__ sv) {
+                           const T* __restrict__ ftab, T* __restrict__ sv) {
   pdl_enter();
   constexpr int K = D == 2 ? 3 : 7;
   int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -83,7 +83,7 @@ __global__ void k_adj_seed(int F, int4 role, double mu, double dd0, double dd1, 
 
 void launch_adj_seed(int dtype, int dim, int F, const int* role, double mu, const double* dirs,
                      const double* seed, int ng, const int* g_geo, const double* g_n,
-                     const double* ftab, void* sv, cudaStream_t s, int T) {
+                     const void* ftab, void* sv, cudaStream_t s, int T) {
   if (ng <= 0) return;
   int4 r = make_int4(role[0], role[1], role[2], role[3]);
   double dd[3] = {0, 0, 0}, dl[3] = {0, 0, 0};
@@ -91,21 +91,21 @@ void launch_adj_seed(int dtype, int dim, int F, const int* role, double mu, cons
   const unsigned nb = (unsigned)((ng + T - 1) / T);
   if (dtype == 0 && dim == 2)
     launch(k_adj_seed<float, 2>, nb, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2], seed, ng,
-           g_geo, g_n, ftab, (float*)sv);
+           g_geo, g_n, (const float*)ftab, (float*)sv);
   else if (dtype == 0)
     launch(k_adj_seed<float, 3>, nb, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2], seed, ng,
-           g_geo, g_n, ftab, (float*)sv);
+           g_geo, g_n, (const float*)ftab, (float*)sv);
   else if (dim == 2)
     launch(k_adj_seed<double, 2>, nb, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2], seed, ng,
-           g_geo, g_n, ftab, (double*)sv);
+           g_geo, g_n, (const double*)ftab, (double*)sv);
   else
     launch(k_adj_seed<double, 3>, nb, T, 0, s, F, r, mu, dd[0], dd[1], dd[2], dl[0], dl[1], dl[2], seed, ng,
-           g_geo, g_n, ftab, (double*)sv);
+           g_geo, g_n, (const double*)ftab, (double*)sv);
 }
 
 template <typename T>
 __device__ inline T pull_sum(int f, int kind, int j0, int j1, const int* __restrict__ src,
-                             const uint32_t* __restrict__ g_meta, const double* __restrict__ wtab,
+                             const uint32_t* __restrict__ g_meta, const T* __restrict__ wtab,
                              const T* __restrict__ sv, int ng, const T* __restrict__ lam) {
   T acc = T(0);
   for (int j = j0; j < j1; ++j) {
@@ -121,7 +121,7 @@ __device__ inline T pull_sum(int f, int kind, int j0, int j1, const int* __restr
 template <typename T>
 __global__ void k_adj_level(AdjSet A, int F, int p0, int p1, const int* __restrict__ gsrc_ptr,
                             const int* __restrict__ gsrc, const uint32_t* __restrict__ g_meta,
-                            const double* __restrict__ wtab, const T* __restrict__ sv, int ng,
+                            const T* __restrict__ wtab, const T* __restrict__ sv, int ng,
                             T* __restrict__ lam) {
   pdl_enter();
   int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -133,16 +133,16 @@ __global__ void k_adj_level(AdjSet A, int F, int p0, int p1, const int* __restri
 
 void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int p1,
                       const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
-                      const double* wtab, const void* sv, int ng_total, void* lam, cudaStream_t s) {
+                      const void* wtab, const void* sv, int ng_total, void* lam, cudaStream_t s) {
   (void)dim;
   if (p1 <= p0) return;
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) A.kind[f] = bc_kind[f];
   int n = p1 - p0, T = n < 128 ? 64 : 128;
   if (dtype == 0)
-    launch(k_adj_level<float>, (n + T - 1) / T, T, 0, s, A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, (const float*)sv, ng_total, (float*)lam);
+    launch(k_adj_level<float>, (n + T - 1) / T, T, 0, s, A, F, p0, p1, gsrc_ptr, gsrc, g_meta, (const float*)wtab, (const float*)sv, ng_total, (float*)lam);
   else
-    launch(k_adj_level<double>, (n + T - 1) / T, T, 0, s, A, F, p0, p1, gsrc_ptr, gsrc, g_meta, wtab, (const double*)sv, ng_total, (double*)lam);
+    launch(k_adj_level<double>, (n + T - 1) / T, T, 0, s, A, F, p0, p1, gsrc_ptr, gsrc, g_meta, (const double*)wtab, (const double*)sv, ng_total, (double*)lam);
 }
 
 // Per ghost, grid-wide (one thread per ghost): lambda's start value, the sum
@@ -152,7 +152,7 @@ void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int
 // weights of both kinds.
 template <typename T>
 __global__ void k_adj_part(int F, int ng, const int* __restrict__ gsrc_ptr, const int* __restrict__ gsrc,
-                           const uint32_t* __restrict__ g_meta, const double* __restrict__ wtab,
+                           const uint32_t* __restrict__ g_meta, const T* __restrict__ wtab,
                            const T* __restrict__ sv, T* __restrict__ lpart, int* __restrict__ cq_g,
                            T* __restrict__ cw_g, int n_src) {
   pdl_enter();
@@ -185,14 +185,14 @@ __global__ void k_adj_part(int F, int ng, const int* __restrict__ gsrc_ptr, cons
 }
 
 void launch_adj_part(int dtype, int F, int ng, const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
-                     const double* wtab, const void* sv, void* lpart, int* cq_g, void* cw_g, int n_src,
+                     const void* wtab, const void* sv, void* lpart, int* cq_g, void* cw_g, int n_src,
                      cudaStream_t s, int T) {
   if (ng <= 0) return;
   if (dtype == 0)
-    launch(k_adj_part<float>, (ng + T - 1) / T, T, 0, s, F, ng, gsrc_ptr, gsrc, g_meta, wtab, (const float*)sv, (float*)lpart,
+    launch(k_adj_part<float>, (ng + T - 1) / T, T, 0, s, F, ng, gsrc_ptr, gsrc, g_meta, (const float*)wtab, (const float*)sv, (float*)lpart,
                                                      cq_g, (float*)cw_g, n_src);
   else
-    launch(k_adj_part<double>, (ng + T - 1) / T, T, 0, s, F, ng, gsrc_ptr, gsrc, g_meta, wtab, (const double*)sv, (double*)lpart,
+    launch(k_adj_part<double>, (ng + T - 1) / T, T, 0, s, F, ng, gsrc_ptr, gsrc, g_meta, (const double*)wtab, (const double*)sv, (double*)lpart,
                                                       cq_g, (double*)cw_g, n_src);
 }
 
@@ -322,7 +322,7 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
                             const int* __restrict__ g_geo, const int* __restrict__ g_cell,
                             const uint32_t* __restrict__ g_meta, const int8_t* __restrict__ tags,
                             const int* __restrict__ pos_of_cell, int rmax,
-                            const double* __restrict__ wtab, const T* __restrict__ sv,
+                            const T* __restrict__ wtab, const T* __restrict__ sv,
                             const T* __restrict__ lam, int accumulate, int kmax) {
   pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -371,7 +371,7 @@ __global__ void k_adj_fluid(AdjSet A, int F, int ng, const Geom* __restrict__ G,
 
 void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                       const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
-                      const int* pos_of_cell, int rmax, const double* wtab, const void* sv,
+                      const int* pos_of_cell, int rmax, const void* wtab, const void* sv,
                       const void* lam, void* const* grad, int accumulate, int kmax, cudaStream_t s, int T) {
   if (ng <= 0) return;
   AdjSet A{};
@@ -379,9 +379,9 @@ void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* 
   // one thread per (ghost, member): K = 3 in 2D, 7 in 3D (kmax covers both)
   int n = ng * kmax;
   if (dtype == 0)
-    launch(k_adj_fluid<float>, (n + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, (const float*)sv, (const float*)lam, accumulate, kmax);
+    launch(k_adj_fluid<float>, (n + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, (const float*)wtab, (const float*)sv, (const float*)lam, accumulate, kmax);
   else
-    launch(k_adj_fluid<double>, (n + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, wtab, (const double*)sv, (const double*)lam, accumulate, kmax);
+    launch(k_adj_fluid<double>, (n + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, g_meta, tags, pos_of_cell, rmax, (const double*)wtab, (const double*)sv, (const double*)lam, accumulate, kmax);
 }
 
 // Fluid targets in two passes at reach 1: the probe needs no lambda, so it
@@ -436,7 +436,7 @@ __global__ void k_adj_fprobe(int ng, const Geom* __restrict__ G, const int* __re
 template <typename T>
 __global__ void k_adj_fpull(AdjSet A, int F, int ng, int n_inc, int cap, const int* __restrict__ fcnt,
                             const int* __restrict__ fcell, const int* __restrict__ fsrc,
-                            const double* __restrict__ wtab, const T* __restrict__ sv,
+                            const T* __restrict__ wtab, const T* __restrict__ sv,
                             const T* __restrict__ lam, int accumulate) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -481,24 +481,24 @@ void launch_adj_fprobe(int ng, const Geom* G, const int* g_geo, const int* g_cel
 }
 
 void launch_adj_fpull(int dtype, int F, const int* bc_kind, int ng, int kmax, int cap, const int* fcnt,
-                      const int* fcell, const int* fsrc, const double* wtab, const void* sv, const void* lam,
+                      const int* fcell, const int* fsrc, const void* wtab, const void* sv, const void* lam,
                       void* const* grad, int accumulate, cudaStream_t s, int T) {
   if (ng <= 0) return;
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.grad[f] = grad[f]; }
   const int n = ng * kmax;
   if (dtype == 0)
-    launch(k_adj_fpull<float>, (n + T - 1) / T, T, 0, s, A, F, ng, n, cap, fcnt, fcell, fsrc, wtab,
+    launch(k_adj_fpull<float>, (n + T - 1) / T, T, 0, s, A, F, ng, n, cap, fcnt, fcell, fsrc, (const float*)wtab,
            (const float*)sv, (const float*)lam, accumulate);
   else
-    launch(k_adj_fpull<double>, (n + T - 1) / T, T, 0, s, A, F, ng, n, cap, fcnt, fcell, fsrc, wtab,
+    launch(k_adj_fpull<double>, (n + T - 1) / T, T, 0, s, A, F, ng, n, cap, fcnt, fcell, fsrc, (const double*)wtab,
            (const double*)sv, (const double*)lam, accumulate);
 }
 
 template <typename T>
 __global__ void k_adj_bc(AdjSet A, int F, int ng, const Geom* __restrict__ G,
                          const int* __restrict__ g_geo, const int* __restrict__ g_cell,
-                         const double* __restrict__ wtab, const T* __restrict__ lam, int accumulate) {
+                         const T* __restrict__ wtab, const T* __restrict__ lam, int accumulate) {
   pdl_enter();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
@@ -512,15 +512,15 @@ __global__ void k_adj_bc(AdjSet A, int F, int ng, const Geom* __restrict__ G,
 }
 
 void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
-                   const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,
+                   const int* g_cell, const void* wtab, const void* lam, void* const* grad_bc,
                    void* const* grad, int accumulate, cudaStream_t s, int T) {
   if (ng <= 0) return;
   AdjSet A{};
   for (int f = 0; f < F && f < 8; ++f) { A.kind[f] = bc_kind[f]; A.gbc[f] = grad_bc[f]; A.grad[f] = grad[f]; }
   if (dtype == 0)
-    launch(k_adj_bc<float>, (ng + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, wtab, (const float*)lam, accumulate);
+    launch(k_adj_bc<float>, (ng + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, (const float*)wtab, (const float*)lam, accumulate);
   else
-    launch(k_adj_bc<double>, (ng + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, wtab, (const double*)lam, accumulate);
+    launch(k_adj_bc<double>, (ng + T - 1) / T, T, 0, s, A, F, ng, G, g_geo, g_cell, (const double*)wtab, (const double*)lam, accumulate);
 }
 
 }  // namespace ebr

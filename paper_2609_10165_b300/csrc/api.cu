@@ -129,6 +129,8 @@ struct Ctx {
   std::vector<int> h_lev_ptr;
   double* wtab = nullptr;
   double* ftab = nullptr;
+  float* wtab_f = nullptr;     // float copies of the tables (kernels of FP32 fields)
+  float* ftab_f = nullptr;
   int *gsrc_cnt = nullptr, *gsrc_ptr = nullptr, *gsrc = nullptr;
   int* gsrc_mem = nullptr;     // ghost position of each stencil member [K][ng] (-1: not a ghost)
   int n_gsrc = 0;
@@ -197,6 +199,7 @@ struct Ctx {
   // events, so that a stream capture records them as parallel graph branches)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_lam = nullptr, ev_bc = nullptr;   // adjoint: lambda final / BC gradients done
 };
 
 cudaEvent_t take_event(Ctx* c) {
@@ -347,15 +350,19 @@ ebr_status ensure_side(Ctx* c) {
   CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c->ev_lam, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c->ev_bc, cudaEventDisableTiming));
   return EBR_OK;
 }
 
 void destroy_side(Ctx* c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_lam) cudaEventDestroy(c->ev_lam);
+  if (c->ev_bc) cudaEventDestroy(c->ev_bc);
   if (c->side) cudaStreamDestroy(c->side);
   c->side = nullptr;
-  c->ev_fork = c->ev_join = nullptr;
+  c->ev_fork = c->ev_join = c->ev_lam = c->ev_bc = nullptr;
 }
 
 int max_smem_optin() {
@@ -368,6 +375,14 @@ int max_smem_optin() {
 ebr_status upload_geoms(Ctx* c) {
   CK(cudaMemcpy(c->dG, c->hG.data(), sizeof(Geom) * c->B, cudaMemcpyHostToDevice));
   return EBR_OK;
+}
+
+// the coefficient tables in a field type (FP32: the float copies)
+const void* wtab_of(const Ctx* c, int dtype) {
+  return dtype == EBR_F32 ? static_cast<const void*>(c->wtab_f) : static_cast<const void*>(c->wtab);
+}
+const void* ftab_of(const Ctx* c, int dtype) {
+  return dtype == EBR_F32 ? static_cast<const void*>(c->ftab_f) : static_cast<const void*>(c->ftab);
 }
 
 // the single-pass scan states of the re-run kernels (sizes of the plan)
@@ -552,6 +567,8 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     }
     AL(c->wtab, 16 * (size_t)ng);
     AL(c->ftab, 33 * (size_t)ng);
+    AL(c->wtab_f, 16 * (size_t)ng);
+    AL(c->ftab_f, 33 * (size_t)ng);
     AL(c->gsrc_cnt, ng);
     AL(c->gsrc_ptr, ng + 1);
     AL(c->gsrc_mem, (size_t)stencil_k(c->hG[0].dim) * ng);
@@ -618,7 +635,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   }
   prof_begin(c, s, "tables");
   launch_tables(c->dG, ng, c->g_cell, c->g_geo, c->g_psi, c->g_n, c->g_meta, c->tags, c->wtab,
-                c->ftab, s, c->tb[TU_TABLES]);
+                c->ftab, c->wtab_f, c->ftab_f, s, c->tb[TU_TABLES]);
   prof_end(c, s);
   c->launches += 2;   // reorder, tables
   // ghost-target sources by transposition: member positions and counts; when
@@ -1155,11 +1172,11 @@ ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
     if (cp->n_list > 0) {
       prof_begin(c, s, "fill_part");
       launch_fill_partial(dtype, n_fields, d_fields, kinds, d_bc, c->dG, c->g_geo, c->g_cell, c->g_meta,
-                          c->wtab, c->ng, c->fpart, s, c->tb[TU_FILL_PART]);
+                          wtab_of(c, dtype), c->ng, c->fpart, s, c->tb[TU_FILL_PART]);
       prof_end(c, s);
       prof_begin(c, s, "fill_chain");
       launch_fill_chain(dtype, 0, n_fields, d_fields, kinds, d_bc, c->dG, cp->d_list, cp->n_list,
-                        c->g_cell, c->g_meta, c->g_dep, c->lev_ptr, c->wtab, c->ng, cp->smem,
+                        c->g_cell, c->g_meta, c->g_dep, c->lev_ptr, wtab_of(c, dtype), c->ng, cp->smem,
                         c->fpart, c->d_status, s);
       prof_end(c, s);
       c->launches += 2;
@@ -1177,7 +1194,7 @@ ebr_status ebr_reconstruct(void* ctx, int32_t n_fields, void* const* d_fields,
       int p0 = c->h_lev_ptr[g.lev_off + lv - 1], p1 = c->h_lev_ptr[g.lev_off + lv];
       prof_begin(c, s, "fill_level");
       launch_fill_level(dtype, g.dim, n_fields, d_fields, kinds, d_bc, g.cell_off, p0, p1, c->g_cell,
-                        c->g_meta, c->wtab, c->ng, g.n[0], g.n[1], c->d_status, s);
+                        c->g_meta, wtab_of(c, dtype), c->ng, g.n[0], g.n[1], c->d_status, s);
       prof_end(c, s);
       c->launches += 1;
     }
@@ -1201,7 +1218,7 @@ ebr_status ebr_boundary_forces(void* ctx, const void* const* d_vel, const void* 
   cudaStream_t s = S(stream);
   prof_begin(c, s, "forces");
   launch_forces(dtype, dim, d_vel, d_p, mu, h_dirs, c->dG, c->n_chunks, c->chunks, c->g_cell,
-                c->g_geo, c->g_n, c->g_meta, c->ftab, c->ng, c->partial, c->chunk_done, c->B, d_out,
+                c->g_geo, c->g_n, c->g_meta, ftab_of(c, dtype), c->ng, c->partial, c->chunk_done, c->B, d_out,
                 c->chunk_ptr, s);
   prof_end(c, s);
   c->launches += 1;
@@ -1264,7 +1281,7 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
     c->launches += 1;
   }
   prof_begin(c, s, "adj_seed");
-  launch_adj_seed(dtype, dim, n_fields, role, mu, h_dirs, d_seed, c->ng, c->g_geo, c->g_n, c->ftab, c->sv, s,
+  launch_adj_seed(dtype, dim, n_fields, role, mu, h_dirs, d_seed, c->ng, c->g_geo, c->g_n, ftab_of(c, dtype), c->sv, s,
                   c->tb[TU_ADJ_SEED]);
   prof_end(c, s);
   c->launches += 1;
@@ -1272,7 +1289,7 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
   if (mode == EBR_MODE_PERSISTENT) {
     if (cp->n_list > 0) {
       prof_begin(c, s, "adj_part");
-      launch_adj_part(dtype, n_fields, c->ng, c->gsrc_ptr, c->gsrc, c->g_meta, c->wtab, c->sv, c->apart,
+      launch_adj_part(dtype, n_fields, c->ng, c->gsrc_ptr, c->gsrc, c->g_meta, wtab_of(c, dtype), c->sv, c->apart,
                       c->acq, c->acw, c->n_gsrc, s, c->tb[TU_ADJ_PART]);
       prof_end(c, s);
       prof_begin(c, s, "adj_chain");
@@ -1290,28 +1307,43 @@ ebr_status ebr_reconstruct_adjoint(void* ctx, int32_t n_fields, const int32_t* h
     for (int lv = g.n_levels; lv >= 1; --lv) {
       int p0 = c->h_lev_ptr[g.lev_off + lv - 1], p1 = c->h_lev_ptr[g.lev_off + lv];
       prof_begin(c, s, "adj_level");
-      launch_adj_level(dtype, dim, n_fields, kinds, p0, p1, c->gsrc_ptr, c->gsrc, c->g_meta, c->wtab,
+      launch_adj_level(dtype, dim, n_fields, kinds, p0, p1, c->gsrc_ptr, c->gsrc, c->g_meta, wtab_of(c, dtype),
                        c->sv, c->ng, c->lam, s);
       prof_end(c, s);
       c->launches += 1;
     }
   }
   if (split) {
+    // lambda is final: the BC gradients (and the zeros of the ghost cells'
+    // gradient entries) on the second stream beside the fluid targets' pull
+    // (disjoint outputs: ghost cells and boundary data there, fluid cells here)
+    CK(cudaEventRecord(c->ev_lam, s));
+    CK(cudaStreamWaitEvent(c->side, c->ev_lam, 0));
+    prof_begin(c, c->side, "adj_bc");
+    launch_adj_bc(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, wtab_of(c, dtype), c->lam, d_grad_bc,
+                  d_grad_fields, accumulate, c->side, c->tb[TU_ADJ_BC]);
+    prof_end(c, c->side);
+    CK(cudaEventRecord(c->ev_bc, c->side));
+    c->launches += 1;
     CK(cudaStreamWaitEvent(s, c->ev_join, 0));
     prof_begin(c, s, "adj_fluid");
-    launch_adj_fpull(dtype, n_fields, kinds, c->ng, kmax, c->af_cap, c->af_cnt, c->af_cell, c->af_src, c->wtab,
+    launch_adj_fpull(dtype, n_fields, kinds, c->ng, kmax, c->af_cap, c->af_cnt, c->af_cell, c->af_src, wtab_of(c, dtype),
                      c->sv, c->lam, d_grad_fields, accumulate, s, c->tb[TU_ADJ_FLUID]);
     prof_end(c, s);
+    c->launches += 1;
+    CK(cudaStreamWaitEvent(s, c->ev_bc, 0));
+    CKL();
+    return EBR_OK;
   } else {
     prof_begin(c, s, "adj_fluid");
     launch_adj_fluid(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->g_meta, c->tags,
-                     c->pos_of_cell, c->rmax, c->wtab, c->sv, c->lam, d_grad_fields, accumulate, kmax, s,
+                     c->pos_of_cell, c->rmax, wtab_of(c, dtype), c->sv, c->lam, d_grad_fields, accumulate, kmax, s,
                      c->tb[TU_ADJ_FLUID]);
     prof_end(c, s);
   }
   c->launches += 1;
   prof_begin(c, s, "adj_bc");
-  launch_adj_bc(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, c->wtab, c->lam, d_grad_bc,
+  launch_adj_bc(dtype, n_fields, kinds, c->ng, c->dG, c->g_geo, c->g_cell, wtab_of(c, dtype), c->lam, d_grad_bc,
                 d_grad_fields, accumulate, s, c->tb[TU_ADJ_BC]);
   prof_end(c, s);
   c->launches += 1;
@@ -1727,7 +1759,7 @@ ebr_status ebr_reconstruct_tiled(void* ctx, int32_t n_fields, void* const* d_fie
   tp.extra_once = tp.spin_once = 0;
   prof_begin(c, s, "tiled_fill");
   cudaError_t e = launch_tiled_fill(dtype, c->hG[0].dim, n_fields, d_fields, h_bc_kind, d_bc, c->dG, A, tp.grid[dtype],
-                                    c->g_geo, c->g_cell, c->g_meta, c->g_dep, c->wtab, c->ng, tp.xbuf, tp.bar,
+                                    c->g_geo, c->g_cell, c->g_meta, c->g_dep, wtab_of(c, dtype), c->ng, tp.xbuf, tp.bar,
                                     extra, c->d_status, s);
   prof_end(c, s);
   c->launches += 1;

@@ -538,7 +538,9 @@ __global__ void __launch_bounds__(256, 5) k_rows(const Geom* __restrict__ G, con
                                               int8_t* __restrict__ tags, int* status, int* stats) {
   pdl_enter();
   const int lane = threadIdx.x & 31;
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) / RG;
+  // rows interleaved across blocks: an airfoil's chord band searches for
+  // longer than other rows
+  const int row = interleaved_item() / RG;
   if (row >= total_rows) return;                 // the whole group leaves together
   RowGrp Gp;
   Gp.sl = lane & (RG - 1);
@@ -953,7 +955,7 @@ __global__ void __launch_bounds__(256, 5) k_place(const Geom* __restrict__ G, in
   pdl_enter();
   (void)psi_out;
   (void)n_out;
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = interleaved_item();     // airfoil cells cost several times ellipse cells
   if (m >= n_iface) return;
   const Geom& g = G[iface_geo[m]];
   int cell = iface_cell[m];
@@ -1213,7 +1215,7 @@ __global__ void k_ghost_geom(const Geom* __restrict__ G, int ng, int placement,
                              uint32_t* __restrict__ gs_meta, int* rmax, int* status, const PlanCheck chk) {
   pdl_enter();
   plan_check(G, chk, status);
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = interleaved_item();     // airfoil ghosts cost several times ellipse ghosts
   if (s >= ng) return;
   const Geom& g = G[gs_geo[s]];
   int cell = gs_cell[s];

@@ -34,6 +34,17 @@ __device__ inline int find_seg(const int* off, int B, int x) {
 // stream of a step and made the step slower.  A no-op for a plain launch.
 __device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Item of this thread when the warps of the grid take 32-item chunks
+// interleaved across blocks (warp w of block b: chunk w * gridDim.x + b)
+// instead of consecutively: consecutive chunks land in different blocks, so
+// that a stretch of expensive items (one geometry's airfoil cells, say) is
+// spread over all SMs instead of loading a few.  A bijection onto
+// [0, gridDim.x * blockDim.x) for a block size that is a multiple of 32;
+// every warp still reads 32 consecutive items.
+__device__ __forceinline__ int interleaved_item() {
+  return ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+}
+
 // process-wide switch (ebr_set_pdl), on by default
 extern int g_pdl;
 
@@ -156,9 +167,11 @@ void launch_reorder(const Geom* G, int* pos_of_cell, int ng, const int* order_po
                     double* g_n, uint32_t* g_meta, int* g_dep, int* g_level, cudaStream_t s,
                     const PlanCheck& chk = PlanCheck{nullptr, nullptr, nullptr, 0, 0, 0, -1},
                     int* status = nullptr);
+// weight table wtab [2][8][ng], force table ftab [33][ng] (double) and
+// their float copies
 void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, const double* g_psi,
                    const double* g_n, const uint32_t* g_meta, const int8_t* tags, double* wtab,
-                   double* ftab, cudaStream_t s, int T = 128);
+                   double* ftab, float* wtab_f, float* ftab_f, cudaStream_t s, int T = 128);
 // ghost targets' source lists by transposition: member ghost positions
 // mem [MAXK][ng] and source counts (cnt preset to 1); offsets by a scan, then
 // the own entries (self, planning), the scattered sources and the sort; or
@@ -175,40 +188,40 @@ void launch_gsrc_place(int ng, int* cnt_cursor, int* ptr, int* src, int cap, con
 // ---- fill.cu
 void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
                        const void* const* bc, long long cell_off, int p0, int p1, const int* g_cell,
-                       const uint32_t* g_meta, const double* wtab, int ng_total, int nx, int ny,
+                       const uint32_t* g_meta, const void* wtab, int ng_total, int nx, int ny,
                        int* status, cudaStream_t s);
 size_t fill_chain_smem(int dtype, int dim, int F, int n_ghost);
 void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
                        const void* const* bc, const Geom* G, const int* geo_list, int n_list,
                        const int* g_cell, const uint32_t* g_meta, const int* g_dep,
-                       const int* lev_ptr, const double* wtab, int ng_total, size_t smem,
+                       const int* lev_ptr, const void* wtab, int ng_total, size_t smem,
                        const void* part, int* status, cudaStream_t s);
 // partial sums [F][ng] (boundary term + fluid members) of every ghost, read
 // by the chain kernel
 void launch_fill_partial(int dtype, int F, void* const* fields, const int* bc_kind, const void* const* bc,
                          const Geom* G, const int* g_geo, const int* g_cell, const uint32_t* g_meta,
-                         const double* wtab, int ng, void* part, cudaStream_t s, int T = 128);
+                         const void* wtab, int ng, void* part, cudaStream_t s, int T = 128);
 
 // ---- forces.cu
 void launch_forces(int dtype, int dim, const void* const* vel, const void* p, double mu,
                    const double* dirs, const Geom* G, int n_chunks, const int4* chunks,
                    const int* g_cell, const int* g_geo, const double* g_n, const uint32_t* g_meta,
-                   const double* ftab, int ng_total, double* partial, int* done, int B, double* out,
+                   const void* ftab, int ng_total, double* partial, int* done, int B, double* out,
                    const int* chunk_ptr, cudaStream_t s);
 
 // ---- adjoint.cu
 // the force coefficients sv [F * 8][ng] in the field type (dtype)
 void launch_adj_seed(int dtype, int dim, int F, const int* role, double mu, const double* dirs,
                      const double* seed, int ng, const int* g_geo, const double* g_n,
-                     const double* ftab, void* sv, cudaStream_t s, int T = 128);
+                     const void* ftab, void* sv, cudaStream_t s, int T = 128);
 void launch_adj_level(int dtype, int dim, int F, const int* bc_kind, int p0, int p1,
                       const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
-                      const double* wtab, const void* sv, int ng_total, void* lam, cudaStream_t s);
+                      const void* wtab, const void* sv, int ng_total, void* lam, cudaStream_t s);
 size_t adj_chain_smem(int dtype, int F, int n_ghost, int n_src);
 // lambda's start values [F][ng] and the incidence records of the source
 // lists (consumer position or -1, weights [2][n_src]) for the chain kernel
 void launch_adj_part(int dtype, int F, int ng, const int* gsrc_ptr, const int* gsrc, const uint32_t* g_meta,
-                     const double* wtab, const void* sv, void* lpart, int* cq_g, void* cw_g, int n_src,
+                     const void* wtab, const void* sv, void* lpart, int* cq_g, void* cw_g, int n_src,
                      cudaStream_t s, int T = 128);
 void launch_adj_chain(int dtype, int dim, int F, const int* bc_kind, const Geom* G,
                       const int* geo_list, int n_list, const int* lev_ptr, const int* gsrc_ptr,
@@ -220,14 +233,14 @@ void launch_adj_fprobe(int ng, const Geom* G, const int* g_geo, const int* g_cel
                        const int8_t* tags, const int* pos_of_cell, int kmax, int cap, int* fcnt, int* fcell,
                        int* fsrc, int* status, cudaStream_t s, int T = 128);
 void launch_adj_fpull(int dtype, int F, const int* bc_kind, int ng, int kmax, int cap, const int* fcnt,
-                      const int* fcell, const int* fsrc, const double* wtab, const void* sv, const void* lam,
+                      const int* fcell, const int* fsrc, const void* wtab, const void* sv, const void* lam,
                       void* const* grad, int accumulate, cudaStream_t s, int T = 128);
 void launch_adj_fluid(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
                       const int* g_cell, const uint32_t* g_meta, const int8_t* tags,
-                      const int* pos_of_cell, int rmax, const double* wtab, const void* sv,
+                      const int* pos_of_cell, int rmax, const void* wtab, const void* sv,
                       const void* lam, void* const* grad, int accumulate, int kmax, cudaStream_t s, int T = 128);
 void launch_adj_bc(int dtype, int F, const int* bc_kind, int ng, const Geom* G, const int* g_geo,
-                   const int* g_cell, const double* wtab, const void* lam, void* const* grad_bc,
+                   const int* g_cell, const void* wtab, const void* lam, void* const* grad_bc,
                    void* const* grad, int accumulate, cudaStream_t s, int T = 128);
 
 // ---- stats.cu (Sec. 7, Eq. stability_alpha_max): ext [B][6] ordered bits of
@@ -259,7 +272,7 @@ int tiled_grid(int dtype, int n_tiles);
 // wait then reports EBR_ETIMEOUT)
 cudaError_t launch_tiled_fill(int dtype, int dim, int F, void* const* fields, const int* bc_kind, const void* const* bc,
                               const Geom* G, const TiledPlanDev& A, int grid, const int* g_geo,
-                              const int* g_cell, const uint32_t* g_meta, const int* g_dep, const double* wtab,
+                              const int* g_cell, const uint32_t* g_meta, const int* g_dep, const void* wtab,
                               int ng, void* xbuf, unsigned* bar, int extra_arrivals, int* status,
                               cudaStream_t s);
 

@@ -22,9 +22,11 @@ struct FieldSet {
   int kind[8];
 };
 
+// the weight table in the field type (FP32 fields: the float copy of the
+// double table)
 template <typename T>
-__device__ inline T wload(const double* wtab, int ng, int bc, int slot, int p) {
-  return (T)wtab[(size_t)(bc * 8 + slot) * ng + p];
+__device__ inline T wload(const T* wtab, int ng, int bc, int slot, int p) {
+  return wtab[(size_t)(bc * 8 + slot) * ng + p];
 }
 
 __device__ inline int member_cell(int dim, int cell, int nx, int ny, uint32_t m, int k) {
@@ -43,7 +45,7 @@ __device__ inline int member_cell(int dim, int cell, int nx, int ny, uint32_t m,
 template <typename T, int D>
 __global__ void k_fill_level(FieldSet P, int F, long long cell_off, int p0, int p1,
                              const int* __restrict__ g_cell, const uint32_t* __restrict__ g_meta,
-                             const double* __restrict__ wtab, int ng, int nx, int ny, int* status) {
+                             const T* __restrict__ wtab, int ng, int nx, int ny, int* status) {
   pdl_enter();
   constexpr int K = D == 2 ? 3 : 7;
   int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -88,7 +90,7 @@ __global__ void k_fill_level(FieldSet P, int F, long long cell_off, int p0, int 
 
 void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
                        const void* const* bc, long long cell_off, int p0, int p1, const int* g_cell,
-                       const uint32_t* g_meta, const double* wtab, int ng_total, int nx, int ny,
+                       const uint32_t* g_meta, const void* wtab, int ng_total, int nx, int ny,
                        int* status, cudaStream_t s) {
   if (p1 <= p0) return;
   FieldSet P;
@@ -101,13 +103,13 @@ void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int
   int T = n < 128 ? 64 : 128;
   const unsigned nb = (unsigned)((n + T - 1) / T);
   if (dtype == 0 && dim == 2)
-    launch(k_fill_level<float, 2>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+    launch(k_fill_level<float, 2>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, (const float*)wtab, ng_total, nx, ny, status);
   else if (dtype == 0)
-    launch(k_fill_level<float, 3>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+    launch(k_fill_level<float, 3>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, (const float*)wtab, ng_total, nx, ny, status);
   else if (dim == 2)
-    launch(k_fill_level<double, 2>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+    launch(k_fill_level<double, 2>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, (const double*)wtab, ng_total, nx, ny, status);
   else
-    launch(k_fill_level<double, 3>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, wtab, ng_total, nx, ny, status);
+    launch(k_fill_level<double, 3>, nb, T, 0, s, P, F, cell_off, p0, p1, g_cell, g_meta, (const double*)wtab, ng_total, nx, ny, status);
 }
 
 // Partial sum of every ghost and field: w_s b_G plus the fluid (non-
@@ -117,7 +119,7 @@ void launch_fill_level(int dtype, int dim, int F, void* const* fields, const int
 template <typename T>
 __global__ void k_fill_partial(FieldSet P, int F, const Geom* __restrict__ G, const int* __restrict__ g_geo,
                                const int* __restrict__ g_cell, const uint32_t* __restrict__ g_meta,
-                               const double* __restrict__ wtab, int ng, T* __restrict__ part) {
+                               const T* __restrict__ wtab, int ng, T* __restrict__ part) {
   pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
@@ -145,7 +147,7 @@ __global__ void k_fill_partial(FieldSet P, int F, const Geom* __restrict__ G, co
 
 void launch_fill_partial(int dtype, int F, void* const* fields, const int* bc_kind, const void* const* bc,
                          const Geom* G, const int* g_geo, const int* g_cell, const uint32_t* g_meta,
-                         const double* wtab, int ng, void* part, cudaStream_t s, int T) {
+                         const void* wtab, int ng, void* part, cudaStream_t s, int T) {
   if (ng <= 0) return;
   FieldSet P;
   for (int f = 0; f < 8; ++f) {
@@ -154,9 +156,9 @@ void launch_fill_partial(int dtype, int F, void* const* fields, const int* bc_ki
     P.kind[f] = f < F ? bc_kind[f] : 0;
   }
   if (dtype == 0)
-    launch(k_fill_partial<float>, (ng + T - 1) / T, T, 0, s, P, F, G, g_geo, g_cell, g_meta, wtab, ng, (float*)part);
+    launch(k_fill_partial<float>, (ng + T - 1) / T, T, 0, s, P, F, G, g_geo, g_cell, g_meta, (const float*)wtab, ng, (float*)part);
   else
-    launch(k_fill_partial<double>, (ng + T - 1) / T, T, 0, s, P, F, G, g_geo, g_cell, g_meta, wtab, ng, (double*)part);
+    launch(k_fill_partial<double>, (ng + T - 1) / T, T, 0, s, P, F, G, g_geo, g_cell, g_meta, (const double*)wtab, ng, (double*)part);
 }
 
 constexpr int CH_T = 512;
@@ -174,7 +176,7 @@ size_t fill_chain_smem(int dtype, int dim, int F, int n) {
 template <typename T>
 __device__ inline void chain_walk(const FieldSet& P, int F, const Geom& g, const int* __restrict__ g_cell,
                                   const uint32_t* __restrict__ g_meta, const int* __restrict__ g_dep,
-                                  const int* __restrict__ lev_ptr, const double* __restrict__ wtab, int ng,
+                                  const int* __restrict__ lev_ptr, const T* __restrict__ wtab, int ng,
                                   const T* __restrict__ part, int* status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = g.n_ghost, g0 = g.ghost_off, dim = g.dim;
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
                                                      const uint32_t* __restrict__ g_meta,
                                                      const int* __restrict__ g_dep,
                                                      const int* __restrict__ lev_ptr,
-                                                     const double* __restrict__ wtab, int ng,
+                                                     const T* __restrict__ wtab, int ng,
                                                      const T* __restrict__ part, int* status) {
   pdl_enter();
   chain_walk<T>(P, F, G[geo_list[blockIdx.x]], g_cell, g_meta, g_dep, lev_ptr, wtab, ng, part, status);
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(CH_T) k_fill_chain(FieldSet P, int F, const Ge
 void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int* bc_kind,
                        const void* const* bc, const Geom* G, const int* geo_list, int n_list,
                        const int* g_cell, const uint32_t* g_meta, const int* g_dep,
-                       const int* lev_ptr, const double* wtab, int ng_total, size_t smem,
+                       const int* lev_ptr, const void* wtab, int ng_total, size_t smem,
                        const void* part, int* status, cudaStream_t s) {
   (void)dim;
   if (n_list <= 0) return;
@@ -297,10 +299,10 @@ void launch_fill_chain(int dtype, int dim, int F, void* const* fields, const int
   }
   if (dtype == 0) {
     smem_raise<k_fill_chain<float>>(smem);
-    launch(k_fill_chain<float>, n_list, CH_T, smem, s, P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, (const float*)part, status);
+    launch(k_fill_chain<float>, n_list, CH_T, smem, s, P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, (const float*)wtab, ng_total, (const float*)part, status);
   } else {
     smem_raise<k_fill_chain<double>>(smem);
-    launch(k_fill_chain<double>, n_list, CH_T, smem, s, P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, wtab, ng_total, (const double*)part, status);
+    launch(k_fill_chain<double>, n_list, CH_T, smem, s, P, F, G, geo_list, g_cell, g_meta, g_dep, lev_ptr, (const double*)wtab, ng_total, (const double*)part, status);
   }
 }
 

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(FC_T) k_forces_chunk(VelSet V, double mu, cons
                                                        const int* __restrict__ g_geo,
                                                        const double* __restrict__ g_n,
                                                        const uint32_t* __restrict__ g_meta,
-                                                       const double* __restrict__ ftab, int ng,
+                                                       const T* __restrict__ ftab, int ng,
                                                        double* __restrict__ partial,
                                                        const int* __restrict__ chunk_ptr,
                                                        int* __restrict__ done, int B,
@@ -99,7 +99,7 @@ __global__ void k_forces_zero(int n, double* __restrict__ out) {
 void launch_forces(int dtype, int dim, const void* const* vel, const void* p, double mu,
                    const double* dirs, const Geom* G, int n_chunks, const int4* chunks,
                    const int* g_cell, const int* g_geo, const double* g_n, const uint32_t* g_meta,
-                   const double* ftab, int ng_total, double* partial, int* done, int B, double* out,
+                   const void* ftab, int ng_total, double* partial, int* done, int B, double* out,
                    const int* chunk_ptr, cudaStream_t s) {
   VelSet V;
   for (int i = 0; i < 3; ++i) V.u[i] = i < dim ? vel[i] : nullptr;
@@ -111,16 +111,16 @@ void launch_forces(int dtype, int dim, const void* const* vel, const void* p, do
     return;
   }
   if (dtype == 0 && dim == 2)
-    launch(k_forces_chunk<float, 2>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab,
+    launch(k_forces_chunk<float, 2>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, (const float*)ftab,
            ng_total, partial, chunk_ptr, done, B, out);
   else if (dtype == 0)
-    launch(k_forces_chunk<float, 3>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab,
+    launch(k_forces_chunk<float, 3>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, (const float*)ftab,
            ng_total, partial, chunk_ptr, done, B, out);
   else if (dim == 2)
-    launch(k_forces_chunk<double, 2>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab,
+    launch(k_forces_chunk<double, 2>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, (const double*)ftab,
            ng_total, partial, chunk_ptr, done, B, out);
   else
-    launch(k_forces_chunk<double, 3>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, ftab,
+    launch(k_forces_chunk<double, 3>, n_chunks, FC_T, 0, s, V, mu, G, chunks, g_cell, g_geo, g_n, g_meta, (const double*)ftab,
            ng_total, partial, chunk_ptr, done, B, out);
 }
 

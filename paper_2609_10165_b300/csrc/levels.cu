@@ -480,7 +480,8 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
                          const int* __restrict__ g_geo, const double* __restrict__ g_psi,
                          const double* __restrict__ g_n, const uint32_t* __restrict__ g_meta,
                          const int8_t* __restrict__ tags, double* __restrict__ wtab,
-                         double* __restrict__ ftab) {
+                         double* __restrict__ ftab, float* __restrict__ wtab_f,
+                         float* __restrict__ ftab_f) {
   pdl_enter();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
@@ -514,9 +515,17 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
   double wd[8], wn[8];
   dirichlet_w(d, X2, Xs, wd);
   neumann_w(d, X2, Xs, n, wn);
+  // the tables and their float copies (what the kernels of FP32 fields read:
+  // the same rounding as converting on use, without the conversions); only
+  // the entries a stencil of this dimension has (slots 0 .. K-1 and the
+  // boundary slot 7) are written, since no kernel reads the others
+  const int Kd = stencil_k(d);
   for (int q = 0; q < 8; ++q) {
+    if (q >= Kd && q != 7) continue;
     wtab[(size_t)q * ng + p] = wd[q];
     wtab[(size_t)(8 + q) * ng + p] = wn[q];
+    wtab_f[(size_t)q * ng + p] = (float)wd[q];
+    wtab_f[(size_t)(8 + q) * ng + p] = (float)wn[q];
   }
   // surface weight: faces shared with tag-0 cells, |n_face . n| times face
   // area (the ghost cell's own widths)
@@ -569,14 +578,22 @@ __global__ void k_tables(const Geom* __restrict__ G, int ng, const int* __restri
     bz[0] = -fx0 * fy0 * iz; bz[3] = fx0 * fy0 * iz; bz[1] = -fx1 * fy0 * iz; bz[6] = fx1 * fy0 * iz;
     bz[2] = -fx0 * fy1 * iz; bz[5] = fx0 * fy1 * iz; bz[4] = -fx1 * fy1 * iz; bz[7] = fx1 * fy1 * iz;
   }
-  for (int q = 0; q < 33; ++q) ftab[(size_t)q * ng + p] = f[q];
+  // ftab entries read for this dimension: w_G, the phi_s weights of the
+  // ghost and its K members, the gradient weights of each axis
+  for (int q = 0; q < 33; ++q) {
+    const int a = q < 9 ? -1 : (q - 9) / 8, sl = q < 9 ? q - 1 : (q - 9) % 8;
+    if (q > 0 && (sl > Kd || a >= d)) continue;
+    ftab[(size_t)q * ng + p] = f[q];
+    ftab_f[(size_t)q * ng + p] = (float)f[q];
+  }
 }
 
 void launch_tables(const Geom* G, int ng, const int* g_cell, const int* g_geo, const double* g_psi,
                    const double* g_n, const uint32_t* g_meta, const int8_t* tags, double* wtab,
-                   double* ftab, cudaStream_t s, int T) {
+                   double* ftab, float* wtab_f, float* ftab_f, cudaStream_t s, int T) {
   if (ng <= 0) return;
-  launch(k_tables, (ng + T - 1) / T, T, 0, s, G, ng, g_cell, g_geo, g_psi, g_n, g_meta, tags, wtab, ftab);
+  launch(k_tables, (ng + T - 1) / T, T, 0, s, G, ng, g_cell, g_geo, g_psi, g_n, g_meta, tags, wtab, ftab, wtab_f,
+         ftab_f);
 }
 
 // ---------------------------------------------------------------------------

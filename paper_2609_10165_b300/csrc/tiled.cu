@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(TL_T) k_tiled_fill(TiledFields P, int F, const
                                                      const int* __restrict__ g_cell,
                                                      const uint32_t* __restrict__ g_meta,
                                                      const int* __restrict__ g_dep,
-                                                     const double* __restrict__ wtab, int ng,
+                                                     const T* __restrict__ wtab, int ng,
                                                      T* __restrict__ xbuf, unsigned* bar,
                                                      int extra_arrivals, int* status) {
   constexpr int K = D == 2 ? 3 : 7;
@@ -171,7 +171,7 @@ int tiled_grid(int dtype, int n_tiles) {
 
 cudaError_t launch_tiled_fill(int dtype, int dim, int F, void* const* fields, const int* bc_kind, const void* const* bc,
                               const Geom* G, const TiledPlanDev& A, int grid, const int* g_geo,
-                              const int* g_cell, const uint32_t* g_meta, const int* g_dep, const double* wtab,
+                              const int* g_cell, const uint32_t* g_meta, const int* g_dep, const void* wtab,
                               int ng, void* xbuf, unsigned* bar, int extra_arrivals, int* status,
                               cudaStream_t s) {
   TiledFields P;
@@ -193,15 +193,15 @@ cudaError_t launch_tiled_fill(int dtype, int dim, int F, void* const* fields, co
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (dtype == 0 && dim == 2)
-    return cudaLaunchKernelEx(&cfg, k_tiled_fill<float, 2>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, wtab, ng,
+    return cudaLaunchKernelEx(&cfg, k_tiled_fill<float, 2>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, (const float*)wtab, ng,
                               static_cast<float*>(xbuf), bar, extra_arrivals, status);
   if (dtype == 0)
-    return cudaLaunchKernelEx(&cfg, k_tiled_fill<float, 3>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, wtab, ng,
+    return cudaLaunchKernelEx(&cfg, k_tiled_fill<float, 3>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, (const float*)wtab, ng,
                               static_cast<float*>(xbuf), bar, extra_arrivals, status);
   if (dim == 2)
-    return cudaLaunchKernelEx(&cfg, k_tiled_fill<double, 2>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, wtab, ng,
+    return cudaLaunchKernelEx(&cfg, k_tiled_fill<double, 2>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, (const double*)wtab, ng,
                               static_cast<double*>(xbuf), bar, extra_arrivals, status);
-  return cudaLaunchKernelEx(&cfg, k_tiled_fill<double, 3>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, wtab, ng,
+  return cudaLaunchKernelEx(&cfg, k_tiled_fill<double, 3>, P, F, G, A, g_geo, g_cell, g_meta, g_dep, (const double*)wtab, ng,
                             static_cast<double*>(xbuf), bar, extra_arrivals, status);
 }
 

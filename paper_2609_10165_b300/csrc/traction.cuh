@@ -20,13 +20,14 @@ struct VelSet {
 
 // Adds ghost p's pressure force [0, D), viscous force [D, 2D), drag (2D) and
 // lift (2D + 1) to acc.  The stencil values are read from the field arrays.
-// The ghost's terms are computed in the field type (FP32 fields: the
-// coefficients rounded to float, as the fill does with its weights; FP64
-// fields: all in double) and added to acc in double.
+// The ghost's terms are computed in the field type from the coefficient
+// table in that type (FP32 fields: the float copy of the double table, as the
+// fill does with its weights; FP64 fields: all in double) and added to acc in
+// double.
 template <typename T, int D>
 __device__ inline void ghost_traction(const VelSet& V, double mu, const Geom& g, int p,
                                       const int* __restrict__ g_cell, const double* __restrict__ g_n,
-                                      const uint32_t* __restrict__ g_meta, const double* __restrict__ ftab,
+                                      const uint32_t* __restrict__ g_meta, const T* __restrict__ ftab,
                                       int ng, double acc[8]) {
   constexpr int K = D == 2 ? 3 : 7;
   const int nx = g.n[0], ny = g.n[1];
