@@ -73,14 +73,17 @@ __device__ __forceinline__ unsigned long long lb_pack(unsigned epoch, unsigned s
   return ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | ((unsigned long long)state << 32) | value;
 }
 
+// A tile word carries its own data (epoch, state and value in one 64-bit
+// access), so the polls need no ordering with other memory: relaxed
+// device-scope accesses (acquire loads would order, and cost, every poll)
 __device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
 __device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // Per-block state of one single-pass scan.
