@@ -217,8 +217,7 @@ class Step:
         import torch
         R = self.R
         if self.geometry:
-            R.classify()
-            R.build_levels()
+            R.classify_levels()
         if self.side is not None:
             main = torch.cuda.current_stream()
             self.side.wait_stream(main)

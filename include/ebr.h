@@ -213,6 +213,23 @@ ebr_status ebr_counts(const void* ctx, ebr_geom_counts* h_counts);
  * branches as parallel graph nodes). */
 ebr_status ebr_build_levels(void* ctx, ebr_stream stream);
 
+/* ebr_classify followed by ebr_build_levels on a planned and levelled
+ * context, in one call (the per-step work of a body re-classified every
+ * step; capturable).  Same results, bitwise, as the two calls.  For a
+ * one-layer EBR_HGC plan the two overlap: the placement kernel (Eqs.
+ * delta_n, HGC_criterion) also records the sign and zero pattern of each
+ * candidate's normal -- from its float closest point where that is well
+ * conditioned (no component within 1e-3 of zero, no near tie of the closest
+ * point's branches, no foot point near the evolute), else from the double
+ * closest point -- so the ghost records carry their stencil orientation
+ * (Sec. 3.1: e_i from the sign of n_i; r_i = 1) before the double closest
+ * points (psi, S, n; Eq. signed_distance) are evaluated; those then run on
+ * the library's second stream beside the dependency levels and join before
+ * the canonical reorder, and check the recorded signs (a difference sets
+ * EBR_EINVAL in the device status).  Other placements run the two steps one
+ * after the other.  The call is ordered on `stream` like the two calls. */
+ebr_status ebr_classify_levels(void* ctx, int8_t* d_tags, ebr_stream stream);
+
 /* Ghost records in canonical order, copied to host arrays sized by the total
  * ghost count (sum of n_ghosts); any pointer may be NULL to skip it.
  *   h_geom  [Ng] int32 geometry of each ghost,

@@ -44,6 +44,7 @@ _SIGS = {
     "ebr_plan_faces": (c_int32, [c_void_p, c_int32, ctypes.POINTER(Grid), ctypes.POINTER(c_void_p),
                                  ctypes.POINTER(Body), c_int32, c_void_p, c_void_p]),
     "ebr_classify": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "ebr_classify_levels": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "ebr_move": (c_int32, [c_void_p, ctypes.POINTER(Body), c_void_p, c_void_p]),
     "ebr_layout": (c_int32, [c_void_p, ctypes.POINTER(c_int64)]),
     "ebr_counts": (c_int32, [c_void_p, ctypes.POINTER(GeomCounts)]),

@@ -149,6 +149,16 @@ class Reconstructor:
         self._check(self.lib.ebr_build_levels(self.ctx, self._stream()))
         self.levelled = True
 
+    def classify_levels(self, tags=None):
+        """Re-run the classification and the levels of a levelled context in
+        one call (ebr_classify_levels: for one-layer HGC the double closest
+        points overlap the levels)."""
+        if not self.levelled:
+            raise RuntimeError("classify_levels needs a levelled context (build_levels first)")
+        t = self.tags if tags is None else tags
+        self._check(self.lib.ebr_classify_levels(self.ctx, _ptr(t), self._stream()))
+        return t
+
     def counts(self):
         arr = (_lib.GeomCounts * self.B)()
         self._check(self.lib.ebr_counts(self.ctx, arr))

@@ -103,8 +103,7 @@ struct Ctx {
   int* iface_cell = nullptr;
   int* iface_geo = nullptr;
   int8_t* iface_solid = nullptr;
-  double* iface_psi = nullptr;
-  double* iface_n = nullptr;
+  uint8_t* iface_meta = nullptr;   // normal sign / zero bytes of the HGC candidates
   int* gflag = nullptr;
   int* gpos = nullptr;
   void* scan_tmp = nullptr;
@@ -200,6 +199,10 @@ struct Ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_lam = nullptr, ev_bc = nullptr;   // adjoint: lambda final / BC gradients done
+  // the closest points of a split re-run (ebr_classify_levels), still
+  // running on the side stream until the reorder waits for them
+  cudaEvent_t ev_geom = nullptr;
+  bool geom_pending = false;
 };
 
 cudaEvent_t take_event(Ctx* c) {
@@ -352,6 +355,7 @@ ebr_status ensure_side(Ctx* c) {
   CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&c->ev_lam, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&c->ev_bc, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c->ev_geom, cudaEventDisableTiming));
   return EBR_OK;
 }
 
@@ -360,9 +364,11 @@ void destroy_side(Ctx* c) {
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_lam) cudaEventDestroy(c->ev_lam);
   if (c->ev_bc) cudaEventDestroy(c->ev_bc);
+  if (c->ev_geom) cudaEventDestroy(c->ev_geom);
   if (c->side) cudaStreamDestroy(c->side);
   c->side = nullptr;
-  c->ev_fork = c->ev_join = c->ev_lam = c->ev_bc = nullptr;
+  c->ev_fork = c->ev_join = c->ev_lam = c->ev_bc = c->ev_geom = nullptr;
+  c->geom_pending = false;
 }
 
 int max_smem_optin() {
@@ -371,6 +377,7 @@ int max_smem_optin() {
   cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   return v;
 }
+
 
 ebr_status upload_geoms(Ctx* c) {
   CK(cudaMemcpy(c->dG, c->hG.data(), sizeof(Geom) * c->B, cudaMemcpyHostToDevice));
@@ -409,7 +416,12 @@ ebr_status lookback_alloc(Ctx* c, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // classification pipeline (planning == true: synchronise and size buffers)
 // ---------------------------------------------------------------------------
-ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
+// split (re-run of one-layer HGC only): the placement records the signs and
+// zeros of the candidates' normals, the compaction completes the meta words
+// from them, and the double closest points run on the side stream beside the
+// positions, dependencies and levels; run_levels joins them before the
+// reorder.
+ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning, bool split) {
   c->tags = d_tags;
   prof_begin(c, s, "rows");
   launch_rows(c->dG, c->d_row_off, c->B, c->total_rows, c->runs, d_tags, c->d_status, c->d_stats, s);
@@ -439,8 +451,7 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
     AL(c->iface_cell, ni);
     AL(c->iface_geo, ni);
     AL(c->iface_solid, ni);
-    AL(c->iface_psi, ni);
-    AL(c->iface_n, 3 * (size_t)ni);
+    AL(c->iface_meta, ni);
     AL(c->gflag, ni);
     AL(c->gpos, ni + 1);
     prof_begin(c, s, "iface");
@@ -456,14 +467,15 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
     prof_end(c, s);
     c->launches += 1;
   }
-  prof_begin(c, s, "place");
-  launch_place(c->dG, c->n_iface, c->iface_cell, c->iface_geo, c->iface_solid, c->placement,
-               d_tags, c->iface_psi, c->iface_n, c->d_status, s, c->tb[TU_PLACE]);
-  prof_end(c, s);
-  c->launches += 1;
   // a re-run of one-layer HGC takes pass B of the reclassification into the
   // compaction launch
   const bool fuse_b = !planning && c->placement == EBR_HGC && c->layers == 1;
+  split = split && fuse_b;
+  prof_begin(c, s, "place");
+  launch_place(c->dG, c->n_iface, c->iface_cell, c->iface_geo, c->iface_solid, c->placement,
+               d_tags, split ? c->iface_meta : nullptr, c->d_status, s, c->tb[TU_PLACE]);
+  prof_end(c, s);
+  c->launches += 1;
   if (c->placement == EBR_HGC) {
     prof_begin(c, s, "reclassify");
     launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 0, s);
@@ -484,15 +496,28 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
   }
   if (!planning) {
     prof_begin(c, s, "ghost_compact");
-    launch_ghost_compact(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, fuse_b ? 1 : 0, c->gpos,
-                         c->ng, c->gs_cell, c->gs_geo, c->gs_meta, c->lb_iface, c->d_status, s);
+    launch_ghost_compact(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, fuse_b ? 1 : 0,
+                         split ? c->iface_meta : nullptr, c->gpos, c->ng, c->gs_cell, c->gs_geo, c->gs_meta,
+                         c->lb_iface, c->d_status, s);
     prof_end(c, s);
     // the offsets against the plan: block 0 of the closest-point kernel
-    prof_begin(c, s, "ghost_geom");
+    cudaStream_t sg = s;
+    if (split) {
+      ebr_status st = ensure_side(c);
+      if (st) return st;
+      CK(cudaEventRecord(c->ev_fork, s));
+      CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+      sg = c->side;
+    }
+    prof_begin(c, sg, "ghost_geom");
     launch_ghost_geom(c->dG, c->placement, c->ng, c->gs_cell, c->gs_geo, c->gs_psi, c->gs_n, c->gs_meta,
-                      c->d_stats + 1, c->d_status, s, c->tb[TU_GHOST],
+                      split ? 1 : 0, c->d_stats + 1, c->d_status, sg, c->tb[TU_GHOST],
                       PlanCheck{c->row_ptr, c->gpos, c->d_nlev, c->B, c->n_iface, c->ng, 0});
-    prof_end(c, s);
+    prof_end(c, sg);
+    if (split) {
+      CK(cudaEventRecord(c->ev_geom, c->side));
+      c->geom_pending = true;
+    }
     c->launches += 2;
     CKL();
     return EBR_OK;
@@ -525,8 +550,8 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning) {
     CK(cudaMemsetAsync(c->d_stats + 1, 0, sizeof(int), s));
   }
   prof_begin(c, s, "ghost_write");
-  launch_ghost_write(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->iface_psi,
-                     c->iface_n, c->gpos, c->placement, c->ng, c->gs_cell, c->gs_geo, c->gs_psi,
+  launch_ghost_write(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, c->gpos, c->placement,
+                     c->ng, c->gs_cell, c->gs_geo, c->gs_psi,
                      c->gs_n, c->gs_meta, c->d_stats + 1, c->d_status, s, c->tb[TU_GHOST]);
   prof_end(c, s);
   c->launches += 2;
@@ -593,7 +618,7 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
   launch_poscell(c->dG, ng, c->gs_cell, c->gs_geo, nullptr, c->pos_of_cell, c->gsrc_cnt, s);
   prof_end(c, s);
   prof_begin(c, s, "deps");
-  launch_deps(c->dG, ng, c->gs_cell, c->gs_geo, c->gs_meta, c->gs_n, c->tags, c->pos_of_cell,
+  launch_deps(c->dG, ng, c->gs_cell, c->gs_geo, c->gs_meta, c->tags, c->pos_of_cell,
               c->dep, c->d_status, s, c->tb[TU_DEPS]);
   prof_end(c, s);
   prof_begin(c, s, "levels");
@@ -614,6 +639,11 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     CK(cudaMemcpy(c->h_lev_ptr.data(), c->lev_ptr, sizeof(int) * (ng + c->B + 1), cudaMemcpyDeviceToHost));
     ebr_status st = upload_geoms(c);
     if (st) return st;
+  }
+  // the closest points of a split re-run join here: the reorder moves them
+  if (c->geom_pending) {
+    CK(cudaStreamWaitEvent(s, c->ev_geom, 0));
+    c->geom_pending = false;
   }
   prof_begin(c, s, "reorder");
   // a re-run checks the level counts against the plan in block 0 of the reorder
@@ -984,7 +1014,7 @@ ebr_status plan_impl(Ctx* c, int32_t n_geom, const ebr_grid* h_grids, const doub
   CK(cudaMemset(c->d_status, 0, sizeof(int)));
   CK(cudaMemset(c->d_stats, 0, 4 * sizeof(int)));
   cudaStream_t s = S(stream);
-  st = run_classify(c, d_tags, s, true);
+  st = run_classify(c, d_tags, s, true, false);
   if (st) return st;
   int hs = 0;
   CK(cudaMemcpyAsync(&hs, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1025,7 +1055,25 @@ ebr_status ebr_classify(void* ctx, int8_t* d_tags, ebr_stream stream) {
   c->err.clear();
   if (!c->planned) return fail(c, EBR_EINVAL, "ebr_classify: call ebr_plan first");
   if (!d_tags) return fail(c, EBR_EINVAL, "ebr_classify: null tags");
-  return run_classify(c, d_tags, S(stream), false);
+  return run_classify(c, d_tags, S(stream), false, false);
+}
+
+ebr_status ebr_classify_levels(void* ctx, int8_t* d_tags, ebr_stream stream) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return EBR_EINVAL;
+  EbrRange range_("ebr_classify_levels");
+  c->err.clear();
+  if (!c->planned || !c->levelled)
+    return fail(c, EBR_EINVAL, "ebr_classify_levels: call ebr_plan and ebr_build_levels first");
+  if (!d_tags) return fail(c, EBR_EINVAL, "ebr_classify_levels: null tags");
+  cudaStream_t s = S(stream);
+  ebr_status st = run_classify(c, d_tags, s, false, true);
+  if (st == EBR_OK) st = run_levels(c, s, false);
+  if (c->geom_pending) {
+    cudaStreamWaitEvent(s, c->ev_geom, 0);
+    c->geom_pending = false;
+  }
+  return st;
 }
 
 ebr_status ebr_move(void* ctx, const ebr_body* h_bodies, int8_t* d_tags, ebr_stream stream) {
@@ -1055,7 +1103,7 @@ ebr_status ebr_move(void* ctx, const ebr_body* h_bodies, int8_t* d_tags, ebr_str
   if (st) return st;
   CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(c->d_stats, 0, 4 * sizeof(int), s));
-  st = run_classify(c, d_tags, s, true);
+  st = run_classify(c, d_tags, s, true, false);
   if (st) return st;
   int hs = 0;
   CK(cudaMemcpyAsync(&hs, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -948,13 +948,16 @@ __device__ inline void cell_ijk(const Geom& g, int cell, int& i, int& j, int& k)
   k = r / g.n[1];
 }
 
+// iface_meta (HGC only, may be null): for every candidate, the sign bits of
+// its normal (bits 0..2, n_a < 0) and its zero components (bits 3..5, n_a ==
+// 0), as the double closest point has them: from the float normal where it
+// is well conditioned (no component within 1e-3 of zero, no near tie), else
+// from the double closest point.
 __global__ void __launch_bounds__(256, 5) k_place(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
                         const int* __restrict__ iface_geo, const int8_t* __restrict__ iface_solid,
-                        int placement, int8_t* __restrict__ tags, double* __restrict__ psi_out,
-                        double* __restrict__ n_out, int* status) {
+                        int placement, int8_t* __restrict__ tags, uint8_t* __restrict__ iface_meta,
+                        int* status) {
   pdl_enter();
-  (void)psi_out;
-  (void)n_out;
   const int m = interleaved_item();     // airfoil cells cost several times ellipse cells
   if (m >= n_iface) return;
   const Geom& g = G[iface_geo[m]];
@@ -972,15 +975,14 @@ __global__ void __launch_bounds__(256, 5) k_place(const Geom* __restrict__ G, in
   } else {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
-    double x = centre_of(g, 0, i), y = centre_of(g, 1, j);
-    double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
     // Eq. HGC_criterion decided in float where the float psi and dn/2 are
     // clearly apart; the few cells within the safety margin use double
     const float xf = fcentre_of(g, 0, i);
     const float yf = fcentre_of(g, 1, j);
     const float zf = g.dim == 3 ? fcentre_of(g, 2, k) : 0.0f;
     float n32[3];
-    float psi32 = closest_point_f32(g, xf, yf, zf, solid, n32);
+    bool unsure = false;
+    float psi32 = closest_point_f32(g, xf, yf, zf, solid, n32, iface_meta ? &unsure : nullptr);
     float s32 = 0.0f;
     const int ijk[3] = {i, j, k};
 #pragma unroll
@@ -991,28 +993,46 @@ __global__ void __launch_bounds__(256, 5) k_place(const Geom* __restrict__ G, in
     }
     float half32 = 0.5f / sqrtf(s32);
     float gap = fabsf(psi32) - half32;
-    bool cand;
+    bool cand, dbl = false;
+    double psi, nv[3];
+    // the double closest point of the cell centre (false: normal undefined)
+    auto exact = [&]() {
+      double x = centre_of(g, 0, i), y = centre_of(g, 1, j);
+      double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
+      dbl = closest_point(g, x, y, z, solid, psi, nv);
+      return dbl;
+    };
     if (fabsf(gap) > g.hgc_mrg) {
       cand = gap <= 0.0f;
     } else {
-      double x = centre_of(g, 0, i), y = centre_of(g, 1, j);
-      double z = g.dim == 3 ? centre_of(g, 2, k) : 0.0;
-      double psi, nv[3];
-      if (!closest_point(g, x, y, z, solid, psi, nv)) { set_status(status, S_EINVAL); return; }
+      if (!exact()) { set_status(status, S_EINVAL); return; }
       double half = 0.5 * delta_n(g, nv, i, j, k);
       cand = solid ? (psi <= half) : (-psi < half);
     }
-    if (cand) tag = solid ? 2 : -2;
+    if (cand) {
+      tag = solid ? 2 : -2;
+      if (iface_meta) {
+        if (unsure && !dbl && !exact()) { set_status(status, S_EINVAL); return; }
+        uint32_t mb = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (a >= g.dim) continue;
+          if (dbl ? nv[a] < 0.0 : n32[a] < 0.0f) mb |= 1u << a;
+          if (dbl && nv[a] == 0.0) mb |= 8u << a;
+        }
+        iface_meta[m] = (uint8_t)mb;
+      }
+    }
   }
   tags[g.cell_off + cell] = tag;
 }
 
 void launch_place(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
-                  const int8_t* iface_solid, int placement, int8_t* tags, double* iface_psi,
-                  double* iface_n, int* status, cudaStream_t s, int T) {
+                  const int8_t* iface_solid, int placement, int8_t* tags, uint8_t* iface_meta,
+                  int* status, cudaStream_t s, int T) {
   if (n_iface <= 0) return;
   launch(k_place, (n_iface + T - 1) / T, T, 0, s, G, n_iface, iface_cell, iface_geo, iface_solid,
-                                                placement, tags, iface_psi, iface_n, status);
+                                                placement, tags, iface_meta, status);
 }
 
 // HGC reclassification.  pass 0 (A): -2 without a tag-1 face neighbour -> 0.
@@ -1160,11 +1180,14 @@ __global__ void k_ghost_write(const Geom* __restrict__ G, int n_iface, const int
 // order).  Then the ghost flag (tag +-2) of every interface cell, the offsets
 // by a single-pass scan in list order (the scan of the flags) and the ghost
 // records (cell, geometry, fluid-side flag).  gpos[n_iface] = total.
+// With iface_meta (one-layer HGC) the meta word of a ghost is complete here:
+// normal signs and structurally active members from the placement's normal
+// bytes, r = 1 on every axis; the closest points then only supply psi, S, n.
 __global__ void k_ghost_compact(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
                                 const int* __restrict__ iface_geo, int8_t* __restrict__ tags, int pass_b,
-                                int* __restrict__ gpos, int cap, int* __restrict__ gs_cell,
-                                int* __restrict__ gs_geo, uint32_t* __restrict__ gs_meta, const Lookback L,
-                                int* status) {
+                                const uint8_t* __restrict__ iface_meta, int* __restrict__ gpos, int cap,
+                                int* __restrict__ gs_cell, int* __restrict__ gs_geo,
+                                uint32_t* __restrict__ gs_meta, const Lookback L, int* status) {
   pdl_enter();
   __shared__ int sh[32];
   const LbBlock blk = lb_begin(L);
@@ -1172,10 +1195,12 @@ __global__ void k_ghost_compact(const Geom* __restrict__ G, int n_iface, const i
   const bool on = m < n_iface;
   int b = 0, cell = 0;
   int8_t t = 0;
+  uint32_t mb = 0;
   if (on) {
     b = iface_geo[m];
     const Geom& g = G[b];
     cell = iface_cell[m];
+    if (iface_meta) mb = iface_meta[m];     // loaded before the scan's waits
     int8_t* tg = tags + g.cell_off;
     t = tg[cell];
     if (pass_b && t == 2 && !has_face_tag(g, tg, cell, 0)) {
@@ -1197,7 +1222,13 @@ __global__ void k_ghost_compact(const Geom* __restrict__ G, int n_iface, const i
         } else {
           gs_cell[q] = cell;
           gs_geo[q] = b;
-          gs_meta[q] = t == -2 ? (1u << 22) : 0u;
+          uint32_t meta = t == -2 ? (1u << 22) : 0u;
+          if (iface_meta) {
+            const int dim = G[b].dim;
+            meta |= (mb & 7u) | (active_of_zero(dim, mb >> 3) << 15);
+            for (int a = 0; a < dim; ++a) meta |= 1u << (3 + 4 * a);
+          }
+          gs_meta[q] = meta;
         }
       }
     }
@@ -1208,18 +1239,24 @@ __global__ void k_ghost_compact(const Geom* __restrict__ G, int n_iface, const i
 
 // psi, S and n in double for the compacted ghosts only (Eq. signed_distance),
 // one ghost per thread so that no lane idles through the FP64 work; sign
-// bits e and stencil multipliers r (Eq. stencil_anisotropic for CGC_ES)
+// bits e, stencil multipliers r (Eq. stencil_anisotropic for CGC_ES) and the
+// structurally active members.  split: the compaction wrote the meta words
+// from the placement's normals (one-layer HGC) and the dependency kernels
+// may be reading them already; this kernel then leaves them alone and only
+// checks them against the double normal (EBR_EINVAL on a difference).
 __global__ void k_ghost_geom(const Geom* __restrict__ G, int ng, int placement,
                              const int* __restrict__ gs_cell, const int* __restrict__ gs_geo,
                              double* __restrict__ gs_psi, double* __restrict__ gs_n,
-                             uint32_t* __restrict__ gs_meta, int* rmax, int* status, const PlanCheck chk) {
+                             uint32_t* __restrict__ gs_meta, int split, int* rmax, int* status,
+                             const PlanCheck chk) {
   pdl_enter();
   plan_check(G, chk, status);
   const int s = interleaved_item();     // airfoil ghosts cost several times ellipse ghosts
   if (s >= ng) return;
   const Geom& g = G[gs_geo[s]];
   int cell = gs_cell[s];
-  uint32_t meta = gs_meta[s] & (1u << 22);
+  const uint32_t m0 = gs_meta[s];
+  uint32_t meta = m0 & (1u << 22);
   bool solid = meta == 0;
   double psi, nv[3];
   int i, j, k;
@@ -1244,44 +1281,55 @@ __global__ void k_ghost_geom(const Geom* __restrict__ G, int ng, int placement,
     rloc = max(rloc, r);
     meta |= (uint32_t)r << (3 + 4 * a);
   }
+  uint32_t zero = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < g.dim && nv[a] == 0.0) zero |= 1u << a;
+  const uint32_t act = active_of_zero(g.dim, zero);
+  meta |= act << 15;
   gs_psi[s] = psi;
   gs_n[s] = nv[0];
   gs_n[ng + s] = nv[1];
   gs_n[2 * (size_t)ng + s] = nv[2];
-  gs_meta[s] = meta;
+  if (split) {
+    // the dependency kernel keeps bits 0..14 and narrows the active bits to
+    // the in-grid members (an out-of-grid member is an error of its own)
+    if ((m0 & 0x7fffu) != (meta & 0x7fffu) || ((m0 >> 15) & 127u & ~act) != 0u)
+      set_status(status, S_EINVAL);
+  } else {
+    gs_meta[s] = meta;
+  }
   if (rloc > 1) atomicMax(rmax, rloc);
 }
 
 void launch_ghost_compact(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
-                          int8_t* tags, int pass_b, int* gpos, int ng_cap, int* gs_cell, int* gs_geo,
-                          uint32_t* gs_meta, const Lookback& L, int* status, cudaStream_t s) {
+                          int8_t* tags, int pass_b, const uint8_t* iface_meta, int* gpos, int ng_cap,
+                          int* gs_cell, int* gs_geo, uint32_t* gs_meta, const Lookback& L, int* status,
+                          cudaStream_t s) {
   if (n_iface <= 0) return;
   launch(k_ghost_compact, (n_iface + LB_T - 1) / LB_T, LB_T, 0, s, G, n_iface, iface_cell, iface_geo, tags,
-         pass_b, gpos, ng_cap, gs_cell, gs_geo, gs_meta, L, status);
+         pass_b, iface_meta, gpos, ng_cap, gs_cell, gs_geo, gs_meta, L, status);
 }
 
-// psi, S, n and the meta words of the compacted ghosts
+// psi, S, n and (split == 0) the meta words of the compacted ghosts
 void launch_ghost_geom(const Geom* G, int placement, int ng_cap, int* gs_cell, int* gs_geo, double* gs_psi,
-                       double* gs_n, uint32_t* gs_meta, int* rmax, int* status, cudaStream_t s, int T,
-                       const PlanCheck& chk) {
+                       double* gs_n, uint32_t* gs_meta, int split, int* rmax, int* status, cudaStream_t s,
+                       int T, const PlanCheck& chk) {
   if (ng_cap <= 0) return;
-  launch(k_ghost_geom, (ng_cap + T - 1) / T, T, 0, s, G, ng_cap, placement, gs_cell, gs_geo, gs_psi,
-         gs_n, gs_meta, rmax, status, chk);
+  launch(k_ghost_geom, (ng_cap + T - 1) / T, T, 0, s, G, ng_cap, placement, gs_cell, gs_geo, gs_psi, gs_n,
+         gs_meta, split, rmax, status, chk);
 }
 
 void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
-                        const int8_t* tags, const double* iface_psi, const double* iface_n,
-                        const int* gpos, int placement, int ng_cap, int* gs_cell, int* gs_geo,
-                        double* gs_psi, double* gs_n, uint32_t* gs_meta, int* rmax,
+                        const int8_t* tags, const int* gpos, int placement, int ng_cap, int* gs_cell,
+                        int* gs_geo, double* gs_psi, double* gs_n, uint32_t* gs_meta, int* rmax,
                         int* status, cudaStream_t s, int T) {
-  (void)iface_psi;
-  (void)iface_n;
   if (n_iface <= 0) return;
   launch(k_ghost_write, (n_iface + 255) / 256, 256, 0, s, G, n_iface, iface_cell, iface_geo, tags, gpos,
                                                       ng_cap, gs_cell, gs_geo, gs_meta, status);
   if (ng_cap <= 0) return;
   launch(k_ghost_geom, (ng_cap + T - 1) / T, T, 0, s, G, ng_cap, placement, gs_cell, gs_geo, gs_psi,
-         gs_n, gs_meta, rmax, status, PlanCheck{nullptr, nullptr, nullptr, 0, 0, 0, -1});
+         gs_n, gs_meta, 0, rmax, status, PlanCheck{nullptr, nullptr, nullptr, 0, 0, 0, -1});
 }
 
 }  // namespace ebr

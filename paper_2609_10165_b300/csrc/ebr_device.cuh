@@ -89,6 +89,22 @@ __host__ __device__ inline void stencil_off(int dim, int k, int o[3]) {
   o[2] = (v >> 2) & 1u;
 }
 
+// Structurally active members (meta bits 15..21 before the grid and tag
+// checks): P_k drops out when its offset runs along an axis on which the
+// normal has no component (zero: bit a set when n_a == 0).
+__host__ __device__ inline uint32_t active_of_zero(int dim, uint32_t zero) {
+  uint32_t act = 0;
+  for (int k = 0; k < stencil_k(dim); ++k) {
+    int o[3];
+    stencil_off(dim, k, o);
+    bool on = true;
+    for (int a = 0; a < dim; ++a)
+      if (o[a] && (zero >> a & 1u)) on = false;
+    if (on) act |= 1u << k;
+  }
+  return act;
+}
+
 // Cell centre along axis a, evaluated without contraction (uniform grids).
 __device__ __forceinline__ double centre_of(const Geom& g, int a, int i) {
   if (g.stretched) return g.cen[a][i];
@@ -411,14 +427,22 @@ __device__ inline void airfoil_closest(double t, double c, double px, double py,
 }
 
 // ---------------------------------------------------------------------------
-// float closest point, used only to decide HGC candidacy away from the
+// float closest point, used to decide HGC candidacy away from the
 // thresholds (a cell whose float decision is within a safety margin of a
-// threshold is decided with the double closest point instead)
+// threshold is decided with the double closest point instead) and the sign
+// and zero pattern of the normal.  *unsure (when given) is set where the
+// normal's signs and zeros may differ from the double closest point's: a
+// component within 1e-3 of zero, a foot point whose position is
+// ill-conditioned (the point within a quarter of the radius of curvature of
+// the evolute, where a perturbation of the input moves the normal by several
+// times itself), a near tie between two branches of the airfoil's closest
+// point (surface or base, upper or lower surface).
 // ---------------------------------------------------------------------------
 __device__ inline float closest_point_f32(const Geom& g, float x, float y, float z, bool solid,
-                                          float n[3]) {
+                                          float n[3], bool* unsure = nullptr) {
   n[0] = n[1] = n[2] = 0.0f;
   float dist = 0.0f;
+  bool ill = false;
   switch (g.kind) {
     case CIRCLE:
     case SPHERE: {
@@ -428,6 +452,7 @@ __device__ inline float closest_point_f32(const Geom& g, float x, float y, float
       float r = 1.0f / fmaxf(rho, 1e-30f);
       dist = fabsf(g.fradii[0] - rho);
       n[0] = dx * r; n[1] = dy * r; n[2] = dz * r;
+      ill = rho < 0.25f * g.fradii[0];
       break;
     }
     case ELLIPSE: {
@@ -435,17 +460,21 @@ __device__ inline float closest_point_f32(const Geom& g, float x, float y, float
       const float p = g.frot[0] * wx + g.frot[3] * wy, q = g.frot[1] * wx + g.frot[4] * wy;
       const float a = g.fradii[0], b = g.fradii[1];
       float a2 = a * a, b2 = b * b, tmin = -fminf(a2, b2), t = 0.0f;
+      bool conv = false;
       for (int it = 0; it < 16; ++it) {
         float rua = 1.0f / (a2 + t), rub = 1.0f / (b2 + t);
         float fx = a * p * rua, fy = b * q * rub;
         float F = fx * fx + fy * fy - 1.0f;
         float dF = -2.0f * (fx * fx * rua + fy * fy * rub);
-        if (F == 0.0f || dF == 0.0f) break;
+        if (F == 0.0f || dF == 0.0f) { conv = true; break; }
         float tn = t - F / dF;
         if (!(tn > tmin)) tn = 0.5f * (t + tmin);
         float dt = fabsf(tn - t);
         t = tn;
-        if (dt <= 1e-5f * fabsf(t)) break;
+        // converged: a step small against t, or against a^2 + t and b^2 + t
+        // (which set the normal; near the boundary t itself is near 0 and the
+        // float rounding of F keeps the steps above 1e-5 |t|)
+        if (dt <= 1e-5f * fabsf(t) || dt <= 1e-6f * fminf(a2 + t, b2 + t)) { conv = true; break; }
       }
       float rua = 1.0f / (a2 + t), rub = 1.0f / (b2 + t);
       float ex = p * t * rua, ey = q * t * rub;
@@ -455,6 +484,8 @@ __device__ inline float closest_point_f32(const Geom& g, float x, float y, float
       float bx = mx * mn, by = my * mn;
       n[0] = g.frot[0] * bx + g.frot[1] * by;
       n[1] = g.frot[3] * bx + g.frot[4] * by;
+      // inside (t < 0) near the evolute a^2 + t or b^2 + t approaches 0
+      ill = !conv || a2 + t < 0.25f * a2 || b2 + t < 0.25f * b2;
       break;
     }
     default: {  // AIRFOIL4
@@ -477,17 +508,24 @@ __device__ inline float closest_point_f32(const Geom& g, float x, float y, float
       airfoil_u32(t, c, hi, xx, yy, dx, dy, ddx, ddy);
       float ghi = (xx - qx) * dx + (yy - qy) * dy;
       float u;
+      bool conv = true;
       if (glo >= 0.0f) u = lo;
       else if (ghi <= 0.0f) u = hi;
       else {
         u = 0.5f * (lo + hi);
+        conv = false;
         for (int it = 0; it < 16; ++it) {
           airfoil_u32(t, c, u, xx, yy, dx, dy, ddx, ddy);
           float gv = (xx - qx) * dx + (yy - qy) * dy;
           float dg = dx * dx + dy * dy + (xx - qx) * ddx + (yy - qy) * ddy;
-          if (gv == 0.0f) break;
-          if (dg > 0.0f && fabsf(gv / dg) <= 1e-5f * fmaxf(u, 1e-3f)) {
+          if (gv == 0.0f) { conv = true; break; }
+          // converged: a step below 1e-5 u, or below 1e-6 (near the leading
+          // edge the float rounding of g keeps the steps above 1e-5 u; the
+          // distance is stationary in u at the foot point, the normal moves
+          // by about |P''| / |P'| times the step)
+          if (dg > 0.0f && fabsf(gv / dg) <= fmaxf(1e-5f * fmaxf(u, 1e-3f), 1e-6f)) {
             u = fminf(fmaxf(u - gv / dg, lo), hi);
+            conv = true;
             break;
           }
           if (gv < 0.0f) lo = u; else hi = u;
@@ -502,6 +540,12 @@ __device__ inline float closest_point_f32(const Geom& g, float x, float y, float
       airfoil_u32(t, c, 1.0f, t1, yte, t2, t3, t4, t5);
       float byy = fminf(qy, yte);
       float d2b = (qx - c) * (qx - c) + (qy - byy) * (qy - byy);
+      // second derivative of the squared distance along the surface, |P'|^2
+      // (1 - d kappa) at the foot point: small near the evolute
+      const float tt = dx * dx + dy * dy;
+      const float dg = tt + (xx - qx) * ddx + (yy - qy) * ddy;
+      ill = !conv || fabsf(qd) <= 1e-4f * c || fabsf(d2b - d2u) <= 1e-2f * (d2b + d2u) ||
+            (!(d2b < d2u) && dg < 0.25f * tt);
       float bx, by;
       if (d2b < d2u) {
         dist = sqrtf(d2b);
@@ -520,6 +564,10 @@ __device__ inline float closest_point_f32(const Geom& g, float x, float y, float
       n[1] = g.frot[3] * bx + g.frot[4] * by;
       break;
     }
+  }
+  if (unsure) {
+    for (int a = 0; a < g.dim; ++a) ill = ill || fabsf(n[a]) < 1e-3f;
+    *unsure = ill;
   }
   return solid ? dist : -dist;
 }

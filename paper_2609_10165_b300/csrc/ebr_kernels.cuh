@@ -116,33 +116,36 @@ void launch_rows(const Geom* G, const int* row_off, int B, int total_rows, int2*
 void launch_iface(const Geom* G, const int* row_off, int B, int total_rows, const int2* runs,
                   int* row_cnt, const int* row_ptr, int* iface_cell, int* iface_geo,
                   int8_t* iface_solid, int write, int iface_cap, int* status, cudaStream_t s, int T = 128);
+// iface_meta (may be null): normal sign / zero bytes of the HGC candidates
 void launch_place(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
-                  const int8_t* iface_solid, int placement, int8_t* tags, double* iface_psi,
-                  double* iface_n, int* status, cudaStream_t s, int T = 128);
+                  const int8_t* iface_solid, int placement, int8_t* tags, uint8_t* iface_meta,
+                  int* status, cudaStream_t s, int T = 128);
 void launch_reclassify(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                        int8_t* tags, int pass, cudaStream_t s);
 // single-pass variants for a classification re-run (sizes known from the
 // plan): interface cells with their row offsets in one launch; ghost flags,
 // offsets and records in one launch (pass_b: HGC reclassification pass B of
-// each cell first); the per-ghost geometry after either
+// each cell first; iface_meta: complete meta words from the placement's
+// normal bytes); the per-ghost geometry after either (split: it leaves the
+// compaction's meta words alone and checks them)
 void launch_iface_fused(const Geom* G, const int* row_off, int B, int total_rows, const int2* runs,
                         int* row_ptr, int* iface_cell, int* iface_geo, int8_t* iface_solid, int iface_cap,
                         const Lookback& L, int* status, cudaStream_t s);
 void launch_ghost_compact(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
-                          int8_t* tags, int pass_b, int* gpos, int ng_cap, int* gs_cell, int* gs_geo,
-                          uint32_t* gs_meta, const Lookback& L, int* status, cudaStream_t s);
+                          int8_t* tags, int pass_b, const uint8_t* iface_meta, int* gpos, int ng_cap,
+                          int* gs_cell, int* gs_geo, uint32_t* gs_meta, const Lookback& L, int* status,
+                          cudaStream_t s);
 void launch_ghost_geom(const Geom* G, int placement, int ng_cap, int* gs_cell, int* gs_geo, double* gs_psi,
-                       double* gs_n, uint32_t* gs_meta, int* rmax, int* status, cudaStream_t s, int T = 128,
-                       const PlanCheck& chk = PlanCheck{nullptr, nullptr, nullptr, 0, 0, 0, -1});
+                       double* gs_n, uint32_t* gs_meta, int split, int* rmax, int* status, cudaStream_t s,
+                       int T = 128, const PlanCheck& chk = PlanCheck{nullptr, nullptr, nullptr, 0, 0, 0, -1});
 // second ghost layer (geometries with layers == 2), after the reclassification
 void launch_layer2(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo, int8_t* tags,
                    int* status, cudaStream_t s);
 void launch_ghost_flags(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
                         const int8_t* tags, int* flags, cudaStream_t s);
 void launch_ghost_write(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
-                        const int8_t* tags, const double* iface_psi, const double* iface_n,
-                        const int* gpos, int placement, int ng_cap, int* gs_cell, int* gs_geo,
-                        double* gs_psi, double* gs_n, uint32_t* gs_meta, int* rmax,
+                        const int8_t* tags, const int* gpos, int placement, int ng_cap, int* gs_cell,
+                        int* gs_geo, double* gs_psi, double* gs_n, uint32_t* gs_meta, int* rmax,
                         int* status, cudaStream_t s, int T = 128);
 
 // ---- scan.cu : exclusive scan of n int32 values into out[0..n]; out[n] = total
@@ -153,8 +156,8 @@ void launch_scan(const int* in, int* out, int n, void* temp, cudaStream_t s);
 void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, const int* pos_of,
                     int* pos_of_cell, int* src_cnt, cudaStream_t s);
 void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, uint32_t* gs_meta,
-                 const double* gs_n, const int8_t* tags, const int* pos_of_cell, int* dep,
-                 int* status, cudaStream_t s, int T = 128);
+                 const int8_t* tags, const int* pos_of_cell, int* dep, int* status, cudaStream_t s,
+                 int T = 128);
 size_t levels_smem(int dim, int n_ghost);
 void launch_levels(const Geom* G, int B, const int* dep, int ng_total, int* level, int* order_pos,
                    int* lev_ptr, int* n_levels, size_t smem, int* status, cudaStream_t s);

@@ -23,39 +23,37 @@ void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, cons
   launch(k_poscell, (ng + 255) / 256, 256, 0, s, G, ng, cell, geo, pos_of, pos_of_cell, src_cnt);
 }
 
-// Stencil members: validate (inside the grid, not tag 1), active mask
-// (n_i != 0 along every offset axis), dependencies on ghost members.  A
-// member tagged +-2 in the caller's tag buffer is a dependency only when it
-// is a ghost of this plan (ghost_slot_of); any other +-2 tag (the buffer was
+// Stencil members: validate (inside the grid, not tag 1), active mask (the
+// structurally active members of the meta word -- n_i != 0 along every offset
+// axis -- that lie in the grid), dependencies on ghost members.  A member
+// tagged +-2 in the caller's tag buffer is a dependency only when it is a
+// ghost of this plan (ghost_slot_of); any other +-2 tag (the buffer was
 // edited after planning) sets EBR_ESHAPE and adds no edge, so no position
 // read from pos_of_cell is used unchecked.
 __global__ void k_deps(const Geom* __restrict__ G, int ng, const int* __restrict__ gs_cell,
                        const int* __restrict__ gs_geo, uint32_t* __restrict__ gs_meta,
-                       const double* __restrict__ gs_n, const int8_t* __restrict__ tags,
-                       const int* __restrict__ pos_of_cell, int* __restrict__ dep, int* status) {
+                       const int8_t* __restrict__ tags, const int* __restrict__ pos_of_cell,
+                       int* __restrict__ dep, int* status) {
   pdl_enter();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ng) return;
   const Geom& g = G[gs_geo[s]];
   int ijk[3];
   cell_ijk3(g, gs_cell[s], ijk);
-  uint32_t m = gs_meta[s] & ~((127u << 15) | (127u << 23));
-  double nv[3] = {gs_n[s], gs_n[ng + s], gs_n[2 * (size_t)ng + s]};
+  const uint32_t m0 = gs_meta[s];
+  const uint32_t pre = meta_active(m0);
+  uint32_t m = m0 & ~((127u << 15) | (127u << 23));
   const int K = stencil_k(g.dim);
   uint32_t active = 0, depm = 0;
   for (int k = 0; k < MAXK; ++k) {
     int d = -1;
     if (k < K) {
-      int mijk[3], o[3];
+      int mijk[3];
       member_ijk(g, ijk, m, k, mijk);
-      stencil_off(g.dim, k, o);
       if (!in_grid(g, mijk)) {
         set_status(status, S_ESTENCIL_OOB);
       } else {
-        bool act = true;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-          if (a < g.dim && o[a] && nv[a] == 0.0) act = false;
+        const bool act = pre >> k & 1u;
         long long mc = g.cell_off + cell_lin(g, mijk);
         int8_t t = tags[mc];
         if (t == 1) set_status(status, S_ESTENCIL_SOLID);
@@ -73,11 +71,9 @@ __global__ void k_deps(const Geom* __restrict__ G, int ng, const int* __restrict
 }
 
 void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, uint32_t* gs_meta,
-                 const double* gs_n, const int8_t* tags, const int* pos_of_cell, int* dep,
-                 int* status, cudaStream_t s, int T) {
+                 const int8_t* tags, const int* pos_of_cell, int* dep, int* status, cudaStream_t s, int T) {
   if (ng <= 0) return;
-  launch(k_deps, (ng + T - 1) / T, T, 0, s, G, ng, gs_cell, gs_geo, gs_meta, gs_n, tags,
-                                          pos_of_cell, dep, status);
+  launch(k_deps, (ng + T - 1) / T, T, 0, s, G, ng, gs_cell, gs_geo, gs_meta, tags, pos_of_cell, dep, status);
 }
 
 // One CTA per geometry, integer arithmetic only.  Geometries whose arrays fit
@@ -93,6 +89,7 @@ void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, u
 // pass per chunk (warps in order, __match_any_sync within a warp), else one
 // block scan per level.
 constexpr int LV_T = 1024;
+constexpr int LV_W = LV_T / 32;  // warps per CTA
 constexpr int LV_NL = 64;        // levels ranked with per-warp counts (more: warp by warp)
 
 // shared-memory ints of the fast path: levels, local dependencies [K][n],
@@ -112,7 +109,7 @@ __global__ void __launch_bounds__(LV_T, 2) k_levels(const Geom* __restrict__ G, 
   extern __shared__ int sm[];
   __shared__ int sh_cnt3[3];
   __shared__ int sh_warp[32];
-  __shared__ int sh_wl[LV_T / 32][LV_NL];     // per-warp counts of each level (ranking)
+  __shared__ int sh_wl[LV_W][LV_NL];          // per-warp counts of each level (ranking)
   __shared__ int sh_tot[LV_NL];               // chunk total of each level
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
@@ -177,13 +174,13 @@ __global__ void __launch_bounds__(LV_T, 2) k_levels(const Geom* __restrict__ G, 
         if (lane == 31) sh_warp[w] = x;
         __syncthreads();
         if (w == 0) {
-          int v = sh_warp[lane];
+          int v = lane < LV_W ? sh_warp[lane] : 0;
 #pragma unroll
           for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, v, o);
             if (lane >= o) v += y;
           }
-          sh_warp[lane] = v;
+          if (lane < LV_W) sh_warp[lane] = v;
         }
         __syncthreads();
         int ex = (w > 0 ? sh_warp[w - 1] : 0) + x - loc;
@@ -192,7 +189,7 @@ __global__ void __launch_bounds__(LV_T, 2) k_levels(const Geom* __restrict__ G, 
           cptr[q] = ex;
           ex += c;
         }
-        if (threadIdx.x == LV_T - 1) cptr[n] = sh_warp[31];
+        if (threadIdx.x == LV_T - 1) cptr[n] = sh_warp[LV_W - 1];
         __syncthreads();
       }
       for (int q = threadIdx.x; q < n; q += LV_T) fr1[q] = cptr[q];
@@ -347,18 +344,18 @@ __global__ void __launch_bounds__(LV_T, 2) k_levels(const Geom* __restrict__ G, 
           if (lane == 0) sh_warp[w] = __popc(bal);
           __syncthreads();
           if (w == 0) {
-            int v = sh_warp[lane];
+            int v = lane < LV_W ? sh_warp[lane] : 0;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
               int y = __shfl_up_sync(0xffffffffu, v, o);
               if (lane >= o) v += y;
             }
-            sh_warp[lane] = v;
+            if (lane < LV_W) sh_warp[lane] = v;
           }
           __syncthreads();
           int before = (w > 0 ? sh_warp[w - 1] : 0);
           if (f) order_pos[g0 + s] = carry + before + inwarp;
-          int tot = sh_warp[31];
+          int tot = sh_warp[LV_W - 1];
           __syncthreads();
           carry += tot;
         }

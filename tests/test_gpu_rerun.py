@@ -1,6 +1,7 @@
 """A re-run of the classification and the levels on a planned, levelled
-context (ebr_classify + ebr_build_levels: the single-pass compactions of the
-interface cells, the ghosts and the ghost targets' sources) gives exactly
+context (ebr_classify + ebr_build_levels, and the fused ebr_classify_levels:
+the single-pass compactions of the interface cells, the ghosts and the ghost
+targets' sources; the closest points beside the levels) gives exactly
 what the plan gave: tags, ghost records and levels bitwise, the same source
 count, and the adjoint (which walks the source lists in their order) bitwise;
 and the re-run's structure matches the oracle.  Every placement, both layer
@@ -56,9 +57,12 @@ def test_rerun_equals_plan(which, placement, layers):
     info0 = run.R.ghost_info()
     n_gsrc0 = run.R.diagnostics()["n_gsrc"]
     adj0 = _adjoint(run, geoms)
-    for _ in range(3):
-        run.R.classify()
-        run.R.build_levels()
+    # the two calls, then the fused call (for one-layer HGC the closest
+    # points overlap the levels there)
+    run.R.classify()
+    run.R.build_levels()
+    for _ in range(2):
+        run.R.classify_levels()
     run.R.sync_status()
     assert torch.equal(run.R.tags, tags0)
     info1 = run.R.ghost_info()
