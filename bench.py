@@ -559,34 +559,34 @@ def kernel_source_hash(kernel):
 # write-back hides most writes of a short kernel).  A figure whose hash no
 # longer matches the source is reported as null, with the reason.
 TRAFFIC_PER_LAUNCH = {
-    "rows": (0.88e6, "24ebace65ebb6311"),
-    "iface": (1.25e6, "24ebace65ebb6311"),
-    "place": (1.77e6, "24ebace65ebb6311"),
-    "reclassify": (7.40e6, "24ebace65ebb6311"),
-    "ghost_compact": (7.36e6, "24ebace65ebb6311"),
-    "ghost_geom": (1.28e6, "24ebace65ebb6311"),
-    "poscell": (0.80e6, "fa0a8eb5e01b2102"),
-    "deps": (13.17e6, "fa0a8eb5e01b2102"),
-    "levels": (1.13e6, "fa0a8eb5e01b2102"),
-    "reorder": (7.29e6, "fa0a8eb5e01b2102"),
-    "tables": (9.87e6, "fa0a8eb5e01b2102"),
-    "gsrc": (3.44e6, "fa0a8eb5e01b2102"),
-    "fill_part": (27.85e6, "c3872033bc21d552"),
-    "fill_chain": (6.16e6, "c3872033bc21d552"),
-    "forces": (32.55e6, "c64d33658b142d14"),
-    "adj_seed": (10.62e6, "001f2684c5abf787"),
-    "adj_part": (4.52e6, "001f2684c5abf787"),
-    "adj_chain": (3.13e6, "001f2684c5abf787"),
-    "adj_probe": (14.01e6, "001f2684c5abf787"),
-    "adj_fluid": (20.95e6, "001f2684c5abf787"),
-    "adj_bc": (6.12e6, "001f2684c5abf787"),
+    "rows": (0.82e6, "f08188e63c229518"),
+    "iface": (1.61e6, "f08188e63c229518"),
+    "place": (2.92e6, "f08188e63c229518"),
+    "reclassify": (7.40e6, "f08188e63c229518"),
+    "ghost_compact": (7.57e6, "f08188e63c229518"),
+    "ghost_geom": (1.28e6, "f08188e63c229518"),
+    "poscell": (0.80e6, "2779aaff33f0290c"),
+    "deps": (11.11e6, "2779aaff33f0290c"),
+    "levels": (1.13e6, "2779aaff33f0290c"),
+    "reorder": (7.46e6, "2779aaff33f0290c"),
+    "tables": (9.88e6, "2779aaff33f0290c"),
+    "gsrc": (3.44e6, "2779aaff33f0290c"),
+    "fill_part": (25.41e6, "3f255953449244f9"),
+    "fill_chain": (5.66e6, "3f255953449244f9"),
+    "forces": (28.10e6, "aa850d82ac7ea977"),
+    "adj_seed": (6.17e6, "f02b50541c911a5c"),
+    "adj_part": (4.00e6, "f02b50541c911a5c"),
+    "adj_chain": (3.13e6, "f02b50541c911a5c"),
+    "adj_probe": (13.96e6, "f02b50541c911a5c"),
+    "adj_fluid": (19.21e6, "f02b50541c911a5c"),
+    "adj_bc": (5.44e6, "f02b50541c911a5c"),
 }
 
 # FP64 flops per launch (DADD + DMUL + 2 x DFMA thread instructions from one
 # ncu capture on this workload) of the kernels bound by the FP64 pipe, with
 # the source hash of the captured version.
 FP64_FLOPS_PER_LAUNCH = {
-    "ghost_geom": (11_876_551, "24ebace65ebb6311"), "tables": (10_419_154, "fa0a8eb5e01b2102"),
+    "ghost_geom": (11_920_293, "f08188e63c229518"), "tables": (10_419_154, "2779aaff33f0290c"),
 }
 
 
