@@ -5,7 +5,8 @@ targets' sources; the closest points beside the levels) gives exactly
 what the plan gave: tags, ghost records and levels bitwise, the same source
 count, and the adjoint (which walks the source lists in their order) bitwise;
 and the re-run's structure matches the oracle.  Every placement, both layer
-counts, a batch of uneven 2D grids and a 3D sphere."""
+counts, a batch of uneven 2D grids, a 3D sphere, bodies centred on odd grids
+(normal components exactly zero) and stretched grids."""
 
 import numpy as np
 import pytest
@@ -40,8 +41,29 @@ def _adjoint(run, geoms):
     return [t.cpu().numpy() for t in gf + gb]
 
 
+def _fields(g, seed):
+    d = g["grid"]["dim"]
+    g.update({"fields": [I.FourierField(d, 4, g["grid"]["lo"], g["grid"]["hi"], seed + f) for f in range(d + 1)],
+              "bc": [I.DIRICHLET] * d + [I.NEUMANN], "roles": {"p": d, "vel": list(range(d))}, "mu": 0.01})
+    return g
+
+
+def _axis_aligned():
+    # odd grids centred on the bodies: cell centres on the bodies' axes, where
+    # normal components are exactly zero (structurally inactive members)
+    return [_fields({"grid": I.grid(2, [41, 41], [-1.0, -1.0], [1.0, 1.0]), "body": I.circle(0.0, 0.0, 0.5)}, 960),
+            _fields({"grid": I.grid(2, [45, 31], [-1.5, -1.0], [1.5, 1.0]),
+                     "body": I.ellipse(0.0, 0.0, 0.83, 0.47, 0.0)}, 970)]
+
+
+def _stretched():
+    from tests.test_oracle_stretched import CASES as SC
+    return [_fields({"grid": gd, "body": bd}, 980 + 10 * k) for k, (gd, bd) in enumerate(SC[:2])]
+
+
 CASES = [("batch", "HGC", 1), ("batch", "CGC", 1), ("batch", "CGC_ES", 1), ("batch", "HGC", 2),
-         ("sphere", "HGC", 1), ("sphere", "CGC_ES", 1), ("sphere", "HGC", 2)]
+         ("sphere", "HGC", 1), ("sphere", "CGC_ES", 1), ("sphere", "HGC", 2),
+         ("axis_aligned", "HGC", 1), ("stretched", "HGC", 1), ("stretched", "CGC_ES", 1)]
 
 
 @pytest.mark.parametrize("which,placement,layers", CASES)
@@ -50,6 +72,10 @@ def test_rerun_equals_plan(which, placement, layers):
         # the smaller grids of the batch (ellipses and airfoils), so that the
         # oracle's structure finishes in seconds
         geoms = [g for g in I.batch(64) if int(np.prod(g["grid"]["n"])) <= 160_000][:12]
+    elif which == "axis_aligned":
+        geoms = _axis_aligned()
+    elif which == "stretched":
+        geoms = _stretched()
     else:
         geoms = [_sphere()]
     run = DeviceRun(geoms, placement, dtype=torch.float32, layers=layers)
