@@ -226,8 +226,12 @@ ebr_status ebr_build_levels(void* ctx, ebr_stream stream);
  * points (psi, S, n; Eq. signed_distance) are evaluated; those then run on
  * the library's second stream beside the dependency levels and join before
  * the canonical reorder, and check the recorded signs (a difference sets
- * EBR_EINVAL in the device status).  Other placements run the two steps one
- * after the other.  The call is ordered on `stream` like the two calls. */
+ * EBR_EINVAL in the device status).  Both reclassification passes are then
+ * decided by the ghost compaction from the placement's tags (pass A of a
+ * neighbour evaluated where pass B needs it), and the final tags of the
+ * interface cells reach d_tags with the ghost positions, inside this call.
+ * Other placements run the two steps one after the other.  The call is
+ * ordered on `stream` like the two calls. */
 ebr_status ebr_classify_levels(void* ctx, int8_t* d_tags, ebr_stream stream);
 
 /* Ghost records in canonical order, copied to host arrays sized by the total

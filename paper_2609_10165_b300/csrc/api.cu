@@ -104,6 +104,8 @@ struct Ctx {
   int* iface_geo = nullptr;
   int8_t* iface_solid = nullptr;
   uint8_t* iface_meta = nullptr;   // normal sign / zero bytes of the HGC candidates
+  int8_t* iface_tag = nullptr;     // final tags of a fused re-run, written by the position kernel
+  bool tags_pending = false;       // iface_tag holds tags not yet in the tag array
   int* gflag = nullptr;
   int* gpos = nullptr;
   void* scan_tmp = nullptr;
@@ -452,6 +454,7 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning, b
     AL(c->iface_geo, ni);
     AL(c->iface_solid, ni);
     AL(c->iface_meta, ni);
+    AL(c->iface_tag, ni);
     AL(c->gflag, ni);
     AL(c->gpos, ni + 1);
     prof_begin(c, s, "iface");
@@ -476,11 +479,15 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning, b
                d_tags, split ? c->iface_meta : nullptr, c->d_status, s, c->tb[TU_PLACE]);
   prof_end(c, s);
   c->launches += 1;
+  c->tags_pending = false;
   if (c->placement == EBR_HGC) {
-    prof_begin(c, s, "reclassify");
-    launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 0, s);
-    prof_end(c, s);
-    c->launches += 1;
+    // the fused re-run decides both passes in the compaction (split below)
+    if (!split) {
+      prof_begin(c, s, "reclassify");
+      launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 0, s);
+      prof_end(c, s);
+      c->launches += 1;
+    }
     if (!fuse_b) {
       prof_begin(c, s, "reclassify");
       launch_reclassify(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, 1, s);
@@ -496,10 +503,13 @@ ebr_status run_classify(Ctx* c, int8_t* d_tags, cudaStream_t s, bool planning, b
   }
   if (!planning) {
     prof_begin(c, s, "ghost_compact");
-    launch_ghost_compact(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, fuse_b ? 1 : 0,
-                         split ? c->iface_meta : nullptr, c->gpos, c->ng, c->gs_cell, c->gs_geo, c->gs_meta,
-                         c->lb_iface, c->d_status, s);
+    launch_ghost_compact(c->dG, c->n_iface, c->iface_cell, c->iface_geo, d_tags, split ? 2 : (fuse_b ? 1 : 0),
+                         split ? c->iface_meta : nullptr, c->iface_tag, c->gpos, c->ng, c->gs_cell, c->gs_geo,
+                         c->gs_meta, c->lb_iface, c->d_status, s);
     prof_end(c, s);
+    // the final tags of the interface cells reach the tag array with the
+    // positions (the next launch of run_levels)
+    c->tags_pending = split;
     // the offsets against the plan: block 0 of the closest-point kernel
     cudaStream_t sg = s;
     if (split) {
@@ -615,7 +625,9 @@ ebr_status run_levels(Ctx* c, cudaStream_t s, bool planning) {
     }
   }
   prof_begin(c, s, "poscell");
-  launch_poscell(c->dG, ng, c->gs_cell, c->gs_geo, nullptr, c->pos_of_cell, c->gsrc_cnt, s);
+  launch_poscell(c->dG, ng, c->gs_cell, c->gs_geo, nullptr, c->pos_of_cell, c->gsrc_cnt, s, c->n_iface,
+                 c->iface_cell, c->iface_geo, c->tags_pending ? c->iface_tag : nullptr, c->tags);
+  c->tags_pending = false;
   prof_end(c, s);
   prof_begin(c, s, "deps");
   launch_deps(c->dG, ng, c->gs_cell, c->gs_geo, c->gs_meta, c->tags, c->pos_of_cell,

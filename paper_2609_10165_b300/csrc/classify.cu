@@ -1183,11 +1183,39 @@ __global__ void k_ghost_write(const Geom* __restrict__ G, int n_iface, const int
 // With iface_meta (one-layer HGC) the meta word of a ghost is complete here:
 // normal signs and structurally active members from the placement's normal
 // bytes, r = 1 on every axis; the closest points then only supply psi, S, n.
+// After pass A, is a face neighbour of `cell` tagged 0?  From the tags of the
+// placement: a neighbour tagged 0, or tagged -2 without a tag-1 face
+// neighbour (which pass A turns into 0).
+__device__ inline bool zero_after_pass_a(const Geom& g, const int8_t* tg, int cell) {
+  int i, j, k;
+  cell_ijk(g, cell, i, j, k);
+  const int ijk[3] = {i, j, k};
+  const int stride[3] = {1, g.n[0], g.n[0] * g.n[1]};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.dim) continue;
+#pragma unroll
+    for (int sd = -1; sd <= 1; sd += 2) {
+      const int ia = ijk[a] + sd;
+      if (ia < 0 || ia >= g.n[a]) continue;
+      const int nb = cell + sd * stride[a];
+      const int8_t v = tg[nb];
+      if (v == 0 || (v == -2 && !has_face_tag(g, tg, nb, 1))) return true;
+    }
+  }
+  return false;
+}
+
+// pass: 0 none, 1 reclassification pass B of each cell first (in place), 2
+// passes A and B both, decided from the placement's tags (nothing written to
+// the tag array; the final tag of every interface cell goes to iface_tag,
+// for the position kernel to write).
 __global__ void k_ghost_compact(const Geom* __restrict__ G, int n_iface, const int* __restrict__ iface_cell,
-                                const int* __restrict__ iface_geo, int8_t* __restrict__ tags, int pass_b,
-                                const uint8_t* __restrict__ iface_meta, int* __restrict__ gpos, int cap,
-                                int* __restrict__ gs_cell, int* __restrict__ gs_geo,
-                                uint32_t* __restrict__ gs_meta, const Lookback L, int* status) {
+                                const int* __restrict__ iface_geo, int8_t* __restrict__ tags, int pass,
+                                const uint8_t* __restrict__ iface_meta, int8_t* __restrict__ iface_tag,
+                                int* __restrict__ gpos, int cap, int* __restrict__ gs_cell,
+                                int* __restrict__ gs_geo, uint32_t* __restrict__ gs_meta, const Lookback L,
+                                int* status) {
   pdl_enter();
   __shared__ int sh[32];
   const LbBlock blk = lb_begin(L);
@@ -1203,9 +1231,13 @@ __global__ void k_ghost_compact(const Geom* __restrict__ G, int n_iface, const i
     if (iface_meta) mb = iface_meta[m];     // loaded before the scan's waits
     int8_t* tg = tags + g.cell_off;
     t = tg[cell];
-    if (pass_b && t == 2 && !has_face_tag(g, tg, cell, 0)) {
+    if (pass == 1 && t == 2 && !has_face_tag(g, tg, cell, 0)) {
       t = 1;
       tg[cell] = 1;
+    } else if (pass == 2) {
+      if (t == -2 && !has_face_tag(g, tg, cell, 1)) t = 0;
+      else if (t == 2 && !zero_after_pass_a(g, tg, cell)) t = 1;
+      iface_tag[m] = t;
     }
   }
   const int flag = (t == 2 || t == -2) ? 1 : 0;
@@ -1303,12 +1335,12 @@ __global__ void k_ghost_geom(const Geom* __restrict__ G, int ng, int placement,
 }
 
 void launch_ghost_compact(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
-                          int8_t* tags, int pass_b, const uint8_t* iface_meta, int* gpos, int ng_cap,
-                          int* gs_cell, int* gs_geo, uint32_t* gs_meta, const Lookback& L, int* status,
-                          cudaStream_t s) {
+                          int8_t* tags, int pass, const uint8_t* iface_meta, int8_t* iface_tag, int* gpos,
+                          int ng_cap, int* gs_cell, int* gs_geo, uint32_t* gs_meta, const Lookback& L,
+                          int* status, cudaStream_t s) {
   if (n_iface <= 0) return;
   launch(k_ghost_compact, (n_iface + LB_T - 1) / LB_T, LB_T, 0, s, G, n_iface, iface_cell, iface_geo, tags,
-         pass_b, iface_meta, gpos, ng_cap, gs_cell, gs_geo, gs_meta, L, status);
+         pass, iface_meta, iface_tag, gpos, ng_cap, gs_cell, gs_geo, gs_meta, L, status);
 }
 
 // psi, S, n and (split == 0) the meta words of the compacted ghosts

@@ -124,17 +124,18 @@ void launch_reclassify(const Geom* G, int n_iface, const int* iface_cell, const 
                        int8_t* tags, int pass, cudaStream_t s);
 // single-pass variants for a classification re-run (sizes known from the
 // plan): interface cells with their row offsets in one launch; ghost flags,
-// offsets and records in one launch (pass_b: HGC reclassification pass B of
-// each cell first; iface_meta: complete meta words from the placement's
-// normal bytes); the per-ghost geometry after either (split: it leaves the
-// compaction's meta words alone and checks them)
+// offsets and records in one launch (pass 1: HGC reclassification pass B of
+// each cell first, in place; pass 2: passes A and B both from the placement's
+// tags, the final tags to iface_tag; iface_meta: complete meta words from the
+// placement's normal bytes); the per-ghost geometry after either (split: it
+// leaves the compaction's meta words alone and checks them)
 void launch_iface_fused(const Geom* G, const int* row_off, int B, int total_rows, const int2* runs,
                         int* row_ptr, int* iface_cell, int* iface_geo, int8_t* iface_solid, int iface_cap,
                         const Lookback& L, int* status, cudaStream_t s);
 void launch_ghost_compact(const Geom* G, int n_iface, const int* iface_cell, const int* iface_geo,
-                          int8_t* tags, int pass_b, const uint8_t* iface_meta, int* gpos, int ng_cap,
-                          int* gs_cell, int* gs_geo, uint32_t* gs_meta, const Lookback& L, int* status,
-                          cudaStream_t s);
+                          int8_t* tags, int pass, const uint8_t* iface_meta, int8_t* iface_tag, int* gpos,
+                          int ng_cap, int* gs_cell, int* gs_geo, uint32_t* gs_meta, const Lookback& L,
+                          int* status, cudaStream_t s);
 void launch_ghost_geom(const Geom* G, int placement, int ng_cap, int* gs_cell, int* gs_geo, double* gs_psi,
                        double* gs_n, uint32_t* gs_meta, int split, int* rmax, int* status, cudaStream_t s,
                        int T = 128, const PlanCheck& chk = PlanCheck{nullptr, nullptr, nullptr, 0, 0, 0, -1});
@@ -153,8 +154,12 @@ size_t scan_temp_bytes(int n);
 void launch_scan(const int* in, int* out, int n, void* temp, cudaStream_t s);
 
 // ---- levels.cu
+// (iface_tag non-null: also the final tags of the n_iface interface cells,
+// decided by a compaction with pass 2, written to tags)
 void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, const int* pos_of,
-                    int* pos_of_cell, int* src_cnt, cudaStream_t s);
+                    int* pos_of_cell, int* src_cnt, cudaStream_t s, int n_iface = 0,
+                    const int* iface_cell = nullptr, const int* iface_geo = nullptr,
+                    const int8_t* iface_tag = nullptr, int8_t* tags = nullptr);
 void launch_deps(const Geom* G, int ng, const int* gs_cell, const int* gs_geo, uint32_t* gs_meta,
                  const int8_t* tags, const int* pos_of_cell, int* dep, int* status, cudaStream_t s,
                  int T = 128);

@@ -6,21 +6,29 @@
 namespace ebr {
 
 // position of every ghost cell in the ghost arrays; src_cnt (optional): the
-// ghost-source counts set to 1 (each ghost is its own first source)
+// ghost-source counts set to 1 (each ghost is its own first source);
+// iface_tag (optional): the final tag of every interface cell, written to the
+// tag array
 __global__ void k_poscell(const Geom* __restrict__ G, int ng, const int* __restrict__ cell,
                           const int* __restrict__ geo, const int* __restrict__ pos_of,
-                          int* __restrict__ pos_of_cell, int* __restrict__ src_cnt) {
+                          int* __restrict__ pos_of_cell, int* __restrict__ src_cnt, int n_iface,
+                          const int* __restrict__ iface_cell, const int* __restrict__ iface_geo,
+                          const int8_t* __restrict__ iface_tag, int8_t* __restrict__ tags) {
   pdl_enter();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (iface_tag && s < n_iface) tags[G[iface_geo[s]].cell_off + iface_cell[s]] = iface_tag[s];
   if (s >= ng) return;
   pos_of_cell[G[geo[s]].cell_off + cell[s]] = pos_of ? pos_of[s] : s;
   if (src_cnt) src_cnt[s] = 1;
 }
 
 void launch_poscell(const Geom* G, int ng, const int* cell, const int* geo, const int* pos_of,
-                    int* pos_of_cell, int* src_cnt, cudaStream_t s) {
-  if (ng <= 0) return;
-  launch(k_poscell, (ng + 255) / 256, 256, 0, s, G, ng, cell, geo, pos_of, pos_of_cell, src_cnt);
+                    int* pos_of_cell, int* src_cnt, cudaStream_t s, int n_iface, const int* iface_cell,
+                    const int* iface_geo, const int8_t* iface_tag, int8_t* tags) {
+  const int n = std::max(ng, iface_tag ? n_iface : 0);
+  if (n <= 0) return;
+  launch(k_poscell, (n + 255) / 256, 256, 0, s, G, ng, cell, geo, pos_of, pos_of_cell, src_cnt, n_iface,
+         iface_cell, iface_geo, iface_tag, tags);
 }
 
 // Stencil members: validate (inside the grid, not tag 1), active mask (the
