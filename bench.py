@@ -484,15 +484,18 @@ def algorithmic_bytes(n_cells, rows, ni, ng, n_gsrc, F, dim=2):
         "iface": rows * (8 + 4) + ni * 9,                        # runs, offsets; cell, geo, side
         "place": ni * 10,                                        # interface record + tag
         "reclassify": ni * 9,                                    # pass A over the interface
-        # pass B, flags, offsets and ghost records: interface record, tag,
-        # offset; per ghost cell, geometry, meta
-        "ghost_compact": ni * 13 + ng * 12,
+        # passes A and B (a step's fused re-run), flags, offsets and ghost
+        # records: interface record, tag, normal byte, final tag, offset; per
+        # ghost cell, geometry, meta
+        "ghost_compact": ni * 15 + ng * 12,
         "ghost_geom": ng * (12 + 8 + 8 * dim + 4),               # record in; psi, n, meta out
         # the planning path's separate kernels (counts, scans, compaction)
         "scan": 8 * (rows + ni + ng),
         "ghost_flags": ni * 13,
         "ghost_write": ni * 13 + ng * (12 + 12 + 8 + 8 * dim + 4),
-        "poscell": 2 * ng * 12,
+        # positions and preset counts; a step's fused re-run also writes the
+        # final tags of the interface cells (record, final tag in, tag out)
+        "poscell": 2 * ng * 12 + ni * 10,
         "deps": ng * (12 + 8 * dim + K + 4 * K + 4 * K + 4),
         "levels": ng * (4 * K + 12),
         "reorder": ng * 2 * (4 + 4 + 8 + 8 * dim + 4 + 4 * K + 4),
@@ -559,34 +562,34 @@ def kernel_source_hash(kernel):
 # write-back hides most writes of a short kernel).  A figure whose hash no
 # longer matches the source is reported as null, with the reason.
 TRAFFIC_PER_LAUNCH = {
-    "rows": (0.82e6, "f08188e63c229518"),
-    "iface": (1.61e6, "f08188e63c229518"),
-    "place": (2.92e6, "f08188e63c229518"),
-    "reclassify": (7.40e6, "f08188e63c229518"),
-    "ghost_compact": (7.57e6, "f08188e63c229518"),
-    "ghost_geom": (1.28e6, "f08188e63c229518"),
-    "poscell": (0.80e6, "2779aaff33f0290c"),
-    "deps": (11.11e6, "2779aaff33f0290c"),
-    "levels": (1.13e6, "2779aaff33f0290c"),
-    "reorder": (7.46e6, "2779aaff33f0290c"),
-    "tables": (9.88e6, "2779aaff33f0290c"),
-    "gsrc": (3.44e6, "2779aaff33f0290c"),
-    "fill_part": (25.41e6, "3f255953449244f9"),
-    "fill_chain": (5.66e6, "3f255953449244f9"),
-    "forces": (28.10e6, "aa850d82ac7ea977"),
-    "adj_seed": (6.17e6, "f02b50541c911a5c"),
-    "adj_part": (4.00e6, "f02b50541c911a5c"),
-    "adj_chain": (3.13e6, "f02b50541c911a5c"),
-    "adj_probe": (13.96e6, "f02b50541c911a5c"),
-    "adj_fluid": (19.21e6, "f02b50541c911a5c"),
-    "adj_bc": (5.44e6, "f02b50541c911a5c"),
+    "rows": (0.81e6, "478e26ce0c77a842"),
+    "iface": (1.61e6, "478e26ce0c77a842"),
+    "place": (2.92e6, "478e26ce0c77a842"),
+    "reclassify": (7.38e6, "478e26ce0c77a842"),
+    "ghost_compact": (7.65e6, "478e26ce0c77a842"),
+    "ghost_geom": (1.28e6, "478e26ce0c77a842"),
+    "poscell": (2.87e6, "18552c01f4b1666b"),
+    "deps": (11.11e6, "18552c01f4b1666b"),
+    "levels": (1.13e6, "18552c01f4b1666b"),
+    "reorder": (7.44e6, "18552c01f4b1666b"),
+    "tables": (9.88e6, "18552c01f4b1666b"),
+    "gsrc": (3.44e6, "18552c01f4b1666b"),
+    "fill_part": (25.41e6, "f1719b13f009c807"),
+    "fill_chain": (5.64e6, "f1719b13f009c807"),
+    "forces": (28.10e6, "a9750440223f0be2"),
+    "adj_seed": (6.17e6, "9cc1332683806213"),
+    "adj_part": (4.00e6, "9cc1332683806213"),
+    "adj_chain": (3.13e6, "9cc1332683806213"),
+    "adj_probe": (13.96e6, "9cc1332683806213"),
+    "adj_fluid": (19.21e6, "9cc1332683806213"),
+    "adj_bc": (5.46e6, "9cc1332683806213"),
 }
 
 # FP64 flops per launch (DADD + DMUL + 2 x DFMA thread instructions from one
 # ncu capture on this workload) of the kernels bound by the FP64 pipe, with
 # the source hash of the captured version.
 FP64_FLOPS_PER_LAUNCH = {
-    "ghost_geom": (11_920_293, "f08188e63c229518"), "tables": (10_419_154, "2779aaff33f0290c"),
+    "ghost_geom": (11_920_293, "478e26ce0c77a842"), "tables": (10_419_154, "18552c01f4b1666b"),
 }
 
 
