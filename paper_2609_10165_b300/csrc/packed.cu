@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(PK_T) k_pa_grid(T* __restrict__ cot, T* __rest
 }
 
 // tail chain, adjoint: levels n..L0+1 of one geometry per CTA (at most
-// PACKED_TAIL_MAX_ADJ ghosts per level: at most two per warp, all fields);
+// PACKED_TAIL_MAX_ADJ ghosts per level: at most one per warp, all fields);
 // each warp loads the record of its ghost of the next level before the
 // level barrier, so only the lambda rows wait on memory inside a level
 template <typename T>
