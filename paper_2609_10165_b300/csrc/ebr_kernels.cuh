@@ -290,12 +290,12 @@ cudaError_t launch_tiled_fill(int dtype, int dim, int F, void* const* fields, co
 // d_lvl[h_lvl_off[l - 1] .. h_lvl_off[l]); the levels above (at most
 // PACKED_TAIL_MAX, resp. PACKED_TAIL_MAX_ADJ, ghosts per geometry and level)
 // run in one CTA per geometry of d_tail (d_tail_a).
-// (measured on the 256-geometry batch with 192 fields: forward 24 / transpose
-// 16 against 128 / 128 took the overlapped step from 0.285 to 0.258 ms --
-// more levels as grid-wide launches, shorter shared-memory tails with fewer
-// waves of tail CTAs)
+// (measured on the 256-geometry batch with 192 fields, with 256-thread tail
+// CTAs: forward 64 / transpose 16 against 128 / 128 with 512-thread CTAs
+// took the overlapped step from 0.285 to 0.246 ms -- more levels as
+// grid-wide launches, shorter shared-memory tails, more tail CTAs per SM)
 #ifndef EBR_PACKED_TAIL_MAX
-#define EBR_PACKED_TAIL_MAX 24
+#define EBR_PACKED_TAIL_MAX 64
 #endif
 #ifndef EBR_PACKED_TAIL_MAX_ADJ
 #define EBR_PACKED_TAIL_MAX_ADJ 16

@@ -36,7 +36,10 @@
 namespace ebr {
 
 constexpr int PK_T = 256;        // grid-wide kernels: 8 warps per CTA
-constexpr int PK_CT = 512;       // shared-memory tail kernels: 16 warps per CTA, two per SM
+#ifndef EBR_PK_CT
+#define EBR_PK_CT 256
+#endif
+constexpr int PK_CT = EBR_PK_CT;  // shared-memory tail kernels: 8 warps per CTA
 constexpr int PK_CA = 512;       // adjoint tail: 16 warps per CTA, two CTAs per SM
 constexpr int PK_G = 4;          // 32-field chunks per warp pass (128 fields)
 constexpr int CI = 4;            // inline source entries per record
