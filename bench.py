@@ -562,34 +562,34 @@ def kernel_source_hash(kernel):
 # write-back hides most writes of a short kernel).  A figure whose hash no
 # longer matches the source is reported as null, with the reason.
 TRAFFIC_PER_LAUNCH = {
-    "rows": (0.81e6, "478e26ce0c77a842"),
-    "iface": (1.61e6, "478e26ce0c77a842"),
-    "place": (2.92e6, "478e26ce0c77a842"),
-    "reclassify": (7.38e6, "478e26ce0c77a842"),
-    "ghost_compact": (7.65e6, "478e26ce0c77a842"),
-    "ghost_geom": (1.28e6, "478e26ce0c77a842"),
-    "poscell": (2.87e6, "18552c01f4b1666b"),
-    "deps": (11.11e6, "18552c01f4b1666b"),
-    "levels": (1.13e6, "18552c01f4b1666b"),
-    "reorder": (7.44e6, "18552c01f4b1666b"),
-    "tables": (9.88e6, "18552c01f4b1666b"),
-    "gsrc": (3.44e6, "18552c01f4b1666b"),
-    "fill_part": (25.41e6, "f1719b13f009c807"),
-    "fill_chain": (5.64e6, "f1719b13f009c807"),
-    "forces": (28.10e6, "a9750440223f0be2"),
-    "adj_seed": (6.17e6, "9cc1332683806213"),
-    "adj_part": (4.00e6, "9cc1332683806213"),
-    "adj_chain": (3.13e6, "9cc1332683806213"),
-    "adj_probe": (13.96e6, "9cc1332683806213"),
-    "adj_fluid": (19.21e6, "9cc1332683806213"),
-    "adj_bc": (5.46e6, "9cc1332683806213"),
+    "rows": (0.82e6, "fd3f4e6fc115cb04"),
+    "iface": (1.62e6, "fd3f4e6fc115cb04"),
+    "place": (2.92e6, "fd3f4e6fc115cb04"),
+    "reclassify": (7.38e6, "fd3f4e6fc115cb04"),
+    "ghost_compact": (7.65e6, "fd3f4e6fc115cb04"),
+    "ghost_geom": (1.28e6, "fd3f4e6fc115cb04"),
+    "poscell": (2.87e6, "123c8594a95264bf"),
+    "deps": (11.11e6, "123c8594a95264bf"),
+    "levels": (1.13e6, "123c8594a95264bf"),
+    "reorder": (7.45e6, "123c8594a95264bf"),
+    "tables": (9.88e6, "123c8594a95264bf"),
+    "gsrc": (3.43e6, "123c8594a95264bf"),
+    "fill_part": (25.41e6, "c73c35a163a29288"),
+    "fill_chain": (5.66e6, "c73c35a163a29288"),
+    "forces": (28.10e6, "983ee207011997bd"),
+    "adj_seed": (6.17e6, "e86c2f12d673d229"),
+    "adj_part": (4.00e6, "e86c2f12d673d229"),
+    "adj_chain": (3.13e6, "e86c2f12d673d229"),
+    "adj_probe": (13.96e6, "e86c2f12d673d229"),
+    "adj_fluid": (19.21e6, "e86c2f12d673d229"),
+    "adj_bc": (5.44e6, "e86c2f12d673d229"),
 }
 
 # FP64 flops per launch (DADD + DMUL + 2 x DFMA thread instructions from one
 # ncu capture on this workload) of the kernels bound by the FP64 pipe, with
 # the source hash of the captured version.
 FP64_FLOPS_PER_LAUNCH = {
-    "ghost_geom": (11_920_293, "478e26ce0c77a842"), "tables": (10_419_154, "18552c01f4b1666b"),
+    "ghost_geom": (11_920_293, "fd3f4e6fc115cb04"), "tables": (10_419_154, "123c8594a95264bf"),
 }
 
 
