@@ -583,6 +583,9 @@ TRAFFIC_PER_LAUNCH = {
     "adj_probe": (13.96e6, "e86c2f12d673d229"),
     "adj_fluid": (19.21e6, "e86c2f12d673d229"),
     "adj_bc": (5.44e6, "e86c2f12d673d229"),
+    # many-field mode (192 FP32 fields): all launches of one call, summed
+    "pfill": (279.88e6, "8058ec0ee428c269"),
+    "padj": (359.71e6, "8058ec0ee428c269"),
 }
 
 # FP64 flops per launch (DADD + DMUL + 2 x DFMA thread instructions from one
