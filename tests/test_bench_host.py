@@ -128,3 +128,16 @@ def test_cpu_samples_cover_the_whole_batch():
     order = bench.sample_order(256)
     assert sorted(order) == list(range(256))
     assert order[:20] != list(range(20))
+
+
+def test_committed_counters_match_the_committed_sources():
+    # every ncu figure the bench line can report names a profiled kernel and
+    # was taken on the kernel source as it stands (a kernel changed after its
+    # capture needs a new capture, or its figure removed)
+    import re
+    for table in (bench.TRAFFIC_PER_LAUNCH, bench.FP64_FLOPS_PER_LAUNCH):
+        for kernel, (value, h) in table.items():
+            assert re.fullmatch(r"[0-9a-f]{16}", h), (kernel, h)
+            assert value > 0, kernel
+            got, why = bench.counter(table, kernel)
+            assert got == value, (kernel, why)
